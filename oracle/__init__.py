@@ -1,0 +1,269 @@
+"""FP64 CPU oracle for the CppFlow planner core -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. It loads ``liboracle_cppflow.so`` (plain C,
+built with ``gcc -O2 -ffp-contract=off``) and marshals numpy arrays; every step
+of the computation is in ``cppflow_oracle.c``. It shares no code with the CUDA
+library: the two meet only through the seeded input arrays.
+
+Paper sections cited below: §II Problem Specification, §III-B Global discrete
+search, §III-C Levenberg-Marquardt for trajectory optimization (arXiv 2309.09102).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cppflow_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle_cppflow.so")
+
+MAXJ = 16
+OUT, NEAR, POSE, NONFINITE, PAD = 1, 2, 4, 8, 16
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(_SRC[:-2] + ".h")
+    ):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(
+            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC",
+             "-shared", _SRC, "-o", tmp, "-lm"]
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Robot(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pad_", C.c_int32)] + [
+        (f, C.c_double * MAXJ) for f in ("a", "d", "alpha", "theta0", "lo", "hi")
+    ]
+
+
+class Params(C.Structure):
+    _fields_ = [(f, C.c_double) for f in (
+        "tau_pos", "tau_rot", "near_margin", "pen_limit", "pen_pose", "jump_max",
+        "lambda0", "lambda_up", "lambda_down", "lambda_min", "lambda_max",
+        "freeze_step", "freeze_cost")] + [("lm_iters", C.c_int32), ("free_mask", C.c_uint32)]
+
+
+class Report(C.Structure):
+    _fields_ = [(f, C.c_double) for f in ("max_pos", "max_rot", "mjac", "sum_linf", "traj_len")] + [
+        (f, C.c_int32) for f in ("n_pose_fail", "n_limit_fail", "n_jump_fail", "valid")]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.c_void_p
+        sig = {
+            "orc_fk": (None, [P, P, P, P]),
+            "orc_fk_frames": (None, [P, P, P, P, P, P]),
+            "orc_quat_to_R": (None, [P, P]),
+            "orc_R_to_quat": (None, [P, P]),
+            "orc_rot_angle": (C.c_double, [P, P]),
+            "orc_fk_pose": (None, [P, P, C.c_int64, P]),
+            "orc_mask": (None, [P, P, P, P, C.c_int, C.c_int, C.c_int, P, P, P]),
+            "orc_dp_f32": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]),
+            "orc_dp_f64": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]),
+            "orc_log_rot": (None, [P, P]),
+            "orc_jacobian": (None, [P, P, P]),
+            "orc_residual": (None, [P, P, P, P]),
+            "orc_lm": (None, [P, P, P, P, C.c_int, P, P, P]),
+            "orc_check": (None, [P, P, P, P, C.c_int, P, P]),
+            "orc_plan": (C.c_int, [P, P, P, P, C.c_int, C.c_int, C.c_int, P, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(_lib, name)
+            f.restype = res
+            f.argtypes = args
+    return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_robot(a, d, alpha, lo, hi, theta0=None) -> Robot:
+    n = len(a)
+    assert 1 <= n <= MAXJ
+    r = Robot()
+    r.n = n
+    for name, v in (("a", a), ("d", d), ("alpha", alpha), ("lo", lo), ("hi", hi),
+                    ("theta0", np.zeros(n) if theta0 is None else theta0)):
+        arr = getattr(r, name)
+        for j in range(n):
+            arr[j] = float(v[j])
+    return r
+
+
+def make_params(**kw) -> Params:
+    """Defaults: 1 mm / 0.1 deg pose threshold (Table I caption), 1.5 deg near-limit
+    band and +10 / +100 node costs (§III-B), 7 deg discontinuity bound (§II)."""
+    p = Params()
+    d = dict(tau_pos=1e-3, tau_rot=math.radians(0.1), near_margin=math.radians(1.5),
+             pen_limit=10.0, pen_pose=100.0, jump_max=math.radians(7.0), lambda0=1e-3,
+             lambda_up=10.0, lambda_down=10.0, lambda_min=1e-12, lambda_max=1e12,
+             freeze_step=1e-10, freeze_cost=1e-20, lm_iters=10, free_mask=0xFFFF)
+    d.update(kw)
+    for k, v in d.items():
+        setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------- §II FK
+def fk(robot: Robot, q) -> tuple[np.ndarray, np.ndarray]:
+    q = _f64(q)
+    R = np.zeros(9)
+    p = np.zeros(3)
+    lib().orc_fk(C.byref(robot), _p(q), _p(R), _p(p))
+    return R.reshape(3, 3), p
+
+
+def fk_frames(robot: Robot, q):
+    q = _f64(q)
+    z = np.zeros((MAXJ + 1, 3))
+    o = np.zeros((MAXJ + 1, 3))
+    R = np.zeros(9)
+    p = np.zeros(3)
+    lib().orc_fk_frames(C.byref(robot), _p(q), _p(z), _p(o), _p(R), _p(p))
+    return z[: robot.n + 1], o[: robot.n + 1], R.reshape(3, 3), p
+
+
+def fk_pose(robot: Robot, q) -> np.ndarray:
+    """FP64 FK of q [N][n] -> poses [N][7] (x, y, z, qw, qx, qy, qz)."""
+    q = _f64(q).reshape(-1, robot.n)
+    out = np.zeros((q.shape[0], 7))
+    lib().orc_fk_pose(C.byref(robot), _p(q), q.shape[0], _p(out))
+    return out
+
+
+def quat_to_R(qwxyz) -> np.ndarray:
+    q = _f64(qwxyz)
+    R = np.zeros(9)
+    lib().orc_quat_to_R(_p(q), _p(R))
+    return R.reshape(3, 3)
+
+
+def R_to_quat(R) -> np.ndarray:
+    R = _f64(R).reshape(9)
+    q = np.zeros(4)
+    lib().orc_R_to_quat(_p(R), _p(q))
+    return q
+
+
+def rot_angle(Rt, R) -> float:
+    return lib().orc_rot_angle(_p(_f64(Rt).reshape(9)), _p(_f64(R).reshape(9)))
+
+
+def log_rot(M) -> np.ndarray:
+    w = np.zeros(3)
+    lib().orc_log_rot(_p(_f64(M).reshape(9)), _p(w))
+    return w
+
+
+# ---------------------------------------------------------------- §II / §III-B mask
+def mask(robot: Robot, params: Params, cand: np.ndarray, targets: np.ndarray, K: int,
+         want_err: bool = True):
+    cand = np.ascontiguousarray(cand, dtype=np.float32)
+    T, n, Kp = cand.shape
+    assert n == robot.n
+    targets = _f64(targets).reshape(T, 7)
+    m = np.zeros((T, Kp), np.uint8)
+    pen = np.zeros((T, Kp), np.float32)
+    err = np.zeros((T, Kp, 2)) if want_err else None
+    lib().orc_mask(C.byref(robot), C.byref(params), _p(cand), _p(targets), T, K, Kp,
+                   _p(m), _p(pen), _p(err))
+    return m, pen, err
+
+
+# ---------------------------------------------------------------- §III-B search
+def dp_f32(cand: np.ndarray, pen: np.ndarray, K: int):
+    cand = np.ascontiguousarray(cand, dtype=np.float32)
+    T, n, Kp = cand.shape
+    pen = np.ascontiguousarray(pen, dtype=np.float32).reshape(T, Kp)
+    sel = np.zeros(T, np.int32)
+    best = np.zeros(1, np.float32)
+    cT = np.zeros(Kp, np.float32)
+    bp = np.zeros((T, Kp), np.uint16)
+    st = lib().orc_dp_f32(_p(cand), _p(pen), T, K, Kp, n, _p(sel), _p(best), _p(cT), _p(bp))
+    return dict(status=st, sel=sel, best=best[0], cost_T=cT, bp=bp)
+
+
+def dp_f64(cand: np.ndarray, pen: np.ndarray, K: int):
+    cand = np.ascontiguousarray(cand, dtype=np.float32)
+    T, n, Kp = cand.shape
+    pen = np.ascontiguousarray(pen, dtype=np.float32).reshape(T, Kp)
+    sel = np.zeros(T, np.int32)
+    best = np.zeros(1, np.float64)
+    st = lib().orc_dp_f64(_p(cand), _p(pen), T, K, Kp, n, _p(sel), _p(best))
+    return dict(status=st, sel=sel, best=best[0])
+
+
+# ---------------------------------------------------------------- §III-C LM
+def jacobian(robot: Robot, q) -> np.ndarray:
+    J = np.zeros(6 * robot.n)
+    lib().orc_jacobian(C.byref(robot), _p(_f64(q)), _p(J))
+    return J.reshape(6, robot.n)
+
+
+def residual(robot: Robot, q, target7) -> np.ndarray:
+    e = np.zeros(6)
+    lib().orc_residual(C.byref(robot), _p(_f64(q)), _p(_f64(target7)), _p(e))
+    return e
+
+
+def lm(robot: Robot, params: Params, q_in, targets, want_hist: bool = False):
+    q_in = _f64(q_in).reshape(-1, robot.n)
+    T = q_in.shape[0]
+    targets = _f64(targets).reshape(T, 7)
+    q_out = np.zeros_like(q_in)
+    hist = np.zeros((T, params.lm_iters + 1)) if want_hist else None
+    iters = np.zeros(T, np.int32)
+    lib().orc_lm(C.byref(robot), C.byref(params), _p(q_in), _p(targets), T, _p(q_out),
+                 _p(hist), _p(iters))
+    return q_out, hist, iters
+
+
+# ---------------------------------------------------------------- §II report
+def check(robot: Robot, params: Params, q, targets):
+    q = _f64(q).reshape(-1, robot.n)
+    T = q.shape[0]
+    targets = _f64(targets).reshape(T, 7)
+    err = np.zeros((T, 2))
+    rep = Report()
+    lib().orc_check(C.byref(robot), C.byref(params), _p(q), _p(targets), T, _p(err),
+                    C.byref(rep))
+    return err, rep.as_dict()
+
+
+def plan(robot: Robot, params: Params, cand: np.ndarray, targets: np.ndarray, K: int):
+    """Whole post-generation pipeline for one request: mask, FP32 search, LM, check."""
+    cand = np.ascontiguousarray(cand, dtype=np.float32)
+    T, n, Kp = cand.shape
+    targets = _f64(targets).reshape(T, 7)
+    sel = np.zeros(T, np.int32)
+    best = np.zeros(1, np.float32)
+    q_out = np.zeros((T, n))
+    err = np.zeros((T, 2))
+    rep = Report()
+    st = lib().orc_plan(C.byref(robot), C.byref(params), _p(cand), _p(targets), T, K, Kp,
+                        _p(sel), _p(best), _p(q_out), _p(err), C.byref(rep))
+    return dict(status=st, sel=sel, best=best[0], q=q_out, err=err, report=rep.as_dict())

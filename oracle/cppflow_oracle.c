@@ -1,0 +1,594 @@
+/*
+ * cppflow_oracle.c -- plain, slow FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * Only the test-suite, the smoke check and the benchmark's CPU-baseline leg may
+ * use this file. It is written for a reader who checks it against the paper by
+ * eye: no blocking, no fusion, no reordering beyond what each definition says.
+ * Build: gcc -O2 -ffp-contract=off (no fast-math, no FMA contraction), so the
+ * FP32 DP cost path rounds exactly once per IEEE operation.
+ *
+ * Paper: "CppFlow: Generative Inverse Kinematics for Efficient and Robust
+ * Cartesian Path Planning", arXiv 2309.09102. Section tags: §II Problem
+ * Specification, §III-B Global discrete search, §III-C Levenberg-Marquardt.
+ *
+ * Parity status: every routine is pinned by a CPU test (closed forms, SciPy
+ * rotation routines, finite differences, brute-force enumeration, invariants).
+ */
+#include "cppflow_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* small 4x4 / 3x3 helpers (plain row-major loops)                           */
+/* ------------------------------------------------------------------------- */
+static void mat4_identity(double M[16]) {
+    memset(M, 0, 16 * sizeof(double));
+    M[0] = M[5] = M[10] = M[15] = 1.0;
+}
+
+static void mat4_mul(const double A[16], const double B[16], double C[16]) {
+    double T[16];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 4; ++k) s += A[4 * r + k] * B[4 * k + c];
+            T[4 * r + c] = s;
+        }
+    memcpy(C, T, sizeof(T));
+}
+
+static void rot_z(double th, double M[16]) {
+    mat4_identity(M);
+    M[0] = cos(th); M[1] = -sin(th);
+    M[4] = sin(th); M[5] = cos(th);
+}
+
+static void rot_x(double al, double M[16]) {
+    mat4_identity(M);
+    M[5] = cos(al);  M[6] = -sin(al);
+    M[9] = sin(al);  M[10] = cos(al);
+}
+
+static void trans_z(double d, double M[16]) { mat4_identity(M); M[11] = d; }
+static void trans_x(double a, double M[16]) { mat4_identity(M); M[3] = a; }
+
+/* §II: FK(q): R^d -> SE(3). Reading (the paper gives no convention): standard
+ * (distal) DH, A_j = Rz(q_j + theta0_j) Tz(d_j) Tx(a_j) Rx(alpha_j), base and
+ * tool frames are the identity. Returns A_j as a 4x4 homogeneous matrix. */
+static void dh_link(const orc_robot* r, int j, double qj, double A[16]) {
+    double M[16];
+    rot_z(qj + r->theta0[j], A);
+    trans_z(r->d[j], M);  mat4_mul(A, M, A);
+    trans_x(r->a[j], M);  mat4_mul(A, M, A);
+    rot_x(r->alpha[j], M); mat4_mul(A, M, A);
+}
+
+static void split_pose(const double M[16], double R[9], double p[3]) {
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) R[3 * r + c] = M[4 * r + c];
+        p[r] = M[4 * r + 3];
+    }
+}
+
+/* §II: T(q) = A_1 A_2 ... A_n. */
+void orc_fk(const orc_robot* r, const double* q, double R[9], double p[3]) {
+    double T[16], A[16];
+    mat4_identity(T);
+    for (int j = 0; j < r->n; ++j) {
+        dh_link(r, j, q[j], A);
+        mat4_mul(T, A, T);
+    }
+    split_pose(T, R, p);
+}
+
+/* Frames T_j = A_1..A_j for j = 0..n (T_0 = identity): z_j = third column of
+ * the rotation of T_j, o_j = its origin. Joint j (0-based) turns about z_j. */
+void orc_fk_frames(const orc_robot* r, const double* q, double z[][3], double o[][3],
+                   double R[9], double p[3]) {
+    double T[16], A[16];
+    mat4_identity(T);
+    for (int j = 0; j <= r->n; ++j) {
+        for (int c = 0; c < 3; ++c) { z[j][c] = T[4 * c + 2]; o[j][c] = T[4 * c + 3]; }
+        if (j == r->n) break;
+        dh_link(r, j, q[j], A);
+        mat4_mul(T, A, T);
+    }
+    split_pose(T, R, p);
+}
+
+/* Unit quaternion (w, x, y, z) -> rotation matrix (normalised first). */
+void orc_quat_to_R(const double qq[4], double R[9]) {
+    double nrm = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
+    double w = qq[0] / nrm, x = qq[1] / nrm, y = qq[2] / nrm, z = qq[3] / nrm;
+    R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - w * z);       R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);       R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);       R[7] = 2.0 * (y * z + w * x);       R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+/* Rotation matrix -> unit quaternion (w >= 0), by the largest-pivot branch. */
+void orc_R_to_quat(const double R[9], double q[4]) {
+    double tr = R[0] + R[4] + R[8];
+    double w, x, y, z;
+    if (tr > 0.0) {
+        double s = sqrt(tr + 1.0) * 2.0;
+        w = 0.25 * s; x = (R[7] - R[5]) / s; y = (R[2] - R[6]) / s; z = (R[3] - R[1]) / s;
+    } else if (R[0] > R[4] && R[0] > R[8]) {
+        double s = sqrt(1.0 + R[0] - R[4] - R[8]) * 2.0;
+        w = (R[7] - R[5]) / s; x = 0.25 * s; y = (R[1] + R[3]) / s; z = (R[2] + R[6]) / s;
+    } else if (R[4] > R[8]) {
+        double s = sqrt(1.0 + R[4] - R[0] - R[8]) * 2.0;
+        w = (R[2] - R[6]) / s; x = (R[1] + R[3]) / s; y = 0.25 * s; z = (R[5] + R[7]) / s;
+    } else {
+        double s = sqrt(1.0 + R[8] - R[0] - R[4]) * 2.0;
+        w = (R[3] - R[1]) / s; x = (R[2] + R[6]) / s; y = (R[5] + R[7]) / s; z = 0.25 * s;
+    }
+    if (w < 0.0) { w = -w; x = -x; y = -y; z = -z; }
+    double nrm = sqrt(w * w + x * x + y * y + z * z);
+    q[0] = w / nrm; q[1] = x / nrm; q[2] = y / nrm; q[3] = z / nrm;
+}
+
+/* §II "Pose error": the rotational error is the geodesic distance between the
+ * rotations of FK(q) and the target, i.e. the angle of E = Rt^T R, computed as
+ * atan2(|vee(E - E^T)| / 2, (tr E - 1) / 2) in [0, pi]. */
+double orc_rot_angle(const double Rt[9], const double R[9]) {
+    double E[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += Rt[3 * k + r] * R[3 * k + c];
+            E[3 * r + c] = s;
+        }
+    double vx = E[7] - E[5], vy = E[2] - E[6], vz = E[3] - E[1];
+    double s = 0.5 * sqrt(vx * vx + vy * vy + vz * vz);
+    double c = 0.5 * (E[0] + E[4] + E[8] - 1.0);
+    return atan2(s, c);
+}
+
+/* §II "Pose error": position error is the Euclidean norm of the difference. */
+void orc_pose_error(const double Rt[9], const double pt[3], const double R[9],
+                    const double p[3], double* pos, double* rot) {
+    double dx = p[0] - pt[0], dy = p[1] - pt[1], dz = p[2] - pt[2];
+    *pos = sqrt(dx * dx + dy * dy + dz * dz);
+    *rot = orc_rot_angle(Rt, R);
+}
+
+void orc_fk_pose(const orc_robot* r, const double* q, int64_t N, double* pose) {
+    for (int64_t i = 0; i < N; ++i) {
+        double R[9], p[3];
+        orc_fk(r, q + i * r->n, R, p);
+        pose[7 * i + 0] = p[0]; pose[7 * i + 1] = p[1]; pose[7 * i + 2] = p[2];
+        orc_R_to_quat(R, pose + 7 * i + 3);
+    }
+}
+
+static void target_pose(const double* t7, double Rt[9], double pt[3]) {
+    pt[0] = t7[0]; pt[1] = t7[1]; pt[2] = t7[2];
+    orc_quat_to_R(t7 + 3, Rt);
+}
+
+/* ------------------------------------------------------------------------- */
+/* §II joint limits + §III-B node costs                                      */
+/* ------------------------------------------------------------------------- */
+/* Per candidate (i, k):
+ *   NONFINITE: some joint value is not finite -> node cost +inf, no other bit.
+ *   OUT:  some q_j < lo_j or q_j > hi_j                (§II "Joint limits")
+ *   NEAR: some q_j within near_margin of a limit       (§III-B, +10 band)
+ *   POSE: position error > tau_pos or rotation error > tau_rot (§II)
+ *   pen = pen_limit * [OUT or NEAR] + pen_pose * [POSE]  (§III-B additive costs)
+ * Readings: limit comparisons are made in FP32 on the FP32 candidate against
+ * the FP32-rounded thresholds (lo, hi, lo+m, hi-m, each formed in FP64 and
+ * rounded once), so the OUT/NEAR bits are exact on any IEEE machine; a
+ * configuration outside the limits is charged like one inside the band; the
+ * pose bit takes its errors from FP64 forward kinematics of the upcast
+ * candidate. Padding lanes k in [K, Kp) get PAD and +inf. */
+void orc_mask(const orc_robot* r, const orc_params* P, const float* cand,
+              const double* targets, int T, int K, int Kp,
+              uint8_t* mask, float* pen, double* err) {
+    const int n = r->n;
+    float lo_f[ORC_MAXJ], hi_f[ORC_MAXJ], nlo_f[ORC_MAXJ], nhi_f[ORC_MAXJ];
+    for (int j = 0; j < n; ++j) {
+        lo_f[j] = (float)r->lo[j];
+        hi_f[j] = (float)r->hi[j];
+        nlo_f[j] = (float)(r->lo[j] + P->near_margin);
+        nhi_f[j] = (float)(r->hi[j] - P->near_margin);
+    }
+    for (int i = 0; i < T; ++i) {
+        double Rt[9], pt[3];
+        target_pose(targets + 7 * i, Rt, pt);
+        for (int k = 0; k < Kp; ++k) {
+            size_t o = (size_t)i * Kp + k;
+            if (k >= K) {
+                mask[o] = ORC_PAD; pen[o] = INFINITY;
+                if (err) { err[2 * o] = NAN; err[2 * o + 1] = NAN; }
+                continue;
+            }
+            float qf[ORC_MAXJ];
+            double qd[ORC_MAXJ];
+            int finite = 1;
+            for (int j = 0; j < n; ++j) {
+                qf[j] = cand[((size_t)i * n + j) * Kp + k];
+                qd[j] = (double)qf[j];
+                if (!isfinite(qf[j])) finite = 0;
+            }
+            if (!finite) {
+                mask[o] = ORC_NONFINITE; pen[o] = INFINITY;
+                if (err) { err[2 * o] = NAN; err[2 * o + 1] = NAN; }
+                continue;
+            }
+            unsigned bits = 0;
+            for (int j = 0; j < n; ++j) {
+                if (qf[j] < lo_f[j] || qf[j] > hi_f[j]) bits |= ORC_OUT;
+                if (qf[j] < nlo_f[j] || qf[j] > nhi_f[j]) bits |= ORC_NEAR;
+            }
+            double R[9], p[3], pos, rot;
+            orc_fk(r, qd, R, p);
+            orc_pose_error(Rt, pt, R, p, &pos, &rot);
+            if (pos > P->tau_pos || rot > P->tau_rot) bits |= ORC_POSE;
+            double c = 0.0;
+            if (bits & (ORC_OUT | ORC_NEAR)) c += P->pen_limit;
+            if (bits & ORC_POSE) c += P->pen_pose;
+            mask[o] = (uint8_t)bits;
+            pen[o] = (float)c;
+            if (err) { err[2 * o] = pos; err[2 * o + 1] = rot; }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* §III-B global discrete search                                             */
+/* ------------------------------------------------------------------------- */
+/* Nodes are the K candidates at each of the T waypoints; every node at step i
+ * has an edge to every node at step i+1. Objective (reading of the search's
+ * cost): the SUM over steps of the per-step L-inf joint jump
+ *   d(k, k') = max_j |q_{i+1,k',j} - q_{i,k,j}|,
+ * plus the node costs. Node costs enter relative to the cheapest node of their
+ * waypoint, r_i[k] = fl(pen_i[k] - m_i) with m_i = min_{k<K} pen_i[k] (m_i = 0
+ * when that min is +inf): a constant added to every node of one waypoint
+ * changes no path's rank, and it keeps the running FP32 cost small enough to
+ * resolve the joint jumps (a uniform +100 per waypoint would otherwise grow it
+ * to 100 T). Recurrence, evaluated literally in FP32:
+ *   C_0[k]      = r_0[k]
+ *   C_{i+1}[k'] = fl( min_k fl(C_i[k] + d(k, k')) + r_{i+1}[k'] )
+ *   bp[i+1][k'] = smallest k attaining that min (strict '<' scan from k = 0)
+ * then k_{T-1} = smallest argmin of C_{T-1}, and backtracking k_i = bp[i+1][k_{i+1}].
+ * best_cost is min_k C_{T-1}[k] (the relative cost). The max over joints uses
+ * fmaxf (a NaN term is ignored). Returns 0, or 3 when every final cost is +inf
+ * (no feasible path). */
+static float layer_min_f32(const float* pen_i, int K) {
+    float m = INFINITY;
+    for (int k = 0; k < K; ++k) m = fminf(m, pen_i[k]);
+    return isinf(m) ? 0.0f : m;
+}
+
+int orc_dp_f32(const float* cand, const float* pen, int T, int K, int Kp, int n,
+               int32_t* sel, float* best_cost, float* cost_T, uint16_t* bp_out) {
+    float* C = (float*)malloc(sizeof(float) * (size_t)Kp);
+    float* Cn = (float*)malloc(sizeof(float) * (size_t)Kp);
+    uint16_t* bp = (uint16_t*)calloc((size_t)T * Kp, sizeof(uint16_t));
+    float m0 = layer_min_f32(pen, K);
+    for (int k = 0; k < Kp; ++k) C[k] = (k < K) ? pen[k] - m0 : INFINITY;
+    for (int i = 0; i + 1 < T; ++i) {
+        const float* qa = cand + (size_t)i * n * Kp;        /* step i   */
+        const float* qb = cand + (size_t)(i + 1) * n * Kp;  /* step i+1 */
+        const float m1 = layer_min_f32(pen + (size_t)(i + 1) * Kp, K);
+        for (int kp = 0; kp < Kp; ++kp) {
+            if (kp >= K) { Cn[kp] = INFINITY; continue; }
+            float best = INFINITY;
+            int arg = 0;
+            for (int k = 0; k < K; ++k) {
+                float d = fabsf(qb[kp] - qa[k]);
+                for (int j = 1; j < n; ++j)
+                    d = fmaxf(d, fabsf(qb[(size_t)j * Kp + kp] - qa[(size_t)j * Kp + k]));
+                float v = C[k] + d;
+                if (v < best) { best = v; arg = k; }
+            }
+            Cn[kp] = best + (pen[(size_t)(i + 1) * Kp + kp] - m1);
+            bp[(size_t)(i + 1) * Kp + kp] = (uint16_t)arg;
+        }
+        float* t = C; C = Cn; Cn = t;
+    }
+    float best = INFINITY;
+    int arg = 0;
+    for (int k = 0; k < K; ++k)
+        if (C[k] < best) { best = C[k]; arg = k; }
+    sel[T - 1] = arg;
+    for (int i = T - 1; i > 0; --i) sel[i - 1] = bp[(size_t)i * Kp + sel[i]];
+    *best_cost = best;
+    if (cost_T) memcpy(cost_T, C, sizeof(float) * (size_t)Kp);
+    if (bp_out) memcpy(bp_out, bp, sizeof(uint16_t) * (size_t)T * Kp);
+    free(C); free(Cn); free(bp);
+    return isinf(best) ? 3 : 0;
+}
+
+/* The same recurrence in FP64 (used for the error report, not for indices),
+ * with the same per-waypoint relative node costs. */
+static double layer_min_f64(const float* pen_i, int K) {
+    double m = INFINITY;
+    for (int k = 0; k < K; ++k) m = fmin(m, (double)pen_i[k]);
+    return isinf(m) ? 0.0 : m;
+}
+
+int orc_dp_f64(const float* cand, const float* pen, int T, int K, int Kp, int n,
+               int32_t* sel, double* best_cost) {
+    double* C = (double*)malloc(sizeof(double) * (size_t)Kp);
+    double* Cn = (double*)malloc(sizeof(double) * (size_t)Kp);
+    int32_t* bp = (int32_t*)calloc((size_t)T * Kp, sizeof(int32_t));
+    double m0 = layer_min_f64(pen, K);
+    for (int k = 0; k < Kp; ++k) C[k] = (k < K) ? (double)pen[k] - m0 : INFINITY;
+    for (int i = 0; i + 1 < T; ++i) {
+        const float* qa = cand + (size_t)i * n * Kp;
+        const float* qb = cand + (size_t)(i + 1) * n * Kp;
+        const double m1 = layer_min_f64(pen + (size_t)(i + 1) * Kp, K);
+        for (int kp = 0; kp < K; ++kp) {
+            double best = INFINITY;
+            int arg = 0;
+            for (int k = 0; k < K; ++k) {
+                double d = fabs((double)qb[kp] - (double)qa[k]);
+                for (int j = 1; j < n; ++j)
+                    d = fmax(d, fabs((double)qb[(size_t)j * Kp + kp] - (double)qa[(size_t)j * Kp + k]));
+                double v = C[k] + d;
+                if (v < best) { best = v; arg = k; }
+            }
+            Cn[kp] = best + ((double)pen[(size_t)(i + 1) * Kp + kp] - m1);
+            bp[(size_t)(i + 1) * Kp + kp] = arg;
+        }
+        double* t = C; C = Cn; Cn = t;
+    }
+    double best = INFINITY;
+    int arg = 0;
+    for (int k = 0; k < K; ++k)
+        if (C[k] < best) { best = C[k]; arg = k; }
+    sel[T - 1] = arg;
+    for (int i = T - 1; i > 0; --i) sel[i - 1] = bp[(size_t)i * Kp + sel[i]];
+    *best_cost = best;
+    free(C); free(Cn); free(bp);
+    return isinf(best) ? 3 : 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* §III-C Levenberg-Marquardt                                                */
+/* ------------------------------------------------------------------------- */
+/* Matrix logarithm of a rotation as a rotation vector w (|w| = angle).
+ * Reading of the r_pose rotation rows: the paper subtracts roll/pitch/yaw
+ * elementwise; this oracle uses the world-frame rotation vector log(Rt R^T),
+ * which matches the geometric Jacobian and has no gimbal or wrap issue.
+ * Small angles (< 1e-6) use w = vee(M - M^T)/2 (theta/sin(theta) -> 1); angles
+ * within 1e-6 of pi take the axis from the largest diagonal of (M + I)/2. */
+void orc_log_rot(const double M[9], double w[3]) {
+    double v[3] = {M[7] - M[5], M[2] - M[6], M[3] - M[1]};
+    double s = 0.5 * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double c = 0.5 * (M[0] + M[4] + M[8] - 1.0);
+    double th = atan2(s, c);
+    if (th < 1e-6) {
+        w[0] = 0.5 * v[0]; w[1] = 0.5 * v[1]; w[2] = 0.5 * v[2];
+    } else if (th > M_PI - 1e-6) {
+        /* M ~ 2 a a^T - I: pick the column of (M + I)/2 with the largest diagonal */
+        int m = 0;
+        if (M[4] > M[0]) m = 1;
+        if (M[8] > M[3 * m + m]) m = 2;
+        double col[3];
+        for (int r = 0; r < 3; ++r) col[r] = 0.5 * (M[3 * r + m] + (r == m ? 1.0 : 0.0));
+        double nrm = sqrt(col[0] * col[0] + col[1] * col[1] + col[2] * col[2]);
+        double sgn = (col[0] * v[0] + col[1] * v[1] + col[2] * v[2]) < 0.0 ? -1.0 : 1.0;
+        for (int r = 0; r < 3; ++r) w[r] = sgn * th * col[r] / nrm;
+    } else {
+        double f = th / (2.0 * s);
+        w[0] = f * v[0]; w[1] = f * v[1]; w[2] = f * v[2];
+    }
+}
+
+/* Geometric Jacobian in the world frame, 6 x n row-major:
+ * column j = [z_j x (p_e - o_j); z_j] for revolute joint j (§III-C "kinematic
+ * Jacobian"). */
+void orc_jacobian(const orc_robot* r, const double* q, double J[]) {
+    double z[ORC_MAXJ + 1][3], o[ORC_MAXJ + 1][3], R[9], p[3];
+    const int n = r->n;
+    orc_fk_frames(r, q, z, o, R, p);
+    for (int j = 0; j < n; ++j) {
+        double dx = p[0] - o[j][0], dy = p[1] - o[j][1], dz = p[2] - o[j][2];
+        J[0 * n + j] = z[j][1] * dz - z[j][2] * dy;
+        J[1 * n + j] = z[j][2] * dx - z[j][0] * dz;
+        J[2 * n + j] = z[j][0] * dy - z[j][1] * dx;
+        J[3 * n + j] = z[j][0];
+        J[4 * n + j] = z[j][1];
+        J[5 * n + j] = z[j][2];
+    }
+}
+
+/* r_pose rows for one waypoint (§III-C), as target minus current:
+ * e = [p_t - p(q); log(R_t R(q)^T)]. */
+void orc_residual(const orc_robot* r, const double* q, const double* t7, double e[6]) {
+    double R[9], p[3], Rt[9], pt[3], M[9];
+    orc_fk(r, q, R, p);
+    target_pose(t7, Rt, pt);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += Rt[3 * a + k] * R[3 * b + k];
+            M[3 * a + b] = s;
+        }
+    e[0] = pt[0] - p[0]; e[1] = pt[1] - p[1]; e[2] = pt[2] - p[2];
+    orc_log_rot(M, e + 3);
+}
+
+static double half_sq(const double e[6]) {
+    double s = 0.0;
+    for (int a = 0; a < 6; ++a) s += e[a] * e[a];
+    return 0.5 * s;
+}
+
+/* Solve (L L^T) x = b for SPD A (n x n, row-major) by Cholesky. Returns 0 on a
+ * non-positive or non-finite pivot. */
+static int chol_solve(int n, const double* A, const double* b, double* x) {
+    double L[ORC_MAXJ * ORC_MAXJ];
+    memset(L, 0, sizeof(L));
+    for (int j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int k = 0; k < j; ++k) s -= L[j * n + k] * L[j * n + k];
+        if (!(s > 0.0) || !isfinite(s)) return 0;
+        L[j * n + j] = sqrt(s);
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = t / L[j * n + j];
+        }
+    }
+    double y[ORC_MAXJ];
+    for (int i = 0; i < n; ++i) {
+        double t = b[i];
+        for (int k = 0; k < i; ++k) t -= L[i * n + k] * y[k];
+        y[i] = t / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double t = y[i];
+        for (int k = i + 1; k < n; ++k) t -= L[k * n + i] * x[k];
+        x[i] = t / L[i * n + i];
+    }
+    return 1;
+}
+
+/* §III-C: LM on r_pose. Because each waypoint's pose residual depends on that
+ * waypoint's configuration only, J is block diagonal and every waypoint is an
+ * independent n x n problem (the paper's observation; its commented text).
+ * Per waypoint, seeded with q_in[i], lambda = lambda0, F = |e|^2 / 2:
+ *   repeat lm_iters times:
+ *     stop if F < freeze_cost
+ *     J = geometric Jacobian, columns of joints outside free_mask set to 0
+ *     solve (J^T J + lambda I) delta = J^T e     (the paper's update, with the
+ *                                                 transpose on J restored)
+ *     stop if max_j |delta_j| < freeze_step
+ *     q' = clamp(q + delta, lo, hi)              (§III-C "Joint limits")
+ *     if F(q') < F(q): accept, lambda = max(lambda / lambda_down, lambda_min)
+ *     else:            reject, lambda = min(lambda * lambda_up, lambda_max)
+ * A failed factorisation counts as a rejection. */
+void orc_lm(const orc_robot* r, const orc_params* P, const double* q_in,
+            const double* targets, int T, double* q_out, double* F_hist,
+            int32_t* iters_run) {
+    const int n = r->n;
+    const int N = P->lm_iters;
+    for (int i = 0; i < T; ++i) {
+        const double* t7 = targets + 7 * i;
+        double q[ORC_MAXJ], e[6];
+        for (int j = 0; j < n; ++j) q[j] = q_in[(size_t)i * n + j];
+        orc_residual(r, q, t7, e);
+        double F = half_sq(e);
+        double lam = P->lambda0;
+        int it = 0;
+        if (F_hist) F_hist[(size_t)i * (N + 1)] = F;
+        for (; it < N; ++it) {
+            if (F < P->freeze_cost) break;
+            double J[6 * ORC_MAXJ], A[ORC_MAXJ * ORC_MAXJ], g[ORC_MAXJ], dq[ORC_MAXJ];
+            orc_jacobian(r, q, J);
+            for (int j = 0; j < n; ++j)
+                if (!((P->free_mask >> j) & 1u))
+                    for (int a = 0; a < 6; ++a) J[a * n + j] = 0.0;
+            for (int a = 0; a < n; ++a) {
+                for (int b = 0; b < n; ++b) {
+                    double s = 0.0;
+                    for (int k = 0; k < 6; ++k) s += J[k * n + a] * J[k * n + b];
+                    A[a * n + b] = s + (a == b ? lam : 0.0);
+                }
+                double s = 0.0;
+                for (int k = 0; k < 6; ++k) s += J[k * n + a] * e[k];
+                g[a] = s;
+            }
+            int ok = chol_solve(n, A, g, dq);
+            if (ok) {
+                double mx = 0.0;
+                for (int j = 0; j < n; ++j) mx = fmax(mx, fabs(dq[j]));
+                if (mx < P->freeze_step) break;
+                double qn[ORC_MAXJ], en[6];
+                for (int j = 0; j < n; ++j) {
+                    double v = q[j] + dq[j];
+                    if (v < r->lo[j]) v = r->lo[j];
+                    if (v > r->hi[j]) v = r->hi[j];
+                    qn[j] = v;
+                }
+                orc_residual(r, qn, t7, en);
+                double Fn = half_sq(en);
+                if (Fn < F) {
+                    memcpy(q, qn, sizeof(double) * n);
+                    memcpy(e, en, sizeof(e));
+                    F = Fn;
+                    lam = fmax(lam / P->lambda_down, P->lambda_min);
+                } else {
+                    lam = fmin(lam * P->lambda_up, P->lambda_max);
+                }
+            } else {
+                lam = fmin(lam * P->lambda_up, P->lambda_max);
+            }
+            if (F_hist) F_hist[(size_t)i * (N + 1) + it + 1] = F;
+        }
+        if (F_hist)
+            for (int k = it + 1; k <= N; ++k) F_hist[(size_t)i * (N + 1) + k] = F;
+        if (iters_run) iters_run[i] = it;
+        for (int j = 0; j < n; ++j) q_out[(size_t)i * n + j] = q[j];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* §II constraints and metrics on a finished trajectory                      */
+/* ------------------------------------------------------------------------- */
+/* Pose error per waypoint (FP64), joint-limit check on the exact limits, the
+ * discontinuity bound per step (§II "Discontinuities", all joints revolute),
+ * mjac = max over steps and joints of |dq| (§III-B, steps i = 1..n-1),
+ * the summed per-step L-inf jump (the search objective), and trajectory length
+ * = sum over steps and joints of |dq| (§II). valid = every check passes. */
+void orc_check(const orc_robot* r, const orc_params* P, const double* q,
+               const double* targets, int T, double* pose_err, orc_report* rep) {
+    const int n = r->n;
+    memset(rep, 0, sizeof(*rep));
+    for (int i = 0; i < T; ++i) {
+        double R[9], p[3], Rt[9], pt[3], pos, rot;
+        orc_fk(r, q + (size_t)i * n, R, p);
+        target_pose(targets + 7 * i, Rt, pt);
+        orc_pose_error(Rt, pt, R, p, &pos, &rot);
+        if (pose_err) { pose_err[2 * i] = pos; pose_err[2 * i + 1] = rot; }
+        rep->max_pos = fmax(rep->max_pos, pos);
+        rep->max_rot = fmax(rep->max_rot, rot);
+        if (!(pos <= P->tau_pos && rot <= P->tau_rot)) rep->n_pose_fail++;
+        int out = 0;
+        for (int j = 0; j < n; ++j) {
+            double v = q[(size_t)i * n + j];
+            if (!(v >= r->lo[j] && v <= r->hi[j])) out = 1;
+        }
+        rep->n_limit_fail += out;
+        if (i + 1 < T) {
+            double linf = 0.0;
+            for (int j = 0; j < n; ++j) {
+                double dq = fabs(q[(size_t)(i + 1) * n + j] - q[(size_t)i * n + j]);
+                linf = fmax(linf, dq);
+                rep->traj_len += dq;
+            }
+            rep->mjac = fmax(rep->mjac, linf);
+            rep->sum_linf += linf;
+            if (linf > P->jump_max) rep->n_jump_fail++;
+        }
+    }
+    rep->valid = (rep->n_pose_fail == 0 && rep->n_limit_fail == 0 && rep->n_jump_fail == 0);
+}
+
+/* Mask -> FP32 search -> seed -> LM -> check, for one request. */
+int orc_plan(const orc_robot* r, const orc_params* P, const float* cand,
+             const double* targets, int T, int K, int Kp, int32_t* sel,
+             float* best_cost, double* q_out, double* pose_err, orc_report* rep) {
+    const int n = r->n;
+    uint8_t* mask = (uint8_t*)malloc((size_t)T * Kp);
+    float* pen = (float*)malloc(sizeof(float) * (size_t)T * Kp);
+    double* seed = (double*)malloc(sizeof(double) * (size_t)T * n);
+    orc_mask(r, P, cand, targets, T, K, Kp, mask, pen, 0);
+    int st = orc_dp_f32(cand, pen, T, K, Kp, n, sel, best_cost, 0, 0);
+    for (int i = 0; i < T; ++i)
+        for (int j = 0; j < n; ++j)
+            seed[(size_t)i * n + j] = (double)cand[((size_t)i * n + j) * Kp + sel[i]];
+    orc_lm(r, P, seed, targets, T, q_out, 0, 0);
+    orc_check(r, P, q_out, targets, T, pose_err, rep);
+    free(mask); free(pen); free(seed);
+    return st;
+}
