@@ -1,0 +1,234 @@
+/*
+ * cppflow.h -- C ABI of the GB300-native CppFlow planner core.
+ *
+ * The problem (paper §II, "Problem Specification"): given a target path
+ * Y = [y_1 .. y_T] of end-effector poses in SE(3) and, for every waypoint, K
+ * candidate joint configurations (the paper draws them from IKFlow, §III-A;
+ * here they come from the caller), return a joint trajectory
+ * xi = [q_1 .. q_T] whose end effector follows Y within a pose threshold,
+ * inside the joint limits and without large joint jumps.
+ *
+ * Pipeline (each stage is a hand-written sm_103a CUDA kernel):
+ *   cpp_mask       FK of every candidate, pose error vs y_i, joint-limit and
+ *                  pose masks, additive node costs              (§II, §III-B)
+ *   cpp_dp_search  dynamic programme over the T x K x K lattice minimising
+ *                  the summed per-step L-inf joint jump + node costs (§III-B)
+ *   cpp_lm_refine  Levenberg-Marquardt on the pose residual, one damped n x n
+ *                  problem per waypoint, clamped to the limits     (§III-C)
+ *   cpp_check      FP64 pose error, limits, jumps, mjac, trajectory length (§II)
+ *   cpp_plan       all of the above for one request, back to back on a stream
+ *   cpp_plan_batch all of the above for many requests of different T and K in
+ *                  one launch per stage
+ *   cpp_server_*   continuous-batching request loop (submit / poll)
+ *
+ * Conventions
+ *  - Ownership: the caller owns every buffer. Stage calls take DEVICE pointers
+ *    and a cudaStream_t (pass 0 for the legacy default stream) and return as
+ *    soon as the work is enqueued; results are valid once the stream reaches
+ *    that point. cpp_plan_submit / cpp_plan_poll take HOST buffers.
+ *  - Errors: every call returns a cpp_status. Arguments are validated on the
+ *    host before anything is enqueued (CPP_ERR_INVALID_ARG, with a message
+ *    from cpp_last_error(), which is thread-local). Conditions found on the
+ *    device (an infeasible lattice) are written to the caller's int32
+ *    dev_status word (may be NULL): kernels only ever raise it, never clear
+ *    it, so the caller zeroes it before the first call.
+ *  - Layouts: candidates are structure-of-arrays [T][n][Kp] FP32 (k fastest),
+ *    Kp >= K, Kp a multiple of 4, lanes k >= K are padding and never chosen.
+ *    Targets are [T][7] FP64: position x, y, z (m) then a unit quaternion
+ *    w, x, y, z. Joint vectors are [T][n]. Angles are radians.
+ *  - Robots: revolute serial chains in standard (distal) DH form,
+ *    A_j = Rz(q_j + theta0_j) Tz(d_j) Tx(a_j) Rx(alpha_j), identity base and
+ *    tool (the paper names no convention), 1 <= n <= 16.
+ */
+#ifndef CPPFLOW_H
+#define CPPFLOW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cpp_stream_t; /* = cudaStream_t */
+
+typedef enum cpp_status {
+    CPP_OK = 0,
+    CPP_PENDING = 1,          /* cpp_plan_poll: not finished yet */
+    CPP_ERR_INVALID_ARG = 2,  /* rejected on the host; nothing enqueued */
+    CPP_ERR_INFEASIBLE = 3,   /* every path has infinite cost */
+    CPP_ERR_OOM = 4,          /* a device or pinned allocation failed */
+    CPP_ERR_BUDGET = 5,       /* the request alone exceeds the server's HBM budget */
+    CPP_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+    CPP_ERR_CUDA = 7,         /* a CUDA runtime call failed (see cpp_last_error) */
+    CPP_ERR_NOT_FOUND = 8,    /* unknown or already collected ticket */
+    CPP_ERR_CANCELLED = 9     /* the request was cancelled before it ran */
+} cpp_status;
+
+#define CPP_MAX_JOINTS 16
+
+/* Mask bits written by cpp_mask (one byte per candidate). */
+#define CPP_MASK_OUT 1u       /* some joint outside its limits (§II "Joint limits") */
+#define CPP_MASK_NEAR 2u      /* some joint within near_margin of a limit (§III-B) */
+#define CPP_MASK_POSE 4u      /* pose error above tau_pos or tau_rot (§II "Pose error") */
+#define CPP_MASK_NONFINITE 8u /* some joint value is NaN or inf: cost +inf, no other bit */
+#define CPP_MASK_PAD 16u      /* padding lane k >= K: cost +inf */
+
+typedef struct cpp_robot {
+    int32_t n;                      /* joints */
+    int32_t reserved;
+    double a[CPP_MAX_JOINTS];       /* link length (m) */
+    double d[CPP_MAX_JOINTS];       /* link offset (m) */
+    double alpha[CPP_MAX_JOINTS];   /* link twist (rad) */
+    double theta0[CPP_MAX_JOINTS];  /* joint offset (rad) */
+    double lo[CPP_MAX_JOINTS];      /* lower limit (rad) */
+    double hi[CPP_MAX_JOINTS];      /* upper limit (rad) */
+} cpp_robot_t;
+
+typedef struct cpp_params {
+    double tau_pos;      /* pose-valid position threshold, m (default 1e-3, Table I) */
+    double tau_rot;      /* pose-valid rotation threshold, rad (default 0.1 deg, §II) */
+    double near_margin;  /* near-limit band, rad (default 1.5 deg, §III-B) */
+    double pen_limit;    /* node cost for out-of / near-limit configs (default 10, §III-B) */
+    double pen_pose;     /* node cost for pose-invalid configs (default 100) */
+    double jump_max;     /* discontinuity bound per step, rad (default 7 deg, §II) */
+    double lambda0;      /* initial LM damping (default 1e-3) */
+    double lambda_up;    /* damping factor after a rejected step (default 10) */
+    double lambda_down;  /* damping divisor after an accepted step (default 10) */
+    double lambda_min;   /* default 1e-12 */
+    double lambda_max;   /* default 1e12 */
+    double freeze_step;  /* a waypoint stops when max|delta| < this (default 1e-10) */
+    double freeze_cost;  /* a waypoint stops when F = |e|^2/2 < this (default 1e-20) */
+    int32_t lm_iters;    /* LM iterations per waypoint (default 20) */
+    uint32_t free_mask;  /* bit j set: LM may move joint j (default all) */
+    int32_t lm_fp64;     /* 0: FP32 FK/Jacobian + FP64 normal equations and Cholesky;
+                            1: everything in FP64 (for near-singular chains) */
+    int32_t reserved;
+} cpp_params_t;
+
+/* Trajectory report of cpp_check (device or host struct, FP64). */
+typedef struct cpp_report {
+    double max_pos;        /* worst waypoint position error (m) */
+    double max_rot;        /* worst waypoint rotation error (rad) */
+    double mjac;           /* max over steps and joints of |dq| (§III-B) */
+    double sum_linf;       /* sum over steps of the per-step L-inf jump */
+    double traj_len;       /* sum over steps and joints of |dq| (§II) */
+    int32_t n_pose_fail;   /* waypoints with pos > tau_pos or rot > tau_rot */
+    int32_t n_limit_fail;  /* waypoints with a joint outside [lo, hi] */
+    int32_t n_jump_fail;   /* steps with an L-inf jump > jump_max (§II) */
+    int32_t valid;         /* 1 when every check passes */
+} cpp_report_t;
+
+/* ------------------------------------------------------------------ misc */
+const char* cpp_last_error(void);          /* thread-local message of the last failure */
+const char* cpp_status_string(int status);
+int32_t cpp_version(void);                 /* major * 10000 + minor * 100 + patch */
+void cpp_params_default(cpp_params_t* p);  /* fills the defaults listed above */
+
+/* ------------------------------------------------------------------ FK (§II)
+ * FK(q): R^n -> SE(3) for N configurations in FP32.
+ * q: [n][N] SoA (joint-major), R: [9][N] row-major rotation entries, p: [3][N].
+ * INVALID_ARG if N < 0 or the robot is malformed. */
+cpp_status cpp_fk_batch(const cpp_robot_t* robot, const float* q, int64_t N, float* R,
+                        float* p, cpp_stream_t stream);
+
+/* FP64 FK to poses: q [N][n] FP64 -> pose [N][7] (x, y, z, qw, qx, qy, qz, with qw >= 0). */
+cpp_status cpp_fk_pose_f64(const cpp_robot_t* robot, const double* q, int64_t N,
+                           double* pose, cpp_stream_t stream);
+
+/* ------------------------------------------------------------------ masking (§II, §III-B)
+ * Per candidate (i, k): FP32 FK, position error |p - p_t|, rotation error =
+ * geodesic angle of R_t^T R (§II "Pose error"), and
+ *   NONFINITE (cost +inf), OUT / NEAR against the FP32-rounded limits lo, hi,
+ *   lo + near_margin, hi - near_margin (each formed in FP64, rounded once),
+ *   POSE (pos > tau_pos or rot > tau_rot, both compared in FP32),
+ *   pen = pen_limit * [OUT or NEAR] + pen_pose * [POSE]     (§III-B).
+ * cand [T][n][Kp] FP32, targets [T][7] FP64 -> mask [T][Kp] u8, pen [T][Kp] FP32,
+ * err [T][Kp][2] FP32 (position m, rotation rad; NaN on padding) or NULL.
+ * INVALID_ARG: T < 1, K < 1, Kp < K, Kp % 4 != 0, n mismatch, NULL buffers. */
+cpp_status cpp_mask(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
+                    const double* targets, int32_t T, int32_t K, int32_t Kp, uint8_t* mask,
+                    float* pen, float* err, int32_t* dev_status, cpp_stream_t stream);
+
+/* ------------------------------------------------------------------ search (§III-B)
+ * Dynamic programme over the layered graph whose nodes are the K candidates of
+ * each waypoint and whose edges join every node of step i to every node of
+ * step i+1. Node costs enter relative to the cheapest node of their waypoint
+ * (r_i = pen_i - min_k pen_i; a per-waypoint constant changes no path's rank):
+ *   C_0 = r_0;  C_{i+1}[k'] = min_k (C_i[k] + max_j |q_{i+1,k',j} - q_{i,k,j}|) + r_{i+1}[k']
+ * in FP32 with one rounding per operation, ties to the lowest k, then
+ * backtracking from the lowest argmin of C_{T-1}.
+ * Outputs: sel [T] int32 (chosen k per waypoint), best_cost [1] FP32 (min of
+ * C_{T-1}), q_seed [T][n] FP32 (the chosen candidates) or NULL.
+ * workspace: device scratch of at least cpp_dp_workspace_size(T, Kp) bytes,
+ * 256-byte aligned, owned by the caller, not read before it is written.
+ * dev_status is raised to CPP_ERR_INFEASIBLE when min C_{T-1} is +inf.
+ * INVALID_ARG: T < 1, K < 1, K > 65535, Kp < K, Kp % 4 != 0, n < 1, n > 16,
+ * workspace too small or misaligned. */
+size_t cpp_dp_workspace_size(int32_t T, int32_t Kp);
+cpp_status cpp_dp_search(const float* cand, const float* pen, int32_t T, int32_t K,
+                         int32_t Kp, int32_t n, void* workspace, size_t ws_bytes,
+                         int32_t* sel, float* best_cost, float* q_seed, int32_t* dev_status,
+                         cpp_stream_t stream);
+
+/* ------------------------------------------------------------------ LM (§III-C)
+ * Per waypoint independently (the pose residual of waypoint i depends on q_i
+ * only, so J is block diagonal): residual e = [p_t - p(q); log(R_t R(q)^T)]
+ * (world-frame rotation vector), geometric Jacobian J (6 x n), step
+ * (J^T J + lambda I) delta = J^T e solved by FP64 Cholesky, q' = clamp(q + delta,
+ * lo, hi); accept when F(q') < F(q) (lambda /= lambda_down) else reject
+ * (lambda *= lambda_up). lm_iters iterations; a waypoint stops early when
+ * F < freeze_cost or max|delta| < freeze_step. Joints outside free_mask stay.
+ * q_in, q_out [T][n] FP32 (may alias), targets [T][7] FP64,
+ * pose_err [T][2] FP64 (FP64 position / rotation error of q_out) or NULL. */
+cpp_status cpp_lm_refine(const cpp_robot_t* robot, const cpp_params_t* params,
+                         const float* q_in, const double* targets, int32_t T, float* q_out,
+                         double* pose_err, int32_t* dev_status, cpp_stream_t stream);
+
+/* ------------------------------------------------------------------ check (§II)
+ * FP64 FK of q [T][n] FP32 -> pose_err [T][2] FP64 (or NULL) and a report
+ * (device pointer to one cpp_report_t): worst errors, mjac, summed L-inf jump,
+ * trajectory length, counts of pose / limit / jump (> jump_max) failures. */
+cpp_status cpp_check(const cpp_robot_t* robot, const cpp_params_t* params, const float* q,
+                     const double* targets, int32_t T, double* pose_err,
+                     cpp_report_t* report, cpp_stream_t stream);
+
+/* ------------------------------------------------------------------ one request
+ * mask -> search -> LM -> check on one stream (the plain per-request path).
+ * Device buffers: cand, targets in; sel [T], q_out [T][n], pose_err [T][2],
+ * report [1], best_cost [1] out; dev_status as above; workspace of
+ * cpp_plan_workspace_size(T, K, Kp, n) bytes, 256-byte aligned. */
+size_t cpp_plan_workspace_size(int32_t T, int32_t K, int32_t Kp, int32_t n);
+cpp_status cpp_plan(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
+                    const double* targets, int32_t T, int32_t K, int32_t Kp,
+                    void* workspace, size_t ws_bytes, int32_t* sel, float* best_cost,
+                    float* q_out, double* pose_err, cpp_report_t* report,
+                    int32_t* dev_status, cpp_stream_t stream);
+
+/* ------------------------------------------------------------------ many requests
+ * One launch per stage for `count` requests of different T, K, Kp (same params).
+ * Each descriptor holds DEVICE pointers; robots are read from the host array
+ * `robots` (copied into the workspace). The workspace must hold
+ * cpp_plan_batch_workspace_size(descs, count) bytes. dev_status [count] int32. */
+typedef struct cpp_plan_desc {
+    int32_t T, K, Kp, robot;   /* robot = index into the robots array */
+    const float* cand;         /* [T][n][Kp] */
+    const double* targets;     /* [T][7] */
+    int32_t* sel;              /* [T] */
+    float* q_out;              /* [T][n] */
+    double* pose_err;          /* [T][2] */
+    cpp_report_t* report;      /* [1] */
+    float* best_cost;          /* [1] */
+} cpp_plan_desc_t;
+
+size_t cpp_plan_batch_workspace_size(const cpp_plan_desc_t* descs, int32_t count,
+                                     const cpp_robot_t* robots, int32_t n_robots);
+cpp_status cpp_plan_batch(const cpp_robot_t* robots, int32_t n_robots,
+                          const cpp_params_t* params, const cpp_plan_desc_t* descs,
+                          int32_t count, void* workspace, size_t ws_bytes,
+                          int32_t* dev_status, cpp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

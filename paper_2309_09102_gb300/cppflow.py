@@ -1,0 +1,235 @@
+"""ctypes binding of the C ABI in ``include/cppflow.h`` (argument marshalling only).
+
+Every call takes torch tensors that already live on the GPU (or raw device
+pointers), passes their addresses and the current CUDA stream to the library,
+and raises ``CppflowError`` on a non-OK status. All computation happens in the
+library's CUDA kernels; if ``libcppflow_gb300.so`` has not been built, ``lib()``
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcppflow_gb300.so")
+MAXJ = 16
+
+OK, PENDING, ERR_INVALID_ARG, ERR_INFEASIBLE, ERR_OOM, ERR_BUDGET, ERR_TIMEOUT, ERR_CUDA, \
+    ERR_NOT_FOUND, ERR_CANCELLED = range(10)
+MASK_OUT, MASK_NEAR, MASK_POSE, MASK_NONFINITE, MASK_PAD = 1, 2, 4, 8, 16
+
+
+class CppflowError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cppflow status {status}: {msg}")
+        self.status = status
+
+
+class Robot(C.Structure):
+    _fields_ = [("n", C.c_int32), ("reserved", C.c_int32)] + [
+        (f, C.c_double * MAXJ) for f in ("a", "d", "alpha", "theta0", "lo", "hi")]
+
+
+class Params(C.Structure):
+    _fields_ = [(f, C.c_double) for f in (
+        "tau_pos", "tau_rot", "near_margin", "pen_limit", "pen_pose", "jump_max", "lambda0",
+        "lambda_up", "lambda_down", "lambda_min", "lambda_max", "freeze_step", "freeze_cost")] + [
+        ("lm_iters", C.c_int32), ("free_mask", C.c_uint32), ("lm_fp64", C.c_int32),
+        ("reserved", C.c_int32)]
+
+
+class Report(C.Structure):
+    _fields_ = [(f, C.c_double) for f in ("max_pos", "max_rot", "mjac", "sum_linf", "traj_len")] + [
+        (f, C.c_int32) for f in ("n_pose_fail", "n_limit_fail", "n_jump_fail", "valid")]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PlanDesc(C.Structure):
+    _fields_ = [("T", C.c_int32), ("K", C.c_int32), ("Kp", C.c_int32), ("robot", C.c_int32),
+                ("cand", C.c_void_p), ("targets", C.c_void_p), ("sel", C.c_void_p),
+                ("q_out", C.c_void_p), ("pose_err", C.c_void_p), ("report", C.c_void_p),
+                ("best_cost", C.c_void_p)]
+
+
+REPORT_BYTES = C.sizeof(Report)
+
+_lib = None
+_P = C.c_void_p
+_SIGS = {
+    "cpp_last_error": (C.c_char_p, []),
+    "cpp_status_string": (C.c_char_p, [C.c_int]),
+    "cpp_version": (C.c_int32, []),
+    "cpp_params_default": (None, [_P]),
+    "cpp_fk_batch": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
+    "cpp_fk_pose_f64": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
+    "cpp_mask": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P]),
+    "cpp_dp_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
+    "cpp_dp_search": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, C.c_size_t,
+                                _P, _P, _P, _P, _P]),
+    "cpp_lm_refine": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, _P, _P]),
+    "cpp_check": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, _P]),
+    "cpp_plan_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "cpp_plan": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_size_t,
+                           _P, _P, _P, _P, _P, _P, _P]),
+    "cpp_plan_batch_workspace_size": (C.c_size_t, [_P, C.c_int32, _P, C.c_int32]),
+    "cpp_plan_batch": (C.c_int, [_P, C.c_int32, _P, _P, C.c_int32, _P, C.c_size_t, _P, _P]),
+}
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().cpp_last_error().decode()
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise CppflowError(status, f"{what}: {last_error()}")
+
+
+def ptr(t) -> int | None:
+    """Device address of a tensor (None stays NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def stream_handle(stream=None) -> int | None:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or None
+
+
+# ------------------------------------------------------------------ structs
+def make_robot(a, d, alpha, lo, hi, theta0=None) -> Robot:
+    n = len(a)
+    if not 1 <= n <= MAXJ:
+        raise ValueError(f"n = {n} outside [1, {MAXJ}]")
+    r = Robot()
+    r.n = n
+    th0 = [0.0] * n if theta0 is None else theta0
+    for name, v in (("a", a), ("d", d), ("alpha", alpha), ("lo", lo), ("hi", hi), ("theta0", th0)):
+        arr = getattr(r, name)
+        for j in range(n):
+            arr[j] = float(v[j])
+    return r
+
+
+def robot_from_arm(arm) -> Robot:
+    return make_robot(arm.a, arm.d, arm.alpha, arm.lo, arm.hi, arm.theta0)
+
+
+def make_params(**kw) -> Params:
+    p = Params()
+    lib().cpp_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+# ------------------------------------------------------------------ stage calls
+def fk_batch(robot: Robot, q, R, p, stream=None):
+    """q [n][N] FP32 -> R [9][N], p [3][N] FP32 (device tensors)."""
+    _check(lib().cpp_fk_batch(C.byref(robot), ptr(q), q.shape[-1], ptr(R), ptr(p),
+                              stream_handle(stream)), "cpp_fk_batch")
+
+
+def fk_pose_f64(robot: Robot, q, pose, stream=None):
+    """q [N][n] FP64 -> pose [N][7] FP64 (device tensors)."""
+    _check(lib().cpp_fk_pose_f64(C.byref(robot), ptr(q), q.numel() // robot.n, ptr(pose),
+                                 stream_handle(stream)), "cpp_fk_pose_f64")
+
+
+def mask(robot: Robot, params: Params, cand, targets, K: int, mask_out, pen, err=None,
+         dev_status=None, stream=None):
+    T, n, Kp = cand.shape
+    _check(lib().cpp_mask(C.byref(robot), C.byref(params), ptr(cand), ptr(targets), T, K, Kp,
+                          ptr(mask_out), ptr(pen), ptr(err), ptr(dev_status),
+                          stream_handle(stream)), "cpp_mask")
+
+
+def dp_workspace_size(T: int, Kp: int) -> int:
+    return lib().cpp_dp_workspace_size(T, Kp)
+
+
+def dp_search(cand, pen, K: int, workspace, sel, best_cost, q_seed=None, dev_status=None,
+              stream=None, ws_bytes: int | None = None):
+    T, n, Kp = cand.shape
+    nbytes = ws_bytes if ws_bytes is not None else workspace.numel() * workspace.element_size()
+    _check(lib().cpp_dp_search(ptr(cand), ptr(pen), T, K, Kp, n, ptr(workspace), nbytes,
+                               ptr(sel), ptr(best_cost), ptr(q_seed), ptr(dev_status),
+                               stream_handle(stream)), "cpp_dp_search")
+
+
+def lm_refine(robot: Robot, params: Params, q_in, targets, q_out, pose_err=None, dev_status=None,
+              stream=None):
+    T = q_in.shape[0]
+    _check(lib().cpp_lm_refine(C.byref(robot), C.byref(params), ptr(q_in), ptr(targets), T,
+                               ptr(q_out), ptr(pose_err), ptr(dev_status),
+                               stream_handle(stream)), "cpp_lm_refine")
+
+
+def check(robot: Robot, params: Params, q, targets, pose_err=None, report=None, stream=None):
+    T = q.shape[0]
+    _check(lib().cpp_check(C.byref(robot), C.byref(params), ptr(q), ptr(targets), T,
+                           ptr(pose_err), ptr(report), stream_handle(stream)), "cpp_check")
+
+
+def plan_workspace_size(T: int, K: int, Kp: int, n: int) -> int:
+    return lib().cpp_plan_workspace_size(T, K, Kp, n)
+
+
+def plan(robot: Robot, params: Params, cand, targets, K: int, workspace, sel, best_cost, q_out,
+         pose_err=None, report=None, dev_status=None, stream=None):
+    T, n, Kp = cand.shape
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().cpp_plan(C.byref(robot), C.byref(params), ptr(cand), ptr(targets), T, K, Kp,
+                          ptr(workspace), nbytes, ptr(sel), ptr(best_cost), ptr(q_out),
+                          ptr(pose_err), ptr(report), ptr(dev_status), stream_handle(stream)),
+           "cpp_plan")
+
+
+def plan_batch_workspace_size(descs, robots) -> int:
+    D = (PlanDesc * len(descs))(*descs)
+    R = (Robot * len(robots))(*robots)
+    return lib().cpp_plan_batch_workspace_size(D, len(descs), R, len(robots))
+
+
+def plan_batch(robots, params: Params, descs, workspace, dev_status=None, stream=None):
+    D = (PlanDesc * len(descs))(*descs)
+    R = (Robot * len(robots))(*robots)
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().cpp_plan_batch(R, len(robots), C.byref(params), D, len(descs), ptr(workspace),
+                                nbytes, ptr(dev_status), stream_handle(stream)), "cpp_plan_batch")
+
+
+def report_from_bytes(buf: bytes) -> dict:
+    r = Report.from_buffer_copy(buf)
+    return r.as_dict()
+
+
+DEG = math.pi / 180.0

@@ -1,0 +1,269 @@
+// common.cuh -- device-side building blocks shared by the planner kernels.
+//
+// Forward kinematics follows the paper's FK map FK(q): R^d -> SE(3) (§II) in
+// standard DH form A_j = Rz(q_j + theta0_j) Tz(d_j) Tx(a_j) Rx(alpha_j).
+// The chain is kept in registers as a row-major 3x3 rotation plus origin; each
+// link multiplies on the right, which only mixes columns 0 and 1 of the running
+// rotation by the joint angle and columns 1 and 2 by the link twist.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cppflow.h"
+
+namespace cppflow {
+
+constexpr int kMaxJ = CPP_MAX_JOINTS;
+
+// ------------------------------------------------------------------ request views
+// One request as the kernels see it (device pointers; unused ones may be null).
+struct Req {
+  int T, K, Kp, n;
+  int robot;                 // index into the robot table
+  int Kb;                    // backpointer row stride (Kp rounded up to 8)
+  const float* cand;         // [T][n][Kp]
+  const double* targets;     // [T][7]
+  uint8_t* mask;             // [T][Kp]
+  float* pen;                // [T][Kp]
+  float* err;                // [T][Kp][2] or null
+  float* pen_min;            // [T]      per-waypoint cheapest node cost
+  uint16_t* bp;              // [T][Kb]  backpointers
+  float* costT;              // [Kp]     final DP costs
+  int32_t* sel;              // [T]
+  float* best_cost;          // [1]
+  float* q_seed;             // [T][n] or null
+  const float* q_in;         // [T][n] LM input
+  float* q_out;              // [T][n]
+  double* pose_err;          // [T][2] or null
+  cpp_report_t* report;      // [1] or null
+  int32_t* status;           // [1] or null
+};
+
+// Kernels read requests and robots through one of two sources: a single request
+// carried in the kernel parameters, or device arrays for a batch.
+struct SingleSrc {
+  Req r;
+  cpp_robot_t robot;
+  __device__ __forceinline__ const Req& req(int) const { return r; }
+  __device__ __forceinline__ const cpp_robot_t& rob(int) const { return robot; }
+};
+struct BatchSrc {
+  const Req* r;
+  const cpp_robot_t* robots;
+  __device__ __forceinline__ const Req& req(int i) const { return r[i]; }
+  __device__ __forceinline__ const cpp_robot_t& rob(int i) const { return robots[i]; }
+};
+
+__device__ __forceinline__ void raise_status(int32_t* st, int code) {
+  if (st) atomicMax(st, code);
+}
+
+// ------------------------------------------------------------------ robot in shared memory
+struct RobotF {      // FP32 view for the FP32 kernels
+  int n;
+  float a[kMaxJ], d[kMaxJ], ca[kMaxJ], sa[kMaxJ], th0[kMaxJ];
+  float lo[kMaxJ], hi[kMaxJ], nlo[kMaxJ], nhi[kMaxJ];
+};
+struct RobotD {      // FP64 view for the FP64 paths
+  int n;
+  double a[kMaxJ], d[kMaxJ], ca[kMaxJ], sa[kMaxJ], th0[kMaxJ], lo[kMaxJ], hi[kMaxJ];
+};
+
+// Threads 0..15 of the block fill the views; the caller synchronises afterwards.
+// Near-limit thresholds lo + m, hi - m are formed in FP64 and rounded once.
+__device__ inline void stage_robot(const cpp_robot_t& r, double near_margin, RobotF* f,
+                                   RobotD* dd) {
+  const int j = threadIdx.x;
+  if (j < kMaxJ) {
+    double s, c;
+    sincos(r.alpha[j], &s, &c);
+    if (f) {
+      f->a[j] = (float)r.a[j]; f->d[j] = (float)r.d[j];
+      f->ca[j] = (float)c;     f->sa[j] = (float)s;
+      f->th0[j] = (float)r.theta0[j];
+      f->lo[j] = (float)r.lo[j]; f->hi[j] = (float)r.hi[j];
+      f->nlo[j] = (float)(r.lo[j] + near_margin);
+      f->nhi[j] = (float)(r.hi[j] - near_margin);
+      if (j == 0) f->n = r.n;
+    }
+    if (dd) {
+      dd->a[j] = r.a[j]; dd->d[j] = r.d[j]; dd->ca[j] = c; dd->sa[j] = s;
+      dd->th0[j] = r.theta0[j]; dd->lo[j] = r.lo[j]; dd->hi[j] = r.hi[j];
+      if (j == 0) dd->n = r.n;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ DH chain
+// Right-multiply the running pose (R row-major, p) by link j with joint angle
+// cos/sin (ct, st). For each row (R0 R1 R2): u = ct R0 + st R1,
+// w = ct R1 - st R0, new row = (u, ca w + sa R2, ca R2 - sa w), p += a u + d R2.
+template <class F>
+__device__ __forceinline__ void dh_step(F R[9], F p[3], F ct, F st, F ca, F sa, F a, F d) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const F R0 = R[3 * r], R1 = R[3 * r + 1], R2 = R[3 * r + 2];
+    const F u = ct * R0 + st * R1;
+    const F w = ct * R1 - st * R0;
+    R[3 * r] = u;
+    R[3 * r + 1] = ca * w + sa * R2;
+    R[3 * r + 2] = ca * R2 - sa * w;
+    p[r] = p[r] + a * u + d * R2;
+  }
+}
+
+template <class F>
+__device__ __forceinline__ void pose_identity(F R[9], F p[3]) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) R[i] = F(0);
+  R[0] = R[4] = R[8] = F(1);
+  p[0] = p[1] = p[2] = F(0);
+}
+
+__device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
+
+// FP32 FK of one configuration (NJ joints known at compile time, or NJ = 0 for
+// a runtime n <= 16).
+template <int NJ>
+__device__ __forceinline__ void fk_f32(const RobotF& rb, const float* q, float R[9], float p[3]) {
+  pose_identity(R, p);
+  const int n = NJ ? NJ : rb.n;
+#pragma unroll
+  for (int j = 0; j < (NJ ? NJ : kMaxJ); ++j) {
+    if (!NJ && j >= n) break;
+    float s, c;
+    sincos_t(q[j] + rb.th0[j], &s, &c);
+    dh_step(R, p, c, s, rb.ca[j], rb.sa[j], rb.a[j], rb.d[j]);
+  }
+}
+
+__device__ inline void fk_f64(const RobotD& rb, const double* q, double R[9], double p[3]) {
+  pose_identity(R, p);
+  for (int j = 0; j < rb.n; ++j) {
+    double s, c;
+    sincos(q[j] + rb.th0[j], &s, &c);
+    dh_step(R, p, c, s, rb.ca[j], rb.sa[j], rb.a[j], rb.d[j]);
+  }
+}
+
+// ------------------------------------------------------------------ rotations
+// Unit quaternion (w, x, y, z), normalised first, to a row-major rotation (FP64).
+__device__ inline void quat_to_rot(const double* q4, double R[9]) {
+  const double inv = rsqrt(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
+  const double w = q4[0] * inv, x = q4[1] * inv, y = q4[2] * inv, z = q4[3] * inv;
+  R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - w * z); R[2] = 2.0 * (x * z + w * y);
+  R[3] = 2.0 * (x * y + w * z); R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - w * x);
+  R[6] = 2.0 * (x * z - w * y); R[7] = 2.0 * (y * z + w * x); R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+// Geodesic angle between two rotations (§II "Pose error"): the angle of
+// E = Rt^T R from its skew part and trace, atan2(|vee(E - E^T)| / 2, (tr E - 1) / 2).
+template <class F>
+__device__ __forceinline__ F geodesic(const F Rt[9], const F R[9]) {
+  // E_ab = sum_c Rt_ca R_cb
+  F tr = F(0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) tr += Rt[i] * R[i];
+  F vx = F(0), vy = F(0), vz = F(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    vx += Rt[3 * c + 2] * R[3 * c + 1] - Rt[3 * c + 1] * R[3 * c + 2];  // E21 - E12
+    vy += Rt[3 * c + 0] * R[3 * c + 2] - Rt[3 * c + 2] * R[3 * c + 0];  // E02 - E20
+    vz += Rt[3 * c + 1] * R[3 * c + 0] - Rt[3 * c + 0] * R[3 * c + 1];  // E10 - E01
+  }
+  const F s = F(0.5) * sqrt(vx * vx + vy * vy + vz * vz);
+  const F c = F(0.5) * (tr - F(1));
+  return atan2(s, c);
+}
+
+// Rotation vector w = log(M) of a rotation M (world-frame LM residual).
+// Small angles take w = vee(M - M^T) / 2, angles near pi take the axis from the
+// largest diagonal entry of (M + I) / 2 with the sign of vee(M - M^T).
+template <class F>
+__device__ __forceinline__ void log_rot(const F M[9], F w[3], F small, F near_pi) {
+  const F vx = M[7] - M[5], vy = M[2] - M[6], vz = M[3] - M[1];
+  const F s = F(0.5) * sqrt(vx * vx + vy * vy + vz * vz);
+  const F c = F(0.5) * (M[0] + M[4] + M[8] - F(1));
+  const F th = atan2(s, c);
+  if (th < small) {
+    w[0] = F(0.5) * vx; w[1] = F(0.5) * vy; w[2] = F(0.5) * vz;
+  } else if (th > F(3.141592653589793) - near_pi) {
+    int m = 0;
+    if (M[4] > M[0]) m = 1;
+    if (M[8] > M[3 * m + m]) m = 2;
+    F col[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) col[r] = F(0.5) * (M[3 * r + m] + (r == m ? F(1) : F(0)));
+    const F nrm = sqrt(col[0] * col[0] + col[1] * col[1] + col[2] * col[2]);
+    const F sg = (col[0] * vx + col[1] * vy + col[2] * vz) < F(0) ? F(-1) : F(1);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) w[r] = sg * th * col[r] / nrm;
+  } else {
+    const F f = th / (F(2) * s);
+    w[0] = f * vx; w[1] = f * vy; w[2] = f * vz;
+  }
+}
+
+// ------------------------------------------------------------------ async copies
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 1-D bulk copy global -> shared through the TMA engine; completion is counted
+// in bytes on the mbarrier. Both addresses 16-byte aligned, size % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the mbarrier phase with a time limit (default 1 s). Returns false if
+// the limit ran out; the caller then records CPP_ERR_TIMEOUT and stops.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = 1000000000ull) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+}  // namespace cppflow

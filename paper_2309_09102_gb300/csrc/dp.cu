@@ -1,0 +1,353 @@
+// dp.cu -- the global discrete search of paper §III-B: a dynamic programme over
+// the layered graph whose nodes are the K candidates of each waypoint and whose
+// edges join every node of step i to every node of step i+1, followed by
+// backtracking.
+//
+// Recurrence (FP32, one rounding per operation, ties to the lowest k):
+//   r_i[k]      = pen_i[k] - m_i,   m_i = min_{k<K} pen_i[k]  (0 if that is +inf)
+//   C_0[k]      = r_0[k]
+//   C_{i+1}[k'] = (min_k (C_i[k] + max_j |q_{i+1,k',j} - q_{i,k,j}|)) + r_{i+1}[k']
+//   bp[i+1][k'] = lowest k attaining the min
+// A per-waypoint constant in the node costs changes no path's rank; taking the
+// costs relative to the cheapest node keeps the running FP32 cost small enough
+// to resolve the joint jumps.
+//
+// Kernels
+//   layer_min_kernel    m_i for every waypoint (one warp per waypoint)
+//   dp_forward_kernel   one CTA per request walks the T steps. The whole layer
+//                       q_i ([n][Kp]) and C_i sit in shared memory; each thread
+//                       owns R successor nodes k' whose joint values stay in
+//                       registers, and streams every predecessor k through a
+//                       float4 broadcast read (4 k per load). Per edge: n FADD,
+//                       n-1 abs-max, one FADD, one compare/select -- pure ALU
+//                       work, no HBM traffic except 2 bytes of backpointer.
+//   dp_backtrack_kernel lowest argmin of C_{T-1}, then the serial walk
+//                       k_i = bp[i+1][k_{i+1}] over backpointer rows staged into
+//                       shared memory by 1-D bulk copies (TMA engine, mbarrier
+//                       completion, double-buffered), then the seed gather.
+#include "internal.h"
+
+namespace cppflow {
+
+constexpr int kDpThreads = 256;
+constexpr int kBtThreads = 256;
+constexpr uint32_t kBtChunkBytes = 32768;
+
+int bp_stride(int Kp) { return (Kp + 7) & ~7; }
+
+size_t dp_smem_bytes(int n, int Kp) { return (size_t)(2 * n + 2) * Kp * sizeof(float); }
+
+bool dp_supported(int n, int Kp) { return dp_smem_bytes(n, Kp) <= 227u * 1024u; }
+
+// ------------------------------------------------------------------ layer minimum
+template <class Src>
+__global__ void __launch_bounds__(256) layer_min_kernel(const __grid_constant__ Src src) {
+  const Req& rq = src.req(blockIdx.y);
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= rq.T) return;
+  const float* row = rq.pen + (size_t)i * rq.Kp;
+  float m = CUDART_INF_F;
+  for (int k = lane; k < rq.K; k += 32) m = fminf(m, row[k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) rq.pen_min[i] = isinf(m) ? 0.f : m;
+}
+
+// ------------------------------------------------------------------ forward sweep
+template <int NJ, int R>
+__device__ __forceinline__ void load_own(const float* __restrict__ cand, int i, int Kp,
+                                         const int (&kp)[R], float (&dst)[R][NJ]) {
+  const float* layer = cand + (size_t)i * NJ * Kp;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) dst[r][j] = kp[r] < Kp ? __ldg(layer + (size_t)j * Kp + kp[r]) : 0.f;
+}
+
+#define CPP_DP_EDGE(CMP, OFF)                                              \
+  {                                                                        \
+    const float cv = c.CMP;                                                \
+    _Pragma("unroll") for (int r = 0; r < R; ++r) {                        \
+      float d = fabsf(qn[r][0] - qa[0].CMP);                               \
+      _Pragma("unroll") for (int j = 1; j < NJ; ++j)                       \
+          d = fmaxf(d, fabsf(qn[r][j] - qa[j].CMP));                       \
+      const float v = cv + d;                                              \
+      if (v < best[r]) {                                                   \
+        best[r] = v;                                                       \
+        arg[r] = 4 * k4 + (OFF);                                           \
+      }                                                                    \
+    }                                                                      \
+  }
+
+template <int NJ, int R, class Src>
+__global__ void __launch_bounds__(kDpThreads) dp_forward_kernel(const __grid_constant__ Src src) {
+  const Req& rq = src.req(blockIdx.x);
+  const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
+  extern __shared__ __align__(16) float sm[];
+  // q layers at sm + b * NJ * Kp, cost vectors at sm + 2 * NJ * Kp + b * Kp (b = step parity)
+  float* const qbase = sm;
+  float* const cbase = sm + 2 * NJ * Kp;
+  const int tid = threadIdx.x;
+  const float* __restrict__ cand = rq.cand;
+
+  // layer 0 and C_0
+  {
+    const float m0 = rq.pen_min[0];
+    const float4* src4 = reinterpret_cast<const float4*>(cand);
+    float4* dst4 = reinterpret_cast<float4*>(qbase);
+    for (int x = tid; x < NJ * Kp / 4; x += kDpThreads) dst4[x] = __ldg(src4 + x);
+    for (int k = tid; k < Kp; k += kDpThreads) cbase[k] = k < K ? rq.pen[k] - m0 : CUDART_INF_F;
+  }
+  int kp[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) kp[r] = tid + r * kDpThreads;
+  float qn[R][NJ];
+  if (T > 1) load_own<NJ, R>(cand, 1, Kp, kp, qn);
+  __syncthreads();
+
+  const int K4 = (K + 3) >> 2, Kp4 = Kp >> 2;
+  for (int i = 0; i + 1 < T; ++i) {
+    const int cur = i & 1, nxt = cur ^ 1;
+    const float4* __restrict__ q4 = reinterpret_cast<const float4*>(qbase + cur * NJ * Kp);
+    const float4* __restrict__ c4 = reinterpret_cast<const float4*>(cbase + cur * Kp);
+    float* qnxt = qbase + nxt * NJ * Kp;
+    float* cnxt = cbase + nxt * Kp;
+
+    float qnn[R][NJ];
+    if (i + 2 < T) load_own<NJ, R>(cand, i + 2, Kp, kp, qnn);
+    const float m1 = rq.pen_min[i + 1];
+    float rpen[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      rpen[r] = kp[r] < K ? __ldg(rq.pen + (size_t)(i + 1) * Kp + kp[r]) - m1 : CUDART_INF_F;
+
+    float best[R];
+    int arg[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; arg[r] = 0; }
+
+#pragma unroll 1
+    for (int k4 = 0; k4 < K4; ++k4) {
+      const float4 c = c4[k4];
+      float4 qa[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) qa[j] = q4[j * Kp4 + k4];
+      CPP_DP_EDGE(x, 0)
+      CPP_DP_EDGE(y, 1)
+      CPP_DP_EDGE(z, 2)
+      CPP_DP_EDGE(w, 3)
+    }
+
+    uint16_t* bprow = rq.bp + (size_t)(i + 1) * Kb;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (kp[r] < Kp) {
+        cnxt[kp[r]] = kp[r] < K ? best[r] + rpen[r] : CUDART_INF_F;
+        bprow[kp[r]] = (uint16_t)arg[r];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) qnxt[j * Kp + kp[r]] = qn[r][j];
+      }
+    }
+    __syncthreads();
+    if (i + 2 < T) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) qn[r][j] = qnn[r][j];
+    }
+  }
+  const float* cfin = cbase + ((T - 1) & 1) * Kp;
+  for (int k = tid; k < Kp; k += kDpThreads) rq.costT[k] = cfin[k];
+}
+
+// Any n and Kp that fit in shared memory: successor values are read back from
+// shared memory instead of registers.
+template <class Src>
+__global__ void __launch_bounds__(kDpThreads) dp_forward_generic(const __grid_constant__ Src src) {
+  const Req& rq = src.req(blockIdx.x);
+  const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb, n = rq.n;
+  extern __shared__ __align__(16) float sm[];
+  float* const qbase = sm;
+  float* const cbase = sm + 2 * n * Kp;
+  const int tid = threadIdx.x;
+  const float* __restrict__ cand = rq.cand;
+  const float m0 = rq.pen_min[0];
+  for (int x = tid; x < n * Kp; x += kDpThreads) qbase[x] = cand[x];
+  for (int k = tid; k < Kp; k += kDpThreads) cbase[k] = k < K ? rq.pen[k] - m0 : CUDART_INF_F;
+  __syncthreads();
+  for (int i = 0; i + 1 < T; ++i) {
+    const int cur = i & 1, nxt = cur ^ 1;
+    const float* qc = qbase + cur * n * Kp;
+    const float* cc = cbase + cur * Kp;
+    float* qx = qbase + nxt * n * Kp;
+    float* cx = cbase + nxt * Kp;
+    const float* layer = cand + (size_t)(i + 1) * n * Kp;
+    for (int x = tid; x < Kp; x += kDpThreads)
+      for (int j = 0; j < n; ++j) qx[j * Kp + x] = layer[(size_t)j * Kp + x];
+    const float m1 = rq.pen_min[i + 1];
+    for (int x = tid; x < Kp; x += kDpThreads) {
+      float best = CUDART_INF_F;
+      int arg = 0;
+      for (int k = 0; k < K; ++k) {
+        float d = fabsf(qx[x] - qc[k]);
+        for (int j = 1; j < n; ++j) d = fmaxf(d, fabsf(qx[j * Kp + x] - qc[j * Kp + k]));
+        const float v = cc[k] + d;
+        if (v < best) { best = v; arg = k; }
+      }
+      cx[x] = x < K ? best + (rq.pen[(size_t)(i + 1) * Kp + x] - m1) : CUDART_INF_F;
+      rq.bp[(size_t)(i + 1) * Kb + x] = (uint16_t)arg;
+    }
+    __syncthreads();
+  }
+  const float* cfin = cbase + ((T - 1) & 1) * Kp;
+  for (int k = tid; k < Kp; k += kDpThreads) rq.costT[k] = cfin[k];
+}
+
+// ------------------------------------------------------------------ backtrack
+template <class Src>
+__global__ void __launch_bounds__(kBtThreads) dp_backtrack_kernel(const __grid_constant__ Src src) {
+  const Req& rq = src.req(blockIdx.x);
+  const int T = rq.T, K = rq.K, Kb = rq.Kb, n = rq.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  extern __shared__ __align__(128) uint16_t sbp[];
+  __shared__ uint64_t bars[2];
+  __shared__ float rv[kBtThreads / 32];
+  __shared__ int rk[kBtThreads / 32];
+  __shared__ int start_k;
+
+  // lowest argmin of C_{T-1} over k < K (strict '<' scan per thread, then a
+  // lexicographic (value, index) reduction)
+  float bv = CUDART_INF_F;
+  int bk = 0x7fffffff;
+  for (int k = tid; k < K; k += kBtThreads) {
+    const float v = rq.costT[k];
+    if (v < bv) { bv = v; bk = k; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+    if (ov < bv || (ov == bv && ok < bk)) { bv = ov; bk = ok; }
+  }
+  if (lane == 0) { rv[warp] = bv; rk[warp] = bk; }
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < kBtThreads / 32; ++w)
+      if (rv[w] < bv || (rv[w] == bv && rk[w] < bk)) { bv = rv[w]; bk = rk[w]; }
+    if (bk == 0x7fffffff) bk = 0;
+    start_k = bk;
+    if (rq.best_cost) *rq.best_cost = bv;
+    if (isinf(bv)) raise_status(rq.status, CPP_ERR_INFEASIBLE);
+
+    // serial walk over staged backpointer rows
+    const int row_bytes = Kb * (int)sizeof(uint16_t);
+    const int L = max(1, min(T > 1 ? T - 1 : 1, (int)(kBtChunkBytes / row_bytes)));
+    uint16_t* const buf0 = sbp;
+    uint16_t* const buf1 = sbp + (size_t)L * Kb;
+    int k = bk;
+    rq.sel[T - 1] = k;
+    // chunk c covers rows [lo_c, hi_c], hi_0 = T-1, descending to row 1
+    auto chunk_hi = [&](int c) { return T - 1 - c * L; };
+    auto issue = [&](int c) {
+      const int hi = chunk_hi(c);
+      if (hi < 1) return;
+      const int lo = max(1, hi - L + 1);
+      const uint32_t bytes = (uint32_t)(hi - lo + 1) * row_bytes;
+      mbar_expect_tx(&bars[c & 1], bytes);
+      bulk_g2s((c & 1) ? buf1 : buf0, rq.bp + (size_t)lo * Kb, bytes, &bars[c & 1]);
+    };
+    issue(0);
+    issue(1);
+    bool ok = true;
+    for (int c = 0; chunk_hi(c) >= 1; ++c) {
+      if (!mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1))) {
+        raise_status(rq.status, CPP_ERR_TIMEOUT);
+        ok = false;
+        if (chunk_hi(c + 1) >= 1) mbar_wait_bounded(&bars[(c + 1) & 1], (uint32_t)(((c + 1) >> 1) & 1));
+        break;
+      }
+      const int hi = chunk_hi(c), lo = max(1, hi - L + 1);
+      const uint16_t* b = (c & 1) ? buf1 : buf0;
+      for (int row = hi; row >= lo; --row) {
+        k = b[(size_t)(row - lo) * Kb + k];
+        rq.sel[row - 1] = k;
+      }
+      // the buffer was read through the generic proxy; order those reads before
+      // the next asynchronous write into it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(c + 2);
+    }
+    (void)ok;
+  }
+  __syncthreads();
+  if (rq.q_seed) {
+    for (int x = tid; x < T * n; x += kBtThreads) {
+      const int i = x / n, j = x - i * n;
+      const int k = rq.sel[i];
+      rq.q_seed[x] = rq.cand[((size_t)i * n + j) * rq.Kp + k];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <class KernelT>
+static void allow_smem(KernelT kernel) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+template <int NJ, class Src>
+static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
+  const size_t smem = dp_smem_bytes(NJ, max_Kp);
+  const int R = (max_Kp + kDpThreads - 1) / kDpThreads;
+  if (R <= 1) {
+    allow_smem(dp_forward_kernel<NJ, 1, Src>);
+    dp_forward_kernel<NJ, 1, Src><<<nreq, kDpThreads, smem, st>>>(s);
+  } else if (R <= 2) {
+    allow_smem(dp_forward_kernel<NJ, 2, Src>);
+    dp_forward_kernel<NJ, 2, Src><<<nreq, kDpThreads, smem, st>>>(s);
+  } else {
+    allow_smem(dp_forward_kernel<NJ, 4, Src>);
+    dp_forward_kernel<NJ, 4, Src><<<nreq, kDpThreads, smem, st>>>(s);
+  }
+  return cudaGetLastError();
+}
+
+template <class Src>
+static cudaError_t launch_dp_t(const Src& s, int n, int nreq, int max_T, int max_Kp,
+                               cudaStream_t st) {
+  {
+    dim3 grid((unsigned)((max_T + 7) / 8), (unsigned)nreq);
+    layer_min_kernel<Src><<<grid, 256, 0, st>>>(s);
+  }
+  cudaError_t e;
+  const bool fast = max_Kp <= 4 * kDpThreads;
+  if (fast && n == 7) e = launch_fwd_nj<7>(s, nreq, max_Kp, st);
+  else if (fast && n == 9) e = launch_fwd_nj<9>(s, nreq, max_Kp, st);
+  else if (fast && n == 6) e = launch_fwd_nj<6>(s, nreq, max_Kp, st);
+  else {
+    allow_smem(dp_forward_generic<Src>);
+    dp_forward_generic<Src><<<nreq, kDpThreads, dp_smem_bytes(n, max_Kp), st>>>(s);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return e;
+  allow_smem(dp_backtrack_kernel<Src>);
+  dp_backtrack_kernel<Src><<<nreq, kBtThreads, 2 * kBtChunkBytes, st>>>(s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dp(const SingleSrc& s, cudaStream_t st) {
+  return launch_dp_t(s, s.r.n, 1, s.r.T, s.r.Kp, st);
+}
+
+cudaError_t launch_dp_batch(const BatchSrc& s, int n, int nreq, int max_T, int max_Kp,
+                            cudaStream_t st) {
+  return launch_dp_t(s, n, nreq, max_T, max_Kp, st);
+}
+
+}  // namespace cppflow

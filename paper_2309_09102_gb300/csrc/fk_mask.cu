@@ -1,0 +1,238 @@
+// fk_mask.cu -- batched forward kinematics, pose error, joint-limit / pose masks
+// and node costs for the candidate lattice (paper §II "Pose error", "Joint
+// limits"; §III-B node costs).
+//
+// Layout: candidates are [T][n][Kp] FP32, k fastest. One warp owns one waypoint
+// and a block of 128 candidates; lane l reads joints j of candidates
+// 4l .. 4l+3 as one float4 per joint (512 contiguous bytes per warp per joint),
+// runs the FP32 DH chain for its four candidates in registers, and writes one
+// uchar4 mask word, one float4 of costs and two float4 of errors.
+#include "internal.h"
+
+namespace cppflow {
+
+constexpr int kMaskThreads = 256;
+constexpr int kMaskWarps = kMaskThreads / 32;
+constexpr int kMaskBlockK = 128;
+
+struct MaskArgs {
+  float tau_pos, tau_rot;
+  float pen_table[4];  // [limit bit | pose bit << 1], each formed in FP64, rounded once
+  double near_margin;
+};
+
+// The target of waypoint i as FP32 rotation + position, computed in FP64 by
+// lanes 0..11 (one entry each) and broadcast through the warp.
+__device__ __forceinline__ void warp_target_f32(const double* t7, float Rt[9], float pt[3]) {
+  const int lane = threadIdx.x & 31;
+  double R[9];
+  quat_to_rot(t7 + 3, R);
+  float mine = 0.f;
+#pragma unroll
+  for (int e = 0; e < 9; ++e)
+    if (lane == e) mine = (float)R[e];
+#pragma unroll
+  for (int e = 0; e < 3; ++e)
+    if (lane == 9 + e) mine = (float)t7[e];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) Rt[e] = __shfl_sync(0xffffffffu, mine, e);
+#pragma unroll
+  for (int e = 0; e < 3; ++e) pt[e] = __shfl_sync(0xffffffffu, mine, 9 + e);
+}
+
+template <int NJ>
+__device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, const float* q,
+                                         int n, bool pad, const float Rt[9], const float pt[3],
+                                         uint8_t& bits, float& cost, float& epos, float& erot) {
+  if (pad) {
+    bits = CPP_MASK_PAD; cost = CUDART_INF_F; epos = erot = CUDART_NAN_F;
+    return;
+  }
+  bool finite = true;
+  uint32_t b = 0;
+#pragma unroll
+  for (int j = 0; j < (NJ ? NJ : kMaxJ); ++j) {
+    if (!NJ && j >= n) break;
+    const float v = q[j];
+    finite &= isfinite(v);
+    if (v < rb.lo[j] || v > rb.hi[j]) b |= CPP_MASK_OUT;
+    if (v < rb.nlo[j] || v > rb.nhi[j]) b |= CPP_MASK_NEAR;
+  }
+  if (!finite) {
+    bits = CPP_MASK_NONFINITE; cost = CUDART_INF_F; epos = erot = CUDART_NAN_F;
+    return;
+  }
+  float R[9], p[3];
+  fk_f32<NJ>(rb, q, R, p);
+  const float dx = p[0] - pt[0], dy = p[1] - pt[1], dz = p[2] - pt[2];
+  epos = sqrtf(dx * dx + dy * dy + dz * dz);
+  erot = geodesic<float>(Rt, R);
+  if (epos > a.tau_pos || erot > a.tau_rot) b |= CPP_MASK_POSE;
+  bits = (uint8_t)b;
+  cost = a.pen_table[((b & (CPP_MASK_OUT | CPP_MASK_NEAR)) ? 1 : 0) | ((b & CPP_MASK_POSE) ? 2 : 0)];
+}
+
+template <int NJ, class Src>
+__global__ void __launch_bounds__(kMaskThreads) mask_kernel(const __grid_constant__ Src src,
+                                                             const MaskArgs a) {
+  const Req& rq = src.req(blockIdx.y);
+  __shared__ RobotF rb;
+  stage_robot(src.rob(rq.robot), a.near_margin, &rb, nullptr);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nblk = (rq.Kp + kMaskBlockK - 1) / kMaskBlockK;
+  const long long task = (long long)blockIdx.x * kMaskWarps + warp;
+  if (task >= (long long)rq.T * nblk) return;
+  const int i = (int)(task / nblk), kb = (int)(task % nblk);
+  const int n = NJ ? NJ : rq.n;
+
+  float Rt[9], pt[3];
+  warp_target_f32(rq.targets + 7 * (size_t)i, Rt, pt);
+
+  const int k0 = kb * kMaskBlockK + 4 * lane;
+  if (k0 >= rq.Kp) return;
+  float4 qv[NJ ? NJ : kMaxJ];
+  const float* base = rq.cand + (size_t)i * n * rq.Kp + k0;
+#pragma unroll
+  for (int j = 0; j < (NJ ? NJ : kMaxJ); ++j) {
+    if (!NJ && j >= n) break;
+    qv[j] = __ldg(reinterpret_cast<const float4*>(base + (size_t)j * rq.Kp));
+  }
+  uint8_t bits[4];
+  float cost[4], ep[4], er[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float q[NJ ? NJ : kMaxJ];
+#pragma unroll
+    for (int j = 0; j < (NJ ? NJ : kMaxJ); ++j) {
+      if (!NJ && j >= n) break;
+      q[j] = c == 0 ? qv[j].x : c == 1 ? qv[j].y : c == 2 ? qv[j].z : qv[j].w;
+    }
+    mask_one<NJ>(rb, a, q, n, k0 + c >= rq.K, Rt, pt, bits[c], cost[c], ep[c], er[c]);
+  }
+  const size_t o = (size_t)i * rq.Kp + k0;
+  *reinterpret_cast<uchar4*>(rq.mask + o) = make_uchar4(bits[0], bits[1], bits[2], bits[3]);
+  *reinterpret_cast<float4*>(rq.pen + o) = make_float4(cost[0], cost[1], cost[2], cost[3]);
+  if (rq.err) {
+    float4* e = reinterpret_cast<float4*>(rq.err + 2 * o);
+    e[0] = make_float4(ep[0], er[0], ep[1], er[1]);
+    e[1] = make_float4(ep[2], er[2], ep[3], er[3]);
+  }
+}
+
+// ------------------------------------------------------------------ plain FK calls
+__global__ void fk_batch_kernel(const cpp_robot_t robot, const float* __restrict__ q, long long N,
+                                float* __restrict__ R, float* __restrict__ p) {
+  __shared__ RobotF rb;
+  stage_robot(robot, 0.0, &rb, nullptr);
+  __syncthreads();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x) {
+    float qq[kMaxJ];
+    for (int j = 0; j < rb.n; ++j) qq[j] = q[j * N + t];
+    float Rl[9], pl[3];
+    fk_f32<0>(rb, qq, Rl, pl);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) R[e * N + t] = Rl[e];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) p[e * N + t] = pl[e];
+  }
+}
+
+// Rotation -> unit quaternion (w >= 0), largest-pivot branch.
+__device__ inline void rot_to_quat(const double R[9], double* q) {
+  const double tr = R[0] + R[4] + R[8];
+  double w, x, y, z;
+  if (tr > 0.0) {
+    const double s = 2.0 * sqrt(tr + 1.0);
+    w = 0.25 * s; x = (R[7] - R[5]) / s; y = (R[2] - R[6]) / s; z = (R[3] - R[1]) / s;
+  } else if (R[0] > R[4] && R[0] > R[8]) {
+    const double s = 2.0 * sqrt(1.0 + R[0] - R[4] - R[8]);
+    w = (R[7] - R[5]) / s; x = 0.25 * s; y = (R[1] + R[3]) / s; z = (R[2] + R[6]) / s;
+  } else if (R[4] > R[8]) {
+    const double s = 2.0 * sqrt(1.0 + R[4] - R[0] - R[8]);
+    w = (R[2] - R[6]) / s; x = (R[1] + R[3]) / s; y = 0.25 * s; z = (R[5] + R[7]) / s;
+  } else {
+    const double s = 2.0 * sqrt(1.0 + R[8] - R[0] - R[4]);
+    w = (R[3] - R[1]) / s; x = (R[2] + R[6]) / s; y = (R[5] + R[7]) / s; z = 0.25 * s;
+  }
+  const double sg = w < 0.0 ? -1.0 : 1.0;
+  const double inv = sg / sqrt(w * w + x * x + y * y + z * z);
+  q[0] = w * inv; q[1] = x * inv; q[2] = y * inv; q[3] = z * inv;
+}
+
+__global__ void fk_pose64_kernel(const cpp_robot_t robot, const double* __restrict__ q,
+                                 long long N, double* __restrict__ pose) {
+  __shared__ RobotD rb;
+  stage_robot(robot, 0.0, nullptr, &rb);
+  __syncthreads();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x) {
+    double R[9], p[3];
+    fk_f64(rb, q + t * rb.n, R, p);
+    double* o = pose + 7 * t;
+    o[0] = p[0]; o[1] = p[1]; o[2] = p[2];
+    rot_to_quat(R, o + 3);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+static MaskArgs make_mask_args(const cpp_params_t& P) {
+  MaskArgs a;
+  a.tau_pos = (float)P.tau_pos;
+  a.tau_rot = (float)P.tau_rot;
+  a.pen_table[0] = 0.f;
+  a.pen_table[1] = (float)P.pen_limit;
+  a.pen_table[2] = (float)P.pen_pose;
+  a.pen_table[3] = (float)(P.pen_limit + P.pen_pose);
+  a.near_margin = P.near_margin;
+  return a;
+}
+
+template <class Src>
+static cudaError_t launch_mask_t(const Src& src, int n, int nreq, long long max_tasks,
+                                 const cpp_params_t& P, cudaStream_t st) {
+  const MaskArgs a = make_mask_args(P);
+  dim3 grid((unsigned)((max_tasks + kMaskWarps - 1) / kMaskWarps), (unsigned)nreq);
+  switch (n) {
+    case 6: mask_kernel<6, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+    case 7: mask_kernel<7, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+    case 9: mask_kernel<9, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+    default: mask_kernel<0, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st) {
+  const long long tasks = (long long)s.r.T * ((s.r.Kp + kMaskBlockK - 1) / kMaskBlockK);
+  return launch_mask_t(s, s.r.n, 1, tasks, P, st);
+}
+
+cudaError_t launch_mask_batch(const BatchSrc& s, int n, int nreq, long long max_tasks,
+                              const cpp_params_t& P, cudaStream_t st) {
+  return launch_mask_t(s, n, nreq, max_tasks, P, st);
+}
+
+long long mask_tasks(int T, int Kp) {
+  return (long long)T * ((Kp + kMaskBlockK - 1) / kMaskBlockK);
+}
+
+cudaError_t launch_fk_batch(const cpp_robot_t& r, const float* q, long long N, float* R,
+                            float* p, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  const int threads = 256;
+  const long long blocks = std::min<long long>((N + threads - 1) / threads, 152LL * 16);
+  fk_batch_kernel<<<(unsigned)blocks, threads, 0, st>>>(r, q, N, R, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fk_pose64(const cpp_robot_t& r, const double* q, long long N, double* pose,
+                             cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  const int threads = 128;
+  const long long blocks = std::min<long long>((N + threads - 1) / threads, 152LL * 16);
+  fk_pose64_kernel<<<(unsigned)blocks, threads, 0, st>>>(r, q, N, pose);
+  return cudaGetLastError();
+}
+
+}  // namespace cppflow

@@ -1,0 +1,57 @@
+"""The C-ABI library loads and exports every function that include/*.h declares
+(no GPU needed: nothing is called that would touch a device)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(cpp_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2309_09102_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("cpp_fk_batch", "cpp_mask", "cpp_dp_search", "cpp_lm_refine", "cpp_check",
+                     "cpp_plan", "cpp_plan_batch", "cpp_dp_workspace_size", "cpp_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls(lib):
+    from paper_2309_09102_gb300 import cppflow
+    p = cppflow.make_params()
+    assert p.lm_iters == 20 and abs(p.tau_pos - 1e-3) < 1e-18
+    assert cppflow.lib().cpp_version() >= 100
+    assert cppflow.dp_workspace_size(300, 512) >= 300 * 512 * 2
+    # host-side validation rejects bad arguments before touching a device
+    r = cppflow.make_robot([0.1] * 7, [0.1] * 7, [0.0] * 7, [-1] * 7, [1] * 7)
+    st = cppflow.lib().cpp_mask(ctypes.byref(r), ctypes.byref(p), None, None, 0, 1, 4,
+                                None, None, None, None, None)
+    assert st == cppflow.ERR_INVALID_ARG
+    assert "T" in cppflow.last_error()
+    bad = cppflow.make_robot([0.1] * 7, [0.1] * 7, [0.0] * 7, [1] * 7, [-1] * 7)
+    assert cppflow.lib().cpp_check(ctypes.byref(bad), ctypes.byref(p), None, None, 5, None, None,
+                                   None) == cppflow.ERR_INVALID_ARG

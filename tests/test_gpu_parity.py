@@ -1,0 +1,217 @@
+"""GPU vs oracle parity for every stage of the planner core, through the C ABI.
+
+Bars: FK within 1e-5 m / rad of FP64; masks bit-exact outside a 1e-5 guard band
+around the thresholds; search indices and cost bit-exact given the same node
+costs; refined trajectories within 1 mm / 0.1 deg and their max joint jump
+within 1e-4 rad of the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import problems
+from gpu_util import (FK_TOL, GUARD, JUMP_TOL, TAU_POS, TAU_ROT, dev, params_pair, path_cost_f32,
+                      run_dp, run_lm, run_mask, run_plan, torch)
+from paper_2309_09102_gb300 import cppflow, synth
+
+pytestmark = pytest.mark.gpu
+
+RNG = np.random.default_rng(2024)
+
+
+def crob(arm):
+    return cppflow.robot_from_arm(arm)
+
+
+# --------------------------------------------------------------------- FK
+@pytest.mark.parametrize("n,wrist", [(7, False), (9, True), (3, False), (12, False)])
+def test_fk_batch_matches_oracle(n, wrist):
+    tt = torch()
+    arm = synth.draw_arm(40 + n, n, wrist)
+    orob = problems.oracle_robot(arm)
+    N = 1000 + 37  # several blocks and a ragged tail
+    q = RNG.uniform(-2.8, 2.8, (N, n)).astype(np.float32)
+    R = tt.empty(9, N, dtype=tt.float32, device="cuda:0")
+    p = tt.empty(3, N, dtype=tt.float32, device="cuda:0")
+    cppflow.fk_batch(crob(arm), dev(q.T.copy()), R, p)
+    tt.cuda.synchronize()
+    R, p = R.cpu().numpy(), p.cpu().numpy()
+    for t in range(0, N, 7):
+        Ro, po = oracle.fk(orob, q[t].astype(np.float64))
+        assert np.max(np.abs(R[:, t].reshape(3, 3) - Ro)) <= FK_TOL
+        assert np.max(np.abs(p[:, t] - po)) <= FK_TOL
+
+
+def test_fk_pose_f64_matches_oracle():
+    tt = torch()
+    arm = synth.draw_arm(7, 7)
+    orob = problems.oracle_robot(arm)
+    q = RNG.uniform(-2.8, 2.8, (333, 7))
+    out = tt.empty(333, 7, dtype=tt.float64, device="cuda:0")
+    cppflow.fk_pose_f64(crob(arm), dev(q), out)
+    tt.cuda.synchronize()
+    np.testing.assert_allclose(out.cpu().numpy(), oracle.fk_pose(orob, q), atol=1e-12)
+
+
+# --------------------------------------------------------------------- mask
+def _mask_compare(pb, **kw):
+    op, cp = params_pair(**kw)
+    g = run_mask(crob(pb.arm), cp, pb.cand, pb.targets, pb.K)
+    m, pen, err = oracle.mask(pb.robot, op, pb.cand, pb.targets, pb.K)
+    # errors
+    finite = np.isfinite(err[..., 0])
+    assert np.all(np.isfinite(g.err[..., 0]) == finite)
+    assert np.max(np.abs(g.err[finite] - err[finite])) <= FK_TOL
+    # bits outside the guard band
+    near_tau = (np.abs(err[..., 0] - op.tau_pos) <= GUARD) | (np.abs(err[..., 1] - op.tau_rot) <= GUARD)
+    ok = ~near_tau
+    np.testing.assert_array_equal(g.mask[ok], m[ok])
+    np.testing.assert_array_equal(g.pen[ok], pen[ok])
+    # limit bits never depend on the guard band
+    lim = np.uint8(cppflow.MASK_OUT | cppflow.MASK_NEAR | cppflow.MASK_NONFINITE | cppflow.MASK_PAD)
+    np.testing.assert_array_equal(g.mask & lim, m & lim)
+    return g, m, near_tau.sum()
+
+
+@pytest.mark.parametrize("T,K,n,wrist", [(12, 40, 7, False), (9, 130, 9, True), (5, 33, 3, False),
+                                         (4, 70, 12, False), (3, 1, 7, False)])
+def test_mask_matches_oracle(T, K, n, wrist):
+    pb = problems.small(T=T, K=K, n=n, wrist=wrist, seed=T * 100 + K)
+    _mask_compare(pb)                                          # 1 mm / 0.1 deg: almost all POSE
+    g, m, guarded = _mask_compare(pb, tau_pos=0.05, tau_rot=math.radians(5.0))  # bits vary
+    assert guarded <= max(2, m.size // 1000)
+
+
+def test_mask_nonfinite_and_padding():
+    pb = problems.small(T=4, K=30, seed=5)
+    cand = pb.cand.copy()
+    cand[1, 2, 3] = np.nan
+    cand[2, 0, 7] = np.inf
+    op, cp = params_pair()
+    g = run_mask(crob(pb.arm), cp, cand, pb.targets, pb.K)
+    assert g.mask[1, 3] == cppflow.MASK_NONFINITE and np.isinf(g.pen[1, 3])
+    assert g.mask[2, 7] == cppflow.MASK_NONFINITE and np.isinf(g.pen[2, 7])
+    assert np.all(g.mask[:, pb.K:] == cppflow.MASK_PAD) and np.all(np.isinf(g.pen[:, pb.K:]))
+    assert np.all(np.isnan(g.err[:, pb.K:]))
+
+
+# --------------------------------------------------------------------- search
+@pytest.mark.parametrize("T,K,n,wrist", [(50, 32, 7, False), (20, 100, 7, False), (7, 1, 7, False),
+                                         (2, 5, 7, False), (15, 257, 7, False), (11, 600, 9, True),
+                                         (6, 45, 6, False), (8, 50, 3, False), (5, 1200, 7, False),
+                                         (1, 9, 7, False)])
+def test_dp_matches_oracle_bit_exact(T, K, n, wrist):
+    """The GPU search fed the GPU's own node costs returns the oracle's FP32 indices and cost."""
+    pb = problems.small(T=T, K=K, n=n, wrist=wrist, seed=3 * T + K)
+    op, cp = params_pair(tau_pos=0.05, tau_rot=math.radians(5.0))
+    g = run_mask(crob(pb.arm), cp, pb.cand, pb.targets, pb.K)
+    got = run_dp(pb.cand, g.pen, pb.K)
+    ref = oracle.dp_f32(pb.cand, g.pen, pb.K)
+    np.testing.assert_array_equal(got["sel"], ref["sel"])
+    assert got["best"] == ref["best"]
+    assert got["status"] == 0
+    np.testing.assert_array_equal(got["seed"], pb.cand[np.arange(T), :, ref["sel"]])
+
+
+def test_dp_ties_and_infeasible():
+    T, K, n = 6, 40, 7
+    base = RNG.normal(0, 0.2, (T, n, 20)).astype(np.float32)
+    cand = np.zeros((T, n, 40), np.float32)
+    cand[:, :, :20] = base
+    cand[:, :, 20:] = base
+    pen = np.zeros((T, 40), np.float32)
+    got = run_dp(cand, pen, K)
+    ref = oracle.dp_f32(cand, pen, K)
+    assert np.all(got["sel"] < 20)
+    np.testing.assert_array_equal(got["sel"], ref["sel"])
+    pen[3, :] = np.inf
+    got = run_dp(cand, pen, K)
+    assert got["status"] == cppflow.ERR_INFEASIBLE and np.isinf(got["best"])
+    np.testing.assert_array_equal(got["sel"], oracle.dp_f32(cand, pen, K)["sel"])
+
+
+# --------------------------------------------------------------------- LM
+def test_lm_matches_oracle_plain_workload():
+    pb = problems.build(synth.PLAIN)
+    op, cp = params_pair(lm_iters=pb.w.lm_iters)
+    g = run_mask(crob(pb.arm), cp, pb.cand, pb.targets, pb.K)
+    seed = run_dp(pb.cand, g.pen, pb.K)["seed"]
+    q_gpu, err_gpu = run_lm(crob(pb.arm), cp, seed, pb.targets)
+    q_orc, _, _ = oracle.lm(pb.robot, op, seed.astype(np.float64), pb.targets)
+    e_orc, rep_orc = oracle.check(pb.robot, op, q_orc, pb.targets)
+    e_gpu, rep_gpu = oracle.check(pb.robot, op, q_gpu.astype(np.float64), pb.targets)
+    assert np.max(err_gpu[:, 0]) <= TAU_POS and np.max(err_gpu[:, 1]) <= TAU_ROT
+    np.testing.assert_allclose(err_gpu, e_gpu, atol=1e-12)   # device FP64 check == host FP64
+    assert rep_orc["n_pose_fail"] == 0 and rep_gpu["n_pose_fail"] == 0
+    assert abs(rep_gpu["mjac"] - rep_orc["mjac"]) <= JUMP_TOL
+    assert np.max(np.abs(q_gpu - q_orc)) <= 1e-3
+
+
+def test_lm_fp64_mode_and_free_mask():
+    pb = problems.small(T=16, K=32, n=9, wrist=True, seed=77, lm_iters=20)
+    op, cp = params_pair(lm_iters=20, lm_fp64=1)
+    seed = pb.truth + RNG.normal(0, 0.02, pb.truth.shape)
+    q_gpu, err = run_lm(crob(pb.arm), cp, seed.astype(np.float32), pb.targets)
+    q_orc, _, _ = oracle.lm(pb.robot, op, seed.astype(np.float32).astype(np.float64), pb.targets)
+    assert np.max(err[:, 0]) <= TAU_POS and np.max(err[:, 1]) <= TAU_ROT
+    assert np.max(np.abs(q_gpu - q_orc)) <= 1e-4
+    mask = synth.wrong_branch_free_mask(9)
+    op2, cp2 = params_pair(lm_iters=10, free_mask=mask)
+    q2, _ = run_lm(crob(pb.arm), cp2, seed.astype(np.float32), pb.targets)
+    np.testing.assert_array_equal(q2[:, :4], seed.astype(np.float32)[:, :4])
+
+
+# --------------------------------------------------------------------- whole plan
+@pytest.mark.parametrize("w", [synth.PLAIN, synth.SINGLE], ids=lambda w: w.name)
+def test_plan_matches_oracle(w):
+    pb = problems.build(w)
+    op, cp = params_pair(lm_iters=w.lm_iters, lambda0=w.lambda0)
+    got = run_plan(crob(pb.arm), cp, pb.cand, pb.targets, pb.K)
+    g = run_mask(crob(pb.arm), cp, pb.cand, pb.targets, pb.K)
+    ref_dp = oracle.dp_f32(pb.cand, g.pen, pb.K)
+    np.testing.assert_array_equal(got["sel"], ref_dp["sel"])
+    assert got["best"] == ref_dp["best"]
+    ref = oracle.plan(pb.robot, op, pb.cand, pb.targets, pb.K)
+    assert got["status"] == 0 and ref["status"] == 0
+    r = got["report"]
+    assert r["valid"] == 1 and ref["report"]["valid"] == 1
+    assert r["max_pos"] <= TAU_POS and r["max_rot"] <= TAU_ROT
+    assert abs(r["mjac"] - ref["report"]["mjac"]) <= JUMP_TOL
+    assert abs(r["sum_linf"] - ref["report"]["sum_linf"]) <= JUMP_TOL * pb.w.T
+
+
+def test_batch_equals_alone():
+    """Requests of different T and K in one batched launch give exactly the results each
+    gets alone (same kernels, same inputs)."""
+    tt = torch()
+    shapes = [(30, 40), (61, 128), (12, 7), (45, 256), (2, 3)]
+    pbs = [problems.small(T=T, K=K, seed=500 + i) for i, (T, K) in enumerate(shapes)]
+    op, cp = params_pair(lm_iters=10)
+    robots = [crob(pb.arm) for pb in pbs]
+    keep, descs = [], []
+    for r, pb in enumerate(pbs):
+        T, n, Kp = pb.cand.shape
+        bufs = dict(cand=dev(pb.cand), targets=dev(pb.targets),
+                    sel=tt.empty(T, dtype=tt.int32, device="cuda:0"),
+                    q=tt.empty(T, n, dtype=tt.float32, device="cuda:0"),
+                    err=tt.empty(T, 2, dtype=tt.float64, device="cuda:0"),
+                    rep=tt.zeros(cppflow.REPORT_BYTES, dtype=tt.uint8, device="cuda:0"),
+                    best=tt.empty(1, dtype=tt.float32, device="cuda:0"))
+        keep.append(bufs)
+        d = cppflow.PlanDesc(T, pb.K, Kp, r, bufs["cand"].data_ptr(), bufs["targets"].data_ptr(),
+                             bufs["sel"].data_ptr(), bufs["q"].data_ptr(), bufs["err"].data_ptr(),
+                             bufs["rep"].data_ptr(), bufs["best"].data_ptr())
+        descs.append(d)
+    ws = tt.empty(cppflow.plan_batch_workspace_size(descs, robots), dtype=tt.uint8, device="cuda:0")
+    st = tt.zeros(len(descs), dtype=tt.int32, device="cuda:0")
+    cppflow.plan_batch(robots, cp, descs, ws, st)
+    tt.cuda.synchronize()
+    assert np.all(st.cpu().numpy() == 0)
+    for r, pb in enumerate(pbs):
+        alone = run_plan(robots[r], cp, pb.cand, pb.targets, pb.K)
+        np.testing.assert_array_equal(keep[r]["sel"].cpu().numpy(), alone["sel"])
+        np.testing.assert_array_equal(keep[r]["q"].cpu().numpy(), alone["q"])
+        np.testing.assert_array_equal(keep[r]["err"].cpu().numpy(), alone["err"])
+        assert float(keep[r]["best"].item()) == float(alone["best"])
