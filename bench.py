@@ -1,0 +1,408 @@
+"""Benchmark of the GB300 planner core: served plans/s on the T = 300, K = 512,
+7-DoF workload (the single-request-at-scale configuration), batched.
+
+One step = one pass of the whole path (FK + masks, search, backtracking, LM,
+FP64 check) over one batch of B synthetic requests of that shape, inputs
+resident in HBM. Beside it the script measures, on the same requests:
+  * the plain per-request GPU path (cpp_plan one request at a time, one stream):
+    plans/s and p50 / p99 latency,
+  * end to end: host pinned inputs copied in, the batch run, results copied out,
+    all inside the timed region,
+  * the search kernel's duration (CUDA events on its stream) for the roofline,
+  * SM clocks during the timed region (nvidia-smi),
+  * the CPU oracle on a bounded sample of the same workload (rank 0 only).
+``--impl reference`` times the CPU oracle alone as the reference arm.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl cuda|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2309_09102_gb300 import synth  # noqa: E402
+
+METRIC = "served plans/s, T=300 K=512 7-DoF, valid at <=1mm/<=0.1deg"
+SMS = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def workload_requests(B: int, rank: int):
+    """B requests shaped like the single-request-at-scale workload; arm r mod 8 of 8
+    seeded chains, distinct paths and candidates per request (and per rank)."""
+    base = synth.SINGLE
+    out = []
+    for r in range(B):
+        g = rank * B + r
+        out.append(synth.Workload(f"{base.name}_r{g}", base.n, base.T, base.K, base.sigma,
+                                  base.p_wb, base.p_out, base.lm_iters, base.lambda0,
+                                  arm_seed=100 + (g % 8), path_seed=7000 + g, cand_seed=9000 + g))
+    return out
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, device_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_problem(w: synth.Workload):
+    import oracle
+    arm = synth.draw_arm(w.arm_seed, w.n, w.wrist)
+    rob = oracle.make_robot(arm.a, arm.d, arm.alpha, arm.lo, arm.hi, arm.theta0)
+    truth = synth.draw_truth(w.path_seed, w.n, w.T, w.wrist)
+    targets = oracle.fk_pose(rob, truth)
+    P_wb = oracle.make_params(lm_iters=30, free_mask=synth.wrong_branch_free_mask(w.n))
+    q_wb, _, _ = oracle.lm(rob, P_wb, synth.wrong_branch_start(truth), targets)
+    draws = synth.draw_candidates(w.cand_seed, w.T, w.K, w.n, w.p_wb, w.p_out)
+    cand = synth.assemble(truth, q_wb, draws, w.sigma, arm.lo, arm.hi)
+    return rob, targets, cand
+
+
+def cpu_oracle_run(reqs, threads: int, steps: int = 1):
+    """Time the oracle (mask, FP32 search, LM, check) on `reqs`, one request per thread
+    (the C oracle releases the GIL), `steps` times. Returns (plans/s, valid, seconds)."""
+    import oracle
+    oracle.build()
+    probs = [oracle_problem(w) for w in reqs]
+    P = oracle.make_params(lm_iters=reqs[0].lm_iters, lambda0=reqs[0].lambda0)
+
+    def one(i):
+        rob, targets, cand = probs[i]
+        return oracle.plan(rob, P, cand, targets, reqs[i].K)["report"]["valid"]
+
+    t0 = time.perf_counter()
+    valid = 0
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        for _ in range(steps):
+            valid += sum(ex.map(one, range(len(probs))))
+    dt = time.perf_counter() - t0
+    return len(probs) * steps / dt, valid, dt
+
+
+def cpu_baseline(rank: int) -> dict:
+    cores = os.cpu_count() or 1
+    S = max(1, min(cores, 16))
+    reqs = workload_requests(S, 0)
+    value, valid, dt = cpu_oracle_run(reqs, S)
+    return {"value": round(value, 3), "unit": "plans/s", "cores": S, "kind": "oracle",
+            "sample": f"{S} requests of T=300 K=512 n=7 (mask + FP32 search + FP64 LM + check), "
+                      f"one per thread, {dt:.1f} s wall", "valid": int(valid)}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    S = max(1, min(cores, 16))
+    reqs = workload_requests(S, 0)
+    cpu_oracle_run(reqs[:1], 1)  # warm the library
+    value, valid, dt = cpu_oracle_run(reqs, S, steps=args.steps)
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "plans/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1000 * dt / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": synth.SINGLE.name, "T": 300, "K": 512, "n": 7,
+                       "requests_per_step": S},
+            "cpu_baseline": {"value": round(value, 3), "unit": "plans/s", "cores": S,
+                             "kind": "oracle",
+                             "sample": f"{S} requests per step, one per thread"},
+            "e2e": {"value": round(value, 3), "unit": "plans/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_cuda(args, rank: int, world: int, dist):
+    import torch
+
+    from paper_2309_09102_gb300 import cppflow
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cppflow.lib()
+    B = args.batch
+    reqs = workload_requests(B, rank)
+    n, T, K = synth.SINGLE.n, synth.SINGLE.T, synth.SINGLE.K
+    Kp = synth.pad_k(K)
+
+    # ---- inputs: random draws on the host, target FK and wrong-branch re-solve on the GPU
+    arms = [synth.draw_arm(100 + k, n) for k in range(8)]
+    robots = [cppflow.robot_from_arm(a) for a in arms]
+    P = cppflow.make_params(lm_iters=synth.SINGLE.lm_iters, lambda0=synth.SINGLE.lambda0)
+    P_wb = cppflow.make_params(lm_iters=30, lm_fp64=1, free_mask=synth.wrong_branch_free_mask(n))
+
+    def draws_of(w):
+        truth = synth.draw_truth(w.path_seed, n, T)
+        return truth, synth.draw_candidates(w.cand_seed, T, K, n, w.p_wb, w.p_out)
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        drawn = list(ex.map(draws_of, reqs))
+    cand_h, targets_h = [], []
+    for r, w in enumerate(reqs):
+        truth, draws = drawn[r]
+        rob = robots[w.arm_seed - 100]
+        tq = torch.from_numpy(truth).to(dev)
+        tgt = torch.empty(T, 7, dtype=torch.float64, device=dev)
+        cppflow.fk_pose_f64(rob, tq, tgt)
+        q0 = torch.from_numpy(synth.wrong_branch_start(truth).astype(np.float32)).to(dev)
+        qwb = torch.empty(T, n, dtype=torch.float32, device=dev)
+        cppflow.lm_refine(rob, P_wb, q0, tgt, qwb)
+        torch.cuda.synchronize()
+        arm = arms[w.arm_seed - 100]
+        cand = synth.assemble(truth, qwb.cpu().numpy().astype(np.float64), draws, w.sigma,
+                              arm.lo, arm.hi, Kp)
+        cand_h.append(torch.from_numpy(cand).pin_memory())
+        targets_h.append(tgt.cpu().pin_memory())
+    del drawn
+
+    # ---- device buffers and the prepared batch
+    cand_d = [c.to(dev) for c in cand_h]
+    targ_d = [t.to(dev) for t in targets_h]
+    sel = torch.empty(B, T, dtype=torch.int32, device=dev)
+    q_out = torch.empty(B, T, n, dtype=torch.float32, device=dev)
+    err = torch.empty(B, T, 2, dtype=torch.float64, device=dev)
+    rep = torch.zeros(B, cppflow.REPORT_BYTES, dtype=torch.uint8, device=dev)
+    best = torch.empty(B, dtype=torch.float32, device=dev)
+    status = torch.zeros(B, dtype=torch.int32, device=dev)
+    descs = [cppflow.PlanDesc(T, K, Kp, reqs[r].arm_seed - 100, cand_d[r].data_ptr(),
+                              targ_d[r].data_ptr(), sel[r].data_ptr(), q_out[r].data_ptr(),
+                              err[r].data_ptr(), rep[r].data_ptr(), best[r].data_ptr())
+             for r in range(B)]
+    ws = torch.empty(cppflow.plan_batch_workspace_size(descs, robots), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    batch = cppflow.Batch(robots, P, descs, ws, status, stream)
+    launches_per_step = batch.launches(cppflow.STAGE_ALL)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        batch.run(cppflow.STAGE_ALL, stream)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident batched path
+    pre = cppflow.STAGE_MASK | cppflow.STAGE_LAYER_MIN
+    post = cppflow.STAGE_BACKTRACK | cppflow.STAGE_LM | cppflow.STAGE_CHECK
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        ev[s][0].record(stream)
+        batch.run(pre, stream)
+        ev[s][1].record(stream)
+        batch.run(cppflow.STAGE_DP_FORWARD, stream)
+        ev[s][2].record(stream)
+        batch.run(post, stream)
+        ev[s][3].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms = ev[0][0].elapsed_time(ev[-1][3])
+    dp_ms = [ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps)]
+    pre_ms = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)]
+    post_ms = [ev[s][2].elapsed_time(ev[s][3]) for s in range(args.steps)]
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * B * args.steps / (total_ms / 1000.0)
+
+    # ---- results valid?
+    st = status.cpu().numpy()
+    reps = [cppflow.report_from_bytes(rep[r].cpu().numpy().tobytes()) for r in range(B)]
+    valid = sum(int(r["valid"]) for r in reps)
+    max_pos = max(r["max_pos"] for r in reps)
+    max_rot = max(r["max_rot"] for r in reps)
+
+    # ---- plain per-request path (one request at a time, one stream)
+    n_plain = min(B, args.plain)
+    pws = torch.empty(cppflow.plan_workspace_size(T, K, Kp, n), dtype=torch.uint8, device=dev)
+    psel = torch.empty(T, dtype=torch.int32, device=dev)
+    pbest = torch.empty(1, dtype=torch.float32, device=dev)
+    pq = torch.empty(T, n, dtype=torch.float32, device=dev)
+    perr = torch.empty(T, 2, dtype=torch.float64, device=dev)
+    prep = torch.zeros(cppflow.REPORT_BYTES, dtype=torch.uint8, device=dev)
+    pst = torch.zeros(1, dtype=torch.int32, device=dev)
+    for r in range(min(2, n_plain)):
+        cppflow.plan(robots[reqs[r].arm_seed - 100], P, cand_d[r], targ_d[r], K, pws, psel, pbest,
+                     pq, perr, prep, pst, stream)
+    torch.cuda.synchronize()
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(n_plain)]
+    for r in range(n_plain):
+        pev[r][0].record(stream)
+        cppflow.plan(robots[reqs[r].arm_seed - 100], P, cand_d[r], targ_d[r], K, pws, psel, pbest,
+                     pq, perr, prep, pst, stream)
+        pev[r][1].record(stream)
+    torch.cuda.synchronize()
+    lat = sorted(a.elapsed_time(b) for a, b in pev)
+    plain_total = pev[0][0].elapsed_time(pev[-1][1])
+    plain = {"value": round(n_plain / (plain_total / 1000.0), 3), "unit": "plans/s",
+             "p50_ms": round(lat[len(lat) // 2], 3),
+             "p99_ms": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 3),
+             "requests": n_plain}
+
+    # ---- end to end: pinned host inputs in, batch, results out (all timed)
+    h2d = sum(c.numel() * 4 + t.numel() * 8 for c, t in zip(cand_h, targets_h))
+    sel_h = torch.empty_like(sel, device="cpu").pin_memory()
+    q_h = torch.empty_like(q_out, device="cpu").pin_memory()
+    err_h = torch.empty_like(err, device="cpu").pin_memory()
+    rep_h = torch.empty_like(rep, device="cpu").pin_memory()
+    d2h = (sel.numel() * 4 + q_out.numel() * 4 + err.numel() * 8 + rep.numel())
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for r in range(B):
+            cand_d[r].copy_(cand_h[r], non_blocking=True)
+            targ_d[r].copy_(targets_h[r], non_blocking=True)
+        batch.run(cppflow.STAGE_ALL, stream)
+        sel_h.copy_(sel, non_blocking=True)
+        q_h.copy_(q_out, non_blocking=True)
+        err_h.copy_(err, non_blocking=True)
+        rep_h.copy_(rep, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": round(world * B * e2e_steps / (e2e_ms / 1000.0), 3), "unit": "plans/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "path": "pinned host -> cudaMemcpyAsync -> cpp_batch_run -> pinned host"}
+
+    # ---- roofline of the search kernel (the dominant kernel)
+    edges = B * (T - 1) * K * K
+    ops_per_edge = 2 * n + 1
+    dp_s = statistics.mean(dp_ms) / 1000.0
+    achieved = edges * ops_per_edge / dp_s / 1e12
+    peak = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "kernel": "dp_forward_kernel", "achieved": round(achieved, 3),
+            "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "traffic": None,
+            "ops": f"{ops_per_edge} FP32 ALU ops per edge (n sub, n-1 abs-max, add, min) x "
+                   f"{edges:.4g} edges per launch",
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max clock (derived, not measured)",
+            "kernel_ms": round(statistics.mean(dp_ms), 4),
+            "edges_per_s": round(edges / dp_s, 1)}
+
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "plans/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": synth.SINGLE.name, "T": T, "K": K, "n": n,
+                       "requests_per_step": B, "per_gpu_requests": B,
+                       "l2": f"inputs larger than L2 ({B * T * n * Kp * 4 / 1e6:.0f} MB lattice per step)",
+                       "lm_iters": P.lm_iters, "parallelism": f"replicas x{world}"},
+            "p99_ms": round(ms_per_step, 4),
+            "stage_ms": {"mask_and_layer_min": round(statistics.mean(pre_ms), 4),
+                         "dp_forward": round(statistics.mean(dp_ms), 4),
+                         "backtrack_lm_check": round(statistics.mean(post_ms), 4)},
+            "plain_per_request": plain,
+            "valid_plans": f"{valid}/{B}", "max_pos_err_m": max_pos, "max_rot_err_rad": max_rot,
+            "dev_status_nonzero": int((st != 0).sum()),
+            "roofline": roof, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=304)
+    ap.add_argument("--plain", type=int, default=32, help="requests timed on the plain path")
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "cuda":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if args.impl == "cuda" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group(backend)
+        dist = tdist
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_cuda(args, rank, world, dist)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -228,6 +228,32 @@ cpp_status cpp_plan_batch(const cpp_robot_t* robots, int32_t n_robots,
                           int32_t count, void* workspace, size_t ws_bytes,
                           int32_t* dev_status, cpp_stream_t stream);
 
+/* ------------------------------------------------------------------ prepared batches
+ * cpp_batch_create validates a batch exactly like cpp_plan_batch, copies its
+ * request table into the workspace (enqueued on `stream`; the host arrays may be
+ * freed on return) and returns a host handle. cpp_batch_run then enqueues any
+ * subset of the stages below, in pipeline order, on any stream; it launches
+ * kernels only, so it can be repeated, timed stage by stage, or captured into a
+ * CUDA graph. The workspace and every descriptor buffer must stay valid until
+ * the handle is destroyed. cpp_plan_batch = create + run(CPP_STAGE_ALL) + destroy. */
+#define CPP_STAGE_MASK 1u        /* S1+S2: FK, pose error, masks, node costs */
+#define CPP_STAGE_LAYER_MIN 2u   /* per-waypoint cheapest node cost */
+#define CPP_STAGE_DP_FORWARD 4u  /* S3: the min-plus sweep over the T x K x K lattice */
+#define CPP_STAGE_BACKTRACK 8u   /* S4: final argmin, backtracking, seed gather */
+#define CPP_STAGE_LM 16u         /* S5: Levenberg-Marquardt */
+#define CPP_STAGE_CHECK 32u      /* S6: FP64 check and report */
+#define CPP_STAGE_ALL 63u
+
+typedef struct cpp_batch cpp_batch_t;
+cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots,
+                            const cpp_params_t* params, const cpp_plan_desc_t* descs,
+                            int32_t count, void* workspace, size_t ws_bytes,
+                            int32_t* dev_status, cpp_stream_t stream, cpp_batch_t** out);
+cpp_status cpp_batch_run(cpp_batch_t* batch, uint32_t stages, cpp_stream_t stream);
+/* Number of kernel launches cpp_batch_run(batch, stages, ...) enqueues. */
+int32_t cpp_batch_launches(const cpp_batch_t* batch, uint32_t stages);
+void cpp_batch_destroy(cpp_batch_t* batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,9 @@ MAXJ = 16
 OK, PENDING, ERR_INVALID_ARG, ERR_INFEASIBLE, ERR_OOM, ERR_BUDGET, ERR_TIMEOUT, ERR_CUDA, \
     ERR_NOT_FOUND, ERR_CANCELLED = range(10)
 MASK_OUT, MASK_NEAR, MASK_POSE, MASK_NONFINITE, MASK_PAD = 1, 2, 4, 8, 16
+STAGE_MASK, STAGE_LAYER_MIN, STAGE_DP_FORWARD, STAGE_BACKTRACK, STAGE_LM, STAGE_CHECK = \
+    1, 2, 4, 8, 16, 32
+STAGE_ALL = 63
 
 
 class CppflowError(RuntimeError):
@@ -77,6 +80,11 @@ _SIGS = {
                            _P, _P, _P, _P, _P, _P, _P]),
     "cpp_plan_batch_workspace_size": (C.c_size_t, [_P, C.c_int32, _P, C.c_int32]),
     "cpp_plan_batch": (C.c_int, [_P, C.c_int32, _P, _P, C.c_int32, _P, C.c_size_t, _P, _P]),
+    "cpp_batch_create": (C.c_int, [_P, C.c_int32, _P, _P, C.c_int32, _P, C.c_size_t, _P, _P,
+                                   C.POINTER(C.c_void_p)]),
+    "cpp_batch_run": (C.c_int, [_P, C.c_uint32, _P]),
+    "cpp_batch_launches": (C.c_int32, [_P, C.c_uint32]),
+    "cpp_batch_destroy": (None, [_P]),
 }
 
 
@@ -225,6 +233,38 @@ def plan_batch(robots, params: Params, descs, workspace, dev_status=None, stream
     nbytes = workspace.numel() * workspace.element_size()
     _check(lib().cpp_plan_batch(R, len(robots), C.byref(params), D, len(descs), ptr(workspace),
                                 nbytes, ptr(dev_status), stream_handle(stream)), "cpp_plan_batch")
+
+
+class Batch:
+    """A prepared batch (cpp_batch_create); run() enqueues any subset of stages."""
+
+    def __init__(self, robots, params: Params, descs, workspace, dev_status=None, stream=None):
+        D = (PlanDesc * len(descs))(*descs)
+        R = (Robot * len(robots))(*robots)
+        h = C.c_void_p()
+        nbytes = workspace.numel() * workspace.element_size()
+        _check(lib().cpp_batch_create(R, len(robots), C.byref(params), D, len(descs),
+                                      ptr(workspace), nbytes, ptr(dev_status),
+                                      stream_handle(stream), C.byref(h)), "cpp_batch_create")
+        self.handle = h
+        self.count = len(descs)
+
+    def run(self, stages: int = STAGE_ALL, stream=None):
+        _check(lib().cpp_batch_run(self.handle, stages, stream_handle(stream)), "cpp_batch_run")
+
+    def launches(self, stages: int = STAGE_ALL) -> int:
+        return lib().cpp_batch_launches(self.handle, stages)
+
+    def close(self):
+        if self.handle:
+            lib().cpp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def report_from_bytes(buf: bytes) -> dict:

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -222,7 +223,8 @@ cpp_status cpp_dp_search(const float* cand, const float* pen, int32_t T, int32_t
   s.r.costT = reinterpret_cast<float*>(ws + L.costT);
   s.r.sel = sel; s.r.best_cost = best_cost; s.r.q_seed = q_seed; s.r.status = dev_status;
   memset(&s.robot, 0, sizeof(s.robot));
-  return cuda_status(launch_dp(s, (cudaStream_t)stream), "cpp_dp_search");
+  return cuda_status(launch_dp(s, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK,
+                               (cudaStream_t)stream), "cpp_dp_search");
 }
 
 cpp_status cpp_lm_refine(const cpp_robot_t* robot, const cpp_params_t* params, const float* q_in,
@@ -296,7 +298,9 @@ cpp_status cpp_plan(const cpp_robot_t* robot, const cpp_params_t* params, const 
   s.r.status = dev_status;
   s.robot = *robot;
   if (cpp_status e = cuda_status(launch_mask(s, *params, st), "cpp_plan/mask")) return e;
-  if (cpp_status e = cuda_status(launch_dp(s, st), "cpp_plan/dp")) return e;
+  if (cpp_status e = cuda_status(launch_dp(s, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD |
+                                                   CPP_STAGE_BACKTRACK, st), "cpp_plan/dp"))
+    return e;
   // the check below writes the FP64 pose errors
   if (cpp_status e = cuda_status(launch_lm(s, *params, false, st), "cpp_plan/lm")) return e;
   return cuda_status(launch_check(s, *params, st), "cpp_plan/check");
@@ -334,9 +338,23 @@ size_t cpp_plan_batch_workspace_size(const cpp_plan_desc_t* descs, int32_t count
   return batch_layout(descs, count, n_robots, robots).total;
 }
 
-cpp_status cpp_plan_batch(const cpp_robot_t* robots, int32_t n_robots, const cpp_params_t* params,
-                          const cpp_plan_desc_t* descs, int32_t count, void* workspace,
-                          size_t ws_bytes, int32_t* dev_status, cpp_stream_t stream) {
+}  // extern "C"
+
+struct cpp_batch {
+  BatchSrc src;
+  cpp_params_t params;
+  int n, count, max_T, max_Kp;
+  long long max_tasks;
+};
+
+extern "C" {
+
+cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const cpp_params_t* params,
+                            const cpp_plan_desc_t* descs, int32_t count, void* workspace,
+                            size_t ws_bytes, int32_t* dev_status, cpp_stream_t stream,
+                            cpp_batch_t** out) {
+  if (!out) return fail(CPP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
   if (!robots || n_robots < 1) return fail(CPP_ERR_INVALID_ARG, "no robots");
   for (int k = 0; k < n_robots; ++k)
     if (cpp_status s = check_robot(&robots[k])) return s;
@@ -386,21 +404,63 @@ cpp_status cpp_plan_batch(const cpp_robot_t* robots, int32_t n_robots, const cpp
   cudaStream_t st = (cudaStream_t)stream;
   // pageable sources: the copies are staged before cudaMemcpyAsync returns
   if (cpp_status e = cuda_status(cudaMemcpyAsync(ws + B.reqs, reqs.data(), sizeof(Req) * count,
-                                                 cudaMemcpyHostToDevice, st), "cpp_plan_batch/H2D"))
+                                                 cudaMemcpyHostToDevice, st), "cpp_batch_create"))
     return e;
   if (cpp_status e = cuda_status(cudaMemcpyAsync(ws + B.robots, robots,
                                                  sizeof(cpp_robot_t) * n_robots,
-                                                 cudaMemcpyHostToDevice, st), "cpp_plan_batch/H2D"))
+                                                 cudaMemcpyHostToDevice, st), "cpp_batch_create"))
     return e;
-  BatchSrc s{reinterpret_cast<const Req*>(ws + B.reqs),
-             reinterpret_cast<const cpp_robot_t*>(ws + B.robots)};
-  if (cpp_status e = cuda_status(launch_mask_batch(s, n, count, max_tasks, *params, st), "batch/mask"))
+  cpp_batch* b = new (std::nothrow) cpp_batch;
+  if (!b) return fail(CPP_ERR_OOM, "host allocation failed");
+  b->src = BatchSrc{reinterpret_cast<const Req*>(ws + B.reqs),
+                    reinterpret_cast<const cpp_robot_t*>(ws + B.robots)};
+  b->params = *params;
+  b->n = n; b->count = count; b->max_T = max_T; b->max_Kp = max_Kp; b->max_tasks = max_tasks;
+  *out = b;
+  return CPP_OK;
+}
+
+cpp_status cpp_batch_run(cpp_batch_t* b, uint32_t stages, cpp_stream_t stream) {
+  if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (stages & CPP_STAGE_MASK)
+    if (cpp_status e = cuda_status(launch_mask_batch(b->src, b->n, b->count, b->max_tasks,
+                                                     b->params, st), "batch/mask"))
+      return e;
+  const unsigned dp = stages & (CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK);
+  if (dp)
+    if (cpp_status e = cuda_status(launch_dp_batch(b->src, dp, b->n, b->count, b->max_T,
+                                                   b->max_Kp, st), "batch/dp"))
+      return e;
+  if (stages & CPP_STAGE_LM)
+    if (cpp_status e = cuda_status(launch_lm_batch(b->src, b->count, b->max_T, b->params, st),
+                                   "batch/lm"))
+      return e;
+  if (stages & CPP_STAGE_CHECK)
+    return cuda_status(launch_check_batch(b->src, b->count, b->params, st), "batch/check");
+  return CPP_OK;
+}
+
+int32_t cpp_batch_launches(const cpp_batch_t* b, uint32_t stages) {
+  if (!b) return 0;
+  int c = 0;
+  for (unsigned s = 1; s <= CPP_STAGE_CHECK; s <<= 1)
+    if (stages & s) ++c;
+  return c;
+}
+
+void cpp_batch_destroy(cpp_batch_t* b) { delete b; }
+
+cpp_status cpp_plan_batch(const cpp_robot_t* robots, int32_t n_robots, const cpp_params_t* params,
+                          const cpp_plan_desc_t* descs, int32_t count, void* workspace,
+                          size_t ws_bytes, int32_t* dev_status, cpp_stream_t stream) {
+  cpp_batch_t* b = nullptr;
+  if (cpp_status e = cpp_batch_create(robots, n_robots, params, descs, count, workspace, ws_bytes,
+                                      dev_status, stream, &b))
     return e;
-  if (cpp_status e = cuda_status(launch_dp_batch(s, n, count, max_T, max_Kp, st), "batch/dp"))
-    return e;
-  if (cpp_status e = cuda_status(launch_lm_batch(s, count, max_T, *params, st), "batch/lm"))
-    return e;
-  return cuda_status(launch_check_batch(s, count, *params, st), "batch/check");
+  const cpp_status e = cpp_batch_run(b, CPP_STAGE_ALL, stream);
+  cpp_batch_destroy(b);
+  return e;
 }
 
 }  // extern "C"

@@ -297,57 +297,65 @@ __global__ void __launch_bounds__(kBtThreads) dp_backtrack_kernel(const __grid_c
 
 // ------------------------------------------------------------------ launchers
 template <class KernelT>
-static void allow_smem(KernelT kernel) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+static cudaError_t allow_smem(KernelT kernel, size_t bytes) {
+  if (bytes <= 48u * 1024u) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int NJ, int R, class Src>
+static cudaError_t launch_fwd_r(const Src& s, int nreq, size_t smem, cudaStream_t st) {
+  cudaError_t e = allow_smem(dp_forward_kernel<NJ, R, Src>, smem);
+  if (e != cudaSuccess) return e;
+  dp_forward_kernel<NJ, R, Src><<<nreq, kDpThreads, smem, st>>>(s);
+  return cudaGetLastError();
 }
 
 template <int NJ, class Src>
 static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
   const size_t smem = dp_smem_bytes(NJ, max_Kp);
   const int R = (max_Kp + kDpThreads - 1) / kDpThreads;
-  if (R <= 1) {
-    allow_smem(dp_forward_kernel<NJ, 1, Src>);
-    dp_forward_kernel<NJ, 1, Src><<<nreq, kDpThreads, smem, st>>>(s);
-  } else if (R <= 2) {
-    allow_smem(dp_forward_kernel<NJ, 2, Src>);
-    dp_forward_kernel<NJ, 2, Src><<<nreq, kDpThreads, smem, st>>>(s);
-  } else {
-    allow_smem(dp_forward_kernel<NJ, 4, Src>);
-    dp_forward_kernel<NJ, 4, Src><<<nreq, kDpThreads, smem, st>>>(s);
-  }
-  return cudaGetLastError();
+  if (R <= 1) return launch_fwd_r<NJ, 1>(s, nreq, smem, st);
+  if (R <= 2) return launch_fwd_r<NJ, 2>(s, nreq, smem, st);
+  return launch_fwd_r<NJ, 4>(s, nreq, smem, st);
 }
 
 template <class Src>
-static cudaError_t launch_dp_t(const Src& s, int n, int nreq, int max_T, int max_Kp,
-                               cudaStream_t st) {
-  {
+static cudaError_t launch_dp_t(const Src& s, unsigned stages, int n, int nreq, int max_T,
+                               int max_Kp, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (stages & CPP_STAGE_LAYER_MIN) {
     dim3 grid((unsigned)((max_T + 7) / 8), (unsigned)nreq);
     layer_min_kernel<Src><<<grid, 256, 0, st>>>(s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  cudaError_t e;
-  const bool fast = max_Kp <= 4 * kDpThreads;
-  if (fast && n == 7) e = launch_fwd_nj<7>(s, nreq, max_Kp, st);
-  else if (fast && n == 9) e = launch_fwd_nj<9>(s, nreq, max_Kp, st);
-  else if (fast && n == 6) e = launch_fwd_nj<6>(s, nreq, max_Kp, st);
-  else {
-    allow_smem(dp_forward_generic<Src>);
-    dp_forward_generic<Src><<<nreq, kDpThreads, dp_smem_bytes(n, max_Kp), st>>>(s);
+  if (stages & CPP_STAGE_DP_FORWARD) {
+    const bool fast = max_Kp <= 4 * kDpThreads;
+    if (fast && n == 7) e = launch_fwd_nj<7>(s, nreq, max_Kp, st);
+    else if (fast && n == 9) e = launch_fwd_nj<9>(s, nreq, max_Kp, st);
+    else if (fast && n == 6) e = launch_fwd_nj<6>(s, nreq, max_Kp, st);
+    else {
+      const size_t smem = dp_smem_bytes(n, max_Kp);
+      if ((e = allow_smem(dp_forward_generic<Src>, smem)) != cudaSuccess) return e;
+      dp_forward_generic<Src><<<nreq, kDpThreads, smem, st>>>(s);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if (stages & CPP_STAGE_BACKTRACK) {
+    if ((e = allow_smem(dp_backtrack_kernel<Src>, 2 * kBtChunkBytes)) != cudaSuccess) return e;
+    dp_backtrack_kernel<Src><<<nreq, kBtThreads, 2 * kBtChunkBytes, st>>>(s);
     e = cudaGetLastError();
   }
-  if (e != cudaSuccess) return e;
-  allow_smem(dp_backtrack_kernel<Src>);
-  dp_backtrack_kernel<Src><<<nreq, kBtThreads, 2 * kBtChunkBytes, st>>>(s);
-  return cudaGetLastError();
+  return e;
 }
 
-cudaError_t launch_dp(const SingleSrc& s, cudaStream_t st) {
-  return launch_dp_t(s, s.r.n, 1, s.r.T, s.r.Kp, st);
+cudaError_t launch_dp(const SingleSrc& s, unsigned stages, cudaStream_t st) {
+  return launch_dp_t(s, stages, s.r.n, 1, s.r.T, s.r.Kp, st);
 }
 
-cudaError_t launch_dp_batch(const BatchSrc& s, int n, int nreq, int max_T, int max_Kp,
-                            cudaStream_t st) {
-  return launch_dp_t(s, n, nreq, max_T, max_Kp, st);
+cudaError_t launch_dp_batch(const BatchSrc& s, unsigned stages, int n, int nreq, int max_T,
+                            int max_Kp, cudaStream_t st) {
+  return launch_dp_t(s, stages, n, nreq, max_T, max_Kp, st);
 }
 
 }  // namespace cppflow

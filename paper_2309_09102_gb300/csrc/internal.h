@@ -24,9 +24,9 @@ cudaError_t launch_fk_pose64(const cpp_robot_t& r, const double* q, long long N,
 int bp_stride(int Kp);
 size_t dp_smem_bytes(int n, int Kp);
 bool dp_supported(int n, int Kp);
-cudaError_t launch_dp(const SingleSrc& s, cudaStream_t st);
-cudaError_t launch_dp_batch(const BatchSrc& s, int n, int nreq, int max_T, int max_Kp,
-                            cudaStream_t st);
+cudaError_t launch_dp(const SingleSrc& s, unsigned stages, cudaStream_t st);
+cudaError_t launch_dp_batch(const BatchSrc& s, unsigned stages, int n, int nreq, int max_T,
+                            int max_Kp, cudaStream_t st);
 
 // lm.cu
 cudaError_t launch_lm(const SingleSrc& s, const cpp_params_t& P, bool want_err, cudaStream_t st);

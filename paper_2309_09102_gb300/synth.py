@@ -133,14 +133,16 @@ def draw_truth(seed: int, n: int, T: int, wrist: bool = False, max_jump_deg: flo
 
 
 def wrong_branch_start(truth: np.ndarray, joint: int = 3) -> np.ndarray:
-    """Start of the wrong-branch re-solve: joint 4 (1-based) negated."""
+    """Start of the wrong-branch re-solve: joint 4 (1-based) negated. Arms with
+    fewer than 5 joints have no wrong branch (the true configuration is returned)."""
     q = truth.copy()
-    q[:, joint] = -q[:, joint]
+    if q.shape[1] > joint + 1:
+        q[:, joint] = -q[:, joint]
     return q
 
 
 def wrong_branch_free_mask(n: int, first: int = 4) -> int:
-    """Joints 5..n (1-based) are re-solved; the others stay fixed."""
+    """Joints 5..n (1-based) are re-solved; the others stay fixed (0 if n < 5)."""
     return sum(1 << j for j in range(first, n))
 
 

@@ -40,8 +40,12 @@ def build(w: synth.Workload, **param_overrides) -> Problem:
     robot = oracle_robot(arm)
     truth = synth.draw_truth(w.path_seed, w.n, w.T, w.wrist)
     targets = oracle.fk_pose(robot, truth)
-    P_wb = oracle.make_params(lm_iters=30, free_mask=synth.wrong_branch_free_mask(w.n))
-    q_wb, _, _ = oracle.lm(robot, P_wb, synth.wrong_branch_start(truth), targets)
+    free = synth.wrong_branch_free_mask(w.n)
+    if free:
+        P_wb = oracle.make_params(lm_iters=30, free_mask=free)
+        q_wb, _, _ = oracle.lm(robot, P_wb, synth.wrong_branch_start(truth), targets)
+    else:
+        q_wb = truth.copy()
     draws = synth.draw_candidates(w.cand_seed, w.T, w.K, w.n, w.p_wb, w.p_out)
     cand = synth.assemble(truth, q_wb, draws, w.sigma, arm.lo, arm.hi)
     kw = dict(lm_iters=w.lm_iters, lambda0=w.lambda0)
