@@ -254,6 +254,78 @@ cpp_status cpp_batch_run(cpp_batch_t* batch, uint32_t stages, cpp_stream_t strea
 int32_t cpp_batch_launches(const cpp_batch_t* batch, uint32_t stages);
 void cpp_batch_destroy(cpp_batch_t* batch);
 
+/* ------------------------------------------------------------------ serving
+ * A continuous-batching request loop (not in the paper). Clients submit plans
+ * with HOST buffers from any thread; a worker thread admits queued requests
+ * while request slots and the HBM budget allow (each admitted request keeps its
+ * lattice, targets, search tables and results resident in a device arena of
+ * hbm_budget_bytes), groups requests of the same joint count into one batched
+ * launch per stage, and keeps up to max_inflight launches on the device at once,
+ * so requests that arrive while others run are admitted as memory frees up and
+ * their work overlaps. Every request runs with the server's params. */
+typedef struct cpp_server cpp_server_t;
+
+typedef struct cpp_server_config {
+    int32_t device;           /* CUDA device ordinal */
+    int32_t max_slots;        /* requests resident on the device at once (default 1024) */
+    int32_t max_batch;        /* requests per launch (default 512) */
+    int32_t max_inflight;     /* launches in flight, 1..16 (default 2) */
+    size_t hbm_budget_bytes;  /* device arena for resident requests (default 40 GiB) */
+    size_t pinned_bytes;      /* pinned host staging; 0 = pageable only (default 1 GiB) */
+    cpp_params_t params;      /* settings of every request */
+} cpp_server_config_t;
+
+#define CPP_REQ_BORROW 1  /* inputs stay valid and unchanged until the plan is collected:
+                             no copy at submit (pinned inputs then go straight to the device) */
+
+typedef struct cpp_plan_req {
+    const cpp_robot_t* robot;  /* host */
+    int32_t T, K, Kp;          /* lattice shape, as for cpp_plan */
+    int32_t flags;             /* 0 or CPP_REQ_BORROW */
+    const float* cand;         /* host [T][n][Kp] */
+    const double* targets;     /* host [T][7] */
+} cpp_plan_req_t;
+
+typedef struct cpp_plan_result {  /* caller-owned HOST buffers; any pointer may be NULL */
+    int32_t* sel;           /* [T] */
+    float* q;               /* [T][n] */
+    double* pose_err;       /* [T][2] */
+    cpp_report_t* report;   /* [1] */
+    float* best_cost;       /* [1] */
+    double latency_ms;      /* out: submit -> completion seen by the server */
+    int32_t dev_status;     /* out: device status word of the request */
+    int32_t reserved;
+} cpp_plan_result_t;
+
+typedef struct cpp_server_stats {
+    uint64_t submitted, completed, failed, cancelled, batches, sum_batch;
+    int32_t max_batch_seen, resident, queued, reserved;
+    size_t hbm_used, hbm_high_water;
+} cpp_server_stats_t;
+
+void cpp_server_config_default(cpp_server_config_t* cfg);
+/* Allocates the device arena and pinned pool and starts the worker.
+ * OOM if the arena cannot be allocated. */
+cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out);
+/* Validates on the host (robot, lattice shape, finite targets with unit
+ * quaternions within 1e-6), copies the inputs unless CPP_REQ_BORROW, queues the
+ * request and returns its ticket. BUDGET if the request alone exceeds the arena.
+ * Non-finite candidates are allowed (masked on the device). */
+cpp_status cpp_plan_submit(cpp_server_t* srv, const cpp_plan_req_t* req, uint64_t* ticket);
+/* PENDING until the plan is done; then copies the results into `res`, forgets the
+ * ticket and returns the plan's status (OK, INFEASIBLE, CUDA, CANCELLED).
+ * NOT_FOUND for an unknown or already collected ticket. */
+cpp_status cpp_plan_poll(cpp_server_t* srv, uint64_t ticket, cpp_plan_result_t* res);
+/* As poll, but blocks up to timeout_us (negative = no limit); PENDING on timeout. */
+cpp_status cpp_plan_wait(cpp_server_t* srv, uint64_t ticket, cpp_plan_result_t* res,
+                         int64_t timeout_us);
+/* Removes a request that is still queued (OK; its poll returns CANCELLED);
+ * PENDING if it is already on the device or finished. */
+cpp_status cpp_plan_cancel(cpp_server_t* srv, uint64_t ticket);
+cpp_status cpp_server_get_stats(cpp_server_t* srv, cpp_server_stats_t* out);
+/* Finishes the launches in flight, cancels queued requests, frees everything. */
+void cpp_server_destroy(cpp_server_t* srv);
+
 #ifdef __cplusplus
 }
 #endif

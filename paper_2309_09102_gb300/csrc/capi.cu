@@ -33,8 +33,6 @@ cpp_status cuda_status(cudaError_t e, const char* where) {
   return fail(CPP_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
 bool finite_d(double v) { return std::isfinite(v); }
 
 cpp_status check_robot(const cpp_robot_t* r) {
@@ -77,36 +75,6 @@ cpp_status check_lattice(int T, int K, int Kp, int n) {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-struct DpLayout {
-  size_t pen_min, bp, costT, total;
-};
-DpLayout dp_layout(int T, int Kp) {
-  DpLayout L;
-  size_t o = 0;
-  L.pen_min = o; o += align256((size_t)T * sizeof(float));
-  L.bp = o;      o += align256((size_t)T * bp_stride(Kp) * sizeof(uint16_t));
-  L.costT = o;   o += align256((size_t)Kp * sizeof(float));
-  L.total = o;
-  return L;
-}
-
-struct PlanLayout {
-  DpLayout dp;
-  size_t dp_base, mask, pen, q_seed, total;
-};
-PlanLayout plan_layout(int T, int K, int Kp, int n) {
-  (void)K;
-  PlanLayout L;
-  L.dp = dp_layout(T, Kp);
-  size_t o = 0;
-  L.dp_base = o; o += L.dp.total;
-  L.mask = o;    o += align256((size_t)T * Kp);
-  L.pen = o;     o += align256((size_t)T * Kp * sizeof(float));
-  L.q_seed = o;  o += align256((size_t)T * n * sizeof(float));
-  L.total = o;
-  return L;
-}
-
 Req empty_req() {
   Req r;
   memset(&r, 0, sizeof(r));
@@ -114,6 +82,10 @@ Req empty_req() {
 }
 
 }  // namespace
+
+namespace cppflow {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace cppflow
 
 extern "C" {
 
@@ -261,7 +233,7 @@ cpp_status cpp_check(const cpp_robot_t* robot, const cpp_params_t* params, const
 
 size_t cpp_plan_workspace_size(int32_t T, int32_t K, int32_t Kp, int32_t n) {
   if (T < 1 || K < 1 || Kp < K || n < 1) return 0;
-  return plan_layout(T, K, Kp, n).total;
+  return plan_layout(T, Kp, n).total;
 }
 
 cpp_status cpp_plan(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
@@ -278,7 +250,7 @@ cpp_status cpp_plan(const cpp_robot_t* robot, const cpp_params_t* params, const 
   if (!cand || !targets || !sel || !best_cost || !q_out || !workspace)
     return fail(CPP_ERR_INVALID_ARG, "NULL buffer");
   if (!aligned(cand, 16)) return fail(CPP_ERR_INVALID_ARG, "cand must be 16-byte aligned");
-  const PlanLayout L = plan_layout(T, K, Kp, n);
+  const PlanLayout L = plan_layout(T, Kp, n);
   if (ws_bytes < L.total || !aligned(workspace, 256))
     return fail(CPP_ERR_INVALID_ARG, "workspace needs %zu bytes, 256-byte aligned", L.total);
   char* ws = static_cast<char*>(workspace);
@@ -321,7 +293,7 @@ BatchLayout batch_layout(const cpp_plan_desc_t* d, int count, int n_robots, cons
   B.per_req_base = o;
   for (int r = 0; r < count; ++r) {
     const int n = robots[d[r].robot].n;
-    B.L.push_back(plan_layout(d[r].T, d[r].K, d[r].Kp, n));
+    B.L.push_back(plan_layout(d[r].T, d[r].Kp, n));
     B.off.push_back(o);
     o += B.L.back().total;
   }
@@ -433,7 +405,7 @@ cpp_status cpp_batch_run(cpp_batch_t* b, uint32_t stages, cpp_stream_t stream) {
                                                    b->max_Kp, st), "batch/dp"))
       return e;
   if (stages & CPP_STAGE_LM)
-    if (cpp_status e = cuda_status(launch_lm_batch(b->src, b->count, b->max_T, b->params, st),
+    if (cpp_status e = cuda_status(launch_lm_batch(b->src, b->n, b->count, b->max_T, b->params, st),
                                    "batch/lm"))
       return e;
   if (stages & CPP_STAGE_CHECK)

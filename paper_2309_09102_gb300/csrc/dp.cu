@@ -37,7 +37,13 @@ int bp_stride(int Kp) { return (Kp + 7) & ~7; }
 
 size_t dp_smem_bytes(int n, int Kp) { return (size_t)(2 * n + 2) * Kp * sizeof(float); }
 
-bool dp_supported(int n, int Kp) { return dp_smem_bytes(n, Kp) <= 227u * 1024u; }
+size_t dp2_smem_bytes(int nj, int Kp);
+
+bool dp_supported(int n, int Kp) {
+  if (dp_smem_bytes(n, Kp) > 227u * 1024u) return false;
+  const bool fast = (n == 6 || n == 7 || n == 9) && Kp <= 1024;
+  return !fast || dp2_smem_bytes(n, Kp) <= 227u * 1024u;
+}
 
 // ------------------------------------------------------------------ layer minimum
 template <class Src>
@@ -159,6 +165,259 @@ __global__ void __launch_bounds__(kDpThreads) dp_forward_kernel(const __grid_con
   }
   const float* cfin = cbase + ((T - 1) & 1) * Kp;
   for (int k = tid; k < Kp; k += kDpThreads) rq.costT[k] = cfin[k];
+}
+
+// ------------------------------------------------------------------ forward sweep, staged
+// Second form of the sweep (used for n in {6, 7, 9}, Kp <= 1024):
+//  * each layer's raw block q_i [n][Kp] and node-cost row pen_i arrive in shared
+//    memory by 1-D bulk copies (TMA engine, mbarrier completion) issued two
+//    steps ahead, so no thread waits on HBM inside the sweep;
+//  * every node k of the current layer is a record [-q_{k,0} .. -q_{k,n-1}, C_k]
+//    (NW floats, 16-byte multiple): one predecessor costs NW/4 broadcast float4
+//    loads, and the joint differences are packed FP32 pair additions
+//    q' + (-q) (bit-identical to q' - q, round-to-nearest);
+//  * the sweep keeps only the running minimum per 32-node tile and the first
+//    tile that lowered it; the lowest index attaining the minimum is then
+//    recovered by re-evaluating that one tile. Same values, same ties.
+template <int NJ>
+struct Rec {
+  static constexpr int NW = ((NJ + 1 + 3) / 4) * 4;  // floats per record
+  static constexpr int NP = (NJ + 1) / 2;             // packed pairs of own joints
+};
+
+__device__ __forceinline__ uint64_t pack2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t addx2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// max_j |own_j - q_j| for one predecessor record (negated joints in rec[0..NJ-1]).
+// The differences are packed pair additions own + (-q); the absolute values are
+// folded into three-input max operations (max is exact, so any grouping gives the
+// same value, and NaN terms are ignored as with fmaxf).
+template <int NJ>
+__device__ __forceinline__ float linf_rec(const uint64_t (&own)[Rec<NJ>::NP], const float* rec) {
+  float a[2 * Rec<NJ>::NP];
+#pragma unroll
+  for (int p = 0; p < Rec<NJ>::NP; ++p) {
+    if (2 * p + 1 < NJ) {
+      unpack2(addx2(own[p], pack2(rec[2 * p], rec[2 * p + 1])), a[2 * p], a[2 * p + 1]);
+    } else {
+      float ol, oh;
+      unpack2(own[p], ol, oh);
+      a[2 * p] = ol + rec[2 * p];
+    }
+  }
+  if (NJ == 1) return fabsf(a[0]);
+  if (NJ == 2) return fmaxf(fabsf(a[0]), fabsf(a[1]));
+  float d = max3f(fabsf(a[0]), fabsf(a[1]), fabsf(a[2]));
+  int j = 3;
+#pragma unroll
+  for (; j + 1 < NJ; j += 2) d = max3f(d, fabsf(a[j]), fabsf(a[j + 1]));
+  if (j < NJ) d = fmaxf(d, fabsf(a[j]));
+  return d;
+}
+
+constexpr int kDp2Threads = 256;
+constexpr int kDp2Tile = 32;
+
+// Records of one layer: node k at float offset k * NW + (k / 32) * 4. The
+// 16-byte skew per 32-node tile puts the same slot of different tiles on
+// different shared-memory banks (the tile rescan reads one tile per thread).
+__host__ __device__ __forceinline__ int rec_layer_floats(int NW, int Kp) {
+  return Kp * NW + ((Kp + 31) / 32) * 4;
+}
+__device__ __forceinline__ int rec_off(int NW, int k) { return k * NW + (k >> 5) * 4; }
+
+size_t dp2_smem_bytes(int nj, int Kp) {
+  const int NW = ((nj + 1 + 3) / 4) * 4;
+  return (size_t)2 * rec_layer_floats(NW, Kp) * 4  // records, two layers
+         + (size_t)2 * nj * Kp * 4    // raw layer staging, two slots
+         + (size_t)2 * Kp * 4         // node-cost staging, two slots
+         + 64;                        // barriers
+}
+
+template <int NJ, int R, class Src>
+__global__ void __launch_bounds__(kDp2Threads) dp2_forward_kernel(const __grid_constant__ Src src) {
+  constexpr int NW = Rec<NJ>::NW, NP = Rec<NJ>::NP;
+  const Req& rq = src.req(blockIdx.x);
+  const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
+  const int tid = threadIdx.x;
+  extern __shared__ __align__(128) float sm2[];
+  const int RL = rec_layer_floats(NW, Kp);
+  float* const rec = sm2;                                 // [2][RL] (records, skewed)
+  float* const stg = rec + 2 * (size_t)RL;                // [2][NJ][Kp]
+  float* const pst = stg + 2 * (size_t)NJ * Kp;           // [2][Kp]
+  uint64_t* const bars = reinterpret_cast<uint64_t*>(pst + 2 * (size_t)Kp);
+  __shared__ int timeout_flag;
+
+  const uint32_t layer_bytes = (uint32_t)(NJ * Kp * 4), pen_bytes = (uint32_t)(Kp * 4);
+  auto issue = [&](int L) {  // one thread: stage layer L into slot L & 1
+    const int sl = L & 1;
+    mbar_expect_tx(&bars[sl], layer_bytes + pen_bytes);
+    bulk_g2s(stg + (size_t)sl * NJ * Kp, rq.cand + (size_t)L * NJ * Kp, layer_bytes, &bars[sl]);
+    bulk_g2s(pst + (size_t)sl * Kp, rq.pen + (size_t)L * Kp, pen_bytes, &bars[sl]);
+  };
+  auto wait_layer = [&](int L) -> bool {
+    return mbar_wait_bounded(&bars[L & 1], (uint32_t)((L >> 1) & 1));
+  };
+
+  if (tid == 0) {
+    timeout_flag = 0;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    issue(0);
+    if (T > 1) issue(1);
+  }
+  if (!wait_layer(0)) atomicExch(&timeout_flag, 1);
+  {
+    const float m0 = rq.pen_min[0];
+    for (int k = tid; k < Kp; k += kDp2Threads) {
+      float* rk = rec + rec_off(NW, k);
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) rk[j] = -stg[(size_t)j * Kp + k];
+      rk[NJ] = k < K ? pst[k] - m0 : CUDART_INF_F;
+#pragma unroll
+      for (int j = NJ + 1; j < NW; ++j) rk[j] = 0.f;
+    }
+  }
+  __syncthreads();
+  if (timeout_flag) {
+    raise_status(rq.status, CPP_ERR_TIMEOUT);
+    if (tid == 0 && T > 1) wait_layer(1);
+    return;
+  }
+  if (tid == 0 && T > 2) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(2);
+  }
+
+  int kp[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) kp[r] = tid + r * kDp2Threads;
+  const int K4 = (K + 3) & ~3;
+  const int ntiles = (K4 + kDp2Tile - 1) / kDp2Tile;
+
+  for (int i = 0; i + 1 < T; ++i) {
+    const int L = i + 1;
+    if (!wait_layer(L)) atomicExch(&timeout_flag, 1);
+    const float* sq = stg + (size_t)(L & 1) * NJ * Kp;
+    const float* sp = pst + (size_t)(L & 1) * Kp;
+    const float* rc = rec + (size_t)(i & 1) * RL;
+    float* rn = rec + (size_t)(L & 1) * RL;
+    const float m1 = rq.pen_min[L];
+
+    uint64_t own[R][NP];
+    float rpen[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = kp[r] < Kp ? kp[r] : Kp - 1;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const float a = sq[(size_t)(2 * p) * Kp + k];
+        const float b = (2 * p + 1 < NJ) ? sq[(size_t)(2 * p + 1) * Kp + k] : 0.f;
+        own[r][p] = pack2(a, b);
+      }
+      rpen[r] = kp[r] < K ? sp[kp[r]] - m1 : CUDART_INF_F;
+    }
+
+    float best[R];
+    int btile[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; btile[r] = -1; }
+
+#pragma unroll 1
+    for (int t = 0; t < ntiles; ++t) {
+      const int kb = t * kDp2Tile, ke = min(kb + kDp2Tile, K4);
+      float tb[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) tb[r] = CUDART_INF_F;
+#pragma unroll 2
+      for (int k = kb; k < ke; k += 2) {  // ke - kb is a multiple of 4
+        float r0[NW], r1[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(rc + rec_off(NW, k) + w);
+          const float4 u = *reinterpret_cast<const float4*>(rc + rec_off(NW, k + 1) + w);
+          r0[w] = v.x; r0[w + 1] = v.y; r0[w + 2] = v.z; r0[w + 3] = v.w;
+          r1[w] = u.x; r1[w + 1] = u.y; r1[w + 2] = u.z; r1[w + 3] = u.w;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          tb[r] = min3f(tb[r], r0[NJ] + linf_rec<NJ>(own[r], r0), r1[NJ] + linf_rec<NJ>(own[r], r1));
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (tb[r] < best[r]) { best[r] = tb[r]; btile[r] = t; }
+    }
+
+    // lowest index attaining the minimum, inside the first tile that reached it
+    uint16_t* bprow = rq.bp + (size_t)L * Kb;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int arg = 0;
+      if (btile[r] >= 0) {
+        const int kb = btile[r] * kDp2Tile, ke = min(kb + kDp2Tile, K4);
+        for (int k = kb; k < ke; ++k) {
+          const float* rk = rc + rec_off(NW, k);
+          if (rk[NJ] + linf_rec<NJ>(own[r], rk) == best[r]) { arg = k; break; }
+        }
+      }
+      if (kp[r] < Kp) {
+        float v[NW];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          float a, b;
+          unpack2(own[r][p], a, b);
+          v[2 * p] = -a;
+          if (2 * p + 1 < NJ) v[2 * p + 1] = -b;
+        }
+        v[NJ] = kp[r] < K ? best[r] + rpen[r] : CUDART_INF_F;
+#pragma unroll
+        for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
+        float4* dst = reinterpret_cast<float4*>(rn + rec_off(NW, kp[r]));
+#pragma unroll
+        for (int w = 0; w < NW / 4; ++w)
+          dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
+        bprow[kp[r]] = (uint16_t)arg;
+      }
+    }
+    __syncthreads();
+    if (timeout_flag) {
+      raise_status(rq.status, CPP_ERR_TIMEOUT);
+      if (tid == 0 && L + 1 < T) wait_layer(L + 1);
+      return;
+    }
+    if (tid == 0 && L + 2 < T) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(L + 2);
+    }
+  }
+  const float* rf = rec + (size_t)((T - 1) & 1) * RL;
+  for (int k = tid; k < Kp; k += kDp2Threads) rq.costT[k] = rf[rec_off(NW, k) + NJ];
 }
 
 // Any n and Kp that fit in shared memory: successor values are read back from
@@ -310,13 +569,21 @@ static cudaError_t launch_fwd_r(const Src& s, int nreq, size_t smem, cudaStream_
   return cudaGetLastError();
 }
 
+template <int NJ, int R, class Src>
+static cudaError_t launch_fwd2_r(const Src& s, int nreq, size_t smem, cudaStream_t st) {
+  cudaError_t e = allow_smem(dp2_forward_kernel<NJ, R, Src>, smem);
+  if (e != cudaSuccess) return e;
+  dp2_forward_kernel<NJ, R, Src><<<nreq, kDp2Threads, smem, st>>>(s);
+  return cudaGetLastError();
+}
+
 template <int NJ, class Src>
 static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
-  const size_t smem = dp_smem_bytes(NJ, max_Kp);
-  const int R = (max_Kp + kDpThreads - 1) / kDpThreads;
-  if (R <= 1) return launch_fwd_r<NJ, 1>(s, nreq, smem, st);
-  if (R <= 2) return launch_fwd_r<NJ, 2>(s, nreq, smem, st);
-  return launch_fwd_r<NJ, 4>(s, nreq, smem, st);
+  const size_t smem = dp2_smem_bytes(NJ, max_Kp);
+  const int R = (max_Kp + kDp2Threads - 1) / kDp2Threads;
+  if (R <= 1) return launch_fwd2_r<NJ, 1>(s, nreq, smem, st);
+  if (R <= 2) return launch_fwd2_r<NJ, 2>(s, nreq, smem, st);
+  return launch_fwd2_r<NJ, 4>(s, nreq, smem, st);
 }
 
 template <class Src>

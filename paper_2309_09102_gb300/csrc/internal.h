@@ -30,10 +30,56 @@ cudaError_t launch_dp_batch(const BatchSrc& s, unsigned stages, int n, int nreq,
 
 // lm.cu
 cudaError_t launch_lm(const SingleSrc& s, const cpp_params_t& P, bool want_err, cudaStream_t st);
-cudaError_t launch_lm_batch(const BatchSrc& s, int nreq, int max_T, const cpp_params_t& P,
+cudaError_t launch_lm_batch(const BatchSrc& s, int n, int nreq, int max_T, const cpp_params_t& P,
                             cudaStream_t st);
 cudaError_t launch_check(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st);
 cudaError_t launch_check_batch(const BatchSrc& s, int nreq, const cpp_params_t& P,
                                cudaStream_t st);
+
+// capi.cu
+void set_last_error(const char* msg);  // message returned by cpp_last_error()
+
+// ------------------------------------------------------------------ workspace layouts
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct DpLayout {  // scratch of the search: layer minima, backpointers, final costs
+  size_t pen_min, bp, costT, total;
+};
+inline DpLayout dp_layout(int T, int Kp) {
+  DpLayout L;
+  size_t o = 0;
+  L.pen_min = o; o += align256((size_t)T * sizeof(float));
+  L.bp = o;      o += align256((size_t)T * bp_stride(Kp) * sizeof(uint16_t));
+  L.costT = o;   o += align256((size_t)Kp * sizeof(float));
+  L.total = o;
+  return L;
+}
+
+struct PlanLayout {  // scratch of one whole plan: the search's, masks, node costs, seed
+  DpLayout dp;
+  size_t dp_base, mask, pen, q_seed, total;
+};
+inline PlanLayout plan_layout(int T, int Kp, int n) {
+  PlanLayout L;
+  L.dp = dp_layout(T, Kp);
+  size_t o = 0;
+  L.dp_base = o; o += L.dp.total;
+  L.mask = o;    o += align256((size_t)T * Kp);
+  L.pen = o;     o += align256((size_t)T * Kp * sizeof(float));
+  L.q_seed = o;  o += align256((size_t)T * n * sizeof(float));
+  L.total = o;
+  return L;
+}
+
+// Fill the scratch pointers of a request from a plan workspace at `base`.
+inline void carve_plan(Req& q, char* base, const PlanLayout& L) {
+  q.mask = reinterpret_cast<uint8_t*>(base + L.mask);
+  q.pen = reinterpret_cast<float*>(base + L.pen);
+  q.pen_min = reinterpret_cast<float*>(base + L.dp_base + L.dp.pen_min);
+  q.bp = reinterpret_cast<uint16_t*>(base + L.dp_base + L.dp.bp);
+  q.costT = reinterpret_cast<float*>(base + L.dp_base + L.dp.costT);
+  q.q_seed = reinterpret_cast<float*>(base + L.q_seed);
+  q.q_in = q.q_seed;
+}
 
 }  // namespace cppflow

@@ -2,24 +2,27 @@
 // §III-C) and the FP64 trajectory check (§II constraints and metrics).
 //
 // The pose residual of waypoint i depends on q_i only, so its Jacobian is block
-// diagonal and every waypoint is an independent damped n x n problem. One warp
-// owns one waypoint:
-//   * every lane runs the same DH chain (FP32, or FP64 in the all-FP64 mode);
-//     lane j keeps the frame (z_j, o_j) it needs for Jacobian column j,
-//   * lane j forms column j = [z_j x (p_e - o_j); z_j] of the geometric Jacobian,
-//   * the n(n+1)/2 entries of J^T J and the n entries of J^T e are spread over
-//     the lanes (columns fetched with per-lane shuffles) and accumulated in FP64,
-//   * the Cholesky factorisation and both triangular solves run in FP64 in a
-//     per-warp shared-memory tile, lanes parallel over rows,
+// diagonal and every waypoint is an independent damped n x n problem. One
+// thread owns one waypoint (32 waypoints per warp):
+//   * the DH chain runs in FP32 (or FP64 in the all-FP64 mode) and records the
+//     frames (z_j, o_j); column j of the geometric Jacobian is
+//     [z_j x (p_e - o_j); z_j],
+//   * J^T J + lambda I and J^T e are accumulated in FP64 registers one Jacobian
+//     row at a time (products of FP32 values are exact in FP64),
+//   * the Cholesky factorisation and both triangular solves run in FP64 registers,
 //   * the trial q' = clamp(q + delta, lo, hi) is accepted iff F(q') < F(q)
-//     (F = |e|^2 / 2 accumulated in FP64), with lambda / 10 or * 10.
+//     (F = |e|^2 / 2 summed in FP64), with lambda / 10 or * 10.
+// Why a thread and not a warp per waypoint: GB300 issues FP64 at about two lanes
+// per clock per SM, so an FP64 warp instruction costs the same ~16 cycles
+// whether one lane or 32 do useful work. Spreading one waypoint's n x n algebra
+// over a warp leaves most lanes of every FP64 instruction idle; a thread per
+// waypoint fills all 32.
 // The joint state is held in FP64; q_out is its FP32 rounding.
 #include "internal.h"
 
 namespace cppflow {
 
-constexpr int kLmWarps = 4;
-constexpr int kLmThreads = 32 * kLmWarps;
+constexpr int kLmThreads = 128;
 constexpr int kChkThreads = 256;
 
 struct LmArgs {
@@ -33,7 +36,6 @@ struct CheckArgs {
   double tau_pos, tau_rot, jump_max;
 };
 
-// ------------------------------------------------------------------ chain evaluation
 __device__ __forceinline__ float to_angle(double q, const RobotF& rb, int j) {
   return (float)q + rb.th0[j];
 }
@@ -41,25 +43,37 @@ __device__ __forceinline__ double to_angle(double q, const RobotD& rb, int j) {
   return q + rb.th0[j];
 }
 
-// FK of q on every lane; lane j records (z_j, o_j); returns e = [p_t - p; log(R_t R^T)]
-// and F = |e|^2 / 2 (FP64 sum).
-template <class F, class RB>
-__device__ __forceinline__ double chain_eval(const RB& rb, const double* q, int lane,
-                                             const F Rt[9], const F pt[3], F z[3], F o[3],
-                                             F e[6]) {
+template <class F>
+struct RobotFor;
+template <>
+struct RobotFor<float> {
+  __device__ static const RobotF& get(const RobotF& f, const RobotD&) { return f; }
+};
+template <>
+struct RobotFor<double> {
+  __device__ static const RobotD& get(const RobotF&, const RobotD& d) { return d; }
+};
+
+// FK of q; e = [p_t - p; log(R_t R^T)]; returns F = |e|^2 / 2 summed in FP64.
+// With FRAMES the frames (z_j, o_j) before each joint and the end position are kept.
+template <int NJ, bool FRAMES, class F, class RB>
+__device__ __forceinline__ double lm_eval(const RB& rb, int n, const double* q, const F Rt[9],
+                                          const F pt[3], F e[6], F (*z)[3], F (*o)[3], F* pe) {
+  constexpr int MJ = NJ ? NJ : kMaxJ;
   F R[9], p[3];
   pose_identity(R, p);
 #pragma unroll
-  for (int j = 0; j < kMaxJ; ++j) {
-    if (j >= rb.n) break;
-    if (lane == j) {
-      z[0] = R[2]; z[1] = R[5]; z[2] = R[8];
-      o[0] = p[0]; o[1] = p[1]; o[2] = p[2];
+  for (int j = 0; j < MJ; ++j) {
+    if (!NJ && j >= n) break;
+    if (FRAMES) {
+      z[j][0] = R[2]; z[j][1] = R[5]; z[j][2] = R[8];
+      o[j][0] = p[0]; o[j][1] = p[1]; o[j][2] = p[2];
     }
     F s, c;
     sincos_t(to_angle(q[j], rb, j), &s, &c);
     dh_step(R, p, c, s, (F)rb.ca[j], (F)rb.sa[j], (F)rb.a[j], (F)rb.d[j]);
   }
+  if (FRAMES) { pe[0] = p[0]; pe[1] = p[1]; pe[2] = p[2]; }
   e[0] = pt[0] - p[0]; e[1] = pt[1] - p[1]; e[2] = pt[2] - p[2];
   F M[9];  // M = R_t R^T
 #pragma unroll
@@ -74,34 +88,20 @@ __device__ __forceinline__ double chain_eval(const RB& rb, const double* q, int 
   return 0.5 * s;
 }
 
-template <class F>
-struct RobotFor;
-template <>
-struct RobotFor<float> {
-  __device__ static const RobotF& get(const RobotF& f, const RobotD&) { return f; }
-};
-template <>
-struct RobotFor<double> {
-  __device__ static const RobotD& get(const RobotF&, const RobotD& d) { return d; }
-};
-
-template <class F, class Src>
+template <int NJ, class F, class Src>
 __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ Src src,
                                                          const LmArgs a) {
+  constexpr int MJ = NJ ? NJ : kMaxJ;
+  constexpr int MT = MJ * (MJ + 1) / 2;  // packed lower triangle
   const Req& rq = src.req(blockIdx.y);
   __shared__ RobotF rf;
   __shared__ RobotD rd;
-  __shared__ double sA[kLmWarps][kMaxJ * kMaxJ];
-  __shared__ double sg[kLmWarps][kMaxJ];
   stage_robot(src.rob(rq.robot), 0.0, &rf, &rd);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kLmWarps + warp;
+  const int i = blockIdx.x * kLmThreads + threadIdx.x;
   if (i >= rq.T) return;
   const auto& rb = RobotFor<F>::get(rf, rd);
-  const int n = rd.n;
-  double* A = sA[warp];
-  double* g = sg[warp];
+  const int n = NJ ? NJ : rd.n;
 
   F Rt[9], pt[3];
   {
@@ -112,135 +112,124 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
     for (int k = 0; k < 9; ++k) Rt[k] = (F)R[k];
     pt[0] = (F)t7[0]; pt[1] = (F)t7[1]; pt[2] = (F)t7[2];
   }
-  double q[kMaxJ];
+  double q[MJ];
 #pragma unroll
-  for (int j = 0; j < kMaxJ; ++j) q[j] = j < n ? (double)rq.q_in[(size_t)i * n + j] : 0.0;
+  for (int j = 0; j < MJ; ++j) q[j] = (NJ || j < n) ? (double)rq.q_in[(size_t)i * n + j] : 0.0;
 
-  F z[3] = {F(0), F(0), F(0)}, o[3] = {F(0), F(0), F(0)}, e[6];
-  double Fc = chain_eval<F>(rb, q, lane, Rt, pt, z, o, e);
+  F e[6];
+  double Fc = lm_eval<NJ, false, F>(rb, n, q, Rt, pt, e, nullptr, nullptr, nullptr);
   double lam = a.lambda0;
-  const int NT = n * (n + 1) / 2;
 
   for (int it = 0; it < a.iters; ++it) {
     if (Fc < a.freeze_cost) break;
-    // Jacobian column of this lane
-    F Jc[6];
-    {
-      F pe[3];
-      // p_e = p_t - e_pos
-      pe[0] = pt[0] - e[0]; pe[1] = pt[1] - e[1]; pe[2] = pt[2] - e[2];
-      const bool on = lane < n && ((a.free_mask >> lane) & 1u);
-      const F dx = pe[0] - o[0], dy = pe[1] - o[1], dz = pe[2] - o[2];
-      Jc[0] = on ? z[1] * dz - z[2] * dy : F(0);
-      Jc[1] = on ? z[2] * dx - z[0] * dz : F(0);
-      Jc[2] = on ? z[0] * dy - z[1] * dx : F(0);
-      Jc[3] = on ? z[0] : F(0);
-      Jc[4] = on ? z[1] : F(0);
-      Jc[5] = on ? z[2] : F(0);
-    }
-    // normal equations: entries (a >= b) of J^T J + lam I, then J^T e
-    for (int t0 = 0; t0 < NT + n; t0 += 32) {
-      const int t = t0 + lane;
-      int ra = 0, cb = 0;
-      if (t < NT) {
-        while ((ra + 1) * (ra + 2) / 2 <= t) ++ra;
-        cb = t - ra * (ra + 1) / 2;
-      } else if (t < NT + n) {
-        ra = t - NT;
-        cb = ra;
-      }
-      F ja[6], jb[6];
+    F z[MJ][3], o[MJ][3], pe[3];
+    lm_eval<NJ, true, F>(rb, n, q, Rt, pt, e, z, o, pe);
+    // J^T J + lam I (packed lower triangle) and J^T e, one Jacobian row at a time
+    double A[MT], g[MJ];
 #pragma unroll
-      for (int r = 0; r < 6; ++r) {
-        ja[r] = __shfl_sync(0xffffffffu, Jc[r], ra);
-        jb[r] = __shfl_sync(0xffffffffu, Jc[r], cb);
-      }
-      double s = 0.0;
-      if (t < NT) {
+    for (int t = 0; t < MT; ++t) A[t] = 0.0;
 #pragma unroll
-        for (int r = 0; r < 6; ++r) s += (double)ja[r] * (double)jb[r];
-        if (ra == cb) s += lam;
-        A[ra * kMaxJ + cb] = s;
-      } else if (t < NT + n) {
+    for (int j = 0; j < MJ; ++j) g[j] = 0.0;
 #pragma unroll
-        for (int r = 0; r < 6; ++r) s += (double)ja[r] * (double)e[r];
-        g[ra] = s;
-      }
-    }
-    __syncwarp();
-    // Cholesky A = L L^T (lower triangle, in place), lanes own rows
-    bool ok = true;
-    for (int k = 0; k < n; ++k) {
-      const double piv = A[k * kMaxJ + k];
-      if (!(piv > 0.0) || !isfinite(piv)) { ok = false; break; }
-      const double lkk = sqrt(piv);
-      __syncwarp();
-      if (lane == k) A[k * kMaxJ + k] = lkk;
-      if (lane > k && lane < n) A[lane * kMaxJ + k] = A[lane * kMaxJ + k] / lkk;
-      __syncwarp();
-      if (lane > k && lane < n) {
-        const double lak = A[lane * kMaxJ + k];
-        for (int b = k + 1; b <= lane; ++b) A[lane * kMaxJ + b] -= lak * A[b * kMaxJ + k];
-      }
-      __syncwarp();
-    }
-    if (ok) {
-      // L y = g
-      for (int m = 0; m < n; ++m) {
-        const double ym = g[m] / A[m * kMaxJ + m];
-        __syncwarp();
-        if (lane == m) g[m] = ym;
-        if (lane > m && lane < n) g[lane] -= A[lane * kMaxJ + m] * ym;
-        __syncwarp();
-      }
-      // L^T x = y
-      for (int m = n - 1; m >= 0; --m) {
-        const double xm = g[m] / A[m * kMaxJ + m];
-        __syncwarp();
-        if (lane == m) g[m] = xm;
-        if (lane < m) g[lane] -= A[m * kMaxJ + lane] * xm;
-        __syncwarp();
-      }
-      double dq[kMaxJ];
-      double mx = 0.0;
+    for (int r = 0; r < 6; ++r) {
+      double Jr[MJ];
 #pragma unroll
-      for (int j = 0; j < kMaxJ; ++j) {
-        dq[j] = j < n ? g[j] : 0.0;
-        mx = fmax(mx, fabs(dq[j]));
-      }
-      __syncwarp();
-      if (mx < a.freeze_step) break;
-      double qt[kMaxJ];
-#pragma unroll
-      for (int j = 0; j < kMaxJ; ++j) {
-        double v = q[j] + dq[j];
-        if (j < n) {
-          if (v < rd.lo[j]) v = rd.lo[j];
-          if (v > rd.hi[j]) v = rd.hi[j];
+      for (int j = 0; j < MJ; ++j) {
+        F v = F(0);
+        if ((NJ || j < n) && ((a.free_mask >> j) & 1u)) {
+          const F dx = pe[0] - o[j][0], dy = pe[1] - o[j][1], dz = pe[2] - o[j][2];
+          v = r == 0 ? z[j][1] * dz - z[j][2] * dy
+            : r == 1 ? z[j][2] * dx - z[j][0] * dz
+            : r == 2 ? z[j][0] * dy - z[j][1] * dx
+            : z[j][r - 3];
         }
-        qt[j] = v;
+        Jr[j] = (double)v;
       }
-      F zt[3] = {z[0], z[1], z[2]}, ot[3] = {o[0], o[1], o[2]}, et[6];
-      const double Ft = chain_eval<F>(rb, qt, lane, Rt, pt, zt, ot, et);
-      if (Ft < Fc) {
+      const double er = (double)e[r];
 #pragma unroll
-        for (int j = 0; j < kMaxJ; ++j) q[j] = qt[j];
+      for (int x = 0; x < MJ; ++x) {
+        g[x] += Jr[x] * er;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) { z[k] = zt[k]; o[k] = ot[k]; }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) e[k] = et[k];
-        Fc = Ft;
-        lam = fmax(lam / a.lambda_down, a.lambda_min);
-      } else {
-        lam = fmin(lam * a.lambda_up, a.lambda_max);
+        for (int y = 0; y <= x; ++y) A[x * (x + 1) / 2 + y] += Jr[x] * Jr[y];
       }
+    }
+    // Cholesky, left-looking, in place: L_jj = sqrt(A_jj - sum L_jm^2),
+    // L_xj = (A_xj - sum L_xm L_jm) / L_jj
+    bool ok = true;
+    double inv[MJ];
+#pragma unroll
+    for (int j = 0; j < MJ; ++j) {
+      if (!NJ && j >= n) { inv[j] = 0.0; continue; }
+      double d = A[j * (j + 1) / 2 + j] + lam;
+#pragma unroll
+      for (int m = 0; m < j; ++m) d -= A[j * (j + 1) / 2 + m] * A[j * (j + 1) / 2 + m];
+      ok = ok && (d > 0.0) && isfinite(d);
+      const double ljj = sqrt(d);
+      A[j * (j + 1) / 2 + j] = ljj;
+      inv[j] = 1.0 / ljj;
+#pragma unroll
+      for (int x = j + 1; x < MJ; ++x) {
+        if (!NJ && x >= n) break;
+        double t = A[x * (x + 1) / 2 + j];
+#pragma unroll
+        for (int m = 0; m < j; ++m) t -= A[x * (x + 1) / 2 + m] * A[j * (j + 1) / 2 + m];
+        A[x * (x + 1) / 2 + j] = t * inv[j];
+      }
+    }
+    if (!ok) {
+      lam = fmin(lam * a.lambda_up, a.lambda_max);
+      continue;
+    }
+    // L y = g, then L^T x = y (x overwrites g)
+#pragma unroll
+    for (int x = 0; x < MJ; ++x) {
+      if (!NJ && x >= n) break;
+      double t = g[x];
+#pragma unroll
+      for (int m = 0; m < x; ++m) t -= A[x * (x + 1) / 2 + m] * g[m];
+      g[x] = t * inv[x];
+    }
+#pragma unroll
+    for (int x = MJ - 1; x >= 0; --x) {
+      if (!NJ && x >= n) continue;
+      double t = g[x];
+#pragma unroll
+      for (int m = x + 1; m < MJ; ++m) {
+        if (!NJ && m >= n) break;
+        t -= A[m * (m + 1) / 2 + x] * g[m];
+      }
+      g[x] = t * inv[x];
+    }
+    double mx = 0.0;
+#pragma unroll
+    for (int j = 0; j < MJ; ++j)
+      if (NJ || j < n) mx = fmax(mx, fabs(g[j]));
+    if (mx < a.freeze_step) break;
+    double qt[MJ];
+#pragma unroll
+    for (int j = 0; j < MJ; ++j) {
+      double v = q[j] + g[j];
+      if (NJ || j < n) {
+        if (v < rd.lo[j]) v = rd.lo[j];
+        if (v > rd.hi[j]) v = rd.hi[j];
+      }
+      qt[j] = v;
+    }
+    F et[6];
+    const double Ft = lm_eval<NJ, false, F>(rb, n, qt, Rt, pt, et, nullptr, nullptr, nullptr);
+    if (Ft < Fc) {
+#pragma unroll
+      for (int j = 0; j < MJ; ++j) q[j] = qt[j];
+      Fc = Ft;
+      lam = fmax(lam / a.lambda_down, a.lambda_min);
     } else {
-      __syncwarp();
       lam = fmin(lam * a.lambda_up, a.lambda_max);
     }
   }
-  if (lane < n) rq.q_out[(size_t)i * n + lane] = (float)q[lane];
-  if (a.want_err && rq.pose_err && lane == 0) {
+#pragma unroll
+  for (int j = 0; j < MJ; ++j)
+    if (NJ || j < n) rq.q_out[(size_t)i * n + j] = (float)q[j];
+  if (a.want_err && rq.pose_err) {
     // FP64 pose error of the delivered (FP32-rounded) configuration
     double qq[kMaxJ], R[9], p[3], RtD[9];
     for (int j = 0; j < n; ++j) qq[j] = (double)(float)q[j];
@@ -347,22 +336,32 @@ static LmArgs make_lm_args(const cpp_params_t& P, bool want_err) {
   return a;
 }
 
+template <int NJ, class Src>
+static void launch_lm_nj(const Src& s, dim3 grid, const LmArgs& a, bool fp64, cudaStream_t st) {
+  if (fp64) lm_kernel<NJ, double, Src><<<grid, kLmThreads, 0, st>>>(s, a);
+  else lm_kernel<NJ, float, Src><<<grid, kLmThreads, 0, st>>>(s, a);
+}
+
 template <class Src>
-static cudaError_t launch_lm_t(const Src& s, int nreq, int max_T, const cpp_params_t& P,
+static cudaError_t launch_lm_t(const Src& s, int n, int nreq, int max_T, const cpp_params_t& P,
                                bool want_err, cudaStream_t st) {
   const LmArgs a = make_lm_args(P, want_err);
-  dim3 grid((unsigned)((max_T + kLmWarps - 1) / kLmWarps), (unsigned)nreq);
-  if (P.lm_fp64) lm_kernel<double, Src><<<grid, kLmThreads, 0, st>>>(s, a);
-  else lm_kernel<float, Src><<<grid, kLmThreads, 0, st>>>(s, a);
+  dim3 grid((unsigned)((max_T + kLmThreads - 1) / kLmThreads), (unsigned)nreq);
+  switch (n) {
+    case 6: launch_lm_nj<6>(s, grid, a, P.lm_fp64 != 0, st); break;
+    case 7: launch_lm_nj<7>(s, grid, a, P.lm_fp64 != 0, st); break;
+    case 9: launch_lm_nj<9>(s, grid, a, P.lm_fp64 != 0, st); break;
+    default: launch_lm_nj<0>(s, grid, a, P.lm_fp64 != 0, st); break;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_lm(const SingleSrc& s, const cpp_params_t& P, bool want_err, cudaStream_t st) {
-  return launch_lm_t(s, 1, s.r.T, P, want_err, st);
+  return launch_lm_t(s, s.r.n, 1, s.r.T, P, want_err, st);
 }
-cudaError_t launch_lm_batch(const BatchSrc& s, int nreq, int max_T, const cpp_params_t& P,
+cudaError_t launch_lm_batch(const BatchSrc& s, int n, int nreq, int max_T, const cpp_params_t& P,
                             cudaStream_t st) {
-  return launch_lm_t(s, nreq, max_T, P, false, st);
+  return launch_lm_t(s, n, nreq, max_T, P, false, st);
 }
 
 template <class Src>

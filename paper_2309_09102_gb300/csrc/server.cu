@@ -1,0 +1,621 @@
+// server.cu -- continuous-batching request loop (cpp_server_*, cpp_plan_submit /
+// poll / wait / cancel). Not in the paper: it serves the planner core to many
+// clients at once.
+//
+// Structure
+//  * a device arena of hbm_budget_bytes, sub-allocated first-fit per request:
+//    a request is admitted only when its whole footprint (lattice, targets,
+//    plan scratch, outputs) fits, so lattices and search tables stay resident
+//    on the device for the request's lifetime on the GPU;
+//  * a pinned host pool for staged inputs and results (pageable fallback);
+//  * one worker thread: it retires finished launches (event query), then forms
+//    the next batch from the queue -- requests of the same joint count in
+//    arrival order, while slots, batch size and arena space allow -- and
+//    enqueues H2D copies, the six stage launches and the D2H copy of results
+//    on one of max_inflight streams. Requests that arrive while earlier
+//    batches run are admitted into the next batch as memory frees up, and
+//    the batches overlap on the device.
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+using namespace cppflow;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+cpp_status sfail(cpp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  set_last_error(buf);
+  return s;
+}
+
+// First-fit allocator over [0, size) in 256-byte units.
+class Arena {
+ public:
+  void reset(size_t size) {
+    free_.clear();
+    if (size) free_[0] = size;
+    used_ = high_ = 0;
+    size_ = size;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = align256(bytes);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const size_t start = it->first + bytes, rest = it->second - bytes;
+      free_.erase(it);
+      if (rest) free_[start] = rest;
+      used_ += bytes;
+      high_ = std::max(high_, used_);
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = align256(bytes);
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+    used_ -= bytes;
+  }
+  size_t used() const { return used_; }
+  size_t high_water() const { return high_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t used_ = 0, high_ = 0, size_ = 0;
+};
+
+enum class St { Queued, Running, Done, Failed, Cancelled };
+
+struct Request {
+  uint64_t ticket = 0;
+  cpp_robot_t robot;
+  int T = 0, K = 0, Kp = 0, n = 0;
+  // inputs on the host (borrowed, pinned copy or pageable copy)
+  const float* cand = nullptr;
+  const double* targets = nullptr;
+  std::vector<char> own_in;
+  // results on the host (pinned or pageable)
+  char* h_out = nullptr;
+  std::vector<char> own_out;
+  size_t pin_off = 0, pin_bytes = 0;
+  bool pinned = false;
+  // device slot: [cand][targets][outputs][plan scratch]
+  size_t dev_off = 0, dev_bytes = 0;
+  size_t o_cand = 0, o_tgt = 0, o_out = 0, o_ws = 0;
+  size_t out_bytes = 0, o_sel = 0, o_q = 0, o_err = 0, o_rep = 0, o_best = 0;
+  St state = St::Queued;
+  cpp_status result = CPP_OK;
+  int32_t dev_status = 0;
+  Clock::time_point t_submit, t_done;
+};
+
+struct Layout {
+  size_t cand, tgt, out, ws, total;
+  size_t sel, q, err, rep, best, out_bytes;
+};
+
+Layout slot_layout(int T, int Kp, int n) {
+  Layout L;
+  size_t o = 0;
+  L.cand = o; o += align256((size_t)T * n * Kp * sizeof(float));
+  L.tgt = o;  o += align256((size_t)T * 7 * sizeof(double));
+  L.out = o;
+  size_t u = 0;
+  L.err = u;  u += (size_t)T * 2 * sizeof(double);
+  L.rep = u;  u += sizeof(cpp_report_t);
+  L.q = u;    u += (size_t)T * n * sizeof(float);
+  L.sel = u;  u += (size_t)T * sizeof(int32_t);
+  L.best = u; u += sizeof(float);
+  L.out_bytes = u;
+  o += align256(u);
+  L.ws = o;   o += plan_layout(T, Kp, n).total;
+  L.total = o;
+  return L;
+}
+
+struct Launch {
+  std::vector<Request*> reqs;
+  int stream = 0;
+  cudaEvent_t done = nullptr;
+  size_t tab_off = 0, tab_bytes = 0;      // device: Req[] | robots[] | status[]
+  size_t tab_pin = 0, tab_pin_bytes = 0;  // pinned host mirror
+  bool tab_pinned = false;
+  std::vector<char> tab_host;             // pageable fallback
+  char* tab_h = nullptr;
+};
+
+}  // namespace
+
+struct cpp_server {
+  cpp_server_config_t cfg;
+  char* d_arena = nullptr;
+  Arena darena;
+  char* h_pinned = nullptr;
+  Arena parena;
+  std::vector<cudaStream_t> streams;
+  std::vector<bool> stream_busy;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::unordered_map<uint64_t, Request*> reqs;
+  std::vector<Launch*> inflight;
+  int resident = 0;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread worker;
+  cpp_server_stats_t stats;
+  std::string fatal;
+
+  void run();
+  bool form_batch(Launch* L);
+  cpp_status enqueue(Launch* L);
+  void retire(Launch* L, cudaError_t e);
+  void release_host(Request* r);
+};
+
+void cpp_server::release_host(Request* r) {
+  if (r->pinned) {
+    parena.release(r->pin_off, r->pin_bytes);
+    r->pinned = false;
+  }
+  r->own_in.clear();
+  r->own_in.shrink_to_fit();
+}
+
+// Take same-n requests in arrival order while batch size, slots and arena allow.
+bool cpp_server::form_batch(Launch* L) {
+  if (queue.empty()) return false;
+  const int n0 = queue.front()->n;
+  for (auto it = queue.begin(); it != queue.end();) {
+    Request* r = *it;
+    if ((int)L->reqs.size() >= cfg.max_batch || resident >= cfg.max_slots) break;
+    if (r->n != n0) { ++it; continue; }
+    size_t off;
+    if (!darena.alloc(r->dev_bytes, &off)) break;  // keep arrival order within the class
+    r->dev_off = off;
+    r->state = St::Running;
+    ++resident;
+    L->reqs.push_back(r);
+    it = queue.erase(it);
+  }
+  if (L->reqs.empty()) return false;
+  const int count = (int)L->reqs.size();
+  L->tab_bytes = align256(sizeof(Req) * count) + align256(sizeof(cpp_robot_t) * count) +
+                 align256(sizeof(int32_t) * count);
+  if (!darena.alloc(L->tab_bytes, &L->tab_off)) {
+    // no room for the table: give the requests back
+    for (Request* r : L->reqs) {
+      darena.release(r->dev_off, r->dev_bytes);
+      r->state = St::Queued;
+      --resident;
+    }
+    for (auto it = L->reqs.rbegin(); it != L->reqs.rend(); ++it) queue.push_front(*it);
+    L->reqs.clear();
+    return false;
+  }
+  L->tab_pin_bytes = L->tab_bytes;
+  if (parena.alloc(L->tab_pin_bytes, &L->tab_pin)) {
+    L->tab_pinned = true;
+    L->tab_h = h_pinned + L->tab_pin;
+  } else {
+    L->tab_host.resize(L->tab_bytes);
+    L->tab_h = L->tab_host.data();
+  }
+  return true;
+}
+
+cpp_status cpp_server::enqueue(Launch* L) {
+  const cudaStream_t st = streams[L->stream];
+  const int count = (int)L->reqs.size();
+  const int n = L->reqs[0]->n;
+  char* tab_d = d_arena + L->tab_off;
+  Req* tq = reinterpret_cast<Req*>(L->tab_h);
+  cpp_robot_t* trob = reinterpret_cast<cpp_robot_t*>(L->tab_h + align256(sizeof(Req) * count));
+  int32_t* tst = reinterpret_cast<int32_t*>(L->tab_h + align256(sizeof(Req) * count) +
+                                            align256(sizeof(cpp_robot_t) * count));
+  int32_t* tst_d = reinterpret_cast<int32_t*>(tab_d + align256(sizeof(Req) * count) +
+                                              align256(sizeof(cpp_robot_t) * count));
+  int max_T = 0, max_Kp = 0;
+  long long max_tasks = 0;
+  for (int i = 0; i < count; ++i) {
+    Request* r = L->reqs[i];
+    char* b = d_arena + r->dev_off;
+    cudaError_t e = cudaMemcpyAsync(b + r->o_cand, r->cand, (size_t)r->T * r->n * r->Kp * sizeof(float),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b + r->o_tgt, r->targets, (size_t)r->T * 7 * sizeof(double),
+                          cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server H2D: %s", cudaGetErrorString(e));
+    Req q;
+    memset(&q, 0, sizeof(q));
+    q.T = r->T; q.K = r->K; q.Kp = r->Kp; q.n = r->n; q.robot = i; q.Kb = bp_stride(r->Kp);
+    q.cand = reinterpret_cast<const float*>(b + r->o_cand);
+    q.targets = reinterpret_cast<const double*>(b + r->o_tgt);
+    carve_plan(q, b + r->o_ws, plan_layout(r->T, r->Kp, r->n));
+    char* out = b + r->o_out;
+    q.sel = reinterpret_cast<int32_t*>(out + r->o_sel);
+    q.q_out = reinterpret_cast<float*>(out + r->o_q);
+    q.pose_err = reinterpret_cast<double*>(out + r->o_err);
+    q.report = reinterpret_cast<cpp_report_t*>(out + r->o_rep);
+    q.best_cost = reinterpret_cast<float*>(out + r->o_best);
+    q.status = tst_d + i;
+    tq[i] = q;
+    trob[i] = r->robot;
+    tst[i] = 0;
+    max_T = std::max(max_T, r->T);
+    max_Kp = std::max(max_Kp, r->Kp);
+    max_tasks = std::max(max_tasks, mask_tasks(r->T, r->Kp));
+  }
+  cudaError_t e = cudaMemcpyAsync(tab_d, L->tab_h, L->tab_bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server H2D table: %s", cudaGetErrorString(e));
+  BatchSrc src{reinterpret_cast<const Req*>(tab_d),
+               reinterpret_cast<const cpp_robot_t*>(tab_d + align256(sizeof(Req) * count))};
+  if ((e = launch_mask_batch(src, n, count, max_tasks, cfg.params, st)) != cudaSuccess ||
+      (e = launch_dp_batch(src, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK, n,
+                           count, max_T, max_Kp, st)) != cudaSuccess ||
+      (e = launch_lm_batch(src, n, count, max_T, cfg.params, st)) != cudaSuccess ||
+      (e = launch_check_batch(src, count, cfg.params, st)) != cudaSuccess)
+    return sfail(CPP_ERR_CUDA, "server launch: %s", cudaGetErrorString(e));
+  for (int i = 0; i < count; ++i) {
+    Request* r = L->reqs[i];
+    e = cudaMemcpyAsync(r->h_out, d_arena + r->dev_off + r->o_out, r->out_bytes,
+                        cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server D2H: %s", cudaGetErrorString(e));
+  }
+  e = cudaMemcpyAsync(tst, tst_d, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventRecord(L->done, st);
+  if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server D2H: %s", cudaGetErrorString(e));
+  return CPP_OK;
+}
+
+void cpp_server::retire(Launch* L, cudaError_t e) {
+  const int count = (int)L->reqs.size();
+  const int32_t* tst = reinterpret_cast<const int32_t*>(
+      L->tab_h + align256(sizeof(Req) * count) + align256(sizeof(cpp_robot_t) * count));
+  const auto now = Clock::now();
+  for (int i = 0; i < count; ++i) {
+    Request* r = L->reqs[i];
+    darena.release(r->dev_off, r->dev_bytes);
+    --resident;
+    r->t_done = now;
+    if (e != cudaSuccess) {
+      r->state = St::Failed;
+      r->result = CPP_ERR_CUDA;
+      ++stats.failed;
+    } else {
+      r->dev_status = tst[i];
+      r->state = St::Done;
+      r->result = tst[i] == 0 ? CPP_OK : (cpp_status)tst[i];
+      ++stats.completed;
+    }
+    if (r->state == St::Failed) release_host(r);
+  }
+  darena.release(L->tab_off, L->tab_bytes);
+  if (L->tab_pinned) parena.release(L->tab_pin, L->tab_pin_bytes);
+  stream_busy[L->stream] = false;
+}
+
+void cpp_server::run() {
+  cudaSetDevice(cfg.device);
+  std::unique_lock<std::mutex> lk(mu);
+  for (;;) {
+    // retire finished launches
+    for (size_t k = 0; k < inflight.size();) {
+      Launch* L = inflight[k];
+      const cudaError_t q = cudaEventQuery(L->done);
+      if (q == cudaErrorNotReady) { ++k; continue; }
+      retire(L, q);
+      cudaEventDestroy(L->done);
+      delete L;
+      inflight.erase(inflight.begin() + k);
+      cv_done.notify_all();
+    }
+    if (stop && inflight.empty()) break;
+    // launch the next batch
+    bool launched = false;
+    if (!stop && (int)inflight.size() < cfg.max_inflight && !queue.empty()) {
+      int sidx = -1;
+      for (int k = 0; k < (int)streams.size(); ++k)
+        if (!stream_busy[k]) { sidx = k; break; }
+      Launch* L = new Launch;
+      if (sidx >= 0 && form_batch(L)) {
+        L->stream = sidx;
+        stream_busy[sidx] = true;
+        cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
+        ++stats.batches;
+        stats.max_batch_seen = std::max<int32_t>(stats.max_batch_seen, (int32_t)L->reqs.size());
+        stats.sum_batch += L->reqs.size();
+        lk.unlock();
+        const cpp_status s = enqueue(L);
+        lk.lock();
+        if (s != CPP_OK) {
+          fatal = cpp_last_error();
+          retire(L, cudaErrorUnknown);
+          cudaEventDestroy(L->done);
+          delete L;
+          cv_done.notify_all();
+        } else {
+          inflight.push_back(L);
+          launched = true;
+        }
+      } else {
+        delete L;
+      }
+    }
+    if (launched) continue;
+    if (inflight.empty()) {
+      cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+    } else {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+    }
+  }
+  // cancel what never ran
+  for (Request* r : queue) {
+    r->state = St::Cancelled;
+    r->result = CPP_ERR_CANCELLED;
+    release_host(r);
+  }
+  queue.clear();
+  cv_done.notify_all();
+}
+
+extern "C" {
+
+void cpp_server_config_default(cpp_server_config_t* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->device = 0;
+  c->max_slots = 1024;
+  c->max_batch = 512;
+  c->max_inflight = 2;
+  c->hbm_budget_bytes = (size_t)40 << 30;
+  c->pinned_bytes = (size_t)1 << 30;
+  cpp_params_default(&c->params);
+}
+
+cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out) {
+  if (!out) return sfail(CPP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return sfail(CPP_ERR_INVALID_ARG, "config is NULL");
+  if (cfg->max_slots < 1 || cfg->max_batch < 1 || cfg->max_inflight < 1 || cfg->max_inflight > 16)
+    return sfail(CPP_ERR_INVALID_ARG, "max_slots, max_batch >= 1 and max_inflight in [1, 16]");
+  if (cfg->hbm_budget_bytes < 4096) return sfail(CPP_ERR_INVALID_ARG, "hbm_budget_bytes too small");
+  cpp_server* s = new (std::nothrow) cpp_server;
+  if (!s) return sfail(CPP_ERR_OOM, "host allocation failed");
+  s->cfg = *cfg;
+  memset(&s->stats, 0, sizeof(s->stats));
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_arena, cfg->hbm_budget_bytes);
+  if (e != cudaSuccess) {
+    delete s;
+    return sfail(e == cudaErrorMemoryAllocation ? CPP_ERR_OOM : CPP_ERR_CUDA,
+                 "server device arena: %s", cudaGetErrorString(e));
+  }
+  s->darena.reset(cfg->hbm_budget_bytes);
+  if (cfg->pinned_bytes) {
+    if (cudaHostAlloc(&s->h_pinned, cfg->pinned_bytes, cudaHostAllocDefault) == cudaSuccess)
+      s->parena.reset(cfg->pinned_bytes);
+    else
+      s->h_pinned = nullptr;
+  }
+  s->streams.resize(cfg->max_inflight);
+  s->stream_busy.assign(cfg->max_inflight, false);
+  for (auto& st : s->streams) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  s->worker = std::thread([s] { s->run(); });
+  *out = s;
+  return CPP_OK;
+}
+
+cpp_status cpp_plan_submit(cpp_server_t* s, const cpp_plan_req_t* rq, uint64_t* ticket) {
+  if (!s || !rq || !ticket) return sfail(CPP_ERR_INVALID_ARG, "NULL argument");
+  if (!rq->robot) return sfail(CPP_ERR_INVALID_ARG, "robot is NULL");
+  const cpp_robot_t& rb = *rq->robot;
+  if (rb.n < 1 || rb.n > CPP_MAX_JOINTS) return sfail(CPP_ERR_INVALID_ARG, "robot.n out of range");
+  for (int j = 0; j < rb.n; ++j)
+    if (!std::isfinite(rb.a[j]) || !std::isfinite(rb.d[j]) || !std::isfinite(rb.alpha[j]) ||
+        !std::isfinite(rb.theta0[j]) || !(rb.lo[j] <= rb.hi[j]))
+      return sfail(CPP_ERR_INVALID_ARG, "robot joint %d malformed", j);
+  const int T = rq->T, K = rq->K, Kp = rq->Kp, n = rb.n;
+  if (T < 1 || K < 1 || K > 65535 || Kp < K || Kp % 4)
+    return sfail(CPP_ERR_INVALID_ARG, "invalid lattice T=%d K=%d Kp=%d", T, K, Kp);
+  if (!dp_supported(n, Kp)) return sfail(CPP_ERR_INVALID_ARG, "Kp too large for shared memory");
+  if (!rq->cand || !rq->targets) return sfail(CPP_ERR_INVALID_ARG, "NULL input");
+  for (int i = 0; i < T; ++i) {
+    const double* t = rq->targets + 7 * (size_t)i;
+    double qn = 0;
+    for (int k = 0; k < 7; ++k)
+      if (!std::isfinite(t[k])) return sfail(CPP_ERR_INVALID_ARG, "target %d is not finite", i);
+    for (int k = 3; k < 7; ++k) qn += t[k] * t[k];
+    if (std::fabs(std::sqrt(qn) - 1.0) > 1e-6)
+      return sfail(CPP_ERR_INVALID_ARG, "target %d: quaternion norm %.9f is not 1", i, std::sqrt(qn));
+  }
+  const Layout L = slot_layout(T, Kp, n);
+  const size_t table = 3 * 256 + align256(sizeof(Req)) + align256(sizeof(cpp_robot_t));
+  if (L.total + table > s->cfg.hbm_budget_bytes)
+    return sfail(CPP_ERR_BUDGET, "request needs %zu bytes of device memory; the budget is %zu",
+                 L.total + table, s->cfg.hbm_budget_bytes);
+  Request* r = new (std::nothrow) Request;
+  if (!r) return sfail(CPP_ERR_OOM, "host allocation failed");
+  r->robot = rb;
+  r->T = T; r->K = K; r->Kp = Kp; r->n = n;
+  r->dev_bytes = L.total;
+  r->o_cand = L.cand; r->o_tgt = L.tgt; r->o_out = L.out; r->o_ws = L.ws;
+  r->out_bytes = L.out_bytes; r->o_sel = L.sel; r->o_q = L.q; r->o_err = L.err;
+  r->o_rep = L.rep; r->o_best = L.best;
+  const size_t cand_b = (size_t)T * n * Kp * sizeof(float), tgt_b = (size_t)T * 7 * sizeof(double);
+  const bool borrow = (rq->flags & CPP_REQ_BORROW) != 0;
+  const size_t in_b = borrow ? 0 : align256(cand_b) + align256(tgt_b);
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (s->h_pinned && s->parena.alloc(in_b + r->out_bytes, &r->pin_off)) {
+    r->pinned = true;
+    r->pin_bytes = in_b + r->out_bytes;
+    char* base = s->h_pinned + r->pin_off;
+    r->h_out = base + in_b;
+    if (!borrow) {
+      lk.unlock();
+      memcpy(base, rq->cand, cand_b);
+      memcpy(base + align256(cand_b), rq->targets, tgt_b);
+      lk.lock();
+      r->cand = reinterpret_cast<const float*>(base);
+      r->targets = reinterpret_cast<const double*>(base + align256(cand_b));
+    }
+  } else {
+    r->own_out.resize(r->out_bytes);
+    r->h_out = r->own_out.data();
+    if (!borrow) {
+      r->own_in.resize(align256(cand_b) + tgt_b);
+      memcpy(r->own_in.data(), rq->cand, cand_b);
+      memcpy(r->own_in.data() + align256(cand_b), rq->targets, tgt_b);
+      r->cand = reinterpret_cast<const float*>(r->own_in.data());
+      r->targets = reinterpret_cast<const double*>(r->own_in.data() + align256(cand_b));
+    }
+  }
+  if (borrow) {
+    r->cand = rq->cand;
+    r->targets = rq->targets;
+  }
+  if (s->stop) {
+    s->release_host(r);
+    delete r;
+    return sfail(CPP_ERR_CANCELLED, "server is shutting down");
+  }
+  r->ticket = s->next_ticket++;
+  r->t_submit = Clock::now();
+  s->reqs[r->ticket] = r;
+  s->queue.push_back(r);
+  ++s->stats.submitted;
+  *ticket = r->ticket;
+  lk.unlock();
+  s->cv_work.notify_one();
+  return CPP_OK;
+}
+
+static cpp_status collect(cpp_server_t* s, Request* r, cpp_plan_result_t* res) {
+  const cpp_status st = r->result;
+  if (res) {
+    res->latency_ms =
+        std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    res->dev_status = r->dev_status;
+    if (r->state == St::Done) {
+      const char* o = r->h_out;
+      if (res->sel) memcpy(res->sel, o + r->o_sel, (size_t)r->T * sizeof(int32_t));
+      if (res->q) memcpy(res->q, o + r->o_q, (size_t)r->T * r->n * sizeof(float));
+      if (res->pose_err) memcpy(res->pose_err, o + r->o_err, (size_t)r->T * 2 * sizeof(double));
+      if (res->report) memcpy(res->report, o + r->o_rep, sizeof(cpp_report_t));
+      if (res->best_cost) memcpy(res->best_cost, o + r->o_best, sizeof(float));
+    }
+  }
+  s->release_host(r);
+  s->reqs.erase(r->ticket);
+  delete r;
+  return st;
+}
+
+cpp_status cpp_plan_poll(cpp_server_t* s, uint64_t ticket, cpp_plan_result_t* res) {
+  if (!s) return sfail(CPP_ERR_INVALID_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return sfail(CPP_ERR_NOT_FOUND, "unknown ticket %llu",
+                                        (unsigned long long)ticket);
+  Request* r = it->second;
+  if (r->state == St::Queued || r->state == St::Running) return CPP_PENDING;
+  return collect(s, r, res);
+}
+
+cpp_status cpp_plan_wait(cpp_server_t* s, uint64_t ticket, cpp_plan_result_t* res,
+                         int64_t timeout_us) {
+  if (!s) return sfail(CPP_ERR_INVALID_ARG, "server is NULL");
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
+  for (;;) {
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return sfail(CPP_ERR_NOT_FOUND, "unknown ticket %llu",
+                                          (unsigned long long)ticket);
+    Request* r = it->second;
+    if (r->state != St::Queued && r->state != St::Running) return collect(s, r, res);
+    if (timeout_us >= 0 && Clock::now() >= deadline) return CPP_PENDING;
+    if (timeout_us < 0) s->cv_done.wait(lk);
+    else s->cv_done.wait_until(lk, deadline);
+  }
+}
+
+cpp_status cpp_plan_cancel(cpp_server_t* s, uint64_t ticket) {
+  if (!s) return sfail(CPP_ERR_INVALID_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return sfail(CPP_ERR_NOT_FOUND, "unknown ticket");
+  Request* r = it->second;
+  if (r->state != St::Queued) return CPP_PENDING;  // already on the device or finished
+  for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+    if (*q == r) { s->queue.erase(q); break; }
+  r->state = St::Cancelled;
+  r->result = CPP_ERR_CANCELLED;
+  r->t_done = Clock::now();
+  ++s->stats.cancelled;
+  s->release_host(r);
+  return CPP_OK;
+}
+
+cpp_status cpp_server_get_stats(cpp_server_t* s, cpp_server_stats_t* out) {
+  if (!s || !out) return sfail(CPP_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  out->resident = s->resident;
+  out->queued = (int32_t)s->queue.size();
+  out->hbm_used = s->darena.used();
+  out->hbm_high_water = s->darena.high_water();
+  return CPP_OK;
+}
+
+void cpp_server_destroy(cpp_server_t* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto& kv : s->reqs) {
+    s->release_host(kv.second);
+    delete kv.second;
+  }
+  s->reqs.clear();
+  for (auto st : s->streams) cudaStreamDestroy(st);
+  if (s->d_arena) cudaFree(s->d_arena);
+  if (s->h_pinned) cudaFreeHost(s->h_pinned);
+  delete s;
+}
+
+}  // extern "C"

@@ -215,3 +215,25 @@ def test_batch_equals_alone():
         np.testing.assert_array_equal(keep[r]["q"].cpu().numpy(), alone["q"])
         np.testing.assert_array_equal(keep[r]["err"].cpu().numpy(), alone["err"])
         assert float(keep[r]["best"].item()) == float(alone["best"])
+
+
+@pytest.mark.parametrize("n", [7, 9, 6])
+def test_dp_nonfinite_candidates_and_padding(n):
+    """NaN / inf candidates (node cost +inf, as the mask gives them) and NaN padding lanes:
+    the GPU search ignores NaN terms exactly like the oracle's fmaxf / strict-< scan."""
+    T, K, Kp = 9, 70, 96
+    rng = np.random.default_rng(n)
+    cand = rng.normal(0, 0.3, (T, n, Kp)).astype(np.float32)
+    cand[:, :, K:] = np.nan
+    pen = np.zeros((T, Kp), np.float32)
+    pen[:, K:] = np.inf
+    for (i, k, j) in [(2, 5, 0), (4, 0, n - 1), (7, 69, 3), (0, 1, 1)]:
+        cand[i, j, k] = np.nan
+        pen[i, k] = np.inf
+    cand[5, 2, 10] = np.inf
+    pen[5, 10] = np.inf
+    pen[3, ::3] = 10.0
+    got = run_dp(cand, pen, K)
+    ref = oracle.dp_f32(cand, pen, K)
+    np.testing.assert_array_equal(got["sel"], ref["sel"])
+    assert got["best"] == ref["best"]
