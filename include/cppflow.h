@@ -171,6 +171,33 @@ cpp_status cpp_dp_search(const float* cand, const float* pen, int32_t T, int32_t
                          int32_t* sel, float* best_cost, float* q_seed, int32_t* dev_status,
                          cpp_stream_t stream);
 
+/* ------------------------------------------------------------------ search without allocation
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory when they plan: code between stream-capture
+ * begin and end (a plain cudaMalloc breaks the capture), real-time loops that
+ * forbid allocation after start-up, and plug-ins whose host application owns
+ * every device allocation. It computes exactly what cpp_dp_search computes, but
+ * its scratch (layer minima, backpointers, final costs) lives in one
+ * file-scope device array of CPP_DP_STATIC_SCRATCH_BYTES inside the library.
+ * That array is reserved on every GPU that loads the library and held until the
+ * process exits; the call itself allocates nothing (no cudaMalloc, no cudaFree,
+ * no allocating library routine). The caller still passes inputs and outputs.
+ * Limit: scratch = align256(4T) + align256(2 T Kb) + align256(4 Kp) bytes with
+ * Kb = Kp rounded up to 8 -- e.g. T = 2000, Kp = 1024 fits, T = 2000, Kp = 2048
+ * does not; larger lattices are rejected with CPP_ERR_INVALID_ARG and a message
+ * (use cpp_dp_search with a caller workspace for them).
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture. Every call uses the same array and leaves its
+ * contents behind, so calls that overlap on the GPU (other streams, other host
+ * threads) race with each other. Each call writes every scratch word it reads,
+ * so nothing needs clearing between calls. Arguments, layouts and errors
+ * otherwise as cpp_dp_search. */
+#define CPP_DP_STATIC_SCRATCH_BYTES (8u << 20)
+cpp_status cpp_dp_search_static(const float* cand, const float* pen, int32_t T, int32_t K,
+                                int32_t Kp, int32_t n, int32_t* sel, float* best_cost,
+                                float* q_seed, int32_t* dev_status, cpp_stream_t stream);
+
 /* ------------------------------------------------------------------ LM (§III-C)
  * Per waypoint independently (the pose residual of waypoint i depends on q_i
  * only, so J is block diagonal): residual e = [p_t - p(q); log(R_t R(q)^T)]
