@@ -6,8 +6,9 @@ FP64 check) over one batch of B synthetic requests of that shape, inputs
 resident in HBM. Beside it the script measures, on the same requests:
   * the plain per-request GPU path (cpp_plan one request at a time, one stream):
     plans/s and p50 / p99 latency,
-  * end to end: host pinned inputs copied in, the batch run, results copied out,
-    all inside the timed region,
+  * end to end through the serving API (cpp_plan_submit / cpp_plan_wait): host
+    inputs copied in, continuous batching, results copied out to host memory,
+    all inside the timed region, with per-request p50 / p99 latency,
   * the search kernel's duration (CUDA events on its stream) for the roofline,
   * SM clocks during the timed region (nvidia-smi),
   * the CPU oracle on a bounded sample of the same workload (rank 0 only).
@@ -118,7 +119,8 @@ def cpu_oracle_run(reqs, threads: int, steps: int = 1):
     (the C oracle releases the GIL), `steps` times. Returns (plans/s, valid, seconds)."""
     import oracle
     oracle.build()
-    probs = [oracle_problem(w) for w in reqs]
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        probs = list(ex.map(oracle_problem, reqs))
     P = oracle.make_params(lm_iters=reqs[0].lm_iters, lambda0=reqs[0].lambda0)
 
     def one(i):
@@ -134,14 +136,15 @@ def cpu_oracle_run(reqs, threads: int, steps: int = 1):
     return len(probs) * steps / dt, valid, dt
 
 
-def cpu_baseline(rank: int) -> dict:
+def cpu_baseline(rank: int, per_core: int = 4) -> dict:
     cores = os.cpu_count() or 1
     S = max(1, min(cores, 16))
-    reqs = workload_requests(S, 0)
+    reqs = workload_requests(S * per_core, 0)
     value, valid, dt = cpu_oracle_run(reqs, S)
     return {"value": round(value, 3), "unit": "plans/s", "cores": S, "kind": "oracle",
-            "sample": f"{S} requests of T=300 K=512 n=7 (mask + FP32 search + FP64 LM + check), "
-                      f"one per thread, {dt:.1f} s wall", "valid": int(valid)}
+            "sample": f"{len(reqs)} requests of T=300 K=512 n=7 (mask + FP32 search + FP64 LM + "
+                      f"check) on {S} threads, {dt:.1f} s wall (~{dt * S:.0f} s of CPU work)",
+            "valid": int(valid)}
 
 
 def run_reference(args, rank: int, world: int):
@@ -305,32 +308,37 @@ def run_cuda(args, rank: int, world: int, dist):
              "p99_ms": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 3),
              "requests": n_plain}
 
-    # ---- end to end: pinned host inputs in, batch, results out (all timed)
+    # ---- end to end through the serving API: host inputs in, results in host memory out
     h2d = sum(c.numel() * 4 + t.numel() * 8 for c, t in zip(cand_h, targets_h))
-    sel_h = torch.empty_like(sel, device="cpu").pin_memory()
-    q_h = torch.empty_like(q_out, device="cpu").pin_memory()
-    err_h = torch.empty_like(err, device="cpu").pin_memory()
-    rep_h = torch.empty_like(rep, device="cpu").pin_memory()
-    d2h = (sel.numel() * 4 + q_out.numel() * 4 + err.numel() * 8 + rep.numel())
+    d2h_per_req = T * 4 + T * n * 4 + T * 16 + cppflow.REPORT_BYTES + 4
+    cand_np = [c.numpy() for c in cand_h]     # pinned host memory, borrowed by the server
+    targ_np = [t.numpy() for t in targets_h]
     e2e_steps = max(1, min(args.steps, 5))
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        for r in range(B):
-            cand_d[r].copy_(cand_h[r], non_blocking=True)
-            targ_d[r].copy_(targets_h[r], non_blocking=True)
-        batch.run(cppflow.STAGE_ALL, stream)
-        sel_h.copy_(sel, non_blocking=True)
-        q_h.copy_(q_out, non_blocking=True)
-        err_h.copy_(err, non_blocking=True)
-        rep_h.copy_(rep, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e = {"value": round(world * B * e2e_steps / (e2e_ms / 1000.0), 3), "unit": "plans/s",
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-           "path": "pinned host -> cudaMemcpyAsync -> cpp_batch_run -> pinned host"}
+    lat = []
+    e2e_valid = 0
+    with cppflow.Server(P, device=local, hbm_budget=int(B * 6.5e6) + (256 << 20),
+                        max_batch=args.serve_batch, max_inflight=2, pinned_bytes=64 << 20) as srv:
+        for rep_i in range(e2e_steps + 1):       # the first pass warms the server up
+            t0 = time.perf_counter()
+            tickets = [srv.submit(robots[reqs[r].arm_seed - 100], cand_np[r], targ_np[r], K,
+                                  borrow=True) for r in range(B)]
+            outs = [srv.wait(tk) for tk in tickets]
+            dt = time.perf_counter() - t0
+            if rep_i == 0:
+                continue
+            lat += [o[1]["latency_ms"] for o in outs]
+            e2e_valid += sum(int(o[1]["report"]["valid"]) for o in outs)
+            e2e_total = dt if rep_i == 1 else e2e_total + dt
+        sstats = srv.stats()
+    lat.sort()
+    e2e = {"value": round(world * B * e2e_steps / e2e_total, 3), "unit": "plans/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(B * d2h_per_req),
+           "path": "cpp_plan_submit (pinned host inputs, borrowed) -> continuous batching -> "
+                   "cpp_plan_wait (results in host memory)",
+           "p50_ms": round(lat[len(lat) // 2], 3),
+           "p99_ms": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 3),
+           "valid_plans": f"{e2e_valid}/{B * e2e_steps}",
+           "batches_per_step": round(sstats["batches"] / (e2e_steps + 1), 2)}
 
     # ---- roofline of the search kernel (the dominant kernel)
     edges = B * (T - 1) * K * K
@@ -378,6 +386,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=304)
     ap.add_argument("--plain", type=int, default=32, help="requests timed on the plain path")
+    ap.add_argument("--serve-batch", type=int, default=152, help="server: requests per launch")
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     args = ap.parse_args()

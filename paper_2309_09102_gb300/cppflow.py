@@ -59,6 +59,34 @@ class PlanDesc(C.Structure):
 
 
 REPORT_BYTES = C.sizeof(Report)
+REQ_BORROW = 1
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("device", C.c_int32), ("max_slots", C.c_int32), ("max_batch", C.c_int32),
+                ("max_inflight", C.c_int32), ("hbm_budget_bytes", C.c_size_t),
+                ("pinned_bytes", C.c_size_t), ("params", Params)]
+
+
+class PlanReq(C.Structure):
+    _fields_ = [("robot", C.c_void_p), ("T", C.c_int32), ("K", C.c_int32), ("Kp", C.c_int32),
+                ("flags", C.c_int32), ("cand", C.c_void_p), ("targets", C.c_void_p)]
+
+
+class PlanResult(C.Structure):
+    _fields_ = [("sel", C.c_void_p), ("q", C.c_void_p), ("pose_err", C.c_void_p),
+                ("report", C.c_void_p), ("best_cost", C.c_void_p), ("latency_ms", C.c_double),
+                ("dev_status", C.c_int32), ("reserved", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(f, C.c_uint64) for f in ("submitted", "completed", "failed", "cancelled",
+                                           "batches", "sum_batch")] + [
+        (f, C.c_int32) for f in ("max_batch_seen", "resident", "queued", "reserved")] + [
+        ("hbm_used", C.c_size_t), ("hbm_high_water", C.c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 _lib = None
 _P = C.c_void_p
@@ -85,6 +113,14 @@ _SIGS = {
     "cpp_batch_run": (C.c_int, [_P, C.c_uint32, _P]),
     "cpp_batch_launches": (C.c_int32, [_P, C.c_uint32]),
     "cpp_batch_destroy": (None, [_P]),
+    "cpp_server_config_default": (None, [_P]),
+    "cpp_server_create": (C.c_int, [_P, C.POINTER(C.c_void_p)]),
+    "cpp_plan_submit": (C.c_int, [_P, _P, C.POINTER(C.c_uint64)]),
+    "cpp_plan_poll": (C.c_int, [_P, C.c_uint64, _P]),
+    "cpp_plan_wait": (C.c_int, [_P, C.c_uint64, _P, C.c_int64]),
+    "cpp_plan_cancel": (C.c_int, [_P, C.c_uint64]),
+    "cpp_server_get_stats": (C.c_int, [_P, _P]),
+    "cpp_server_destroy": (None, [_P]),
 }
 
 
@@ -259,6 +295,93 @@ class Batch:
         if self.handle:
             lib().cpp_batch_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """cpp_server_* with host numpy buffers. submit() returns a ticket; poll()/wait()
+    return (status, result dict) once the plan is done."""
+
+    def __init__(self, params: Params | None = None, device: int = 0, hbm_budget: int | None = None,
+                 max_slots: int | None = None, max_batch: int | None = None,
+                 max_inflight: int | None = None, pinned_bytes: int | None = None):
+        cfg = ServerConfig()
+        lib().cpp_server_config_default(C.byref(cfg))
+        cfg.device = device
+        if params is not None:
+            cfg.params = params
+        for name, v in (("hbm_budget_bytes", hbm_budget), ("max_slots", max_slots),
+                        ("max_batch", max_batch), ("max_inflight", max_inflight),
+                        ("pinned_bytes", pinned_bytes)):
+            if v is not None:
+                setattr(cfg, name, v)
+        h = C.c_void_p()
+        _check(lib().cpp_server_create(C.byref(cfg), C.byref(h)), "cpp_server_create")
+        self.handle = h
+        self._live = {}  # ticket -> (robot, inputs kept alive, shape)
+
+    def submit(self, robot: Robot, cand, targets, K: int, borrow: bool = False) -> int:
+        import numpy as np
+        cand = np.ascontiguousarray(cand, dtype=np.float32)
+        targets = np.ascontiguousarray(targets, dtype=np.float64)
+        T, n, Kp = cand.shape
+        req = PlanReq(C.addressof(robot), T, K, Kp, REQ_BORROW if borrow else 0,
+                      cand.ctypes.data, targets.ctypes.data)
+        t = C.c_uint64()
+        _check(lib().cpp_plan_submit(self.handle, C.byref(req), C.byref(t)), "cpp_plan_submit")
+        self._live[t.value] = (robot, (cand, targets) if borrow else None, (T, n))
+        return t.value
+
+    def _result(self, ticket: int, fn, *extra):
+        import numpy as np
+        if ticket not in self._live:  # unknown here: let the library answer (NOT_FOUND)
+            _check(fn(self.handle, ticket, None, *extra), "cpp_plan_poll")
+        robot, _, (T, n) = self._live[ticket]
+        sel = np.zeros(T, np.int32)
+        q = np.zeros((T, n), np.float32)
+        err = np.zeros((T, 2), np.float64)
+        rep = Report()
+        best = np.zeros(1, np.float32)
+        res = PlanResult(sel.ctypes.data, q.ctypes.data, err.ctypes.data, C.addressof(rep),
+                         best.ctypes.data, 0.0, 0, 0)
+        st = fn(self.handle, ticket, C.byref(res), *extra)
+        if st == PENDING:
+            return st, None
+        self._live.pop(ticket, None)
+        if st == ERR_NOT_FOUND:
+            raise CppflowError(st, last_error())
+        return st, dict(sel=sel, q=q, err=err, report=rep.as_dict(), best=float(best[0]),
+                        latency_ms=res.latency_ms, dev_status=res.dev_status)
+
+    def poll(self, ticket: int):
+        return self._result(ticket, lib().cpp_plan_poll)
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        return self._result(ticket, lib().cpp_plan_wait, timeout_us)
+
+    def cancel(self, ticket: int) -> int:
+        return lib().cpp_plan_cancel(self.handle, ticket)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().cpp_server_get_stats(self.handle, C.byref(s)), "cpp_server_get_stats")
+        return s.as_dict()
+
+    def close(self):
+        if self.handle:
+            lib().cpp_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
     def __del__(self):
         try:

@@ -420,6 +420,232 @@ __global__ void __launch_bounds__(kDp2Threads) dp2_forward_kernel(const __grid_c
   for (int k = tid; k < Kp; k += kDp2Threads) rq.costT[k] = rf[rec_off(NW, k) + NJ];
 }
 
+// ------------------------------------------------------------------ forward sweep, split
+// Third form (the one used for n in {6, 7, 9}, Kp <= 1024). As the staged form,
+// plus:
+//  * the 256 threads form two groups of 128 that own the same R successors per
+//    thread (Kp <= 128 R) and split the predecessor tiles in two contiguous
+//    halves, so each broadcast record feeds R edges; the halves' (minimum,
+//    tile) pairs merge through shared memory, the lower half winning ties, so
+//    the lowest index still wins;
+//  * one staging buffer and one record buffer: the bulk copy of layer i+2 is
+//    issued as soon as every thread has taken its own layer-(i+1) values, and
+//    the new records overwrite the old ones after the rescans;
+//  * full 32-record tiles are unrolled from a tile base pointer.
+constexpr int kDp3Threads = 256;
+constexpr int kDp3Group = 128;
+
+size_t dp3_smem_bytes(int nj, int Kp, int R) {
+  const int NW = ((nj + 1 + 3) / 4) * 4;
+  return (size_t)rec_layer_floats(NW, Kp) * 4  // records
+         + (size_t)nj * Kp * 4                  // raw layer staging
+         + (size_t)Kp * 4                       // node-cost staging
+         + (size_t)3 * R * kDp3Group * 4        // group exchange: min, tile, index
+         + 64;                                  // barrier
+}
+
+template <int NJ, int R>
+__device__ __forceinline__ void sweep_pair(const uint64_t (&own)[R][Rec<NJ>::NP], const float* r0,
+                                           const float* r1, float (&tb)[R]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    tb[r] = min3f(tb[r], r0[NJ] + linf_rec<NJ>(own[r], r0), r1[NJ] + linf_rec<NJ>(own[r], r1));
+}
+
+template <int NW>
+__device__ __forceinline__ void load_rec(const float* p, float (&v)[NW]) {
+#pragma unroll
+  for (int w = 0; w < NW; w += 4) {
+    const float4 x = *reinterpret_cast<const float4*>(p + w);
+    v[w] = x.x; v[w + 1] = x.y; v[w + 2] = x.z; v[w + 3] = x.w;
+  }
+}
+
+template <int NJ, int R, class Src>
+__global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __grid_constant__ Src src) {
+  constexpr int NW = Rec<NJ>::NW, NP = Rec<NJ>::NP;
+  const Req& rq = src.req(blockIdx.x);
+  const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
+  const int tid = threadIdx.x, g = tid / kDp3Group, lt = tid % kDp3Group;
+  extern __shared__ __align__(128) float sm3[];
+  const int RL = rec_layer_floats(NW, Kp);
+  float* const rec = sm3;                                   // [RL] records (skewed)
+  float* const stg = rec + RL;                              // [NJ][Kp] staged layer
+  float* const pst = stg + (size_t)NJ * Kp;                 // [Kp] staged node costs
+  float* const xmin = pst + Kp;                             // [R][128]
+  int* const xtile = reinterpret_cast<int*>(xmin + R * kDp3Group);  // [R][128]
+  int* const xarg = xtile + R * kDp3Group;                  // [R][128]
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(xarg + R * kDp3Group);
+  __shared__ int timeout_flag;
+
+  const uint32_t layer_bytes = (uint32_t)(NJ * Kp * 4), pen_bytes = (uint32_t)(Kp * 4);
+  auto issue = [&](int L) {  // one thread; layer L completes phase L of the barrier
+    mbar_expect_tx(bar, layer_bytes + pen_bytes);
+    bulk_g2s(stg, rq.cand + (size_t)L * NJ * Kp, layer_bytes, bar);
+    bulk_g2s(pst, rq.pen + (size_t)L * Kp, pen_bytes, bar);
+  };
+  auto wait_layer = [&](int L) -> bool { return mbar_wait_bounded(bar, (uint32_t)(L & 1)); };
+
+  if (tid == 0) {
+    timeout_flag = 0;
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) issue(0);
+  if (!wait_layer(0)) atomicExch(&timeout_flag, 1);
+  {
+    const float m0 = rq.pen_min[0];
+    for (int k = tid; k < Kp; k += kDp3Threads) {
+      float v[NW];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) v[j] = -stg[(size_t)j * Kp + k];
+      v[NJ] = k < K ? pst[k] - m0 : CUDART_INF_F;
+#pragma unroll
+      for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
+      float4* dst = reinterpret_cast<float4*>(rec + rec_off(NW, k));
+#pragma unroll
+      for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
+    }
+  }
+  __syncthreads();
+  if (timeout_flag) {  // a copy that never completed: wait once more (bounded), then stop
+    raise_status(rq.status, CPP_ERR_TIMEOUT);
+    if (tid == 0) wait_layer(0);
+    return;
+  }
+  if (tid == 0 && T > 1) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(1);
+  }
+
+  int kp[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) kp[r] = lt + r * kDp3Group;
+  const int K4 = (K + 3) & ~3;
+  const int ntiles = (K4 + kDp2Tile - 1) / kDp2Tile;
+  const int half = (ntiles + 1) / 2;
+  const int t_lo = g == 0 ? 0 : half, t_hi = g == 0 ? half : ntiles;
+
+  for (int i = 0; i + 1 < T; ++i) {
+    const int L = i + 1;
+    if (!wait_layer(L)) atomicExch(&timeout_flag, 1);
+    uint64_t own[R][NP];
+    float rpen[R];
+    const float m1 = rq.pen_min[L];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = kp[r] < Kp ? kp[r] : Kp - 1;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const float a = stg[(size_t)(2 * p) * Kp + k];
+        const float b = (2 * p + 1 < NJ) ? stg[(size_t)(2 * p + 1) * Kp + k] : 0.f;
+        own[r][p] = pack2(a, b);
+      }
+      rpen[r] = kp[r] < K ? pst[kp[r]] - m1 : CUDART_INF_F;
+    }
+    __syncthreads();  // everyone holds its layer-L values: the staging buffer is free
+    if (timeout_flag) {
+      raise_status(rq.status, CPP_ERR_TIMEOUT);
+      if (tid == 0) wait_layer(L);
+      return;
+    }
+    if (tid == 0 && L + 1 < T) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(L + 1);
+    }
+
+    float best[R];
+    int btile[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; btile[r] = -1; }
+#pragma unroll 1
+    for (int t = t_lo; t < t_hi; ++t) {
+      const int kb = t * kDp2Tile;
+      const float* base = rec + rec_off(NW, kb);
+      float tb[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) tb[r] = CUDART_INF_F;
+      if (kb + kDp2Tile <= K4) {
+#pragma unroll
+        for (int k = 0; k < kDp2Tile; k += 2) {
+          float r0[NW], r1[NW];
+          load_rec<NW>(base + k * NW, r0);
+          load_rec<NW>(base + (k + 1) * NW, r1);
+          sweep_pair<NJ, R>(own, r0, r1, tb);
+        }
+      } else {
+        for (int k = 0; kb + k < K4; k += 2) {
+          float r0[NW], r1[NW];
+          load_rec<NW>(base + k * NW, r0);
+          load_rec<NW>(base + (k + 1) * NW, r1);
+          sweep_pair<NJ, R>(own, r0, r1, tb);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (tb[r] < best[r]) { best[r] = tb[r]; btile[r] = t; }
+    }
+    // merge the halves: the upper half (larger k) replaces only a strictly smaller minimum
+    if (g == 1) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) { xmin[r * kDp3Group + lt] = best[r]; xtile[r * kDp3Group + lt] = btile[r]; }
+    }
+    __syncthreads();
+    if (g == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float b1 = xmin[r * kDp3Group + lt];
+        const int t1 = xtile[r * kDp3Group + lt];
+        if (b1 < best[r]) { best[r] = b1; btile[r] = t1; }
+        xmin[r * kDp3Group + lt] = best[r];
+        xtile[r * kDp3Group + lt] = btile[r];
+      }
+    }
+    __syncthreads();
+    // rescans: successor r is handled by group r % 2 (group 0 when R == 1)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if ((R == 1 ? 0 : (r & 1)) != g) continue;
+      const float bv = xmin[r * kDp3Group + lt];
+      const int bt = xtile[r * kDp3Group + lt];
+      int arg = 0;
+      if (bt >= 0) {
+        const int kb = bt * kDp2Tile, ke = min(kb + kDp2Tile, K4);
+        const float* base = rec + rec_off(NW, kb);
+        for (int k = kb; k < ke; ++k) {
+          const float* rk = base + (k - kb) * NW;
+          if (rk[NJ] + linf_rec<NJ>(own[r], rk) == bv) { arg = k; break; }
+        }
+      }
+      xarg[r * kDp3Group + lt] = arg;
+    }
+    __syncthreads();  // rescans done: the records may be replaced
+    uint16_t* bprow = rq.bp + (size_t)L * Kb;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if ((R == 1 ? 0 : (r & 1)) != g || kp[r] >= Kp) continue;
+      float v[NW];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        float a, b;
+        unpack2(own[r][p], a, b);
+        v[2 * p] = -a;
+        if (2 * p + 1 < NJ) v[2 * p + 1] = -b;
+      }
+      v[NJ] = kp[r] < K ? xmin[r * kDp3Group + lt] + rpen[r] : CUDART_INF_F;
+#pragma unroll
+      for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
+      float4* dst = reinterpret_cast<float4*>(rec + rec_off(NW, kp[r]));
+#pragma unroll
+      for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
+      bprow[kp[r]] = (uint16_t)xarg[r * kDp3Group + lt];
+    }
+    __syncthreads();
+  }
+  for (int k = tid; k < Kp; k += kDp3Threads) rq.costT[k] = rec[rec_off(NW, k) + NJ];
+}
+
 // Any n and Kp that fit in shared memory: successor values are read back from
 // shared memory instead of registers.
 template <class Src>
@@ -577,13 +803,22 @@ static cudaError_t launch_fwd2_r(const Src& s, int nreq, size_t smem, cudaStream
   return cudaGetLastError();
 }
 
+template <int NJ, int R, class Src>
+static cudaError_t launch_fwd3_r(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
+  const size_t smem = dp3_smem_bytes(NJ, max_Kp, R);
+  cudaError_t e = allow_smem(dp3_forward_kernel<NJ, R, Src>, smem);
+  if (e != cudaSuccess) return e;
+  dp3_forward_kernel<NJ, R, Src><<<nreq, kDp3Threads, smem, st>>>(s);
+  return cudaGetLastError();
+}
+
 template <int NJ, class Src>
 static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
-  const size_t smem = dp2_smem_bytes(NJ, max_Kp);
-  const int R = (max_Kp + kDp2Threads - 1) / kDp2Threads;
-  if (R <= 1) return launch_fwd2_r<NJ, 1>(s, nreq, smem, st);
-  if (R <= 2) return launch_fwd2_r<NJ, 2>(s, nreq, smem, st);
-  return launch_fwd2_r<NJ, 4>(s, nreq, smem, st);
+  const int R = (max_Kp + kDp3Group - 1) / kDp3Group;
+  if (R <= 1) return launch_fwd3_r<NJ, 1>(s, nreq, max_Kp, st);
+  if (R <= 2) return launch_fwd3_r<NJ, 2>(s, nreq, max_Kp, st);
+  if (R <= 4) return launch_fwd3_r<NJ, 4>(s, nreq, max_Kp, st);
+  return launch_fwd3_r<NJ, 8>(s, nreq, max_Kp, st);
 }
 
 template <class Src>

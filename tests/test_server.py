@@ -1,0 +1,93 @@
+"""The serving loop (cpp_server_*): every plan is the same alone and in the mix;
+admission by HBM budget; rejection of a request larger than the budget;
+cancellation of queued requests; host-side validation. Failures are made on the
+host (bad inputs, tiny budgets, cancelled tickets) -- nothing here faults a GPU."""
+import math
+
+import numpy as np
+import pytest
+
+import problems
+from gpu_util import params_pair, run_plan
+from paper_2309_09102_gb300 import cppflow
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix(count, seed0=700):
+    shapes = [(30, 40), (61, 128), (12, 7), (45, 256), (2, 3), (80, 96), (17, 33), (50, 512)]
+    return [problems.small(T=shapes[i % len(shapes)][0], K=shapes[i % len(shapes)][1],
+                           seed=seed0 + i) for i in range(count)]
+
+
+def test_served_equals_alone():
+    """Requests submitted together (batched, overlapping launches) return exactly what each
+    returns from cpp_plan alone."""
+    pbs = _mix(12)
+    _, cp = params_pair(lm_iters=10)
+    robots = [cppflow.robot_from_arm(pb.arm) for pb in pbs]
+    with cppflow.Server(cp, hbm_budget=1 << 30, max_inflight=2, max_batch=5) as srv:
+        tickets = [srv.submit(robots[i], pb.cand, pb.targets, pb.K) for i, pb in enumerate(pbs)]
+        results = [srv.wait(t) for t in tickets]
+        stats = srv.stats()
+    assert stats["completed"] == len(pbs) and stats["batches"] >= 3
+    for i, pb in enumerate(pbs):
+        st, res = results[i]
+        assert st == cppflow.OK
+        alone = run_plan(robots[i], cp, pb.cand, pb.targets, pb.K)
+        np.testing.assert_array_equal(res["sel"], alone["sel"])
+        np.testing.assert_array_equal(res["q"], alone["q"])
+        np.testing.assert_array_equal(res["err"], alone["err"])
+        assert res["best"] == float(alone["best"])
+        assert res["report"]["valid"] == alone["report"]["valid"]
+        assert res["latency_ms"] > 0
+
+
+def test_borrowed_inputs_and_tiny_budget():
+    """A budget that holds about one request at a time: every request still completes,
+    admitted as memory frees up; a request larger than the whole budget is refused."""
+    pbs = _mix(6, seed0=900)
+    _, cp = params_pair(lm_iters=5)
+    robots = [cppflow.robot_from_arm(pb.arm) for pb in pbs]
+    big = max(pb.cand.nbytes for pb in pbs)
+    budget = 3 * big + (1 << 20)
+    with cppflow.Server(cp, hbm_budget=budget, max_inflight=2) as srv:
+        tickets = [srv.submit(robots[i], pb.cand, pb.targets, pb.K, borrow=True)
+                   for i, pb in enumerate(pbs)]
+        for t in tickets:
+            st, res = srv.wait(t)
+            assert st == cppflow.OK
+        s = srv.stats()
+        assert s["hbm_high_water"] <= budget
+        huge = problems.small(T=200, K=512, seed=5)
+        with pytest.raises(cppflow.CppflowError) as e:
+            srv.submit(cppflow.robot_from_arm(huge.arm), huge.cand, huge.targets, huge.K)
+        assert e.value.status == cppflow.ERR_BUDGET
+
+
+def test_cancel_and_validation():
+    pbs = _mix(40, seed0=1100)
+    _, cp = params_pair(lm_iters=5)
+    robots = [cppflow.robot_from_arm(pb.arm) for pb in pbs]
+    with cppflow.Server(cp, hbm_budget=1 << 30, max_inflight=1, max_batch=2) as srv:
+        tickets = [srv.submit(robots[i], pb.cand, pb.targets, pb.K) for i, pb in enumerate(pbs)]
+        cancelled = [t for t in tickets[20:] if srv.cancel(t) == cppflow.OK]
+        for t in tickets:
+            st, res = srv.wait(t)
+            assert st == (cppflow.ERR_CANCELLED if t in cancelled else cppflow.OK)
+        with pytest.raises(cppflow.CppflowError) as e:
+            srv.poll(tickets[0])  # already collected
+        assert e.value.status == cppflow.ERR_NOT_FOUND
+        bad = pbs[0].targets.copy()
+        bad[3, 4] = math.nan
+        with pytest.raises(cppflow.CppflowError) as e:
+            srv.submit(robots[0], pbs[0].cand, bad, pbs[0].K)
+        assert e.value.status == cppflow.ERR_INVALID_ARG
+        bad = pbs[0].targets.copy()
+        bad[1, 3:] *= 1.01
+        with pytest.raises(cppflow.CppflowError) as e:
+            srv.submit(robots[0], pbs[0].cand, bad, pbs[0].K)
+        assert e.value.status == cppflow.ERR_INVALID_ARG
+        s = srv.stats()
+    assert s["cancelled"] == len(cancelled)
+    assert s["completed"] == len(pbs) - len(cancelled)
