@@ -346,7 +346,7 @@ def run_cuda(args, rank: int, world: int, dist):
     dp_s = statistics.mean(dp_ms) / 1000.0
     achieved = edges * ops_per_edge / dp_s / 1e12
     peak = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    roof = {"bound": "alu", "kernel": "dp_forward_kernel", "achieved": round(achieved, 3),
+    roof = {"bound": "alu", "kernel": "dp3_forward_kernel", "achieved": round(achieved, 3),
             "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
             "traffic": None,
             "ops": f"{ops_per_edge} FP32 ALU ops per edge (n sub, n-1 abs-max, add, min) x "

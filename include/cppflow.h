@@ -98,7 +98,8 @@ typedef struct cpp_params {
     double lambda_min;   /* default 1e-12 */
     double lambda_max;   /* default 1e12 */
     double freeze_step;  /* a waypoint stops when max|delta| < this (default 1e-10) */
-    double freeze_cost;  /* a waypoint stops when F = |e|^2/2 < this (default 1e-20) */
+    double freeze_cost;  /* a waypoint stops when F = |e|^2/2 < this (default 1e-13: |e| ~ 4.5e-7,
+                            the resolution of FP32 forward kinematics) */
     int32_t lm_iters;    /* LM iterations per waypoint (default 20) */
     uint32_t free_mask;  /* bit j set: LM may move joint j (default all) */
     int32_t lm_fp64;     /* 0: FP32 FK/Jacobian + FP64 normal equations and Cholesky;

@@ -121,7 +121,7 @@ def make_params(**kw) -> Params:
     d = dict(tau_pos=1e-3, tau_rot=math.radians(0.1), near_margin=math.radians(1.5),
              pen_limit=10.0, pen_pose=100.0, jump_max=math.radians(7.0), lambda0=1e-3,
              lambda_up=10.0, lambda_down=10.0, lambda_min=1e-12, lambda_max=1e12,
-             freeze_step=1e-10, freeze_cost=1e-20, lm_iters=10, free_mask=0xFFFF)
+             freeze_step=1e-10, freeze_cost=1e-13, lm_iters=10, free_mask=0xFFFF)
     d.update(kw)
     for k, v in d.items():
         setattr(p, k, v)

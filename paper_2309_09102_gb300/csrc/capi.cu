@@ -124,7 +124,7 @@ void cpp_params_default(cpp_params_t* p) {
   p->lambda_min = 1e-12;
   p->lambda_max = 1e12;
   p->freeze_step = 1e-10;
-  p->freeze_cost = 1e-20;
+  p->freeze_cost = 1e-13;
   p->lm_iters = 20;
   p->free_mask = 0xFFFFFFFFu;
   p->lm_fp64 = 0;

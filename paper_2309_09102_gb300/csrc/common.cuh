@@ -125,7 +125,10 @@ __device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(
 __device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
 
 // FP32 FK of one configuration (NJ joints known at compile time, or NJ = 0 for
-// a runtime n <= 16).
+// a runtime n <= 16). The candidate path (masks, cpp_fk_batch) uses the
+// hardware sine/cosine (__sincosf: absolute error below 2^-21.4 on [-pi, pi],
+// which covers every in-limit joint angle; it carries at most a few 1e-6 m /
+// rad into the pose), the LM uses the correctly range-reduced sincosf.
 template <int NJ>
 __device__ __forceinline__ void fk_f32(const RobotF& rb, const float* q, float R[9], float p[3]) {
   pose_identity(R, p);
@@ -134,7 +137,7 @@ __device__ __forceinline__ void fk_f32(const RobotF& rb, const float* q, float R
   for (int j = 0; j < (NJ ? NJ : kMaxJ); ++j) {
     if (!NJ && j >= n) break;
     float s, c;
-    sincos_t(q[j] + rb.th0[j], &s, &c);
+    __sincosf(q[j] + rb.th0[j], &s, &c);
     dh_step(R, p, c, s, rb.ca[j], rb.sa[j], rb.a[j], rb.d[j]);
   }
 }

@@ -14,13 +14,18 @@
 //
 // Kernels
 //   layer_min_kernel    m_i for every waypoint (one warp per waypoint)
-//   dp_forward_kernel   one CTA per request walks the T steps. The whole layer
-//                       q_i ([n][Kp]) and C_i sit in shared memory; each thread
-//                       owns R successor nodes k' whose joint values stay in
-//                       registers, and streams every predecessor k through a
-//                       float4 broadcast read (4 k per load). Per edge: n FADD,
-//                       n-1 abs-max, one FADD, one compare/select -- pure ALU
-//                       work, no HBM traffic except 2 bytes of backpointer.
+//   dp3_forward_kernel  one CTA per request walks the T steps (n in {6, 7, 9},
+//                       Kp <= 1024). Each layer's raw block q_i [n][Kp] and its
+//                       node-cost row arrive in shared memory by 1-D bulk copies
+//                       (TMA engine, mbarrier completion) a step ahead; every node
+//                       of the current layer becomes a record [-q_k, C_k] in
+//                       shared memory; each thread owns R successors whose joint
+//                       values stay in registers, and two thread groups split
+//                       the predecessors. Per edge: n subtractions, n - 1
+//                       abs-max, one add, one min -- 2n + 1 FP32 lane
+//                       operations, no HBM traffic except 2 bytes of backpointer
+//                       per successor and step.
+//   dp_forward_generic  any other n or Kp that fits shared memory (slow path).
 //   dp_backtrack_kernel lowest argmin of C_{T-1}, then the serial walk
 //                       k_i = bp[i+1][k_{i+1}] over backpointer rows staged into
 //                       shared memory by 1-D bulk copies (TMA engine, mbarrier
@@ -37,12 +42,12 @@ int bp_stride(int Kp) { return (Kp + 7) & ~7; }
 
 size_t dp_smem_bytes(int n, int Kp) { return (size_t)(2 * n + 2) * Kp * sizeof(float); }
 
-size_t dp2_smem_bytes(int nj, int Kp);
+size_t dp3_smem_bytes(int nj, int Kp, int R);
 
 bool dp_supported(int n, int Kp) {
-  if (dp_smem_bytes(n, Kp) > 227u * 1024u) return false;
+  if (dp_smem_bytes(n, Kp) > 227u * 1024u) return false;  // generic kernel
   const bool fast = (n == 6 || n == 7 || n == 9) && Kp <= 1024;
-  return !fast || dp2_smem_bytes(n, Kp) <= 227u * 1024u;
+  return !fast || dp3_smem_bytes(n, Kp, (Kp + 127) / 128) <= 227u * 1024u;
 }
 
 // ------------------------------------------------------------------ layer minimum
@@ -60,129 +65,18 @@ __global__ void __launch_bounds__(256) layer_min_kernel(const __grid_constant__ 
   if (lane == 0) rq.pen_min[i] = isinf(m) ? 0.f : m;
 }
 
-// ------------------------------------------------------------------ forward sweep
-template <int NJ, int R>
-__device__ __forceinline__ void load_own(const float* __restrict__ cand, int i, int Kp,
-                                         const int (&kp)[R], float (&dst)[R][NJ]) {
-  const float* layer = cand + (size_t)i * NJ * Kp;
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) dst[r][j] = kp[r] < Kp ? __ldg(layer + (size_t)j * Kp + kp[r]) : 0.f;
-}
-
-#define CPP_DP_EDGE(CMP, OFF)                                              \
-  {                                                                        \
-    const float cv = c.CMP;                                                \
-    _Pragma("unroll") for (int r = 0; r < R; ++r) {                        \
-      float d = fabsf(qn[r][0] - qa[0].CMP);                               \
-      _Pragma("unroll") for (int j = 1; j < NJ; ++j)                       \
-          d = fmaxf(d, fabsf(qn[r][j] - qa[j].CMP));                       \
-      const float v = cv + d;                                              \
-      if (v < best[r]) {                                                   \
-        best[r] = v;                                                       \
-        arg[r] = 4 * k4 + (OFF);                                           \
-      }                                                                    \
-    }                                                                      \
-  }
-
-template <int NJ, int R, class Src>
-__global__ void __launch_bounds__(kDpThreads) dp_forward_kernel(const __grid_constant__ Src src) {
-  const Req& rq = src.req(blockIdx.x);
-  const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
-  extern __shared__ __align__(16) float sm[];
-  // q layers at sm + b * NJ * Kp, cost vectors at sm + 2 * NJ * Kp + b * Kp (b = step parity)
-  float* const qbase = sm;
-  float* const cbase = sm + 2 * NJ * Kp;
-  const int tid = threadIdx.x;
-  const float* __restrict__ cand = rq.cand;
-
-  // layer 0 and C_0
-  {
-    const float m0 = rq.pen_min[0];
-    const float4* src4 = reinterpret_cast<const float4*>(cand);
-    float4* dst4 = reinterpret_cast<float4*>(qbase);
-    for (int x = tid; x < NJ * Kp / 4; x += kDpThreads) dst4[x] = __ldg(src4 + x);
-    for (int k = tid; k < Kp; k += kDpThreads) cbase[k] = k < K ? rq.pen[k] - m0 : CUDART_INF_F;
-  }
-  int kp[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) kp[r] = tid + r * kDpThreads;
-  float qn[R][NJ];
-  if (T > 1) load_own<NJ, R>(cand, 1, Kp, kp, qn);
-  __syncthreads();
-
-  const int K4 = (K + 3) >> 2, Kp4 = Kp >> 2;
-  for (int i = 0; i + 1 < T; ++i) {
-    const int cur = i & 1, nxt = cur ^ 1;
-    const float4* __restrict__ q4 = reinterpret_cast<const float4*>(qbase + cur * NJ * Kp);
-    const float4* __restrict__ c4 = reinterpret_cast<const float4*>(cbase + cur * Kp);
-    float* qnxt = qbase + nxt * NJ * Kp;
-    float* cnxt = cbase + nxt * Kp;
-
-    float qnn[R][NJ];
-    if (i + 2 < T) load_own<NJ, R>(cand, i + 2, Kp, kp, qnn);
-    const float m1 = rq.pen_min[i + 1];
-    float rpen[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      rpen[r] = kp[r] < K ? __ldg(rq.pen + (size_t)(i + 1) * Kp + kp[r]) - m1 : CUDART_INF_F;
-
-    float best[R];
-    int arg[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; arg[r] = 0; }
-
-#pragma unroll 1
-    for (int k4 = 0; k4 < K4; ++k4) {
-      const float4 c = c4[k4];
-      float4 qa[NJ];
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) qa[j] = q4[j * Kp4 + k4];
-      CPP_DP_EDGE(x, 0)
-      CPP_DP_EDGE(y, 1)
-      CPP_DP_EDGE(z, 2)
-      CPP_DP_EDGE(w, 3)
-    }
-
-    uint16_t* bprow = rq.bp + (size_t)(i + 1) * Kb;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (kp[r] < Kp) {
-        cnxt[kp[r]] = kp[r] < K ? best[r] + rpen[r] : CUDART_INF_F;
-        bprow[kp[r]] = (uint16_t)arg[r];
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) qnxt[j * Kp + kp[r]] = qn[r][j];
-      }
-    }
-    __syncthreads();
-    if (i + 2 < T) {
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) qn[r][j] = qnn[r][j];
-    }
-  }
-  const float* cfin = cbase + ((T - 1) & 1) * Kp;
-  for (int k = tid; k < Kp; k += kDpThreads) rq.costT[k] = cfin[k];
-}
-
-// ------------------------------------------------------------------ forward sweep, staged
-// Second form of the sweep (used for n in {6, 7, 9}, Kp <= 1024):
-//  * each layer's raw block q_i [n][Kp] and node-cost row pen_i arrive in shared
-//    memory by 1-D bulk copies (TMA engine, mbarrier completion) issued two
-//    steps ahead, so no thread waits on HBM inside the sweep;
-//  * every node k of the current layer is a record [-q_{k,0} .. -q_{k,n-1}, C_k]
-//    (NW floats, 16-byte multiple): one predecessor costs NW/4 broadcast float4
-//    loads, and the joint differences are packed FP32 pair additions
-//    q' + (-q) (bit-identical to q' - q, round-to-nearest);
-//  * the sweep keeps only the running minimum per 32-node tile and the first
-//    tile that lowered it; the lowest index attaining the minimum is then
-//    recovered by re-evaluating that one tile. Same values, same ties.
+// ------------------------------------------------------------------ predecessor records
+// Every node k of the current layer is a record [-q_{k,0} .. -q_{k,n-1}, C_k]
+// (NW floats, a 16-byte multiple): one predecessor costs NW/4 broadcast float4
+// loads, and the joint differences are additions q' + (-q) (bit-identical to
+// q' - q, round-to-nearest). The sweep keeps only the running
+// minimum per 32-node tile and the first tile that lowered it; the lowest index
+// attaining the minimum is then recovered by re-evaluating that one tile. Same
+// values, same ties.
 template <int NJ>
 struct Rec {
   static constexpr int NW = ((NJ + 1 + 3) / 4) * 4;  // floats per record
-  static constexpr int NP = (NJ + 1) / 2;             // packed pairs of own joints
+  static constexpr int NP = (NJ + 1) / 2;             // register pairs of own joints
 };
 
 __device__ __forceinline__ uint64_t pack2(float a, float b) {
@@ -193,52 +87,28 @@ __device__ __forceinline__ uint64_t pack2(float a, float b) {
 __device__ __forceinline__ void unpack2(uint64_t v, float& a, float& b) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
 }
-__device__ __forceinline__ uint64_t addx2(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
 
-__device__ __forceinline__ float max3f(float a, float b, float c) {
-  float r;
-  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-__device__ __forceinline__ float min3f(float a, float b, float c) {
-  float r;
-  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
 
 // max_j |own_j - q_j| for one predecessor record (negated joints in rec[0..NJ-1]).
-// The differences are packed pair additions own + (-q); the absolute values are
-// folded into three-input max operations (max is exact, so any grouping gives the
-// same value, and NaN terms are ignored as with fmaxf).
+// IEEE subtraction a - b is a + (-b); max is exact, so the grouping does not
+// matter, and NaN terms are ignored as with fmaxf. (Packed pair additions and
+// three-input max/min give the same values but measured no faster on GB300:
+// every one of the 2n + 1 operations per edge still occupies an FP32 lane.)
 template <int NJ>
 __device__ __forceinline__ float linf_rec(const uint64_t (&own)[Rec<NJ>::NP], const float* rec) {
-  float a[2 * Rec<NJ>::NP];
+  float d = 0.f;
 #pragma unroll
   for (int p = 0; p < Rec<NJ>::NP; ++p) {
-    if (2 * p + 1 < NJ) {
-      unpack2(addx2(own[p], pack2(rec[2 * p], rec[2 * p + 1])), a[2 * p], a[2 * p + 1]);
-    } else {
-      float ol, oh;
-      unpack2(own[p], ol, oh);
-      a[2 * p] = ol + rec[2 * p];
-    }
+    float ol, oh;
+    unpack2(own[p], ol, oh);
+    const float a0 = fabsf(ol + rec[2 * p]);
+    d = p == 0 ? a0 : fmaxf(d, a0);
+    if (2 * p + 1 < NJ) d = fmaxf(d, fabsf(oh + rec[2 * p + 1]));
   }
-  if (NJ == 1) return fabsf(a[0]);
-  if (NJ == 2) return fmaxf(fabsf(a[0]), fabsf(a[1]));
-  float d = max3f(fabsf(a[0]), fabsf(a[1]), fabsf(a[2]));
-  int j = 3;
-#pragma unroll
-  for (; j + 1 < NJ; j += 2) d = max3f(d, fabsf(a[j]), fabsf(a[j + 1]));
-  if (j < NJ) d = fmaxf(d, fabsf(a[j]));
   return d;
 }
 
-constexpr int kDp2Threads = 256;
-constexpr int kDp2Tile = 32;
+constexpr int kDp2Tile = 32;  // predecessor nodes per tile of the deferred argmin
 
 // Records of one layer: node k at float offset k * NW + (k / 32) * 4. The
 // 16-byte skew per 32-node tile puts the same slot of different tiles on
@@ -248,181 +118,7 @@ __host__ __device__ __forceinline__ int rec_layer_floats(int NW, int Kp) {
 }
 __device__ __forceinline__ int rec_off(int NW, int k) { return k * NW + (k >> 5) * 4; }
 
-size_t dp2_smem_bytes(int nj, int Kp) {
-  const int NW = ((nj + 1 + 3) / 4) * 4;
-  return (size_t)2 * rec_layer_floats(NW, Kp) * 4  // records, two layers
-         + (size_t)2 * nj * Kp * 4    // raw layer staging, two slots
-         + (size_t)2 * Kp * 4         // node-cost staging, two slots
-         + 64;                        // barriers
-}
-
-template <int NJ, int R, class Src>
-__global__ void __launch_bounds__(kDp2Threads) dp2_forward_kernel(const __grid_constant__ Src src) {
-  constexpr int NW = Rec<NJ>::NW, NP = Rec<NJ>::NP;
-  const Req& rq = src.req(blockIdx.x);
-  const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
-  const int tid = threadIdx.x;
-  extern __shared__ __align__(128) float sm2[];
-  const int RL = rec_layer_floats(NW, Kp);
-  float* const rec = sm2;                                 // [2][RL] (records, skewed)
-  float* const stg = rec + 2 * (size_t)RL;                // [2][NJ][Kp]
-  float* const pst = stg + 2 * (size_t)NJ * Kp;           // [2][Kp]
-  uint64_t* const bars = reinterpret_cast<uint64_t*>(pst + 2 * (size_t)Kp);
-  __shared__ int timeout_flag;
-
-  const uint32_t layer_bytes = (uint32_t)(NJ * Kp * 4), pen_bytes = (uint32_t)(Kp * 4);
-  auto issue = [&](int L) {  // one thread: stage layer L into slot L & 1
-    const int sl = L & 1;
-    mbar_expect_tx(&bars[sl], layer_bytes + pen_bytes);
-    bulk_g2s(stg + (size_t)sl * NJ * Kp, rq.cand + (size_t)L * NJ * Kp, layer_bytes, &bars[sl]);
-    bulk_g2s(pst + (size_t)sl * Kp, rq.pen + (size_t)L * Kp, pen_bytes, &bars[sl]);
-  };
-  auto wait_layer = [&](int L) -> bool {
-    return mbar_wait_bounded(&bars[L & 1], (uint32_t)((L >> 1) & 1));
-  };
-
-  if (tid == 0) {
-    timeout_flag = 0;
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    issue(0);
-    if (T > 1) issue(1);
-  }
-  if (!wait_layer(0)) atomicExch(&timeout_flag, 1);
-  {
-    const float m0 = rq.pen_min[0];
-    for (int k = tid; k < Kp; k += kDp2Threads) {
-      float* rk = rec + rec_off(NW, k);
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) rk[j] = -stg[(size_t)j * Kp + k];
-      rk[NJ] = k < K ? pst[k] - m0 : CUDART_INF_F;
-#pragma unroll
-      for (int j = NJ + 1; j < NW; ++j) rk[j] = 0.f;
-    }
-  }
-  __syncthreads();
-  if (timeout_flag) {
-    raise_status(rq.status, CPP_ERR_TIMEOUT);
-    if (tid == 0 && T > 1) wait_layer(1);
-    return;
-  }
-  if (tid == 0 && T > 2) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    issue(2);
-  }
-
-  int kp[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) kp[r] = tid + r * kDp2Threads;
-  const int K4 = (K + 3) & ~3;
-  const int ntiles = (K4 + kDp2Tile - 1) / kDp2Tile;
-
-  for (int i = 0; i + 1 < T; ++i) {
-    const int L = i + 1;
-    if (!wait_layer(L)) atomicExch(&timeout_flag, 1);
-    const float* sq = stg + (size_t)(L & 1) * NJ * Kp;
-    const float* sp = pst + (size_t)(L & 1) * Kp;
-    const float* rc = rec + (size_t)(i & 1) * RL;
-    float* rn = rec + (size_t)(L & 1) * RL;
-    const float m1 = rq.pen_min[L];
-
-    uint64_t own[R][NP];
-    float rpen[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int k = kp[r] < Kp ? kp[r] : Kp - 1;
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const float a = sq[(size_t)(2 * p) * Kp + k];
-        const float b = (2 * p + 1 < NJ) ? sq[(size_t)(2 * p + 1) * Kp + k] : 0.f;
-        own[r][p] = pack2(a, b);
-      }
-      rpen[r] = kp[r] < K ? sp[kp[r]] - m1 : CUDART_INF_F;
-    }
-
-    float best[R];
-    int btile[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; btile[r] = -1; }
-
-#pragma unroll 1
-    for (int t = 0; t < ntiles; ++t) {
-      const int kb = t * kDp2Tile, ke = min(kb + kDp2Tile, K4);
-      float tb[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) tb[r] = CUDART_INF_F;
-#pragma unroll 2
-      for (int k = kb; k < ke; k += 2) {  // ke - kb is a multiple of 4
-        float r0[NW], r1[NW];
-#pragma unroll
-        for (int w = 0; w < NW; w += 4) {
-          const float4 v = *reinterpret_cast<const float4*>(rc + rec_off(NW, k) + w);
-          const float4 u = *reinterpret_cast<const float4*>(rc + rec_off(NW, k + 1) + w);
-          r0[w] = v.x; r0[w + 1] = v.y; r0[w + 2] = v.z; r0[w + 3] = v.w;
-          r1[w] = u.x; r1[w + 1] = u.y; r1[w + 2] = u.z; r1[w + 3] = u.w;
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          tb[r] = min3f(tb[r], r0[NJ] + linf_rec<NJ>(own[r], r0), r1[NJ] + linf_rec<NJ>(own[r], r1));
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (tb[r] < best[r]) { best[r] = tb[r]; btile[r] = t; }
-    }
-
-    // lowest index attaining the minimum, inside the first tile that reached it
-    uint16_t* bprow = rq.bp + (size_t)L * Kb;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      int arg = 0;
-      if (btile[r] >= 0) {
-        const int kb = btile[r] * kDp2Tile, ke = min(kb + kDp2Tile, K4);
-        for (int k = kb; k < ke; ++k) {
-          const float* rk = rc + rec_off(NW, k);
-          if (rk[NJ] + linf_rec<NJ>(own[r], rk) == best[r]) { arg = k; break; }
-        }
-      }
-      if (kp[r] < Kp) {
-        float v[NW];
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          float a, b;
-          unpack2(own[r][p], a, b);
-          v[2 * p] = -a;
-          if (2 * p + 1 < NJ) v[2 * p + 1] = -b;
-        }
-        v[NJ] = kp[r] < K ? best[r] + rpen[r] : CUDART_INF_F;
-#pragma unroll
-        for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
-        float4* dst = reinterpret_cast<float4*>(rn + rec_off(NW, kp[r]));
-#pragma unroll
-        for (int w = 0; w < NW / 4; ++w)
-          dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
-        bprow[kp[r]] = (uint16_t)arg;
-      }
-    }
-    __syncthreads();
-    if (timeout_flag) {
-      raise_status(rq.status, CPP_ERR_TIMEOUT);
-      if (tid == 0 && L + 1 < T) wait_layer(L + 1);
-      return;
-    }
-    if (tid == 0 && L + 2 < T) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(L + 2);
-    }
-  }
-  const float* rf = rec + (size_t)((T - 1) & 1) * RL;
-  for (int k = tid; k < Kp; k += kDp2Threads) rq.costT[k] = rf[rec_off(NW, k) + NJ];
-}
-
-// ------------------------------------------------------------------ forward sweep, split
-// Third form (the one used for n in {6, 7, 9}, Kp <= 1024). As the staged form,
-// plus:
+// ------------------------------------------------------------------ forward sweep
 //  * the 256 threads form two groups of 128 that own the same R successors per
 //    thread (Kp <= 128 R) and split the predecessor tiles in two contiguous
 //    halves, so each broadcast record feeds R edges; the halves' (minimum,
@@ -448,8 +144,11 @@ template <int NJ, int R>
 __device__ __forceinline__ void sweep_pair(const uint64_t (&own)[R][Rec<NJ>::NP], const float* r0,
                                            const float* r1, float (&tb)[R]) {
 #pragma unroll
-  for (int r = 0; r < R; ++r)
-    tb[r] = min3f(tb[r], r0[NJ] + linf_rec<NJ>(own[r], r0), r1[NJ] + linf_rec<NJ>(own[r], r1));
+  for (int r = 0; r < R; ++r) {
+    const float v0 = r0[NJ] + linf_rec<NJ>(own[r], r0);
+    const float v1 = r1[NJ] + linf_rec<NJ>(own[r], r1);
+    tb[r] = fminf(fminf(tb[r], v0), v1);
+  }
 }
 
 template <int NW>
@@ -646,6 +345,172 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __gri
   for (int k = tid; k < Kp; k += kDp3Threads) rq.costT[k] = rec[rec_off(NW, k) + NJ];
 }
 
+// ------------------------------------------------------------------ forward sweep, cluster
+// One request alone (the plain per-request path, or a batch too small to fill
+// the GPU) would leave most SMs idle with one CTA per request, and its T
+// dependent steps would each run on a single SM. This form spreads one request
+// over a thread-block cluster of CS CTAs (CS = ceil(Kp / 32R) <= 8):
+//  * CTA c owns successors [32 R c, 32 R (c + 1)); its 8 warps split the
+//    predecessors into 8 contiguous ranges and keep an exact argmin per edge
+//    (strict '<' in index order);
+//  * the 8 partial (minimum, index) pairs merge in warp order, the lower range
+//    winning ties, so the lowest index wins;
+//  * each new record [-q', C'] is stored into the record buffer of every CTA of
+//    the cluster (distributed shared memory), and a release/acquire cluster
+//    barrier ends the step. Records are double-buffered: a CTA that starts step
+//    i+1 writes only the buffer every CTA finished reading before the barrier
+//    of step i.
+constexpr int kDpcThreads = 256;
+constexpr int kDpcWarps = kDpcThreads / 32;
+
+size_t dpc_smem_bytes(int nj, int Kp, int R) {
+  const int NW = ((nj + 1 + 3) / 4) * 4;
+  return (size_t)2 * Kp * NW * 4 + (size_t)2 * kDpcWarps * 32 * R * 4;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t map_peer(uint32_t smem_addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_peer_v4(uint32_t addr, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int NJ, int R, class Src>
+__global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_constant__ Src src,
+                                                                   const int CS) {
+  constexpr int NW = Rec<NJ>::NW, NP = Rec<NJ>::NP, S = 32 * R;
+  const uint32_t crank = cluster_rank();
+  const Req& rq = src.req(blockIdx.x / CS);
+  const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  extern __shared__ __align__(16) float smc[];
+  float* const recb = smc;                               // [2][Kp][NW]
+  float* const xmin = recb + 2 * (size_t)Kp * NW;        // [warps][S]
+  int* const xarg = reinterpret_cast<int*>(xmin + kDpcWarps * S);
+  const float* __restrict__ cand = rq.cand;
+
+  // layer 0: every CTA builds all records locally
+  {
+    const float m0 = rq.pen_min[0];
+    for (int k = tid; k < Kp; k += kDpcThreads) {
+      float v[NW];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) v[j] = -cand[(size_t)j * Kp + k];
+      v[NJ] = k < K ? rq.pen[k] - m0 : CUDART_INF_F;
+#pragma unroll
+      for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
+      float4* dst = reinterpret_cast<float4*>(recb + (size_t)k * NW);
+#pragma unroll
+      for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
+    }
+  }
+  int kp[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) kp[r] = (int)crank * S + lane + 32 * r;
+  float qn[R][NJ];  // own successor values of the next layer
+  auto load_own = [&](int L) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = kp[r] < Kp ? kp[r] : Kp - 1;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) qn[r][j] = __ldg(cand + ((size_t)L * NJ + j) * Kp + k);
+    }
+  };
+  if (T > 1) load_own(1);
+  const int K4 = (K + 3) & ~3;
+  const int chunk = ((K4 + 2 * kDpcWarps - 1) / (2 * kDpcWarps)) * 2;
+  const int kb = min(warp * chunk, K4), ke = min(kb + chunk, K4);
+  __syncthreads();
+  cluster_barrier();
+
+  for (int i = 0; i + 1 < T; ++i) {
+    const int L = i + 1;
+    const float* cur = recb + (size_t)(i & 1) * Kp * NW;
+    float* nxt = recb + (size_t)(L & 1) * Kp * NW;
+    uint64_t own[R][NP];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        own[r][p] = pack2(qn[r][2 * p], (2 * p + 1 < NJ) ? qn[r][2 * p + 1] : 0.f);
+    float rpen[R];
+    const float m1 = rq.pen_min[L];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      rpen[r] = kp[r] < K ? __ldg(rq.pen + (size_t)L * Kp + kp[r]) - m1 : CUDART_INF_F;
+    if (L + 1 < T) load_own(L + 1);  // prefetch, consumed next step
+
+    float best[R];
+    int arg[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; arg[r] = 0; }
+    for (int k = kb; k < ke; k += 2) {
+      float r0[NW], r1[NW];
+      load_rec<NW>(cur + (size_t)k * NW, r0);
+      load_rec<NW>(cur + (size_t)(k + 1) * NW, r1);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float v0 = r0[NJ] + linf_rec<NJ>(own[r], r0);
+        const float v1 = r1[NJ] + linf_rec<NJ>(own[r], r1);
+        if (v0 < best[r]) { best[r] = v0; arg[r] = k; }
+        if (v1 < best[r]) { best[r] = v1; arg[r] = k + 1; }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      xmin[warp * S + lane + 32 * r] = best[r];
+      xarg[warp * S + lane + 32 * r] = arg[r];
+    }
+    __syncthreads();
+    // slot (warp r, lane): merge the 8 ranges in order, write the record everywhere
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (warp != r || kp[r] >= Kp) continue;
+      const int slot = lane + 32 * r;
+      float bv = xmin[slot];
+      int ba = xarg[slot];
+      for (int w = 1; w < kDpcWarps; ++w)
+        if (xmin[w * S + slot] < bv) { bv = xmin[w * S + slot]; ba = xarg[w * S + slot]; }
+      float v[NW];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        float a, b;
+        unpack2(own[r][p], a, b);
+        v[2 * p] = -a;
+        if (2 * p + 1 < NJ) v[2 * p + 1] = -b;
+      }
+      v[NJ] = kp[r] < K ? bv + rpen[r] : CUDART_INF_F;
+#pragma unroll
+      for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
+      const uint32_t base = smem_u32(nxt + (size_t)kp[r] * NW);
+      for (int c = 0; c < CS; ++c) {
+        const uint32_t peer = map_peer(base, (uint32_t)c);
+#pragma unroll
+        for (int w = 0; w < NW / 4; ++w)
+          st_peer_v4(peer + 16 * w, make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]));
+      }
+      rq.bp[(size_t)L * Kb + kp[r]] = (uint16_t)ba;
+    }
+    cluster_barrier();
+  }
+  const float* fin = recb + (size_t)((T - 1) & 1) * Kp * NW;
+  for (int k = (int)crank * S + tid; k < min(Kp, ((int)crank + 1) * S); k += kDpcThreads)
+    rq.costT[k] = fin[(size_t)k * NW + NJ];
+}
+
 // Any n and Kp that fit in shared memory: successor values are read back from
 // shared memory instead of registers.
 template <class Src>
@@ -788,22 +653,6 @@ static cudaError_t allow_smem(KernelT kernel, size_t bytes) {
 }
 
 template <int NJ, int R, class Src>
-static cudaError_t launch_fwd_r(const Src& s, int nreq, size_t smem, cudaStream_t st) {
-  cudaError_t e = allow_smem(dp_forward_kernel<NJ, R, Src>, smem);
-  if (e != cudaSuccess) return e;
-  dp_forward_kernel<NJ, R, Src><<<nreq, kDpThreads, smem, st>>>(s);
-  return cudaGetLastError();
-}
-
-template <int NJ, int R, class Src>
-static cudaError_t launch_fwd2_r(const Src& s, int nreq, size_t smem, cudaStream_t st) {
-  cudaError_t e = allow_smem(dp2_forward_kernel<NJ, R, Src>, smem);
-  if (e != cudaSuccess) return e;
-  dp2_forward_kernel<NJ, R, Src><<<nreq, kDp2Threads, smem, st>>>(s);
-  return cudaGetLastError();
-}
-
-template <int NJ, int R, class Src>
 static cudaError_t launch_fwd3_r(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
   const size_t smem = dp3_smem_bytes(NJ, max_Kp, R);
   cudaError_t e = allow_smem(dp3_forward_kernel<NJ, R, Src>, smem);
@@ -812,8 +661,48 @@ static cudaError_t launch_fwd3_r(const Src& s, int nreq, int max_Kp, cudaStream_
   return cudaGetLastError();
 }
 
+template <int NJ, int R, class Src>
+static cudaError_t launch_fwdc_r(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
+  const int CS = (max_Kp + 32 * R - 1) / (32 * R);
+  const size_t smem = dpc_smem_bytes(NJ, max_Kp, R);
+  cudaError_t e = allow_smem(dpc_forward_kernel<NJ, R, Src>, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nreq * CS));
+  cfg.blockDim = dim3(kDpcThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, dpc_forward_kernel<NJ, R, Src>, s, CS);
+}
+
+// Requests that one wave of clusters covers use the cluster form (lower latency);
+// larger batches use one CTA per request (higher throughput).
+static int sm_count() {
+  static int n = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
+  return n;
+}
+
 template <int NJ, class Src>
 static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
+  if (max_Kp > 64) {
+    const int Rc = max_Kp <= 512 ? 2 : 4;
+    const int CS = (max_Kp + 32 * Rc - 1) / (32 * Rc);
+    if (nreq * CS <= sm_count())
+      return Rc == 2 ? launch_fwdc_r<NJ, 2>(s, nreq, max_Kp, st)
+                     : launch_fwdc_r<NJ, 4>(s, nreq, max_Kp, st);
+  }
   const int R = (max_Kp + kDp3Group - 1) / kDp3Group;
   if (R <= 1) return launch_fwd3_r<NJ, 1>(s, nreq, max_Kp, st);
   if (R <= 2) return launch_fwd3_r<NJ, 2>(s, nreq, max_Kp, st);
@@ -831,7 +720,7 @@ static cudaError_t launch_dp_t(const Src& s, unsigned stages, int n, int nreq, i
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (stages & CPP_STAGE_DP_FORWARD) {
-    const bool fast = max_Kp <= 4 * kDpThreads;
+    const bool fast = max_Kp <= 1024;
     if (fast && n == 7) e = launch_fwd_nj<7>(s, nreq, max_Kp, st);
     else if (fast && n == 9) e = launch_fwd_nj<9>(s, nreq, max_Kp, st);
     else if (fast && n == 6) e = launch_fwd_nj<6>(s, nreq, max_Kp, st);

@@ -237,3 +237,37 @@ def test_dp_nonfinite_candidates_and_padding(n):
     ref = oracle.dp_f32(cand, pen, K)
     np.testing.assert_array_equal(got["sel"], ref["sel"])
     assert got["best"] == ref["best"]
+
+
+def test_large_batch_search_kernel_matches_oracle():
+    """A batch too large for one wave of clusters (40 requests x 8-CTA clusters > 152 SMs)
+    runs the one-CTA-per-request search; each result equals the oracle's FP32 search on the
+    GPU's node costs, including requests with non-finite candidates."""
+    tt = torch()
+    pbs = [problems.small(T=6 + (i % 5), K=400 + 16 * (i % 7), seed=3000 + i) for i in range(40)]
+    for i in (3, 17):
+        pbs[i].cand[2, 1, 5] = np.nan
+    _, cp = params_pair(tau_pos=0.05, tau_rot=math.radians(5.0), lm_iters=5)
+    robots = [cppflow.robot_from_arm(pb.arm) for pb in pbs]
+    keep, descs = [], []
+    for r, pb in enumerate(pbs):
+        T, n, Kp = pb.cand.shape
+        b = dict(cand=dev(pb.cand), targets=dev(pb.targets),
+                 sel=tt.empty(T, dtype=tt.int32, device="cuda:0"),
+                 q=tt.empty(T, n, dtype=tt.float32, device="cuda:0"),
+                 err=tt.empty(T, 2, dtype=tt.float64, device="cuda:0"),
+                 rep=tt.zeros(cppflow.REPORT_BYTES, dtype=tt.uint8, device="cuda:0"),
+                 best=tt.empty(1, dtype=tt.float32, device="cuda:0"))
+        keep.append(b)
+        descs.append(cppflow.PlanDesc(T, pb.K, Kp, r, b["cand"].data_ptr(), b["targets"].data_ptr(),
+                                      b["sel"].data_ptr(), b["q"].data_ptr(), b["err"].data_ptr(),
+                                      b["rep"].data_ptr(), b["best"].data_ptr()))
+    ws = tt.empty(cppflow.plan_batch_workspace_size(descs, robots), dtype=tt.uint8, device="cuda:0")
+    st = tt.zeros(len(descs), dtype=tt.int32, device="cuda:0")
+    cppflow.plan_batch(robots, cp, descs, ws, st)
+    tt.cuda.synchronize()
+    for r, pb in enumerate(pbs):
+        g = run_mask(robots[r], cp, pb.cand, pb.targets, pb.K)
+        ref = oracle.dp_f32(pb.cand, g.pen, pb.K)
+        np.testing.assert_array_equal(keep[r]["sel"].cpu().numpy(), ref["sel"])
+        assert float(keep[r]["best"].item()) == float(ref["best"])

@@ -39,7 +39,7 @@ def planar3_ik(a, x, y, phi):
 def test_lm_converges_to_both_planar_branches(orc):
     a = [0.4, 0.3, 0.15]
     robot = planar3(orc, a)
-    P = orc.make_params(lm_iters=40)
+    P = orc.make_params(lm_iters=40, freeze_cost=1e-20)  # run to FP64 convergence
     for _ in range(10):
         x, y = RNG.uniform(0.2, 0.5), RNG.uniform(-0.3, 0.3)
         phi = RNG.uniform(-1, 1)
