@@ -170,6 +170,109 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- serving mix
+def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_requests: int):
+    """Open-loop Poisson arrivals of the serving mix (T = floor(exp U(ln 50, ln 2000)),
+    K in {128, 256, 512, 1024}, 7-DoF arms), drawn with replacement from a pool of
+    distinct requests. Served: real-time submission to cpp_plan_submit, latency =
+    arrival -> completion. Plain: the same arrivals through one stream, one request at
+    a time (cpp_plan), as a FIFO queue fed by each request's measured GPU service
+    time. The first 10 % of requests are dropped as warm-up."""
+    n = 7
+    pool = []
+    P = cppflow.make_params()
+    P_wb = cppflow.make_params(lm_iters=30, lm_fp64=1, free_mask=synth.wrong_branch_free_mask(n))
+    arms = [synth.draw_arm(100 + k, n) for k in range(8)]
+    robots = [cppflow.robot_from_arm(a) for a in arms]
+
+    def draw(r):
+        w = synth.serving_request(r)
+        truth = synth.draw_truth(w.path_seed, n, w.T)
+        return w, truth, synth.draw_candidates(w.cand_seed, w.T, w.K, n, w.p_wb, w.p_out)
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        drawn = list(ex.map(draw, range(pool_size)))
+    for w, truth, d in drawn:
+        rob = robots[w.arm_seed - 100]
+        tgt = torch.empty(w.T, 7, dtype=torch.float64, device=dev)
+        cppflow.fk_pose_f64(rob, torch.from_numpy(truth).to(dev), tgt)
+        qwb = torch.empty(w.T, n, dtype=torch.float32, device=dev)
+        cppflow.lm_refine(rob, P_wb, torch.from_numpy(synth.wrong_branch_start(truth).astype(np.float32)).to(dev),
+                          tgt, qwb)
+        torch.cuda.synchronize()
+        arm = arms[w.arm_seed - 100]
+        cand = synth.assemble(truth, qwb.cpu().numpy().astype(np.float64), d, w.sigma, arm.lo, arm.hi)
+        pool.append((w, rob, torch.from_numpy(cand).pin_memory(), tgt.cpu().pin_memory(),
+                     torch.from_numpy(cand).to(dev), tgt))
+    # plain service time of every pool entry (cpp_plan alone, one stream)
+    st = torch.cuda.current_stream()
+    service = []
+    for w, rob, ch, th, cd, td in pool:
+        T, Kp = w.T, cd.shape[2]
+        ws = torch.empty(cppflow.plan_workspace_size(T, w.K, Kp, n), dtype=torch.uint8, device=dev)
+        bufs = (torch.empty(T, dtype=torch.int32, device=dev), torch.empty(1, device=dev),
+                torch.empty(T, n, device=dev), torch.empty(T, 2, dtype=torch.float64, device=dev),
+                torch.zeros(cppflow.REPORT_BYTES, dtype=torch.uint8, device=dev),
+                torch.zeros(1, dtype=torch.int32, device=dev))
+        times = []
+        for rep in range(3):
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record(st)
+            cppflow.plan(rob, P, cd, td, w.K, ws, *bufs, stream=st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        service.append(min(times[1:]) / 1000.0)
+    out = {}
+    rng_pick = synth.uniform(991, synth.S_MIX, 10 * max_requests)
+    for rate in rates:
+        count = int(min(max_requests, rate * seconds))
+        arr = synth.poisson_arrivals(rate, count, seed=int(rate))
+        pick = (rng_pick[:count] * len(pool)).astype(int)
+        # plain: FIFO single server with measured service times
+        done = 0.0
+        plat = []
+        for a, k in zip(arr, pick):
+            start = max(a, done)
+            done = start + service[k]
+            plat.append(done - a)
+        plain_span = done - arr[0]
+        # served: real-time open-loop submission
+        with cppflow.Server(P, device=dev.index or 0, hbm_budget=40 << 30, max_batch=512,
+                            max_inflight=2, pinned_bytes=64 << 20) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for a, k in zip(arr, pick):
+                now = time.perf_counter() - t0
+                if a > now:
+                    time.sleep(a - now)
+                w, rob, ch, th, cd, td = pool[k]
+                lag = max(0.0, time.perf_counter() - t0 - a)  # submitted after its arrival time
+                tickets.append((srv.submit(rob, ch.numpy(), th.numpy(), w.K, borrow=True), lag))
+            slat = []
+            valid = 0
+            for tk, lag in tickets:
+                stt, res = srv.wait(tk)
+                slat.append(lag + res["latency_ms"] / 1000.0)
+                valid += int(res["report"]["valid"])
+            span = time.perf_counter() - t0
+            ss = srv.stats()
+        drop = count // 10
+
+        def pct(v, q):
+            v = sorted(v[drop:])
+            return round(1000 * v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)], 3)
+
+        out[str(rate)] = {
+            "requests": count,
+            "served": {"plans_per_s": round(count / span, 1), "p50_ms": pct(slat, 0.5),
+                       "p99_ms": pct(slat, 0.99), "valid": f"{valid}/{count}",
+                       "mean_batch": round(ss["sum_batch"] / max(1, ss["batches"]), 1)},
+            "plain": {"plans_per_s": round(count / plain_span, 1), "p50_ms": pct(plat, 0.5),
+                      "p99_ms": pct(plat, 0.99)}}
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_cuda(args, rank: int, world: int, dist):
     import torch
@@ -355,6 +458,10 @@ def run_cuda(args, rank: int, world: int, dist):
             "kernel_ms": round(statistics.mean(dp_ms), 4),
             "edges_per_s": round(edges / dp_s, 1)}
 
+    mix = None
+    if args.serve_rates and rank == 0:
+        mix = serving_mix(cppflow, torch, dev, [float(x) for x in args.serve_rates.split(",")],
+                          args.mix_pool, args.mix_seconds, args.mix_max)
     line = {"metric": METRIC, "value": round(value, 3), "unit": "plans/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -372,6 +479,10 @@ def run_cuda(args, rank: int, world: int, dist):
             "dev_status_nonzero": int((st != 0).sum()),
             "roofline": roof, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches_per_step * args.steps}
+    if mix is not None:
+        line["serving_mix"] = {"workload": "serving mix: T = floor(exp U(ln 50, ln 2000)), "
+                                           "K in {128, 256, 512, 1024}, 7-DoF, Poisson arrivals",
+                               "rates": mix}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(rank)
     if rank == 0:
@@ -387,6 +498,11 @@ def main():
     ap.add_argument("--batch", type=int, default=304)
     ap.add_argument("--plain", type=int, default=32, help="requests timed on the plain path")
     ap.add_argument("--serve-batch", type=int, default=152, help="server: requests per launch")
+    ap.add_argument("--serve-rates", default="1000", help="Poisson rates (req/s) of the serving "
+                    "mix, comma separated; empty to skip")
+    ap.add_argument("--mix-pool", type=int, default=48, help="distinct requests in the mix pool")
+    ap.add_argument("--mix-seconds", type=float, default=2.0)
+    ap.add_argument("--mix-max", type=int, default=3000)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     args = ap.parse_args()
