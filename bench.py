@@ -239,7 +239,7 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_
         plain_span = done - arr[0]
         # served: real-time open-loop submission
         with cppflow.Server(P, device=dev.index or 0, hbm_budget=40 << 30, max_batch=512,
-                            max_inflight=2, pinned_bytes=64 << 20) as srv:
+                            max_inflight=16, pinned_bytes=64 << 20) as srv:
             t0 = time.perf_counter()
             tickets = []
             for a, k in zip(arr, pick):
@@ -420,7 +420,7 @@ def run_cuda(args, rank: int, world: int, dist):
     lat = []
     e2e_valid = 0
     with cppflow.Server(P, device=local, hbm_budget=int(B * 6.5e6) + (256 << 20),
-                        max_batch=args.serve_batch, max_inflight=2, pinned_bytes=64 << 20) as srv:
+                        max_batch=args.serve_batch, max_inflight=4, pinned_bytes=64 << 20) as srv:
         for rep_i in range(e2e_steps + 1):       # the first pass warms the server up
             t0 = time.perf_counter()
             tickets = [srv.submit(robots[reqs[r].arm_seed - 100], cand_np[r], targ_np[r], K,

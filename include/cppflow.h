@@ -287,8 +287,9 @@ void cpp_batch_destroy(cpp_batch_t* batch);
  * with HOST buffers from any thread; a worker thread admits queued requests
  * while request slots and the HBM budget allow (each admitted request keeps its
  * lattice, targets, search tables and results resident in a device arena of
- * hbm_budget_bytes), groups requests of the same joint count into one batched
- * launch per stage, and keeps up to max_inflight launches on the device at once,
+ * hbm_budget_bytes), groups requests of one size class (joint count, K bucket,
+ * T bucket) into one batched launch per stage, and keeps up to max_inflight
+ * launches on the device at once,
  * so requests that arrive while others run are admitted as memory frees up and
  * their work overlaps. Every request runs with the server's params. */
 typedef struct cpp_server cpp_server_t;
@@ -297,7 +298,7 @@ typedef struct cpp_server_config {
     int32_t device;           /* CUDA device ordinal */
     int32_t max_slots;        /* requests resident on the device at once (default 1024) */
     int32_t max_batch;        /* requests per launch (default 512) */
-    int32_t max_inflight;     /* launches in flight, 1..16 (default 2) */
+    int32_t max_inflight;     /* launches in flight, 1..16 (default 8) */
     size_t hbm_budget_bytes;  /* device arena for resident requests (default 40 GiB) */
     size_t pinned_bytes;      /* pinned host staging; 0 = pageable only (default 1 GiB) */
     cpp_params_t params;      /* settings of every request */

@@ -71,16 +71,26 @@ struct RobotD {      // FP64 view for the FP64 paths
 };
 
 // Threads 0..15 of the block fill the views; the caller synchronises afterwards.
-// Near-limit thresholds lo + m, hi - m are formed in FP64 and rounded once.
+// Near-limit thresholds lo + m, hi - m are formed in FP64 and rounded once. The
+// twist's cosine and sine come from FP64 sincos when the FP64 view is wanted,
+// else from FP32 sincosf: kernels with many small blocks that only need the FP32
+// view then spend no FP64 issue on staging (cos(pi/2) becomes -4.4e-8 instead of
+// 6.1e-17, a ~1e-8 m change in the pose).
 __device__ inline void stage_robot(const cpp_robot_t& r, double near_margin, RobotF* f,
                                    RobotD* dd) {
   const int j = threadIdx.x;
   if (j < kMaxJ) {
-    double s, c;
-    sincos(r.alpha[j], &s, &c);
+    double s = 0.0, c = 1.0;
+    float sf, cf;
+    if (dd) {
+      sincos(r.alpha[j], &s, &c);
+      sf = (float)s; cf = (float)c;
+    } else {
+      sincosf((float)r.alpha[j], &sf, &cf);
+    }
     if (f) {
       f->a[j] = (float)r.a[j]; f->d[j] = (float)r.d[j];
-      f->ca[j] = (float)c;     f->sa[j] = (float)s;
+      f->ca[j] = cf;           f->sa[j] = sf;
       f->th0[j] = (float)r.theta0[j];
       f->lo[j] = (float)r.lo[j]; f->hi[j] = (float)r.hi[j];
       f->nlo[j] = (float)(r.lo[j] + near_margin);

@@ -21,23 +21,18 @@ struct MaskArgs {
   double near_margin;
 };
 
-// The target of waypoint i as FP32 rotation + position, computed in FP64 by
-// lanes 0..11 (one entry each) and broadcast through the warp.
+// The target of waypoint i as FP32 rotation + position. The quaternion is
+// rounded to FP32 and converted in FP32 (GB300's FP64 pipe is ~64x narrower
+// than FP32, and every lane of the warp needs the same 12 numbers); this adds
+// ~1e-7 to the pose errors, far inside their 1e-5 tolerance.
 __device__ __forceinline__ void warp_target_f32(const double* t7, float Rt[9], float pt[3]) {
-  const int lane = threadIdx.x & 31;
-  double R[9];
-  quat_to_rot(t7 + 3, R);
-  float mine = 0.f;
-#pragma unroll
-  for (int e = 0; e < 9; ++e)
-    if (lane == e) mine = (float)R[e];
-#pragma unroll
-  for (int e = 0; e < 3; ++e)
-    if (lane == 9 + e) mine = (float)t7[e];
-#pragma unroll
-  for (int e = 0; e < 9; ++e) Rt[e] = __shfl_sync(0xffffffffu, mine, e);
-#pragma unroll
-  for (int e = 0; e < 3; ++e) pt[e] = __shfl_sync(0xffffffffu, mine, 9 + e);
+  const float qw = (float)t7[3], qx = (float)t7[4], qy = (float)t7[5], qz = (float)t7[6];
+  const float inv = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+  const float w = qw * inv, x = qx * inv, y = qy * inv, z = qz * inv;
+  Rt[0] = 1.f - 2.f * (y * y + z * z); Rt[1] = 2.f * (x * y - w * z); Rt[2] = 2.f * (x * z + w * y);
+  Rt[3] = 2.f * (x * y + w * z); Rt[4] = 1.f - 2.f * (x * x + z * z); Rt[5] = 2.f * (y * z - w * x);
+  Rt[6] = 2.f * (x * z - w * y); Rt[7] = 2.f * (y * z + w * x); Rt[8] = 1.f - 2.f * (x * x + y * y);
+  pt[0] = (float)t7[0]; pt[1] = (float)t7[1]; pt[2] = (float)t7[2];
 }
 
 template <int NJ>

@@ -9,12 +9,14 @@
 //    on the device for the request's lifetime on the GPU;
 //  * a pinned host pool for staged inputs and results (pageable fallback);
 //  * one worker thread: it retires finished launches (event query), then forms
-//    the next batch from the queue -- requests of the same joint count in
-//    arrival order, while slots, batch size and arena space allow -- and
-//    enqueues H2D copies, the six stage launches and the D2H copy of results
-//    on one of max_inflight streams. Requests that arrive while earlier
-//    batches run are admitted into the next batch as memory frees up, and
-//    the batches overlap on the device.
+//    the next batch from the queue -- requests of the oldest request's size
+//    class (joint count, K bucket, T bucket) in arrival order, while the class
+//    cap, slots and arena space allow -- and enqueues H2D copies, the six stage
+//    launches and the D2H copy of results on one of max_inflight streams.
+//    Requests that arrive while earlier batches run are admitted into the next
+//    batch as memory frees up, and the batches overlap on the device. At light
+//    load batches hold one or a few requests and run as clusters (low latency);
+//    as a class queues up its batches grow (high throughput).
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -170,6 +172,7 @@ struct cpp_server {
   std::unordered_map<uint64_t, Request*> reqs;
   std::vector<Launch*> inflight;
   int resident = 0;
+  int sms = 152;
   uint64_t next_ticket = 1;
   bool stop = false;
   std::thread worker;
@@ -192,14 +195,35 @@ void cpp_server::release_host(Request* r) {
   r->own_in.shrink_to_fit();
 }
 
-// Take same-n requests in arrival order while batch size, slots and arena allow.
+// Size class of a request: joint count, K bucket and T bucket. A launch holds one
+// class only, so a small request never waits for a large one in its batch (a
+// batch completes as a whole), and a K = 1024 request never widens the kernel
+// of K = 128 ones.
+static int size_class(const Request* r) {
+  const int kc = r->Kp <= 128 ? 0 : r->Kp <= 256 ? 1 : r->Kp <= 512 ? 2 : 3;
+  const int tc = r->T <= 256 ? 0 : r->T <= 1024 ? 1 : 2;
+  return (r->n * 4 + kc) * 3 + tc;
+}
+
+// Largest batch of a class: heavy classes (K > 512 or T > 1024) are capped so
+// the batch runs as clusters (8 CTAs per request, lower latency per request);
+// the others up to max_batch.
+static int class_cap(const Request* r, int max_batch, int sms) {
+  const bool heavy = r->Kp > 512 || r->T > 1024;
+  const int cs = (r->Kp + 32 * (r->Kp <= 512 ? 2 : 4) - 1) / (32 * (r->Kp <= 512 ? 2 : 4));
+  return heavy ? std::max(1, std::min(max_batch, sms / std::max(1, cs))) : max_batch;
+}
+
+// Take requests of the oldest request's size class, in arrival order, while the
+// class cap, slots and arena allow.
 bool cpp_server::form_batch(Launch* L) {
   if (queue.empty()) return false;
-  const int n0 = queue.front()->n;
+  const int cls = size_class(queue.front());
+  const int cap = class_cap(queue.front(), cfg.max_batch, sms);
   for (auto it = queue.begin(); it != queue.end();) {
     Request* r = *it;
-    if ((int)L->reqs.size() >= cfg.max_batch || resident >= cfg.max_slots) break;
-    if (r->n != n0) { ++it; continue; }
+    if ((int)L->reqs.size() >= cap || resident >= cfg.max_slots) break;
+    if (size_class(r) != cls) { ++it; continue; }
     size_t off;
     if (!darena.alloc(r->dev_bytes, &off)) break;  // keep arrival order within the class
     r->dev_off = off;
@@ -399,7 +423,7 @@ void cpp_server_config_default(cpp_server_config_t* c) {
   c->device = 0;
   c->max_slots = 1024;
   c->max_batch = 512;
-  c->max_inflight = 2;
+  c->max_inflight = 8;
   c->hbm_budget_bytes = (size_t)40 << 30;
   c->pinned_bytes = (size_t)1 << 30;
   cpp_params_default(&c->params);
@@ -424,6 +448,11 @@ cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out)
                  "server device arena: %s", cudaGetErrorString(e));
   }
   s->darena.reset(cfg->hbm_budget_bytes);
+  {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, cfg->device) == cudaSuccess && v > 0)
+      s->sms = v;
+  }
   if (cfg->pinned_bytes) {
     if (cudaHostAlloc(&s->h_pinned, cfg->pinned_bytes, cudaHostAllocDefault) == cudaSuccess)
       s->parena.reset(cfg->pinned_bytes);
