@@ -79,6 +79,8 @@ def lib():
             "orc_mask": (None, [P, P, P, P, C.c_int, C.c_int, C.c_int, P, P, P]),
             "orc_dp_f32": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]),
             "orc_dp_f64": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]),
+            "orc_dp_f32_ex": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]),
+            "orc_path_mjac_f32": (C.c_float, [P, C.c_int, C.c_int, C.c_int, P]),
             "orc_log_rot": (None, [P, P]),
             "orc_jacobian": (None, [P, P, P]),
             "orc_residual": (None, [P, P, P, P]),
@@ -195,7 +197,8 @@ def mask(robot: Robot, params: Params, cand: np.ndarray, targets: np.ndarray, K:
 
 
 # ---------------------------------------------------------------- §III-B search
-def dp_f32(cand: np.ndarray, pen: np.ndarray, K: int):
+def dp_f32(cand: np.ndarray, pen: np.ndarray, K: int, objective: int = 0):
+    """objective 0: summed per-step L-inf jump; 1: the paper's min-max (mjac) objective."""
     cand = np.ascontiguousarray(cand, dtype=np.float32)
     T, n, Kp = cand.shape
     pen = np.ascontiguousarray(pen, dtype=np.float32).reshape(T, Kp)
@@ -203,8 +206,16 @@ def dp_f32(cand: np.ndarray, pen: np.ndarray, K: int):
     best = np.zeros(1, np.float32)
     cT = np.zeros(Kp, np.float32)
     bp = np.zeros((T, Kp), np.uint16)
-    st = lib().orc_dp_f32(_p(cand), _p(pen), T, K, Kp, n, _p(sel), _p(best), _p(cT), _p(bp))
+    st = lib().orc_dp_f32_ex(_p(cand), _p(pen), T, K, Kp, n, objective, _p(sel), _p(best),
+                             _p(cT), _p(bp))
     return dict(status=st, sel=sel, best=best[0], cost_T=cT, bp=bp)
+
+
+def path_mjac_f32(cand: np.ndarray, sel) -> float:
+    cand = np.ascontiguousarray(cand, dtype=np.float32)
+    T, n, Kp = cand.shape
+    sel = np.ascontiguousarray(sel, dtype=np.int32)
+    return float(lib().orc_path_mjac_f32(_p(cand), T, Kp, n, _p(sel)))
 
 
 def dp_f64(cand: np.ndarray, pen: np.ndarray, K: int):

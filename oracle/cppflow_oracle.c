@@ -266,8 +266,16 @@ static float layer_min_f32(const float* pen_i, int K) {
     return isinf(m) ? 0.0f : m;
 }
 
-int orc_dp_f32(const float* cand, const float* pen, int T, int K, int Kp, int n,
-               int32_t* sel, float* best_cost, float* cost_T, uint16_t* bp_out) {
+/* Objective 1 is the paper's own: "the cost at each node is the minimum mjac
+ * achievable if the node is included" -- a bottleneck (min-max) path. With the
+ * node costs it reads
+ *   C_0[k] = r_0[k],  C_{i+1}[k'] = fmaxf( min_k fmaxf(C_i[k], d(k, k')), r_{i+1}[k'] ),
+ * i.e. a path costs max(largest per-step L-inf jump, largest relative node cost);
+ * a node cost of 10 exceeds any revolute jump (pi), as the paper intends. max
+ * and min are exact, so this objective involves no rounding at all. */
+int orc_dp_f32_ex(const float* cand, const float* pen, int T, int K, int Kp, int n,
+                  int objective, int32_t* sel, float* best_cost, float* cost_T,
+                  uint16_t* bp_out) {
     float* C = (float*)malloc(sizeof(float) * (size_t)Kp);
     float* Cn = (float*)malloc(sizeof(float) * (size_t)Kp);
     uint16_t* bp = (uint16_t*)calloc((size_t)T * Kp, sizeof(uint16_t));
@@ -285,10 +293,11 @@ int orc_dp_f32(const float* cand, const float* pen, int T, int K, int Kp, int n,
                 float d = fabsf(qb[kp] - qa[k]);
                 for (int j = 1; j < n; ++j)
                     d = fmaxf(d, fabsf(qb[(size_t)j * Kp + kp] - qa[(size_t)j * Kp + k]));
-                float v = C[k] + d;
+                float v = objective ? fmaxf(C[k], d) : C[k] + d;
                 if (v < best) { best = v; arg = k; }
             }
-            Cn[kp] = best + (pen[(size_t)(i + 1) * Kp + kp] - m1);
+            const float r = pen[(size_t)(i + 1) * Kp + kp] - m1;
+            Cn[kp] = objective ? fmaxf(best, r) : best + r;
             bp[(size_t)(i + 1) * Kp + kp] = (uint16_t)arg;
         }
         float* t = C; C = Cn; Cn = t;
@@ -304,6 +313,21 @@ int orc_dp_f32(const float* cand, const float* pen, int T, int K, int Kp, int n,
     if (bp_out) memcpy(bp_out, bp, sizeof(uint16_t) * (size_t)T * Kp);
     free(C); free(Cn); free(bp);
     return isinf(best) ? 3 : 0;
+}
+
+int orc_dp_f32(const float* cand, const float* pen, int T, int K, int Kp, int n,
+               int32_t* sel, float* best_cost, float* cost_T, uint16_t* bp_out) {
+    return orc_dp_f32_ex(cand, pen, T, K, Kp, n, 0, sel, best_cost, cost_T, bp_out);
+}
+
+/* mjac of a selection (§III-B): max over steps and joints of |q_{i+1} - q_i|, in FP32. */
+float orc_path_mjac_f32(const float* cand, int T, int Kp, int n, const int32_t* sel) {
+    float m = 0.0f;
+    for (int i = 0; i + 1 < T; ++i)
+        for (int j = 0; j < n; ++j)
+            m = fmaxf(m, fabsf(cand[((size_t)(i + 1) * n + j) * Kp + sel[i + 1]] -
+                               cand[((size_t)i * n + j) * Kp + sel[i]]));
+    return m;
 }
 
 /* The same recurrence in FP64 (used for the error report, not for indices),

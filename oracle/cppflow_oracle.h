@@ -82,6 +82,10 @@ void orc_mask(const orc_robot* r, const orc_params* P, const float* cand /*[T][n
 int orc_dp_f32(const float* cand, const float* pen, int T, int K, int Kp, int n,
                int32_t* sel, float* best_cost, float* cost_T /*[Kp] or 0*/,
                uint16_t* bp /*[T][Kp] or 0*/);
+int orc_dp_f32_ex(const float* cand, const float* pen, int T, int K, int Kp, int n,
+                  int objective /* 0 sum, 1 min-max */, int32_t* sel, float* best_cost,
+                  float* cost_T, uint16_t* bp);
+float orc_path_mjac_f32(const float* cand, int T, int Kp, int n, const int32_t* sel);
 int orc_dp_f64(const float* cand, const float* pen, int T, int K, int Kp, int n,
                int32_t* sel, double* best_cost);
 

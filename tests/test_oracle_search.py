@@ -228,3 +228,59 @@ def test_dp_f64_twin_agrees_when_separated(orc):
     b = orc.dp_f64(cand, pen, K)
     assert abs(a["best"] - b["best"]) < 1e-4
     np.testing.assert_array_equal(a["sel"], b["sel"])
+
+
+# --------------------------------------------------------------------- min-max objective (§III-B)
+def brute_force_minmax(cand, pen, K):
+    """All K^T selections under the paper's objective: a path costs the max of its per-step
+    L-inf jumps and of its relative node costs (max/min are exact: no rounding)."""
+    T = cand.shape[0]
+    r = rel_pen(pen, K)
+    costs = {}
+    for path in itertools.product(range(K), repeat=T):
+        c = r[0, path[0]]
+        for i in range(1, T):
+            c = max(c, linf32(cand[i - 1, :, path[i - 1]], cand[i, :, path[i]]), r[i, path[i]])
+        costs[path] = f32(c)
+    return min(costs.values()), costs
+
+
+@pytest.mark.parametrize("T,K,n,seed", [(3, 4, 3, 0), (5, 3, 7, 1), (6, 4, 2, 2), (4, 4, 9, 3)])
+def test_minmax_dp_equals_brute_force(orc, T, K, n, seed):
+    rng = np.random.default_rng(100 + seed)
+    cand = np.zeros((T, n, 32), np.float32)
+    cand[:, :, :K] = rng.normal(0, 0.4, (T, n, K)).astype(np.float32)
+    pen = np.full((T, 32), np.inf, np.float32)
+    pen[:, :K] = rng.choice([0.0, 0.0, 10.0, 100.0], (T, K)).astype(np.float32)
+    out = orc.dp_f32(cand, pen, K, objective=1)
+    best, costs = brute_force_minmax(cand, pen, K)
+    assert out["status"] == 0
+    assert out["best"] == best
+    assert costs[tuple(out["sel"])] == best  # the backtracked path attains it
+
+
+def test_minmax_closed_forms_and_bottleneck(orc):
+    rng = np.random.default_rng(8)
+    T, n = 12, 7
+    # K = 1: the cost is the largest jump of the only path
+    cand = np.zeros((T, n, 32), np.float32)
+    cand[:, :, 0] = rng.normal(0, 1, (T, n)).astype(np.float32)
+    pen = np.full((T, 32), np.inf, np.float32)
+    pen[:, 0] = 0.0
+    out = orc.dp_f32(cand, pen, 1, objective=1)
+    assert out["best"] == f32(max(linf32(cand[i - 1, :, 0], cand[i, :, 0]) for i in range(1, T)))
+    # with no node costs the min-max path's mjac is the smallest of all paths', so at most
+    # the min-sum path's; and the reported cost is that path's mjac
+    K = 20
+    cand = rng.normal(0, 0.3, (T, n, 32)).astype(np.float32)
+    pen = np.zeros((T, 32), np.float32)
+    pen[:, K:] = np.inf
+    mm = orc.dp_f32(cand, pen, K, objective=1)
+    ms = orc.dp_f32(cand, pen, K, objective=0)
+    assert mm["best"] == f32(orc.path_mjac_f32(cand, mm["sel"]))
+    assert orc.path_mjac_f32(cand, mm["sel"]) <= orc.path_mjac_f32(cand, ms["sel"])
+    # a node cost of 10 (near a limit) outweighs any revolute jump
+    pen[5, :K] = 10.0
+    pen[5, 3] = 0.0
+    mm2 = orc.dp_f32(cand, pen, K, objective=1)
+    assert mm2["sel"][5] == 3 and mm2["best"] < 10.0
