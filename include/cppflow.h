@@ -104,8 +104,11 @@ typedef struct cpp_params {
     uint32_t free_mask;  /* bit j set: LM may move joint j (default all) */
     int32_t lm_fp64;     /* 0: FP32 FK/Jacobian + FP64 normal equations and Cholesky;
                             1: everything in FP64 (for near-singular chains) */
-    int32_t reserved;
+    int32_t dp_objective; /* CPP_DP_SUM (default) or CPP_DP_MINMAX, see cpp_dp_search_ex */
 } cpp_params_t;
+
+#define CPP_DP_SUM 0     /* minimise the summed per-step L-inf joint jump */
+#define CPP_DP_MINMAX 1  /* the paper's objective: minimise the largest per-step jump (mjac) */
 
 /* Trajectory report of cpp_check (device or host struct, FP64). */
 typedef struct cpp_report {
@@ -151,6 +154,18 @@ cpp_status cpp_mask(const cpp_robot_t* robot, const cpp_params_t* params, const 
                     const double* targets, int32_t T, int32_t K, int32_t Kp, uint8_t* mask,
                     float* pen, float* err, int32_t* dev_status, cpp_stream_t stream);
 
+/* cpp_mask on the candidate lanes [k_begin, K) only (k_begin a multiple of 4); the
+ * lanes below k_begin keep the mask and cost they already have. This is how a
+ * re-search reuses a resident lattice: allocate Kp for the largest K expected,
+ * mask and search the first K0 lanes, and when the search path's mjac is too
+ * large (§III-B: 12 deg) write more candidates into lanes [K0, K1), mask just
+ * those, and search again with K = K1 -- "collision and joint limit checks
+ * performed on the initial plans are retained". */
+cpp_status cpp_mask_range(const cpp_robot_t* robot, const cpp_params_t* params,
+                          const float* cand, const double* targets, int32_t T, int32_t K,
+                          int32_t Kp, int32_t k_begin, uint8_t* mask, float* pen, float* err,
+                          int32_t* dev_status, cpp_stream_t stream);
+
 /* ------------------------------------------------------------------ search (§III-B)
  * Dynamic programme over the layered graph whose nodes are the K candidates of
  * each waypoint and whose edges join every node of step i to every node of
@@ -167,6 +182,20 @@ cpp_status cpp_mask(const cpp_robot_t* robot, const cpp_params_t* params, const 
  * INVALID_ARG: T < 1, K < 1, K > 65535, Kp < K, Kp % 4 != 0, n < 1, n > 16,
  * workspace too small or misaligned. */
 size_t cpp_dp_workspace_size(int32_t T, int32_t Kp);
+
+/* The search with a choice of objective (§III-B). CPP_DP_SUM is cpp_dp_search.
+ * CPP_DP_MINMAX is the paper's own cost, "the minimum mjac achievable if the node
+ * is included": C_0 = r_0, C_{i+1}[k'] = max(min_k max(C_i[k], d(k, k')), r_{i+1}[k']),
+ * so a path costs the larger of its largest per-step L-inf jump and its largest
+ * relative node cost (a near-limit cost of 10 outweighs any revolute jump); max
+ * and min are exact, so it involves no rounding. search_mjac [1] FP32 (or NULL)
+ * receives the mjac of the selected path, max over steps and joints of |dq|, for
+ * the paper's re-search test (more candidates when it exceeds 12 deg). Other
+ * arguments as cpp_dp_search; INVALID_ARG for another objective. */
+cpp_status cpp_dp_search_ex(const float* cand, const float* pen, int32_t T, int32_t K,
+                            int32_t Kp, int32_t n, int32_t objective, void* workspace,
+                            size_t ws_bytes, int32_t* sel, float* best_cost, float* q_seed,
+                            float* search_mjac, int32_t* dev_status, cpp_stream_t stream);
 cpp_status cpp_dp_search(const float* cand, const float* pen, int32_t T, int32_t K,
                          int32_t Kp, int32_t n, void* workspace, size_t ws_bytes,
                          int32_t* sel, float* best_cost, float* q_seed, int32_t* dev_status,

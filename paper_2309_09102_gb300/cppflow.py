@@ -22,6 +22,7 @@ MASK_OUT, MASK_NEAR, MASK_POSE, MASK_NONFINITE, MASK_PAD = 1, 2, 4, 8, 16
 STAGE_MASK, STAGE_LAYER_MIN, STAGE_DP_FORWARD, STAGE_BACKTRACK, STAGE_LM, STAGE_CHECK = \
     1, 2, 4, 8, 16, 32
 STAGE_ALL = 63
+DP_SUM, DP_MINMAX = 0, 1
 
 
 class CppflowError(RuntimeError):
@@ -40,7 +41,7 @@ class Params(C.Structure):
         "tau_pos", "tau_rot", "near_margin", "pen_limit", "pen_pose", "jump_max", "lambda0",
         "lambda_up", "lambda_down", "lambda_min", "lambda_max", "freeze_step", "freeze_cost")] + [
         ("lm_iters", C.c_int32), ("free_mask", C.c_uint32), ("lm_fp64", C.c_int32),
-        ("reserved", C.c_int32)]
+        ("dp_objective", C.c_int32)]
 
 
 class Report(C.Structure):
@@ -99,6 +100,10 @@ _SIGS = {
     "cpp_fk_pose_f64": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
     "cpp_mask": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P]),
     "cpp_dp_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
+    "cpp_mask_range": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P,
+                                 _P, _P, _P]),
+    "cpp_dp_search_ex": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P,
+                                   C.c_size_t, _P, _P, _P, _P, _P, _P]),
     "cpp_dp_search": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, C.c_size_t,
                                 _P, _P, _P, _P, _P]),
     "cpp_lm_refine": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, _P, _P]),
@@ -216,6 +221,15 @@ def mask(robot: Robot, params: Params, cand, targets, K: int, mask_out, pen, err
                           stream_handle(stream)), "cpp_mask")
 
 
+def mask_range(robot: Robot, params: Params, cand, targets, K: int, k_begin: int, mask_out, pen,
+               err=None, dev_status=None, stream=None):
+    """cpp_mask on lanes [k_begin, K) only (appended candidates)."""
+    T, n, Kp = cand.shape
+    _check(lib().cpp_mask_range(C.byref(robot), C.byref(params), ptr(cand), ptr(targets), T, K, Kp,
+                                k_begin, ptr(mask_out), ptr(pen), ptr(err), ptr(dev_status),
+                                stream_handle(stream)), "cpp_mask_range")
+
+
 def dp_workspace_size(T: int, Kp: int) -> int:
     return lib().cpp_dp_workspace_size(T, Kp)
 
@@ -227,6 +241,15 @@ def dp_search(cand, pen, K: int, workspace, sel, best_cost, q_seed=None, dev_sta
     _check(lib().cpp_dp_search(ptr(cand), ptr(pen), T, K, Kp, n, ptr(workspace), nbytes,
                                ptr(sel), ptr(best_cost), ptr(q_seed), ptr(dev_status),
                                stream_handle(stream)), "cpp_dp_search")
+
+
+def dp_search_ex(cand, pen, K: int, objective: int, workspace, sel, best_cost, q_seed=None,
+                 search_mjac=None, dev_status=None, stream=None):
+    T, n, Kp = cand.shape
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().cpp_dp_search_ex(ptr(cand), ptr(pen), T, K, Kp, n, objective, ptr(workspace),
+                                  nbytes, ptr(sel), ptr(best_cost), ptr(q_seed), ptr(search_mjac),
+                                  ptr(dev_status), stream_handle(stream)), "cpp_dp_search_ex")
 
 
 def lm_refine(robot: Robot, params: Params, q_in, targets, q_out, pose_err=None, dev_status=None,

@@ -61,6 +61,9 @@ cpp_status check_params(const cpp_params_t* p) {
       p->lambda_up < 1 || p->lambda_down < 1)
     return fail(CPP_ERR_INVALID_ARG, "invalid damping schedule");
   if (p->lm_iters < 0 || p->lm_iters > 100000) return fail(CPP_ERR_INVALID_ARG, "lm_iters out of range");
+  if (p->dp_objective != CPP_DP_SUM && p->dp_objective != CPP_DP_MINMAX)
+    return fail(CPP_ERR_INVALID_ARG, "dp_objective %d is neither CPP_DP_SUM nor CPP_DP_MINMAX",
+                p->dp_objective);
   return CPP_OK;
 }
 
@@ -128,7 +131,7 @@ void cpp_params_default(cpp_params_t* p) {
   p->lm_iters = 20;
   p->free_mask = 0xFFFFFFFFu;
   p->lm_fp64 = 0;
-  p->reserved = 0;
+  p->dp_objective = CPP_DP_SUM;
 }
 
 cpp_status cpp_fk_batch(const cpp_robot_t* robot, const float* q, int64_t N, float* R, float* p,
@@ -147,22 +150,39 @@ cpp_status cpp_fk_pose_f64(const cpp_robot_t* robot, const double* q, int64_t N,
   return cuda_status(launch_fk_pose64(*robot, q, N, pose, (cudaStream_t)stream), "cpp_fk_pose_f64");
 }
 
-cpp_status cpp_mask(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
-                    const double* targets, int32_t T, int32_t K, int32_t Kp, uint8_t* mask,
-                    float* pen, float* err, int32_t* dev_status, cpp_stream_t stream) {
+static cpp_status mask_impl(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
+                            const double* targets, int32_t T, int32_t K, int32_t Kp,
+                            int32_t k_begin, uint8_t* mask, float* pen, float* err,
+                            int32_t* dev_status, cpp_stream_t stream) {
   if (cpp_status s = check_robot(robot)) return s;
   if (cpp_status s = check_params(params)) return s;
   if (cpp_status s = check_lattice(T, K, Kp, robot->n)) return s;
+  if (k_begin < 0 || k_begin > K || k_begin % 4 != 0)
+    return fail(CPP_ERR_INVALID_ARG, "k_begin = %d must be a multiple of 4 in [0, K]", k_begin);
   if (!cand || !targets || !mask || !pen) return fail(CPP_ERR_INVALID_ARG, "NULL buffer");
   if (!aligned(cand, 16) || !aligned(pen, 16) || !aligned(mask, 4) || (err && !aligned(err, 16)))
     return fail(CPP_ERR_INVALID_ARG, "cand/pen/err must be 16-byte and mask 4-byte aligned");
   SingleSrc s;
   s.r = empty_req();
-  s.r.T = T; s.r.K = K; s.r.Kp = Kp; s.r.n = robot->n;
+  s.r.T = T; s.r.K = K; s.r.Kp = Kp; s.r.n = robot->n; s.r.k_begin = k_begin;
   s.r.cand = cand; s.r.targets = targets; s.r.mask = mask; s.r.pen = pen; s.r.err = err;
   s.r.status = dev_status;
   s.robot = *robot;
   return cuda_status(launch_mask(s, *params, (cudaStream_t)stream), "cpp_mask");
+}
+
+cpp_status cpp_mask(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
+                    const double* targets, int32_t T, int32_t K, int32_t Kp, uint8_t* mask,
+                    float* pen, float* err, int32_t* dev_status, cpp_stream_t stream) {
+  return mask_impl(robot, params, cand, targets, T, K, Kp, 0, mask, pen, err, dev_status, stream);
+}
+
+cpp_status cpp_mask_range(const cpp_robot_t* robot, const cpp_params_t* params,
+                          const float* cand, const double* targets, int32_t T, int32_t K,
+                          int32_t Kp, int32_t k_begin, uint8_t* mask, float* pen, float* err,
+                          int32_t* dev_status, cpp_stream_t stream) {
+  return mask_impl(robot, params, cand, targets, T, K, Kp, k_begin, mask, pen, err, dev_status,
+                   stream);
 }
 
 size_t cpp_dp_workspace_size(int32_t T, int32_t Kp) {
@@ -170,11 +190,14 @@ size_t cpp_dp_workspace_size(int32_t T, int32_t Kp) {
   return dp_layout(T, Kp).total;
 }
 
-cpp_status cpp_dp_search(const float* cand, const float* pen, int32_t T, int32_t K, int32_t Kp,
-                         int32_t n, void* workspace, size_t ws_bytes, int32_t* sel,
-                         float* best_cost, float* q_seed, int32_t* dev_status,
-                         cpp_stream_t stream) {
+cpp_status cpp_dp_search_ex(const float* cand, const float* pen, int32_t T, int32_t K, int32_t Kp,
+                            int32_t n, int32_t objective, void* workspace, size_t ws_bytes,
+                            int32_t* sel, float* best_cost, float* q_seed, float* search_mjac,
+                            int32_t* dev_status, cpp_stream_t stream) {
   if (cpp_status s = check_lattice(T, K, Kp, n)) return s;
+  if (objective != CPP_DP_SUM && objective != CPP_DP_MINMAX)
+    return fail(CPP_ERR_INVALID_ARG, "objective %d is neither CPP_DP_SUM nor CPP_DP_MINMAX",
+                objective);
   if (!dp_supported(n, Kp))
     return fail(CPP_ERR_INVALID_ARG, "Kp * (n + 1) = %d exceeds the shared-memory limit (29056)",
                 Kp * (n + 1));
@@ -193,10 +216,19 @@ cpp_status cpp_dp_search(const float* cand, const float* pen, int32_t T, int32_t
   s.r.pen_min = reinterpret_cast<float*>(ws + L.pen_min);
   s.r.bp = reinterpret_cast<uint16_t*>(ws + L.bp);
   s.r.costT = reinterpret_cast<float*>(ws + L.costT);
-  s.r.sel = sel; s.r.best_cost = best_cost; s.r.q_seed = q_seed; s.r.status = dev_status;
+  s.r.sel = sel; s.r.best_cost = best_cost; s.r.q_seed = q_seed; s.r.search_mjac = search_mjac;
+  s.r.status = dev_status;
   memset(&s.robot, 0, sizeof(s.robot));
   return cuda_status(launch_dp(s, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK,
-                               (cudaStream_t)stream), "cpp_dp_search");
+                               objective, (cudaStream_t)stream), "cpp_dp_search");
+}
+
+cpp_status cpp_dp_search(const float* cand, const float* pen, int32_t T, int32_t K, int32_t Kp,
+                         int32_t n, void* workspace, size_t ws_bytes, int32_t* sel,
+                         float* best_cost, float* q_seed, int32_t* dev_status,
+                         cpp_stream_t stream) {
+  return cpp_dp_search_ex(cand, pen, T, K, Kp, n, CPP_DP_SUM, workspace, ws_bytes, sel,
+                          best_cost, q_seed, nullptr, dev_status, stream);
 }
 
 cpp_status cpp_lm_refine(const cpp_robot_t* robot, const cpp_params_t* params, const float* q_in,
@@ -271,7 +303,8 @@ cpp_status cpp_plan(const cpp_robot_t* robot, const cpp_params_t* params, const 
   s.robot = *robot;
   if (cpp_status e = cuda_status(launch_mask(s, *params, st), "cpp_plan/mask")) return e;
   if (cpp_status e = cuda_status(launch_dp(s, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD |
-                                                   CPP_STAGE_BACKTRACK, st), "cpp_plan/dp"))
+                                                   CPP_STAGE_BACKTRACK, params->dp_objective, st),
+                                 "cpp_plan/dp"))
     return e;
   // the check below writes the FP64 pose errors
   if (cpp_status e = cuda_status(launch_lm(s, *params, false, st), "cpp_plan/lm")) return e;
@@ -401,8 +434,8 @@ cpp_status cpp_batch_run(cpp_batch_t* b, uint32_t stages, cpp_stream_t stream) {
       return e;
   const unsigned dp = stages & (CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK);
   if (dp)
-    if (cpp_status e = cuda_status(launch_dp_batch(b->src, dp, b->n, b->count, b->max_T,
-                                                   b->max_Kp, st), "batch/dp"))
+    if (cpp_status e = cuda_status(launch_dp_batch(b->src, dp, b->params.dp_objective, b->n,
+                                                   b->count, b->max_T, b->max_Kp, st), "batch/dp"))
       return e;
   if (stages & CPP_STAGE_LM)
     if (cpp_status e = cuda_status(launch_lm_batch(b->src, b->n, b->count, b->max_T, b->params, st),

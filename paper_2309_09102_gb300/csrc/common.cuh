@@ -20,6 +20,7 @@ constexpr int kMaxJ = CPP_MAX_JOINTS;
 // One request as the kernels see it (device pointers; unused ones may be null).
 struct Req {
   int T, K, Kp, n;
+  int k_begin;               // first candidate lane the mask writes (a multiple of 4)
   int robot;                 // index into the robot table
   int Kb;                    // backpointer row stride (Kp rounded up to 8)
   const float* cand;         // [T][n][Kp]
@@ -32,6 +33,7 @@ struct Req {
   float* costT;              // [Kp]     final DP costs
   int32_t* sel;              // [T]
   float* best_cost;          // [1]
+  float* search_mjac;        // [1] or null: mjac of the selected path
   float* q_seed;             // [T][n] or null
   const float* q_in;         // [T][n] LM input
   float* q_out;              // [T][n]

@@ -25,24 +25,25 @@
 //                       abs-max, one add, one min -- 2n + 1 FP32 lane
 //                       operations, no HBM traffic except 2 bytes of backpointer
 //                       per successor and step.
+//   dpc_forward_kernel  the same sweep for one request spread over a cluster of CTAs
+//                       (requests that one wave of clusters covers).
 //   dp_forward_generic  any other n or Kp that fits shared memory (slow path).
+// The forward kernels live in dp_forward.cuh, compiled once per objective
+// (dp_fwd_sum.cu: summed jumps; dp_fwd_minmax.cu: the paper's min-max mjac).
 //   dp_backtrack_kernel lowest argmin of C_{T-1}, then the serial walk
 //                       k_i = bp[i+1][k_{i+1}] over backpointer rows staged into
 //                       shared memory by 1-D bulk copies (TMA engine, mbarrier
 //                       completion, double-buffered), then the seed gather.
-#include "internal.h"
+#include "dp_forward.cuh"
 
 namespace cppflow {
 
-constexpr int kDpThreads = 256;
 constexpr int kBtThreads = 256;
 constexpr uint32_t kBtChunkBytes = 32768;
 
 int bp_stride(int Kp) { return (Kp + 7) & ~7; }
 
 size_t dp_smem_bytes(int n, int Kp) { return (size_t)(2 * n + 2) * Kp * sizeof(float); }
-
-size_t dp3_smem_bytes(int nj, int Kp, int R);
 
 bool dp_supported(int n, int Kp) {
   if (dp_smem_bytes(n, Kp) > 227u * 1024u) return false;  // generic kernel
@@ -63,495 +64,6 @@ __global__ void __launch_bounds__(256) layer_min_kernel(const __grid_constant__ 
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0) rq.pen_min[i] = isinf(m) ? 0.f : m;
-}
-
-// ------------------------------------------------------------------ predecessor records
-// Every node k of the current layer is a record [-q_{k,0} .. -q_{k,n-1}, C_k]
-// (NW floats, a 16-byte multiple): one predecessor costs NW/4 broadcast float4
-// loads, and the joint differences are additions q' + (-q) (bit-identical to
-// q' - q, round-to-nearest). The sweep keeps only the running
-// minimum per 32-node tile and the first tile that lowered it; the lowest index
-// attaining the minimum is then recovered by re-evaluating that one tile. Same
-// values, same ties.
-template <int NJ>
-struct Rec {
-  static constexpr int NW = ((NJ + 1 + 3) / 4) * 4;  // floats per record
-  static constexpr int NP = (NJ + 1) / 2;             // register pairs of own joints
-};
-
-__device__ __forceinline__ uint64_t pack2(float a, float b) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void unpack2(uint64_t v, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-
-
-// max_j |own_j - q_j| for one predecessor record (negated joints in rec[0..NJ-1]).
-// IEEE subtraction a - b is a + (-b); max is exact, so the grouping does not
-// matter, and NaN terms are ignored as with fmaxf. (Packed pair additions and
-// three-input max/min give the same values but measured no faster on GB300:
-// every one of the 2n + 1 operations per edge still occupies an FP32 lane.)
-template <int NJ>
-__device__ __forceinline__ float linf_rec(const uint64_t (&own)[Rec<NJ>::NP], const float* rec) {
-  float d = 0.f;
-#pragma unroll
-  for (int p = 0; p < Rec<NJ>::NP; ++p) {
-    float ol, oh;
-    unpack2(own[p], ol, oh);
-    const float a0 = fabsf(ol + rec[2 * p]);
-    d = p == 0 ? a0 : fmaxf(d, a0);
-    if (2 * p + 1 < NJ) d = fmaxf(d, fabsf(oh + rec[2 * p + 1]));
-  }
-  return d;
-}
-
-constexpr int kDp2Tile = 32;  // predecessor nodes per tile of the deferred argmin
-
-// Records of one layer: node k at float offset k * NW + (k / 32) * 4. The
-// 16-byte skew per 32-node tile puts the same slot of different tiles on
-// different shared-memory banks (the tile rescan reads one tile per thread).
-__host__ __device__ __forceinline__ int rec_layer_floats(int NW, int Kp) {
-  return Kp * NW + ((Kp + 31) / 32) * 4;
-}
-__device__ __forceinline__ int rec_off(int NW, int k) { return k * NW + (k >> 5) * 4; }
-
-// ------------------------------------------------------------------ forward sweep
-//  * the 256 threads form two groups of 128 that own the same R successors per
-//    thread (Kp <= 128 R) and split the predecessor tiles in two contiguous
-//    halves, so each broadcast record feeds R edges; the halves' (minimum,
-//    tile) pairs merge through shared memory, the lower half winning ties, so
-//    the lowest index still wins;
-//  * one staging buffer and one record buffer: the bulk copy of layer i+2 is
-//    issued as soon as every thread has taken its own layer-(i+1) values, and
-//    the new records overwrite the old ones after the rescans;
-//  * full 32-record tiles are unrolled from a tile base pointer.
-constexpr int kDp3Threads = 256;
-constexpr int kDp3Group = 128;
-
-size_t dp3_smem_bytes(int nj, int Kp, int R) {
-  const int NW = ((nj + 1 + 3) / 4) * 4;
-  return (size_t)rec_layer_floats(NW, Kp) * 4  // records
-         + (size_t)nj * Kp * 4                  // raw layer staging
-         + (size_t)Kp * 4                       // node-cost staging
-         + (size_t)3 * R * kDp3Group * 4        // group exchange: min, tile, index
-         + 64;                                  // barrier
-}
-
-template <int NJ, int R>
-__device__ __forceinline__ void sweep_pair(const uint64_t (&own)[R][Rec<NJ>::NP], const float* r0,
-                                           const float* r1, float (&tb)[R]) {
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const float v0 = r0[NJ] + linf_rec<NJ>(own[r], r0);
-    const float v1 = r1[NJ] + linf_rec<NJ>(own[r], r1);
-    tb[r] = fminf(fminf(tb[r], v0), v1);
-  }
-}
-
-template <int NW>
-__device__ __forceinline__ void load_rec(const float* p, float (&v)[NW]) {
-#pragma unroll
-  for (int w = 0; w < NW; w += 4) {
-    const float4 x = *reinterpret_cast<const float4*>(p + w);
-    v[w] = x.x; v[w + 1] = x.y; v[w + 2] = x.z; v[w + 3] = x.w;
-  }
-}
-
-template <int NJ, int R, class Src>
-__global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __grid_constant__ Src src) {
-  constexpr int NW = Rec<NJ>::NW, NP = Rec<NJ>::NP;
-  const Req& rq = src.req(blockIdx.x);
-  const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
-  const int tid = threadIdx.x, g = tid / kDp3Group, lt = tid % kDp3Group;
-  extern __shared__ __align__(128) float sm3[];
-  const int RL = rec_layer_floats(NW, Kp);
-  float* const rec = sm3;                                   // [RL] records (skewed)
-  float* const stg = rec + RL;                              // [NJ][Kp] staged layer
-  float* const pst = stg + (size_t)NJ * Kp;                 // [Kp] staged node costs
-  float* const xmin = pst + Kp;                             // [R][128]
-  int* const xtile = reinterpret_cast<int*>(xmin + R * kDp3Group);  // [R][128]
-  int* const xarg = xtile + R * kDp3Group;                  // [R][128]
-  uint64_t* const bar = reinterpret_cast<uint64_t*>(xarg + R * kDp3Group);
-  __shared__ int timeout_flag;
-
-  const uint32_t layer_bytes = (uint32_t)(NJ * Kp * 4), pen_bytes = (uint32_t)(Kp * 4);
-  auto issue = [&](int L) {  // one thread; layer L completes phase L of the barrier
-    mbar_expect_tx(bar, layer_bytes + pen_bytes);
-    bulk_g2s(stg, rq.cand + (size_t)L * NJ * Kp, layer_bytes, bar);
-    bulk_g2s(pst, rq.pen + (size_t)L * Kp, pen_bytes, bar);
-  };
-  auto wait_layer = [&](int L) -> bool { return mbar_wait_bounded(bar, (uint32_t)(L & 1)); };
-
-  if (tid == 0) {
-    timeout_flag = 0;
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid == 0) issue(0);
-  if (!wait_layer(0)) atomicExch(&timeout_flag, 1);
-  {
-    const float m0 = rq.pen_min[0];
-    for (int k = tid; k < Kp; k += kDp3Threads) {
-      float v[NW];
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) v[j] = -stg[(size_t)j * Kp + k];
-      v[NJ] = k < K ? pst[k] - m0 : CUDART_INF_F;
-#pragma unroll
-      for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
-      float4* dst = reinterpret_cast<float4*>(rec + rec_off(NW, k));
-#pragma unroll
-      for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
-    }
-  }
-  __syncthreads();
-  if (timeout_flag) {  // a copy that never completed: wait once more (bounded), then stop
-    raise_status(rq.status, CPP_ERR_TIMEOUT);
-    if (tid == 0) wait_layer(0);
-    return;
-  }
-  if (tid == 0 && T > 1) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    issue(1);
-  }
-
-  int kp[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) kp[r] = lt + r * kDp3Group;
-  const int K4 = (K + 3) & ~3;
-  const int ntiles = (K4 + kDp2Tile - 1) / kDp2Tile;
-  const int half = (ntiles + 1) / 2;
-  const int t_lo = g == 0 ? 0 : half, t_hi = g == 0 ? half : ntiles;
-
-  for (int i = 0; i + 1 < T; ++i) {
-    const int L = i + 1;
-    if (!wait_layer(L)) atomicExch(&timeout_flag, 1);
-    uint64_t own[R][NP];
-    float rpen[R];
-    const float m1 = rq.pen_min[L];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int k = kp[r] < Kp ? kp[r] : Kp - 1;
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const float a = stg[(size_t)(2 * p) * Kp + k];
-        const float b = (2 * p + 1 < NJ) ? stg[(size_t)(2 * p + 1) * Kp + k] : 0.f;
-        own[r][p] = pack2(a, b);
-      }
-      rpen[r] = kp[r] < K ? pst[kp[r]] - m1 : CUDART_INF_F;
-    }
-    __syncthreads();  // everyone holds its layer-L values: the staging buffer is free
-    if (timeout_flag) {
-      raise_status(rq.status, CPP_ERR_TIMEOUT);
-      if (tid == 0) wait_layer(L);
-      return;
-    }
-    if (tid == 0 && L + 1 < T) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(L + 1);
-    }
-
-    float best[R];
-    int btile[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; btile[r] = -1; }
-#pragma unroll 1
-    for (int t = t_lo; t < t_hi; ++t) {
-      const int kb = t * kDp2Tile;
-      const float* base = rec + rec_off(NW, kb);
-      float tb[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) tb[r] = CUDART_INF_F;
-      if (kb + kDp2Tile <= K4) {
-#pragma unroll
-        for (int k = 0; k < kDp2Tile; k += 2) {
-          float r0[NW], r1[NW];
-          load_rec<NW>(base + k * NW, r0);
-          load_rec<NW>(base + (k + 1) * NW, r1);
-          sweep_pair<NJ, R>(own, r0, r1, tb);
-        }
-      } else {
-        for (int k = 0; kb + k < K4; k += 2) {
-          float r0[NW], r1[NW];
-          load_rec<NW>(base + k * NW, r0);
-          load_rec<NW>(base + (k + 1) * NW, r1);
-          sweep_pair<NJ, R>(own, r0, r1, tb);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (tb[r] < best[r]) { best[r] = tb[r]; btile[r] = t; }
-    }
-    // merge the halves: the upper half (larger k) replaces only a strictly smaller minimum
-    if (g == 1) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) { xmin[r * kDp3Group + lt] = best[r]; xtile[r * kDp3Group + lt] = btile[r]; }
-    }
-    __syncthreads();
-    if (g == 0) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float b1 = xmin[r * kDp3Group + lt];
-        const int t1 = xtile[r * kDp3Group + lt];
-        if (b1 < best[r]) { best[r] = b1; btile[r] = t1; }
-        xmin[r * kDp3Group + lt] = best[r];
-        xtile[r * kDp3Group + lt] = btile[r];
-      }
-    }
-    __syncthreads();
-    // rescans: successor r is handled by group r % 2 (group 0 when R == 1)
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if ((R == 1 ? 0 : (r & 1)) != g) continue;
-      const float bv = xmin[r * kDp3Group + lt];
-      const int bt = xtile[r * kDp3Group + lt];
-      int arg = 0;
-      if (bt >= 0) {
-        const int kb = bt * kDp2Tile, ke = min(kb + kDp2Tile, K4);
-        const float* base = rec + rec_off(NW, kb);
-        for (int k = kb; k < ke; ++k) {
-          const float* rk = base + (k - kb) * NW;
-          if (rk[NJ] + linf_rec<NJ>(own[r], rk) == bv) { arg = k; break; }
-        }
-      }
-      xarg[r * kDp3Group + lt] = arg;
-    }
-    __syncthreads();  // rescans done: the records may be replaced
-    uint16_t* bprow = rq.bp + (size_t)L * Kb;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if ((R == 1 ? 0 : (r & 1)) != g || kp[r] >= Kp) continue;
-      float v[NW];
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        float a, b;
-        unpack2(own[r][p], a, b);
-        v[2 * p] = -a;
-        if (2 * p + 1 < NJ) v[2 * p + 1] = -b;
-      }
-      v[NJ] = kp[r] < K ? xmin[r * kDp3Group + lt] + rpen[r] : CUDART_INF_F;
-#pragma unroll
-      for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
-      float4* dst = reinterpret_cast<float4*>(rec + rec_off(NW, kp[r]));
-#pragma unroll
-      for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
-      bprow[kp[r]] = (uint16_t)xarg[r * kDp3Group + lt];
-    }
-    __syncthreads();
-  }
-  for (int k = tid; k < Kp; k += kDp3Threads) rq.costT[k] = rec[rec_off(NW, k) + NJ];
-}
-
-// ------------------------------------------------------------------ forward sweep, cluster
-// One request alone (the plain per-request path, or a batch too small to fill
-// the GPU) would leave most SMs idle with one CTA per request, and its T
-// dependent steps would each run on a single SM. This form spreads one request
-// over a thread-block cluster of CS CTAs (CS = ceil(Kp / 32R) <= 8):
-//  * CTA c owns successors [32 R c, 32 R (c + 1)); its 8 warps split the
-//    predecessors into 8 contiguous ranges and keep an exact argmin per edge
-//    (strict '<' in index order);
-//  * the 8 partial (minimum, index) pairs merge in warp order, the lower range
-//    winning ties, so the lowest index wins;
-//  * each new record [-q', C'] is stored into the record buffer of every CTA of
-//    the cluster (distributed shared memory), and a release/acquire cluster
-//    barrier ends the step. Records are double-buffered: a CTA that starts step
-//    i+1 writes only the buffer every CTA finished reading before the barrier
-//    of step i.
-constexpr int kDpcThreads = 256;
-constexpr int kDpcWarps = kDpcThreads / 32;
-
-size_t dpc_smem_bytes(int nj, int Kp, int R) {
-  const int NW = ((nj + 1 + 3) / 4) * 4;
-  return (size_t)2 * Kp * NW * 4 + (size_t)2 * kDpcWarps * 32 * R * 4;
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t map_peer(uint32_t smem_addr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void st_peer_v4(uint32_t addr, float4 v) {
-  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y),
-               "f"(v.z), "f"(v.w)
-               : "memory");
-}
-__device__ __forceinline__ void cluster_barrier() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n"
-               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-template <int NJ, int R, class Src>
-__global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_constant__ Src src,
-                                                                   const int CS) {
-  constexpr int NW = Rec<NJ>::NW, NP = Rec<NJ>::NP, S = 32 * R;
-  const uint32_t crank = cluster_rank();
-  const Req& rq = src.req(blockIdx.x / CS);
-  const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  extern __shared__ __align__(16) float smc[];
-  float* const recb = smc;                               // [2][Kp][NW]
-  float* const xmin = recb + 2 * (size_t)Kp * NW;        // [warps][S]
-  int* const xarg = reinterpret_cast<int*>(xmin + kDpcWarps * S);
-  const float* __restrict__ cand = rq.cand;
-
-  // layer 0: every CTA builds all records locally
-  {
-    const float m0 = rq.pen_min[0];
-    for (int k = tid; k < Kp; k += kDpcThreads) {
-      float v[NW];
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) v[j] = -cand[(size_t)j * Kp + k];
-      v[NJ] = k < K ? rq.pen[k] - m0 : CUDART_INF_F;
-#pragma unroll
-      for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
-      float4* dst = reinterpret_cast<float4*>(recb + (size_t)k * NW);
-#pragma unroll
-      for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
-    }
-  }
-  int kp[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) kp[r] = (int)crank * S + lane + 32 * r;
-  float qn[R][NJ];  // own successor values of the next layer
-  auto load_own = [&](int L) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int k = kp[r] < Kp ? kp[r] : Kp - 1;
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) qn[r][j] = __ldg(cand + ((size_t)L * NJ + j) * Kp + k);
-    }
-  };
-  if (T > 1) load_own(1);
-  const int K4 = (K + 3) & ~3;
-  const int chunk = ((K4 + 2 * kDpcWarps - 1) / (2 * kDpcWarps)) * 2;
-  const int kb = min(warp * chunk, K4), ke = min(kb + chunk, K4);
-  __syncthreads();
-  cluster_barrier();
-
-  for (int i = 0; i + 1 < T; ++i) {
-    const int L = i + 1;
-    const float* cur = recb + (size_t)(i & 1) * Kp * NW;
-    float* nxt = recb + (size_t)(L & 1) * Kp * NW;
-    uint64_t own[R][NP];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int p = 0; p < NP; ++p)
-        own[r][p] = pack2(qn[r][2 * p], (2 * p + 1 < NJ) ? qn[r][2 * p + 1] : 0.f);
-    float rpen[R];
-    const float m1 = rq.pen_min[L];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      rpen[r] = kp[r] < K ? __ldg(rq.pen + (size_t)L * Kp + kp[r]) - m1 : CUDART_INF_F;
-    if (L + 1 < T) load_own(L + 1);  // prefetch, consumed next step
-
-    float best[R];
-    int arg[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; arg[r] = 0; }
-    for (int k = kb; k < ke; k += 2) {
-      float r0[NW], r1[NW];
-      load_rec<NW>(cur + (size_t)k * NW, r0);
-      load_rec<NW>(cur + (size_t)(k + 1) * NW, r1);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float v0 = r0[NJ] + linf_rec<NJ>(own[r], r0);
-        const float v1 = r1[NJ] + linf_rec<NJ>(own[r], r1);
-        if (v0 < best[r]) { best[r] = v0; arg[r] = k; }
-        if (v1 < best[r]) { best[r] = v1; arg[r] = k + 1; }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      xmin[warp * S + lane + 32 * r] = best[r];
-      xarg[warp * S + lane + 32 * r] = arg[r];
-    }
-    __syncthreads();
-    // slot (warp r, lane): merge the 8 ranges in order, write the record everywhere
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (warp != r || kp[r] >= Kp) continue;
-      const int slot = lane + 32 * r;
-      float bv = xmin[slot];
-      int ba = xarg[slot];
-      for (int w = 1; w < kDpcWarps; ++w)
-        if (xmin[w * S + slot] < bv) { bv = xmin[w * S + slot]; ba = xarg[w * S + slot]; }
-      float v[NW];
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        float a, b;
-        unpack2(own[r][p], a, b);
-        v[2 * p] = -a;
-        if (2 * p + 1 < NJ) v[2 * p + 1] = -b;
-      }
-      v[NJ] = kp[r] < K ? bv + rpen[r] : CUDART_INF_F;
-#pragma unroll
-      for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
-      const uint32_t base = smem_u32(nxt + (size_t)kp[r] * NW);
-      for (int c = 0; c < CS; ++c) {
-        const uint32_t peer = map_peer(base, (uint32_t)c);
-#pragma unroll
-        for (int w = 0; w < NW / 4; ++w)
-          st_peer_v4(peer + 16 * w, make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]));
-      }
-      rq.bp[(size_t)L * Kb + kp[r]] = (uint16_t)ba;
-    }
-    cluster_barrier();
-  }
-  const float* fin = recb + (size_t)((T - 1) & 1) * Kp * NW;
-  for (int k = (int)crank * S + tid; k < min(Kp, ((int)crank + 1) * S); k += kDpcThreads)
-    rq.costT[k] = fin[(size_t)k * NW + NJ];
-}
-
-// Any n and Kp that fit in shared memory: successor values are read back from
-// shared memory instead of registers.
-template <class Src>
-__global__ void __launch_bounds__(kDpThreads) dp_forward_generic(const __grid_constant__ Src src) {
-  const Req& rq = src.req(blockIdx.x);
-  const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb, n = rq.n;
-  extern __shared__ __align__(16) float sm[];
-  float* const qbase = sm;
-  float* const cbase = sm + 2 * n * Kp;
-  const int tid = threadIdx.x;
-  const float* __restrict__ cand = rq.cand;
-  const float m0 = rq.pen_min[0];
-  for (int x = tid; x < n * Kp; x += kDpThreads) qbase[x] = cand[x];
-  for (int k = tid; k < Kp; k += kDpThreads) cbase[k] = k < K ? rq.pen[k] - m0 : CUDART_INF_F;
-  __syncthreads();
-  for (int i = 0; i + 1 < T; ++i) {
-    const int cur = i & 1, nxt = cur ^ 1;
-    const float* qc = qbase + cur * n * Kp;
-    const float* cc = cbase + cur * Kp;
-    float* qx = qbase + nxt * n * Kp;
-    float* cx = cbase + nxt * Kp;
-    const float* layer = cand + (size_t)(i + 1) * n * Kp;
-    for (int x = tid; x < Kp; x += kDpThreads)
-      for (int j = 0; j < n; ++j) qx[j * Kp + x] = layer[(size_t)j * Kp + x];
-    const float m1 = rq.pen_min[i + 1];
-    for (int x = tid; x < Kp; x += kDpThreads) {
-      float best = CUDART_INF_F;
-      int arg = 0;
-      for (int k = 0; k < K; ++k) {
-        float d = fabsf(qx[x] - qc[k]);
-        for (int j = 1; j < n; ++j) d = fmaxf(d, fabsf(qx[j * Kp + x] - qc[j * Kp + k]));
-        const float v = cc[k] + d;
-        if (v < best) { best = v; arg = k; }
-      }
-      cx[x] = x < K ? best + (rq.pen[(size_t)(i + 1) * Kp + x] - m1) : CUDART_INF_F;
-      rq.bp[(size_t)(i + 1) * Kb + x] = (uint16_t)arg;
-    }
-    __syncthreads();
-  }
-  const float* cfin = cbase + ((T - 1) & 1) * Kp;
-  for (int k = tid; k < Kp; k += kDpThreads) rq.costT[k] = cfin[k];
 }
 
 // ------------------------------------------------------------------ backtrack
@@ -636,6 +148,23 @@ __global__ void __launch_bounds__(kBtThreads) dp_backtrack_kernel(const __grid_c
     (void)ok;
   }
   __syncthreads();
+  if (rq.search_mjac) {  // mjac of the selected path: max over steps and joints of |dq|
+    float m = 0.f;
+    for (int i = tid; i + 1 < T; i += kBtThreads) {
+      const int a = rq.sel[i], b = rq.sel[i + 1];
+      for (int j = 0; j < n; ++j)
+        m = fmaxf(m, fabsf(rq.cand[((size_t)(i + 1) * n + j) * rq.Kp + b] -
+                           rq.cand[((size_t)i * n + j) * rq.Kp + a]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) rv[warp] = m;
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < kBtThreads / 32; ++w) m = fmaxf(m, rv[w]);
+      *rq.search_mjac = m;
+    }
+  }
   if (rq.q_seed) {
     for (int x = tid; x < T * n; x += kBtThreads) {
       const int i = x / n, j = x - i * n;
@@ -646,73 +175,9 @@ __global__ void __launch_bounds__(kBtThreads) dp_backtrack_kernel(const __grid_c
 }
 
 // ------------------------------------------------------------------ launchers
-template <class KernelT>
-static cudaError_t allow_smem(KernelT kernel, size_t bytes) {
-  if (bytes <= 48u * 1024u) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <int NJ, int R, class Src>
-static cudaError_t launch_fwd3_r(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
-  const size_t smem = dp3_smem_bytes(NJ, max_Kp, R);
-  cudaError_t e = allow_smem(dp3_forward_kernel<NJ, R, Src>, smem);
-  if (e != cudaSuccess) return e;
-  dp3_forward_kernel<NJ, R, Src><<<nreq, kDp3Threads, smem, st>>>(s);
-  return cudaGetLastError();
-}
-
-template <int NJ, int R, class Src>
-static cudaError_t launch_fwdc_r(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
-  const int CS = (max_Kp + 32 * R - 1) / (32 * R);
-  const size_t smem = dpc_smem_bytes(NJ, max_Kp, R);
-  cudaError_t e = allow_smem(dpc_forward_kernel<NJ, R, Src>, smem);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nreq * CS));
-  cfg.blockDim = dim3(kDpcThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)CS;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, dpc_forward_kernel<NJ, R, Src>, s, CS);
-}
-
-// Requests that one wave of clusters covers use the cluster form (lower latency);
-// larger batches use one CTA per request (higher throughput).
-static int sm_count() {
-  static int n = [] {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    return v > 0 ? v : 1;
-  }();
-  return n;
-}
-
-template <int NJ, class Src>
-static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
-  if (max_Kp > 64) {
-    const int Rc = max_Kp <= 512 ? 2 : 4;
-    const int CS = (max_Kp + 32 * Rc - 1) / (32 * Rc);
-    if (nreq * CS <= sm_count())
-      return Rc == 2 ? launch_fwdc_r<NJ, 2>(s, nreq, max_Kp, st)
-                     : launch_fwdc_r<NJ, 4>(s, nreq, max_Kp, st);
-  }
-  const int R = (max_Kp + kDp3Group - 1) / kDp3Group;
-  if (R <= 1) return launch_fwd3_r<NJ, 1>(s, nreq, max_Kp, st);
-  if (R <= 2) return launch_fwd3_r<NJ, 2>(s, nreq, max_Kp, st);
-  if (R <= 4) return launch_fwd3_r<NJ, 4>(s, nreq, max_Kp, st);
-  return launch_fwd3_r<NJ, 8>(s, nreq, max_Kp, st);
-}
-
 template <class Src>
-static cudaError_t launch_dp_t(const Src& s, unsigned stages, int n, int nreq, int max_T,
-                               int max_Kp, cudaStream_t st) {
+static cudaError_t launch_dp_t(const Src& s, unsigned stages, int objective, int n, int nreq,
+                               int max_T, int max_Kp, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (stages & CPP_STAGE_LAYER_MIN) {
     dim3 grid((unsigned)((max_T + 7) / 8), (unsigned)nreq);
@@ -720,16 +185,8 @@ static cudaError_t launch_dp_t(const Src& s, unsigned stages, int n, int nreq, i
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (stages & CPP_STAGE_DP_FORWARD) {
-    const bool fast = max_Kp <= 1024;
-    if (fast && n == 7) e = launch_fwd_nj<7>(s, nreq, max_Kp, st);
-    else if (fast && n == 9) e = launch_fwd_nj<9>(s, nreq, max_Kp, st);
-    else if (fast && n == 6) e = launch_fwd_nj<6>(s, nreq, max_Kp, st);
-    else {
-      const size_t smem = dp_smem_bytes(n, max_Kp);
-      if ((e = allow_smem(dp_forward_generic<Src>, smem)) != cudaSuccess) return e;
-      dp_forward_generic<Src><<<nreq, kDpThreads, smem, st>>>(s);
-      e = cudaGetLastError();
-    }
+    e = objective == CPP_DP_MINMAX ? launch_forward_minmax(s, n, nreq, max_Kp, st)
+                                   : launch_forward_sum(s, n, nreq, max_Kp, st);
     if (e != cudaSuccess) return e;
   }
   if (stages & CPP_STAGE_BACKTRACK) {
@@ -740,13 +197,13 @@ static cudaError_t launch_dp_t(const Src& s, unsigned stages, int n, int nreq, i
   return e;
 }
 
-cudaError_t launch_dp(const SingleSrc& s, unsigned stages, cudaStream_t st) {
-  return launch_dp_t(s, stages, s.r.n, 1, s.r.T, s.r.Kp, st);
+cudaError_t launch_dp(const SingleSrc& s, unsigned stages, int objective, cudaStream_t st) {
+  return launch_dp_t(s, stages, objective, s.r.n, 1, s.r.T, s.r.Kp, st);
 }
 
-cudaError_t launch_dp_batch(const BatchSrc& s, unsigned stages, int n, int nreq, int max_T,
-                            int max_Kp, cudaStream_t st) {
-  return launch_dp_t(s, stages, n, nreq, max_T, max_Kp, st);
+cudaError_t launch_dp_batch(const BatchSrc& s, unsigned stages, int objective, int n, int nreq,
+                            int max_T, int max_Kp, cudaStream_t st) {
+  return launch_dp_t(s, stages, objective, n, nreq, max_T, max_Kp, st);
 }
 
 }  // namespace cppflow

@@ -101,7 +101,7 @@ cpp_status cpp_dp_search_static(const float* cand, const float* pen, int32_t T, 
   s.r.bp = reinterpret_cast<uint16_t*>(ws + L.bp);
   s.r.costT = reinterpret_cast<float*>(ws + L.costT);
   s.r.sel = sel; s.r.best_cost = best_cost; s.r.q_seed = q_seed; s.r.status = dev_status;
-  e = launch_dp(s, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK,
+  e = launch_dp(s, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK, CPP_DP_SUM,
                 (cudaStream_t)stream);
   if (e != cudaSuccess)
     return reject(CPP_ERR_CUDA, "cpp_dp_search_static: launch: %s", cudaGetErrorString(e));

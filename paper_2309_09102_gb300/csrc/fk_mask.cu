@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kMaskThreads) mask_kernel(const __grid_constan
   warp_target_f32(rq.targets + 7 * (size_t)i, Rt, pt);
 
   const int k0 = kb * kMaskBlockK + 4 * lane;
-  if (k0 >= rq.Kp) return;
+  if (k0 >= rq.Kp || k0 < rq.k_begin) return;  // k_begin is a multiple of 4
   float4 qv[NJ ? NJ : kMaxJ];
   const float* base = rq.cand + (size_t)i * n * rq.Kp + k0;
 #pragma unroll

@@ -24,9 +24,15 @@ cudaError_t launch_fk_pose64(const cpp_robot_t& r, const double* q, long long N,
 int bp_stride(int Kp);
 size_t dp_smem_bytes(int n, int Kp);
 bool dp_supported(int n, int Kp);
-cudaError_t launch_dp(const SingleSrc& s, unsigned stages, cudaStream_t st);
-cudaError_t launch_dp_batch(const BatchSrc& s, unsigned stages, int n, int nreq, int max_T,
-                            int max_Kp, cudaStream_t st);
+cudaError_t launch_dp(const SingleSrc& s, unsigned stages, int objective, cudaStream_t st);
+cudaError_t launch_dp_batch(const BatchSrc& s, unsigned stages, int objective, int n, int nreq,
+                            int max_T, int max_Kp, cudaStream_t st);
+
+// dp_fwd_sum.cu, dp_fwd_minmax.cu
+cudaError_t launch_forward_sum(const SingleSrc& s, int n, int nreq, int max_Kp, cudaStream_t st);
+cudaError_t launch_forward_sum(const BatchSrc& s, int n, int nreq, int max_Kp, cudaStream_t st);
+cudaError_t launch_forward_minmax(const SingleSrc& s, int n, int nreq, int max_Kp, cudaStream_t st);
+cudaError_t launch_forward_minmax(const BatchSrc& s, int n, int nreq, int max_Kp, cudaStream_t st);
 
 // lm.cu
 cudaError_t launch_lm(const SingleSrc& s, const cpp_params_t& P, bool want_err, cudaStream_t st);

@@ -305,8 +305,8 @@ cpp_status cpp_server::enqueue(Launch* L) {
   BatchSrc src{reinterpret_cast<const Req*>(tab_d),
                reinterpret_cast<const cpp_robot_t*>(tab_d + align256(sizeof(Req) * count))};
   if ((e = launch_mask_batch(src, n, count, max_tasks, cfg.params, st)) != cudaSuccess ||
-      (e = launch_dp_batch(src, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK, n,
-                           count, max_T, max_Kp, st)) != cudaSuccess ||
+      (e = launch_dp_batch(src, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK,
+                           cfg.params.dp_objective, n, count, max_T, max_Kp, st)) != cudaSuccess ||
       (e = launch_lm_batch(src, n, count, max_T, cfg.params, st)) != cudaSuccess ||
       (e = launch_check_batch(src, count, cfg.params, st)) != cudaSuccess)
     return sfail(CPP_ERR_CUDA, "server launch: %s", cudaGetErrorString(e));

@@ -27,7 +27,7 @@ TAU_POS, TAU_ROT = 1e-3, math.radians(0.1)
 
 def params_pair(**kw):
     """The same settings as an oracle.Params and a cppflow.Params."""
-    op = oracle.make_params(**{k: v for k, v in kw.items() if k != "lm_fp64"})
+    op = oracle.make_params(**{k: v for k, v in kw.items() if k not in ("lm_fp64", "dp_objective")})
     cp = cppflow.make_params(**kw)
     return op, cp
 
@@ -68,6 +68,20 @@ def run_dp(cand, pen, K):
     cppflow.dp_search(dev(cand), dev(pen), K, ws, sel, best, seed, st)
     tt.cuda.synchronize()
     return dict(sel=sel.cpu().numpy(), best=np.float32(best.item()), seed=seed.cpu().numpy(),
+                status=int(st.item()))
+
+
+def run_dp_ex(cand, pen, K, objective):
+    T, n, Kp = cand.shape
+    tt = torch()
+    ws = tt.empty(cppflow.dp_workspace_size(T, Kp), dtype=tt.uint8, device=DEV)
+    sel = tt.empty(T, dtype=tt.int32, device=DEV)
+    best = tt.empty(1, dtype=tt.float32, device=DEV)
+    mj = tt.empty(1, dtype=tt.float32, device=DEV)
+    st = tt.zeros(1, dtype=tt.int32, device=DEV)
+    cppflow.dp_search_ex(dev(cand), dev(pen), K, objective, ws, sel, best, None, mj, st)
+    tt.cuda.synchronize()
+    return dict(sel=sel.cpu().numpy(), best=np.float32(best.item()), mjac=np.float32(mj.item()),
                 status=int(st.item()))
 
 
