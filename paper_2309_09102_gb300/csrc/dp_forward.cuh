@@ -15,7 +15,7 @@ constexpr int kDpThreads = 256;
 // (NW floats, a 16-byte multiple): one predecessor costs NW/4 broadcast float4
 // loads, and the joint differences are additions q' + (-q) (bit-identical to
 // q' - q, round-to-nearest). The sweep keeps only the running
-// minimum per 32-node tile and the first tile that lowered it; the lowest index
+// minimum per 16-node tile and the first tile that lowered it; the lowest index
 // attaining the minimum is then recovered by re-evaluating that one tile. Same
 // values, same ties.
 template <int NJ>
@@ -53,7 +53,7 @@ __device__ __forceinline__ float linf_rec(const uint64_t (&own)[Rec<NJ>::NP], co
   return d;
 }
 
-constexpr int kDp2Tile = 32;  // predecessor nodes per tile of the deferred argmin
+constexpr int kDp2Tile = 16;  // predecessor nodes per tile of the deferred argmin
 
 // The search objective (§III-B): OBJ 0 sums the per-step L-inf jumps (C + d);
 // OBJ 1 is the paper's own "minimum mjac achievable", a bottleneck path
@@ -63,13 +63,13 @@ __device__ __forceinline__ float comb(float c, float d) {
   return OBJ ? fmaxf(c, d) : c + d;
 }
 
-// Records of one layer: node k at float offset k * NW + (k / 32) * 4. The
-// 16-byte skew per 32-node tile puts the same slot of different tiles on
+// Records of one layer: node k at float offset k * NW + (k / 16) * 4. The
+// 16-byte skew per 16-node tile puts the same slot of different tiles on
 // different shared-memory banks (the tile rescan reads one tile per thread).
 __host__ __device__ __forceinline__ int rec_layer_floats(int NW, int Kp) {
-  return Kp * NW + ((Kp + 31) / 32) * 4;
+  return Kp * NW + ((Kp + kDp2Tile - 1) / kDp2Tile) * 4;
 }
-__device__ __forceinline__ int rec_off(int NW, int k) { return k * NW + (k >> 5) * 4; }
+__device__ __forceinline__ int rec_off(int NW, int k) { return k * NW + (k / kDp2Tile) * 4; }
 
 // ------------------------------------------------------------------ forward sweep
 //  * the 256 threads form two groups of 128 that own the same R successors per
@@ -80,7 +80,7 @@ __device__ __forceinline__ int rec_off(int NW, int k) { return k * NW + (k >> 5)
 //  * one staging buffer and one record buffer: the bulk copy of layer i+2 is
 //    issued as soon as every thread has taken its own layer-(i+1) values, and
 //    the new records overwrite the old ones after the rescans;
-//  * full 32-record tiles are unrolled from a tile base pointer.
+//  * full 16-record tiles are unrolled from a tile base pointer.
 constexpr int kDp3Threads = 256;
 constexpr int kDp3Group = 128;
 

@@ -2,11 +2,14 @@
 // and node costs for the candidate lattice (paper §II "Pose error", "Joint
 // limits"; §III-B node costs).
 //
-// Layout: candidates are [T][n][Kp] FP32, k fastest. One warp owns one waypoint
-// and a block of 128 candidates; lane l reads joints j of candidates
-// 4l .. 4l+3 as one float4 per joint (512 contiguous bytes per warp per joint),
-// runs the FP32 DH chain for its four candidates in registers, and writes one
-// uchar4 mask word, one float4 of costs and two float4 of errors.
+// Layout: candidates are [T][n][Kp] FP32, k fastest. A task is one waypoint and
+// a block of 128 candidates; one warp runs kMaskTasksPerWarp consecutive tasks
+// (the 4 blocks of one waypoint at K = 512), so the robot staging of a block and
+// the target conversion of a waypoint are paid once for several tasks. Lane l
+// reads joints j of candidates 4l .. 4l+3 as one float4 per joint (512
+// contiguous bytes per warp per joint), runs the FP32 DH chain for its four
+// candidates in registers, and writes one uchar4 mask word, one float4 of costs
+// and two float4 of errors.
 #include "internal.h"
 
 namespace cppflow {
@@ -14,6 +17,7 @@ namespace cppflow {
 constexpr int kMaskThreads = 256;
 constexpr int kMaskWarps = kMaskThreads / 32;
 constexpr int kMaskBlockK = 128;
+constexpr int kMaskTasksPerWarp = 4;
 
 struct MaskArgs {
   float tau_pos, tau_rot;
@@ -23,16 +27,22 @@ struct MaskArgs {
 
 // The target of waypoint i as FP32 rotation + position. The quaternion is
 // rounded to FP32 and converted in FP32 (GB300's FP64 pipe is ~64x narrower
-// than FP32, and every lane of the warp needs the same 12 numbers); this adds
-// ~1e-7 to the pose errors, far inside their 1e-5 tolerance.
-__device__ __forceinline__ void warp_target_f32(const double* t7, float Rt[9], float pt[3]) {
-  const float qw = (float)t7[3], qx = (float)t7[4], qy = (float)t7[5], qz = (float)t7[6];
+// than FP32); this adds ~1e-7 to the pose errors, far inside their 1e-5
+// tolerance. Lanes 0..6 each round one of the seven numbers, the warp shares
+// them by shuffles. Called by all 32 lanes.
+__device__ __forceinline__ void warp_target_f32(const double* t7, int lane, float Rt[9],
+                                                float pt[3]) {
+  const float v = lane < 7 ? (float)__ldg(t7 + lane) : 0.f;
+  pt[0] = __shfl_sync(0xffffffffu, v, 0);
+  pt[1] = __shfl_sync(0xffffffffu, v, 1);
+  pt[2] = __shfl_sync(0xffffffffu, v, 2);
+  const float qw = __shfl_sync(0xffffffffu, v, 3), qx = __shfl_sync(0xffffffffu, v, 4);
+  const float qy = __shfl_sync(0xffffffffu, v, 5), qz = __shfl_sync(0xffffffffu, v, 6);
   const float inv = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
   const float w = qw * inv, x = qx * inv, y = qy * inv, z = qz * inv;
   Rt[0] = 1.f - 2.f * (y * y + z * z); Rt[1] = 2.f * (x * y - w * z); Rt[2] = 2.f * (x * z + w * y);
   Rt[3] = 2.f * (x * y + w * z); Rt[4] = 1.f - 2.f * (x * x + z * z); Rt[5] = 2.f * (y * z - w * x);
   Rt[6] = 2.f * (x * z - w * y); Rt[7] = 2.f * (y * z + w * x); Rt[8] = 1.f - 2.f * (x * x + y * y);
-  pt[0] = (float)t7[0]; pt[1] = (float)t7[1]; pt[2] = (float)t7[2];
 }
 
 template <int NJ>
@@ -64,7 +74,8 @@ __device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, co
   erot = geodesic<float>(Rt, R);
   if (epos > a.tau_pos || erot > a.tau_rot) b |= CPP_MASK_POSE;
   bits = (uint8_t)b;
-  cost = a.pen_table[((b & (CPP_MASK_OUT | CPP_MASK_NEAR)) ? 1 : 0) | ((b & CPP_MASK_POSE) ? 2 : 0)];
+  const bool lim = (b & (CPP_MASK_OUT | CPP_MASK_NEAR)) != 0, pose = (b & CPP_MASK_POSE) != 0;
+  cost = lim ? (pose ? a.pen_table[3] : a.pen_table[1]) : (pose ? a.pen_table[2] : a.pen_table[0]);
 }
 
 template <int NJ, class Src>
@@ -76,42 +87,48 @@ __global__ void __launch_bounds__(kMaskThreads) mask_kernel(const __grid_constan
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (rq.Kp + kMaskBlockK - 1) / kMaskBlockK;
-  const long long task = (long long)blockIdx.x * kMaskWarps + warp;
-  if (task >= (long long)rq.T * nblk) return;
-  const int i = (int)(task / nblk), kb = (int)(task % nblk);
+  const long long ntask = (long long)rq.T * nblk;
+  const long long t0 = ((long long)blockIdx.x * kMaskWarps + warp) * kMaskTasksPerWarp;
+  const long long t1 = t0 + kMaskTasksPerWarp < ntask ? t0 + kMaskTasksPerWarp : ntask;
   const int n = NJ ? NJ : rq.n;
 
+  int cur_i = -1;
   float Rt[9], pt[3];
-  warp_target_f32(rq.targets + 7 * (size_t)i, Rt, pt);
-
-  const int k0 = kb * kMaskBlockK + 4 * lane;
-  if (k0 >= rq.Kp || k0 < rq.k_begin) return;  // k_begin is a multiple of 4
-  float4 qv[NJ ? NJ : kMaxJ];
-  const float* base = rq.cand + (size_t)i * n * rq.Kp + k0;
-#pragma unroll
-  for (int j = 0; j < (NJ ? NJ : kMaxJ); ++j) {
-    if (!NJ && j >= n) break;
-    qv[j] = __ldg(reinterpret_cast<const float4*>(base + (size_t)j * rq.Kp));
-  }
-  uint8_t bits[4];
-  float cost[4], ep[4], er[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    float q[NJ ? NJ : kMaxJ];
+  for (long long task = t0; task < t1; ++task) {
+    const int i = (int)(task / nblk), kb = (int)(task % nblk);
+    if (i != cur_i) {  // warp-uniform
+      warp_target_f32(rq.targets + 7 * (size_t)i, lane, Rt, pt);
+      cur_i = i;
+    }
+    const int k0 = kb * kMaskBlockK + 4 * lane;
+    if (k0 >= rq.Kp || k0 < rq.k_begin) continue;  // k_begin is a multiple of 4
+    float4 qv[NJ ? NJ : kMaxJ];
+    const float* base = rq.cand + (size_t)i * n * rq.Kp + k0;
 #pragma unroll
     for (int j = 0; j < (NJ ? NJ : kMaxJ); ++j) {
       if (!NJ && j >= n) break;
-      q[j] = c == 0 ? qv[j].x : c == 1 ? qv[j].y : c == 2 ? qv[j].z : qv[j].w;
+      qv[j] = __ldg(reinterpret_cast<const float4*>(base + (size_t)j * rq.Kp));
     }
-    mask_one<NJ>(rb, a, q, n, k0 + c >= rq.K, Rt, pt, bits[c], cost[c], ep[c], er[c]);
-  }
-  const size_t o = (size_t)i * rq.Kp + k0;
-  *reinterpret_cast<uchar4*>(rq.mask + o) = make_uchar4(bits[0], bits[1], bits[2], bits[3]);
-  *reinterpret_cast<float4*>(rq.pen + o) = make_float4(cost[0], cost[1], cost[2], cost[3]);
-  if (rq.err) {
-    float4* e = reinterpret_cast<float4*>(rq.err + 2 * o);
-    e[0] = make_float4(ep[0], er[0], ep[1], er[1]);
-    e[1] = make_float4(ep[2], er[2], ep[3], er[3]);
+    uint8_t bits[4];
+    float cost[4], ep[4], er[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float q[NJ ? NJ : kMaxJ];
+#pragma unroll
+      for (int j = 0; j < (NJ ? NJ : kMaxJ); ++j) {
+        if (!NJ && j >= n) break;
+        q[j] = c == 0 ? qv[j].x : c == 1 ? qv[j].y : c == 2 ? qv[j].z : qv[j].w;
+      }
+      mask_one<NJ>(rb, a, q, n, k0 + c >= rq.K, Rt, pt, bits[c], cost[c], ep[c], er[c]);
+    }
+    const size_t o = (size_t)i * rq.Kp + k0;
+    *reinterpret_cast<uchar4*>(rq.mask + o) = make_uchar4(bits[0], bits[1], bits[2], bits[3]);
+    *reinterpret_cast<float4*>(rq.pen + o) = make_float4(cost[0], cost[1], cost[2], cost[3]);
+    if (rq.err) {
+      float4* e = reinterpret_cast<float4*>(rq.err + 2 * o);
+      e[0] = make_float4(ep[0], er[0], ep[1], er[1]);
+      e[1] = make_float4(ep[2], er[2], ep[3], er[3]);
+    }
   }
 }
 
@@ -188,7 +205,8 @@ template <class Src>
 static cudaError_t launch_mask_t(const Src& src, int n, int nreq, long long max_tasks,
                                  const cpp_params_t& P, cudaStream_t st) {
   const MaskArgs a = make_mask_args(P);
-  dim3 grid((unsigned)((max_tasks + kMaskWarps - 1) / kMaskWarps), (unsigned)nreq);
+  constexpr int per_block = kMaskWarps * kMaskTasksPerWarp;
+  dim3 grid((unsigned)((max_tasks + per_block - 1) / per_block), (unsigned)nreq);
   switch (n) {
     case 6: mask_kernel<6, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
     case 7: mask_kernel<7, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
