@@ -275,18 +275,18 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_
 
 # ----------------------------------------------------------------------------- GPU arm
 def build_inputs(cppflow, torch, dev, reqs):
-    """Pinned host lattices and FP64 targets of the given requests: random draws on the
-    host, target poses by the library's FP64 FK, wrong-branch solutions by its FP64 LM
-    restricted to the wrist joints. Returns (arms, robots, cand_h, targets_h)."""
-    n, T, K = synth.SINGLE.n, synth.SINGLE.T, synth.SINGLE.K
-    Kp = synth.pad_k(K)
+    """Pinned host lattices and FP64 targets of the given requests (each with its own
+    T, K and n): random draws on the host, target poses by the library's FP64 FK,
+    wrong-branch solutions by its FP64 LM restricted to the wrist joints.
+    Returns (arms, robots, cand_h, targets_h); arm a of robots is seed 100 + a."""
+    n = reqs[0].n
     arms = [synth.draw_arm(100 + k, n) for k in range(8)]
     robots = [cppflow.robot_from_arm(a) for a in arms]
     P_wb = cppflow.make_params(lm_iters=30, lm_fp64=1, free_mask=synth.wrong_branch_free_mask(n))
 
     def draws_of(w):
-        truth = synth.draw_truth(w.path_seed, n, T)
-        return truth, synth.draw_candidates(w.cand_seed, T, K, n, w.p_wb, w.p_out)
+        truth = synth.draw_truth(w.path_seed, w.n, w.T)
+        return truth, synth.draw_candidates(w.cand_seed, w.T, w.K, w.n, w.p_wb, w.p_out)
 
     with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         drawn = list(ex.map(draws_of, reqs))
@@ -295,18 +295,78 @@ def build_inputs(cppflow, torch, dev, reqs):
         truth, draws = drawn[r]
         rob = robots[w.arm_seed - 100]
         tq = torch.from_numpy(truth).to(dev)
-        tgt = torch.empty(T, 7, dtype=torch.float64, device=dev)
+        tgt = torch.empty(w.T, 7, dtype=torch.float64, device=dev)
         cppflow.fk_pose_f64(rob, tq, tgt)
         q0 = torch.from_numpy(synth.wrong_branch_start(truth).astype(np.float32)).to(dev)
-        qwb = torch.empty(T, n, dtype=torch.float32, device=dev)
+        qwb = torch.empty(w.T, w.n, dtype=torch.float32, device=dev)
         cppflow.lm_refine(rob, P_wb, q0, tgt, qwb)
         torch.cuda.synchronize()
         arm = arms[w.arm_seed - 100]
         cand = synth.assemble(truth, qwb.cpu().numpy().astype(np.float64), draws, w.sigma,
-                              arm.lo, arm.hi, Kp)
+                              arm.lo, arm.hi, synth.pad_k(w.K))
         cand_h.append(torch.from_numpy(cand).pin_memory())
         targets_h.append(tgt.cpu().pin_memory())
     return arms, robots, cand_h, targets_h
+
+
+def uneven_batch(cppflow, torch, dev, nreq: int) -> dict:
+    """The batched uneven launch: nreq requests (T ~ U{50..1000}, K in {128, 256, 512},
+    7-DoF arms from 8 seeded chains) in one prepared batch, its search schedule
+    tuned on the batch, all stages captured into one CUDA graph and replayed;
+    inputs resident in HBM. Reported beside the headline, not as it."""
+    reqs = [synth.batched_request(r) for r in range(nreq)]
+    _, robots, cand_h, targets_h = build_inputs(cppflow, torch, dev, reqs)
+    P = cppflow.make_params(lm_iters=20, lambda0=1e-3)
+    keep, descs = [], []
+    for r, w in enumerate(reqs):
+        o = dict(cand=cand_h[r].to(dev), targets=targets_h[r].to(dev),
+                 sel=torch.empty(w.T, dtype=torch.int32, device=dev),
+                 q=torch.empty(w.T, w.n, dtype=torch.float32, device=dev),
+                 err=torch.empty(w.T, 2, dtype=torch.float64, device=dev),
+                 rep=torch.zeros(cppflow.REPORT_BYTES, dtype=torch.uint8, device=dev),
+                 best=torch.empty(1, dtype=torch.float32, device=dev))
+        keep.append(o)
+        descs.append(cppflow.PlanDesc(w.T, w.K, synth.pad_k(w.K), w.arm_seed - 100,
+                                      o["cand"].data_ptr(), o["targets"].data_ptr(),
+                                      o["sel"].data_ptr(), o["q"].data_ptr(), o["err"].data_ptr(),
+                                      o["rep"].data_ptr(), o["best"].data_ptr()))
+    del cand_h
+    ws = torch.empty(cppflow.plan_batch_workspace_size(descs, robots), dtype=torch.uint8, device=dev)
+    status = torch.zeros(nreq, dtype=torch.int32, device=dev)
+    st = torch.cuda.Stream()
+    batch = cppflow.Batch(robots, P, descs, ws, status, st)
+
+    def time_runs(fn, reps=5):
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    batch.set_split(0.0, 0, st)
+    unsplit_ms = time_runs(lambda: batch.run(cppflow.STAGE_ALL, st))
+    t0 = time.perf_counter()
+    tune = batch.tune(None, st)
+    tune_s = time.perf_counter() - t0
+    batch.capture(cppflow.STAGE_ALL, st)
+    graph_ms = time_runs(lambda: batch.replay(st))
+    torch.cuda.synchronize()
+    reps = [cppflow.report_from_bytes(o["rep"].cpu().numpy().tobytes()) for o in keep]
+    out = {"workload": f"batched uneven: {nreq} requests, T ~ U{{50..1000}}, K in {{128, 256, 512}}, "
+                       "7-DoF, inputs resident",
+           "plans_per_s": round(nreq / (graph_ms / 1e3), 1), "ms_per_batch": round(graph_ms, 3),
+           "launches": batch.launches(cppflow.STAGE_ALL),
+           "unsplit_ms_per_batch": round(unsplit_ms, 3),
+           "tuned": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in tune.items()},
+           "tune_s": round(tune_s, 2),
+           "valid_plans": f"{sum(int(r['valid']) for r in reps)}/{nreq}",
+           "dev_status_nonzero": int((status != 0).sum())}
+    batch.close()
+    return out
 
 
 def run_cuda(args, rank: int, world: int, dist):
@@ -477,6 +537,7 @@ def run_cuda(args, rank: int, world: int, dist):
             "kernel_ms": round(statistics.mean(dp_ms), 4),
             "edges_per_s": round(edges / dp_s, 1)}
 
+    uneven = uneven_batch(cppflow, torch, dev, args.uneven) if args.uneven and rank == 0 else None
     mix = None
     if args.serve_rates and rank == 0:
         mix = serving_mix(cppflow, torch, dev, [float(x) for x in args.serve_rates.split(",")],
@@ -498,6 +559,8 @@ def run_cuda(args, rank: int, world: int, dist):
             "dev_status_nonzero": int((st != 0).sum()),
             "roofline": roof, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches_per_step * args.steps}
+    if uneven is not None:
+        line["batched_uneven"] = uneven
     if mix is not None:
         line["serving_mix"] = {"workload": "serving mix: T = floor(exp U(ln 50, ln 2000)), "
                                            "K in {128, 256, 512, 1024}, 7-DoF, Poisson arrivals",
@@ -518,6 +581,8 @@ def main():
     ap.add_argument("--plain", type=int, default=32, help="requests timed on the plain path")
     ap.add_argument("--serve-batch", type=int, default=38, help="server: requests per launch")
     ap.add_argument("--serve-inflight", type=int, default=8, help="server: launches in flight")
+    ap.add_argument("--uneven", type=int, default=256,
+                    help="requests of the batched uneven leg (0: skip)")
     ap.add_argument("--serve-rates", default="1000", help="Poisson rates (req/s) of the serving "
                     "mix, comma separated; empty to skip")
     ap.add_argument("--mix-pool", type=int, default=48, help="distinct requests in the mix pool")

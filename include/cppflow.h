@@ -311,6 +311,61 @@ cpp_status cpp_batch_run(cpp_batch_t* batch, uint32_t stages, cpp_stream_t strea
 int32_t cpp_batch_launches(const cpp_batch_t* batch, uint32_t stages);
 void cpp_batch_destroy(cpp_batch_t* batch);
 
+/* Scheduling of the search stage (S3) for uneven batches. The search is serial
+ * in T, so a batch's search time is at least that of its longest request on
+ * whatever runs it. A request whose lattice ((T - 1) * Kp^2 edges) exceeds
+ * alpha times the mean load of a CTA slot (total edges / (2 * SMs)) is "heavy"
+ * and runs as a thread-block cluster (one launch per cluster size, each on an
+ * internal stream forked from and joined back into the caller's stream by
+ * events); the others run one CTA per request, longest first. alpha = 0 sends
+ * every request to the one-launch form (clusters only when one wave of them
+ * covers the whole batch). cpp_batch_create applies alpha = 2.
+ *
+ * The cluster form gives each CTA cands_per_cta successor candidates of a
+ * waypoint (64 or 128; 0 = 64 up to Kp = 512 and 128 above, as long as the
+ * cluster has 2..8 CTAs): 64 halves a long request's latency, 128 halves the
+ * per-step cluster traffic and barriers per candidate.
+ *
+ * cpp_batch_set_split sets alpha (>= 0) and cands_per_cta and uploads the new
+ * schedule on `stream`. cpp_batch_tune picks both by measurement on the batch
+ * itself: it enqueues the mask and node-cost stages, then times the forward
+ * sweep (CUDA events, best of two runs after one warm-up) for alpha = 0 and,
+ * for each cands_per_cta in {64, 128}, a ladder of alpha values from 8 down to
+ * 1e-9 (every cluster-capable request heavy), skipping values that give the same
+ * split, and keeps the fastest. With a
+ * non-NULL table_path the choice is looked up first under a key of the batch's
+ * shape (joints, objective, request count and longest T in powers of two,
+ * cluster sizes present, skew of the largest lattice over the mean, SM count;
+ * plain text, one "key alpha cands_per_cta ms" line per entry, the last entry
+ * wins) and, when
+ * missing, appended after tuning. The call synchronizes `stream`; the batch's
+ * outputs are undefined until its next cpp_batch_run. A new schedule drops any
+ * captured graph. */
+typedef struct cpp_tune_result {
+    double alpha;            /* heavy threshold in use */
+    int32_t cands_per_cta;   /* successor candidates per CTA of the cluster form (0: default) */
+    int32_t heavy;           /* requests run as clusters */
+    int32_t forward_launches;/* launches of the forward sweep */
+    int32_t timed;           /* configurations timed (0 when taken from the table) */
+    int32_t from_table;      /* 1: alpha came from the tuning table */
+    float dp_ms;             /* forward sweep time of the choice (-1 from the table) */
+    float dp_ms_unsplit;     /* forward sweep time with alpha = 0 (-1 from the table) */
+    int32_t reserved;
+} cpp_tune_result_t;
+cpp_status cpp_batch_set_split(cpp_batch_t* batch, double alpha, int32_t cands_per_cta,
+                               cpp_stream_t stream);
+cpp_status cpp_batch_tune(cpp_batch_t* batch, const char* table_path, cpp_stream_t stream,
+                          cpp_tune_result_t* result);
+
+/* CUDA graph of a prepared batch: cpp_batch_capture records the launches of
+ * cpp_batch_run(batch, stages) on `stream` (a created stream, not the legacy
+ * default stream; the batch's internal streams join the capture through its
+ * events) into an executable graph held by the batch, replacing any earlier
+ * one; nothing runs during the capture. cpp_batch_replay launches that graph on
+ * any stream: the same kernels, arguments and buffers, one host call. */
+cpp_status cpp_batch_capture(cpp_batch_t* batch, uint32_t stages, cpp_stream_t stream);
+cpp_status cpp_batch_replay(cpp_batch_t* batch, cpp_stream_t stream);
+
 /* ------------------------------------------------------------------ serving
  * A continuous-batching request loop (not in the paper). Clients submit plans
  * with HOST buffers from any thread; a worker thread admits queued requests

@@ -63,6 +63,15 @@ REPORT_BYTES = C.sizeof(Report)
 REQ_BORROW = 1
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("cands_per_cta", C.c_int32), ("heavy", C.c_int32),
+                ("forward_launches", C.c_int32), ("timed", C.c_int32), ("from_table", C.c_int32),
+                ("dp_ms", C.c_float), ("dp_ms_unsplit", C.c_float), ("reserved", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("device", C.c_int32), ("max_slots", C.c_int32), ("max_batch", C.c_int32),
                 ("max_inflight", C.c_int32), ("hbm_budget_bytes", C.c_size_t),
@@ -118,6 +127,10 @@ _SIGS = {
     "cpp_batch_run": (C.c_int, [_P, C.c_uint32, _P]),
     "cpp_batch_launches": (C.c_int32, [_P, C.c_uint32]),
     "cpp_batch_destroy": (None, [_P]),
+    "cpp_batch_set_split": (C.c_int, [_P, C.c_double, C.c_int32, _P]),
+    "cpp_batch_tune": (C.c_int, [_P, C.c_char_p, _P, _P]),
+    "cpp_batch_capture": (C.c_int, [_P, C.c_uint32, _P]),
+    "cpp_batch_replay": (C.c_int, [_P, _P]),
     "cpp_server_config_default": (None, [_P]),
     "cpp_server_create": (C.c_int, [_P, C.POINTER(C.c_void_p)]),
     "cpp_plan_submit": (C.c_int, [_P, _P, C.POINTER(C.c_uint64)]),
@@ -313,6 +326,24 @@ class Batch:
 
     def launches(self, stages: int = STAGE_ALL) -> int:
         return lib().cpp_batch_launches(self.handle, stages)
+
+    def set_split(self, alpha: float, cands_per_cta: int = 0, stream=None):
+        _check(lib().cpp_batch_set_split(self.handle, float(alpha), int(cands_per_cta),
+                                         stream_handle(stream)), "cpp_batch_set_split")
+
+    def tune(self, table_path: str | None = None, stream=None) -> dict:
+        r = TuneResult()
+        path = table_path.encode() if table_path else None
+        _check(lib().cpp_batch_tune(self.handle, path, stream_handle(stream), C.byref(r)),
+               "cpp_batch_tune")
+        return r.as_dict()
+
+    def capture(self, stages: int = STAGE_ALL, stream=None):
+        _check(lib().cpp_batch_capture(self.handle, stages, stream_handle(stream)),
+               "cpp_batch_capture")
+
+    def replay(self, stream=None):
+        _check(lib().cpp_batch_replay(self.handle, stream_handle(stream)), "cpp_batch_replay")
 
     def close(self):
         if self.handle:

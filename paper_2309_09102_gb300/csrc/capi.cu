@@ -314,7 +314,7 @@ cpp_status cpp_plan(const cpp_robot_t* robot, const cpp_params_t* params, const 
 // ------------------------------------------------------------------ many requests
 namespace {
 struct BatchLayout {
-  size_t reqs, robots, per_req_base, total;
+  size_t reqs, sched, robots, per_req_base, total;
   std::vector<PlanLayout> L;
   std::vector<size_t> off;
 };
@@ -322,6 +322,7 @@ BatchLayout batch_layout(const cpp_plan_desc_t* d, int count, int n_robots, cons
   BatchLayout B;
   size_t o = 0;
   B.reqs = o;   o += align256(sizeof(Req) * (size_t)count);
+  B.sched = o;  o += align256(sizeof(Req) * (size_t)count);
   B.robots = o; o += align256(sizeof(cpp_robot_t) * (size_t)n_robots);
   B.per_req_base = o;
   for (int r = 0; r < count; ++r) {
@@ -345,12 +346,206 @@ size_t cpp_plan_batch_workspace_size(const cpp_plan_desc_t* descs, int32_t count
 
 }  // extern "C"
 
+// ------------------------------------------------------------------ batch schedule
+// The search stage of an uneven batch is scheduled, not launched over the whole
+// table at once: a request is serial in T, so one long request on one CTA sets
+// the batch's time however many SMs sit idle. Requests whose lattice (edges
+// (T - 1) Kp^2) exceeds alpha times the mean load of a CTA slot (total edges /
+// 2 SMs) are "heavy" and run as thread-block clusters (grouped by cluster size,
+// one launch per group, each on its own stream); the rest run one CTA per
+// request in a second table sorted longest first, so the hardware block
+// scheduler hands out the longest requests first. The launches fork from and
+// join back into the caller's stream through events, so a capture of the stream
+// records the whole fork/join. alpha comes from cpp_batch_tune (timed on the
+// batch itself, or read from a persisted table); the default is kDefaultAlpha.
+namespace {
+constexpr int kMaxGroups = 8;
+constexpr double kDefaultAlpha = 2.0;
+
+struct SchedGroup {
+  int begin, count, max_Kp, form, cpc;
+};
+
+bool fast_n(int n) { return n == 6 || n == 7 || n == 9; }
+}  // namespace
+
 struct cpp_batch {
-  BatchSrc src;
+  BatchSrc src;  // request table in descriptor order
   cpp_params_t params;
   int n, count, max_T, max_Kp;
   long long max_tasks;
+  // schedule of the search stage
+  Req* d_sched;
+  const cpp_robot_t* d_robots;
+  std::vector<Req> reqs;            // descriptor order (host copy)
+  std::vector<long long> edges;     // (T - 1) Kp^2 per request
+  std::vector<SchedGroup> groups;   // cluster groups, then the one-CTA group (last)
+  double alpha;
+  int cpc;  // successor candidates per CTA of the cluster form (0: default)
+  int heavy;
+  cudaStream_t aux[kMaxGroups];
+  cudaEvent_t fork, join[kMaxGroups];
+  cudaGraphExec_t graph;
+  uint32_t graph_stages;
 };
+
+namespace {
+
+void drop_graph(cpp_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_stages = 0;
+}
+
+// Split the requests for alpha (<= 0: none heavy) and cluster tiles of cpc
+// successors per CTA, and upload the schedule table.
+cpp_status set_schedule(cpp_batch* b, double alpha, int cpc, cudaStream_t st) {
+  const int count = b->count;
+  long long total = 0;
+  for (long long e : b->edges) total += e;
+  const double slots = 2.0 * device_sm_count();
+  const double thr = alpha > 0 ? alpha * (double)total / slots : HUGE_VAL;
+  std::vector<int> heavy, light;
+  for (int r = 0; r < count; ++r) {
+    const bool h =
+        fast_n(b->n) && cluster_size(b->reqs[r].Kp, cpc) > 0 && (double)b->edges[r] >= thr;
+    (h ? heavy : light).push_back(r);
+  }
+  auto longer = [&](int x, int y) {
+    return b->edges[x] != b->edges[y] ? b->edges[x] > b->edges[y] : x < y;
+  };
+  std::sort(heavy.begin(), heavy.end(), [&](int x, int y) {
+    const int cx = cluster_size(b->reqs[x].Kp, cpc), cy = cluster_size(b->reqs[y].Kp, cpc);
+    return cx != cy ? cx > cy : longer(x, y);
+  });
+  std::sort(light.begin(), light.end(), longer);
+  std::vector<SchedGroup> groups;
+  std::vector<Req> table;
+  table.reserve(count);
+  for (size_t i = 0; i < heavy.size();) {
+    const int cs = cluster_size(b->reqs[heavy[i]].Kp, cpc);
+    SchedGroup g{(int)table.size(), 0, 0, kFormCluster, cpc};
+    for (; i < heavy.size() && cluster_size(b->reqs[heavy[i]].Kp, cpc) == cs; ++i) {
+      table.push_back(b->reqs[heavy[i]]);
+      g.max_Kp = std::max(g.max_Kp, b->reqs[heavy[i]].Kp);
+      ++g.count;
+    }
+    groups.push_back(g);
+  }
+  if ((int)groups.size() > kMaxGroups) return fail(CPP_ERR_INVALID_ARG, "too many cluster groups");
+  SchedGroup lg{(int)table.size(), (int)light.size(), 0, groups.empty() ? kFormAuto : kFormCta, 0};
+  for (int r : light) {
+    table.push_back(b->reqs[r]);
+    lg.max_Kp = std::max(lg.max_Kp, b->reqs[r].Kp);
+  }
+  groups.push_back(lg);
+  for (size_t g = 0; g + 1 < groups.size(); ++g) {
+    if (!b->aux[g])
+      if (cpp_status e = cuda_status(cudaStreamCreateWithFlags(&b->aux[g], cudaStreamNonBlocking),
+                                     "batch schedule"))
+        return e;
+    if (!b->join[g])
+      if (cpp_status e = cuda_status(cudaEventCreateWithFlags(&b->join[g], cudaEventDisableTiming),
+                                     "batch schedule"))
+        return e;
+  }
+  if (!b->fork)
+    if (cpp_status e = cuda_status(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming),
+                                   "batch schedule"))
+      return e;
+  // pageable source: staged before cudaMemcpyAsync returns
+  if (cpp_status e = cuda_status(cudaMemcpyAsync(b->d_sched, table.data(), sizeof(Req) * count,
+                                                 cudaMemcpyHostToDevice, st), "batch schedule"))
+    return e;
+  b->groups = groups;
+  b->alpha = alpha;
+  b->cpc = cpc;
+  b->heavy = (int)heavy.size();
+  drop_graph(b);
+  return CPP_OK;
+}
+
+// The search's forward sweep under the current schedule.
+cudaError_t run_forward(cpp_batch* b, cudaStream_t st) {
+  const int objective = b->params.dp_objective;
+  const int ng = (int)b->groups.size();
+  auto launch = [&](const SchedGroup& g, cudaStream_t s) {
+    const BatchSrc src{b->d_sched + g.begin, b->d_robots};
+    return launch_forward(src, objective, b->n, g.count, g.max_Kp, g.form, g.cpc, s);
+  };
+  if (ng == 1) return launch(b->groups[0], st);
+  cudaError_t e = cudaEventRecord(b->fork, st);
+  for (int g = 0; g + 1 < ng && e == cudaSuccess; ++g) {
+    if ((e = cudaStreamWaitEvent(b->aux[g], b->fork, 0)) != cudaSuccess) break;
+    if ((e = launch(b->groups[g], b->aux[g])) != cudaSuccess) break;
+    e = cudaEventRecord(b->join[g], b->aux[g]);
+  }
+  if (e == cudaSuccess && b->groups[ng - 1].count > 0) e = launch(b->groups[ng - 1], st);
+  for (int g = 0; g + 1 < ng && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(st, b->join[g], 0);
+  return e;
+}
+
+cpp_status run_stages(cpp_batch* b, uint32_t stages, cudaStream_t st) {
+  if (stages & CPP_STAGE_MASK)
+    if (cpp_status e = cuda_status(launch_mask_batch(b->src, b->n, b->count, b->max_tasks,
+                                                     b->params, st), "batch/mask"))
+      return e;
+  if (stages & CPP_STAGE_LAYER_MIN)
+    if (cpp_status e = cuda_status(launch_dp_batch(b->src, CPP_STAGE_LAYER_MIN, b->params.dp_objective,
+                                                   b->n, b->count, b->max_T, b->max_Kp, st),
+                                   "batch/layer_min"))
+      return e;
+  if (stages & CPP_STAGE_DP_FORWARD)
+    if (cpp_status e = cuda_status(run_forward(b, st), "batch/forward")) return e;
+  if (stages & CPP_STAGE_BACKTRACK)
+    if (cpp_status e = cuda_status(launch_dp_batch(b->src, CPP_STAGE_BACKTRACK, b->params.dp_objective,
+                                                   b->n, b->count, b->max_T, b->max_Kp, st),
+                                   "batch/backtrack"))
+      return e;
+  if (stages & CPP_STAGE_LM)
+    if (cpp_status e = cuda_status(launch_lm_batch(b->src, b->n, b->count, b->max_T, b->params, st),
+                                   "batch/lm"))
+      return e;
+  if (stages & CPP_STAGE_CHECK)
+    return cuda_status(launch_check_batch(b->src, b->count, b->params, st), "batch/check");
+  return CPP_OK;
+}
+
+// Key of a batch in the tuning table: joints, objective, and coarse buckets of the
+// batch's shape (request count and longest T as powers of two, the cluster sizes
+// present, and how far the largest lattice stands above the mean, log2).
+std::string tune_key(const cpp_batch* b) {
+  long long total = 0, mx = 0;
+  unsigned cs_mask = 0;
+  for (int r = 0; r < b->count; ++r) {
+    total += b->edges[r];
+    mx = std::max(mx, b->edges[r]);
+    cs_mask |= 1u << cluster_size(b->reqs[r].Kp, 0);
+  }
+  auto lg2 = [](double v) { return v > 0 ? (int)std::lround(std::log2(v)) : -99; };
+  const double mean = (double)total / b->count;
+  char buf[160];
+  snprintf(buf, sizeof(buf), "n%d_obj%d_count%d_tmax%d_cs%x_skew%d_sms%d", b->n,
+           b->params.dp_objective, lg2(b->count), lg2(b->max_T), cs_mask, lg2(mx / mean),
+           device_sm_count());
+  return buf;
+}
+
+bool table_lookup(const char* path, const std::string& key, double* alpha, int* cpc) {
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char k[200];
+  double a, ms;
+  int c;
+  bool found = false;
+  while (fscanf(f, "%199s %lf %d %lf", k, &a, &c, &ms) == 4)
+    if (key == k) { *alpha = a; *cpc = c; found = true; }  // the last entry wins
+  fclose(f);
+  return found;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -388,6 +583,7 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
     return fail(CPP_ERR_INVALID_ARG, "workspace needs %zu bytes, 256-byte aligned", B.total);
   char* ws = static_cast<char*>(workspace);
   std::vector<Req> reqs(count);
+  std::vector<long long> edges(count);
   for (int r = 0; r < count; ++r) {
     const cpp_plan_desc_t& d = descs[r];
     const PlanLayout& L = B.L[r];
@@ -405,6 +601,7 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
     q.q_in = q.q_seed; q.q_out = d.q_out; q.pose_err = d.pose_err; q.report = d.report;
     q.status = dev_status ? dev_status + r : nullptr;
     reqs[r] = q;
+    edges[r] = (long long)(d.T - 1) * d.Kp * d.Kp;
   }
   cudaStream_t st = (cudaStream_t)stream;
   // pageable sources: the copies are staged before cudaMemcpyAsync returns
@@ -421,40 +618,166 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
                     reinterpret_cast<const cpp_robot_t*>(ws + B.robots)};
   b->params = *params;
   b->n = n; b->count = count; b->max_T = max_T; b->max_Kp = max_Kp; b->max_tasks = max_tasks;
+  b->d_sched = reinterpret_cast<Req*>(ws + B.sched);
+  b->d_robots = reinterpret_cast<const cpp_robot_t*>(ws + B.robots);
+  b->reqs = std::move(reqs);
+  b->edges = std::move(edges);
+  b->alpha = 0;
+  b->cpc = 0;
+  b->heavy = 0;
+  for (int g = 0; g < kMaxGroups; ++g) { b->aux[g] = nullptr; b->join[g] = nullptr; }
+  b->fork = nullptr;
+  b->graph = nullptr;
+  b->graph_stages = 0;
+  if (cpp_status e = set_schedule(b, kDefaultAlpha, 0, st)) {
+    cpp_batch_destroy(b);
+    return e;
+  }
   *out = b;
   return CPP_OK;
 }
 
 cpp_status cpp_batch_run(cpp_batch_t* b, uint32_t stages, cpp_stream_t stream) {
   if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (stages & CPP_STAGE_MASK)
-    if (cpp_status e = cuda_status(launch_mask_batch(b->src, b->n, b->count, b->max_tasks,
-                                                     b->params, st), "batch/mask"))
-      return e;
-  const unsigned dp = stages & (CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK);
-  if (dp)
-    if (cpp_status e = cuda_status(launch_dp_batch(b->src, dp, b->params.dp_objective, b->n,
-                                                   b->count, b->max_T, b->max_Kp, st), "batch/dp"))
-      return e;
-  if (stages & CPP_STAGE_LM)
-    if (cpp_status e = cuda_status(launch_lm_batch(b->src, b->n, b->count, b->max_T, b->params, st),
-                                   "batch/lm"))
-      return e;
-  if (stages & CPP_STAGE_CHECK)
-    return cuda_status(launch_check_batch(b->src, b->count, b->params, st), "batch/check");
-  return CPP_OK;
+  return run_stages(b, stages, (cudaStream_t)stream);
 }
 
 int32_t cpp_batch_launches(const cpp_batch_t* b, uint32_t stages) {
   if (!b) return 0;
   int c = 0;
-  for (unsigned s = 1; s <= CPP_STAGE_CHECK; s <<= 1)
-    if (stages & s) ++c;
+  for (unsigned s = 1; s <= CPP_STAGE_CHECK; s <<= 1) {
+    if (!(stages & s)) continue;
+    if (s != CPP_STAGE_DP_FORWARD) { ++c; continue; }
+    for (const SchedGroup& g : b->groups) c += g.count > 0 ? 1 : 0;
+  }
   return c;
 }
 
-void cpp_batch_destroy(cpp_batch_t* b) { delete b; }
+cpp_status cpp_batch_set_split(cpp_batch_t* b, double alpha, int32_t cands_per_cta,
+                               cpp_stream_t stream) {
+  if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
+  if (!std::isfinite(alpha) || alpha < 0) return fail(CPP_ERR_INVALID_ARG, "alpha must be >= 0");
+  if (cands_per_cta != 0 && cands_per_cta != 64 && cands_per_cta != 128)
+    return fail(CPP_ERR_INVALID_ARG, "cands_per_cta must be 0, 64 or 128");
+  return set_schedule(b, alpha, cands_per_cta, (cudaStream_t)stream);
+}
+
+cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t stream,
+                          cpp_tune_result_t* res) {
+  if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  cpp_tune_result_t out;
+  memset(&out, 0, sizeof(out));
+  out.dp_ms = out.dp_ms_unsplit = -1.f;
+  const std::string key = tune_key(b);
+  double alpha = 0;
+  int cpc = 0;
+  if (table_lookup(table_path, key, &alpha, &cpc)) {
+    if (cpp_status e = set_schedule(b, alpha, cpc, st)) return e;
+    out.from_table = 1;
+  } else {
+    // node costs first: the sweeps read them
+    if (cpp_status e = run_stages(b, CPP_STAGE_MASK | CPP_STAGE_LAYER_MIN, st)) return e;
+    static const double kAlphas[] = {8.0, 4.0, 3.0, 2.0, 1.5, 1.0, 0.75, 0.5,
+                                     0.35, 0.25, 0.15, 0.1, 0.05, 1e-9};
+    struct Cand { double alpha; int cpc; };
+    std::vector<Cand> cands{{0.0, 0}};
+    for (int c : {64, 128})
+      for (double a : kAlphas) cands.push_back({a, c});
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cpp_status e = cuda_status(cudaEventCreate(&e0), "cpp_batch_tune")) return e;
+    if (cpp_status e = cuda_status(cudaEventCreate(&e1), "cpp_batch_tune")) {
+      cudaEventDestroy(e0);
+      return e;
+    }
+    float best_ms = HUGE_VALF;
+    Cand best{0.0, 0};
+    int last_heavy = -1, last_cpc = -1;
+    cpp_status err = CPP_OK;
+    for (const Cand& c : cands) {
+      if ((err = set_schedule(b, c.alpha, c.cpc, st)) != CPP_OK) break;
+      if (b->heavy == last_heavy && c.cpc == last_cpc) continue;  // same split as before
+      last_heavy = b->heavy;
+      last_cpc = c.cpc;
+      if (c.alpha > 0 && b->heavy == 0) continue;                 // same as alpha = 0
+      float ms = HUGE_VALF;
+      for (int rep = 0; rep < 3 && err == CPP_OK; ++rep) {  // the first run warms up
+        cudaError_t ce = cudaEventRecord(e0, st);
+        if (ce == cudaSuccess) ce = run_forward(b, st);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float t = 0;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+        err = cuda_status(ce, "cpp_batch_tune");
+        if (rep > 0) ms = std::min(ms, t);
+      }
+      if (err != CPP_OK) break;
+      ++out.timed;
+      if (c.alpha == 0.0) out.dp_ms_unsplit = ms;
+      if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != CPP_OK) return err;
+    if (cpp_status e = set_schedule(b, best.alpha, best.cpc, st)) return e;
+    out.dp_ms = best_ms;
+    if (table_path) {
+      FILE* f = fopen(table_path, "a");
+      if (!f) return fail(CPP_ERR_INVALID_ARG, "cannot append to tuning table %s", table_path);
+      fprintf(f, "%s %.9g %d %.4f\n", key.c_str(), best.alpha, best.cpc, best_ms);
+      fclose(f);
+    }
+  }
+  out.alpha = b->alpha;
+  out.cands_per_cta = b->cpc;
+  out.heavy = b->heavy;
+  out.forward_launches = 0;
+  for (const SchedGroup& g : b->groups) out.forward_launches += g.count > 0 ? 1 : 0;
+  if (res) *res = out;
+  return CPP_OK;
+}
+
+cpp_status cpp_batch_capture(cpp_batch_t* b, uint32_t stages, cpp_stream_t stream) {
+  if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!st) return fail(CPP_ERR_INVALID_ARG, "capture needs a created stream, not the default stream");
+  drop_graph(b);
+  if (cpp_status e = cuda_status(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal),
+                                 "cpp_batch_capture"))
+    return e;
+  const cpp_status run = run_stages(b, stages, st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(st, &g);
+  if (run != CPP_OK) {
+    if (g) cudaGraphDestroy(g);
+    return run;
+  }
+  if (cpp_status e = cuda_status(ee, "cpp_batch_capture")) return e;
+  cudaGraphExec_t x = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (cpp_status e = cuda_status(ie, "cpp_batch_capture")) return e;
+  b->graph = x;
+  b->graph_stages = stages;
+  return CPP_OK;
+}
+
+cpp_status cpp_batch_replay(cpp_batch_t* b, cpp_stream_t stream) {
+  if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
+  if (!b->graph) return fail(CPP_ERR_INVALID_ARG, "no captured graph (cpp_batch_capture first)");
+  return cuda_status(cudaGraphLaunch(b->graph, (cudaStream_t)stream), "cpp_batch_replay");
+}
+
+void cpp_batch_destroy(cpp_batch_t* b) {
+  if (!b) return;
+  drop_graph(b);
+  for (int g = 0; g < kMaxGroups; ++g) {
+    if (b->aux[g]) cudaStreamDestroy(b->aux[g]);
+    if (b->join[g]) cudaEventDestroy(b->join[g]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
 
 cpp_status cpp_plan_batch(const cpp_robot_t* robots, int32_t n_robots, const cpp_params_t* params,
                           const cpp_plan_desc_t* descs, int32_t count, void* workspace,

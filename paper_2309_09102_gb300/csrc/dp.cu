@@ -185,8 +185,8 @@ static cudaError_t launch_dp_t(const Src& s, unsigned stages, int objective, int
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (stages & CPP_STAGE_DP_FORWARD) {
-    e = objective == CPP_DP_MINMAX ? launch_forward_minmax(s, n, nreq, max_Kp, st)
-                                   : launch_forward_sum(s, n, nreq, max_Kp, st);
+    e = objective == CPP_DP_MINMAX ? launch_forward_minmax(s, n, nreq, max_Kp, kFormAuto, 0, st)
+                                   : launch_forward_sum(s, n, nreq, max_Kp, kFormAuto, 0, st);
     if (e != cudaSuccess) return e;
   }
   if (stages & CPP_STAGE_BACKTRACK) {
@@ -204,6 +204,37 @@ cudaError_t launch_dp(const SingleSrc& s, unsigned stages, int objective, cudaSt
 cudaError_t launch_dp_batch(const BatchSrc& s, unsigned stages, int objective, int n, int nreq,
                             int max_T, int max_Kp, cudaStream_t st) {
   return launch_dp_t(s, stages, objective, n, nreq, max_T, max_Kp, st);
+}
+
+cudaError_t launch_forward(const BatchSrc& s, int objective, int n, int nreq, int max_Kp, int form,
+                           int cpc, cudaStream_t st) {
+  return objective == CPP_DP_MINMAX ? launch_forward_minmax(s, n, nreq, max_Kp, form, cpc, st)
+                                    : launch_forward_sum(s, n, nreq, max_Kp, form, cpc, st);
+}
+
+int device_sm_count() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
+  return n;
+}
+
+// Successor candidates per CTA of the cluster form: cpc (64 or 128) or the
+// default (64 up to Kp = 512, 128 above), as long as the cluster has 2..8 CTAs.
+int cluster_succ(int Kp, int cpc) {
+  if (Kp <= 64 || Kp > 1024) return 0;
+  const int S = cpc ? cpc : (Kp <= 512 ? 64 : 128);
+  if (S != 64 && S != 128) return 0;
+  const int CS = (Kp + S - 1) / S;
+  return CS >= 2 && CS <= 8 ? S : 0;
+}
+
+int cluster_size(int Kp, int cpc) {
+  const int S = cluster_succ(Kp, cpc);
+  return S ? (Kp + S - 1) / S : 0;
 }
 
 }  // namespace cppflow

@@ -557,14 +557,12 @@ static int sm_count() {
 }
 
 template <int NJ, int OBJ, class Src>
-static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
-  if (max_Kp > 64) {
-    const int Rc = max_Kp <= 512 ? 2 : 4;
-    const int CS = (max_Kp + 32 * Rc - 1) / (32 * Rc);
-    if (nreq * CS <= sm_count())
-      return Rc == 2 ? launch_fwdc_r<NJ, 2, OBJ>(s, nreq, max_Kp, st)
-                     : launch_fwdc_r<NJ, 4, OBJ>(s, nreq, max_Kp, st);
-  }
+static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, int form, int cpc,
+                                 cudaStream_t st) {
+  const int S = cluster_succ(max_Kp, cpc), CS = cluster_size(max_Kp, cpc);
+  if (S > 0 && form != kFormCta && (form == kFormCluster || nreq * CS <= sm_count()))
+    return S == 64 ? launch_fwdc_r<NJ, 2, OBJ>(s, nreq, max_Kp, st)
+                   : launch_fwdc_r<NJ, 4, OBJ>(s, nreq, max_Kp, st);
   const int R = (max_Kp + kDp3Group - 1) / kDp3Group;
   if (R <= 1) return launch_fwd3_r<NJ, 1, OBJ>(s, nreq, max_Kp, st);
   if (R <= 2) return launch_fwd3_r<NJ, 2, OBJ>(s, nreq, max_Kp, st);
@@ -572,14 +570,17 @@ static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, cudaStream_
   return launch_fwd3_r<NJ, 8, OBJ>(s, nreq, max_Kp, st);
 }
 
-// Forward sweep for n joints: the fast forms for n in {6, 7, 9} and Kp <= 1024,
-// the generic kernel otherwise.
+// Forward sweep for n joints: the fast forms for n in {6, 7, 9} and Kp <= 1024
+// (form: kFormAuto picks clusters when one wave of them covers the requests,
+// kFormCta / kFormCluster force one; cpc: successor candidates per CTA of the
+// cluster form, 64 or 128, 0 for the default), the generic kernel otherwise.
 template <int OBJ, class Src>
-static cudaError_t launch_forward_t(const Src& s, int n, int nreq, int max_Kp, cudaStream_t st) {
+static cudaError_t launch_forward_t(const Src& s, int n, int nreq, int max_Kp, int form, int cpc,
+                                    cudaStream_t st) {
   const bool fast = max_Kp <= 1024;
-  if (fast && n == 7) return launch_fwd_nj<7, OBJ>(s, nreq, max_Kp, st);
-  if (fast && n == 9) return launch_fwd_nj<9, OBJ>(s, nreq, max_Kp, st);
-  if (fast && n == 6) return launch_fwd_nj<6, OBJ>(s, nreq, max_Kp, st);
+  if (fast && n == 7) return launch_fwd_nj<7, OBJ>(s, nreq, max_Kp, form, cpc, st);
+  if (fast && n == 9) return launch_fwd_nj<9, OBJ>(s, nreq, max_Kp, form, cpc, st);
+  if (fast && n == 6) return launch_fwd_nj<6, OBJ>(s, nreq, max_Kp, form, cpc, st);
   const size_t smem = dp_smem_bytes(n, max_Kp);
   cudaError_t e = allow_smem(dp_forward_generic<OBJ, Src>, smem);
   if (e != cudaSuccess) return e;

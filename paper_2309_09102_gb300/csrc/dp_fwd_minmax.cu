@@ -3,11 +3,13 @@
 
 namespace cppflow {
 
-cudaError_t launch_forward_minmax(const SingleSrc& s, int n, int nreq, int max_Kp, cudaStream_t st) {
-  return launch_forward_t<1>(s, n, nreq, max_Kp, st);
+cudaError_t launch_forward_minmax(const SingleSrc& s, int n, int nreq, int max_Kp, int form,
+                              int cpc, cudaStream_t st) {
+  return launch_forward_t<1>(s, n, nreq, max_Kp, form, cpc, st);
 }
-cudaError_t launch_forward_minmax(const BatchSrc& s, int n, int nreq, int max_Kp, cudaStream_t st) {
-  return launch_forward_t<1>(s, n, nreq, max_Kp, st);
+cudaError_t launch_forward_minmax(const BatchSrc& s, int n, int nreq, int max_Kp, int form,
+                              int cpc, cudaStream_t st) {
+  return launch_forward_t<1>(s, n, nreq, max_Kp, form, cpc, st);
 }
 
 }  // namespace cppflow

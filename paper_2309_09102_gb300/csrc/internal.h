@@ -29,10 +29,24 @@ cudaError_t launch_dp_batch(const BatchSrc& s, unsigned stages, int objective, i
                             int max_T, int max_Kp, cudaStream_t st);
 
 // dp_fwd_sum.cu, dp_fwd_minmax.cu
-cudaError_t launch_forward_sum(const SingleSrc& s, int n, int nreq, int max_Kp, cudaStream_t st);
-cudaError_t launch_forward_sum(const BatchSrc& s, int n, int nreq, int max_Kp, cudaStream_t st);
-cudaError_t launch_forward_minmax(const SingleSrc& s, int n, int nreq, int max_Kp, cudaStream_t st);
-cudaError_t launch_forward_minmax(const BatchSrc& s, int n, int nreq, int max_Kp, cudaStream_t st);
+constexpr int kFormAuto = 0;     // clusters when one wave of them covers the requests
+constexpr int kFormCta = 1;      // one CTA per request (throughput form)
+constexpr int kFormCluster = 2;  // one thread-block cluster per request (latency form)
+cudaError_t launch_forward_sum(const SingleSrc& s, int n, int nreq, int max_Kp, int form, int cpc,
+                               cudaStream_t st);
+cudaError_t launch_forward_sum(const BatchSrc& s, int n, int nreq, int max_Kp, int form, int cpc,
+                               cudaStream_t st);
+cudaError_t launch_forward_minmax(const SingleSrc& s, int n, int nreq, int max_Kp, int form,
+                                  int cpc, cudaStream_t st);
+cudaError_t launch_forward_minmax(const BatchSrc& s, int n, int nreq, int max_Kp, int form,
+                                  int cpc, cudaStream_t st);
+// the forward sweep of one objective over nreq requests of a table (cpc: successor
+// candidates per CTA of the cluster form, 0 for the default)
+cudaError_t launch_forward(const BatchSrc& s, int objective, int n, int nreq, int max_Kp, int form,
+                           int cpc, cudaStream_t st);
+int cluster_succ(int Kp, int cpc);  // successors per CTA of the cluster form (0: no cluster form)
+int cluster_size(int Kp, int cpc);  // CTAs per cluster (0: no cluster form)
+int device_sm_count();     // SMs of the current device
 
 // lm.cu
 cudaError_t launch_lm(const SingleSrc& s, const cpp_params_t& P, bool want_err, cudaStream_t st);

@@ -210,7 +210,7 @@ static int size_class(const Request* r) {
 // the others up to max_batch.
 static int class_cap(const Request* r, int max_batch, int sms) {
   const bool heavy = r->Kp > 512 || r->T > 1024;
-  const int cs = (r->Kp + 32 * (r->Kp <= 512 ? 2 : 4) - 1) / (32 * (r->Kp <= 512 ? 2 : 4));
+  const int cs = cluster_size(r->Kp, 0);
   return heavy ? std::max(1, std::min(max_batch, sms / std::max(1, cs))) : max_batch;
 }
 

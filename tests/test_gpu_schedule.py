@@ -1,0 +1,153 @@
+"""Scheduling of the search stage for uneven batches, the tuner and CUDA graph
+replay: every schedule gives bit-identical plans, equal to the oracle's FP32
+search on the same node costs.
+
+The batch mixes short and long requests with K in {128, 256, 512}, so a small
+heavy threshold splits it into one cluster launch per cluster size (2, 4 and 8
+CTAs) beside the one-CTA launch of the rest.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import problems
+from gpu_util import TAU_POS, TAU_ROT, dev, params_pair, run_mask, torch
+from paper_2309_09102_gb300 import cppflow, synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(40, 128), (300, 512), (60, 256), (200, 512), (80, 128), (250, 256), (30, 512),
+          (120, 128), (300, 256), (45, 512), (150, 128), (90, 256), (260, 512), (35, 128)]
+
+
+def workload(r, T, K):
+    return synth.Workload(f"sched_r{r}", 7, T, K, 0.05, 0.25, 0.05, 20, 1e-3,
+                          arm_seed=100 + (r % 8), path_seed=5100 + r, cand_seed=5200 + r)
+
+
+@pytest.fixture(scope="module")
+def batch_setup():
+    tt = torch()
+    pbs = [problems.build(workload(r, T, K)) for r, (T, K) in enumerate(SHAPES)]
+    _, cp = params_pair(lm_iters=20)
+    robots = [cppflow.robot_from_arm(pb.arm) for pb in pbs]
+    bufs, descs = [], []
+    for r, pb in enumerate(pbs):
+        T, n, Kp = pb.cand.shape
+        b = dict(cand=dev(pb.cand), targets=dev(pb.targets),
+                 sel=tt.empty(T, dtype=tt.int32, device="cuda:0"),
+                 q=tt.empty(T, n, dtype=tt.float32, device="cuda:0"),
+                 err=tt.empty(T, 2, dtype=tt.float64, device="cuda:0"),
+                 rep=tt.zeros(cppflow.REPORT_BYTES, dtype=tt.uint8, device="cuda:0"),
+                 best=tt.empty(1, dtype=tt.float32, device="cuda:0"))
+        bufs.append(b)
+        descs.append(cppflow.PlanDesc(T, pb.K, Kp, r, b["cand"].data_ptr(), b["targets"].data_ptr(),
+                                      b["sel"].data_ptr(), b["q"].data_ptr(), b["err"].data_ptr(),
+                                      b["rep"].data_ptr(), b["best"].data_ptr()))
+    ws = tt.empty(cppflow.plan_batch_workspace_size(descs, robots), dtype=tt.uint8, device="cuda:0")
+    st = tt.zeros(len(descs), dtype=tt.int32, device="cuda:0")
+    stream = tt.cuda.Stream()
+    batch = cppflow.Batch(robots, cp, descs, ws, st, stream)
+    return dict(pbs=pbs, cp=cp, robots=robots, bufs=bufs, descs=descs, ws=ws, st=st,
+                stream=stream, batch=batch)
+
+
+def clear(S):
+    for b in S["bufs"]:
+        for k in ("sel", "q", "err", "best"):
+            b[k].fill_(-7)
+        b["rep"].zero_()
+    S["st"].zero_()
+
+
+def results(S):
+    torch().cuda.synchronize()
+    assert np.all(S["st"].cpu().numpy() == 0)
+    return [dict(sel=b["sel"].cpu().numpy(), best=b["best"].cpu().numpy(), q=b["q"].cpu().numpy(),
+                 err=b["err"].cpu().numpy(), rep=b["rep"].cpu().numpy()) for b in S["bufs"]]
+
+
+def assert_same(a, b):
+    for x, y in zip(a, b):
+        for k in x:
+            np.testing.assert_array_equal(x[k], y[k], err_msg=k)
+
+
+def run_with(S, alpha, cpc=0):
+    clear(S)
+    S["batch"].set_split(alpha, cpc, S["stream"])
+    S["batch"].run(cppflow.STAGE_ALL, S["stream"])
+    S["stream"].synchronize()
+    return results(S)
+
+
+def test_every_split_gives_the_same_plans_as_the_oracle(batch_setup):
+    S = batch_setup
+    base = run_with(S, 0.0)
+    assert S["batch"].launches(cppflow.STAGE_DP_FORWARD) == 1
+    # the oracle's FP32 search on the GPU's node costs, and valid refined plans
+    for r, pb in enumerate(S["pbs"]):
+        g = run_mask(S["robots"][r], S["cp"], pb.cand, pb.targets, pb.K)
+        ref = oracle.dp_f32(pb.cand, g.pen, pb.K)
+        np.testing.assert_array_equal(base[r]["sel"], ref["sel"])
+        assert float(base[r]["best"][0]) == float(ref["best"])
+        rep = cppflow.report_from_bytes(base[r]["rep"].tobytes())
+        assert rep["valid"] == 1 and rep["max_pos"] <= TAU_POS and rep["max_rot"] <= TAU_ROT
+    # a small threshold: one cluster launch per cluster size (2, 4, 8 CTAs), no one-CTA launch
+    split = run_with(S, 0.01)
+    assert S["batch"].launches(cppflow.STAGE_DP_FORWARD) == 3
+    assert_same(split, base)
+    # 128 candidates per cluster CTA: K = 256 and K = 512 as clusters of 2 and 4 CTAs,
+    # K = 128 (a single CTA's worth) on the one-CTA form
+    assert_same(run_with(S, 0.01, 128), base)
+    assert S["batch"].launches(cppflow.STAGE_DP_FORWARD) == 3
+    # the default threshold (the two K = 512, T = 300 requests and a few more run as clusters)
+    assert_same(run_with(S, 2.0), base)
+    assert_same(run_with(S, 0.5, 128), base)
+
+
+def test_graph_replay_equals_run(batch_setup):
+    S = batch_setup
+    base = run_with(S, 1.0)
+    assert S["batch"].launches(cppflow.STAGE_DP_FORWARD) >= 2   # the fork/join is captured too
+    S["batch"].capture(cppflow.STAGE_ALL, S["stream"])
+    clear(S)
+    torch().cuda.synchronize()
+    S["batch"].replay(S["stream"])
+    S["stream"].synchronize()
+    assert_same(results(S), base)
+    clear(S)
+    torch().cuda.synchronize()
+    for _ in range(3):
+        S["batch"].replay(S["stream"])
+    S["stream"].synchronize()
+    assert_same(results(S), base)
+    # the legacy default stream cannot be captured
+    rc = cppflow.lib().cpp_batch_capture(S["batch"].handle, cppflow.STAGE_ALL, None)
+    assert rc == cppflow.ERR_INVALID_ARG
+
+
+def test_tuner_and_its_table(batch_setup, tmp_path):
+    S = batch_setup
+    table = tmp_path / "tune.txt"
+    r1 = S["batch"].tune(str(table), S["stream"])
+    assert r1["timed"] >= 2 and r1["from_table"] == 0
+    assert r1["dp_ms"] > 0 and r1["dp_ms"] <= r1["dp_ms_unsplit"]
+    lines = table.read_text().split("\n")
+    assert len([x for x in lines if x]) == 1
+    key, alpha, cpc, ms = lines[0].split()
+    assert key.startswith("n7_obj0_") and float(alpha) == pytest.approx(r1["alpha"], rel=1e-6)
+    assert int(cpc) == r1["cands_per_cta"]
+    after = results_after_run(S)
+    r2 = S["batch"].tune(str(table), S["stream"])
+    assert r2["from_table"] == 1 and r2["timed"] == 0
+    assert r2["alpha"] == pytest.approx(r1["alpha"], rel=1e-6) and r2["heavy"] == r1["heavy"]
+    assert_same(results_after_run(S), after)
+    assert_same(after, run_with(S, 0.0))
+
+
+def results_after_run(S):
+    clear(S)
+    S["batch"].run(cppflow.STAGE_ALL, S["stream"])
+    S["stream"].synchronize()
+    return results(S)
