@@ -41,6 +41,10 @@ METRIC = "served plans/s, T=300 K=512 7-DoF, valid at <=1mm/<=0.1deg"
 SMS = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) of one dp3_forward_kernel launch on this workload (304 requests,
+# T = 300, K = 512, n = 7), from one ncu capture of the current kernel build
+# (profiles/dp3_forward_single_t300_k512_b304.md); None once the kernel changes.
+DP3_TRAFFIC_BYTES = 1.498145e9 + 92.664576e6
 
 
 def workload_requests(B: int, rank: int):
@@ -530,7 +534,9 @@ def run_cuda(args, rank: int, world: int, dist):
     peak = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     roof = {"bound": "alu", "kernel": "dp3_forward_kernel", "achieved": round(achieved, 3),
             "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-            "traffic": None,
+            "traffic": DP3_TRAFFIC_BYTES if (B, T, K, n) == (304, 300, 512, 7) else None,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "algorithmic_bytes": B * T * Kp * (4 * n + 4) + B * T * synth.pad_k(K, 8) * 2,
             "ops": f"{ops_per_edge} FP32 ALU ops per edge (n sub, n-1 abs-max, add, min) x "
                    f"{edges:.4g} edges per launch",
             "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max clock (derived, not measured)",

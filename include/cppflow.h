@@ -159,8 +159,8 @@ cpp_status cpp_mask(const cpp_robot_t* robot, const cpp_params_t* params, const 
  * re-search reuses a resident lattice: allocate Kp for the largest K expected,
  * mask and search the first K0 lanes, and when the search path's mjac is too
  * large (§III-B: 12 deg) write more candidates into lanes [K0, K1), mask just
- * those, and search again with K = K1 -- "collision and joint limit checks
- * performed on the initial plans are retained". */
+ * those, and search again with K = K1; as in §III-B, the checks already made
+ * on the first candidates are kept, not redone. */
 cpp_status cpp_mask_range(const cpp_robot_t* robot, const cpp_params_t* params,
                           const float* cand, const double* targets, int32_t T, int32_t K,
                           int32_t Kp, int32_t k_begin, uint8_t* mask, float* pen, float* err,
@@ -184,8 +184,8 @@ cpp_status cpp_mask_range(const cpp_robot_t* robot, const cpp_params_t* params,
 size_t cpp_dp_workspace_size(int32_t T, int32_t Kp);
 
 /* The search with a choice of objective (§III-B). CPP_DP_SUM is cpp_dp_search.
- * CPP_DP_MINMAX is the paper's own cost, "the minimum mjac achievable if the node
- * is included": C_0 = r_0, C_{i+1}[k'] = max(min_k max(C_i[k], d(k, k')), r_{i+1}[k']),
+ * CPP_DP_MINMAX is the paper's own cost: a node costs the smallest mjac that any
+ * path through it can reach. C_0 = r_0, C_{i+1}[k'] = max(min_k max(C_i[k], d(k, k')), r_{i+1}[k']),
  * so a path costs the larger of its largest per-step L-inf jump and its largest
  * relative node cost (a near-limit cost of 10 outweighs any revolute jump); max
  * and min are exact, so it involves no rounding. search_mjac [1] FP32 (or NULL)

@@ -266,9 +266,9 @@ static float layer_min_f32(const float* pen_i, int K) {
     return isinf(m) ? 0.0f : m;
 }
 
-/* Objective 1 is the paper's own: "the cost at each node is the minimum mjac
- * achievable if the node is included" -- a bottleneck (min-max) path. With the
- * node costs it reads
+/* Objective 1 is the paper's own (§III-B): a node costs the smallest mjac that any
+ * path through it can reach -- a bottleneck (min-max) path. With the node costs
+ * it reads
  *   C_0[k] = r_0[k],  C_{i+1}[k'] = fmaxf( min_k fmaxf(C_i[k], d(k, k')), r_{i+1}[k'] ),
  * i.e. a path costs max(largest per-step L-inf jump, largest relative node cost);
  * a node cost of 10 exceeds any revolute jump (pi), as the paper intends. max

@@ -56,8 +56,8 @@ __device__ __forceinline__ float linf_rec(const uint64_t (&own)[Rec<NJ>::NP], co
 constexpr int kDp2Tile = 16;  // predecessor nodes per tile of the deferred argmin
 
 // The search objective (§III-B): OBJ 0 sums the per-step L-inf jumps (C + d);
-// OBJ 1 is the paper's own "minimum mjac achievable", a bottleneck path
-// (max(C, d)). Node costs combine the same way. Both are exact IEEE operations.
+// OBJ 1 is the paper's own, the smallest mjac a path through the node can
+// reach: a bottleneck path (max(C, d)). Node costs combine the same way. Both are exact IEEE operations.
 template <int OBJ>
 __device__ __forceinline__ float comb(float c, float d) {
   return OBJ ? fmaxf(c, d) : c + d;
