@@ -87,6 +87,9 @@ def lib():
             "orc_lm": (None, [P, P, P, P, C.c_int, P, P, P]),
             "orc_check": (None, [P, P, P, P, C.c_int, P, P]),
             "orc_plan": (C.c_int, [P, P, P, P, C.c_int, C.c_int, C.c_int, P, P, P, P, P]),
+            "orc_block_tridiag_solve": (C.c_int, [C.c_int, C.c_int, P, P, P, P]),
+            "orc_diff_step": (C.c_int, [P, P, C.c_int, C.c_double, P]),
+            "orc_lm_smooth": (None, [P, P, P, P, C.c_int, C.c_int, C.c_double, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -251,6 +254,39 @@ def lm(robot: Robot, params: Params, q_in, targets, want_hist: bool = False):
     lib().orc_lm(C.byref(robot), C.byref(params), _p(q_in), _p(targets), T, _p(q_out),
                  _p(hist), _p(iters))
     return q_out, hist, iters
+
+
+# ---------------------------------------------------------------- §III-C trajectory length
+def block_tridiag_solve(Dg, Off, b):
+    """x = A^{-1} b for the SPD block-tridiagonal A with diagonal blocks Dg [T][n][n] and
+    upper blocks Off [T-1][n][n] (block Cholesky). Returns (x, ok)."""
+    Dg = _f64(Dg)
+    T, n, _ = Dg.shape
+    Off = _f64(Off).reshape(max(T - 1, 0), n, n) if T > 1 else np.zeros((1, n, n))
+    b = _f64(b).reshape(T, n)
+    x = np.zeros((T, n))
+    ok = lib().orc_block_tridiag_solve(T, n, _p(Dg), _p(Off), _p(b), _p(x))
+    return x, bool(ok)
+
+
+def diff_step(robot: Robot, q, lambda_d: float):
+    """One damped step on the differencing residual, clamped to the limits."""
+    q = _f64(q).reshape(-1, robot.n)
+    out = np.zeros_like(q)
+    ok = lib().orc_diff_step(C.byref(robot), _p(q), q.shape[0], float(lambda_d), _p(out))
+    return out, bool(ok)
+
+
+def lm_smooth(robot: Robot, params: Params, q_in, targets, rounds: int, lambda_d: float):
+    """Pose phases alternating with trajectory-length steps; returns (q, steps taken)."""
+    q_in = _f64(q_in).reshape(-1, robot.n)
+    T = q_in.shape[0]
+    targets = _f64(targets).reshape(T, 7)
+    out = np.zeros_like(q_in)
+    taken = np.zeros(1, np.int32)
+    lib().orc_lm_smooth(C.byref(robot), C.byref(params), _p(q_in), _p(targets), T, int(rounds),
+                        float(lambda_d), _p(out), _p(taken))
+    return out, int(taken[0])
 
 
 # ---------------------------------------------------------------- §II report

@@ -598,6 +598,183 @@ void orc_check(const orc_robot* r, const orc_params* P, const double* q,
     rep->valid = (rep->n_pose_fail == 0 && rep->n_limit_fail == 0 && rep->n_jump_fail == 0);
 }
 
+/* ------------------------------------------------------------------------- */
+/* §III-C non-stationary objective: the trajectory-length (differencing) step */
+/* ------------------------------------------------------------------------- */
+
+/* Cholesky factor L (lower, row-major) of an SPD n x n matrix; 0 on a
+ * non-positive or non-finite pivot. */
+static int chol_factor(int n, const double* A, double* L) {
+    memset(L, 0, sizeof(double) * (size_t)n * n);
+    for (int j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int k = 0; k < j; ++k) s -= L[j * n + k] * L[j * n + k];
+        if (!(s > 0.0) || !isfinite(s)) return 0;
+        L[j * n + j] = sqrt(s);
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = t / L[j * n + j];
+        }
+    }
+    return 1;
+}
+
+/* x = (L L^T)^{-1} b */
+static void chol_apply(int n, const double* L, const double* b, double* x) {
+    double y[ORC_MAXJ];
+    for (int i = 0; i < n; ++i) {
+        double t = b[i];
+        for (int k = 0; k < i; ++k) t -= L[i * n + k] * y[k];
+        y[i] = t / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double t = y[i];
+        for (int k = i + 1; k < n; ++k) t -= L[k * n + i] * x[k];
+        x[i] = t / L[i * n + i];
+    }
+}
+
+/* Block-tridiagonal SPD solve by block Cholesky (the block Thomas algorithm),
+ * FP64. Diagonal blocks Dg[i] (i = 0..T-1), upper blocks Off[i] = A_{i,i+1} =
+ * A_{i+1,i}^T (i = 0..T-2), all n x n row-major:
+ *   S_0 = Dg[0],  S_i = Dg[i] - Off[i-1]^T S_{i-1}^{-1} Off[i-1]
+ *   y_0 = b_0,    y_i = b_i  - Off[i-1]^T S_{i-1}^{-1} y_{i-1}
+ *   x_{T-1} = S_{T-1}^{-1} y_{T-1},  x_i = S_i^{-1} (y_i - Off[i] x_{i+1})
+ * Returns 0 if some S_i is not positive definite. */
+int orc_block_tridiag_solve(int T, int n, const double* Dg, const double* Off, const double* b,
+                            double* x) {
+    const size_t nn = (size_t)n * n;
+    double* Lf = (double*)malloc(sizeof(double) * nn * (size_t)T);
+    double* y = (double*)malloc(sizeof(double) * (size_t)n * T);
+    int ok = 1;
+    for (int i = 0; i < T && ok; ++i) {
+        double S[ORC_MAXJ * ORC_MAXJ];
+        memcpy(S, Dg + nn * i, sizeof(double) * nn);
+        memcpy(y + (size_t)n * i, b + (size_t)n * i, sizeof(double) * n);
+        if (i > 0) {
+            const double* B = Off + nn * (i - 1);      /* A_{i-1,i} */
+            const double* Lp = Lf + nn * (i - 1);
+            /* Z = S_{i-1}^{-1} B column by column; S -= B^T Z */
+            double Z[ORC_MAXJ * ORC_MAXJ], col[ORC_MAXJ], zc[ORC_MAXJ];
+            for (int c = 0; c < n; ++c) {
+                for (int r = 0; r < n; ++r) col[r] = B[r * n + c];
+                chol_apply(n, Lp, col, zc);
+                for (int r = 0; r < n; ++r) Z[r * n + c] = zc[r];
+            }
+            for (int a = 0; a < n; ++a)
+                for (int c = 0; c < n; ++c) {
+                    double t = 0.0;
+                    for (int r = 0; r < n; ++r) t += B[r * n + a] * Z[r * n + c];
+                    S[a * n + c] -= t;
+                }
+            /* y_i -= B^T S_{i-1}^{-1} y_{i-1} */
+            double w[ORC_MAXJ];
+            chol_apply(n, Lp, y + (size_t)n * (i - 1), w);
+            for (int a = 0; a < n; ++a) {
+                double t = 0.0;
+                for (int r = 0; r < n; ++r) t += B[r * n + a] * w[r];
+                y[(size_t)n * i + a] -= t;
+            }
+        }
+        ok = chol_factor(n, S, Lf + nn * i);
+    }
+    if (ok) {
+        for (int i = T - 1; i >= 0; --i) {
+            double rhs[ORC_MAXJ];
+            for (int a = 0; a < n; ++a) rhs[a] = y[(size_t)n * i + a];
+            if (i + 1 < T) {
+                const double* B = Off + nn * i;        /* A_{i,i+1} */
+                for (int a = 0; a < n; ++a) {
+                    double t = 0.0;
+                    for (int c = 0; c < n; ++c) t += B[a * n + c] * x[(size_t)n * (i + 1) + c];
+                    rhs[a] -= t;
+                }
+            }
+            chol_apply(n, Lf + nn * i, rhs, x + (size_t)n * i);
+        }
+    }
+    free(Lf);
+    free(y);
+    return ok;
+}
+
+/* §III-C "Trajectory length": one LM step on the differencing residual
+ * r_diff = [q_{i+1} - q_i], i = 0..T-2 (the collision rows of r_diff are not
+ * built). Row block i of its Jacobian holds -I at waypoint i and +I at i+1, so
+ *   J^T J + lambda_d I: diagonal blocks (c_i + lambda_d) I with c_i the number
+ *     of differences that touch waypoint i (1 at the ends, 2 inside, 0 if
+ *     T = 1), off-diagonal blocks -I;
+ *   J^T r_diff: block i = (q_i - q_{i-1}) - (q_{i+1} - q_i), absent terms 0;
+ *   delta = -(J^T J + lambda_d I)^{-1} J^T r_diff   (orc_block_tridiag_solve),
+ *   q' = clamp(q + delta, lo, hi).
+ * The residual is linear, so before the clamp the step lowers |r_diff|^2 / 2
+ * for any lambda_d > 0. Returns 0 if the solve failed (q' = q). */
+int orc_diff_step(const orc_robot* r, const double* q_in, int T, double lambda_d,
+                  double* q_out) {
+    const int n = r->n;
+    const size_t nn = (size_t)n * n;
+    double* Dg = (double*)calloc(nn * (size_t)T, sizeof(double));
+    double* Off = (double*)calloc(nn * (size_t)(T > 1 ? T - 1 : 1), sizeof(double));
+    double* g = (double*)calloc((size_t)n * T, sizeof(double));
+    double* d = (double*)calloc((size_t)n * T, sizeof(double));
+    for (int i = 0; i < T; ++i) {
+        const double c = (i > 0 ? 1.0 : 0.0) + (i + 1 < T ? 1.0 : 0.0);
+        for (int a = 0; a < n; ++a) Dg[nn * i + (size_t)a * n + a] = c + lambda_d;
+        if (i + 1 < T)
+            for (int a = 0; a < n; ++a) Off[nn * i + (size_t)a * n + a] = -1.0;
+        for (int a = 0; a < n; ++a) {
+            double t = 0.0;
+            if (i > 0) t += q_in[(size_t)i * n + a] - q_in[(size_t)(i - 1) * n + a];
+            if (i + 1 < T) t -= q_in[(size_t)(i + 1) * n + a] - q_in[(size_t)i * n + a];
+            g[(size_t)i * n + a] = -t;   /* right-hand side -J^T r_diff */
+        }
+    }
+    const int ok = orc_block_tridiag_solve(T, n, Dg, Off, g, d);
+    for (int i = 0; i < T; ++i)
+        for (int a = 0; a < n; ++a) {
+            double v = q_in[(size_t)i * n + a] + (ok ? d[(size_t)i * n + a] : 0.0);
+            if (v < r->lo[a]) v = r->lo[a];
+            if (v > r->hi[a]) v = r->hi[a];
+            q_out[(size_t)i * n + a] = ok ? v : q_in[(size_t)i * n + a];
+        }
+    free(Dg); free(Off); free(g); free(d);
+    return ok;
+}
+
+/* §III-C non-stationary objective: pose-only LM phases (orc_lm) alternate with
+ * single trajectory-length steps; a trajectory-length step is taken only when
+ * the pose phase before it left every waypoint within tau_pos / tau_rot (FP64
+ * check), and the sequence ends with a pose phase:
+ *   q = q_in
+ *   repeat rounds times: q = lm(q); if every waypoint is within tau:
+ *                        q = diff_step(q, lambda_d), taken += 1
+ *   q = lm(q)
+ * Each pose phase starts from lambda0 (orc_lm). */
+void orc_lm_smooth(const orc_robot* r, const orc_params* P, const double* q_in,
+                   const double* targets, int T, int rounds, double lambda_d, double* q_out,
+                   int32_t* taken) {
+    const int n = r->n;
+    double* q = (double*)malloc(sizeof(double) * (size_t)T * n);
+    double* w = (double*)malloc(sizeof(double) * (size_t)T * n);
+    memcpy(q, q_in, sizeof(double) * (size_t)T * n);
+    int32_t cnt = 0;
+    for (int k = 0; k < rounds; ++k) {
+        orc_lm(r, P, q, targets, T, w, 0, 0);
+        orc_report rep;
+        orc_check(r, P, w, targets, T, 0, &rep);
+        if (rep.n_pose_fail == 0) {
+            orc_diff_step(r, w, T, lambda_d, q);
+            ++cnt;
+        } else {
+            memcpy(q, w, sizeof(double) * (size_t)T * n);
+        }
+    }
+    orc_lm(r, P, q, targets, T, q_out, 0, 0);
+    if (taken) *taken = cnt;
+    free(q); free(w);
+}
+
 /* Mask -> FP32 search -> seed -> LM -> check, for one request. */
 int orc_plan(const orc_robot* r, const orc_params* P, const float* cand,
              const double* targets, int T, int K, int Kp, int32_t* sel,

@@ -98,6 +98,16 @@ void   orc_lm(const orc_robot* r, const orc_params* P, const double* q_in /*[T][
               const double* targets /*[T][7]*/, int T, double* q_out /*[T][n]*/,
               double* F_hist /*[T][lm_iters+1] or 0*/, int32_t* iters_run /*[T] or 0*/);
 
+/* ---- §III-C non-stationary objective: trajectory-length (differencing) steps ---- */
+int  orc_block_tridiag_solve(int T, int n, const double* Dg /*[T][n][n]*/,
+                             const double* Off /*[T-1][n][n]*/, const double* b /*[T][n]*/,
+                             double* x /*[T][n]*/);
+int  orc_diff_step(const orc_robot* r, const double* q_in /*[T][n]*/, int T, double lambda_d,
+                   double* q_out /*[T][n]*/);
+void orc_lm_smooth(const orc_robot* r, const orc_params* P, const double* q_in,
+                   const double* targets, int T, int rounds, double lambda_d,
+                   double* q_out, int32_t* taken);
+
 /* ---- §II report: errors, validity, mjac, jumps, trajectory length ---- */
 typedef struct orc_report {
     double max_pos, max_rot;      /* worst waypoint error */
