@@ -105,6 +105,11 @@ typedef struct cpp_params {
     int32_t lm_fp64;     /* 0: FP32 FK/Jacobian + FP64 normal equations and Cholesky;
                             1: everything in FP64 (for near-singular chains) */
     int32_t dp_objective; /* CPP_DP_SUM (default) or CPP_DP_MINMAX, see cpp_dp_search_ex */
+    int32_t smooth_rounds; /* §III-C non-stationary objective: trajectory-length steps
+                              alternated with pose phases (default 0: pose only), see
+                              cpp_smooth_step; at most 1000 */
+    int32_t reserved_;
+    double smooth_lambda;  /* damping of the trajectory-length step (default 1; > 0) */
 } cpp_params_t;
 
 #define CPP_DP_SUM 0     /* minimise the summed per-step L-inf joint jump */
@@ -241,6 +246,25 @@ cpp_status cpp_dp_search_static(const float* cand, const float* pen, int32_t T, 
 cpp_status cpp_lm_refine(const cpp_robot_t* robot, const cpp_params_t* params,
                          const float* q_in, const double* targets, int32_t T, float* q_out,
                          double* pose_err, int32_t* dev_status, cpp_stream_t stream);
+
+/* §III-C non-stationary objective. The paper alternates pose-only LM phases with
+ * single steps on the trajectory-length residual r_diff = [q_{i+1} - q_i]
+ * (differences of consecutive configurations; its collision rows are not
+ * built), taking such a step only once every waypoint is within tau_pos /
+ * tau_rot. cpp_smooth_step is one such step on q [T][n] FP32 in place: if the
+ * FP64 FK of every waypoint is within tau it applies
+ *   delta = -(J^T J + smooth_lambda I)^{-1} J^T r_diff,  q = clamp(q + delta, lo, hi),
+ * solved in FP64 (J^T J is block tridiagonal with blocks that are multiples of
+ * I, so the block Thomas recursion splits into one scalar recursion per joint),
+ * else it leaves q unchanged. With params->smooth_rounds = R > 0, cpp_lm_refine
+ * (and cpp_plan, batches, the server) run a pose phase, then R times this step
+ * followed by another pose phase (starting from the previous phase's q_out);
+ * pose_err then belongs to the last phase. Limit: (n + 1) * T * 8 bytes of shared
+ * memory per request, at most 227 KB (T <= 3632 at n = 7, 2905 at n = 9);
+ * INVALID_ARG beyond it. */
+cpp_status cpp_smooth_step(const cpp_robot_t* robot, const cpp_params_t* params, float* q,
+                           const double* targets, int32_t T, int32_t* dev_status,
+                           cpp_stream_t stream);
 
 /* ------------------------------------------------------------------ check (§II)
  * FP64 FK of q [T][n] FP32 -> pose_err [T][2] FP64 (or NULL) and a report

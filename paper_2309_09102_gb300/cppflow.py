@@ -41,7 +41,8 @@ class Params(C.Structure):
         "tau_pos", "tau_rot", "near_margin", "pen_limit", "pen_pose", "jump_max", "lambda0",
         "lambda_up", "lambda_down", "lambda_min", "lambda_max", "freeze_step", "freeze_cost")] + [
         ("lm_iters", C.c_int32), ("free_mask", C.c_uint32), ("lm_fp64", C.c_int32),
-        ("dp_objective", C.c_int32)]
+        ("dp_objective", C.c_int32), ("smooth_rounds", C.c_int32), ("reserved_", C.c_int32),
+        ("smooth_lambda", C.c_double)]
 
 
 class Report(C.Structure):
@@ -116,6 +117,7 @@ _SIGS = {
     "cpp_dp_search": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, C.c_size_t,
                                 _P, _P, _P, _P, _P]),
     "cpp_lm_refine": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, _P, _P]),
+    "cpp_smooth_step": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P]),
     "cpp_check": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, _P]),
     "cpp_plan_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "cpp_plan": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_size_t,
@@ -271,6 +273,14 @@ def lm_refine(robot: Robot, params: Params, q_in, targets, q_out, pose_err=None,
     _check(lib().cpp_lm_refine(C.byref(robot), C.byref(params), ptr(q_in), ptr(targets), T,
                                ptr(q_out), ptr(pose_err), ptr(dev_status),
                                stream_handle(stream)), "cpp_lm_refine")
+
+
+def smooth_step(robot: Robot, params: Params, q, targets, dev_status=None, stream=None):
+    """One trajectory-length step on q [T][n] FP32 in place (taken only when every
+    waypoint is within tau)."""
+    T = q.shape[0]
+    _check(lib().cpp_smooth_step(C.byref(robot), C.byref(params), ptr(q), ptr(targets), T,
+                                 ptr(dev_status), stream_handle(stream)), "cpp_smooth_step")
 
 
 def check(robot: Robot, params: Params, q, targets, pose_err=None, report=None, stream=None):

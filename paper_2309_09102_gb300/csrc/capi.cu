@@ -64,6 +64,19 @@ cpp_status check_params(const cpp_params_t* p) {
   if (p->dp_objective != CPP_DP_SUM && p->dp_objective != CPP_DP_MINMAX)
     return fail(CPP_ERR_INVALID_ARG, "dp_objective %d is neither CPP_DP_SUM nor CPP_DP_MINMAX",
                 p->dp_objective);
+  if (p->smooth_rounds < 0 || p->smooth_rounds > 1000)
+    return fail(CPP_ERR_INVALID_ARG, "smooth_rounds outside [0, 1000]");
+  if (!(finite_d(p->smooth_lambda) && p->smooth_lambda > 0))
+    return fail(CPP_ERR_INVALID_ARG, "smooth_lambda must be finite and > 0");
+  return CPP_OK;
+}
+
+constexpr size_t kMaxSmemBytes = 227u * 1024u;
+
+// The trajectory-length step keeps (n + 1) T doubles in shared memory.
+cpp_status check_smooth(const cpp_params_t* p, int T, int n) {
+  if (p->smooth_rounds > 0 && smooth_smem_bytes(T, n) > kMaxSmemBytes)
+    return fail(CPP_ERR_INVALID_ARG, "smooth_rounds > 0 needs (n + 1) * T * 8 <= 227 KB (T = %d)", T);
   return CPP_OK;
 }
 
@@ -132,6 +145,9 @@ void cpp_params_default(cpp_params_t* p) {
   p->free_mask = 0xFFFFFFFFu;
   p->lm_fp64 = 0;
   p->dp_objective = CPP_DP_SUM;
+  p->smooth_rounds = 0;
+  p->reserved_ = 0;
+  p->smooth_lambda = 1.0;
 }
 
 cpp_status cpp_fk_batch(const cpp_robot_t* robot, const float* q, int64_t N, float* R, float* p,
@@ -238,6 +254,7 @@ cpp_status cpp_lm_refine(const cpp_robot_t* robot, const cpp_params_t* params, c
   if (cpp_status s = check_params(params)) return s;
   if (T < 1) return fail(CPP_ERR_INVALID_ARG, "T < 1");
   if (!q_in || !targets || !q_out) return fail(CPP_ERR_INVALID_ARG, "NULL buffer");
+  if (cpp_status e = check_smooth(params, T, robot->n)) return e;
   SingleSrc s;
   s.r = empty_req();
   s.r.T = T; s.r.n = robot->n;
@@ -245,6 +262,24 @@ cpp_status cpp_lm_refine(const cpp_robot_t* robot, const cpp_params_t* params, c
   s.r.status = dev_status;
   s.robot = *robot;
   return cuda_status(launch_lm(s, *params, true, (cudaStream_t)stream), "cpp_lm_refine");
+}
+
+cpp_status cpp_smooth_step(const cpp_robot_t* robot, const cpp_params_t* params, float* q,
+                           const double* targets, int32_t T, int32_t* dev_status,
+                           cpp_stream_t stream) {
+  if (cpp_status s = check_robot(robot)) return s;
+  if (cpp_status s = check_params(params)) return s;
+  if (T < 1) return fail(CPP_ERR_INVALID_ARG, "T < 1");
+  if (!q || !targets) return fail(CPP_ERR_INVALID_ARG, "NULL buffer");
+  if (smooth_smem_bytes(T, robot->n) > kMaxSmemBytes)
+    return fail(CPP_ERR_INVALID_ARG, "(n + 1) * T * 8 exceeds 227 KB (T = %d)", T);
+  SingleSrc s;
+  s.r = empty_req();
+  s.r.T = T; s.r.n = robot->n;
+  s.r.q_out = q; s.r.targets = targets;
+  s.r.status = dev_status;
+  s.robot = *robot;
+  return cuda_status(launch_smooth(s, *params, (cudaStream_t)stream), "cpp_smooth_step");
 }
 
 cpp_status cpp_check(const cpp_robot_t* robot, const cpp_params_t* params, const float* q,
@@ -277,6 +312,7 @@ cpp_status cpp_plan(const cpp_robot_t* robot, const cpp_params_t* params, const 
   if (cpp_status s = check_params(params)) return s;
   const int n = robot->n;
   if (cpp_status s = check_lattice(T, K, Kp, n)) return s;
+  if (cpp_status s = check_smooth(params, T, n)) return s;
   if (!dp_supported(n, Kp))
     return fail(CPP_ERR_INVALID_ARG, "Kp * (n + 1) exceeds the shared-memory limit");
   if (!cand || !targets || !sel || !best_cost || !q_out || !workspace)
@@ -570,6 +606,7 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
     if (robots[d.robot].n != n)
       return fail(CPP_ERR_INVALID_ARG, "request %d: all robots of one batch need the same n", r);
     if (cpp_status s = check_lattice(d.T, d.K, d.Kp, n)) return s;
+    if (cpp_status s = check_smooth(params, d.T, n)) return s;
     if (!d.cand || !d.targets || !d.sel || !d.q_out || !d.best_cost)
       return fail(CPP_ERR_INVALID_ARG, "request %d: NULL buffer", r);
     if (!aligned(d.cand, 16)) return fail(CPP_ERR_INVALID_ARG, "request %d: cand misaligned", r);
@@ -647,6 +684,7 @@ int32_t cpp_batch_launches(const cpp_batch_t* b, uint32_t stages) {
   int c = 0;
   for (unsigned s = 1; s <= CPP_STAGE_CHECK; s <<= 1) {
     if (!(stages & s)) continue;
+    if (s == CPP_STAGE_LM) { c += lm_launches(b->params); continue; }
     if (s != CPP_STAGE_DP_FORWARD) { ++c; continue; }
     for (const SchedGroup& g : b->groups) c += g.count > 0 ? 1 : 0;
   }

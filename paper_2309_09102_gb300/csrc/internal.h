@@ -52,6 +52,9 @@ int device_sm_count();     // SMs of the current device
 cudaError_t launch_lm(const SingleSrc& s, const cpp_params_t& P, bool want_err, cudaStream_t st);
 cudaError_t launch_lm_batch(const BatchSrc& s, int n, int nreq, int max_T, const cpp_params_t& P,
                             cudaStream_t st);
+cudaError_t launch_smooth(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st);
+size_t smooth_smem_bytes(int T, int n);  // shared memory of the trajectory-length step
+int lm_launches(const cpp_params_t& P);  // kernel launches of one refinement
 cudaError_t launch_check(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st);
 cudaError_t launch_check_batch(const BatchSrc& s, int nreq, const cpp_params_t& P,
                                cudaStream_t st);

@@ -30,6 +30,7 @@ struct LmArgs {
   int iters;
   uint32_t free_mask;
   int want_err;  // write the FP64 pose error of q_out (skipped when a check follows)
+  int from_out;  // start from q_out (a later pose phase of the alternation) instead of q_in
 };
 
 struct CheckArgs {
@@ -114,7 +115,8 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
   }
   double q[MJ];
 #pragma unroll
-  for (int j = 0; j < MJ; ++j) q[j] = (NJ || j < n) ? (double)rq.q_in[(size_t)i * n + j] : 0.0;
+  const float* q_src = a.from_out ? rq.q_out : rq.q_in;
+  for (int j = 0; j < MJ; ++j) q[j] = (NJ || j < n) ? (double)q_src[(size_t)i * n + j] : 0.0;
 
   F e[6];
   double Fc = lm_eval<NJ, false, F>(rb, n, q, Rt, pt, e, nullptr, nullptr, nullptr);
@@ -325,10 +327,81 @@ __global__ void __launch_bounds__(kChkThreads) check_kernel(const __grid_constan
   }
 }
 
+// ------------------------------------------------------------------ trajectory-length step
+// §III-C non-stationary objective: pose-only LM phases alternate with single
+// steps on the differencing residual r_diff = [q_{i+1} - q_i] (the collision
+// rows of r_diff are not built). A step is taken only when every waypoint is
+// within tau_pos / tau_rot (FP64 FK of q_out). It is the damped least-squares
+// step delta = -(J^T J + lambda_d I)^{-1} J^T r_diff; J^T J is block tridiagonal
+// with blocks (c_i + lambda_d) I on the diagonal (c_i = 1 at the ends, 2 inside)
+// and -I beside it. Blocks that are multiples of I never mix joints, so the
+// block Thomas recursion is exactly n scalar recursions, one per lane:
+//   s_0 = a_0,  s_i = a_i - 1 / s_{i-1};   y_0 = b_0,  y_i = b_i + y_{i-1} / s_{i-1}
+//   delta_{T-1} = y_{T-1} / s_{T-1},       delta_i = (y_i + delta_{i+1}) / s_i
+// with b_i = (q_{i+1} - q_i) - (q_i - q_{i-1}) (absent terms 0), then
+// q' = clamp(q + delta, lo, hi), stored in FP32. One warp per request; FP64;
+// 1 / s_i and y_i are kept in shared memory ((n + 1) T doubles).
+struct SmoothArgs {
+  double tau_pos, tau_rot, lambda_d;
+};
+
+template <class Src>
+__global__ void __launch_bounds__(32) smooth_kernel(const __grid_constant__ Src src,
+                                                     const SmoothArgs a) {
+  const Req& rq = src.req(blockIdx.x);
+  extern __shared__ double sm_s[];
+  __shared__ RobotD rd;
+  stage_robot(src.rob(rq.robot), 0.0, nullptr, &rd);
+  __syncthreads();
+  const int n = rd.n, T = rq.T, lane = threadIdx.x;
+  bool ok = true;
+  for (int i = lane; i < T; i += 32) {
+    double q[kMaxJ], R[9], p[3], Rt[9];
+    for (int j = 0; j < n; ++j) q[j] = (double)rq.q_out[(size_t)i * n + j];
+    fk_f64(rd, q, R, p);
+    const double* t7 = rq.targets + 7 * (size_t)i;
+    quat_to_rot(t7 + 3, Rt);
+    const double dx = p[0] - t7[0], dy = p[1] - t7[1], dz = p[2] - t7[2];
+    const double pos = sqrt(dx * dx + dy * dy + dz * dz);
+    const double rot = geodesic<double>(Rt, R);
+    ok = ok && pos <= a.tau_pos && rot <= a.tau_rot;
+  }
+  if (!__all_sync(0xffffffffu, ok) || T < 2 || lane >= n) return;
+  double* inv_s = sm_s;       // [T]
+  double* y = sm_s + T;       // [T][n]
+  const int j = lane;
+  float* qc = rq.q_out + j;   // column j, stride n
+  double qp = 0.0, qi = (double)qc[0], ip = 0.0, yp = 0.0;
+  for (int i = 0; i < T; ++i) {
+    const double qn = i + 1 < T ? (double)qc[(size_t)(i + 1) * n] : 0.0;
+    const double c = (i > 0 ? 1.0 : 0.0) + (i + 1 < T ? 1.0 : 0.0);
+    const double b = (i + 1 < T ? qn - qi : 0.0) - (i > 0 ? qi - qp : 0.0);
+    const double s = c + a.lambda_d - (i > 0 ? ip : 0.0);
+    const double yi = b + (i > 0 ? yp * ip : 0.0);
+    ip = 1.0 / s;
+    yp = yi;
+    if (j == 0) inv_s[i] = ip;  // the same in every lane
+    y[(size_t)i * n + j] = yi;
+    qp = qi;
+    qi = qn;
+  }
+  __syncwarp((1u << n) - 1u);
+  double d = 0.0;
+  const double lo = rd.lo[j], hi = rd.hi[j];
+  for (int i = T - 1; i >= 0; --i) {
+    d = (y[(size_t)i * n + j] + (i + 1 < T ? d : 0.0)) * inv_s[i];
+    const double v = fmin(fmax((double)qc[(size_t)i * n] + d, lo), hi);
+    qc[(size_t)i * n] = (float)v;
+  }
+}
+
+size_t smooth_smem_bytes(int T, int n) { return (size_t)T * (n + 1) * sizeof(double); }
+
 // ------------------------------------------------------------------ launchers
-static LmArgs make_lm_args(const cpp_params_t& P, bool want_err) {
+static LmArgs make_lm_args(const cpp_params_t& P, bool want_err, bool from_out) {
   LmArgs a;
   a.want_err = want_err ? 1 : 0;
+  a.from_out = from_out ? 1 : 0;
   a.lambda0 = P.lambda0; a.lambda_up = P.lambda_up; a.lambda_down = P.lambda_down;
   a.lambda_min = P.lambda_min; a.lambda_max = P.lambda_max;
   a.freeze_step = P.freeze_step; a.freeze_cost = P.freeze_cost;
@@ -343,9 +416,9 @@ static void launch_lm_nj(const Src& s, dim3 grid, const LmArgs& a, bool fp64, cu
 }
 
 template <class Src>
-static cudaError_t launch_lm_t(const Src& s, int n, int nreq, int max_T, const cpp_params_t& P,
-                               bool want_err, cudaStream_t st) {
-  const LmArgs a = make_lm_args(P, want_err);
+static cudaError_t launch_lm_phase(const Src& s, int n, int nreq, int max_T, const cpp_params_t& P,
+                                   bool want_err, bool from_out, cudaStream_t st) {
+  const LmArgs a = make_lm_args(P, want_err, from_out);
   dim3 grid((unsigned)((max_T + kLmThreads - 1) / kLmThreads), (unsigned)nreq);
   switch (n) {
     case 6: launch_lm_nj<6>(s, grid, a, P.lm_fp64 != 0, st); break;
@@ -356,12 +429,47 @@ static cudaError_t launch_lm_t(const Src& s, int n, int nreq, int max_T, const c
   return cudaGetLastError();
 }
 
+template <class Src>
+static cudaError_t launch_smooth_t(const Src& s, int n, int nreq, int max_T, const cpp_params_t& P,
+                                   cudaStream_t st) {
+  const SmoothArgs a{P.tau_pos, P.tau_rot, P.smooth_lambda};
+  const size_t smem = smooth_smem_bytes(max_T, n);
+  if (smem > 48u * 1024u) {
+    const cudaError_t e = cudaFuncSetAttribute(smooth_kernel<Src>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  smooth_kernel<Src><<<nreq, 32, smem, st>>>(s, a);
+  return cudaGetLastError();
+}
+
+// The refinement of §III-C: a pose phase, then smooth_rounds times a
+// trajectory-length step (taken per request only when its waypoints are all
+// within tau) followed by another pose phase.
+template <class Src>
+static cudaError_t launch_lm_t(const Src& s, int n, int nreq, int max_T, const cpp_params_t& P,
+                               bool want_err, cudaStream_t st) {
+  const int rounds = P.smooth_rounds > 0 ? P.smooth_rounds : 0;
+  cudaError_t e = launch_lm_phase(s, n, nreq, max_T, P, want_err && rounds == 0, false, st);
+  for (int k = 0; k < rounds && e == cudaSuccess; ++k) {
+    if ((e = launch_smooth_t(s, n, nreq, max_T, P, st)) != cudaSuccess) break;
+    e = launch_lm_phase(s, n, nreq, max_T, P, want_err && k + 1 == rounds, true, st);
+  }
+  return e;
+}
+
 cudaError_t launch_lm(const SingleSrc& s, const cpp_params_t& P, bool want_err, cudaStream_t st) {
   return launch_lm_t(s, s.r.n, 1, s.r.T, P, want_err, st);
 }
 cudaError_t launch_lm_batch(const BatchSrc& s, int n, int nreq, int max_T, const cpp_params_t& P,
                             cudaStream_t st) {
   return launch_lm_t(s, n, nreq, max_T, P, false, st);
+}
+cudaError_t launch_smooth(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st) {
+  return launch_smooth_t(s, s.r.n, 1, s.r.T, P, st);
+}
+int lm_launches(const cpp_params_t& P) {
+  return 1 + 2 * (P.smooth_rounds > 0 ? P.smooth_rounds : 0);
 }
 
 template <class Src>

@@ -436,6 +436,12 @@ cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out)
   if (cfg->max_slots < 1 || cfg->max_batch < 1 || cfg->max_inflight < 1 || cfg->max_inflight > 16)
     return sfail(CPP_ERR_INVALID_ARG, "max_slots, max_batch >= 1 and max_inflight in [1, 16]");
   if (cfg->hbm_budget_bytes < 4096) return sfail(CPP_ERR_INVALID_ARG, "hbm_budget_bytes too small");
+  const cpp_params_t& P = cfg->params;
+  if (P.lm_iters < 0 || P.smooth_rounds < 0 || P.smooth_rounds > 1000 ||
+      !(std::isfinite(P.smooth_lambda) && P.smooth_lambda > 0) ||
+      (P.dp_objective != CPP_DP_SUM && P.dp_objective != CPP_DP_MINMAX))
+    return sfail(CPP_ERR_INVALID_ARG, "invalid params (lm_iters, smooth_rounds, smooth_lambda, "
+                                      "dp_objective)");
   cpp_server* s = new (std::nothrow) cpp_server;
   if (!s) return sfail(CPP_ERR_OOM, "host allocation failed");
   s->cfg = *cfg;
@@ -480,6 +486,8 @@ cpp_status cpp_plan_submit(cpp_server_t* s, const cpp_plan_req_t* rq, uint64_t* 
   if (T < 1 || K < 1 || K > 65535 || Kp < K || Kp % 4)
     return sfail(CPP_ERR_INVALID_ARG, "invalid lattice T=%d K=%d Kp=%d", T, K, Kp);
   if (!dp_supported(n, Kp)) return sfail(CPP_ERR_INVALID_ARG, "Kp too large for shared memory");
+  if (s->cfg.params.smooth_rounds > 0 && smooth_smem_bytes(T, n) > 227u * 1024u)
+    return sfail(CPP_ERR_INVALID_ARG, "smooth_rounds > 0 needs (n + 1) * T * 8 <= 227 KB");
   if (!rq->cand || !rq->targets) return sfail(CPP_ERR_INVALID_ARG, "NULL input");
   for (int i = 0; i < T; ++i) {
     const double* t = rq->targets + 7 * (size_t)i;

@@ -55,3 +55,26 @@ def test_host_only_calls(lib):
     bad = cppflow.make_robot([0.1] * 7, [0.1] * 7, [0.0] * 7, [1] * 7, [-1] * 7)
     assert cppflow.lib().cpp_check(ctypes.byref(bad), ctypes.byref(p), None, None, 5, None, None,
                                    None) == cppflow.ERR_INVALID_ARG
+
+
+def test_smoothing_params_are_validated_on_the_host(lib):
+    """smooth_lambda must be positive, smooth_rounds within [0, 1000], and the
+    trajectory-length step's (n + 1) T doubles must fit in shared memory; every
+    check fails before any device pointer is touched."""
+    from paper_2309_09102_gb300 import cppflow
+    L = cppflow.lib()
+    r = cppflow.make_robot([0.1] * 7, [0.1] * 7, [0.0] * 7, [-1] * 7, [1] * 7)
+    p = cppflow.make_params()
+    assert p.smooth_rounds == 0 and p.smooth_lambda == 1.0
+    fake = ctypes.c_void_p(256)  # never dereferenced: validation fails first
+    for kw in ({"smooth_lambda": 0.0}, {"smooth_lambda": float("nan")}, {"smooth_rounds": -1},
+               {"smooth_rounds": 1001}):
+        q = cppflow.make_params(**kw)
+        assert L.cpp_lm_refine(ctypes.byref(r), ctypes.byref(q), fake, fake, 10, fake, None, None,
+                               None) == cppflow.ERR_INVALID_ARG
+    big = cppflow.make_params(smooth_rounds=1)
+    assert L.cpp_lm_refine(ctypes.byref(r), ctypes.byref(big), fake, fake, 4000, fake, None, None,
+                           None) == cppflow.ERR_INVALID_ARG
+    assert "227" in cppflow.last_error()
+    assert L.cpp_smooth_step(ctypes.byref(r), ctypes.byref(p), fake, fake, 4000, None,
+                             None) == cppflow.ERR_INVALID_ARG
