@@ -53,6 +53,44 @@ class Params(C.Structure):
         "freeze_step", "freeze_cost")] + [("lm_iters", C.c_int32), ("free_mask", C.c_uint32)]
 
 
+MAX_CAPS, MAX_PAIRS, MAX_BOXES = 12, 64, 8
+COLLIDE = 32
+
+
+class Capsule(C.Structure):
+    _fields_ = [("frame", C.c_int32), ("pad_", C.c_int32), ("a", C.c_double * 3),
+                ("b", C.c_double * 3), ("radius", C.c_double)]
+
+
+class Cuboid(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("p", C.c_double * 3), ("half", C.c_double * 3)]
+
+
+class Geometry(C.Structure):
+    _fields_ = [("n_caps", C.c_int32), ("n_pairs", C.c_int32), ("n_boxes", C.c_int32),
+                ("pad_", C.c_int32), ("caps", Capsule * MAX_CAPS),
+                ("pairs", (C.c_int32 * 2) * MAX_PAIRS), ("boxes", Cuboid * MAX_BOXES)]
+
+
+def make_geometry(geo) -> Geometry:
+    """Oracle copy of a collision model (synth.Geometry)."""
+    g = Geometry()
+    g.n_caps, g.n_pairs, g.n_boxes = len(geo.cap_r), len(geo.pairs), len(geo.box_half)
+    assert g.n_caps <= MAX_CAPS and g.n_pairs <= MAX_PAIRS and g.n_boxes <= MAX_BOXES
+    for c in range(g.n_caps):
+        g.caps[c].frame = int(geo.cap_frame[c])
+        g.caps[c].a[:] = [float(x) for x in geo.cap_a[c]]
+        g.caps[c].b[:] = [float(x) for x in geo.cap_b[c]]
+        g.caps[c].radius = float(geo.cap_r[c])
+    for k in range(g.n_pairs):
+        g.pairs[k][0], g.pairs[k][1] = int(geo.pairs[k][0]), int(geo.pairs[k][1])
+    for o in range(g.n_boxes):
+        g.boxes[o].R[:] = [float(x) for x in np.asarray(geo.box_R[o]).ravel()]
+        g.boxes[o].p[:] = [float(x) for x in geo.box_p[o]]
+        g.boxes[o].half[:] = [float(x) for x in geo.box_half[o]]
+    return g
+
+
 class Report(C.Structure):
     _fields_ = [(f, C.c_double) for f in ("max_pos", "max_rot", "mjac", "sum_linf", "traj_len")] + [
         (f, C.c_int32) for f in ("n_pose_fail", "n_limit_fail", "n_jump_fail", "valid")]
@@ -90,6 +128,12 @@ def lib():
             "orc_block_tridiag_solve": (C.c_int, [C.c_int, C.c_int, P, P, P, P]),
             "orc_diff_step": (C.c_int, [P, P, C.c_int, C.c_double, P]),
             "orc_lm_smooth": (None, [P, P, P, P, C.c_int, C.c_int, C.c_double, P, P]),
+            "orc_seg_seg_dist2": (C.c_double, [P, P, P, P, P, P]),
+            "orc_seg_box_dist2": (C.c_double, [P, P, P, P]),
+            "orc_capsules_world": (None, [P, P, P, P, P]),
+            "orc_clearance": (None, [P, P, P, P, P]),
+            "orc_mask_geo": (None, [P, P, P, C.c_double, P, P, C.c_int, C.c_int, C.c_int, P, P, P,
+                                    P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -254,6 +298,54 @@ def lm(robot: Robot, params: Params, q_in, targets, want_hist: bool = False):
     lib().orc_lm(C.byref(robot), C.byref(params), _p(q_in), _p(targets), T, _p(q_out),
                  _p(hist), _p(iters))
     return q_out, hist, iters
+
+
+# ---------------------------------------------------------------- collision distances
+def seg_seg_dist2(a1, b1, a2, b2):
+    """(squared distance, s, t) between segments a1-b1 and a2-b2."""
+    v = [_f64(x).reshape(3) for x in (a1, b1, a2, b2)]
+    s, t = np.zeros(1), np.zeros(1)
+    d = lib().orc_seg_seg_dist2(_p(v[0]), _p(v[1]), _p(v[2]), _p(v[3]), _p(s), _p(t))
+    return d, float(s[0]), float(t[0])
+
+
+def seg_box_dist2(a, b, half):
+    """(squared distance, t) between segment a-b and the box [-half, half]."""
+    v = [_f64(x).reshape(3) for x in (a, b, half)]
+    t = np.zeros(1)
+    d = lib().orc_seg_box_dist2(_p(v[0]), _p(v[1]), _p(v[2]), _p(t))
+    return d, float(t[0])
+
+
+def capsules_world(robot: Robot, geo: Geometry, q):
+    q = _f64(q).reshape(robot.n)
+    A = np.zeros((MAX_CAPS, 3))
+    B = np.zeros((MAX_CAPS, 3))
+    lib().orc_capsules_world(C.byref(robot), C.byref(geo), _p(q), _p(A), _p(B))
+    return A[:geo.n_caps], B[:geo.n_caps]
+
+
+def clearance(robot: Robot, geo: Geometry, q):
+    """(smallest self clearance, smallest obstacle clearance) of one configuration."""
+    q = _f64(q).reshape(robot.n)
+    sm, em = np.zeros(1), np.zeros(1)
+    lib().orc_clearance(C.byref(robot), C.byref(geo), _p(q), _p(sm), _p(em))
+    return float(sm[0]), float(em[0])
+
+
+def mask_geo(robot: Robot, params: Params, geo: Geometry, pen_collide: float, cand: np.ndarray,
+             targets: np.ndarray, K: int):
+    """orc_mask_geo: (mask, pen, err, clearance)."""
+    cand = np.ascontiguousarray(cand, np.float32)
+    T, n, Kp = cand.shape
+    targets = _f64(targets).reshape(T, 7)
+    mask = np.zeros((T, Kp), np.uint8)
+    pen = np.zeros((T, Kp), np.float32)
+    err = np.zeros((T, Kp, 2))
+    cl = np.zeros((T, Kp))
+    lib().orc_mask_geo(C.byref(robot), C.byref(params), C.byref(geo), float(pen_collide), _p(cand),
+                       _p(targets), T, K, Kp, _p(mask), _p(pen), _p(err), _p(cl))
+    return mask, pen, err, cl
 
 
 # ---------------------------------------------------------------- §III-C trajectory length

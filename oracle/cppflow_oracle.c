@@ -175,21 +175,189 @@ static void target_pose(const double* t7, double Rt[9], double pt[3]) {
 /* ------------------------------------------------------------------------- */
 /* §II joint limits + §III-B node costs                                      */
 /* ------------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------- */
+/* Collision geometry: §III-B (+100 node cost) and §III-C (distances)         */
+/* ------------------------------------------------------------------------- */
+static double dist2(const double x[3], const double y[3]) {
+    const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+    return d0 * d0 + d1 * d1 + d2 * d2;
+}
+static double clamp01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
+
+/* Squared distance between segments P(s) = a1 + s (b1 - a1) and Q(t) = a2 +
+ * t (b2 - a2), s, t in [0, 1]: the convex QP of §III-C solved by enumerating its
+ * active sets. f(s, t) = |P(s) - Q(t)|^2 is convex on the unit square, so its
+ * minimum is the interior stationary point when that lies in the square, else
+ * the smallest of the four edge minima, each a 1-D convex problem solved by
+ * clamping the edge's stationary point. Every candidate is evaluated directly
+ * as |P - Q|^2 and the smallest wins (ties: first found). */
+double orc_seg_seg_dist2(const double a1[3], const double b1[3], const double a2[3],
+                         const double b2[3], double* t1, double* t2) {
+    double d1[3], d2[3], r[3];
+    for (int k = 0; k < 3; ++k) { d1[k] = b1[k] - a1[k]; d2[k] = b2[k] - a2[k]; r[k] = a1[k] - a2[k]; }
+    const double A = d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2];
+    const double C = d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2];
+    const double B = d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2];
+    const double D = d1[0] * r[0] + d1[1] * r[1] + d1[2] * r[2];
+    const double E = d2[0] * r[0] + d2[1] * r[1] + d2[2] * r[2];
+    double cs[5], ct[5];
+    int m = 0;
+    const double det = A * C - B * B;
+    if (det > 1e-300) {
+        const double s = (B * E - C * D) / det, t = (A * E - B * D) / det;
+        if (s >= 0.0 && s <= 1.0 && t >= 0.0 && t <= 1.0) { cs[m] = s; ct[m] = t; ++m; }
+    }
+    /* edges s = 0, s = 1 (t free), t = 0, t = 1 (s free) */
+    cs[m] = 0.0; ct[m] = C > 0.0 ? clamp01(E / C) : 0.0; ++m;
+    cs[m] = 1.0; ct[m] = C > 0.0 ? clamp01((B + E) / C) : 0.0; ++m;
+    cs[m] = A > 0.0 ? clamp01(-D / A) : 0.0; ct[m] = 0.0; ++m;
+    cs[m] = A > 0.0 ? clamp01((B - D) / A) : 0.0; ct[m] = 1.0; ++m;
+    double best = INFINITY;
+    for (int c = 0; c < m; ++c) {
+        double P[3], Q[3];
+        for (int k = 0; k < 3; ++k) { P[k] = a1[k] + cs[c] * d1[k]; Q[k] = a2[k] + ct[c] * d2[k]; }
+        const double f = dist2(P, Q);
+        if (f < best) { best = f; if (t1) *t1 = cs[c]; if (t2) *t2 = ct[c]; }
+    }
+    return best;
+}
+
+/* Squared distance between the segment x(t) = a + t (b - a), t in [0, 1], and
+ * the box [-half, half] (both in the box's frame): the QP of §III-C over (t, p).
+ * For fixed t the best p is x(t) clamped to the box, so the cost is
+ * g(t) = sum_k dist(x_k(t), [-h_k, h_k])^2, convex and piecewise quadratic in t
+ * with breakpoints where some x_k(t) crosses -h_k or h_k. On each piece g is one
+ * quadratic (its active faces fixed by the piece's midpoint); its minimiser,
+ * clamped to the piece, and the piece's ends are evaluated, the smallest wins. */
+static double box_cost(const double a[3], const double d[3], const double h[3], double t) {
+    double g = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double x = a[k] + t * d[k];
+        if (x > h[k]) g += (x - h[k]) * (x - h[k]);
+        else if (x < -h[k]) g += (x + h[k]) * (x + h[k]);
+    }
+    return g;
+}
+double orc_seg_box_dist2(const double a[3], const double b[3], const double half[3], double* tout) {
+    double d[3], br[8];
+    int nb = 0;
+    for (int k = 0; k < 3; ++k) d[k] = b[k] - a[k];
+    br[nb++] = 0.0;
+    br[nb++] = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        if (d[k] == 0.0) continue;
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            const double t = (sgn * half[k] - a[k]) / d[k];
+            if (t > 0.0 && t < 1.0) br[nb++] = t;
+        }
+    }
+    for (int i = 1; i < nb; ++i)      /* insertion sort */
+        for (int j = i; j > 0 && br[j] < br[j - 1]; --j) { double x = br[j]; br[j] = br[j - 1]; br[j - 1] = x; }
+    double best = INFINITY, tb = 0.0;
+    for (int i = 0; i + 1 < nb; ++i) {
+        const double ta = br[i], tz = br[i + 1], tm = 0.5 * (ta + tz);
+        double num = 0.0, den = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double x = a[k] + tm * d[k];
+            double c;
+            if (x > half[k]) c = half[k];
+            else if (x < -half[k]) c = -half[k];
+            else continue;
+            num += d[k] * (c - a[k]);
+            den += d[k] * d[k];
+        }
+        double cand[3] = {ta, tz, ta};
+        int nc = 2;
+        if (den > 0.0) {
+            double ts = num / den;
+            if (ts < ta) ts = ta;
+            if (ts > tz) ts = tz;
+            cand[nc++] = ts;
+        }
+        for (int c = 0; c < nc; ++c) {
+            const double g = box_cost(a, d, half, cand[c]);
+            if (g < best) { best = g; tb = cand[c]; }
+        }
+    }
+    if (tout) *tout = tb;
+    return best;
+}
+
+/* World end points of every capsule: frame transforms T_0 = I, T_j = T_{j-1} A_j
+ * (FP64 DH products as in orc_fk), x_w = R_f x + p_f. */
+void orc_capsules_world(const orc_robot* r, const orc_geometry* g, const double* q,
+                        double A[][3], double B[][3]) {
+    double Tf[ORC_MAXJ + 1][16], L[16];
+    mat4_identity(Tf[0]);
+    for (int j = 0; j < r->n; ++j) {
+        dh_link(r, j, q[j], L);
+        mat4_mul(Tf[j], L, Tf[j + 1]);
+    }
+    for (int c = 0; c < g->n_caps; ++c) {
+        const double* M = Tf[g->caps[c].frame];
+        for (int k = 0; k < 3; ++k) {
+            A[c][k] = M[4 * k] * g->caps[c].a[0] + M[4 * k + 1] * g->caps[c].a[1] +
+                      M[4 * k + 2] * g->caps[c].a[2] + M[4 * k + 3];
+            B[c][k] = M[4 * k] * g->caps[c].b[0] + M[4 * k + 1] * g->caps[c].b[1] +
+                      M[4 * k + 2] * g->caps[c].b[2] + M[4 * k + 3];
+        }
+    }
+}
+
+/* Clearances of one configuration (§III-C): over the listed capsule pairs,
+ * segment distance - r_u - r_v; over every capsule and box, segment-box distance
+ * - r_u (the box frame: x_b = R^T (x_w - p)). +inf when a list is empty. */
+void orc_clearance(const orc_robot* r, const orc_geometry* g, const double* q,
+                   double* self_min, double* env_min) {
+    double A[ORC_MAX_CAPS][3], B[ORC_MAX_CAPS][3];
+    orc_capsules_world(r, g, q, A, B);
+    double sm = INFINITY, em = INFINITY;
+    for (int k = 0; k < g->n_pairs; ++k) {
+        const int u = g->pairs[k][0], v = g->pairs[k][1];
+        const double d = sqrt(orc_seg_seg_dist2(A[u], B[u], A[v], B[v], 0, 0)) -
+                         g->caps[u].radius - g->caps[v].radius;
+        if (d < sm) sm = d;
+    }
+    for (int o = 0; o < g->n_boxes; ++o) {
+        const orc_cuboid* bx = &g->boxes[o];
+        for (int c = 0; c < g->n_caps; ++c) {
+            double a[3], b[3];
+            for (int k = 0; k < 3; ++k) {
+                a[k] = bx->R[k] * (A[c][0] - bx->p[0]) + bx->R[3 + k] * (A[c][1] - bx->p[1]) +
+                       bx->R[6 + k] * (A[c][2] - bx->p[2]);
+                b[k] = bx->R[k] * (B[c][0] - bx->p[0]) + bx->R[3 + k] * (B[c][1] - bx->p[1]) +
+                       bx->R[6 + k] * (B[c][2] - bx->p[2]);
+            }
+            const double d = sqrt(orc_seg_box_dist2(a, b, bx->half, 0)) - g->caps[c].radius;
+            if (d < em) em = d;
+        }
+    }
+    *self_min = sm;
+    *env_min = em;
+}
+
 /* Per candidate (i, k):
  *   NONFINITE: some joint value is not finite -> node cost +inf, no other bit.
  *   OUT:  some q_j < lo_j or q_j > hi_j                (§II "Joint limits")
  *   NEAR: some q_j within near_margin of a limit       (§III-B, +10 band)
  *   POSE: position error > tau_pos or rotation error > tau_rot (§II)
- *   pen = pen_limit * [OUT or NEAR] + pen_pose * [POSE]  (§III-B additive costs)
+ *   COLLIDE (orc_mask_geo only): the smaller clearance is negative (§III-B)
+ *   pen = pen_limit * [OUT or NEAR] + pen_pose * [POSE] (+ pen_collide * [COLLIDE])
+ *                                                      (§III-B additive costs)
  * Readings: limit comparisons are made in FP32 on the FP32 candidate against
  * the FP32-rounded thresholds (lo, hi, lo+m, hi-m, each formed in FP64 and
  * rounded once), so the OUT/NEAR bits are exact on any IEEE machine; a
  * configuration outside the limits is charged like one inside the band; the
  * pose bit takes its errors from FP64 forward kinematics of the upcast
  * candidate. Padding lanes k in [K, Kp) get PAD and +inf. */
-void orc_mask(const orc_robot* r, const orc_params* P, const float* cand,
-              const double* targets, int T, int K, int Kp,
-              uint8_t* mask, float* pen, double* err) {
+/* Mask and node costs, with the collision cost of §III-B when g is given:
+ * COLLIDE when the smaller clearance is negative, cost += pen_collide (the sum
+ * of the node's costs formed in FP64 in the order limit, pose, collision, then
+ * rounded to FP32 once). clearance [T][Kp] (or 0) receives the smaller
+ * clearance (+inf without geometry, NaN for padding / non-finite). */
+static void mask_core(const orc_robot* r, const orc_params* P, const orc_geometry* g,
+                      double pen_collide, const float* cand, const double* targets, int T,
+                      int K, int Kp, uint8_t* mask, float* pen, double* err, double* clearance) {
     const int n = r->n;
     float lo_f[ORC_MAXJ], hi_f[ORC_MAXJ], nlo_f[ORC_MAXJ], nhi_f[ORC_MAXJ];
     for (int j = 0; j < n; ++j) {
@@ -206,6 +374,7 @@ void orc_mask(const orc_robot* r, const orc_params* P, const float* cand,
             if (k >= K) {
                 mask[o] = ORC_PAD; pen[o] = INFINITY;
                 if (err) { err[2 * o] = NAN; err[2 * o + 1] = NAN; }
+                if (clearance) clearance[o] = NAN;
                 continue;
             }
             float qf[ORC_MAXJ];
@@ -219,6 +388,7 @@ void orc_mask(const orc_robot* r, const orc_params* P, const float* cand,
             if (!finite) {
                 mask[o] = ORC_NONFINITE; pen[o] = INFINITY;
                 if (err) { err[2 * o] = NAN; err[2 * o + 1] = NAN; }
+                if (clearance) clearance[o] = NAN;
                 continue;
             }
             unsigned bits = 0;
@@ -230,14 +400,35 @@ void orc_mask(const orc_robot* r, const orc_params* P, const float* cand,
             orc_fk(r, qd, R, p);
             orc_pose_error(Rt, pt, R, p, &pos, &rot);
             if (pos > P->tau_pos || rot > P->tau_rot) bits |= ORC_POSE;
+            double cl = INFINITY;
+            if (g) {
+                double sm, em;
+                orc_clearance(r, g, qd, &sm, &em);
+                cl = sm < em ? sm : em;
+                if (cl < 0.0) bits |= ORC_COLLIDE;
+            }
             double c = 0.0;
             if (bits & (ORC_OUT | ORC_NEAR)) c += P->pen_limit;
             if (bits & ORC_POSE) c += P->pen_pose;
+            if (bits & ORC_COLLIDE) c += pen_collide;
             mask[o] = (uint8_t)bits;
             pen[o] = (float)c;
             if (err) { err[2 * o] = pos; err[2 * o + 1] = rot; }
+            if (clearance) clearance[o] = cl;
         }
     }
+}
+
+void orc_mask(const orc_robot* r, const orc_params* P, const float* cand,
+              const double* targets, int T, int K, int Kp,
+              uint8_t* mask, float* pen, double* err) {
+    mask_core(r, P, 0, 0.0, cand, targets, T, K, Kp, mask, pen, err, 0);
+}
+
+void orc_mask_geo(const orc_robot* r, const orc_params* P, const orc_geometry* g,
+                  double pen_collide, const float* cand, const double* targets, int T, int K,
+                  int Kp, uint8_t* mask, float* pen, double* err, double* clearance) {
+    mask_core(r, P, g, pen_collide, cand, targets, T, K, Kp, mask, pen, err, clearance);
 }
 
 /* ------------------------------------------------------------------------- */

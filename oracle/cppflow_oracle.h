@@ -78,6 +78,39 @@ void orc_mask(const orc_robot* r, const orc_params* P, const float* cand /*[T][n
               const double* targets /*[T][7]*/, int T, int K, int Kp,
               uint8_t* mask /*[T][Kp]*/, float* pen /*[T][Kp]*/, double* err /*[T][Kp][2] or 0*/);
 
+/* ---- §III-B collision cost, §III-C collision distances ----
+ * The robot as capsules (segment + radius) fixed to its DH frames, obstacles as
+ * cuboids. Frame f of a capsule: 0 = base, j = the frame after joint j. */
+#define ORC_MAX_CAPS 12
+#define ORC_MAX_PAIRS 64
+#define ORC_MAX_BOXES 8
+#define ORC_COLLIDE  32u
+typedef struct orc_capsule {
+    int32_t frame, pad_;
+    double a[3], b[3];       /* segment end points in the capsule's frame (m) */
+    double radius;
+} orc_capsule;
+typedef struct orc_cuboid {
+    double R[9], p[3];       /* box frame -> world: x_w = R x_b + p */
+    double half[3];          /* the box is [-half, half] in its frame */
+} orc_cuboid;
+typedef struct orc_geometry {
+    int32_t n_caps, n_pairs, n_boxes, pad_;
+    orc_capsule caps[ORC_MAX_CAPS];
+    int32_t pairs[ORC_MAX_PAIRS][2];   /* self-collision capsule pairs */
+    orc_cuboid boxes[ORC_MAX_BOXES];   /* every capsule is checked against every box */
+} orc_geometry;
+double orc_seg_seg_dist2(const double a1[3], const double b1[3], const double a2[3],
+                         const double b2[3], double* t1, double* t2);
+double orc_seg_box_dist2(const double a[3], const double b[3], const double half[3], double* t);
+void   orc_capsules_world(const orc_robot* r, const orc_geometry* g, const double* q,
+                          double A[][3], double B[][3]);
+void   orc_clearance(const orc_robot* r, const orc_geometry* g, const double* q,
+                     double* self_min, double* env_min);
+void   orc_mask_geo(const orc_robot* r, const orc_params* P, const orc_geometry* g,
+                    double pen_collide, const float* cand, const double* targets, int T, int K,
+                    int Kp, uint8_t* mask, float* pen, double* err, double* clearance);
+
 /* ---- §III-B: dynamic-programming search over the T x K x K lattice ---- */
 int orc_dp_f32(const float* cand, const float* pen, int T, int K, int Kp, int n,
                int32_t* sel, float* best_cost, float* cost_T /*[Kp] or 0*/,

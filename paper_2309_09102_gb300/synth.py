@@ -29,7 +29,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 # stream ids (one per purpose, so every draw is independent of array sizes)
-S_ARM, S_TRUTH, S_NOISE, S_WB, S_OUT, S_OUTJ, S_OUTSIGN, S_OUTMAG, S_MIX = range(1, 10)
+S_ARM, S_TRUTH, S_NOISE, S_WB, S_OUT, S_OUTJ, S_OUTSIGN, S_OUTMAG, S_MIX, S_GEO = range(1, 11)
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -102,6 +102,58 @@ def draw_arm(seed: int, n: int = 7, wrist: bool = False, limit: float = 2.8) -> 
         alpha[4] = -math.pi / 2
         alpha[5] = math.pi / 2
     return Arm(a=a, d=d, alpha=alpha, lo=np.full(n, -limit), hi=np.full(n, limit))
+
+
+# --------------------------------------------------------------------- collision model
+@dataclass
+class Geometry:
+    """Collision model of a request (input data only): capsules fixed to DH frames
+    (frame 0 = base, j = the frame after joint j) with end points a, b in that frame
+    and a radius; the self-collision pairs (capsule indices); cuboid obstacles, each
+    the rotation R and centre p of its frame in the world and its half extents."""
+    cap_frame: np.ndarray   # [C] int
+    cap_a: np.ndarray       # [C][3]
+    cap_b: np.ndarray       # [C][3]
+    cap_r: np.ndarray       # [C]
+    pairs: np.ndarray       # [P][2] int
+    box_R: np.ndarray       # [B][3][3]
+    box_p: np.ndarray       # [B][3]
+    box_half: np.ndarray    # [B][3]
+
+
+def link_capsules(arm: Arm, radius: float = 0.03, skip: int = 2) -> Geometry:
+    """One capsule per link: in frame j (j = 1..n) from the frame's origin to the
+    origin of frame j-1, which sits at (-a_j, -d_j sin alpha_j, -d_j cos alpha_j)
+    there whatever q_j (the link is rigid). Pairs: capsules at least ``skip``
+    links apart (neighbours share a joint and always touch). No obstacles."""
+    n = arm.n
+    frame = np.arange(1, n + 1)
+    a = np.zeros((n, 3))
+    b = np.stack([-arm.a, -arm.d * np.sin(arm.alpha), -arm.d * np.cos(arm.alpha)], axis=1)
+    pairs = np.array([(u, v) for u in range(n) for v in range(u + skip, n)], dtype=np.int32)
+    return Geometry(frame, a, b, np.full(n, radius), pairs.reshape(-1, 2),
+                    np.zeros((0, 3, 3)), np.zeros((0, 3)), np.zeros((0, 3)))
+
+
+def with_boxes(geo: Geometry, seed: int, count: int, reach: tuple = (0.3, 0.9),
+               half: tuple = (0.03, 0.12)) -> Geometry:
+    """Add ``count`` cuboids: centre at a uniform direction and a distance U(reach)
+    from the base, half extents U(half), rotated by U(-pi, pi) about the world z."""
+    u = uniform(seed, S_GEO, 7 * count).reshape(count, 7)
+    phi = (2 * u[:, 0] - 1) * math.pi
+    ct = 2 * u[:, 1] - 1
+    az = 2 * math.pi * u[:, 2]
+    st = np.sqrt(1 - ct * ct)
+    dist = reach[0] + (reach[1] - reach[0]) * u[:, 3]
+    p = np.stack([st * np.cos(az), st * np.sin(az), ct], axis=1) * dist[:, None]
+    h = half[0] + (half[1] - half[0]) * u[:, 4:7]
+    R = np.zeros((count, 3, 3))
+    R[:, 0, 0] = np.cos(phi); R[:, 0, 1] = -np.sin(phi)
+    R[:, 1, 0] = np.sin(phi); R[:, 1, 1] = np.cos(phi)
+    R[:, 2, 2] = 1.0
+    return Geometry(geo.cap_frame, geo.cap_a, geo.cap_b, geo.cap_r, geo.pairs,
+                    np.concatenate([geo.box_R, R]), np.concatenate([geo.box_p, p]),
+                    np.concatenate([geo.box_half, h]))
 
 
 # --------------------------------------------------------------------- truth
