@@ -73,6 +73,35 @@ typedef enum cpp_status {
 #define CPP_MASK_POSE 4u      /* pose error above tau_pos or tau_rot (§II "Pose error") */
 #define CPP_MASK_NONFINITE 8u /* some joint value is NaN or inf: cost +inf, no other bit */
 #define CPP_MASK_PAD 16u      /* padding lane k >= K: cost +inf */
+#define CPP_MASK_COLLIDE 32u  /* a capsule pair or a capsule and a box overlap (§III-B, with a
+                                 collision model only; cost + pen_collide) */
+
+/* Collision model of a request (§III-B collision cost, §III-C capsule and cuboid
+ * distances): the robot as capsules (segment + radius) fixed to its DH frames
+ * (frame 0 = base, frame j = the frame after joint j), the self-collision pairs
+ * to test, and cuboid obstacles; every capsule is tested against every box.
+ * Clearance of a pair = segment distance - r_u - r_v; of a capsule and a box =
+ * segment-box distance - r_u; a candidate collides when its smallest clearance
+ * is negative. Host struct; the calls below copy it. */
+#define CPP_MAX_CAPSULES 12
+#define CPP_MAX_PAIRS 64
+#define CPP_MAX_BOXES 8
+typedef struct cpp_capsule {
+    int32_t frame;            /* 0..n */
+    int32_t reserved;
+    double a[3], b[3];        /* segment end points in the frame (m) */
+    double radius;            /* >= 0 (m) */
+} cpp_capsule_t;
+typedef struct cpp_cuboid {
+    double R[9], p[3];        /* box frame -> world, row-major: x_w = R x_b + p */
+    double half[3];           /* half extents >= 0: the box is [-half, half] in its frame */
+} cpp_cuboid_t;
+typedef struct cpp_geometry {
+    int32_t n_caps, n_pairs, n_boxes, reserved;
+    cpp_capsule_t caps[CPP_MAX_CAPSULES];
+    int32_t pairs[CPP_MAX_PAIRS][2];   /* capsule indices, u != v */
+    cpp_cuboid_t boxes[CPP_MAX_BOXES];
+} cpp_geometry_t;
 
 typedef struct cpp_robot {
     int32_t n;                      /* joints */
@@ -110,6 +139,7 @@ typedef struct cpp_params {
                               cpp_smooth_step; at most 1000 */
     int32_t reserved_;
     double smooth_lambda;  /* damping of the trajectory-length step (default 1; > 0) */
+    double pen_collide;    /* node cost of a colliding candidate (default 100, §III-B) */
 } cpp_params_t;
 
 #define CPP_DP_SUM 0     /* minimise the summed per-step L-inf joint jump */
@@ -158,6 +188,20 @@ cpp_status cpp_fk_pose_f64(const cpp_robot_t* robot, const double* q, int64_t N,
 cpp_status cpp_mask(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
                     const double* targets, int32_t T, int32_t K, int32_t Kp, uint8_t* mask,
                     float* pen, float* err, int32_t* dev_status, cpp_stream_t stream);
+
+/* cpp_mask with the collision model `geometry` (host pointer, copied; NULL =
+ * none): COLLIDE bit and + pen_collide per colliding candidate (the node's costs
+ * are summed in FP64 in the order limit, pose, collision and rounded once).
+ * clearance [T][Kp] FP32 (or NULL) receives the smallest clearance of every
+ * candidate (+inf without a model, NaN on padding and non-finite lanes). Distances
+ * are solved in FP32 (errors ~1e-6 m). INVALID_ARG also for a model with counts
+ * above the limits, frames above n, pair indices out of range or equal,
+ * non-finite values, negative radii or half extents. */
+cpp_status cpp_mask_geo(const cpp_robot_t* robot, const cpp_params_t* params,
+                        const cpp_geometry_t* geometry, const float* cand,
+                        const double* targets, int32_t T, int32_t K, int32_t Kp, uint8_t* mask,
+                        float* pen, float* err, float* clearance, int32_t* dev_status,
+                        cpp_stream_t stream);
 
 /* cpp_mask on the candidate lanes [k_begin, K) only (k_begin a multiple of 4); the
  * lanes below k_begin keep the mask and cost they already have. This is how a
@@ -285,6 +329,14 @@ cpp_status cpp_plan(const cpp_robot_t* robot, const cpp_params_t* params, const 
                     void* workspace, size_t ws_bytes, int32_t* sel, float* best_cost,
                     float* q_out, double* pose_err, cpp_report_t* report,
                     int32_t* dev_status, cpp_stream_t stream);
+/* cpp_plan with a collision model (host pointer, copied; NULL = none): the mask
+ * adds the collision cost of §III-B, so the search avoids colliding candidates. */
+cpp_status cpp_plan_geo(const cpp_robot_t* robot, const cpp_params_t* params,
+                        const cpp_geometry_t* geometry, const float* cand,
+                        const double* targets, int32_t T, int32_t K, int32_t Kp,
+                        void* workspace, size_t ws_bytes, int32_t* sel, float* best_cost,
+                        float* q_out, double* pose_err, cpp_report_t* report,
+                        int32_t* dev_status, cpp_stream_t stream);
 
 /* ------------------------------------------------------------------ many requests
  * One launch per stage for `count` requests of different T, K, Kp (same params).
@@ -300,6 +352,7 @@ typedef struct cpp_plan_desc {
     double* pose_err;          /* [T][2] */
     cpp_report_t* report;      /* [1] */
     float* best_cost;          /* [1] */
+    const cpp_geometry_t* geometry;  /* host pointer, copied at batch creation; NULL = none */
 } cpp_plan_desc_t;
 
 size_t cpp_plan_batch_workspace_size(const cpp_plan_desc_t* descs, int32_t count,
@@ -421,6 +474,7 @@ typedef struct cpp_plan_req {
     int32_t flags;             /* 0 or CPP_REQ_BORROW */
     const float* cand;         /* host [T][n][Kp] */
     const double* targets;     /* host [T][7] */
+    const cpp_geometry_t* geometry;  /* host, copied at submit; NULL = no collision model */
 } cpp_plan_req_t;
 
 typedef struct cpp_plan_result {  /* caller-owned HOST buffers; any pointer may be NULL */

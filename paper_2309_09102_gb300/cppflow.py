@@ -42,7 +42,7 @@ class Params(C.Structure):
         "lambda_up", "lambda_down", "lambda_min", "lambda_max", "freeze_step", "freeze_cost")] + [
         ("lm_iters", C.c_int32), ("free_mask", C.c_uint32), ("lm_fp64", C.c_int32),
         ("dp_objective", C.c_int32), ("smooth_rounds", C.c_int32), ("reserved_", C.c_int32),
-        ("smooth_lambda", C.c_double)]
+        ("smooth_lambda", C.c_double), ("pen_collide", C.c_double)]
 
 
 class Report(C.Structure):
@@ -53,11 +53,50 @@ class Report(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+MAX_CAPSULES, MAX_PAIRS, MAX_BOXES = 12, 64, 8
+MASK_COLLIDE = 32
+
+
+class Capsule(C.Structure):
+    _fields_ = [("frame", C.c_int32), ("reserved", C.c_int32), ("a", C.c_double * 3),
+                ("b", C.c_double * 3), ("radius", C.c_double)]
+
+
+class Cuboid(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("p", C.c_double * 3), ("half", C.c_double * 3)]
+
+
+class Geometry(C.Structure):
+    _fields_ = [("n_caps", C.c_int32), ("n_pairs", C.c_int32), ("n_boxes", C.c_int32),
+                ("reserved", C.c_int32), ("caps", Capsule * MAX_CAPSULES),
+                ("pairs", (C.c_int32 * 2) * MAX_PAIRS), ("boxes", Cuboid * MAX_BOXES)]
+
+
+def geometry_from(geo) -> Geometry:
+    """cpp_geometry_t of a collision model given as arrays (synth.Geometry fields)."""
+    g = Geometry()
+    g.n_caps, g.n_pairs, g.n_boxes = len(geo.cap_r), len(geo.pairs), len(geo.box_half)
+    if g.n_caps > MAX_CAPSULES or g.n_pairs > MAX_PAIRS or g.n_boxes > MAX_BOXES:
+        raise ValueError("collision model larger than the library's limits")
+    for c in range(g.n_caps):
+        g.caps[c].frame = int(geo.cap_frame[c])
+        g.caps[c].a[:] = [float(x) for x in geo.cap_a[c]]
+        g.caps[c].b[:] = [float(x) for x in geo.cap_b[c]]
+        g.caps[c].radius = float(geo.cap_r[c])
+    for k in range(g.n_pairs):
+        g.pairs[k][0], g.pairs[k][1] = int(geo.pairs[k][0]), int(geo.pairs[k][1])
+    for o in range(g.n_boxes):
+        g.boxes[o].R[:] = [float(x) for row in geo.box_R[o] for x in row]
+        g.boxes[o].p[:] = [float(x) for x in geo.box_p[o]]
+        g.boxes[o].half[:] = [float(x) for x in geo.box_half[o]]
+    return g
+
+
 class PlanDesc(C.Structure):
     _fields_ = [("T", C.c_int32), ("K", C.c_int32), ("Kp", C.c_int32), ("robot", C.c_int32),
                 ("cand", C.c_void_p), ("targets", C.c_void_p), ("sel", C.c_void_p),
                 ("q_out", C.c_void_p), ("pose_err", C.c_void_p), ("report", C.c_void_p),
-                ("best_cost", C.c_void_p)]
+                ("best_cost", C.c_void_p), ("geometry", C.c_void_p)]
 
 
 REPORT_BYTES = C.sizeof(Report)
@@ -81,7 +120,8 @@ class ServerConfig(C.Structure):
 
 class PlanReq(C.Structure):
     _fields_ = [("robot", C.c_void_p), ("T", C.c_int32), ("K", C.c_int32), ("Kp", C.c_int32),
-                ("flags", C.c_int32), ("cand", C.c_void_p), ("targets", C.c_void_p)]
+                ("flags", C.c_int32), ("cand", C.c_void_p), ("targets", C.c_void_p),
+                ("geometry", C.c_void_p)]
 
 
 class PlanResult(C.Structure):
@@ -110,6 +150,10 @@ _SIGS = {
     "cpp_fk_pose_f64": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
     "cpp_mask": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P]),
     "cpp_dp_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
+    "cpp_mask_geo": (C.c_int, [_P, _P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P,
+                               _P, _P, _P]),
+    "cpp_plan_geo": (C.c_int, [_P, _P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_size_t,
+                               _P, _P, _P, _P, _P, _P, _P]),
     "cpp_mask_range": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P,
                                  _P, _P, _P]),
     "cpp_dp_search_ex": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P,
@@ -236,6 +280,16 @@ def mask(robot: Robot, params: Params, cand, targets, K: int, mask_out, pen, err
                           stream_handle(stream)), "cpp_mask")
 
 
+def mask_geo(robot: Robot, params: Params, geometry: Geometry | None, cand, targets, K: int,
+             mask_out, pen, err=None, clearance=None, dev_status=None, stream=None):
+    """cpp_mask with a collision model (COLLIDE bit, collision cost, clearances)."""
+    T, n, Kp = cand.shape
+    g = C.byref(geometry) if geometry is not None else None
+    _check(lib().cpp_mask_geo(C.byref(robot), C.byref(params), g, ptr(cand), ptr(targets), T, K,
+                              Kp, ptr(mask_out), ptr(pen), ptr(err), ptr(clearance),
+                              ptr(dev_status), stream_handle(stream)), "cpp_mask_geo")
+
+
 def mask_range(robot: Robot, params: Params, cand, targets, K: int, k_begin: int, mask_out, pen,
                err=None, dev_status=None, stream=None):
     """cpp_mask on lanes [k_begin, K) only (appended candidates)."""
@@ -301,6 +355,18 @@ def plan(robot: Robot, params: Params, cand, targets, K: int, workspace, sel, be
                           ptr(workspace), nbytes, ptr(sel), ptr(best_cost), ptr(q_out),
                           ptr(pose_err), ptr(report), ptr(dev_status), stream_handle(stream)),
            "cpp_plan")
+
+
+def plan_geo(robot: Robot, params: Params, geometry: Geometry | None, cand, targets, K: int,
+             workspace, sel, best_cost, q_out, pose_err=None, report=None, dev_status=None,
+             stream=None):
+    T, n, Kp = cand.shape
+    nbytes = workspace.numel() * workspace.element_size()
+    g = C.byref(geometry) if geometry is not None else None
+    _check(lib().cpp_plan_geo(C.byref(robot), C.byref(params), g, ptr(cand), ptr(targets), T, K,
+                              Kp, ptr(workspace), nbytes, ptr(sel), ptr(best_cost), ptr(q_out),
+                              ptr(pose_err), ptr(report), ptr(dev_status), stream_handle(stream)),
+           "cpp_plan_geo")
 
 
 def plan_batch_workspace_size(descs, robots) -> int:
@@ -389,13 +455,15 @@ class Server:
         self.handle = h
         self._live = {}  # ticket -> (robot, inputs kept alive, shape)
 
-    def submit(self, robot: Robot, cand, targets, K: int, borrow: bool = False) -> int:
+    def submit(self, robot: Robot, cand, targets, K: int, borrow: bool = False,
+               geometry: Geometry | None = None) -> int:
         import numpy as np
         cand = np.ascontiguousarray(cand, dtype=np.float32)
         targets = np.ascontiguousarray(targets, dtype=np.float64)
         T, n, Kp = cand.shape
         req = PlanReq(C.addressof(robot), T, K, Kp, REQ_BORROW if borrow else 0,
-                      cand.ctypes.data, targets.ctypes.data)
+                      cand.ctypes.data, targets.ctypes.data,
+                      C.addressof(geometry) if geometry is not None else None)
         t = C.c_uint64()
         _check(lib().cpp_plan_submit(self.handle, C.byref(req), C.byref(t)), "cpp_plan_submit")
         self._live[t.value] = (robot, (cand, targets) if borrow else None, (T, n))

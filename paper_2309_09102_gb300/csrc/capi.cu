@@ -68,6 +68,8 @@ cpp_status check_params(const cpp_params_t* p) {
     return fail(CPP_ERR_INVALID_ARG, "smooth_rounds outside [0, 1000]");
   if (!(finite_d(p->smooth_lambda) && p->smooth_lambda > 0))
     return fail(CPP_ERR_INVALID_ARG, "smooth_lambda must be finite and > 0");
+  if (!(finite_d(p->pen_collide) && p->pen_collide >= 0))
+    return fail(CPP_ERR_INVALID_ARG, "pen_collide must be finite and >= 0");
   return CPP_OK;
 }
 
@@ -101,6 +103,61 @@ Req empty_req() {
 
 namespace cppflow {
 void set_last_error(const char* msg) { g_err = msg; }
+
+size_t geo_bytes() { return sizeof(GeoF); }
+
+bool make_geo(const cpp_geometry_t& g, int n, void* out, char* err) {
+  auto bad = [&](const char* m) {
+    snprintf(err, 160, "collision model: %s", m);
+    return false;
+  };
+  if (g.n_caps < 0 || g.n_caps > kMaxCaps || g.n_pairs < 0 || g.n_pairs > kMaxPairs ||
+      g.n_boxes < 0 || g.n_boxes > kMaxBoxes)
+    return bad("counts outside [0, CPP_MAX_CAPSULES / PAIRS / BOXES]");
+  GeoF f;
+  memset(&f, 0, sizeof(f));
+  f.n_caps = g.n_caps; f.n_pairs = g.n_pairs; f.n_boxes = g.n_boxes;
+  int order[kMaxCaps], pos[kMaxCaps], m = 0;
+  for (int fr = 0; fr <= n; ++fr) {  // sort capsules by frame, stable
+    f.frame_begin[fr] = m;
+    for (int c = 0; c < g.n_caps; ++c)
+      if (g.caps[c].frame == fr) { pos[c] = m; order[m++] = c; }
+  }
+  for (int fr = n + 1; fr < kMaxJ + 2; ++fr) f.frame_begin[fr] = m;
+  if (m != g.n_caps) return bad("a capsule frame is outside [0, n]");
+  for (int k = 0; k < m; ++k) {
+    const cpp_capsule_t& c = g.caps[order[k]];
+    for (int q = 0; q < 3; ++q) {
+      if (!finite_d(c.a[q]) || !finite_d(c.b[q])) return bad("non-finite capsule end point");
+      f.a[k][q] = (float)c.a[q];
+      f.b[k][q] = (float)c.b[q];
+    }
+    if (!(finite_d(c.radius) && c.radius >= 0)) return bad("capsule radius must be finite and >= 0");
+    f.r[k] = (float)c.radius;
+  }
+  for (int k = 0; k < g.n_pairs; ++k) {
+    const int u = g.pairs[k][0], v = g.pairs[k][1];
+    if (u < 0 || u >= g.n_caps || v < 0 || v >= g.n_caps || u == v)
+      return bad("pair index out of range or a capsule paired with itself");
+    f.pu[k] = (int8_t)pos[u];
+    f.pv[k] = (int8_t)pos[v];
+  }
+  for (int o = 0; o < g.n_boxes; ++o) {
+    const cpp_cuboid_t& b = g.boxes[o];
+    for (int q = 0; q < 9; ++q)
+      if (!finite_d(b.R[q])) return bad("non-finite box rotation");
+    for (int q = 0; q < 3; ++q) {
+      if (!finite_d(b.p[q])) return bad("non-finite box centre");
+      if (!(finite_d(b.half[q]) && b.half[q] >= 0)) return bad("box half extents must be >= 0");
+      f.p[o][q] = (float)b.p[q];
+      f.h[o][q] = (float)b.half[q];
+    }
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) f.Rt[o][3 * r + c] = (float)b.R[3 * c + r];  // transpose
+  }
+  memcpy(out, &f, sizeof(f));
+  return true;
+}
 }  // namespace cppflow
 
 extern "C" {
@@ -148,6 +205,7 @@ void cpp_params_default(cpp_params_t* p) {
   p->smooth_rounds = 0;
   p->reserved_ = 0;
   p->smooth_lambda = 1.0;
+  p->pen_collide = 100.0;
 }
 
 cpp_status cpp_fk_batch(const cpp_robot_t* robot, const float* q, int64_t N, float* R, float* p,
@@ -166,9 +224,20 @@ cpp_status cpp_fk_pose_f64(const cpp_robot_t* robot, const double* q, int64_t N,
   return cuda_status(launch_fk_pose64(*robot, q, N, pose, (cudaStream_t)stream), "cpp_fk_pose_f64");
 }
 
-static cpp_status mask_impl(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
+// A collision model into a single request's source (by value), validated.
+static cpp_status set_geo(SingleSrc& s, const cpp_geometry_t* geometry, int n) {
+  s.has_geo = 0;
+  if (!geometry) return CPP_OK;
+  char msg[160];
+  if (!make_geo(*geometry, n, &s.geo, msg)) return fail(CPP_ERR_INVALID_ARG, "%s", msg);
+  s.has_geo = 1;
+  return CPP_OK;
+}
+
+static cpp_status mask_impl(const cpp_robot_t* robot, const cpp_params_t* params,
+                            const cpp_geometry_t* geometry, const float* cand,
                             const double* targets, int32_t T, int32_t K, int32_t Kp,
-                            int32_t k_begin, uint8_t* mask, float* pen, float* err,
+                            int32_t k_begin, uint8_t* mask, float* pen, float* err, float* clear,
                             int32_t* dev_status, cpp_stream_t stream) {
   if (cpp_status s = check_robot(robot)) return s;
   if (cpp_status s = check_params(params)) return s;
@@ -176,29 +245,42 @@ static cpp_status mask_impl(const cpp_robot_t* robot, const cpp_params_t* params
   if (k_begin < 0 || k_begin > K || k_begin % 4 != 0)
     return fail(CPP_ERR_INVALID_ARG, "k_begin = %d must be a multiple of 4 in [0, K]", k_begin);
   if (!cand || !targets || !mask || !pen) return fail(CPP_ERR_INVALID_ARG, "NULL buffer");
-  if (!aligned(cand, 16) || !aligned(pen, 16) || !aligned(mask, 4) || (err && !aligned(err, 16)))
-    return fail(CPP_ERR_INVALID_ARG, "cand/pen/err must be 16-byte and mask 4-byte aligned");
+  if (!aligned(cand, 16) || !aligned(pen, 16) || !aligned(mask, 4) || (err && !aligned(err, 16)) ||
+      (clear && !aligned(clear, 16)))
+    return fail(CPP_ERR_INVALID_ARG, "cand/pen/err/clearance must be 16-byte and mask 4-byte aligned");
   SingleSrc s;
   s.r = empty_req();
   s.r.T = T; s.r.K = K; s.r.Kp = Kp; s.r.n = robot->n; s.r.k_begin = k_begin;
   s.r.cand = cand; s.r.targets = targets; s.r.mask = mask; s.r.pen = pen; s.r.err = err;
+  s.r.clear = clear;
   s.r.status = dev_status;
   s.robot = *robot;
+  if (cpp_status e = set_geo(s, geometry, robot->n)) return e;
   return cuda_status(launch_mask(s, *params, (cudaStream_t)stream), "cpp_mask");
 }
 
 cpp_status cpp_mask(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
                     const double* targets, int32_t T, int32_t K, int32_t Kp, uint8_t* mask,
                     float* pen, float* err, int32_t* dev_status, cpp_stream_t stream) {
-  return mask_impl(robot, params, cand, targets, T, K, Kp, 0, mask, pen, err, dev_status, stream);
+  return mask_impl(robot, params, nullptr, cand, targets, T, K, Kp, 0, mask, pen, err, nullptr,
+                   dev_status, stream);
+}
+
+cpp_status cpp_mask_geo(const cpp_robot_t* robot, const cpp_params_t* params,
+                        const cpp_geometry_t* geometry, const float* cand,
+                        const double* targets, int32_t T, int32_t K, int32_t Kp, uint8_t* mask,
+                        float* pen, float* err, float* clearance, int32_t* dev_status,
+                        cpp_stream_t stream) {
+  return mask_impl(robot, params, geometry, cand, targets, T, K, Kp, 0, mask, pen, err, clearance,
+                   dev_status, stream);
 }
 
 cpp_status cpp_mask_range(const cpp_robot_t* robot, const cpp_params_t* params,
                           const float* cand, const double* targets, int32_t T, int32_t K,
                           int32_t Kp, int32_t k_begin, uint8_t* mask, float* pen, float* err,
                           int32_t* dev_status, cpp_stream_t stream) {
-  return mask_impl(robot, params, cand, targets, T, K, Kp, k_begin, mask, pen, err, dev_status,
-                   stream);
+  return mask_impl(robot, params, nullptr, cand, targets, T, K, Kp, k_begin, mask, pen, err,
+                   nullptr, dev_status, stream);
 }
 
 size_t cpp_dp_workspace_size(int32_t T, int32_t Kp) {
@@ -308,6 +390,16 @@ cpp_status cpp_plan(const cpp_robot_t* robot, const cpp_params_t* params, const 
                     size_t ws_bytes, int32_t* sel, float* best_cost, float* q_out,
                     double* pose_err, cpp_report_t* report, int32_t* dev_status,
                     cpp_stream_t stream) {
+  return cpp_plan_geo(robot, params, nullptr, cand, targets, T, K, Kp, workspace, ws_bytes, sel,
+                      best_cost, q_out, pose_err, report, dev_status, stream);
+}
+
+cpp_status cpp_plan_geo(const cpp_robot_t* robot, const cpp_params_t* params,
+                        const cpp_geometry_t* geometry, const float* cand,
+                        const double* targets, int32_t T, int32_t K, int32_t Kp, void* workspace,
+                        size_t ws_bytes, int32_t* sel, float* best_cost, float* q_out,
+                        double* pose_err, cpp_report_t* report, int32_t* dev_status,
+                        cpp_stream_t stream) {
   if (cpp_status s = check_robot(robot)) return s;
   if (cpp_status s = check_params(params)) return s;
   const int n = robot->n;
@@ -337,6 +429,7 @@ cpp_status cpp_plan(const cpp_robot_t* robot, const cpp_params_t* params, const 
   s.r.q_in = s.r.q_seed; s.r.q_out = q_out; s.r.pose_err = pose_err; s.r.report = report;
   s.r.status = dev_status;
   s.robot = *robot;
+  if (cpp_status e = set_geo(s, geometry, n)) return e;
   if (cpp_status e = cuda_status(launch_mask(s, *params, st), "cpp_plan/mask")) return e;
   if (cpp_status e = cuda_status(launch_dp(s, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD |
                                                    CPP_STAGE_BACKTRACK, params->dp_objective, st),
@@ -416,6 +509,7 @@ struct cpp_batch {
   std::vector<Req> reqs;            // descriptor order (host copy)
   std::vector<long long> edges;     // (T - 1) Kp^2 per request
   std::vector<SchedGroup> groups;   // cluster groups, then the one-CTA group (last)
+  bool any_geo;  // some request has a collision model
   double alpha;
   int cpc;  // successor candidates per CTA of the cluster form (0: default)
   int heavy;
@@ -524,7 +618,7 @@ cudaError_t run_forward(cpp_batch* b, cudaStream_t st) {
 cpp_status run_stages(cpp_batch* b, uint32_t stages, cudaStream_t st) {
   if (stages & CPP_STAGE_MASK)
     if (cpp_status e = cuda_status(launch_mask_batch(b->src, b->n, b->count, b->max_tasks,
-                                                     b->params, st), "batch/mask"))
+                                                     b->params, b->any_geo, st), "batch/mask"))
       return e;
   if (stages & CPP_STAGE_LAYER_MIN)
     if (cpp_status e = cuda_status(launch_dp_batch(b->src, CPP_STAGE_LAYER_MIN, b->params.dp_objective,
@@ -621,6 +715,8 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
   char* ws = static_cast<char*>(workspace);
   std::vector<Req> reqs(count);
   std::vector<long long> edges(count);
+  std::vector<std::vector<char>> geos;  // device forms of the requests' collision models
+  std::vector<char*> geo_dst;
   for (int r = 0; r < count; ++r) {
     const cpp_plan_desc_t& d = descs[r];
     const PlanLayout& L = B.L[r];
@@ -637,10 +733,22 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
     q.q_seed = reinterpret_cast<float*>(b + L.q_seed);
     q.q_in = q.q_seed; q.q_out = d.q_out; q.pose_err = d.pose_err; q.report = d.report;
     q.status = dev_status ? dev_status + r : nullptr;
+    if (d.geometry) {
+      geos.emplace_back(geo_bytes());
+      char msg[160];
+      if (!make_geo(*d.geometry, n, geos.back().data(), msg))
+        return fail(CPP_ERR_INVALID_ARG, "request %d: %s", r, msg);
+      geo_dst.push_back(b + L.geo);
+      q.geo = reinterpret_cast<const GeoF*>(b + L.geo);
+    }
     reqs[r] = q;
     edges[r] = (long long)(d.T - 1) * d.Kp * d.Kp;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  for (size_t k = 0; k < geos.size(); ++k)  // pageable: staged before the call returns
+    if (cpp_status e = cuda_status(cudaMemcpyAsync(geo_dst[k], geos[k].data(), geo_bytes(),
+                                                   cudaMemcpyHostToDevice, st), "cpp_batch_create"))
+      return e;
   // pageable sources: the copies are staged before cudaMemcpyAsync returns
   if (cpp_status e = cuda_status(cudaMemcpyAsync(ws + B.reqs, reqs.data(), sizeof(Req) * count,
                                                  cudaMemcpyHostToDevice, st), "cpp_batch_create"))
@@ -659,6 +767,7 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
   b->d_robots = reinterpret_cast<const cpp_robot_t*>(ws + B.robots);
   b->reqs = std::move(reqs);
   b->edges = std::move(edges);
+  b->any_geo = !geos.empty();
   b->alpha = 0;
   b->cpc = 0;
   b->heavy = 0;

@@ -1,0 +1,154 @@
+// collide.cuh -- capsule / cuboid clearances of one configuration in FP32 (paper
+// §III-B collision cost, §III-C "Robot-robot" and "Robot-environment collision
+// avoidance"): the robot as capsules fixed to its DH frames, obstacles as boxes.
+#pragma once
+
+#include <math_constants.h>
+
+#include "common.cuh"
+
+namespace cppflow {
+
+__device__ __forceinline__ float clamp01f(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
+
+__device__ __forceinline__ float d2_pts(const float* x, const float* y) {
+  const float d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+  return d0 * d0 + d1 * d1 + d2 * d2;
+}
+
+// Squared distance of segments a1 + s (b1 - a1), a2 + t (b2 - a2), s, t in [0, 1]:
+// the convex QP solved by its active sets -- the interior stationary point when
+// it lies in the unit square, and the four edges, each minimised by clamping its
+// 1-D stationary point; the smallest directly evaluated |P - Q|^2 wins.
+__device__ __forceinline__ float seg_seg_d2(const float* a1, const float* b1, const float* a2,
+                                            const float* b2) {
+  float d1[3], d2[3], r[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) { d1[k] = b1[k] - a1[k]; d2[k] = b2[k] - a2[k]; r[k] = a1[k] - a2[k]; }
+  const float A = d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2];
+  const float C = d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2];
+  const float B = d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2];
+  const float D = d1[0] * r[0] + d1[1] * r[1] + d1[2] * r[2];
+  const float E = d2[0] * r[0] + d2[1] * r[1] + d2[2] * r[2];
+  float cs[5], ct[5];
+  const float det = A * C - B * B;
+  const float si = (B * E - C * D) / det, ti = (A * E - B * D) / det;
+  const bool inner = det > 1e-12f * A * C && si >= 0.f && si <= 1.f && ti >= 0.f && ti <= 1.f;
+  cs[0] = inner ? si : 0.f;                 ct[0] = inner ? ti : 0.f;
+  cs[1] = 0.f;                              ct[1] = C > 0.f ? clamp01f(E / C) : 0.f;
+  cs[2] = 1.f;                              ct[2] = C > 0.f ? clamp01f((B + E) / C) : 0.f;
+  cs[3] = A > 0.f ? clamp01f(-D / A) : 0.f; ct[3] = 0.f;
+  cs[4] = A > 0.f ? clamp01f((B - D) / A) : 0.f; ct[4] = 1.f;
+  float best = CUDART_INF_F;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    float P[3], Q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { P[k] = a1[k] + cs[c] * d1[k]; Q[k] = a2[k] + ct[c] * d2[k]; }
+    best = fminf(best, d2_pts(P, Q));
+  }
+  return best;
+}
+
+__device__ __forceinline__ float box_g(const float* a, const float* d, const float* h, float t) {
+  float g = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float x = a[k] + t * d[k];
+    const float e = x > h[k] ? x - h[k] : (x < -h[k] ? x + h[k] : 0.f);
+    g += e * e;
+  }
+  return g;
+}
+
+// Squared distance of the segment a + t (b - a), t in [0, 1], to the box [-h, h]
+// (box frame): for fixed t the nearest box point is the clamped point, so the
+// cost is convex and piecewise quadratic in t with breakpoints where a
+// coordinate crosses a face plane; each piece's quadratic (faces fixed by its
+// midpoint) is minimised by clamping its stationary point to the piece, and the
+// piece's ends are evaluated too.
+__device__ __forceinline__ float seg_box_d2(const float* a, const float* b, const float* h) {
+  float d[3], br[8];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = b[k] - a[k];
+  int nb = 0;
+  br[nb++] = 0.f;
+  br[nb++] = 1.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (d[k] == 0.f) continue;
+    const float t0 = (-h[k] - a[k]) / d[k], t1 = (h[k] - a[k]) / d[k];
+    if (t0 > 0.f && t0 < 1.f) br[nb++] = t0;
+    if (t1 > 0.f && t1 < 1.f) br[nb++] = t1;
+  }
+  for (int i = 1; i < nb; ++i)
+    for (int j = i; j > 0 && br[j] < br[j - 1]; --j) {
+      const float x = br[j]; br[j] = br[j - 1]; br[j - 1] = x;
+    }
+  float best = box_g(a, d, h, 0.f);
+  for (int i = 0; i + 1 < nb; ++i) {
+    const float ta = br[i], tz = br[i + 1], tm = 0.5f * (ta + tz);
+    float num = 0.f, den = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float x = a[k] + tm * d[k];
+      if (x > h[k]) { num += d[k] * (h[k] - a[k]); den += d[k] * d[k]; }
+      else if (x < -h[k]) { num += d[k] * (-h[k] - a[k]); den += d[k] * d[k]; }
+    }
+    best = fminf(best, box_g(a, d, h, tz));
+    if (den > 0.f) best = fminf(best, box_g(a, d, h, fminf(fmaxf(num / den, ta), tz)));
+  }
+  return best;
+}
+
+// World end points of the capsules of frame f, given that frame's pose.
+__device__ __forceinline__ void place_caps(const GeoF& g, int f, const float R[9], const float p[3],
+                                           float (*cA)[3], float (*cB)[3]) {
+  for (int c = g.frame_begin[f]; c < g.frame_begin[f + 1]; ++c) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cA[c][k] = R[3 * k] * g.a[c][0] + R[3 * k + 1] * g.a[c][1] + R[3 * k + 2] * g.a[c][2] + p[k];
+      cB[c][k] = R[3 * k] * g.b[c][0] + R[3 * k + 1] * g.b[c][1] + R[3 * k + 2] * g.b[c][2] + p[k];
+    }
+  }
+}
+
+// Smallest clearance over the listed pairs (segment distance - r_u - r_v) and over
+// every capsule and box (segment-box distance - r_c); +inf when both lists are
+// empty. A pair's exact distance is computed only when its bounding-sphere lower
+// bound is below the running minimum, so the result is the exact minimum.
+__device__ __forceinline__ float clearance(const GeoF& g, const float (*cA)[3],
+                                           const float (*cB)[3]) {
+  float cl = CUDART_INF_F;
+  for (int k = 0; k < g.n_pairs; ++k) {
+    const int u = g.pu[k], v = g.pv[k];
+    float mu[3], mv[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) { mu[q] = 0.5f * (cA[u][q] + cB[u][q]); mv[q] = 0.5f * (cA[v][q] + cB[v][q]); }
+    const float lb = sqrtf(d2_pts(mu, mv)) - 0.5f * sqrtf(d2_pts(cA[u], cB[u])) -
+                     0.5f * sqrtf(d2_pts(cA[v], cB[v])) - g.r[u] - g.r[v];
+    if (lb >= cl) continue;
+    cl = fminf(cl, sqrtf(seg_seg_d2(cA[u], cB[u], cA[v], cB[v])) - g.r[u] - g.r[v]);
+  }
+  for (int o = 0; o < g.n_boxes; ++o) {
+    const float hr = sqrtf(g.h[o][0] * g.h[o][0] + g.h[o][1] * g.h[o][1] + g.h[o][2] * g.h[o][2]);
+    for (int c = 0; c < g.n_caps; ++c) {
+      float a[3], b[3], m[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) m[q] = 0.5f * (cA[c][q] + cB[c][q]);
+      const float lb = sqrtf(d2_pts(m, g.p[o])) - 0.5f * sqrtf(d2_pts(cA[c], cB[c])) - hr - g.r[c];
+      if (lb >= cl) continue;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        a[q] = g.Rt[o][3 * q] * (cA[c][0] - g.p[o][0]) + g.Rt[o][3 * q + 1] * (cA[c][1] - g.p[o][1]) +
+               g.Rt[o][3 * q + 2] * (cA[c][2] - g.p[o][2]);
+        b[q] = g.Rt[o][3 * q] * (cB[c][0] - g.p[o][0]) + g.Rt[o][3 * q + 1] * (cB[c][1] - g.p[o][1]) +
+               g.Rt[o][3 * q + 2] * (cB[c][2] - g.p[o][2]);
+      }
+      cl = fminf(cl, sqrtf(seg_box_d2(a, b, g.h[o])) - g.r[c]);
+    }
+  }
+  return cl;
+}
+
+}  // namespace cppflow

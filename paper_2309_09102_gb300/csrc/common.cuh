@@ -18,6 +18,21 @@ constexpr int kMaxJ = CPP_MAX_JOINTS;
 
 // ------------------------------------------------------------------ request views
 // One request as the kernels see it (device pointers; unused ones may be null).
+constexpr int kMaxCaps = CPP_MAX_CAPSULES;
+constexpr int kMaxPairs = CPP_MAX_PAIRS;
+constexpr int kMaxBoxes = CPP_MAX_BOXES;
+
+// Device copy of a cpp_geometry_t (collision model): FP32, capsules sorted by
+// frame (those of frame f are [frame_begin[f], frame_begin[f + 1])), pairs
+// renumbered to that order, box rotations transposed (world -> box).
+struct GeoF {
+  int n_caps, n_pairs, n_boxes, pad_;
+  int frame_begin[kMaxJ + 2];
+  float a[kMaxCaps][3], b[kMaxCaps][3], r[kMaxCaps];
+  int8_t pu[kMaxPairs], pv[kMaxPairs];
+  float Rt[kMaxBoxes][9], p[kMaxBoxes][3], h[kMaxBoxes][3];
+};
+
 struct Req {
   int T, K, Kp, n;
   int k_begin;               // first candidate lane the mask writes (a multiple of 4)
@@ -40,21 +55,29 @@ struct Req {
   double* pose_err;          // [T][2] or null
   cpp_report_t* report;      // [1] or null
   int32_t* status;           // [1] or null
+  const GeoF* geo;           // collision model or null
+  float* clear;              // [T][Kp] smallest clearance or null
 };
 
 // Kernels read requests and robots through one of two sources: a single request
 // carried in the kernel parameters, or device arrays for a batch.
+// A single request carries its collision model by value (has_geo); a batch
+// request points at its model in the workspace (Req::geo).
 struct SingleSrc {
   Req r;
   cpp_robot_t robot;
+  int has_geo = 0;
+  GeoF geo;
   __device__ __forceinline__ const Req& req(int) const { return r; }
   __device__ __forceinline__ const cpp_robot_t& rob(int) const { return robot; }
+  __device__ __forceinline__ const GeoF* geom(const Req&) const { return has_geo ? &geo : nullptr; }
 };
 struct BatchSrc {
   const Req* r;
   const cpp_robot_t* robots;
   __device__ __forceinline__ const Req& req(int i) const { return r[i]; }
   __device__ __forceinline__ const cpp_robot_t& rob(int i) const { return robots[i]; }
+  __device__ __forceinline__ const GeoF* geom(const Req& q) const { return q.geo; }
 };
 
 __device__ __forceinline__ void raise_status(int32_t* st, int code) {

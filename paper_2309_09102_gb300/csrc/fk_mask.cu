@@ -10,6 +10,7 @@
 // contiguous bytes per warp per joint), runs the FP32 DH chain for its four
 // candidates in registers, and writes one uchar4 mask word, one float4 of costs
 // and two float4 of errors.
+#include "collide.cuh"
 #include "internal.h"
 
 namespace cppflow {
@@ -21,7 +22,8 @@ constexpr int kMaskTasksPerWarp = 4;
 
 struct MaskArgs {
   float tau_pos, tau_rot;
-  float pen_table[4];  // [limit bit | pose bit << 1], each formed in FP64, rounded once
+  float pen_table[8];  // [limit bit | pose bit << 1 | collision bit << 2]: each the FP64 sum
+                       // of its costs in that order, rounded once
   double near_margin;
 };
 
@@ -45,12 +47,31 @@ __device__ __forceinline__ void warp_target_f32(const double* t7, int lane, floa
   Rt[6] = 2.f * (x * z - w * y); Rt[7] = 2.f * (y * z + w * x); Rt[8] = 1.f - 2.f * (x * x + y * y);
 }
 
+// FP32 FK as fk_f32 (the same operations, so the same pose), placing the world
+// end points of each frame's capsules as the frame is reached.
 template <int NJ>
+__device__ __forceinline__ void fk_caps(const RobotF& rb, const GeoF& g, const float* q, float R[9],
+                                        float p[3], float (*cA)[3], float (*cB)[3]) {
+  pose_identity(R, p);
+  place_caps(g, 0, R, p, cA, cB);
+  const int n = NJ ? NJ : rb.n;
+#pragma unroll
+  for (int j = 0; j < (NJ ? NJ : kMaxJ); ++j) {
+    if (!NJ && j >= n) break;
+    float s, c;
+    __sincosf(q[j] + rb.th0[j], &s, &c);
+    dh_step(R, p, c, s, rb.ca[j], rb.sa[j], rb.a[j], rb.d[j]);
+    place_caps(g, j + 1, R, p, cA, cB);
+  }
+}
+
+template <int NJ, bool COLL>
 __device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, const float* q,
                                          int n, bool pad, const float Rt[9], const float pt[3],
-                                         uint8_t& bits, float& cost, float& epos, float& erot) {
+                                         const GeoF* g, uint8_t& bits, float& cost, float& epos,
+                                         float& erot, float& clr) {
   if (pad) {
-    bits = CPP_MASK_PAD; cost = CUDART_INF_F; epos = erot = CUDART_NAN_F;
+    bits = CPP_MASK_PAD; cost = CUDART_INF_F; epos = erot = clr = CUDART_NAN_F;
     return;
   }
   bool finite = true;
@@ -64,27 +85,46 @@ __device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, co
     if (v < rb.nlo[j] || v > rb.nhi[j]) b |= CPP_MASK_NEAR;
   }
   if (!finite) {
-    bits = CPP_MASK_NONFINITE; cost = CUDART_INF_F; epos = erot = CUDART_NAN_F;
+    bits = CPP_MASK_NONFINITE; cost = CUDART_INF_F; epos = erot = clr = CUDART_NAN_F;
     return;
   }
   float R[9], p[3];
-  fk_f32<NJ>(rb, q, R, p);
+  clr = CUDART_INF_F;
+  if (COLL && g) {
+    float cA[kMaxCaps][3], cB[kMaxCaps][3];
+    fk_caps<NJ>(rb, *g, q, R, p, cA, cB);
+    clr = clearance(*g, cA, cB);
+    if (clr < 0.f) b |= CPP_MASK_COLLIDE;
+  } else {
+    fk_f32<NJ>(rb, q, R, p);
+  }
   const float dx = p[0] - pt[0], dy = p[1] - pt[1], dz = p[2] - pt[2];
   epos = sqrtf(dx * dx + dy * dy + dz * dz);
   erot = geodesic<float>(Rt, R);
   if (epos > a.tau_pos || erot > a.tau_rot) b |= CPP_MASK_POSE;
   bits = (uint8_t)b;
   const bool lim = (b & (CPP_MASK_OUT | CPP_MASK_NEAR)) != 0, pose = (b & CPP_MASK_POSE) != 0;
-  cost = lim ? (pose ? a.pen_table[3] : a.pen_table[1]) : (pose ? a.pen_table[2] : a.pen_table[0]);
+  const bool coll = (b & CPP_MASK_COLLIDE) != 0;
+  const float c0 = lim ? (pose ? a.pen_table[3] : a.pen_table[1]) : (pose ? a.pen_table[2] : a.pen_table[0]);
+  const float c1 = lim ? (pose ? a.pen_table[7] : a.pen_table[5]) : (pose ? a.pen_table[6] : a.pen_table[4]);
+  cost = coll ? c1 : c0;
 }
 
-template <int NJ, class Src>
+template <int NJ, bool COLL, class Src>
 __global__ void __launch_bounds__(kMaskThreads) mask_kernel(const __grid_constant__ Src src,
                                                              const MaskArgs a) {
   const Req& rq = src.req(blockIdx.y);
   __shared__ RobotF rb;
+  __shared__ GeoF gsh;
   stage_robot(src.rob(rq.robot), a.near_margin, &rb, nullptr);
+  const GeoF* gsrc = COLL ? src.geom(rq) : nullptr;
+  if (COLL && gsrc) {  // one request per block: stage its model
+    const uint32_t* from = reinterpret_cast<const uint32_t*>(gsrc);
+    uint32_t* to = reinterpret_cast<uint32_t*>(&gsh);
+    for (int w = threadIdx.x; w < (int)(sizeof(GeoF) / 4); w += kMaskThreads) to[w] = from[w];
+  }
   __syncthreads();
+  const GeoF* g = (COLL && gsrc) ? &gsh : nullptr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (rq.Kp + kMaskBlockK - 1) / kMaskBlockK;
   const long long ntask = (long long)rq.T * nblk;
@@ -110,7 +150,7 @@ __global__ void __launch_bounds__(kMaskThreads) mask_kernel(const __grid_constan
       qv[j] = __ldg(reinterpret_cast<const float4*>(base + (size_t)j * rq.Kp));
     }
     uint8_t bits[4];
-    float cost[4], ep[4], er[4];
+    float cost[4], ep[4], er[4], cl[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       float q[NJ ? NJ : kMaxJ];
@@ -119,7 +159,8 @@ __global__ void __launch_bounds__(kMaskThreads) mask_kernel(const __grid_constan
         if (!NJ && j >= n) break;
         q[j] = c == 0 ? qv[j].x : c == 1 ? qv[j].y : c == 2 ? qv[j].z : qv[j].w;
       }
-      mask_one<NJ>(rb, a, q, n, k0 + c >= rq.K, Rt, pt, bits[c], cost[c], ep[c], er[c]);
+      mask_one<NJ, COLL>(rb, a, q, n, k0 + c >= rq.K, Rt, pt, g, bits[c], cost[c], ep[c], er[c],
+                         cl[c]);
     }
     const size_t o = (size_t)i * rq.Kp + k0;
     *reinterpret_cast<uchar4*>(rq.mask + o) = make_uchar4(bits[0], bits[1], bits[2], bits[3]);
@@ -129,6 +170,8 @@ __global__ void __launch_bounds__(kMaskThreads) mask_kernel(const __grid_constan
       e[0] = make_float4(ep[0], er[0], ep[1], er[1]);
       e[1] = make_float4(ep[2], er[2], ep[3], er[3]);
     }
+    if (rq.clear)
+      *reinterpret_cast<float4*>(rq.clear + o) = make_float4(cl[0], cl[1], cl[2], cl[3]);
   }
 }
 
@@ -193,37 +236,46 @@ static MaskArgs make_mask_args(const cpp_params_t& P) {
   MaskArgs a;
   a.tau_pos = (float)P.tau_pos;
   a.tau_rot = (float)P.tau_rot;
-  a.pen_table[0] = 0.f;
-  a.pen_table[1] = (float)P.pen_limit;
-  a.pen_table[2] = (float)P.pen_pose;
-  a.pen_table[3] = (float)(P.pen_limit + P.pen_pose);
+  for (int m = 0; m < 8; ++m) {
+    double c = 0.0;
+    if (m & 1) c += P.pen_limit;
+    if (m & 2) c += P.pen_pose;
+    if (m & 4) c += P.pen_collide;
+    a.pen_table[m] = (float)c;
+  }
   a.near_margin = P.near_margin;
   return a;
 }
 
+template <bool COLL, class Src>
+static void launch_mask_c(const Src& src, int n, dim3 grid, const MaskArgs& a, cudaStream_t st) {
+  switch (n) {
+    case 6: mask_kernel<6, COLL, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+    case 7: mask_kernel<7, COLL, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+    case 9: mask_kernel<9, COLL, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+    default: mask_kernel<0, COLL, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+  }
+}
+
 template <class Src>
 static cudaError_t launch_mask_t(const Src& src, int n, int nreq, long long max_tasks,
-                                 const cpp_params_t& P, cudaStream_t st) {
+                                 const cpp_params_t& P, bool coll, cudaStream_t st) {
   const MaskArgs a = make_mask_args(P);
   constexpr int per_block = kMaskWarps * kMaskTasksPerWarp;
   dim3 grid((unsigned)((max_tasks + per_block - 1) / per_block), (unsigned)nreq);
-  switch (n) {
-    case 6: mask_kernel<6, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
-    case 7: mask_kernel<7, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
-    case 9: mask_kernel<9, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
-    default: mask_kernel<0, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
-  }
+  if (coll) launch_mask_c<true>(src, n, grid, a, st);
+  else launch_mask_c<false>(src, n, grid, a, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mask(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st) {
   const long long tasks = (long long)s.r.T * ((s.r.Kp + kMaskBlockK - 1) / kMaskBlockK);
-  return launch_mask_t(s, s.r.n, 1, tasks, P, st);
+  return launch_mask_t(s, s.r.n, 1, tasks, P, s.has_geo != 0, st);
 }
 
 cudaError_t launch_mask_batch(const BatchSrc& s, int n, int nreq, long long max_tasks,
-                              const cpp_params_t& P, cudaStream_t st) {
-  return launch_mask_t(s, n, nreq, max_tasks, P, st);
+                              const cpp_params_t& P, bool any_geo, cudaStream_t st) {
+  return launch_mask_t(s, n, nreq, max_tasks, P, any_geo, st);
 }
 
 long long mask_tasks(int T, int Kp) {

@@ -13,7 +13,7 @@ namespace cppflow {
 // fk_mask.cu
 cudaError_t launch_mask(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st);
 cudaError_t launch_mask_batch(const BatchSrc& s, int n, int nreq, long long max_tasks,
-                              const cpp_params_t& P, cudaStream_t st);
+                              const cpp_params_t& P, bool any_geo, cudaStream_t st);
 long long mask_tasks(int T, int Kp);
 cudaError_t launch_fk_batch(const cpp_robot_t& r, const float* q, long long N, float* R,
                             float* p, cudaStream_t st);
@@ -61,6 +61,11 @@ cudaError_t launch_check_batch(const BatchSrc& s, int nreq, const cpp_params_t& 
 
 // capi.cu
 void set_last_error(const char* msg);  // message returned by cpp_last_error()
+size_t geo_bytes();                    // sizeof(GeoF)
+// Validate a host collision model for an n-joint robot and convert it to the
+// device form (FP32, capsules sorted by frame) in `out` (geo_bytes() bytes).
+// Returns false with a message in err (>= 160 bytes) when the model is invalid.
+bool make_geo(const cpp_geometry_t& g, int n, void* out, char* err);
 
 // ------------------------------------------------------------------ workspace layouts
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -78,9 +83,10 @@ inline DpLayout dp_layout(int T, int Kp) {
   return L;
 }
 
-struct PlanLayout {  // scratch of one whole plan: the search's, masks, node costs, seed
+struct PlanLayout {  // scratch of one whole plan: the search's, masks, node costs, seed,
+                    // collision model
   DpLayout dp;
-  size_t dp_base, mask, pen, q_seed, total;
+  size_t dp_base, mask, pen, q_seed, geo, total;
 };
 inline PlanLayout plan_layout(int T, int Kp, int n) {
   PlanLayout L;
@@ -90,6 +96,7 @@ inline PlanLayout plan_layout(int T, int Kp, int n) {
   L.mask = o;    o += align256((size_t)T * Kp);
   L.pen = o;     o += align256((size_t)T * Kp * sizeof(float));
   L.q_seed = o;  o += align256((size_t)T * n * sizeof(float));
+  L.geo = o;     o += align256(geo_bytes());
   L.total = o;
   return L;
 }

@@ -109,6 +109,7 @@ struct Request {
   // results on the host (pinned or pageable)
   char* h_out = nullptr;
   std::vector<char> own_out;
+  std::vector<char> geo;  // device form of the collision model (empty: none)
   size_t pin_off = 0, pin_bytes = 0;
   bool pinned = false;
   // device slot: [cand][targets][outputs][plan scratch]
@@ -271,6 +272,7 @@ cpp_status cpp_server::enqueue(Launch* L) {
                                               align256(sizeof(cpp_robot_t) * count));
   int max_T = 0, max_Kp = 0;
   long long max_tasks = 0;
+  bool any_geo = false;
   for (int i = 0; i < count; ++i) {
     Request* r = L->reqs[i];
     char* b = d_arena + r->dev_off;
@@ -285,7 +287,15 @@ cpp_status cpp_server::enqueue(Launch* L) {
     q.T = r->T; q.K = r->K; q.Kp = r->Kp; q.n = r->n; q.robot = i; q.Kb = bp_stride(r->Kp);
     q.cand = reinterpret_cast<const float*>(b + r->o_cand);
     q.targets = reinterpret_cast<const double*>(b + r->o_tgt);
-    carve_plan(q, b + r->o_ws, plan_layout(r->T, r->Kp, r->n));
+    const PlanLayout PL = plan_layout(r->T, r->Kp, r->n);
+    carve_plan(q, b + r->o_ws, PL);
+    if (!r->geo.empty()) {  // pageable source: staged before the call returns
+      e = cudaMemcpyAsync(b + r->o_ws + PL.geo, r->geo.data(), r->geo.size(),
+                          cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server H2D: %s", cudaGetErrorString(e));
+      q.geo = reinterpret_cast<const GeoF*>(b + r->o_ws + PL.geo);
+      any_geo = true;
+    }
     char* out = b + r->o_out;
     q.sel = reinterpret_cast<int32_t*>(out + r->o_sel);
     q.q_out = reinterpret_cast<float*>(out + r->o_q);
@@ -304,7 +314,7 @@ cpp_status cpp_server::enqueue(Launch* L) {
   if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server H2D table: %s", cudaGetErrorString(e));
   BatchSrc src{reinterpret_cast<const Req*>(tab_d),
                reinterpret_cast<const cpp_robot_t*>(tab_d + align256(sizeof(Req) * count))};
-  if ((e = launch_mask_batch(src, n, count, max_tasks, cfg.params, st)) != cudaSuccess ||
+  if ((e = launch_mask_batch(src, n, count, max_tasks, cfg.params, any_geo, st)) != cudaSuccess ||
       (e = launch_dp_batch(src, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK,
                            cfg.params.dp_objective, n, count, max_T, max_Kp, st)) != cudaSuccess ||
       (e = launch_lm_batch(src, n, count, max_T, cfg.params, st)) != cudaSuccess ||
@@ -439,6 +449,7 @@ cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out)
   const cpp_params_t& P = cfg->params;
   if (P.lm_iters < 0 || P.smooth_rounds < 0 || P.smooth_rounds > 1000 ||
       !(std::isfinite(P.smooth_lambda) && P.smooth_lambda > 0) ||
+      !(std::isfinite(P.pen_collide) && P.pen_collide >= 0) ||
       (P.dp_objective != CPP_DP_SUM && P.dp_objective != CPP_DP_MINMAX))
     return sfail(CPP_ERR_INVALID_ARG, "invalid params (lm_iters, smooth_rounds, smooth_lambda, "
                                       "dp_objective)");
@@ -503,9 +514,16 @@ cpp_status cpp_plan_submit(cpp_server_t* s, const cpp_plan_req_t* rq, uint64_t* 
   if (L.total + table > s->cfg.hbm_budget_bytes)
     return sfail(CPP_ERR_BUDGET, "request needs %zu bytes of device memory; the budget is %zu",
                  L.total + table, s->cfg.hbm_budget_bytes);
+  std::vector<char> geo;
+  if (rq->geometry) {
+    geo.resize(geo_bytes());
+    char msg[160];
+    if (!make_geo(*rq->geometry, n, geo.data(), msg)) return sfail(CPP_ERR_INVALID_ARG, "%s", msg);
+  }
   Request* r = new (std::nothrow) Request;
   if (!r) return sfail(CPP_ERR_OOM, "host allocation failed");
   r->robot = rb;
+  r->geo = std::move(geo);
   r->T = T; r->K = K; r->Kp = Kp; r->n = n;
   r->dev_bytes = L.total;
   r->o_cand = L.cand; r->o_tgt = L.tgt; r->o_out = L.out; r->o_ws = L.ws;

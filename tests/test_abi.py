@@ -78,3 +78,39 @@ def test_smoothing_params_are_validated_on_the_host(lib):
     assert "227" in cppflow.last_error()
     assert L.cpp_smooth_step(ctypes.byref(r), ctypes.byref(p), fake, fake, 4000, None,
                              None) == cppflow.ERR_INVALID_ARG
+
+
+def test_collision_models_are_validated_on_the_host(lib):
+    """A capsule paired with itself, a frame above n, too many boxes or a negative
+    radius: INVALID_ARG before any device pointer is touched."""
+    import numpy as np
+    from paper_2309_09102_gb300 import cppflow, synth
+    L = cppflow.lib()
+    arm = synth.draw_arm(2, 7)
+    r = cppflow.robot_from_arm(arm)
+    p = cppflow.make_params()
+    assert p.pen_collide == 100.0
+    fake = ctypes.c_void_p(256)
+    good = cppflow.geometry_from(synth.with_boxes(synth.link_capsules(arm), 1, 2))
+
+    def call(g):
+        return L.cpp_mask_geo(ctypes.byref(r), ctypes.byref(p), ctypes.byref(g), fake, fake, 4, 8, 8,
+                              fake, fake, None, None, None, None)
+
+    for tweak in ("self_pair", "frame", "boxes", "radius"):
+        g = cppflow.geometry_from(synth.with_boxes(synth.link_capsules(arm), 1, 2))
+        if tweak == "self_pair":
+            g.pairs[0][1] = g.pairs[0][0]
+        elif tweak == "frame":
+            g.caps[0].frame = 8
+        elif tweak == "boxes":
+            g.n_boxes = 9
+        else:
+            g.caps[1].radius = -0.01
+        assert call(g) == cppflow.ERR_INVALID_ARG, tweak
+        assert "collision model" in cppflow.last_error()
+    bad_p = cppflow.make_params(pen_collide=float("inf"))
+    assert L.cpp_mask_geo(ctypes.byref(r), ctypes.byref(bad_p), ctypes.byref(good), fake, fake, 4, 8,
+                          8, fake, fake, None, None, None, None) == cppflow.ERR_INVALID_ARG
+    assert good.n_caps == 7 and good.n_pairs == 15 and good.n_boxes == 2
+    assert np.isclose(good.caps[0].radius, 0.03)
