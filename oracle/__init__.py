@@ -134,6 +134,11 @@ def lib():
             "orc_clearance": (None, [P, P, P, P, P]),
             "orc_mask_geo": (None, [P, P, P, C.c_double, P, P, C.c_int, C.c_int, C.c_int, P, P, P,
                                     P]),
+            "orc_collision_rows": (C.c_int, [P, P, P, C.c_double, C.c_double, P, P, C.c_int]),
+            "orc_diff_step_geo": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.c_double,
+                                            P, P]),
+            "orc_lm_smooth_geo": (None, [P, P, P, P, P, C.c_int, C.c_int, C.c_double, C.c_double,
+                                         C.c_double, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -346,6 +351,43 @@ def mask_geo(robot: Robot, params: Params, geo: Geometry, pen_collide: float, ca
     lib().orc_mask_geo(C.byref(robot), C.byref(params), C.byref(geo), float(pen_collide), _p(cand),
                        _p(targets), T, K, Kp, _p(mask), _p(pen), _p(err), _p(cl))
     return mask, pen, err, cl
+
+
+MAX_ROWS = MAX_PAIRS + MAX_CAPS * MAX_BOXES
+
+
+def collision_rows(robot: Robot, geo: Geometry, q, d_safe: float, w: float):
+    """Hinge residuals w (d_safe - d) of the pairs / capsule-box combinations closer
+    than d_safe and their gradient rows: (res [m], J [m][n])."""
+    q = _f64(q).reshape(robot.n)
+    res = np.zeros(MAX_ROWS)
+    J = np.zeros((MAX_ROWS, robot.n))
+    m = lib().orc_collision_rows(C.byref(robot), C.byref(geo), _p(q), float(d_safe), float(w),
+                                 _p(res), _p(J), MAX_ROWS)
+    return res[:m].copy(), J[:m].copy()
+
+
+def diff_step_geo(robot: Robot, geo: Geometry, q, lambda_d: float, d_safe: float, w: float):
+    """Trajectory-length step with collision rows: (q', ok, rows)."""
+    q = _f64(q).reshape(-1, robot.n)
+    out = np.zeros_like(q)
+    rows = np.zeros(1, np.int32)
+    ok = lib().orc_diff_step_geo(C.byref(robot), C.byref(geo), _p(q), q.shape[0], float(lambda_d),
+                                 float(d_safe), float(w), _p(out), _p(rows))
+    return out, bool(ok), int(rows[0])
+
+
+def lm_smooth_geo(robot: Robot, params: Params, geo: Geometry, q_in, targets, rounds: int,
+                  lambda_d: float, d_safe: float, w: float):
+    q_in = _f64(q_in).reshape(-1, robot.n)
+    T = q_in.shape[0]
+    targets = _f64(targets).reshape(T, 7)
+    out = np.zeros_like(q_in)
+    taken = np.zeros(1, np.int32)
+    lib().orc_lm_smooth_geo(C.byref(robot), C.byref(params), C.byref(geo), _p(q_in), _p(targets), T,
+                            int(rounds), float(lambda_d), float(d_safe), float(w), _p(out),
+                            _p(taken))
+    return out, int(taken[0])
 
 
 # ---------------------------------------------------------------- §III-C trajectory length

@@ -336,6 +336,93 @@ void orc_clearance(const orc_robot* r, const orc_geometry* g, const double* q,
     *env_min = em;
 }
 
+/* Collision rows of r_diff for one configuration (§III-C; reading: a hinge on a
+ * safety margin, since the distances themselves are to grow, not shrink): for
+ * every listed pair and every capsule-box combination with clearance d <
+ * d_safe, a residual w (d_safe - d) and its gradient row -w dd/dq. By the
+ * envelope theorem dd/dq is the derivative at the QP's minimiser: with x_u, x_v
+ * the closest points and n = (x_u - x_v) / |x_u - x_v|,
+ *   dd/dq_j = n . (dx_u/dq_j - dx_v/dq_j),   dx/dq_j = z_j x (x - o_j)
+ * for a point on a frame that joint j moves (frame > j), else 0; for a box the
+ * box point is fixed. Rows whose closest points coincide (no direction) are
+ * skipped. Returns the number of rows (at most max_rows); J is [rows][n]. */
+static void point_rate(const double z[][3], const double o[][3], int frame, int n,
+                       const double x[3], double out[][3]) {
+    for (int j = 0; j < n; ++j) {
+        if (frame > j) {
+            const double dx = x[0] - o[j][0], dy = x[1] - o[j][1], dz = x[2] - o[j][2];
+            out[j][0] = z[j][1] * dz - z[j][2] * dy;
+            out[j][1] = z[j][2] * dx - z[j][0] * dz;
+            out[j][2] = z[j][0] * dy - z[j][1] * dx;
+        } else {
+            out[j][0] = out[j][1] = out[j][2] = 0.0;
+        }
+    }
+}
+
+int orc_collision_rows(const orc_robot* r, const orc_geometry* g, const double* q,
+                       double d_safe, double w, double* res, double* J, int max_rows) {
+    const int n = r->n;
+    double z[ORC_MAXJ + 1][3], o[ORC_MAXJ + 1][3], Re[9], pe[3];
+    orc_fk_frames(r, q, z, o, Re, pe);
+    double A[ORC_MAX_CAPS][3], B[ORC_MAX_CAPS][3];
+    orc_capsules_world(r, g, q, A, B);
+    int m = 0;
+    for (int k = 0; k < g->n_pairs && m < max_rows; ++k) {
+        const int u = g->pairs[k][0], v = g->pairs[k][1];
+        double s, t;
+        const double d2 = orc_seg_seg_dist2(A[u], B[u], A[v], B[v], &s, &t);
+        const double dist = sqrt(d2);
+        const double d = dist - g->caps[u].radius - g->caps[v].radius;
+        if (!(d < d_safe) || dist == 0.0) continue;
+        double xu[3], xv[3], nv[3], ru[ORC_MAXJ][3], rv[ORC_MAXJ][3];
+        for (int c = 0; c < 3; ++c) {
+            xu[c] = A[u][c] + s * (B[u][c] - A[u][c]);
+            xv[c] = A[v][c] + t * (B[v][c] - A[v][c]);
+            nv[c] = (xu[c] - xv[c]) / dist;
+        }
+        point_rate(z, o, g->caps[u].frame, n, xu, ru);
+        point_rate(z, o, g->caps[v].frame, n, xv, rv);
+        res[m] = w * (d_safe - d);
+        for (int j = 0; j < n; ++j)
+            J[(size_t)m * n + j] = -w * (nv[0] * (ru[j][0] - rv[j][0]) + nv[1] * (ru[j][1] - rv[j][1]) +
+                                         nv[2] * (ru[j][2] - rv[j][2]));
+        ++m;
+    }
+    for (int ob = 0; ob < g->n_boxes; ++ob) {
+        const orc_cuboid* bx = &g->boxes[ob];
+        for (int c = 0; c < g->n_caps && m < max_rows; ++c) {
+            double a[3], b[3], t;
+            for (int k = 0; k < 3; ++k) {
+                a[k] = bx->R[k] * (A[c][0] - bx->p[0]) + bx->R[3 + k] * (A[c][1] - bx->p[1]) +
+                       bx->R[6 + k] * (A[c][2] - bx->p[2]);
+                b[k] = bx->R[k] * (B[c][0] - bx->p[0]) + bx->R[3 + k] * (B[c][1] - bx->p[1]) +
+                       bx->R[6 + k] * (B[c][2] - bx->p[2]);
+            }
+            const double d2 = orc_seg_box_dist2(a, b, bx->half, &t);
+            const double dist = sqrt(d2);
+            const double d = dist - g->caps[c].radius;
+            if (!(d < d_safe) || dist == 0.0) continue;
+            double xb[3], pb[3], nb[3], nw[3], x[3], rc[ORC_MAXJ][3];
+            for (int k = 0; k < 3; ++k) {
+                xb[k] = a[k] + t * (b[k] - a[k]);
+                pb[k] = xb[k] > bx->half[k] ? bx->half[k] : (xb[k] < -bx->half[k] ? -bx->half[k] : xb[k]);
+                nb[k] = (xb[k] - pb[k]) / dist;
+            }
+            for (int k = 0; k < 3; ++k) {   /* back to the world: R (box) */
+                nw[k] = bx->R[3 * k] * nb[0] + bx->R[3 * k + 1] * nb[1] + bx->R[3 * k + 2] * nb[2];
+                x[k] = A[c][k] + t * (B[c][k] - A[c][k]);
+            }
+            point_rate(z, o, g->caps[c].frame, n, x, rc);
+            res[m] = w * (d_safe - d);
+            for (int j = 0; j < n; ++j)
+                J[(size_t)m * n + j] = -w * (nw[0] * rc[j][0] + nw[1] * rc[j][1] + nw[2] * rc[j][2]);
+            ++m;
+        }
+    }
+    return m;
+}
+
 /* Per candidate (i, k):
  *   NONFINITE: some joint value is not finite -> node cost +inf, no other bit.
  *   OUT:  some q_j < lo_j or q_j > hi_j                (§II "Joint limits")
@@ -933,6 +1020,58 @@ int orc_diff_step(const orc_robot* r, const double* q_in, int T, double lambda_d
     return ok;
 }
 
+/* The trajectory-length step with the collision rows of r_diff (§III-C): one
+ * damped Gauss-Newton step on |r_diff|^2 / 2 with r_diff = [differences;
+ * collision rows of every waypoint]. The collision rows of waypoint i touch q_i
+ * only, so they add J_c,i^T J_c,i to diagonal block i and J_c,i^T r_c,i to the
+ * right-hand side; the system stays block tridiagonal (now with full diagonal
+ * blocks) and is solved by orc_block_tridiag_solve. Returns 0 if the solve
+ * failed (q' = q). rows_out (or 0) receives the number of collision rows. */
+int orc_diff_step_geo(const orc_robot* r, const orc_geometry* g, const double* q_in, int T,
+                      double lambda_d, double d_safe, double w, double* q_out, int32_t* rows_out) {
+    const int n = r->n;
+    const size_t nn = (size_t)n * n;
+    const int max_rows = ORC_MAX_PAIRS + ORC_MAX_CAPS * ORC_MAX_BOXES;
+    double* Dg = (double*)calloc(nn * (size_t)T, sizeof(double));
+    double* Off = (double*)calloc(nn * (size_t)(T > 1 ? T - 1 : 1), sizeof(double));
+    double* gr = (double*)calloc((size_t)n * T, sizeof(double));
+    double* d = (double*)calloc((size_t)n * T, sizeof(double));
+    double* res = (double*)malloc(sizeof(double) * max_rows);
+    double* J = (double*)malloc(sizeof(double) * (size_t)max_rows * n);
+    int32_t rows = 0;
+    for (int i = 0; i < T; ++i) {
+        const double c = (i > 0 ? 1.0 : 0.0) + (i + 1 < T ? 1.0 : 0.0);
+        for (int a = 0; a < n; ++a) Dg[nn * i + (size_t)a * n + a] = c + lambda_d;
+        if (i + 1 < T)
+            for (int a = 0; a < n; ++a) Off[nn * i + (size_t)a * n + a] = -1.0;
+        for (int a = 0; a < n; ++a) {
+            double t = 0.0;
+            if (i > 0) t += q_in[(size_t)i * n + a] - q_in[(size_t)(i - 1) * n + a];
+            if (i + 1 < T) t -= q_in[(size_t)(i + 1) * n + a] - q_in[(size_t)i * n + a];
+            gr[(size_t)i * n + a] = -t;
+        }
+        const int m = orc_collision_rows(r, g, q_in + (size_t)i * n, d_safe, w, res, J, max_rows);
+        rows += m;
+        for (int k = 0; k < m; ++k)
+            for (int a = 0; a < n; ++a) {
+                gr[(size_t)i * n + a] -= J[(size_t)k * n + a] * res[k];
+                for (int b = 0; b < n; ++b)
+                    Dg[nn * i + (size_t)a * n + b] += J[(size_t)k * n + a] * J[(size_t)k * n + b];
+            }
+    }
+    const int ok = orc_block_tridiag_solve(T, n, Dg, Off, gr, d);
+    for (int i = 0; i < T; ++i)
+        for (int a = 0; a < n; ++a) {
+            double v = q_in[(size_t)i * n + a] + (ok ? d[(size_t)i * n + a] : 0.0);
+            if (v < r->lo[a]) v = r->lo[a];
+            if (v > r->hi[a]) v = r->hi[a];
+            q_out[(size_t)i * n + a] = ok ? v : q_in[(size_t)i * n + a];
+        }
+    if (rows_out) *rows_out = rows;
+    free(Dg); free(Off); free(gr); free(d); free(res); free(J);
+    return ok;
+}
+
 /* §III-C non-stationary objective: pose-only LM phases (orc_lm) alternate with
  * single trajectory-length steps; a trajectory-length step is taken only when
  * the pose phase before it left every waypoint within tau_pos / tau_rot (FP64
@@ -964,6 +1103,33 @@ void orc_lm_smooth(const orc_robot* r, const orc_params* P, const double* q_in,
     orc_lm(r, P, q, targets, T, q_out, 0, 0);
     if (taken) *taken = cnt;
     free(q); free(w);
+}
+
+/* orc_lm_smooth with the collision rows in every trajectory-length step
+ * (orc_diff_step_geo); g = 0 gives orc_lm_smooth. */
+void orc_lm_smooth_geo(const orc_robot* r, const orc_params* P, const orc_geometry* g,
+                       const double* q_in, const double* targets, int T, int rounds,
+                       double lambda_d, double d_safe, double w, double* q_out, int32_t* taken) {
+    const int n = r->n;
+    double* q = (double*)malloc(sizeof(double) * (size_t)T * n);
+    double* v = (double*)malloc(sizeof(double) * (size_t)T * n);
+    memcpy(q, q_in, sizeof(double) * (size_t)T * n);
+    int32_t cnt = 0;
+    for (int k = 0; k < rounds; ++k) {
+        orc_lm(r, P, q, targets, T, v, 0, 0);
+        orc_report rep;
+        orc_check(r, P, v, targets, T, 0, &rep);
+        if (rep.n_pose_fail == 0) {
+            if (g) orc_diff_step_geo(r, g, v, T, lambda_d, d_safe, w, q, 0);
+            else orc_diff_step(r, v, T, lambda_d, q);
+            ++cnt;
+        } else {
+            memcpy(q, v, sizeof(double) * (size_t)T * n);
+        }
+    }
+    orc_lm(r, P, q, targets, T, q_out, 0, 0);
+    if (taken) *taken = cnt;
+    free(q); free(v);
 }
 
 /* Mask -> FP32 search -> seed -> LM -> check, for one request. */

@@ -107,6 +107,16 @@ void   orc_capsules_world(const orc_robot* r, const orc_geometry* g, const doubl
                           double A[][3], double B[][3]);
 void   orc_clearance(const orc_robot* r, const orc_geometry* g, const double* q,
                      double* self_min, double* env_min);
+int    orc_collision_rows(const orc_robot* r, const orc_geometry* g, const double* q,
+                          double d_safe, double w, double* res, double* J /*[rows][n]*/,
+                          int max_rows);
+int    orc_diff_step_geo(const orc_robot* r, const orc_geometry* g, const double* q_in, int T,
+                         double lambda_d, double d_safe, double w, double* q_out,
+                         int32_t* rows_out);
+void   orc_lm_smooth_geo(const orc_robot* r, const orc_params* P, const orc_geometry* g,
+                         const double* q_in, const double* targets, int T, int rounds,
+                         double lambda_d, double d_safe, double w, double* q_out,
+                         int32_t* taken);
 void   orc_mask_geo(const orc_robot* r, const orc_params* P, const orc_geometry* g,
                     double pen_collide, const float* cand, const double* targets, int T, int K,
                     int Kp, uint8_t* mask, float* pen, double* err, double* clearance);

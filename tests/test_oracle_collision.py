@@ -135,3 +135,94 @@ def test_self_collision_of_a_folded_arm():
     assert sm == pytest.approx(0.3 - 0.04, abs=1e-12)
     sm2, _ = oracle.clearance(rob, g, np.array([0.0, math.pi - 0.2, math.pi - 0.2]))
     assert sm2 < 0
+
+
+# ------------------------------------------------------------------ collision rows of r_diff
+@pytest.mark.parametrize("seed", range(6))
+def test_collision_rows_gradients_match_finite_differences(seed):
+    arm = synth.draw_arm(4 + seed, 7)
+    rob = problems.oracle_robot(arm)
+    g = oracle.make_geometry(synth.with_boxes(synth.link_capsules(arm), 3 + seed, 3))
+    q = np.random.default_rng(seed).uniform(-2, 2, 7)
+    res, J = oracle.collision_rows(rob, g, q, 10.0, 1.5)   # d_safe = 10 m: every row active
+    assert len(res) >= 30 and np.all(res > 0)
+    h = 1e-6
+    for j in range(7):
+        e = np.zeros(7)
+        e[j] = h
+        rp, _ = oracle.collision_rows(rob, g, q + e, 10.0, 1.5)
+        rm, _ = oracle.collision_rows(rob, g, q - e, 10.0, 1.5)
+        np.testing.assert_allclose((rp - rm) / (2 * h), J[:, j], atol=1e-6)
+
+
+def test_collision_rows_hinge():
+    """Only pairs closer than d_safe contribute, with residual w (d_safe - d)."""
+    arm = synth.draw_arm(9, 7)
+    rob = problems.oracle_robot(arm)
+    g = oracle.make_geometry(synth.link_capsules(arm, radius=0.02))
+    q = np.zeros(7)
+    sm, _ = oracle.clearance(rob, g, q)
+    res, _ = oracle.collision_rows(rob, g, q, sm + 0.01, 2.0)
+    assert len(res) >= 1 and res.max() == pytest.approx(2.0 * 0.01, rel=1e-9)
+    res0, _ = oracle.collision_rows(rob, g, q, sm - 1e-9, 2.0)
+    assert len(res0) == 0
+
+
+def dense_step_geo(rob, g, q, lam, d_safe, w):
+    """One damped Gauss-Newton step on [differences; collision rows] from the explicit
+    stacked Jacobian (NumPy dense solve)."""
+    T, n = q.shape
+    rows, cols = [], []
+    for i in range(T - 1):
+        Jd = np.zeros((n, T * n))
+        Jd[:, i * n:(i + 1) * n] = -np.eye(n)
+        Jd[:, (i + 1) * n:(i + 2) * n] = np.eye(n)
+        rows.append(Jd)
+        cols.append(q[i + 1] - q[i])
+    for i in range(T):
+        res, J = oracle.collision_rows(rob, g, q[i], d_safe, w)
+        if len(res):
+            Jc = np.zeros((len(res), T * n))
+            Jc[:, i * n:(i + 1) * n] = J
+            rows.append(Jc)
+            cols.append(res)
+    Jt = np.concatenate(rows)
+    r = np.concatenate(cols)
+    delta = -np.linalg.solve(Jt.T @ Jt + lam * np.eye(T * n), Jt.T @ r)
+    return q + delta.reshape(T, n)
+
+
+def test_diff_step_geo_matches_dense_and_reduces_to_diff_step():
+    arm = synth.Arm(a=np.full(7, 0.25), d=np.full(7, 0.1), alpha=np.array([0, 1.57, -1.57, 0, 1.57, -1.57, 0]),
+                    lo=np.full(7, -50.0), hi=np.full(7, 50.0))
+    rob = problems.oracle_robot(arm)
+    g = oracle.make_geometry(synth.with_boxes(synth.link_capsules(arm), 7, 4))
+    q = np.random.default_rng(3).uniform(-1.5, 1.5, (12, 7))
+    out, ok, rows = oracle.diff_step_geo(rob, g, q, 0.7, 0.5, 1.3)
+    assert ok and rows > 0
+    np.testing.assert_allclose(out, dense_step_geo(rob, g, q, 0.7, 0.5, 1.3), rtol=1e-9, atol=1e-11)
+    # w = 0: the collision rows vanish and the step is the plain trajectory-length step
+    out0, _, _ = oracle.diff_step_geo(rob, g, q, 0.7, 0.5, 0.0)
+    np.testing.assert_allclose(out0, oracle.diff_step(rob, q, 0.7)[0], rtol=1e-12, atol=1e-14)
+
+
+def test_diff_steps_push_a_trajectory_out_of_a_box():
+    """A trajectory whose middle waypoints graze a box: repeated steps with the
+    collision rows (strong weight) raise the smallest clearance along it."""
+    arm = synth.draw_arm(12, 7)
+    rob = problems.oracle_robot(arm)
+    q = synth.draw_truth(5, 7, 20)
+    A, B = oracle.capsules_world(rob, oracle.make_geometry(synth.link_capsules(arm)), q[10])
+    centre = 0.5 * (A[5] + B[5])
+    geo = synth.link_capsules(arm, radius=0.02)
+    geo = synth.Geometry(geo.cap_frame, geo.cap_a, geo.cap_b, geo.cap_r, geo.pairs[:0],
+                         np.eye(3)[None], centre[None], np.full((1, 3), 0.03))
+    g = oracle.make_geometry(geo)
+    cl = lambda x: min(oracle.clearance(rob, g, qi)[1] for qi in x)
+    before = cl(q)
+    assert before < 0
+    x = q.copy()
+    for _ in range(5):
+        x, ok, rows = oracle.diff_step_geo(rob, g, x, 1.0, 0.05, 20.0)
+        assert ok
+    assert cl(x) > before + 0.01
