@@ -140,6 +140,9 @@ typedef struct cpp_params {
     int32_t reserved_;
     double smooth_lambda;  /* damping of the trajectory-length step (default 1; > 0) */
     double pen_collide;    /* node cost of a colliding candidate (default 100, §III-B) */
+    double coll_margin;    /* collision rows of the trajectory-length step: active where the
+                              clearance is below this (m, default 0.02, >= 0) */
+    double coll_weight;    /* their weight w: residual w (coll_margin - clearance) (default 1) */
 } cpp_params_t;
 
 #define CPP_DP_SUM 0     /* minimise the summed per-step L-inf joint jump */
@@ -309,6 +312,23 @@ cpp_status cpp_lm_refine(const cpp_robot_t* robot, const cpp_params_t* params,
 cpp_status cpp_smooth_step(const cpp_robot_t* robot, const cpp_params_t* params, float* q,
                            const double* targets, int32_t T, int32_t* dev_status,
                            cpp_stream_t stream);
+
+/* The trajectory-length step with the collision rows of r_diff (§III-C): for
+ * every listed pair and capsule-box combination with clearance d below
+ * coll_margin, a residual coll_weight * (coll_margin - d) with its gradient
+ * (closest-point direction times the point Jacobians). Each row touches one
+ * waypoint, so the normal equations stay block tridiagonal with full n x n
+ * diagonal blocks; the block Thomas recursion runs in FP64 (rows and gradients
+ * in FP32). Gate, clamp and in-place update as cpp_smooth_step. geometry: host
+ * pointer (copied); NULL gives cpp_smooth_step. workspace: device scratch of
+ * cpp_smooth_workspace_size(T, n) bytes, 256-byte aligned. In cpp_plan_geo,
+ * batches and the server a request with a collision model takes these steps
+ * whenever smooth_rounds > 0. */
+size_t cpp_smooth_workspace_size(int32_t T, int32_t n);
+cpp_status cpp_smooth_step_geo(const cpp_robot_t* robot, const cpp_params_t* params,
+                               const cpp_geometry_t* geometry, float* q, const double* targets,
+                               int32_t T, void* workspace, size_t ws_bytes, int32_t* dev_status,
+                               cpp_stream_t stream);
 
 /* ------------------------------------------------------------------ check (§II)
  * FP64 FK of q [T][n] FP32 -> pose_err [T][2] FP64 (or NULL) and a report

@@ -344,8 +344,12 @@ void orc_clearance(const orc_robot* r, const orc_geometry* g, const double* q,
  * the closest points and n = (x_u - x_v) / |x_u - x_v|,
  *   dd/dq_j = n . (dx_u/dq_j - dx_v/dq_j),   dx/dq_j = z_j x (x - o_j)
  * for a point on a frame that joint j moves (frame > j), else 0; for a box the
- * box point is fixed. Rows whose closest points coincide (no direction) are
- * skipped. Returns the number of rows (at most max_rows); J is [rows][n]. */
+ * box point is fixed. Rows whose closest points are within ORC_MIN_DIR (1e-6 m)
+ * of each other are skipped: at zero distance (touching or interpenetrating
+ * shapes, where the QP's minimum is 0) the direction is undefined, and below
+ * 1e-6 m it is rounding noise. Returns the number of rows (at most max_rows);
+ * J is [rows][n]. */
+#define ORC_MIN_DIR 1e-6
 static void point_rate(const double z[][3], const double o[][3], int frame, int n,
                        const double x[3], double out[][3]) {
     for (int j = 0; j < n; ++j) {
@@ -374,7 +378,7 @@ int orc_collision_rows(const orc_robot* r, const orc_geometry* g, const double* 
         const double d2 = orc_seg_seg_dist2(A[u], B[u], A[v], B[v], &s, &t);
         const double dist = sqrt(d2);
         const double d = dist - g->caps[u].radius - g->caps[v].radius;
-        if (!(d < d_safe) || dist == 0.0) continue;
+        if (!(d < d_safe) || dist <= ORC_MIN_DIR) continue;
         double xu[3], xv[3], nv[3], ru[ORC_MAXJ][3], rv[ORC_MAXJ][3];
         for (int c = 0; c < 3; ++c) {
             xu[c] = A[u][c] + s * (B[u][c] - A[u][c]);
@@ -402,7 +406,7 @@ int orc_collision_rows(const orc_robot* r, const orc_geometry* g, const double* 
             const double d2 = orc_seg_box_dist2(a, b, bx->half, &t);
             const double dist = sqrt(d2);
             const double d = dist - g->caps[c].radius;
-            if (!(d < d_safe) || dist == 0.0) continue;
+            if (!(d < d_safe) || dist <= ORC_MIN_DIR) continue;
             double xb[3], pb[3], nb[3], nw[3], x[3], rc[ORC_MAXJ][3];
             for (int k = 0; k < 3; ++k) {
                 xb[k] = a[k] + t * (b[k] - a[k]);

@@ -42,7 +42,8 @@ class Params(C.Structure):
         "lambda_up", "lambda_down", "lambda_min", "lambda_max", "freeze_step", "freeze_cost")] + [
         ("lm_iters", C.c_int32), ("free_mask", C.c_uint32), ("lm_fp64", C.c_int32),
         ("dp_objective", C.c_int32), ("smooth_rounds", C.c_int32), ("reserved_", C.c_int32),
-        ("smooth_lambda", C.c_double), ("pen_collide", C.c_double)]
+        ("smooth_lambda", C.c_double), ("pen_collide", C.c_double), ("coll_margin", C.c_double),
+        ("coll_weight", C.c_double)]
 
 
 class Report(C.Structure):
@@ -162,6 +163,8 @@ _SIGS = {
                                 _P, _P, _P, _P, _P]),
     "cpp_lm_refine": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, _P, _P]),
     "cpp_smooth_step": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P]),
+    "cpp_smooth_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
+    "cpp_smooth_step_geo": (C.c_int, [_P, _P, _P, _P, _P, C.c_int32, _P, C.c_size_t, _P, _P]),
     "cpp_check": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, _P]),
     "cpp_plan_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "cpp_plan": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_size_t,
@@ -335,6 +338,21 @@ def smooth_step(robot: Robot, params: Params, q, targets, dev_status=None, strea
     T = q.shape[0]
     _check(lib().cpp_smooth_step(C.byref(robot), C.byref(params), ptr(q), ptr(targets), T,
                                  ptr(dev_status), stream_handle(stream)), "cpp_smooth_step")
+
+
+def smooth_workspace_size(T: int, n: int) -> int:
+    return lib().cpp_smooth_workspace_size(T, n)
+
+
+def smooth_step_geo(robot: Robot, params: Params, geometry: Geometry | None, q, targets, workspace,
+                    dev_status=None, stream=None):
+    """The trajectory-length step with collision rows, on q [T][n] FP32 in place."""
+    T = q.shape[0]
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    g = C.byref(geometry) if geometry is not None else None
+    _check(lib().cpp_smooth_step_geo(C.byref(robot), C.byref(params), g, ptr(q), ptr(targets), T,
+                                     ptr(workspace), nbytes, ptr(dev_status),
+                                     stream_handle(stream)), "cpp_smooth_step_geo")
 
 
 def check(robot: Robot, params: Params, q, targets, pose_err=None, report=None, stream=None):

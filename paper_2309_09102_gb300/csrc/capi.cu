@@ -70,6 +70,9 @@ cpp_status check_params(const cpp_params_t* p) {
     return fail(CPP_ERR_INVALID_ARG, "smooth_lambda must be finite and > 0");
   if (!(finite_d(p->pen_collide) && p->pen_collide >= 0))
     return fail(CPP_ERR_INVALID_ARG, "pen_collide must be finite and >= 0");
+  if (!(finite_d(p->coll_margin) && p->coll_margin >= 0 && finite_d(p->coll_weight) &&
+        p->coll_weight >= 0))
+    return fail(CPP_ERR_INVALID_ARG, "coll_margin and coll_weight must be finite and >= 0");
   return CPP_OK;
 }
 
@@ -206,6 +209,8 @@ void cpp_params_default(cpp_params_t* p) {
   p->reserved_ = 0;
   p->smooth_lambda = 1.0;
   p->pen_collide = 100.0;
+  p->coll_margin = 0.02;
+  p->coll_weight = 1.0;
 }
 
 cpp_status cpp_fk_batch(const cpp_robot_t* robot, const float* q, int64_t N, float* R, float* p,
@@ -364,6 +369,35 @@ cpp_status cpp_smooth_step(const cpp_robot_t* robot, const cpp_params_t* params,
   return cuda_status(launch_smooth(s, *params, (cudaStream_t)stream), "cpp_smooth_step");
 }
 
+size_t cpp_smooth_workspace_size(int32_t T, int32_t n) {
+  if (T < 1 || n < 1 || n > CPP_MAX_JOINTS) return 0;
+  return smooth_ws_bytes(T, n);
+}
+
+cpp_status cpp_smooth_step_geo(const cpp_robot_t* robot, const cpp_params_t* params,
+                               const cpp_geometry_t* geometry, float* q, const double* targets,
+                               int32_t T, void* workspace, size_t ws_bytes, int32_t* dev_status,
+                               cpp_stream_t stream) {
+  if (cpp_status s = check_robot(robot)) return s;
+  if (cpp_status s = check_params(params)) return s;
+  if (T < 1) return fail(CPP_ERR_INVALID_ARG, "T < 1");
+  if (!q || !targets) return fail(CPP_ERR_INVALID_ARG, "NULL buffer");
+  if (smooth_smem_bytes(T, robot->n) > kMaxSmemBytes)
+    return fail(CPP_ERR_INVALID_ARG, "(n + 1) * T * 8 exceeds 227 KB (T = %d)", T);
+  if (geometry && (!workspace || ws_bytes < smooth_ws_bytes(T, robot->n) || !aligned(workspace, 256)))
+    return fail(CPP_ERR_INVALID_ARG, "workspace needs %zu bytes, 256-byte aligned",
+                smooth_ws_bytes(T, robot->n));
+  SingleSrc s;
+  s.r = empty_req();
+  s.r.T = T; s.r.n = robot->n;
+  s.r.q_out = q; s.r.targets = targets;
+  s.r.smooth_ws = static_cast<double*>(workspace);
+  s.r.status = dev_status;
+  s.robot = *robot;
+  if (cpp_status e = set_geo(s, geometry, robot->n)) return e;
+  return cuda_status(launch_smooth(s, *params, (cudaStream_t)stream), "cpp_smooth_step_geo");
+}
+
 cpp_status cpp_check(const cpp_robot_t* robot, const cpp_params_t* params, const float* q,
                      const double* targets, int32_t T, double* pose_err, cpp_report_t* report,
                      cpp_stream_t stream) {
@@ -427,6 +461,7 @@ cpp_status cpp_plan_geo(const cpp_robot_t* robot, const cpp_params_t* params,
   s.r.sel = sel; s.r.best_cost = best_cost;
   s.r.q_seed = reinterpret_cast<float*>(ws + L.q_seed);
   s.r.q_in = s.r.q_seed; s.r.q_out = q_out; s.r.pose_err = pose_err; s.r.report = report;
+  s.r.smooth_ws = reinterpret_cast<double*>(ws + L.smooth);
   s.r.status = dev_status;
   s.robot = *robot;
   if (cpp_status e = set_geo(s, geometry, n)) return e;
@@ -633,8 +668,8 @@ cpp_status run_stages(cpp_batch* b, uint32_t stages, cudaStream_t st) {
                                    "batch/backtrack"))
       return e;
   if (stages & CPP_STAGE_LM)
-    if (cpp_status e = cuda_status(launch_lm_batch(b->src, b->n, b->count, b->max_T, b->params, st),
-                                   "batch/lm"))
+    if (cpp_status e = cuda_status(launch_lm_batch_geo(b->src, b->n, b->count, b->max_T, b->params,
+                                                       b->any_geo, st), "batch/lm"))
       return e;
   if (stages & CPP_STAGE_CHECK)
     return cuda_status(launch_check_batch(b->src, b->count, b->params, st), "batch/check");
@@ -732,6 +767,7 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
     q.sel = d.sel; q.best_cost = d.best_cost;
     q.q_seed = reinterpret_cast<float*>(b + L.q_seed);
     q.q_in = q.q_seed; q.q_out = d.q_out; q.pose_err = d.pose_err; q.report = d.report;
+    q.smooth_ws = reinterpret_cast<double*>(b + L.smooth);
     q.status = dev_status ? dev_status + r : nullptr;
     if (d.geometry) {
       geos.emplace_back(geo_bytes());
@@ -793,7 +829,7 @@ int32_t cpp_batch_launches(const cpp_batch_t* b, uint32_t stages) {
   int c = 0;
   for (unsigned s = 1; s <= CPP_STAGE_CHECK; s <<= 1) {
     if (!(stages & s)) continue;
-    if (s == CPP_STAGE_LM) { c += lm_launches(b->params); continue; }
+    if (s == CPP_STAGE_LM) { c += lm_launches(b->params, b->any_geo); continue; }
     if (s != CPP_STAGE_DP_FORWARD) { ++c; continue; }
     for (const SchedGroup& g : b->groups) c += g.count > 0 ? 1 : 0;
   }

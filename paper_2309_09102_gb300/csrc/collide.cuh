@@ -19,9 +19,10 @@ __device__ __forceinline__ float d2_pts(const float* x, const float* y) {
 // Squared distance of segments a1 + s (b1 - a1), a2 + t (b2 - a2), s, t in [0, 1]:
 // the convex QP solved by its active sets -- the interior stationary point when
 // it lies in the unit square, and the four edges, each minimised by clamping its
-// 1-D stationary point; the smallest directly evaluated |P - Q|^2 wins.
-__device__ __forceinline__ float seg_seg_d2(const float* a1, const float* b1, const float* a2,
-                                            const float* b2) {
+// 1-D stationary point; the smallest directly evaluated |P - Q|^2 wins (s, t:
+// its parameters).
+__device__ __forceinline__ float seg_seg_d2_st(const float* a1, const float* b1, const float* a2,
+                                               const float* b2, float& so, float& to) {
   float d1[3], d2[3], r[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) { d1[k] = b1[k] - a1[k]; d2[k] = b2[k] - a2[k]; r[k] = a1[k] - a2[k]; }
@@ -40,14 +41,22 @@ __device__ __forceinline__ float seg_seg_d2(const float* a1, const float* b1, co
   cs[3] = A > 0.f ? clamp01f(-D / A) : 0.f; ct[3] = 0.f;
   cs[4] = A > 0.f ? clamp01f((B - D) / A) : 0.f; ct[4] = 1.f;
   float best = CUDART_INF_F;
+  so = to = 0.f;
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     float P[3], Q[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) { P[k] = a1[k] + cs[c] * d1[k]; Q[k] = a2[k] + ct[c] * d2[k]; }
-    best = fminf(best, d2_pts(P, Q));
+    const float f = d2_pts(P, Q);
+    if (f < best) { best = f; so = cs[c]; to = ct[c]; }
   }
   return best;
+}
+
+__device__ __forceinline__ float seg_seg_d2(const float* a1, const float* b1, const float* a2,
+                                            const float* b2) {
+  float s, t;
+  return seg_seg_d2_st(a1, b1, a2, b2, s, t);
 }
 
 __device__ __forceinline__ float box_g(const float* a, const float* d, const float* h, float t) {
@@ -66,8 +75,9 @@ __device__ __forceinline__ float box_g(const float* a, const float* d, const flo
 // cost is convex and piecewise quadratic in t with breakpoints where a
 // coordinate crosses a face plane; each piece's quadratic (faces fixed by its
 // midpoint) is minimised by clamping its stationary point to the piece, and the
-// piece's ends are evaluated too.
-__device__ __forceinline__ float seg_box_d2(const float* a, const float* b, const float* h) {
+// piece's ends are evaluated too (to: the minimiser).
+__device__ __forceinline__ float seg_box_d2_t(const float* a, const float* b, const float* h,
+                                              float& to) {
   float d[3], br[8];
 #pragma unroll
   for (int k = 0; k < 3; ++k) d[k] = b[k] - a[k];
@@ -86,6 +96,7 @@ __device__ __forceinline__ float seg_box_d2(const float* a, const float* b, cons
       const float x = br[j]; br[j] = br[j - 1]; br[j - 1] = x;
     }
   float best = box_g(a, d, h, 0.f);
+  to = 0.f;
   for (int i = 0; i + 1 < nb; ++i) {
     const float ta = br[i], tz = br[i + 1], tm = 0.5f * (ta + tz);
     float num = 0.f, den = 0.f;
@@ -95,10 +106,20 @@ __device__ __forceinline__ float seg_box_d2(const float* a, const float* b, cons
       if (x > h[k]) { num += d[k] * (h[k] - a[k]); den += d[k] * d[k]; }
       else if (x < -h[k]) { num += d[k] * (-h[k] - a[k]); den += d[k] * d[k]; }
     }
-    best = fminf(best, box_g(a, d, h, tz));
-    if (den > 0.f) best = fminf(best, box_g(a, d, h, fminf(fmaxf(num / den, ta), tz)));
+    const float gz = box_g(a, d, h, tz);
+    if (gz < best) { best = gz; to = tz; }
+    if (den > 0.f) {
+      const float ts = fminf(fmaxf(num / den, ta), tz);
+      const float gs = box_g(a, d, h, ts);
+      if (gs < best) { best = gs; to = ts; }
+    }
   }
   return best;
+}
+
+__device__ __forceinline__ float seg_box_d2(const float* a, const float* b, const float* h) {
+  float t;
+  return seg_box_d2_t(a, b, h, t);
 }
 
 // World end points of the capsules of frame f, given that frame's pose.

@@ -57,6 +57,7 @@ struct Req {
   int32_t* status;           // [1] or null
   const GeoF* geo;           // collision model or null
   float* clear;              // [T][Kp] smallest clearance or null
+  double* smooth_ws;         // scratch of the trajectory-length step with collision rows, or null
 };
 
 // Kernels read requests and robots through one of two sources: a single request

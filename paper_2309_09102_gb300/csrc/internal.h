@@ -53,8 +53,12 @@ cudaError_t launch_lm(const SingleSrc& s, const cpp_params_t& P, bool want_err, 
 cudaError_t launch_lm_batch(const BatchSrc& s, int n, int nreq, int max_T, const cpp_params_t& P,
                             cudaStream_t st);
 cudaError_t launch_smooth(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st);
+// the refinement (pose phases and trajectory-length steps) of a batch; any_geo:
+// some request has a collision model (its steps then carry the collision rows)
+cudaError_t launch_lm_batch_geo(const BatchSrc& s, int n, int nreq, int max_T,
+                                const cpp_params_t& P, bool any_geo, cudaStream_t st);
 size_t smooth_smem_bytes(int T, int n);  // shared memory of the trajectory-length step
-int lm_launches(const cpp_params_t& P);  // kernel launches of one refinement
+int lm_launches(const cpp_params_t& P, bool any_geo);  // kernel launches of one refinement
 cudaError_t launch_check(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st);
 cudaError_t launch_check_batch(const BatchSrc& s, int nreq, const cpp_params_t& P,
                                cudaStream_t st);
@@ -83,10 +87,17 @@ inline DpLayout dp_layout(int T, int Kp) {
   return L;
 }
 
+// Scratch of the trajectory-length step with collision rows: per waypoint the
+// packed J^T J block and J^T r of its rows, the inverse Schur complement and the
+// eliminated right-hand side (FP64).
+inline size_t smooth_ws_bytes(int T, int n) {
+  return (size_t)T * (n * (n + 1) / 2 + n + n * n + n) * sizeof(double);
+}
+
 struct PlanLayout {  // scratch of one whole plan: the search's, masks, node costs, seed,
-                    // collision model
+                    // collision model, trajectory-length step
   DpLayout dp;
-  size_t dp_base, mask, pen, q_seed, geo, total;
+  size_t dp_base, mask, pen, q_seed, geo, smooth, total;
 };
 inline PlanLayout plan_layout(int T, int Kp, int n) {
   PlanLayout L;
@@ -97,6 +108,7 @@ inline PlanLayout plan_layout(int T, int Kp, int n) {
   L.pen = o;     o += align256((size_t)T * Kp * sizeof(float));
   L.q_seed = o;  o += align256((size_t)T * n * sizeof(float));
   L.geo = o;     o += align256(geo_bytes());
+  L.smooth = o;  o += align256(smooth_ws_bytes(T, n));
   L.total = o;
   return L;
 }
@@ -110,6 +122,7 @@ inline void carve_plan(Req& q, char* base, const PlanLayout& L) {
   q.costT = reinterpret_cast<float*>(base + L.dp_base + L.dp.costT);
   q.q_seed = reinterpret_cast<float*>(base + L.q_seed);
   q.q_in = q.q_seed;
+  q.smooth_ws = reinterpret_cast<double*>(base + L.smooth);
 }
 
 }  // namespace cppflow

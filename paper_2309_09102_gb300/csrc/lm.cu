@@ -18,6 +18,7 @@
 // over a warp leaves most lanes of every FP64 instruction idle; a thread per
 // waypoint fills all 32.
 // The joint state is held in FP64; q_out is its FP32 rounding.
+#include "collide.cuh"
 #include "internal.h"
 
 namespace cppflow {
@@ -343,12 +344,14 @@ __global__ void __launch_bounds__(kChkThreads) check_kernel(const __grid_constan
 // 1 / s_i and y_i are kept in shared memory ((n + 1) T doubles).
 struct SmoothArgs {
   double tau_pos, tau_rot, lambda_d;
+  double coll_margin, coll_weight;  // collision rows: w (margin - d) where d < margin
 };
 
 template <class Src>
 __global__ void __launch_bounds__(32) smooth_kernel(const __grid_constant__ Src src,
                                                      const SmoothArgs a) {
   const Req& rq = src.req(blockIdx.x);
+  if (src.geom(rq) && rq.smooth_ws) return;  // smooth_geo_kernel's request
   extern __shared__ double sm_s[];
   __shared__ RobotD rd;
   stage_robot(src.rob(rq.robot), 0.0, nullptr, &rd);
@@ -397,6 +400,233 @@ __global__ void __launch_bounds__(32) smooth_kernel(const __grid_constant__ Src 
 
 size_t smooth_smem_bytes(int T, int n) { return (size_t)T * (n + 1) * sizeof(double); }
 
+// The trajectory-length step with the collision rows of r_diff (§III-C), for a
+// request with a collision model. Rows: for every listed pair and every
+// capsule-box combination with clearance d < margin, the hinge w (margin - d),
+// whose gradient follows the envelope theorem, -w n . (dx_u/dq - dx_v/dq) with n
+// the unit vector between the closest points and dx/dq_j = z_j x (x - o_j) for
+// a point on a frame that joint j moves (the box point fixed); rows whose closest
+// points are within 1e-6 m (touching or interpenetrating: no direction) are
+// skipped. Each row touches one waypoint, so it adds g g^T to that waypoint's
+// diagonal block and g r to its right-hand side: the normal equations stay block tridiagonal, now with
+// full n x n diagonal blocks D_i = (c_i + lambda_d) I + G_i and -I beside them.
+// One warp per request:
+//   phase 1, lanes over waypoints: the FP64 gate (every waypoint within tau),
+//     FP32 FK with frames and capsules, the rows, G_i and J^T r in FP64 to scratch;
+//   phase 2, the block Thomas recursion over T in FP64:
+//     S_0 = D_0, S_i = D_i - S_{i-1}^{-1};  y_0 = b_0, y_i = b_i + S_{i-1}^{-1} y_{i-1}
+//     (lane 0 factors S_i by Cholesky, lanes c < n form column c of S_i^{-1}),
+//     then x_{T-1} = S^{-1} y, x_i = S_i^{-1} (y_i + x_{i+1}) (lane c: component c),
+//     q' = clamp(q + x) in FP32.
+constexpr float kMinDir = 1e-6f;  // m: closest points nearer than this give no direction
+
+template <class Src>
+__global__ void __launch_bounds__(32) smooth_geo_kernel(const __grid_constant__ Src src,
+                                                         const SmoothArgs a) {
+  const Req& rq = src.req(blockIdx.x);
+  const GeoF* gsrc = src.geom(rq);
+  if (!gsrc || !rq.smooth_ws) return;
+  __shared__ RobotF rf;
+  __shared__ RobotD rd;
+  __shared__ GeoF g;
+  __shared__ double S[kMaxJ * kMaxJ], Lc[kMaxJ * kMaxJ], Wp[kMaxJ * kMaxJ];
+  __shared__ double yb[2][kMaxJ], xs[kMaxJ];
+  __shared__ int chol_fail;
+  stage_robot(src.rob(rq.robot), 0.0, &rf, &rd);
+  {
+    const uint32_t* from = reinterpret_cast<const uint32_t*>(gsrc);
+    uint32_t* to = reinterpret_cast<uint32_t*>(&g);
+    for (int w = threadIdx.x; w < (int)(sizeof(GeoF) / 4); w += 32) to[w] = from[w];
+  }
+  __syncthreads();
+  const int n = rd.n, T = rq.T, lane = threadIdx.x, NP = n * (n + 1) / 2;
+  double* Gh = rq.smooth_ws;                       // [T][NP + n]
+  double* Wg = Gh + (size_t)T * (NP + n);          // [T][n * n]
+  double* Yg = Wg + (size_t)T * n * n;             // [T][n]
+  const float margin = (float)a.coll_margin, wt = (float)a.coll_weight;
+
+  bool ok = true;
+  for (int i = lane; i < T; i += 32) {
+    double qd[kMaxJ], R[9], p[3], Rt[9];
+    float qf[kMaxJ];
+    for (int j = 0; j < n; ++j) { qf[j] = rq.q_out[(size_t)i * n + j]; qd[j] = (double)qf[j]; }
+    fk_f64(rd, qd, R, p);
+    const double* t7 = rq.targets + 7 * (size_t)i;
+    quat_to_rot(t7 + 3, Rt);
+    const double dx = p[0] - t7[0], dy = p[1] - t7[1], dz = p[2] - t7[2];
+    ok = ok && sqrt(dx * dx + dy * dy + dz * dz) <= a.tau_pos && geodesic<double>(Rt, R) <= a.tau_rot;
+    // FP32 frames and capsules
+    float Rf[9], pf[3], z[kMaxJ][3], o[kMaxJ][3], cA[kMaxCaps][3], cB[kMaxCaps][3];
+    pose_identity(Rf, pf);
+    place_caps(g, 0, Rf, pf, cA, cB);
+    for (int j = 0; j < n; ++j) {
+      z[j][0] = Rf[2]; z[j][1] = Rf[5]; z[j][2] = Rf[8];
+      o[j][0] = pf[0]; o[j][1] = pf[1]; o[j][2] = pf[2];
+      float sj, cj;
+      sincosf(qf[j] + rf.th0[j], &sj, &cj);
+      dh_step(Rf, pf, cj, sj, rf.ca[j], rf.sa[j], rf.a[j], rf.d[j]);
+      place_caps(g, j + 1, Rf, pf, cA, cB);
+    }
+    double G[kMaxJ * (kMaxJ + 1) / 2], h[kMaxJ];
+    for (int k = 0; k < NP; ++k) G[k] = 0.0;
+    for (int k = 0; k < n; ++k) h[k] = 0.0;
+    // one row: residual res, unit direction nv, points xu (frame fu) minus xv (frame fv, or -1)
+    auto add_row = [&](float res, const float nv[3], const float xu[3], int fu, const float xv[3],
+                       int fv) {
+      float row[kMaxJ];
+      for (int j = 0; j < n; ++j) {
+        float v = 0.f;
+        if (fu > j) {
+          const float rx = xu[0] - o[j][0], ry = xu[1] - o[j][1], rz = xu[2] - o[j][2];
+          v += nv[0] * (z[j][1] * rz - z[j][2] * ry) + nv[1] * (z[j][2] * rx - z[j][0] * rz) +
+               nv[2] * (z[j][0] * ry - z[j][1] * rx);
+        }
+        if (fv > j) {
+          const float rx = xv[0] - o[j][0], ry = xv[1] - o[j][1], rz = xv[2] - o[j][2];
+          v -= nv[0] * (z[j][1] * rz - z[j][2] * ry) + nv[1] * (z[j][2] * rx - z[j][0] * rz) +
+               nv[2] * (z[j][0] * ry - z[j][1] * rx);
+        }
+        row[j] = -wt * v;
+      }
+      int k = 0;
+      for (int r = 0; r < n; ++r) {
+        h[r] += (double)row[r] * (double)res;
+        for (int c = 0; c <= r; ++c) G[k++] += (double)row[r] * (double)row[c];
+      }
+    };
+    for (int k = 0; k < g.n_pairs; ++k) {
+      const int u = g.pu[k], v = g.pv[k];
+      float su, tv;
+      const float dist = sqrtf(seg_seg_d2_st(cA[u], cB[u], cA[v], cB[v], su, tv));
+      const float d = dist - g.r[u] - g.r[v];
+      if (!(d < margin) || dist <= kMinDir) continue;
+      float xu[3], xv[3], nv[3];
+      for (int c = 0; c < 3; ++c) {
+        xu[c] = cA[u][c] + su * (cB[u][c] - cA[u][c]);
+        xv[c] = cA[v][c] + tv * (cB[v][c] - cA[v][c]);
+        nv[c] = (xu[c] - xv[c]) / dist;
+      }
+      // frame of a capsule: the f with frame_begin[f] <= c < frame_begin[f + 1]
+      int fu = 0, fv = 0;
+      while (g.frame_begin[fu + 1] <= u) ++fu;
+      while (g.frame_begin[fv + 1] <= v) ++fv;
+      add_row(wt * (margin - d), nv, xu, fu, xv, fv);
+    }
+    for (int ob = 0; ob < g.n_boxes; ++ob) {
+      for (int c = 0; c < g.n_caps; ++c) {
+        float ab[3], bb[3];
+        for (int q = 0; q < 3; ++q) {
+          ab[q] = g.Rt[ob][3 * q] * (cA[c][0] - g.p[ob][0]) + g.Rt[ob][3 * q + 1] * (cA[c][1] - g.p[ob][1]) +
+                  g.Rt[ob][3 * q + 2] * (cA[c][2] - g.p[ob][2]);
+          bb[q] = g.Rt[ob][3 * q] * (cB[c][0] - g.p[ob][0]) + g.Rt[ob][3 * q + 1] * (cB[c][1] - g.p[ob][1]) +
+                  g.Rt[ob][3 * q + 2] * (cB[c][2] - g.p[ob][2]);
+        }
+        float t;
+        const float dist = sqrtf(seg_box_d2_t(ab, bb, g.h[ob], t));
+        const float d = dist - g.r[c];
+        if (!(d < margin) || dist <= kMinDir) continue;
+        float nb[3], nv[3], x[3];
+        for (int q = 0; q < 3; ++q) {
+          const float xb = ab[q] + t * (bb[q] - ab[q]);
+          const float pb = fminf(fmaxf(xb, -g.h[ob][q]), g.h[ob][q]);
+          nb[q] = (xb - pb) / dist;
+        }
+        for (int q = 0; q < 3; ++q) {  // back to the world: (R^T)^T n
+          nv[q] = g.Rt[ob][q] * nb[0] + g.Rt[ob][3 + q] * nb[1] + g.Rt[ob][6 + q] * nb[2];
+          x[q] = cA[c][q] + t * (cB[c][q] - cA[c][q]);
+        }
+        int fc = 0;
+        while (g.frame_begin[fc + 1] <= c) ++fc;
+        add_row(wt * (margin - d), nv, x, fc, x, -1);
+      }
+    }
+    double* dst = Gh + (size_t)i * (NP + n);
+    for (int k = 0; k < NP; ++k) dst[k] = G[k];
+    for (int k = 0; k < n; ++k) dst[NP + k] = h[k];
+  }
+  if (!__all_sync(0xffffffffu, ok) || T < 2) return;
+  if (lane == 0) chol_fail = 0;
+  __syncwarp();
+
+  const float* qc = rq.q_out;
+  for (int i = 0; i < T; ++i) {
+    const double* Gi = Gh + (size_t)i * (NP + n);
+    const double* yprev = yb[(i + 1) & 1];
+    double* ycur = yb[i & 1];
+    if (lane < n) {
+      const int c = lane;
+      const double diag = (i > 0 ? 1.0 : 0.0) + (i + 1 < T ? 1.0 : 0.0) + a.lambda_d;
+      for (int r = 0; r < n; ++r) {
+        const int hi = r > c ? r : c, lo = r > c ? c : r;
+        double v = Gi[hi * (hi + 1) / 2 + lo] + (r == c ? diag : 0.0);
+        if (i > 0) v -= Wp[r * n + c];
+        S[r * n + c] = v;
+      }
+      const double qi = (double)qc[(size_t)i * n + c];
+      double b = -Gi[NP + c];
+      if (i + 1 < T) b += (double)qc[(size_t)(i + 1) * n + c] - qi;
+      if (i > 0) b -= qi - (double)qc[(size_t)(i - 1) * n + c];
+      if (i > 0)
+        for (int k = 0; k < n; ++k) b += Wp[c * n + k] * yprev[k];
+      ycur[c] = b;
+    }
+    __syncwarp();
+    if (lane == 0) {  // Cholesky S = L L^T
+      for (int j = 0; j < n; ++j) {
+        double v = S[j * n + j];
+        for (int k = 0; k < j; ++k) v -= Lc[j * n + k] * Lc[j * n + k];
+        if (!(v > 0.0)) { chol_fail = 1; break; }
+        const double l = sqrt(v);
+        Lc[j * n + j] = l;
+        for (int r = j + 1; r < n; ++r) {
+          double t = S[r * n + j];
+          for (int k = 0; k < j; ++k) t -= Lc[r * n + k] * Lc[j * n + k];
+          Lc[r * n + j] = t / l;
+        }
+      }
+    }
+    __syncwarp();
+    if (chol_fail) return;  // warp-uniform: leave q unchanged
+    if (lane < n) {         // column c of S^{-1}: L L^T w = e_c
+      const int c = lane;
+      double v[kMaxJ];
+      for (int k = 0; k < n; ++k) {
+        double t = k == c ? 1.0 : 0.0;
+        for (int m = 0; m < k; ++m) t -= Lc[k * n + m] * v[m];
+        v[k] = t / Lc[k * n + k];
+      }
+      for (int k = n - 1; k >= 0; --k) {
+        double t = v[k];
+        for (int m = k + 1; m < n; ++m) t -= Lc[m * n + k] * v[m];
+        v[k] = t / Lc[k * n + k];
+      }
+      for (int k = 0; k < n; ++k) {
+        Wp[k * n + c] = v[k];
+        Wg[(size_t)i * n * n + k * n + c] = v[k];
+      }
+      Yg[(size_t)i * n + c] = ycur[c];
+    }
+    __syncwarp();
+  }
+  for (int i = T - 1; i >= 0; --i) {
+    double v = 0.0;
+    if (lane < n) {
+      const int c = lane;
+      const double* Wi = Wg + (size_t)i * n * n;
+      for (int k = 0; k < n; ++k)
+        v += Wi[c * n + k] * (Yg[(size_t)i * n + k] + (i + 1 < T ? xs[k] : 0.0));
+    }
+    __syncwarp();
+    if (lane < n) {
+      const int c = lane;
+      xs[c] = v;
+      const double qn = fmin(fmax((double)qc[(size_t)i * n + c] + v, rd.lo[c]), rd.hi[c]);
+      rq.q_out[(size_t)i * n + c] = (float)qn;
+    }
+    __syncwarp();
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 static LmArgs make_lm_args(const cpp_params_t& P, bool want_err, bool from_out) {
   LmArgs a;
@@ -431,8 +661,13 @@ static cudaError_t launch_lm_phase(const Src& s, int n, int nreq, int max_T, con
 
 template <class Src>
 static cudaError_t launch_smooth_t(const Src& s, int n, int nreq, int max_T, const cpp_params_t& P,
-                                   cudaStream_t st) {
-  const SmoothArgs a{P.tau_pos, P.tau_rot, P.smooth_lambda};
+                                   bool any_geo, cudaStream_t st) {
+  const SmoothArgs a{P.tau_pos, P.tau_rot, P.smooth_lambda, P.coll_margin, P.coll_weight};
+  if (any_geo) {
+    smooth_geo_kernel<Src><<<nreq, 32, 0, st>>>(s, a);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const size_t smem = smooth_smem_bytes(max_T, n);
   if (smem > 48u * 1024u) {
     const cudaError_t e = cudaFuncSetAttribute(smooth_kernel<Src>,
@@ -448,28 +683,32 @@ static cudaError_t launch_smooth_t(const Src& s, int n, int nreq, int max_T, con
 // within tau) followed by another pose phase.
 template <class Src>
 static cudaError_t launch_lm_t(const Src& s, int n, int nreq, int max_T, const cpp_params_t& P,
-                               bool want_err, cudaStream_t st) {
+                               bool want_err, bool any_geo, cudaStream_t st) {
   const int rounds = P.smooth_rounds > 0 ? P.smooth_rounds : 0;
   cudaError_t e = launch_lm_phase(s, n, nreq, max_T, P, want_err && rounds == 0, false, st);
   for (int k = 0; k < rounds && e == cudaSuccess; ++k) {
-    if ((e = launch_smooth_t(s, n, nreq, max_T, P, st)) != cudaSuccess) break;
+    if ((e = launch_smooth_t(s, n, nreq, max_T, P, any_geo, st)) != cudaSuccess) break;
     e = launch_lm_phase(s, n, nreq, max_T, P, want_err && k + 1 == rounds, true, st);
   }
   return e;
 }
 
 cudaError_t launch_lm(const SingleSrc& s, const cpp_params_t& P, bool want_err, cudaStream_t st) {
-  return launch_lm_t(s, s.r.n, 1, s.r.T, P, want_err, st);
+  return launch_lm_t(s, s.r.n, 1, s.r.T, P, want_err, s.has_geo && s.r.smooth_ws, st);
 }
 cudaError_t launch_lm_batch(const BatchSrc& s, int n, int nreq, int max_T, const cpp_params_t& P,
                             cudaStream_t st) {
-  return launch_lm_t(s, n, nreq, max_T, P, false, st);
+  return launch_lm_t(s, n, nreq, max_T, P, false, false, st);
+}
+cudaError_t launch_lm_batch_geo(const BatchSrc& s, int n, int nreq, int max_T,
+                                const cpp_params_t& P, bool any_geo, cudaStream_t st) {
+  return launch_lm_t(s, n, nreq, max_T, P, false, any_geo, st);
 }
 cudaError_t launch_smooth(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st) {
-  return launch_smooth_t(s, s.r.n, 1, s.r.T, P, st);
+  return launch_smooth_t(s, s.r.n, 1, s.r.T, P, s.has_geo && s.r.smooth_ws, st);
 }
-int lm_launches(const cpp_params_t& P) {
-  return 1 + 2 * (P.smooth_rounds > 0 ? P.smooth_rounds : 0);
+int lm_launches(const cpp_params_t& P, bool any_geo) {
+  return 1 + (any_geo ? 3 : 2) * (P.smooth_rounds > 0 ? P.smooth_rounds : 0);
 }
 
 template <class Src>

@@ -317,7 +317,7 @@ cpp_status cpp_server::enqueue(Launch* L) {
   if ((e = launch_mask_batch(src, n, count, max_tasks, cfg.params, any_geo, st)) != cudaSuccess ||
       (e = launch_dp_batch(src, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK,
                            cfg.params.dp_objective, n, count, max_T, max_Kp, st)) != cudaSuccess ||
-      (e = launch_lm_batch(src, n, count, max_T, cfg.params, st)) != cudaSuccess ||
+      (e = launch_lm_batch_geo(src, n, count, max_T, cfg.params, any_geo, st)) != cudaSuccess ||
       (e = launch_check_batch(src, count, cfg.params, st)) != cudaSuccess)
     return sfail(CPP_ERR_CUDA, "server launch: %s", cudaGetErrorString(e));
   for (int i = 0; i < count; ++i) {
@@ -450,6 +450,8 @@ cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out)
   if (P.lm_iters < 0 || P.smooth_rounds < 0 || P.smooth_rounds > 1000 ||
       !(std::isfinite(P.smooth_lambda) && P.smooth_lambda > 0) ||
       !(std::isfinite(P.pen_collide) && P.pen_collide >= 0) ||
+      !(std::isfinite(P.coll_margin) && P.coll_margin >= 0) ||
+      !(std::isfinite(P.coll_weight) && P.coll_weight >= 0) ||
       (P.dp_objective != CPP_DP_SUM && P.dp_objective != CPP_DP_MINMAX))
     return sfail(CPP_ERR_INVALID_ARG, "invalid params (lm_iters, smooth_rounds, smooth_lambda, "
                                       "dp_objective)");

@@ -28,7 +28,8 @@ TAU_POS, TAU_ROT = 1e-3, math.radians(0.1)
 def params_pair(**kw):
     """The same settings as an oracle.Params and a cppflow.Params."""
     op = oracle.make_params(**{k: v for k, v in kw.items()
-                               if k not in ("lm_fp64", "dp_objective", "smooth_rounds", "smooth_lambda")})
+                               if k not in ("lm_fp64", "dp_objective", "smooth_rounds", "smooth_lambda",
+                                            "pen_collide", "coll_margin", "coll_weight")})
     cp = cppflow.make_params(**kw)
     return op, cp
 

@@ -165,3 +165,115 @@ def test_models_per_request_in_batches_and_the_server():
             assert status == cppflow.OK
             np.testing.assert_array_equal(res["sel"], alone[r]["sel"])
             np.testing.assert_array_equal(res["q"], alone[r]["q"])
+
+
+# ------------------------------------------------------------------ collision rows of r_diff
+def near_threshold(orob, g, q, margin, w, eps=1e-4):
+    """True if some row's clearance lies within eps of the margin, or some shape pair
+    is within eps of touching (the FP32 and FP64 active sets could differ)."""
+    for qi in q:
+        a, _ = oracle.collision_rows(orob, g, qi, margin - eps, w)
+        b, _ = oracle.collision_rows(orob, g, qi, margin + eps, w)
+        if len(a) != len(b):
+            return True
+        sm, em = oracle.clearance(orob, g, qi)
+        radii = [g.caps[c].radius for c in range(g.n_caps)]
+        if min(sm, em) < -min(radii) + eps:   # closest points (nearly) coincide somewhere
+            return True
+    return False
+
+
+def test_smooth_step_geo_matches_oracle():
+    """Targets are the FK of the trajectory (the gate is open); a box sits next to the
+    trajectory's middle so rows are active at several waypoints."""
+    tt = torch()
+    n, T = 7, 40
+    done = 0
+    for seed in range(30):
+        arm = synth.draw_arm(30 + seed, n)
+        orob = problems.oracle_robot(arm)
+        q32 = synth.draw_truth(200 + seed, n, T).astype(np.float32)
+        A, B = oracle.capsules_world(orob, oracle.make_geometry(synth.link_capsules(arm)),
+                                     q32[T // 2].astype(np.float64))
+        geo = synth.link_capsules(arm, radius=0.02)
+        axis = B[4] - A[4]
+        perp = np.cross(axis, [0.0, 0.0, 1.0])
+        if np.linalg.norm(perp) < 1e-3 * np.linalg.norm(axis):
+            perp = np.cross(axis, [1.0, 0.0, 0.0])
+        centre = 0.5 * (A[4] + B[4]) + 0.07 * perp / np.linalg.norm(perp)   # beside the link
+        geo = synth.Geometry(geo.cap_frame, geo.cap_a, geo.cap_b, geo.cap_r, geo.pairs,
+                             np.eye(3)[None], centre[None], np.full((1, 3), 0.03))
+        g = oracle.make_geometry(geo)
+        margin, w, lam = 0.05, 3.0, 1.0
+        if near_threshold(orob, g, q32.astype(np.float64), margin, w):
+            continue
+        ref, ok, rows = oracle.diff_step_geo(orob, g, q32.astype(np.float64), lam, margin, w)
+        if rows == 0:
+            continue
+        _, cp = params_pair(smooth_lambda=lam, coll_margin=margin, coll_weight=w)
+        qd = dev(q32)
+        ws = tt.empty(cppflow.smooth_workspace_size(T, n), dtype=tt.uint8, device="cuda:0")
+        st = tt.zeros(1, dtype=tt.int32, device="cuda:0")
+        cppflow.smooth_step_geo(cppflow.robot_from_arm(arm), cp, cppflow.geometry_from(geo), qd,
+                                dev(oracle.fk_pose(orob, q32.astype(np.float64))), ws, st)
+        tt.cuda.synchronize()
+        assert int(st.item()) == 0
+        np.testing.assert_allclose(qd.cpu().numpy(), ref, rtol=0, atol=2e-6)
+        # without the rows it is the plain step
+        ref0, _ = oracle.diff_step(orob, q32.astype(np.float64), lam)
+        assert np.abs(ref - ref0).max() > 1e-4
+        done += 1
+        if done == 3:
+            break
+    assert done >= 2
+
+
+def test_alternation_with_collision_rows():
+    """Pose phases alternating with collision-aware steps: valid plans whose smallest
+    clearance along the path is at least that of the plain alternation; batched equals
+    alone."""
+    tt = torch()
+    pb = problems.build(synth.PLAIN)
+    geo = model(pb, boxes=3, radius=0.03, seed=11)
+    g = oracle.make_geometry(geo)
+    _, cp_plain = params_pair(lm_iters=10, smooth_rounds=3, smooth_lambda=1.0)
+    _, cp = params_pair(lm_iters=10, smooth_rounds=3, smooth_lambda=1.0, coll_margin=0.05,
+                        coll_weight=5.0)
+    out = plan_geo(pb, cp, geo)
+    base = plan_geo(pb, cp_plain, geo)   # same search, steps without collision rows
+    np.testing.assert_array_equal(out["sel"], base["sel"])
+    rep = cppflow.report_from_bytes(out["rep"].tobytes())
+    assert rep["valid"] == 1
+    cl = lambda q: min(min(oracle.clearance(pb.robot, g, qi)) for qi in q.astype(np.float64))
+    assert cl(out["q"]) >= cl(base["q"]) - 1e-6
+    # one request with the model and one without, batched
+    pb2 = problems.build(synth.Workload("cg_b", 7, 40, 64, 0.03, 0.2, 0.05, 10, arm_seed=77,
+                                       path_seed=78, cand_seed=79))
+    alone2 = plan_geo(pb2, cp, None)
+    robots = [cppflow.robot_from_arm(pb.arm), cppflow.robot_from_arm(pb2.arm)]
+    gs = cppflow.geometry_from(geo)
+    bufs, descs = [], []
+    for r, p_ in enumerate((pb, pb2)):
+        T, n, Kp = p_.cand.shape
+        b = dict(cand=dev(p_.cand), targets=dev(p_.targets),
+                 sel=tt.empty(T, dtype=tt.int32, device="cuda:0"),
+                 q=tt.empty(T, n, dtype=tt.float32, device="cuda:0"),
+                 err=tt.empty(T, 2, dtype=tt.float64, device="cuda:0"),
+                 rep=tt.zeros(cppflow.REPORT_BYTES, dtype=tt.uint8, device="cuda:0"),
+                 best=tt.empty(1, dtype=tt.float32, device="cuda:0"))
+        bufs.append(b)
+        d = cppflow.PlanDesc(T, p_.K, Kp, r, b["cand"].data_ptr(), b["targets"].data_ptr(),
+                             b["sel"].data_ptr(), b["q"].data_ptr(), b["err"].data_ptr(),
+                             b["rep"].data_ptr(), b["best"].data_ptr())
+        if r == 0:
+            d.geometry = cppflow.C.addressof(gs)
+        descs.append(d)
+    ws = tt.empty(cppflow.plan_batch_workspace_size(descs, robots), dtype=tt.uint8, device="cuda:0")
+    st = tt.zeros(2, dtype=tt.int32, device="cuda:0")
+    batch = cppflow.Batch(robots, cp, descs, ws, st)
+    assert batch.launches(cppflow.STAGE_LM) == 1 + 3 * 3
+    batch.run(cppflow.STAGE_ALL)
+    tt.cuda.synchronize()
+    assert np.all(st.cpu().numpy() == 0)
+    np.testing.assert_array_equal(bufs[0]["q"].cpu().numpy(), out["q"])
+    np.testing.assert_array_equal(bufs[1]["q"].cpu().numpy(), alone2["q"])
