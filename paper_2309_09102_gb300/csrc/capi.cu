@@ -137,6 +137,10 @@ bool make_geo(const cpp_geometry_t& g, int n, void* out, char* err) {
     }
     if (!(finite_d(c.radius) && c.radius >= 0)) return bad("capsule radius must be finite and >= 0");
     f.r[k] = (float)c.radius;
+    // bounding sphere about the midpoint, widened by 1e-5 m so FP32 rounding of the
+    // separation test can only keep extra pairs, never drop a touching one
+    const double dx = c.b[0] - c.a[0], dy = c.b[1] - c.a[1], dz = c.b[2] - c.a[2];
+    f.bound[k] = (float)(0.5 * std::sqrt(dx * dx + dy * dy + dz * dz) + c.radius + 1e-5);
   }
   for (int k = 0; k < g.n_pairs; ++k) {
     const int u = g.pairs[k][0], v = g.pairs[k][1];
@@ -157,6 +161,8 @@ bool make_geo(const cpp_geometry_t& g, int n, void* out, char* err) {
     }
     for (int r = 0; r < 3; ++r)
       for (int c = 0; c < 3; ++c) f.Rt[o][3 * r + c] = (float)b.R[3 * c + r];  // transpose
+    f.box_bound[o] = (float)(std::sqrt(b.half[0] * b.half[0] + b.half[1] * b.half[1] +
+                                       b.half[2] * b.half[2]) + 1e-5);
   }
   memcpy(out, &f, sizeof(f));
   return true;

@@ -70,49 +70,60 @@ __device__ __forceinline__ float box_g(const float* a, const float* d, const flo
   return g;
 }
 
+__device__ __forceinline__ void cswap(float& x, float& y) {
+  const float lo = fminf(x, y), hi = fmaxf(x, y);
+  x = lo;
+  y = hi;
+}
+
 // Squared distance of the segment a + t (b - a), t in [0, 1], to the box [-h, h]
 // (box frame): for fixed t the nearest box point is the clamped point, so the
 // cost is convex and piecewise quadratic in t with breakpoints where a
 // coordinate crosses a face plane; each piece's quadratic (faces fixed by its
 // midpoint) is minimised by clamping its stationary point to the piece, and the
-// piece's ends are evaluated too (to: the minimiser).
+// piece's ends are evaluated too (to: the minimiser). The eight breakpoints
+// (0, 1 and the six crossings, those outside (0, 1) moved to 1) are sorted by a
+// fixed network in registers; empty pieces cost nothing but an evaluation.
 __device__ __forceinline__ float seg_box_d2_t(const float* a, const float* b, const float* h,
                                               float& to) {
   float d[3], br[8];
 #pragma unroll
   for (int k = 0; k < 3; ++k) d[k] = b[k] - a[k];
-  int nb = 0;
-  br[nb++] = 0.f;
-  br[nb++] = 1.f;
+  br[0] = 0.f;
+  br[1] = 1.f;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    if (d[k] == 0.f) continue;
-    const float t0 = (-h[k] - a[k]) / d[k], t1 = (h[k] - a[k]) / d[k];
-    if (t0 > 0.f && t0 < 1.f) br[nb++] = t0;
-    if (t1 > 0.f && t1 < 1.f) br[nb++] = t1;
+    const float t0 = d[k] != 0.f ? (-h[k] - a[k]) / d[k] : 1.f;
+    const float t1 = d[k] != 0.f ? (h[k] - a[k]) / d[k] : 1.f;
+    br[2 + 2 * k] = (t0 > 0.f && t0 < 1.f) ? t0 : 1.f;
+    br[3 + 2 * k] = (t1 > 0.f && t1 < 1.f) ? t1 : 1.f;
   }
-  for (int i = 1; i < nb; ++i)
-    for (int j = i; j > 0 && br[j] < br[j - 1]; --j) {
-      const float x = br[j]; br[j] = br[j - 1]; br[j - 1] = x;
-    }
+  // Batcher's odd-even merge sort for 8 keys (19 compare-exchanges)
+  cswap(br[0], br[1]); cswap(br[2], br[3]); cswap(br[4], br[5]); cswap(br[6], br[7]);
+  cswap(br[0], br[2]); cswap(br[1], br[3]); cswap(br[4], br[6]); cswap(br[5], br[7]);
+  cswap(br[1], br[2]); cswap(br[5], br[6]);
+  cswap(br[0], br[4]); cswap(br[1], br[5]); cswap(br[2], br[6]); cswap(br[3], br[7]);
+  cswap(br[2], br[4]); cswap(br[3], br[5]);
+  cswap(br[1], br[2]); cswap(br[3], br[4]); cswap(br[5], br[6]);
   float best = box_g(a, d, h, 0.f);
   to = 0.f;
-  for (int i = 0; i + 1 < nb; ++i) {
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
     const float ta = br[i], tz = br[i + 1], tm = 0.5f * (ta + tz);
     float num = 0.f, den = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const float x = a[k] + tm * d[k];
-      if (x > h[k]) { num += d[k] * (h[k] - a[k]); den += d[k] * d[k]; }
-      else if (x < -h[k]) { num += d[k] * (-h[k] - a[k]); den += d[k] * d[k]; }
+      const float c = x > h[k] ? h[k] : (x < -h[k] ? -h[k] : x);
+      const float on = x != c ? 1.f : 0.f;   // the face of coordinate k is active
+      num += on * d[k] * (c - a[k]);
+      den += on * d[k] * d[k];
     }
     const float gz = box_g(a, d, h, tz);
     if (gz < best) { best = gz; to = tz; }
-    if (den > 0.f) {
-      const float ts = fminf(fmaxf(num / den, ta), tz);
-      const float gs = box_g(a, d, h, ts);
-      if (gs < best) { best = gs; to = ts; }
-    }
+    const float ts = den > 0.f ? fminf(fmaxf(num / den, ta), tz) : tz;
+    const float gs = box_g(a, d, h, ts);
+    if (gs < best) { best = gs; to = ts; }
   }
   return best;
 }
@@ -132,6 +143,67 @@ __device__ __forceinline__ void place_caps(const GeoF& g, int f, const float R[9
       cB[c][k] = R[3 * k] * g.b[c][0] + R[3 * k + 1] * g.b[c][1] + R[3 * k + 2] * g.b[c][2] + p[k];
     }
   }
+}
+
+// Bounding spheres of capsule c (about its segment midpoint m) and of box o
+// overlap, widened by `extra`; otherwise their clearance is at least `extra`.
+__device__ __forceinline__ bool spheres_meet(const float* mu, float Ru, const float* mv, float Rv,
+                                             float extra) {
+  const float s = Ru + Rv + extra;
+  return d2_pts(mu, mv) < s * s;
+}
+
+// Whether the smallest clearance is negative (the mask's COLLIDE decision): the
+// exact QP runs only for pairs whose bounding spheres overlap, and the search
+// stops at the first negative clearance. Same decision as clearance() < 0 (a
+// pair whose spheres do not overlap has a positive clearance).
+// Axis-aligned boxes of a capsule's segment grown by `grow` (its radius plus any
+// margin): disjoint boxes mean a clearance of at least the margin.
+__device__ __forceinline__ bool aabb_meet(const float* a1, const float* b1, float g1,
+                                          const float* a2, const float* b2, float g2) {
+  bool meet = true;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float lo1 = fminf(a1[q], b1[q]) - g1, hi1 = fmaxf(a1[q], b1[q]) + g1;
+    const float lo2 = fminf(a2[q], b2[q]) - g2, hi2 = fmaxf(a2[q], b2[q]) + g2;
+    meet = meet && lo1 <= hi2 && lo2 <= hi1;
+  }
+  return meet;
+}
+
+// A capsule segment (box frame) grown by `grow` against the box [-h, h].
+__device__ __forceinline__ bool aabb_box_meet(const float* a, const float* b, float grow,
+                                              const float* h) {
+  bool meet = true;
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    meet = meet && fminf(a[q], b[q]) - grow <= h[q] && fmaxf(a[q], b[q]) + grow >= -h[q];
+  return meet;
+}
+
+__device__ __forceinline__ void to_box(const GeoF& g, int o, const float* x, float* y) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    y[q] = g.Rt[o][3 * q] * (x[0] - g.p[o][0]) + g.Rt[o][3 * q + 1] * (x[1] - g.p[o][1]) +
+           g.Rt[o][3 * q + 2] * (x[2] - g.p[o][2]);
+}
+
+__device__ __forceinline__ bool collides(const GeoF& g, const float (*cA)[3], const float (*cB)[3]) {
+  for (int k = 0; k < g.n_pairs; ++k) {
+    const int u = g.pu[k], v = g.pv[k];
+    if (!aabb_meet(cA[u], cB[u], g.r[u] + 1e-5f, cA[v], cB[v], g.r[v] + 1e-5f)) continue;
+    if (sqrtf(seg_seg_d2(cA[u], cB[u], cA[v], cB[v])) - g.r[u] - g.r[v] < 0.f) return true;
+  }
+  for (int o = 0; o < g.n_boxes; ++o) {
+    for (int c = 0; c < g.n_caps; ++c) {
+      float a[3], b[3];
+      to_box(g, o, cA[c], a);
+      to_box(g, o, cB[c], b);
+      if (!aabb_box_meet(a, b, g.r[c] + 1e-5f, g.h[o])) continue;
+      if (sqrtf(seg_box_d2(a, b, g.h[o])) - g.r[c] < 0.f) return true;
+    }
+  }
+  return false;
 }
 
 // Smallest clearance over the listed pairs (segment distance - r_u - r_v) and over

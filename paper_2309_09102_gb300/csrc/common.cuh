@@ -29,8 +29,10 @@ struct GeoF {
   int n_caps, n_pairs, n_boxes, pad_;
   int frame_begin[kMaxJ + 2];
   float a[kMaxCaps][3], b[kMaxCaps][3], r[kMaxCaps];
+  float bound[kMaxCaps];    // bounding-sphere radius about the segment midpoint (>= |b-a|/2 + r)
   int8_t pu[kMaxPairs], pv[kMaxPairs];
   float Rt[kMaxBoxes][9], p[kMaxBoxes][3], h[kMaxBoxes][3];
+  float box_bound[kMaxBoxes];  // bounding-sphere radius of the box about its centre (>= |h|)
 };
 
 struct Req {

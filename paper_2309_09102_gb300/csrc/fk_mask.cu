@@ -68,8 +68,8 @@ __device__ __forceinline__ void fk_caps(const RobotF& rb, const GeoF& g, const f
 template <int NJ, bool COLL>
 __device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, const float* q,
                                          int n, bool pad, const float Rt[9], const float pt[3],
-                                         const GeoF* g, uint8_t& bits, float& cost, float& epos,
-                                         float& erot, float& clr) {
+                                         const GeoF* g, bool want_clear, uint8_t& bits,
+                                         float& cost, float& epos, float& erot, float& clr) {
   if (pad) {
     bits = CPP_MASK_PAD; cost = CUDART_INF_F; epos = erot = clr = CUDART_NAN_F;
     return;
@@ -93,8 +93,12 @@ __device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, co
   if (COLL && g) {
     float cA[kMaxCaps][3], cB[kMaxCaps][3];
     fk_caps<NJ>(rb, *g, q, R, p, cA, cB);
-    clr = clearance(*g, cA, cB);
-    if (clr < 0.f) b |= CPP_MASK_COLLIDE;
+    if (want_clear) {  // the exact smallest clearance is requested
+      clr = clearance(*g, cA, cB);
+      if (clr < 0.f) b |= CPP_MASK_COLLIDE;
+    } else if (collides(*g, cA, cB)) {
+      b |= CPP_MASK_COLLIDE;
+    }
   } else {
     fk_f32<NJ>(rb, q, R, p);
   }
@@ -151,7 +155,10 @@ __global__ void __launch_bounds__(kMaskThreads) mask_kernel(const __grid_constan
     }
     uint8_t bits[4];
     float cost[4], ep[4], er[4], cl[4];
-#pragma unroll
+    // the collision code is large: one copy of it (no unrolling) keeps it in the
+    // instruction cache
+    constexpr int kUnroll = COLL ? 1 : 4;
+#pragma unroll kUnroll
     for (int c = 0; c < 4; ++c) {
       float q[NJ ? NJ : kMaxJ];
 #pragma unroll
@@ -159,8 +166,8 @@ __global__ void __launch_bounds__(kMaskThreads) mask_kernel(const __grid_constan
         if (!NJ && j >= n) break;
         q[j] = c == 0 ? qv[j].x : c == 1 ? qv[j].y : c == 2 ? qv[j].z : qv[j].w;
       }
-      mask_one<NJ, COLL>(rb, a, q, n, k0 + c >= rq.K, Rt, pt, g, bits[c], cost[c], ep[c], er[c],
-                         cl[c]);
+      mask_one<NJ, COLL>(rb, a, q, n, k0 + c >= rq.K, Rt, pt, g, rq.clear != nullptr, bits[c],
+                         cost[c], ep[c], er[c], cl[c]);
     }
     const size_t o = (size_t)i * rq.Kp + k0;
     *reinterpret_cast<uchar4*>(rq.mask + o) = make_uchar4(bits[0], bits[1], bits[2], bits[3]);

@@ -347,6 +347,39 @@ struct SmoothArgs {
   double coll_margin, coll_weight;  // collision rows: w (margin - d) where d < margin
 };
 
+// The trajectory-length step of one request with scalar-identity blocks: lane j
+// (< n) runs the Thomas recursion of joint j over T in FP64 (inv_s: [T] 1 / s_i,
+// the same in every lane; y: [T][n]) and stores clamp(q + delta) in FP32.
+__device__ __forceinline__ void scalar_thomas(const Req& rq, const RobotD& rd, double lambda_d,
+                                              double* inv_s, double* y, int lane) {
+  const int n = rd.n, T = rq.T;
+  if (lane >= n) return;
+  const int j = lane;
+  float* qc = rq.q_out + j;   // column j, stride n
+  double qp = 0.0, qi = (double)qc[0], ip = 0.0, yp = 0.0;
+  for (int i = 0; i < T; ++i) {
+    const double qn = i + 1 < T ? (double)qc[(size_t)(i + 1) * n] : 0.0;
+    const double c = (i > 0 ? 1.0 : 0.0) + (i + 1 < T ? 1.0 : 0.0);
+    const double b = (i + 1 < T ? qn - qi : 0.0) - (i > 0 ? qi - qp : 0.0);
+    const double s = c + lambda_d - (i > 0 ? ip : 0.0);
+    const double yi = b + (i > 0 ? yp * ip : 0.0);
+    ip = 1.0 / s;
+    yp = yi;
+    if (j == 0) inv_s[i] = ip;  // the same in every lane
+    y[(size_t)i * n + j] = yi;
+    qp = qi;
+    qi = qn;
+  }
+  __syncwarp((1u << n) - 1u);
+  double d = 0.0;
+  const double lo = rd.lo[j], hi = rd.hi[j];
+  for (int i = T - 1; i >= 0; --i) {
+    d = (y[(size_t)i * n + j] + (i + 1 < T ? d : 0.0)) * inv_s[i];
+    const double v = fmin(fmax((double)qc[(size_t)i * n] + d, lo), hi);
+    qc[(size_t)i * n] = (float)v;
+  }
+}
+
 template <class Src>
 __global__ void __launch_bounds__(32) smooth_kernel(const __grid_constant__ Src src,
                                                      const SmoothArgs a) {
@@ -369,33 +402,8 @@ __global__ void __launch_bounds__(32) smooth_kernel(const __grid_constant__ Src 
     const double rot = geodesic<double>(Rt, R);
     ok = ok && pos <= a.tau_pos && rot <= a.tau_rot;
   }
-  if (!__all_sync(0xffffffffu, ok) || T < 2 || lane >= n) return;
-  double* inv_s = sm_s;       // [T]
-  double* y = sm_s + T;       // [T][n]
-  const int j = lane;
-  float* qc = rq.q_out + j;   // column j, stride n
-  double qp = 0.0, qi = (double)qc[0], ip = 0.0, yp = 0.0;
-  for (int i = 0; i < T; ++i) {
-    const double qn = i + 1 < T ? (double)qc[(size_t)(i + 1) * n] : 0.0;
-    const double c = (i > 0 ? 1.0 : 0.0) + (i + 1 < T ? 1.0 : 0.0);
-    const double b = (i + 1 < T ? qn - qi : 0.0) - (i > 0 ? qi - qp : 0.0);
-    const double s = c + a.lambda_d - (i > 0 ? ip : 0.0);
-    const double yi = b + (i > 0 ? yp * ip : 0.0);
-    ip = 1.0 / s;
-    yp = yi;
-    if (j == 0) inv_s[i] = ip;  // the same in every lane
-    y[(size_t)i * n + j] = yi;
-    qp = qi;
-    qi = qn;
-  }
-  __syncwarp((1u << n) - 1u);
-  double d = 0.0;
-  const double lo = rd.lo[j], hi = rd.hi[j];
-  for (int i = T - 1; i >= 0; --i) {
-    d = (y[(size_t)i * n + j] + (i + 1 < T ? d : 0.0)) * inv_s[i];
-    const double v = fmin(fmax((double)qc[(size_t)i * n] + d, lo), hi);
-    qc[(size_t)i * n] = (float)v;
-  }
+  if (!__all_sync(0xffffffffu, ok) || T < 2) return;
+  scalar_thomas(rq, rd, a.lambda_d, sm_s, sm_s + T, lane);
 }
 
 size_t smooth_smem_bytes(int T, int n) { return (size_t)T * (n + 1) * sizeof(double); }
@@ -429,7 +437,7 @@ __global__ void __launch_bounds__(32) smooth_geo_kernel(const __grid_constant__ 
   __shared__ RobotF rf;
   __shared__ RobotD rd;
   __shared__ GeoF g;
-  __shared__ double S[kMaxJ * kMaxJ], Lc[kMaxJ * kMaxJ], Wp[kMaxJ * kMaxJ];
+  __shared__ double S[kMaxJ * kMaxJ], Lc[kMaxJ * kMaxJ], Wp[kMaxJ * kMaxJ], il[kMaxJ];
   __shared__ double yb[2][kMaxJ], xs[kMaxJ];
   __shared__ int chol_fail;
   stage_robot(src.rob(rq.robot), 0.0, &rf, &rd);
@@ -445,7 +453,7 @@ __global__ void __launch_bounds__(32) smooth_geo_kernel(const __grid_constant__ 
   double* Yg = Wg + (size_t)T * n * n;             // [T][n]
   const float margin = (float)a.coll_margin, wt = (float)a.coll_weight;
 
-  bool ok = true;
+  bool ok = true, any_rows = false;
   for (int i = lane; i < T; i += 32) {
     double qd[kMaxJ], R[9], p[3], Rt[9];
     float qf[kMaxJ];
@@ -496,6 +504,7 @@ __global__ void __launch_bounds__(32) smooth_geo_kernel(const __grid_constant__ 
     };
     for (int k = 0; k < g.n_pairs; ++k) {
       const int u = g.pu[k], v = g.pv[k];
+      if (!aabb_meet(cA[u], cB[u], g.r[u] + margin, cA[v], cB[v], g.r[v] + 1e-5f)) continue;
       float su, tv;
       const float dist = sqrtf(seg_seg_d2_st(cA[u], cB[u], cA[v], cB[v], su, tv));
       const float d = dist - g.r[u] - g.r[v];
@@ -511,16 +520,14 @@ __global__ void __launch_bounds__(32) smooth_geo_kernel(const __grid_constant__ 
       while (g.frame_begin[fu + 1] <= u) ++fu;
       while (g.frame_begin[fv + 1] <= v) ++fv;
       add_row(wt * (margin - d), nv, xu, fu, xv, fv);
+      any_rows = true;
     }
     for (int ob = 0; ob < g.n_boxes; ++ob) {
       for (int c = 0; c < g.n_caps; ++c) {
         float ab[3], bb[3];
-        for (int q = 0; q < 3; ++q) {
-          ab[q] = g.Rt[ob][3 * q] * (cA[c][0] - g.p[ob][0]) + g.Rt[ob][3 * q + 1] * (cA[c][1] - g.p[ob][1]) +
-                  g.Rt[ob][3 * q + 2] * (cA[c][2] - g.p[ob][2]);
-          bb[q] = g.Rt[ob][3 * q] * (cB[c][0] - g.p[ob][0]) + g.Rt[ob][3 * q + 1] * (cB[c][1] - g.p[ob][1]) +
-                  g.Rt[ob][3 * q + 2] * (cB[c][2] - g.p[ob][2]);
-        }
+        to_box(g, ob, cA[c], ab);
+        to_box(g, ob, cB[c], bb);
+        if (!aabb_box_meet(ab, bb, g.r[c] + margin + 1e-5f, g.h[ob])) continue;
         float t;
         const float dist = sqrtf(seg_box_d2_t(ab, bb, g.h[ob], t));
         const float d = dist - g.r[c];
@@ -538,6 +545,7 @@ __global__ void __launch_bounds__(32) smooth_geo_kernel(const __grid_constant__ 
         int fc = 0;
         while (g.frame_begin[fc + 1] <= c) ++fc;
         add_row(wt * (margin - d), nv, x, fc, x, -1);
+        any_rows = true;
       }
     }
     double* dst = Gh + (size_t)i * (NP + n);
@@ -545,6 +553,11 @@ __global__ void __launch_bounds__(32) smooth_geo_kernel(const __grid_constant__ 
     for (int k = 0; k < n; ++k) dst[NP + k] = h[k];
   }
   if (!__all_sync(0xffffffffu, ok) || T < 2) return;
+  if (!__any_sync(0xffffffffu, any_rows)) {  // no active row: the scalar-identity step
+    __syncwarp();
+    scalar_thomas(rq, rd, a.lambda_d, Wg, Wg + T, lane);
+    return;
+  }
   if (lane == 0) chol_fail = 0;
   __syncwarp();
 
@@ -571,34 +584,38 @@ __global__ void __launch_bounds__(32) smooth_geo_kernel(const __grid_constant__ 
       ycur[c] = b;
     }
     __syncwarp();
-    if (lane == 0) {  // Cholesky S = L L^T
-      for (int j = 0; j < n; ++j) {
+    // Cholesky S = L L^T by columns: lane 0 the pivot and its reciprocal, lanes
+    // r > j the rest of column j (one division per pivot)
+    for (int j = 0; j < n; ++j) {
+      if (lane == 0) {
         double v = S[j * n + j];
         for (int k = 0; k < j; ++k) v -= Lc[j * n + k] * Lc[j * n + k];
-        if (!(v > 0.0)) { chol_fail = 1; break; }
+        if (!(v > 0.0)) chol_fail = 1;
         const double l = sqrt(v);
         Lc[j * n + j] = l;
-        for (int r = j + 1; r < n; ++r) {
-          double t = S[r * n + j];
-          for (int k = 0; k < j; ++k) t -= Lc[r * n + k] * Lc[j * n + k];
-          Lc[r * n + j] = t / l;
-        }
+        il[j] = 1.0 / l;
       }
+      __syncwarp();
+      if (chol_fail) return;  // warp-uniform: leave q unchanged
+      if (lane > j && lane < n) {
+        double t = S[lane * n + j];
+        for (int k = 0; k < j; ++k) t -= Lc[lane * n + k] * Lc[j * n + k];
+        Lc[lane * n + j] = t * il[j];
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    if (chol_fail) return;  // warp-uniform: leave q unchanged
-    if (lane < n) {         // column c of S^{-1}: L L^T w = e_c
+    if (lane < n) {  // column c of S^{-1}: L L^T w = e_c
       const int c = lane;
       double v[kMaxJ];
       for (int k = 0; k < n; ++k) {
         double t = k == c ? 1.0 : 0.0;
         for (int m = 0; m < k; ++m) t -= Lc[k * n + m] * v[m];
-        v[k] = t / Lc[k * n + k];
+        v[k] = t * il[k];
       }
       for (int k = n - 1; k >= 0; --k) {
         double t = v[k];
         for (int m = k + 1; m < n; ++m) t -= Lc[m * n + k] * v[m];
-        v[k] = t / Lc[k * n + k];
+        v[k] = t * il[k];
       }
       for (int k = 0; k < n; ++k) {
         Wp[k * n + c] = v[k];
