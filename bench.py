@@ -278,7 +278,7 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def build_inputs(cppflow, torch, dev, reqs):
+def build_inputs(cppflow, torch, dev, reqs, want_truth: bool = False):
     """Pinned host lattices and FP64 targets of the given requests (each with its own
     T, K and n): random draws on the host, target poses by the library's FP64 FK,
     wrong-branch solutions by its FP64 LM restricted to the wrist joints.
@@ -295,8 +295,10 @@ def build_inputs(cppflow, torch, dev, reqs):
     with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         drawn = list(ex.map(draws_of, reqs))
     cand_h, targets_h = [], []
+    truths = []
     for r, w in enumerate(reqs):
         truth, draws = drawn[r]
+        truths.append(truth)
         rob = robots[w.arm_seed - 100]
         tq = torch.from_numpy(truth).to(dev)
         tgt = torch.empty(w.T, 7, dtype=torch.float64, device=dev)
@@ -310,7 +312,109 @@ def build_inputs(cppflow, torch, dev, reqs):
                               arm.lo, arm.hi, synth.pad_k(w.K))
         cand_h.append(torch.from_numpy(cand).pin_memory())
         targets_h.append(tgt.cpu().pin_memory())
+    if want_truth:
+        return arms, robots, cand_h, targets_h, truths
     return arms, robots, cand_h, targets_h
+
+
+def path_clearance(cppflow, torch, dev, robot, geometry, q, params):
+    """Smallest clearance of each configuration of q [T][n] under a collision model,
+    from the library's collision mask (the configurations as one-lane lattices)."""
+    T, n = q.shape
+    cand = torch.zeros(T, n, 4, dtype=torch.float32, device=dev)
+    cand[:, :, 0] = torch.as_tensor(q, dtype=torch.float32, device=dev)
+    tg = torch.zeros(T, 7, dtype=torch.float64, device=dev)
+    tg[:, 3] = 1.0
+    m = torch.empty(T, 4, dtype=torch.uint8, device=dev)
+    p = torch.empty(T, 4, dtype=torch.float32, device=dev)
+    c = torch.empty(T, 4, dtype=torch.float32, device=dev)
+    cppflow.mask_geo(robot, params, geometry, cand, tg, 1, m, p, None, c)
+    return c[:, 0].cpu().numpy()
+
+
+def collision_leg(cppflow, torch, dev, nreq: int, boxes: int = 4, rounds: int = 3) -> dict:
+    """Collision-aware planning on the T = 300, K = 512 workload: per request link
+    capsules (radius 2 cm) and `boxes` cuboids that the true path clears by 5 cm
+    (drawn, then kept when the library's clearance along the true path allows),
+    the collision cost in the search and `rounds` trajectory-length steps with the
+    collision rows between pose phases. Reports plans/s, validity and the smallest
+    clearance of the refined paths, beside the same run without collision rows."""
+    reqs = workload_requests(nreq, 0)
+    arms, robots, cand_h, targets_h, truths = build_inputs(cppflow, torch, dev, reqs, want_truth=True)
+    T, K, n = synth.SINGLE.T, synth.SINGLE.K, synth.SINGLE.n
+    Kp = synth.pad_k(K)
+    P0 = cppflow.make_params(lm_iters=20)
+    geos, kept = [], []
+    for r, w in enumerate(reqs):
+        arm = arms[w.arm_seed - 100]
+        caps = synth.link_capsules(arm, radius=0.02)
+        # self-collision pairs only where the true path itself keeps 1 cm between them
+        self_cl = path_clearance(cppflow, torch, dev, robots[w.arm_seed - 100],
+                                 cppflow.geometry_from(caps), truths[r], P0)
+        if self_cl.min() < 0.01:
+            caps = synth.Geometry(caps.cap_frame, caps.cap_a, caps.cap_b, caps.cap_r, caps.pairs[:0],
+                                  caps.box_R, caps.box_p, caps.box_half)
+        pool = synth.with_boxes(caps, 60000 + r, 16)
+        good = []
+        for b in range(16):
+            one = synth.Geometry(caps.cap_frame, caps.cap_a, caps.cap_b, caps.cap_r, caps.pairs[:0],
+                                 pool.box_R[b:b + 1], pool.box_p[b:b + 1], pool.box_half[b:b + 1])
+            cl = path_clearance(cppflow, torch, dev, robots[w.arm_seed - 100],
+                                cppflow.geometry_from(one), truths[r], P0)
+            if cl.min() >= 0.05:
+                good.append(b)
+            if len(good) == boxes:
+                break
+        kept.append(len(good))
+        geo = synth.Geometry(caps.cap_frame, caps.cap_a, caps.cap_b, caps.cap_r, caps.pairs,
+                             pool.box_R[good], pool.box_p[good], pool.box_half[good])
+        geos.append(cppflow.geometry_from(geo))
+    cand_d = [c.to(dev) for c in cand_h]
+    targ_d = [t.to(dev) for t in targets_h]
+    out = {"workload": f"collision-aware: {nreq} requests T={T} K={K} n={n}, link capsules r = 2 cm "
+                       f"(pairs >= 2 links apart), up to {boxes} boxes clearing the true path by 5 cm",
+           "boxes_per_request": round(float(np.mean(kept)), 2)}
+    for label, P in (("with_collision_rows", cppflow.make_params(lm_iters=20, smooth_rounds=rounds)),
+                     ("without_collision_rows", cppflow.make_params(lm_iters=20, smooth_rounds=rounds,
+                                                                    coll_weight=0.0))):
+        outs, descs = [], []
+        for r in range(nreq):
+            o = dict(sel=torch.empty(T, dtype=torch.int32, device=dev),
+                     q=torch.empty(T, n, dtype=torch.float32, device=dev),
+                     err=torch.empty(T, 2, dtype=torch.float64, device=dev),
+                     rep=torch.zeros(cppflow.REPORT_BYTES, dtype=torch.uint8, device=dev),
+                     best=torch.empty(1, dtype=torch.float32, device=dev))
+            outs.append(o)
+            d = cppflow.PlanDesc(T, K, Kp, reqs[r].arm_seed - 100, cand_d[r].data_ptr(),
+                                 targ_d[r].data_ptr(), o["sel"].data_ptr(), o["q"].data_ptr(),
+                                 o["err"].data_ptr(), o["rep"].data_ptr(), o["best"].data_ptr())
+            d.geometry = cppflow.C.addressof(geos[r])
+            descs.append(d)
+        ws = torch.empty(cppflow.plan_batch_workspace_size(descs, robots), dtype=torch.uint8, device=dev)
+        st = torch.zeros(nreq, dtype=torch.int32, device=dev)
+        s0 = torch.cuda.Stream()
+        batch = cppflow.Batch(robots, P, descs, ws, st, s0)
+        for _ in range(2):
+            batch.run(cppflow.STAGE_ALL, s0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s0)
+        for _ in range(3):
+            batch.run(cppflow.STAGE_ALL, s0)
+        e1.record(s0)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        reps = [cppflow.report_from_bytes(o["rep"].cpu().numpy().tobytes()) for o in outs]
+        clear = [float(path_clearance(cppflow, torch, dev, robots[reqs[r].arm_seed - 100], geos[r],
+                                      outs[r]["q"].cpu().numpy(), P0).min()) for r in range(nreq)]
+        out[label] = {"ms_per_batch": round(ms, 3), "plans_per_s": round(nreq / (ms / 1e3), 1),
+                      "valid_plans": f"{sum(int(x['valid']) for x in reps)}/{nreq}",
+                      "collision_free_paths": f"{sum(int(c >= 0) for c in clear)}/{nreq}",
+                      "min_clearance_m": round(min(clear), 4),
+                      "median_path_clearance_m": round(float(np.median(clear)), 4),
+                      "mean_mjac_rad": round(float(np.mean([x["mjac"] for x in reps])), 4),
+                      "dev_status_nonzero": int((st != 0).sum())}
+        batch.close()
+    return out
 
 
 def uneven_batch(cppflow, torch, dev, nreq: int) -> dict:
@@ -544,6 +648,7 @@ def run_cuda(args, rank: int, world: int, dist):
             "edges_per_s": round(edges / dp_s, 1)}
 
     uneven = uneven_batch(cppflow, torch, dev, args.uneven) if args.uneven and rank == 0 else None
+    coll = collision_leg(cppflow, torch, dev, args.collision) if args.collision and rank == 0 else None
     mix = None
     if args.serve_rates and rank == 0:
         mix = serving_mix(cppflow, torch, dev, [float(x) for x in args.serve_rates.split(",")],
@@ -567,6 +672,8 @@ def run_cuda(args, rank: int, world: int, dist):
             "gpu_launches": launches_per_step * args.steps}
     if uneven is not None:
         line["batched_uneven"] = uneven
+    if coll is not None:
+        line["collision_aware"] = coll
     if mix is not None:
         line["serving_mix"] = {"workload": "serving mix: T = floor(exp U(ln 50, ln 2000)), "
                                            "K in {128, 256, 512, 1024}, 7-DoF, Poisson arrivals",
@@ -589,6 +696,8 @@ def main():
     ap.add_argument("--serve-inflight", type=int, default=8, help="server: launches in flight")
     ap.add_argument("--uneven", type=int, default=256,
                     help="requests of the batched uneven leg (0: skip)")
+    ap.add_argument("--collision", type=int, default=304,
+                    help="requests of the collision-aware leg (0: skip)")
     ap.add_argument("--serve-rates", default="1000", help="Poisson rates (req/s) of the serving "
                     "mix, comma separated; empty to skip")
     ap.add_argument("--mix-pool", type=int, default=48, help="distinct requests in the mix pool")
