@@ -134,6 +134,8 @@ def lib():
             "orc_clearance": (None, [P, P, P, P, P]),
             "orc_mask_geo": (None, [P, P, P, C.c_double, P, P, C.c_int, C.c_int, C.c_int, P, P, P,
                                     P]),
+            "orc_lane_mjac_f32": (None, [P, C.c_int, C.c_int, C.c_int, C.c_int, P]),
+            "orc_batch_opt": (C.c_int, [P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]),
             "orc_collision_rows": (C.c_int, [P, P, P, C.c_double, C.c_double, P, P, C.c_int]),
             "orc_diff_step_geo": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, C.c_double,
                                             P, P]),
@@ -421,6 +423,30 @@ def lm_smooth(robot: Robot, params: Params, q_in, targets, rounds: int, lambda_d
     lib().orc_lm_smooth(C.byref(robot), C.byref(params), _p(q_in), _p(targets), T, int(rounds),
                         float(lambda_d), _p(out), _p(taken))
     return out, int(taken[0])
+
+
+# ---------------------------------------------------------------- cpf-BatchOpt
+def lane_mjac_f32(cand: np.ndarray, K: int) -> np.ndarray:
+    cand = np.ascontiguousarray(cand, np.float32)
+    T, n, Kp = cand.shape
+    out = np.zeros(K, np.float32)
+    lib().orc_lane_mjac_f32(_p(cand), T, K, Kp, n, _p(out))
+    return out
+
+
+def batch_opt(robot: Robot, params: Params, cand: np.ndarray, targets: np.ndarray, K: int,
+              lanes: int = 5):
+    """The `lanes` smoothest lanes refined and checked: dict(sel, mjac, q, reports, best)."""
+    cand = np.ascontiguousarray(cand, np.float32)
+    T, n, Kp = cand.shape
+    targets = _f64(targets).reshape(T, 7)
+    sel = np.zeros(lanes, np.int32)
+    mj = np.zeros(lanes, np.float32)
+    q = np.zeros((lanes, T, n))
+    reps = (Report * lanes)()
+    best = lib().orc_batch_opt(C.byref(robot), C.byref(params), _p(cand), _p(targets), T, K, Kp,
+                               lanes, _p(sel), _p(mj), _p(q), C.cast(reps, C.c_void_p))
+    return dict(sel=sel, mjac=mj, q=q, reports=[r.as_dict() for r in reps], best=best)
 
 
 # ---------------------------------------------------------------- §II report

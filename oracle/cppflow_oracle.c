@@ -1136,6 +1136,62 @@ void orc_lm_smooth_geo(const orc_robot* r, const orc_params* P, const orc_geomet
     free(q); free(v);
 }
 
+/* ------------------------------------------------------------------------- */
+/* cpf-BatchOpt (§III, commented text): optimise the smoothest lanes directly */
+/* ------------------------------------------------------------------------- */
+/* Lane k across the waypoints is one of the K candidate trajectories. Its
+ * smoothness is its mjac, max over steps and joints of |q_{i+1,k,j} - q_{i,k,j}|,
+ * formed in FP32 (an IEEE subtraction and exact max); a lane with a non-finite
+ * value gets +inf. */
+void orc_lane_mjac_f32(const float* cand, int T, int K, int Kp, int n, float* mjac) {
+    for (int k = 0; k < K; ++k) {
+        float m = 0.0f;
+        int finite = 1;
+        for (int i = 0; i < T; ++i)
+            for (int j = 0; j < n; ++j) {
+                const float v = cand[((size_t)i * n + j) * Kp + k];
+                if (!isfinite(v)) finite = 0;
+                if (i + 1 < T) {
+                    const float d = fabsf(cand[((size_t)(i + 1) * n + j) * Kp + k] - v);
+                    if (d > m) m = d;
+                }
+            }
+        mjac[k] = finite ? m : INFINITY;
+    }
+}
+
+/* The `lanes` smoothest lanes (ascending mjac, lowest index first among
+ * equals), each refined by orc_lm as its own trajectory and checked by
+ * orc_check; returns the position (in that order) of the first valid one, or -1.
+ * q_out [lanes][T][n], reps [lanes]. */
+int orc_batch_opt(const orc_robot* r, const orc_params* P, const float* cand,
+                  const double* targets, int T, int K, int Kp, int lanes, int32_t* lane_sel,
+                  float* lane_mjac, double* q_out, orc_report* reps) {
+    const int n = r->n;
+    float* m = (float*)malloc(sizeof(float) * (size_t)K);
+    unsigned char* used = (unsigned char*)calloc((size_t)K, 1);
+    double* seed = (double*)malloc(sizeof(double) * (size_t)T * n);
+    orc_lane_mjac_f32(cand, T, K, Kp, n, m);
+    int best = -1;
+    for (int l = 0; l < lanes; ++l) {
+        int arg = -1;
+        for (int k = 0; k < K; ++k)   /* smallest unused, lowest index on ties (inf last) */
+            if (!used[k] && (arg < 0 || m[k] < m[arg])) arg = k;
+        used[arg] = 1;
+        lane_sel[l] = arg;
+        lane_mjac[l] = m[arg];
+        for (int i = 0; i < T; ++i)
+            for (int j = 0; j < n; ++j)
+                seed[(size_t)i * n + j] = (double)cand[((size_t)i * n + j) * Kp + arg];
+        double* q = q_out + (size_t)l * T * n;
+        orc_lm(r, P, seed, targets, T, q, 0, 0);
+        orc_check(r, P, q, targets, T, 0, &reps[l]);
+        if (best < 0 && reps[l].valid) best = l;
+    }
+    free(m); free(used); free(seed);
+    return best;
+}
+
 /* Mask -> FP32 search -> seed -> LM -> check, for one request. */
 int orc_plan(const orc_robot* r, const orc_params* P, const float* cand,
              const double* targets, int T, int K, int Kp, int32_t* sel,

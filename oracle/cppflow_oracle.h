@@ -166,6 +166,12 @@ void orc_check(const orc_robot* r, const orc_params* P, const double* q /*[T][n]
                const double* targets, int T, double* pose_err /*[T][2] or 0*/,
                orc_report* rep);
 
+/* ---- cpf-BatchOpt: the smoothest candidate lanes refined directly ---- */
+void orc_lane_mjac_f32(const float* cand, int T, int K, int Kp, int n, float* mjac /*[K]*/);
+int  orc_batch_opt(const orc_robot* r, const orc_params* P, const float* cand,
+                   const double* targets, int T, int K, int Kp, int lanes, int32_t* lane_sel,
+                   float* lane_mjac, double* q_out /*[lanes][T][n]*/, orc_report* reps);
+
 /* ---- whole post-generation pipeline for one request ---- */
 int orc_plan(const orc_robot* r, const orc_params* P, const float* cand,
              const double* targets, int T, int K, int Kp,

@@ -219,6 +219,28 @@ def draw_candidates(seed: int, T: int, K: int, n: int, p_wb: float, p_out: float
     return CandDraws(noise, wb, out, oj, up, mag)
 
 
+def draw_candidates_coherent(seed: int, T: int, K: int, n: int, p_wb: float, p_out: float,
+                             rho: float = 0.98) -> CandDraws:
+    """Lane-coherent draws, shaped like a generative IK model's K motion plans (lane k
+    across the waypoints is one plan): the wrong-branch choice is made once per lane,
+    and each lane's noise follows an AR(1) walk along the path, e_i = rho e_{i-1} +
+    sqrt(1 - rho^2) z_i (standard normal at every waypoint, correlation rho between
+    neighbours). Outliers stay independent per candidate."""
+    z = normal(seed, S_NOISE, T * K * n).reshape(T, K, n)
+    noise = np.empty_like(z)
+    noise[0] = z[0]
+    c = math.sqrt(1.0 - rho * rho)
+    for i in range(1, T):
+        noise[i] = rho * noise[i - 1] + c * z[i]
+    wb_lane = uniform(seed, S_WB, K) < p_wb
+    wb = np.broadcast_to(wb_lane[None, :], (T, K)).copy()
+    out = uniform(seed, S_OUT, T * K).reshape(T, K) < p_out
+    oj = np.minimum((uniform(seed, S_OUTJ, T * K) * n).astype(np.int64), n - 1).reshape(T, K)
+    up = uniform(seed, S_OUTSIGN, T * K).reshape(T, K) < 0.5
+    mag = 0.01 + 0.19 * uniform(seed, S_OUTMAG, T * K).reshape(T, K)
+    return CandDraws(noise, wb, out, oj, up, mag)
+
+
 def pad_k(K: int, mult: int = 32) -> int:
     return ((K + mult - 1) // mult) * mult
 

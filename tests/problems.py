@@ -34,7 +34,9 @@ def oracle_robot(arm: synth.Arm) -> oracle.Robot:
     return oracle.make_robot(arm.a, arm.d, arm.alpha, arm.lo, arm.hi, arm.theta0)
 
 
-def build(w: synth.Workload, **param_overrides) -> Problem:
+def build(w: synth.Workload, coherent: bool = False, **param_overrides) -> Problem:
+    """Oracle-built problem of a workload; coherent=True draws lane-coherent candidates
+    (synth.draw_candidates_coherent) instead of independent ones."""
     oracle.build()
     arm = synth.draw_arm(w.arm_seed, w.n, w.wrist)
     robot = oracle_robot(arm)
@@ -46,7 +48,8 @@ def build(w: synth.Workload, **param_overrides) -> Problem:
         q_wb, _, _ = oracle.lm(robot, P_wb, synth.wrong_branch_start(truth), targets)
     else:
         q_wb = truth.copy()
-    draws = synth.draw_candidates(w.cand_seed, w.T, w.K, w.n, w.p_wb, w.p_out)
+    draw = synth.draw_candidates_coherent if coherent else synth.draw_candidates
+    draws = draw(w.cand_seed, w.T, w.K, w.n, w.p_wb, w.p_out)
     cand = synth.assemble(truth, q_wb, draws, w.sigma, arm.lo, arm.hi)
     kw = dict(lm_iters=w.lm_iters, lambda0=w.lambda0)
     kw.update(param_overrides)
