@@ -358,6 +358,28 @@ cpp_status cpp_plan_geo(const cpp_robot_t* robot, const cpp_params_t* params,
                         float* q_out, double* pose_err, cpp_report_t* report,
                         int32_t* dev_status, cpp_stream_t stream);
 
+/* ------------------------------------------------------------------ cpf-BatchOpt
+ * The paper's fastest planner variant (§III, in its commented text): refine the
+ * smoothest of the K candidate trajectories directly instead of searching. Lane
+ * k across the waypoints is one candidate trajectory; its smoothness is its mjac,
+ * max over steps and joints of |q_{i+1,k,j} - q_{i,k,j}| in FP32 (+inf if it holds
+ * a non-finite value). The `lanes` smoothest (ascending mjac, lowest index first
+ * among equals; the paper uses 5) are refined as separate trajectories by the LM
+ * of cpp_lm_refine (with params->smooth_rounds alternation) and checked as by
+ * cpp_check. Device buffers out: lane_sel [lanes] (lane indices, smoothest
+ * first), lane_mjac [lanes], q_out [lanes][T][n], pose_err [lanes][T][2] (or
+ * NULL), reports [lanes], best [1] (position in lane_sel of the first valid plan,
+ * -1 if none). Workspace: cpp_batch_opt_workspace_size(T, K, n, lanes) bytes,
+ * 256-byte aligned. INVALID_ARG: lanes outside [1, K], lattice and params as
+ * cpp_plan. Meaningful on lane-coherent candidates (a generative model's plans);
+ * on independently drawn candidates the search (cpp_plan) is the planner. */
+size_t cpp_batch_opt_workspace_size(int32_t T, int32_t K, int32_t n, int32_t lanes);
+cpp_status cpp_batch_opt(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
+                         const double* targets, int32_t T, int32_t K, int32_t Kp, int32_t lanes,
+                         void* workspace, size_t ws_bytes, int32_t* lane_sel, float* lane_mjac,
+                         float* q_out, double* pose_err, cpp_report_t* reports, int32_t* best,
+                         int32_t* dev_status, cpp_stream_t stream);
+
 /* ------------------------------------------------------------------ many requests
  * One launch per stage for `count` requests of different T, K, Kp (same params).
  * Each descriptor holds DEVICE pointers; robots are read from the host array

@@ -169,6 +169,9 @@ _SIGS = {
     "cpp_plan_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "cpp_plan": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_size_t,
                            _P, _P, _P, _P, _P, _P, _P]),
+    "cpp_batch_opt_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "cpp_batch_opt": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P,
+                                C.c_size_t, _P, _P, _P, _P, _P, _P, _P, _P]),
     "cpp_plan_batch_workspace_size": (C.c_size_t, [_P, C.c_int32, _P, C.c_int32]),
     "cpp_plan_batch": (C.c_int, [_P, C.c_int32, _P, _P, C.c_int32, _P, C.c_size_t, _P, _P]),
     "cpp_batch_create": (C.c_int, [_P, C.c_int32, _P, _P, C.c_int32, _P, C.c_size_t, _P, _P,
@@ -385,6 +388,23 @@ def plan_geo(robot: Robot, params: Params, geometry: Geometry | None, cand, targ
                               Kp, ptr(workspace), nbytes, ptr(sel), ptr(best_cost), ptr(q_out),
                               ptr(pose_err), ptr(report), ptr(dev_status), stream_handle(stream)),
            "cpp_plan_geo")
+
+
+def batch_opt_workspace_size(T: int, K: int, n: int, lanes: int) -> int:
+    return lib().cpp_batch_opt_workspace_size(T, K, n, lanes)
+
+
+def batch_opt(robot: Robot, params: Params, cand, targets, K: int, lanes: int, workspace, lane_sel,
+              lane_mjac, q_out, reports, best, pose_err=None, dev_status=None, stream=None):
+    """cpf-BatchOpt: the `lanes` smoothest candidate lanes refined and checked (device
+    tensors: lane_sel [lanes] i32, lane_mjac [lanes] f32, q_out [lanes][T][n] f32,
+    reports [lanes * REPORT_BYTES] u8, best [1] i32)."""
+    T, n, Kp = cand.shape
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().cpp_batch_opt(C.byref(robot), C.byref(params), ptr(cand), ptr(targets), T, K, Kp,
+                               lanes, ptr(workspace), nbytes, ptr(lane_sel), ptr(lane_mjac),
+                               ptr(q_out), ptr(pose_err), ptr(reports), ptr(best),
+                               ptr(dev_status), stream_handle(stream)), "cpp_batch_opt")
 
 
 def plan_batch_workspace_size(descs, robots) -> int:

@@ -481,6 +481,34 @@ cpp_status cpp_plan_geo(const cpp_robot_t* robot, const cpp_params_t* params,
   return cuda_status(launch_check(s, *params, st), "cpp_plan/check");
 }
 
+// ------------------------------------------------------------------ cpf-BatchOpt
+size_t cpp_batch_opt_workspace_size(int32_t T, int32_t K, int32_t n, int32_t lanes) {
+  if (T < 1 || K < 1 || n < 1 || lanes < 1) return 0;
+  return batch_opt_layout(T, K, n, lanes).total;
+}
+
+cpp_status cpp_batch_opt(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
+                         const double* targets, int32_t T, int32_t K, int32_t Kp, int32_t lanes,
+                         void* workspace, size_t ws_bytes, int32_t* lane_sel, float* lane_mjac,
+                         float* q_out, double* pose_err, cpp_report_t* reports, int32_t* best,
+                         int32_t* dev_status, cpp_stream_t stream) {
+  if (cpp_status s = check_robot(robot)) return s;
+  if (cpp_status s = check_params(params)) return s;
+  const int n = robot->n;
+  if (cpp_status s = check_lattice(T, K, Kp, n)) return s;
+  if (cpp_status s = check_smooth(params, T, n)) return s;
+  if (lanes < 1 || lanes > K) return fail(CPP_ERR_INVALID_ARG, "lanes = %d outside [1, K]", lanes);
+  if (!cand || !targets || !lane_sel || !lane_mjac || !q_out || !reports || !best || !workspace)
+    return fail(CPP_ERR_INVALID_ARG, "NULL buffer");
+  const BatchOptLayout L = batch_opt_layout(T, K, n, lanes);
+  if (ws_bytes < L.total || !aligned(workspace, 256))
+    return fail(CPP_ERR_INVALID_ARG, "workspace needs %zu bytes, 256-byte aligned", L.total);
+  return cuda_status(launch_batch_opt(*robot, *params, cand, targets, T, K, Kp, lanes,
+                                      static_cast<char*>(workspace), lane_sel, lane_mjac, q_out,
+                                      pose_err, reports, best, dev_status, (cudaStream_t)stream),
+                     "cpp_batch_opt");
+}
+
 // ------------------------------------------------------------------ many requests
 namespace {
 struct BatchLayout {

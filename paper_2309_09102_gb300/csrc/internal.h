@@ -63,6 +63,18 @@ cudaError_t launch_check(const SingleSrc& s, const cpp_params_t& P, cudaStream_t
 cudaError_t launch_check_batch(const BatchSrc& s, int nreq, const cpp_params_t& P,
                                cudaStream_t st);
 
+// batchopt.cu
+struct BatchOptLayout {  // workspace of cpf-BatchOpt: lane mjac, pseudo-request table, robot,
+                         // gathered trajectories
+  size_t mjac, reqs, robot, q_in, total;
+};
+BatchOptLayout batch_opt_layout(int T, int K, int n, int lanes);
+cudaError_t launch_batch_opt(const cpp_robot_t& robot, const cpp_params_t& P, const float* cand,
+                             const double* targets, int T, int K, int Kp, int lanes, char* ws,
+                             int32_t* sel, float* sel_mjac, float* q_out, double* pose_err,
+                             cpp_report_t* reports, int32_t* best, int32_t* dev_status,
+                             cudaStream_t st);
+
 // capi.cu
 void set_last_error(const char* msg);  // message returned by cpp_last_error()
 size_t geo_bytes();                    // sizeof(GeoF)
