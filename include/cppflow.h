@@ -509,14 +509,27 @@ typedef struct cpp_server_config {
 
 #define CPP_REQ_BORROW 1  /* inputs stay valid and unchanged until the plan is collected:
                              no copy at submit (pinned inputs then go straight to the device) */
+/* Anytime planning (§III-C: the latest valid solution is kept and can be taken
+ * while the optimiser goes on improving it). After the plan's first pass the
+ * request keeps its device slot and runs up to anytime_rounds improvement
+ * rounds, each one trajectory-length step (cpp_smooth_step, with the collision
+ * rows when the request has a model) and one pose phase from the current
+ * trajectory, then the check. A result is published as the best so far when it
+ * is valid and, after the first, shorter (trajectory length) than the last one
+ * published. cpp_plan_peek reads the best so far at any time; poll / wait
+ * complete when the rounds are used up (or cancel stops them) and return the
+ * best so far, or the last result if none was valid. */
+#define CPP_REQ_ANYTIME 2
 
 typedef struct cpp_plan_req {
     const cpp_robot_t* robot;  /* host */
     int32_t T, K, Kp;          /* lattice shape, as for cpp_plan */
-    int32_t flags;             /* 0 or CPP_REQ_BORROW */
+    int32_t flags;             /* CPP_REQ_BORROW | CPP_REQ_ANYTIME, or 0 */
     const float* cand;         /* host [T][n][Kp] */
     const double* targets;     /* host [T][7] */
     const cpp_geometry_t* geometry;  /* host, copied at submit; NULL = no collision model */
+    int32_t anytime_rounds;    /* improvement rounds of an anytime request (0..100000) */
+    int32_t reserved;
 } cpp_plan_req_t;
 
 typedef struct cpp_plan_result {  /* caller-owned HOST buffers; any pointer may be NULL */
@@ -525,15 +538,18 @@ typedef struct cpp_plan_result {  /* caller-owned HOST buffers; any pointer may 
     double* pose_err;       /* [T][2] */
     cpp_report_t* report;   /* [1] */
     float* best_cost;       /* [1] */
-    double latency_ms;      /* out: submit -> completion seen by the server */
+    double latency_ms;      /* out: submit -> completion seen by the server (peek: -> now) */
     int32_t dev_status;     /* out: device status word of the request */
-    int32_t reserved;
+    int32_t rounds;         /* out: improvement rounds run when this result was published */
 } cpp_plan_result_t;
 
 typedef struct cpp_server_stats {
     uint64_t submitted, completed, failed, cancelled, batches, sum_batch;
     int32_t max_batch_seen, resident, queued, reserved;
     size_t hbm_used, hbm_high_water;
+    uint64_t improve_batches;  /* launches of anytime improvement rounds */
+    uint64_t improve_rounds;   /* improvement rounds run (over all requests) */
+    uint64_t published;        /* best-so-far results published */
 } cpp_server_stats_t;
 
 void cpp_server_config_default(cpp_server_config_t* cfg);
@@ -552,9 +568,16 @@ cpp_status cpp_plan_poll(cpp_server_t* srv, uint64_t ticket, cpp_plan_result_t* 
 /* As poll, but blocks up to timeout_us (negative = no limit); PENDING on timeout. */
 cpp_status cpp_plan_wait(cpp_server_t* srv, uint64_t ticket, cpp_plan_result_t* res,
                          int64_t timeout_us);
-/* Removes a request that is still queued (OK; its poll returns CANCELLED);
- * PENDING if it is already on the device or finished. */
+/* Removes a request that is still queued (OK; its poll returns CANCELLED); for
+ * an anytime request on the device or improving, stops further rounds (OK; it
+ * completes with its best so far); PENDING if it is on the device (not anytime)
+ * or finished. */
 cpp_status cpp_plan_cancel(cpp_server_t* srv, uint64_t ticket);
+/* Anytime requests: copies the best-so-far result into `res` without collecting
+ * the request and returns OK; PENDING while none is published; a finished
+ * request that never published returns its status as poll would, still
+ * uncollected. NOT_FOUND for an unknown ticket. */
+cpp_status cpp_plan_peek(cpp_server_t* srv, uint64_t ticket, cpp_plan_result_t* res);
 cpp_status cpp_server_get_stats(cpp_server_t* srv, cpp_server_stats_t* out);
 /* Finishes the launches in flight, cancels queued requests, frees everything. */
 void cpp_server_destroy(cpp_server_t* srv);

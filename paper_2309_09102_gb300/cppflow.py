@@ -102,6 +102,7 @@ class PlanDesc(C.Structure):
 
 REPORT_BYTES = C.sizeof(Report)
 REQ_BORROW = 1
+REQ_ANYTIME = 2
 
 
 class TuneResult(C.Structure):
@@ -122,20 +123,21 @@ class ServerConfig(C.Structure):
 class PlanReq(C.Structure):
     _fields_ = [("robot", C.c_void_p), ("T", C.c_int32), ("K", C.c_int32), ("Kp", C.c_int32),
                 ("flags", C.c_int32), ("cand", C.c_void_p), ("targets", C.c_void_p),
-                ("geometry", C.c_void_p)]
+                ("geometry", C.c_void_p), ("anytime_rounds", C.c_int32), ("reserved", C.c_int32)]
 
 
 class PlanResult(C.Structure):
     _fields_ = [("sel", C.c_void_p), ("q", C.c_void_p), ("pose_err", C.c_void_p),
                 ("report", C.c_void_p), ("best_cost", C.c_void_p), ("latency_ms", C.c_double),
-                ("dev_status", C.c_int32), ("reserved", C.c_int32)]
+                ("dev_status", C.c_int32), ("rounds", C.c_int32)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [(f, C.c_uint64) for f in ("submitted", "completed", "failed", "cancelled",
                                            "batches", "sum_batch")] + [
         (f, C.c_int32) for f in ("max_batch_seen", "resident", "queued", "reserved")] + [
-        ("hbm_used", C.c_size_t), ("hbm_high_water", C.c_size_t)]
+        ("hbm_used", C.c_size_t), ("hbm_high_water", C.c_size_t)] + [
+        (f, C.c_uint64) for f in ("improve_batches", "improve_rounds", "published")]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -189,6 +191,7 @@ _SIGS = {
     "cpp_plan_poll": (C.c_int, [_P, C.c_uint64, _P]),
     "cpp_plan_wait": (C.c_int, [_P, C.c_uint64, _P, C.c_int64]),
     "cpp_plan_cancel": (C.c_int, [_P, C.c_uint64]),
+    "cpp_plan_peek": (C.c_int, [_P, C.c_uint64, _P]),
     "cpp_server_get_stats": (C.c_int, [_P, _P]),
     "cpp_server_destroy": (None, [_P]),
 }
@@ -494,20 +497,27 @@ class Server:
         self._live = {}  # ticket -> (robot, inputs kept alive, shape)
 
     def submit(self, robot: Robot, cand, targets, K: int, borrow: bool = False,
-               geometry: Geometry | None = None) -> int:
+               geometry: Geometry | None = None, anytime_rounds: int | None = None) -> int:
+        """anytime_rounds: an anytime request with that many improvement rounds."""
         import numpy as np
         cand = np.ascontiguousarray(cand, dtype=np.float32)
         targets = np.ascontiguousarray(targets, dtype=np.float64)
         T, n, Kp = cand.shape
-        req = PlanReq(C.addressof(robot), T, K, Kp, REQ_BORROW if borrow else 0,
-                      cand.ctypes.data, targets.ctypes.data,
-                      C.addressof(geometry) if geometry is not None else None)
+        flags = (REQ_BORROW if borrow else 0) | (REQ_ANYTIME if anytime_rounds is not None else 0)
+        req = PlanReq(C.addressof(robot), T, K, Kp, flags, cand.ctypes.data, targets.ctypes.data,
+                      C.addressof(geometry) if geometry is not None else None,
+                      int(anytime_rounds or 0), 0)
         t = C.c_uint64()
         _check(lib().cpp_plan_submit(self.handle, C.byref(req), C.byref(t)), "cpp_plan_submit")
         self._live[t.value] = (robot, (cand, targets) if borrow else None, (T, n))
         return t.value
 
-    def _result(self, ticket: int, fn, *extra):
+    def peek(self, ticket: int):
+        """The best-so-far result of an anytime request, without collecting it:
+        (status, result dict) -- status PENDING (and None) while none is published."""
+        return self._result(ticket, lib().cpp_plan_peek, keep=True)
+
+    def _result(self, ticket: int, fn, *extra, keep: bool = False):
         import numpy as np
         if ticket not in self._live:  # unknown here: let the library answer (NOT_FOUND)
             _check(fn(self.handle, ticket, None, *extra), "cpp_plan_poll")
@@ -522,11 +532,12 @@ class Server:
         st = fn(self.handle, ticket, C.byref(res), *extra)
         if st == PENDING:
             return st, None
-        self._live.pop(ticket, None)
+        if not keep:
+            self._live.pop(ticket, None)
         if st == ERR_NOT_FOUND:
             raise CppflowError(st, last_error())
         return st, dict(sel=sel, q=q, err=err, report=rep.as_dict(), best=float(best[0]),
-                        latency_ms=res.latency_ms, dev_status=res.dev_status)
+                        latency_ms=res.latency_ms, dev_status=res.dev_status, rounds=res.rounds)
 
     def poll(self, ticket: int):
         return self._result(ticket, lib().cpp_plan_poll)

@@ -57,6 +57,10 @@ cudaError_t launch_smooth(const SingleSrc& s, const cpp_params_t& P, cudaStream_
 // some request has a collision model (its steps then carry the collision rows)
 cudaError_t launch_lm_batch_geo(const BatchSrc& s, int n, int nreq, int max_T,
                                 const cpp_params_t& P, bool any_geo, cudaStream_t st);
+// one anytime improvement round of a batch: a trajectory-length step, a pose
+// phase from the current trajectory, the check
+cudaError_t launch_improve_batch(const BatchSrc& s, int n, int nreq, int max_T,
+                                 const cpp_params_t& P, bool any_geo, cudaStream_t st);
 size_t smooth_smem_bytes(int T, int n);  // shared memory of the trajectory-length step
 int lm_launches(const cpp_params_t& P, bool any_geo);  // kernel launches of one refinement
 cudaError_t launch_check(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st);

@@ -721,6 +721,16 @@ cudaError_t launch_lm_batch_geo(const BatchSrc& s, int n, int nreq, int max_T,
                                 const cpp_params_t& P, bool any_geo, cudaStream_t st) {
   return launch_lm_t(s, n, nreq, max_T, P, false, any_geo, st);
 }
+template <class Src>
+static cudaError_t launch_check_t(const Src& s, int nreq, const cpp_params_t& P, cudaStream_t st);
+
+cudaError_t launch_improve_batch(const BatchSrc& s, int n, int nreq, int max_T,
+                                 const cpp_params_t& P, bool any_geo, cudaStream_t st) {
+  cudaError_t e = launch_smooth_t(s, n, nreq, max_T, P, any_geo, st);
+  if (e == cudaSuccess) e = launch_lm_phase(s, n, nreq, max_T, P, false, true, st);
+  if (e == cudaSuccess) e = launch_check_t(s, nreq, P, st);
+  return e;
+}
 cudaError_t launch_smooth(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st) {
   return launch_smooth_t(s, s.r.n, 1, s.r.T, P, s.has_geo && s.r.smooth_ws, st);
 }

@@ -96,7 +96,7 @@ class Arena {
   size_t used_ = 0, high_ = 0, size_ = 0;
 };
 
-enum class St { Queued, Running, Done, Failed, Cancelled };
+enum class St { Queued, Running, Improving, Done, Failed, Cancelled };
 
 struct Request {
   uint64_t ticket = 0;
@@ -120,6 +120,11 @@ struct Request {
   cpp_status result = CPP_OK;
   int32_t dev_status = 0;
   Clock::time_point t_submit, t_done;
+  // anytime planning: improvement rounds after the first pass, best result so far
+  bool anytime = false, stop_improving = false, have_best = false;
+  int rounds_left = 0, rounds_done = 0, best_rounds = 0;
+  double best_len = 0.0;
+  std::vector<char> best_out;  // host copy of the best published result (out_bytes)
 };
 
 struct Layout {
@@ -148,6 +153,7 @@ Layout slot_layout(int T, int Kp, int n) {
 
 struct Launch {
   std::vector<Request*> reqs;
+  bool improve = false;  // an anytime improvement round (slots already resident)
   int stream = 0;
   cudaEvent_t done = nullptr;
   size_t tab_off = 0, tab_bytes = 0;      // device: Req[] | robots[] | status[]
@@ -170,6 +176,7 @@ struct cpp_server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> queue;
+  std::deque<Request*> improve_q;  // anytime requests waiting for their next round
   std::unordered_map<uint64_t, Request*> reqs;
   std::vector<Launch*> inflight;
   int resident = 0;
@@ -182,6 +189,10 @@ struct cpp_server {
 
   void run();
   bool form_batch(Launch* L);
+  bool form_improve(Launch* L);
+  bool alloc_table(Launch* L);
+  void finish(Request* r);
+  void anytime_step(Request* r, bool improve_round);
   cpp_status enqueue(Launch* L);
   void retire(Launch* L, cudaError_t e);
   void release_host(Request* r);
@@ -234,10 +245,7 @@ bool cpp_server::form_batch(Launch* L) {
     it = queue.erase(it);
   }
   if (L->reqs.empty()) return false;
-  const int count = (int)L->reqs.size();
-  L->tab_bytes = align256(sizeof(Req) * count) + align256(sizeof(cpp_robot_t) * count) +
-                 align256(sizeof(int32_t) * count);
-  if (!darena.alloc(L->tab_bytes, &L->tab_off)) {
+  if (!alloc_table(L)) {
     // no room for the table: give the requests back
     for (Request* r : L->reqs) {
       darena.release(r->dev_off, r->dev_bytes);
@@ -248,6 +256,15 @@ bool cpp_server::form_batch(Launch* L) {
     L->reqs.clear();
     return false;
   }
+  return true;
+}
+
+// Device table (Req[] | robots[] | status[]) of a launch and its host mirror.
+bool cpp_server::alloc_table(Launch* L) {
+  const int count = (int)L->reqs.size();
+  L->tab_bytes = align256(sizeof(Req) * count) + align256(sizeof(cpp_robot_t) * count) +
+                 align256(sizeof(int32_t) * count);
+  if (!darena.alloc(L->tab_bytes, &L->tab_off)) return false;
   L->tab_pin_bytes = L->tab_bytes;
   if (parena.alloc(L->tab_pin_bytes, &L->tab_pin)) {
     L->tab_pinned = true;
@@ -257,6 +274,66 @@ bool cpp_server::form_batch(Launch* L) {
     L->tab_h = L->tab_host.data();
   }
   return true;
+}
+
+// An improvement launch: anytime requests of one joint count, in queue order.
+bool cpp_server::form_improve(Launch* L) {
+  if (improve_q.empty()) return false;
+  const int n = improve_q.front()->n;
+  for (auto it = improve_q.begin(); it != improve_q.end();) {
+    if ((int)L->reqs.size() >= cfg.max_batch) break;
+    if ((*it)->n != n) { ++it; continue; }
+    (*it)->state = St::Running;
+    L->reqs.push_back(*it);
+    it = improve_q.erase(it);
+  }
+  L->improve = true;
+  if (!alloc_table(L)) {
+    for (auto it = L->reqs.rbegin(); it != L->reqs.rend(); ++it) {
+      (*it)->state = St::Improving;
+      improve_q.push_front(*it);
+    }
+    L->reqs.clear();
+    return false;
+  }
+  return true;
+}
+
+// A finished request: its best published result (anytime) becomes the result;
+// the device slot is freed.
+void cpp_server::finish(Request* r) {
+  if (r->have_best) memcpy(r->h_out, r->best_out.data(), r->out_bytes);
+  darena.release(r->dev_off, r->dev_bytes);
+  --resident;
+  r->t_done = Clock::now();
+  r->state = St::Done;
+  r->result = r->dev_status == 0 ? CPP_OK : (cpp_status)r->dev_status;
+  ++stats.completed;
+}
+
+// After a pass or an improvement round of an anytime request: publish the result
+// when it is valid and (after the first) shorter; queue the next round or finish.
+void cpp_server::anytime_step(Request* r, bool improve_round) {
+  if (improve_round) {
+    ++r->rounds_done;
+    --r->rounds_left;
+    ++stats.improve_rounds;
+  }
+  cpp_report_t rep;
+  memcpy(&rep, r->h_out + r->o_rep, sizeof(rep));
+  if (r->dev_status == 0 && rep.valid && (!r->have_best || rep.traj_len < r->best_len)) {
+    r->best_out.assign(r->h_out, r->h_out + r->out_bytes);
+    r->have_best = true;
+    r->best_len = rep.traj_len;
+    r->best_rounds = r->rounds_done;
+    ++stats.published;
+  }
+  if (r->rounds_left > 0 && !r->stop_improving && r->dev_status == 0) {
+    r->state = St::Improving;
+    improve_q.push_back(r);
+  } else {
+    finish(r);
+  }
 }
 
 cpp_status cpp_server::enqueue(Launch* L) {
@@ -276,12 +353,15 @@ cpp_status cpp_server::enqueue(Launch* L) {
   for (int i = 0; i < count; ++i) {
     Request* r = L->reqs[i];
     char* b = d_arena + r->dev_off;
-    cudaError_t e = cudaMemcpyAsync(b + r->o_cand, r->cand, (size_t)r->T * r->n * r->Kp * sizeof(float),
-                                    cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(b + r->o_tgt, r->targets, (size_t)r->T * 7 * sizeof(double),
+    cudaError_t e = cudaSuccess;
+    if (!L->improve) {  // an improvement round finds its inputs resident
+      e = cudaMemcpyAsync(b + r->o_cand, r->cand, (size_t)r->T * r->n * r->Kp * sizeof(float),
                           cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server H2D: %s", cudaGetErrorString(e));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + r->o_tgt, r->targets, (size_t)r->T * 7 * sizeof(double),
+                            cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server H2D: %s", cudaGetErrorString(e));
+    }
     Req q;
     memset(&q, 0, sizeof(q));
     q.T = r->T; q.K = r->K; q.Kp = r->Kp; q.n = r->n; q.robot = i; q.Kb = bp_stride(r->Kp);
@@ -290,9 +370,11 @@ cpp_status cpp_server::enqueue(Launch* L) {
     const PlanLayout PL = plan_layout(r->T, r->Kp, r->n);
     carve_plan(q, b + r->o_ws, PL);
     if (!r->geo.empty()) {  // pageable source: staged before the call returns
-      e = cudaMemcpyAsync(b + r->o_ws + PL.geo, r->geo.data(), r->geo.size(),
-                          cudaMemcpyHostToDevice, st);
-      if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server H2D: %s", cudaGetErrorString(e));
+      if (!L->improve) {
+        e = cudaMemcpyAsync(b + r->o_ws + PL.geo, r->geo.data(), r->geo.size(),
+                            cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server H2D: %s", cudaGetErrorString(e));
+      }
       q.geo = reinterpret_cast<const GeoF*>(b + r->o_ws + PL.geo);
       any_geo = true;
     }
@@ -314,12 +396,20 @@ cpp_status cpp_server::enqueue(Launch* L) {
   if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server H2D table: %s", cudaGetErrorString(e));
   BatchSrc src{reinterpret_cast<const Req*>(tab_d),
                reinterpret_cast<const cpp_robot_t*>(tab_d + align256(sizeof(Req) * count))};
-  if ((e = launch_mask_batch(src, n, count, max_tasks, cfg.params, any_geo, st)) != cudaSuccess ||
-      (e = launch_dp_batch(src, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK,
-                           cfg.params.dp_objective, n, count, max_T, max_Kp, st)) != cudaSuccess ||
-      (e = launch_lm_batch_geo(src, n, count, max_T, cfg.params, any_geo, st)) != cudaSuccess ||
-      (e = launch_check_batch(src, count, cfg.params, st)) != cudaSuccess)
+  if (L->improve) {
+    if ((e = launch_improve_batch(src, n, count, max_T, cfg.params, any_geo, st)) != cudaSuccess)
+      return sfail(CPP_ERR_CUDA, "server launch: %s", cudaGetErrorString(e));
+  } else if ((e = launch_mask_batch(src, n, count, max_tasks, cfg.params, any_geo, st)) !=
+                 cudaSuccess ||
+             (e = launch_dp_batch(src, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD |
+                                       CPP_STAGE_BACKTRACK,
+                                  cfg.params.dp_objective, n, count, max_T, max_Kp, st)) !=
+                 cudaSuccess ||
+             (e = launch_lm_batch_geo(src, n, count, max_T, cfg.params, any_geo, st)) !=
+                 cudaSuccess ||
+             (e = launch_check_batch(src, count, cfg.params, st)) != cudaSuccess) {
     return sfail(CPP_ERR_CUDA, "server launch: %s", cudaGetErrorString(e));
+  }
   for (int i = 0; i < count; ++i) {
     Request* r = L->reqs[i];
     e = cudaMemcpyAsync(r->h_out, d_arena + r->dev_off + r->o_out, r->out_bytes,
@@ -339,20 +429,27 @@ void cpp_server::retire(Launch* L, cudaError_t e) {
   const auto now = Clock::now();
   for (int i = 0; i < count; ++i) {
     Request* r = L->reqs[i];
-    darena.release(r->dev_off, r->dev_bytes);
-    --resident;
-    r->t_done = now;
     if (e != cudaSuccess) {
+      darena.release(r->dev_off, r->dev_bytes);
+      --resident;
+      r->t_done = now;
       r->state = St::Failed;
       r->result = CPP_ERR_CUDA;
       ++stats.failed;
-    } else {
-      r->dev_status = tst[i];
-      r->state = St::Done;
-      r->result = tst[i] == 0 ? CPP_OK : (cpp_status)tst[i];
-      ++stats.completed;
+      release_host(r);
+      continue;
     }
-    if (r->state == St::Failed) release_host(r);
+    r->dev_status = tst[i];
+    if (r->anytime) {
+      anytime_step(r, L->improve);
+      continue;
+    }
+    darena.release(r->dev_off, r->dev_bytes);
+    --resident;
+    r->t_done = now;
+    r->state = St::Done;
+    r->result = tst[i] == 0 ? CPP_OK : (cpp_status)tst[i];
+    ++stats.completed;
   }
   darena.release(L->tab_off, L->tab_bytes);
   if (L->tab_pinned) parena.release(L->tab_pin, L->tab_pin_bytes);
@@ -377,16 +474,23 @@ void cpp_server::run() {
     if (stop && inflight.empty()) break;
     // launch the next batch
     bool launched = false;
-    if (!stop && (int)inflight.size() < cfg.max_inflight && !queue.empty()) {
+    if (!stop && (int)inflight.size() < cfg.max_inflight && (!queue.empty() || !improve_q.empty())) {
       int sidx = -1;
       for (int k = 0; k < (int)streams.size(); ++k)
         if (!stream_busy[k]) { sidx = k; break; }
       Launch* L = new Launch;
-      if (sidx >= 0 && form_batch(L)) {
+      // new plans first; anytime improvement rounds fill the remaining capacity
+      bool formed = false;
+      if (sidx >= 0) {
+        if (!queue.empty()) formed = form_batch(L);
+        if (!formed && !improve_q.empty()) formed = form_improve(L);
+      }
+      if (formed) {
         L->stream = sidx;
         stream_busy[sidx] = true;
         cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
         ++stats.batches;
+        if (L->improve) ++stats.improve_batches;
         stats.max_batch_seen = std::max<int32_t>(stats.max_batch_seen, (int32_t)L->reqs.size());
         stats.sum_batch += L->reqs.size();
         lk.unlock();
@@ -408,13 +512,16 @@ void cpp_server::run() {
     }
     if (launched) continue;
     if (inflight.empty()) {
-      cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+      cv_work.wait(lk, [&] { return stop || !queue.empty() || !improve_q.empty(); });
     } else {
       lk.unlock();
       std::this_thread::sleep_for(std::chrono::microseconds(20));
       lk.lock();
     }
   }
+  // anytime requests between rounds finish with their best so far
+  for (Request* r : improve_q) finish(r);
+  improve_q.clear();
   // cancel what never ran
   for (Request* r : queue) {
     r->state = St::Cancelled;
@@ -522,10 +629,17 @@ cpp_status cpp_plan_submit(cpp_server_t* s, const cpp_plan_req_t* rq, uint64_t* 
     char msg[160];
     if (!make_geo(*rq->geometry, n, geo.data(), msg)) return sfail(CPP_ERR_INVALID_ARG, "%s", msg);
   }
+  const bool anytime = (rq->flags & CPP_REQ_ANYTIME) != 0;
+  if (anytime && (rq->anytime_rounds < 0 || rq->anytime_rounds > 100000))
+    return sfail(CPP_ERR_INVALID_ARG, "anytime_rounds outside [0, 100000]");
+  if (anytime && smooth_smem_bytes(T, n) > 227u * 1024u)
+    return sfail(CPP_ERR_INVALID_ARG, "anytime needs (n + 1) * T * 8 <= 227 KB");
   Request* r = new (std::nothrow) Request;
   if (!r) return sfail(CPP_ERR_OOM, "host allocation failed");
   r->robot = rb;
   r->geo = std::move(geo);
+  r->anytime = anytime;
+  r->rounds_left = anytime ? rq->anytime_rounds : 0;
   r->T = T; r->K = K; r->Kp = Kp; r->n = n;
   r->dev_bytes = L.total;
   r->o_cand = L.cand; r->o_tgt = L.tgt; r->o_out = L.out; r->o_ws = L.ws;
@@ -585,6 +699,7 @@ static cpp_status collect(cpp_server_t* s, Request* r, cpp_plan_result_t* res) {
     res->latency_ms =
         std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
     res->dev_status = r->dev_status;
+    res->rounds = r->have_best ? r->best_rounds : r->rounds_done;
     if (r->state == St::Done) {
       const char* o = r->h_out;
       if (res->sel) memcpy(res->sel, o + r->o_sel, (size_t)r->T * sizeof(int32_t));
@@ -607,8 +722,36 @@ cpp_status cpp_plan_poll(cpp_server_t* s, uint64_t ticket, cpp_plan_result_t* re
   if (it == s->reqs.end()) return sfail(CPP_ERR_NOT_FOUND, "unknown ticket %llu",
                                         (unsigned long long)ticket);
   Request* r = it->second;
-  if (r->state == St::Queued || r->state == St::Running) return CPP_PENDING;
+  if (r->state == St::Queued || r->state == St::Running || r->state == St::Improving)
+    return CPP_PENDING;
   return collect(s, r, res);
+}
+
+cpp_status cpp_plan_peek(cpp_server_t* s, uint64_t ticket, cpp_plan_result_t* res) {
+  if (!s) return sfail(CPP_ERR_INVALID_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return sfail(CPP_ERR_NOT_FOUND, "unknown ticket %llu",
+                                        (unsigned long long)ticket);
+  Request* r = it->second;
+  const char* o = nullptr;
+  if (r->have_best) o = r->best_out.data();
+  else if (r->state == St::Done) o = r->h_out;
+  else if (r->state == St::Failed || r->state == St::Cancelled) return r->result;
+  else return CPP_PENDING;
+  if (res) {
+    const bool done = r->state == St::Done || r->state == St::Failed || r->state == St::Cancelled;
+    res->latency_ms = std::chrono::duration<double, std::milli>(
+                          (done ? r->t_done : Clock::now()) - r->t_submit).count();
+    res->dev_status = r->dev_status;
+    res->rounds = r->have_best ? r->best_rounds : r->rounds_done;
+    if (res->sel) memcpy(res->sel, o + r->o_sel, (size_t)r->T * sizeof(int32_t));
+    if (res->q) memcpy(res->q, o + r->o_q, (size_t)r->T * r->n * sizeof(float));
+    if (res->pose_err) memcpy(res->pose_err, o + r->o_err, (size_t)r->T * 2 * sizeof(double));
+    if (res->report) memcpy(res->report, o + r->o_rep, sizeof(cpp_report_t));
+    if (res->best_cost) memcpy(res->best_cost, o + r->o_best, sizeof(float));
+  }
+  return r->have_best ? CPP_OK : r->result;
 }
 
 cpp_status cpp_plan_wait(cpp_server_t* s, uint64_t ticket, cpp_plan_result_t* res,
@@ -621,7 +764,8 @@ cpp_status cpp_plan_wait(cpp_server_t* s, uint64_t ticket, cpp_plan_result_t* re
     if (it == s->reqs.end()) return sfail(CPP_ERR_NOT_FOUND, "unknown ticket %llu",
                                           (unsigned long long)ticket);
     Request* r = it->second;
-    if (r->state != St::Queued && r->state != St::Running) return collect(s, r, res);
+    if (r->state != St::Queued && r->state != St::Running && r->state != St::Improving)
+      return collect(s, r, res);
     if (timeout_us >= 0 && Clock::now() >= deadline) return CPP_PENDING;
     if (timeout_us < 0) s->cv_done.wait(lk);
     else s->cv_done.wait_until(lk, deadline);
@@ -634,6 +778,18 @@ cpp_status cpp_plan_cancel(cpp_server_t* s, uint64_t ticket) {
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return sfail(CPP_ERR_NOT_FOUND, "unknown ticket");
   Request* r = it->second;
+  if (r->anytime && r->state == St::Improving) {  // between rounds: finish with the best
+    for (auto q = s->improve_q.begin(); q != s->improve_q.end(); ++q)
+      if (*q == r) { s->improve_q.erase(q); break; }
+    r->stop_improving = true;
+    s->finish(r);
+    s->cv_done.notify_all();
+    return CPP_OK;
+  }
+  if (r->anytime && r->state == St::Running) {  // stops after the launch in flight
+    r->stop_improving = true;
+    return CPP_OK;
+  }
   if (r->state != St::Queued) return CPP_PENDING;  // already on the device or finished
   for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
     if (*q == r) { s->queue.erase(q); break; }
