@@ -271,3 +271,72 @@ def test_large_batch_search_kernel_matches_oracle():
         ref = oracle.dp_f32(pb.cand, g.pen, pb.K)
         np.testing.assert_array_equal(keep[r]["sel"].cpu().numpy(), ref["sel"])
         assert float(keep[r]["best"].item()) == float(ref["best"])
+
+
+def test_dp_largest_supported_lattice():
+    """The largest Kp the generic search holds in shared memory at n = 7 (3616 nodes per
+    layer, K = 3600 with a ragged tail) against the oracle; one lane beyond is refused."""
+    T, K, n = 3, 3600, 7
+    rng = np.random.default_rng(11)
+    cand = rng.normal(0, 0.5, (T, n, 3616)).astype(np.float32)
+    pen = np.where(rng.uniform(size=(T, 3616)) < 0.1, np.float32(10), np.float32(0))
+    pen[:, K:] = np.inf
+    got = run_dp(cand, pen, K)
+    ref = oracle.dp_f32(cand, pen, K)
+    np.testing.assert_array_equal(got["sel"], ref["sel"])
+    assert got["best"] == ref["best"]
+    tt = torch()
+    too_big = 3648
+    ws = tt.empty(cppflow.dp_workspace_size(T, too_big), dtype=tt.uint8, device="cuda:0")
+    with pytest.raises(cppflow.CppflowError):
+        cppflow.dp_search(dev(np.zeros((T, n, too_big), np.float32)),
+                          dev(np.zeros((T, too_big), np.float32)), too_big, ws,
+                          tt.empty(T, dtype=tt.int32, device="cuda:0"),
+                          tt.empty(1, dtype=tt.float32, device="cuda:0"),
+                          tt.empty(T, n, dtype=tt.float32, device="cuda:0"))
+
+
+def test_full_size_batch_in_the_benchmark_configuration():
+    """24 requests of the T = 300, K = 512 workload in one batch -- too many for clusters,
+    so the search runs the one-CTA kernel with four successors per thread, as in the
+    benchmark. Three sampled requests equal the oracle's FP32 search bit for bit; every
+    request's backtracked path costs exactly its reported minimum and its plan is valid."""
+    tt = torch()
+    base = synth.SINGLE
+    ws_ = [synth.Workload(f"fs_{r}", base.n, base.T, base.K, base.sigma, base.p_wb, base.p_out,
+                          base.lm_iters, base.lambda0, arm_seed=100 + r % 8, path_seed=7000 + r,
+                          cand_seed=9000 + r) for r in range(24)]
+    pbs = [problems.build(w) for w in ws_]
+    _, cp = params_pair(lm_iters=base.lm_iters, lambda0=base.lambda0)
+    robots = [cppflow.robot_from_arm(pb.arm) for pb in pbs]
+    keep, descs = [], []
+    for r, pb in enumerate(pbs):
+        T, n, Kp = pb.cand.shape
+        b = dict(cand=dev(pb.cand), targets=dev(pb.targets),
+                 sel=tt.empty(T, dtype=tt.int32, device="cuda:0"),
+                 q=tt.empty(T, n, dtype=tt.float32, device="cuda:0"),
+                 err=tt.empty(T, 2, dtype=tt.float64, device="cuda:0"),
+                 rep=tt.zeros(cppflow.REPORT_BYTES, dtype=tt.uint8, device="cuda:0"),
+                 best=tt.empty(1, dtype=tt.float32, device="cuda:0"))
+        keep.append(b)
+        descs.append(cppflow.PlanDesc(T, pb.K, Kp, r, b["cand"].data_ptr(), b["targets"].data_ptr(),
+                                      b["sel"].data_ptr(), b["q"].data_ptr(), b["err"].data_ptr(),
+                                      b["rep"].data_ptr(), b["best"].data_ptr()))
+    ws = tt.empty(cppflow.plan_batch_workspace_size(descs, robots), dtype=tt.uint8, device="cuda:0")
+    st = tt.zeros(len(descs), dtype=tt.int32, device="cuda:0")
+    batch = cppflow.Batch(robots, cp, descs, ws, st)
+    assert batch.launches(cppflow.STAGE_DP_FORWARD) == 1      # one launch, no split
+    batch.run(cppflow.STAGE_ALL)
+    tt.cuda.synchronize()
+    assert np.all(st.cpu().numpy() == 0)
+    for r, pb in enumerate(pbs):
+        sel = keep[r]["sel"].cpu().numpy()
+        best = float(keep[r]["best"].item())
+        g = run_mask(robots[r], cp, pb.cand, pb.targets, pb.K)
+        assert float(path_cost_f32(pb.cand, g.pen, pb.K, sel)) == best
+        rep = cppflow.report_from_bytes(keep[r]["rep"].cpu().numpy().tobytes())
+        assert rep["valid"] == 1, (r, rep)
+        if r in (0, 11, 23):
+            ref = oracle.dp_f32(pb.cand, g.pen, pb.K)
+            np.testing.assert_array_equal(sel, ref["sel"])
+            assert best == float(ref["best"])
