@@ -223,13 +223,16 @@ int device_sm_count() {
 }
 
 // Successor candidates per CTA of the cluster form: cpc (64 or 128) or the
-// default (64 up to Kp = 512, 128 above), as long as the cluster has 2..8 CTAs.
+// default (64 up to Kp = 512, 128 above), as long as the cluster has 2..8 CTAs,
+// or up to 16 (a non-portable cluster size, opted into at launch) when 64 per
+// CTA is asked for explicitly.
 int cluster_succ(int Kp, int cpc) {
   if (Kp <= 64 || Kp > 1024) return 0;
   const int S = cpc ? cpc : (Kp <= 512 ? 64 : 128);
   if (S != 64 && S != 128) return 0;
   const int CS = (Kp + S - 1) / S;
-  return CS >= 2 && CS <= 8 ? S : 0;
+  const int max_cs = (cpc == 64) ? 16 : 8;
+  return CS >= 2 && CS <= max_cs ? S : 0;
 }
 
 int cluster_size(int Kp, int cpc) {

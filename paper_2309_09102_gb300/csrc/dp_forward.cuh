@@ -529,6 +529,11 @@ static cudaError_t launch_fwdc_r(const Src& s, int nreq, int max_Kp, cudaStream_
   const size_t smem = dpc_smem_bytes(NJ, max_Kp, R);
   cudaError_t e = allow_smem(dpc_forward_kernel<NJ, R, OBJ, Src>, smem);
   if (e != cudaSuccess) return e;
+  if (CS > 8) {  // 9..16 CTAs: a non-portable cluster size
+    e = cudaFuncSetAttribute(dpc_forward_kernel<NJ, R, OBJ, Src>,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nreq * CS));
   cfg.blockDim = dim3(kDpcThreads);
@@ -556,9 +561,48 @@ static int sm_count() {
   return n;
 }
 
+// Whether 16-CTA clusters of this kernel (64 successors per CTA at Kp = 1024) can
+// be resident on this device (asked once).
+template <int NJ, int OBJ, class Src>
+static bool cluster16_ok() {
+  static const bool ok = [] {
+    auto kernel = dpc_forward_kernel<NJ, 2, OBJ, Src>;
+    const size_t smem = dpc_smem_bytes(NJ, 1024, 2);
+    if (allow_smem(kernel, smem) != cudaSuccess) return false;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(kDpcThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return clusters > 0;
+  }();
+  return ok;
+}
+
 template <int NJ, int OBJ, class Src>
 static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, int form, int cpc,
                                  cudaStream_t st) {
+  // the latency form of a few requests with Kp > 512 takes 16-CTA clusters (64
+  // successors per CTA) when one wave of them covers the requests
+  if (cpc == 0 && form == kFormAuto && max_Kp > 512 &&
+      nreq * cluster_size(max_Kp, 64) <= sm_count() && cluster16_ok<NJ, OBJ, Src>())
+    cpc = 64;
   const int S = cluster_succ(max_Kp, cpc), CS = cluster_size(max_Kp, cpc);
   if (S > 0 && form != kFormCta && (form == kFormCluster || nreq * CS <= sm_count()))
     return S == 64 ? launch_fwdc_r<NJ, 2, OBJ>(s, nreq, max_Kp, st)
