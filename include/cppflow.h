@@ -441,13 +441,14 @@ void cpp_batch_destroy(cpp_batch_t* batch);
  * covers the whole batch). cpp_batch_create applies alpha = 2.
  *
  * The cluster form gives each CTA cands_per_cta successor candidates of a
- * waypoint (64 or 128; 0 = 64 up to Kp = 512 and 128 above, as long as the
- * cluster has 2..8 CTAs; an explicit 64 also allows the non-portable sizes of
- * 9..16 CTAs, up to Kp = 1024): 64 halves a long request's latency, 128 halves
- * the per-step cluster traffic and barriers per candidate. The automatic form
- * (alpha = 0, single-request calls, the server) takes 16-CTA clusters for a few
- * requests with Kp > 512 when one wave of them covers the requests and the
- * device can hold such clusters.
+ * waypoint (32, 64 or 128; 0 = 64 up to Kp = 512 and 128 above, as long as the
+ * cluster has 2..8 CTAs; an explicit 32 or 64 also allows the non-portable sizes
+ * of 9..16 CTAs): fewer per CTA shorten a long request's latency, more halve the
+ * per-step cluster traffic and barriers per candidate. The automatic form
+ * (alpha = 0, single-request calls, the server) takes 16-CTA clusters of 64 for
+ * a few requests with Kp > 512 when one wave of them covers the requests, and
+ * 32 per CTA for a lone request with 128 < Kp <= 512, when the device can hold
+ * such clusters.
  *
  * cpp_batch_set_split sets alpha (>= 0) and cands_per_cta and uploads the new
  * schedule on `stream`. cpp_batch_tune picks both by measurement on the batch

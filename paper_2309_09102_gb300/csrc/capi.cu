@@ -874,8 +874,8 @@ cpp_status cpp_batch_set_split(cpp_batch_t* b, double alpha, int32_t cands_per_c
                                cpp_stream_t stream) {
   if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
   if (!std::isfinite(alpha) || alpha < 0) return fail(CPP_ERR_INVALID_ARG, "alpha must be >= 0");
-  if (cands_per_cta != 0 && cands_per_cta != 64 && cands_per_cta != 128)
-    return fail(CPP_ERR_INVALID_ARG, "cands_per_cta must be 0, 64 or 128");
+  if (cands_per_cta != 0 && cands_per_cta != 32 && cands_per_cta != 64 && cands_per_cta != 128)
+    return fail(CPP_ERR_INVALID_ARG, "cands_per_cta must be 0, 32, 64 or 128");
   return set_schedule(b, alpha, cands_per_cta, (cudaStream_t)stream);
 }
 

@@ -229,9 +229,9 @@ int device_sm_count() {
 int cluster_succ(int Kp, int cpc) {
   if (Kp <= 64 || Kp > 1024) return 0;
   const int S = cpc ? cpc : (Kp <= 512 ? 64 : 128);
-  if (S != 64 && S != 128) return 0;
+  if (S != 32 && S != 64 && S != 128) return 0;
   const int CS = (Kp + S - 1) / S;
-  const int max_cs = (cpc == 64) ? 16 : 8;
+  const int max_cs = (cpc == 64 || cpc == 32) ? 16 : 8;
   return CS >= 2 && CS <= max_cs ? S : 0;
 }
 

@@ -599,13 +599,18 @@ template <int NJ, int OBJ, class Src>
 static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, int form, int cpc,
                                  cudaStream_t st) {
   // the latency form of a few requests with Kp > 512 takes 16-CTA clusters (64
-  // successors per CTA) when one wave of them covers the requests
+  // successors per CTA) when one wave of them covers the requests; a lone request
+  // with 128 < Kp <= 512 takes 32 successors per CTA (up to 16 CTAs)
   if (cpc == 0 && form == kFormAuto && max_Kp > 512 &&
       nreq * cluster_size(max_Kp, 64) <= sm_count() && cluster16_ok<NJ, OBJ, Src>())
     cpc = 64;
+  else if (cpc == 0 && form == kFormAuto && nreq == 1 && max_Kp > 128 && max_Kp <= 512 &&
+           cluster16_ok<NJ, OBJ, Src>())
+    cpc = 32;
   const int S = cluster_succ(max_Kp, cpc), CS = cluster_size(max_Kp, cpc);
   if (S > 0 && form != kFormCta && (form == kFormCluster || nreq * CS <= sm_count()))
-    return S == 64 ? launch_fwdc_r<NJ, 2, OBJ>(s, nreq, max_Kp, st)
+    return S == 32 ? launch_fwdc_r<NJ, 1, OBJ>(s, nreq, max_Kp, st)
+         : S == 64 ? launch_fwdc_r<NJ, 2, OBJ>(s, nreq, max_Kp, st)
                    : launch_fwdc_r<NJ, 4, OBJ>(s, nreq, max_Kp, st);
   const int R = (max_Kp + kDp3Group - 1) / kDp3Group;
   if (R <= 1) return launch_fwd3_r<NJ, 1, OBJ>(s, nreq, max_Kp, st);
