@@ -445,10 +445,9 @@ void cpp_batch_destroy(cpp_batch_t* batch);
  * cluster has 2..8 CTAs; an explicit 32 or 64 also allows the non-portable sizes
  * of 9..16 CTAs): fewer per CTA shorten a long request's latency, more halve the
  * per-step cluster traffic and barriers per candidate. The automatic form
- * (alpha = 0, single-request calls, the server) takes 16-CTA clusters of 64 for
- * a few requests with Kp > 512 when one wave of them covers the requests, and
- * 32 per CTA for a lone request with 128 < Kp <= 512, when the device can hold
- * such clusters.
+ * (alpha = 0, single-request calls, the server) takes the smallest tile (32 per
+ * CTA up to Kp = 512, 64 above, clusters of up to 16 CTAs) when the device holds
+ * all the requests' clusters at once with one CTA per SM.
  *
  * cpp_batch_set_split sets alpha (>= 0) and cands_per_cta and uploads the new
  * schedule on `stream`. cpp_batch_tune picks both by measurement on the batch

@@ -4,6 +4,8 @@
 // for one objective each.
 #pragma once
 
+#include <atomic>
+
 #include "internal.h"
 
 namespace cppflow {
@@ -302,12 +304,13 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __gri
 // One request alone (the plain per-request path, or a batch too small to fill
 // the GPU) would leave most SMs idle with one CTA per request, and its T
 // dependent steps would each run on a single SM. This form spreads one request
-// over a thread-block cluster of CS CTAs (CS = ceil(Kp / 32R) <= 8):
+// over a thread-block cluster of CS CTAs (CS = ceil(Kp / 32R) <= 16):
 //  * CTA c owns successors [32 R c, 32 R (c + 1)); its 8 warps split the
-//    predecessors into 8 contiguous ranges and keep an exact argmin per edge
-//    (strict '<' in index order);
-//  * the 8 partial (minimum, index) pairs merge in warp order, the lower range
-//    winning ties, so the lowest index wins;
+//    predecessor tiles into 8 contiguous ranges and keep the running minimum
+//    per 16-node tile and the first tile that lowered it, as the one-CTA form;
+//  * the 8 partial (minimum, tile) pairs merge in warp order, the lower range
+//    winning ties, and the 8 warps re-evaluate 2 nodes each of the winning
+//    tile for the lowest index attaining the minimum;
 //  * each new record [-q', C'] is stored into the record buffer of every CTA of
 //    the cluster (distributed shared memory), and a release/acquire cluster
 //    barrier ends the step. Records are double-buffered: a CTA that starts step
@@ -315,10 +318,11 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __gri
 //    of step i.
 constexpr int kDpcThreads = 256;
 constexpr int kDpcWarps = kDpcThreads / 32;
+static_assert(kDp2Tile == 2 * kDpcWarps, "the rescan gives each warp 2 nodes of a tile");
 
 inline size_t dpc_smem_bytes(int nj, int Kp, int R) {
   const int NW = ((nj + 1 + 3) / 4) * 4;
-  return (size_t)2 * Kp * NW * 4 + (size_t)2 * kDpcWarps * 32 * R * 4;
+  return (size_t)2 * rec_layer_floats(NW, Kp) * 4 + (size_t)3 * kDpcWarps * 32 * R * 4;
 }
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -350,9 +354,11 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
   const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   extern __shared__ __align__(16) float smc[];
-  float* const recb = smc;                               // [2][Kp][NW]
-  float* const xmin = recb + 2 * (size_t)Kp * NW;        // [warps][S]
-  int* const xarg = reinterpret_cast<int*>(xmin + kDpcWarps * S);
+  const int RL = rec_layer_floats(NW, Kp);
+  float* const recb = smc;                               // [2][RL] records (skewed)
+  float* const xmin = recb + 2 * (size_t)RL;             // [warps][S]
+  int* const xtile = reinterpret_cast<int*>(xmin + kDpcWarps * S);
+  int* const xarg = xtile + kDpcWarps * S;
   const float* __restrict__ cand = rq.cand;
 
   // layer 0: every CTA builds all records locally
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       v[NJ] = k < K ? rq.pen[k] - m0 : CUDART_INF_F;
 #pragma unroll
       for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
-      float4* dst = reinterpret_cast<float4*>(recb + (size_t)k * NW);
+      float4* dst = reinterpret_cast<float4*>(recb + rec_off(NW, k));
 #pragma unroll
       for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
     }
@@ -384,15 +390,15 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
   };
   if (T > 1) load_own(1);
   const int K4 = (K + 3) & ~3;
-  const int chunk = ((K4 + 2 * kDpcWarps - 1) / (2 * kDpcWarps)) * 2;
-  const int kb = min(warp * chunk, K4), ke = min(kb + chunk, K4);
+  const int ntiles = (K4 + kDp2Tile - 1) / kDp2Tile;
+  const int t_lo = warp * ntiles / kDpcWarps, t_hi = (warp + 1) * ntiles / kDpcWarps;
   __syncthreads();
   cluster_barrier();
 
   for (int i = 0; i + 1 < T; ++i) {
     const int L = i + 1;
-    const float* cur = recb + (size_t)(i & 1) * Kp * NW;
-    float* nxt = recb + (size_t)(L & 1) * Kp * NW;
+    const float* cur = recb + (size_t)(i & 1) * RL;
+    float* nxt = recb + (size_t)(L & 1) * RL;
     uint64_t own[R][NP];
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -407,36 +413,78 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
     if (L + 1 < T) load_own(L + 1);  // prefetch, consumed next step
 
     float best[R];
-    int arg[R];
+    int btile[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; arg[r] = 0; }
-    for (int k = kb; k < ke; k += 2) {
-      float r0[NW], r1[NW];
-      load_rec<NW>(cur + (size_t)k * NW, r0);
-      load_rec<NW>(cur + (size_t)(k + 1) * NW, r1);
+    for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; btile[r] = -1; }
+#pragma unroll 1
+    for (int t = t_lo; t < t_hi; ++t) {
+      const int kb = t * kDp2Tile;
+      const float* base = cur + rec_off(NW, kb);
+      float tb[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float v0 = comb<OBJ>(r0[NJ], linf_rec<NJ>(own[r], r0));
-        const float v1 = comb<OBJ>(r1[NJ], linf_rec<NJ>(own[r], r1));
-        if (v0 < best[r]) { best[r] = v0; arg[r] = k; }
-        if (v1 < best[r]) { best[r] = v1; arg[r] = k + 1; }
+      for (int r = 0; r < R; ++r) tb[r] = CUDART_INF_F;
+      if (kb + kDp2Tile <= K4) {
+#pragma unroll
+        for (int k = 0; k < kDp2Tile; k += 2) {
+          float r0[NW], r1[NW];
+          load_rec<NW>(base + k * NW, r0);
+          load_rec<NW>(base + (k + 1) * NW, r1);
+          sweep_pair<NJ, R, OBJ>(own, r0, r1, tb);
+        }
+      } else {
+        for (int k = 0; kb + k < K4; k += 2) {
+          float r0[NW], r1[NW];
+          load_rec<NW>(base + k * NW, r0);
+          load_rec<NW>(base + (k + 1) * NW, r1);
+          sweep_pair<NJ, R, OBJ>(own, r0, r1, tb);
+        }
       }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (tb[r] < best[r]) { best[r] = tb[r]; btile[r] = t; }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       xmin[warp * S + lane + 32 * r] = best[r];
-      xarg[warp * S + lane + 32 * r] = arg[r];
+      xtile[warp * S + lane + 32 * r] = btile[r];
     }
     __syncthreads();
-    // slot (warp r, lane): merge the 8 ranges in order, write the record everywhere
+    // every warp merges the 8 ranges of its lane's slots in order (the same
+    // result in all warps) and re-evaluates 2 records of the winning tile:
+    // warp w takes nodes 2w, 2w + 1 of it, so the lowest match is the first
+    // one in warp order
+    float bvr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int slot = lane + 32 * r;
+      float bv = xmin[slot];
+      int bt = xtile[slot];
+      for (int w = 1; w < kDpcWarps; ++w)
+        if (xmin[w * S + slot] < bv) { bv = xmin[w * S + slot]; bt = xtile[w * S + slot]; }
+      bvr[r] = bv;
+      int found = 0x7fffffff;
+      const int k0 = bt * kDp2Tile + 2 * warp;
+      if (bt >= 0 && k0 < K4) {
+        const float* r0 = cur + rec_off(NW, k0);
+        if (comb<OBJ>(r0[NJ], linf_rec<NJ>(own[r], r0)) == bv) {
+          found = k0;
+        } else {
+          const float* r1 = r0 + NW;  // k0 + 1 is in the same tile
+          if (comb<OBJ>(r1[NJ], linf_rec<NJ>(own[r], r1)) == bv) found = k0 + 1;
+        }
+      }
+      xarg[warp * S + slot] = found;
+    }
+    __syncthreads();
+    // slot (warp r, lane): the lowest match, the record written everywhere
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (warp != r || kp[r] >= Kp) continue;
       const int slot = lane + 32 * r;
-      float bv = xmin[slot];
+      const float bv = bvr[r];
       int ba = xarg[slot];
-      for (int w = 1; w < kDpcWarps; ++w)
-        if (xmin[w * S + slot] < bv) { bv = xmin[w * S + slot]; ba = xarg[w * S + slot]; }
+      for (int w = 1; w < kDpcWarps; ++w) ba = min(ba, xarg[w * S + slot]);
+      if (ba == 0x7fffffff) ba = 0;
       float v[NW];
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
@@ -448,7 +496,7 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       v[NJ] = kp[r] < K ? comb<OBJ>(bv, rpen[r]) : CUDART_INF_F;
 #pragma unroll
       for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
-      const uint32_t base = smem_u32(nxt + (size_t)kp[r] * NW);
+      const uint32_t base = smem_u32(nxt + rec_off(NW, kp[r]));
       for (int c = 0; c < CS; ++c) {
         const uint32_t peer = map_peer(base, (uint32_t)c);
 #pragma unroll
@@ -459,9 +507,9 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
     }
     cluster_barrier();
   }
-  const float* fin = recb + (size_t)((T - 1) & 1) * Kp * NW;
+  const float* fin = recb + (size_t)((T - 1) & 1) * RL;
   for (int k = (int)crank * S + tid; k < min(Kp, ((int)crank + 1) * S); k += kDpcThreads)
-    rq.costT[k] = fin[(size_t)k * NW + NJ];
+    rq.costT[k] = fin[rec_off(NW, k) + NJ];
 }
 
 // Any n and Kp that fit in shared memory: successor values are read back from
@@ -595,18 +643,53 @@ static bool cluster16_ok() {
   return ok;
 }
 
+// How many clusters of cs CTAs (32 R successors each) the device holds at once
+// with one CTA per SM: a cluster lives inside one GPC, so past that count
+// clusters share SMs and a step of the latency form slows down (asked once per
+// size; 0 if none).
+template <int NJ, int R, int OBJ, class Src>
+static int spread_clusters(int cs) {
+  static std::atomic<int> cache[17];  // value + 1; 0 = not asked yet
+  if (cs < 2 || cs > 16) return 0;
+  if (const int v = cache[cs].load(std::memory_order_relaxed)) return v - 1;
+  auto kernel = dpc_forward_kernel<NJ, R, OBJ, Src>;
+  constexpr size_t kOnePerSm = 120u * 1024u;  // more than half an SM's shared memory
+  int clusters = 0;
+  if (allow_smem(kernel, kOnePerSm) == cudaSuccess &&
+      (cs <= 8 ||
+       cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+           cudaSuccess)) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cs);
+    cfg.blockDim = dim3(kDpcThreads);
+    cfg.dynamicSmemBytes = kOnePerSm;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) != cudaSuccess) clusters = 0;
+  }
+  cudaGetLastError();
+  cache[cs].store(clusters + 1, std::memory_order_relaxed);
+  return clusters;
+}
+
 template <int NJ, int OBJ, class Src>
 static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, int form, int cpc,
                                  cudaStream_t st) {
-  // the latency form of a few requests with Kp > 512 takes 16-CTA clusters (64
-  // successors per CTA) when one wave of them covers the requests; a lone request
-  // with 128 < Kp <= 512 takes 32 successors per CTA (up to 16 CTAs)
-  if (cpc == 0 && form == kFormAuto && max_Kp > 512 &&
-      nreq * cluster_size(max_Kp, 64) <= sm_count() && cluster16_ok<NJ, OBJ, Src>())
-    cpc = 64;
-  else if (cpc == 0 && form == kFormAuto && nreq == 1 && max_Kp > 128 && max_Kp <= 512 &&
-           cluster16_ok<NJ, OBJ, Src>())
-    cpc = 32;
+  // the latency form takes the smallest tile (32 successors per CTA up to Kp =
+  // 512, 64 above; clusters of up to 16 CTAs) when the device holds all the
+  // requests' clusters at once with one CTA per SM
+  if (cpc == 0 && form == kFormAuto && cluster16_ok<NJ, OBJ, Src>()) {
+    if (max_Kp <= 512 && cluster_size(max_Kp, 32) > 0 &&
+        nreq <= spread_clusters<NJ, 1, OBJ, Src>(cluster_size(max_Kp, 32)))
+      cpc = 32;
+    else if (max_Kp > 512 && nreq <= spread_clusters<NJ, 2, OBJ, Src>(cluster_size(max_Kp, 64)))
+      cpc = 64;
+  }
   const int S = cluster_succ(max_Kp, cpc), CS = cluster_size(max_Kp, cpc);
   if (S > 0 && form != kFormCta && (form == kFormCluster || nreq * CS <= sm_count()))
     return S == 32 ? launch_fwdc_r<NJ, 1, OBJ>(s, nreq, max_Kp, st)
