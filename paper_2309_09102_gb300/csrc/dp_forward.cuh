@@ -344,6 +344,12 @@ __device__ __forceinline__ void cluster_barrier() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n"
                "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 template <int NJ, int R, int OBJ, class Src>
 __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_constant__ Src src,
@@ -379,14 +385,17 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
   int kp[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) kp[r] = (int)crank * S + lane + 32 * r;
-  float qn[R][NJ];  // own successor values of the next layer
+  float qn[R][NJ];  // own successor values and node costs of the next layer
+  float pn[R], mn = 0.f;
   auto load_own = [&](int L) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int k = kp[r] < Kp ? kp[r] : Kp - 1;
 #pragma unroll
       for (int j = 0; j < NJ; ++j) qn[r][j] = __ldg(cand + ((size_t)L * NJ + j) * Kp + k);
+      pn[r] = __ldg(rq.pen + (size_t)L * Kp + k);
     }
+    mn = __ldg(rq.pen_min + L);
   };
   if (T > 1) load_own(1);
   const int K4 = (K + 3) & ~3;
@@ -406,10 +415,8 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       for (int p = 0; p < NP; ++p)
         own[r][p] = pack2(qn[r][2 * p], (2 * p + 1 < NJ) ? qn[r][2 * p + 1] : 0.f);
     float rpen[R];
-    const float m1 = rq.pen_min[L];
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-      rpen[r] = kp[r] < K ? __ldg(rq.pen + (size_t)L * Kp + kp[r]) - m1 : CUDART_INF_F;
+    for (int r = 0; r < R; ++r) rpen[r] = kp[r] < K ? pn[r] - mn : CUDART_INF_F;
     if (L + 1 < T) load_own(L + 1);  // prefetch, consumed next step
 
     float best[R];
@@ -476,15 +483,18 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       xarg[warp * S + slot] = found;
     }
     __syncthreads();
-    // slot (warp r, lane): the lowest match, the record written everywhere
+    // every warp takes the lowest match of its lane's slots and writes the new
+    // records into the CTAs c = warp, warp + 8 of the cluster; the backpointers
+    // go to global memory between the arrival at the cluster barrier and the
+    // wait, outside the release
+    int bsel[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      if (warp != r || kp[r] >= Kp) continue;
       const int slot = lane + 32 * r;
-      const float bv = bvr[r];
       int ba = xarg[slot];
       for (int w = 1; w < kDpcWarps; ++w) ba = min(ba, xarg[w * S + slot]);
-      if (ba == 0x7fffffff) ba = 0;
+      bsel[r] = ba == 0x7fffffff ? 0 : ba;
+      if (kp[r] >= Kp) continue;
       float v[NW];
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
@@ -493,19 +503,22 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
         v[2 * p] = -a;
         if (2 * p + 1 < NJ) v[2 * p + 1] = -b;
       }
-      v[NJ] = kp[r] < K ? comb<OBJ>(bv, rpen[r]) : CUDART_INF_F;
+      v[NJ] = kp[r] < K ? comb<OBJ>(bvr[r], rpen[r]) : CUDART_INF_F;
 #pragma unroll
       for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
       const uint32_t base = smem_u32(nxt + rec_off(NW, kp[r]));
-      for (int c = 0; c < CS; ++c) {
+      for (int c = warp; c < CS; c += kDpcWarps) {
         const uint32_t peer = map_peer(base, (uint32_t)c);
 #pragma unroll
         for (int w = 0; w < NW / 4; ++w)
           st_peer_v4(peer + 16 * w, make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]));
       }
-      rq.bp[(size_t)L * Kb + kp[r]] = (uint16_t)ba;
     }
-    cluster_barrier();
+    cluster_arrive();
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (warp == (r & (kDpcWarps - 1)) && kp[r] < Kp) rq.bp[(size_t)L * Kb + kp[r]] = (uint16_t)bsel[r];
+    cluster_wait();
   }
   const float* fin = recb + (size_t)((T - 1) & 1) * RL;
   for (int k = (int)crank * S + tid; k < min(Kp, ((int)crank + 1) * S); k += kDpcThreads)
