@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
     pt[0] = (F)t7[0]; pt[1] = (F)t7[1]; pt[2] = (F)t7[2];
   }
   double q[MJ];
-#pragma unroll
   const float* q_src = a.from_out ? rq.q_out : rq.q_in;
+#pragma unroll
   for (int j = 0; j < MJ; ++j) q[j] = (NJ || j < n) ? (double)q_src[(size_t)i * n + j] : 0.0;
 
   F e[6];
@@ -418,18 +418,23 @@ size_t smooth_smem_bytes(int T, int n) { return (size_t)T * (n + 1) * sizeof(dou
 // skipped. Each row touches one waypoint, so it adds g g^T to that waypoint's
 // diagonal block and g r to its right-hand side: the normal equations stay block tridiagonal, now with
 // full n x n diagonal blocks D_i = (c_i + lambda_d) I + G_i and -I beside them.
-// One warp per request:
-//   phase 1, lanes over waypoints: the FP64 gate (every waypoint within tau),
+// One block of 4 warps per request:
+//   phase 1, threads over waypoints: the FP64 gate (every waypoint within tau),
 //     FP32 FK with frames and capsules, the rows, G_i and J^T r in FP64 to scratch;
-//   phase 2, the block Thomas recursion over T in FP64:
+//   phase 2, warp 0, the block Thomas recursion over T in FP64:
 //     S_0 = D_0, S_i = D_i - S_{i-1}^{-1};  y_0 = b_0, y_i = b_i + S_{i-1}^{-1} y_{i-1}
-//     (lane 0 factors S_i by Cholesky, lanes c < n form column c of S_i^{-1}),
-//     then x_{T-1} = S^{-1} y, x_i = S_i^{-1} (y_i + x_{i+1}) (lane c: component c),
-//     q' = clamp(q + x) in FP32.
+//     (S_i^{-1} by Gauss-Jordan elimination without pivoting, which is stable for
+//     a symmetric positive definite S_i and has its pivots positive; the lanes
+//     share the n^2 entries, so a pivot costs one reciprocal and one update per
+//     entry on the serial path), then x_{T-1} = S^{-1} y,
+//     x_i = S_i^{-1} (y_i + x_{i+1}) (lane c: component c), q' = clamp(q + x) in FP32.
+//     The blocks of step i + 1 are loaded during step i.
 constexpr float kMinDir = 1e-6f;  // m: closest points nearer than this give no direction
+constexpr int kSmoothGeoThreads = 128;
+constexpr int kGjPerLane = (kMaxJ * kMaxJ + 31) / 32;  // matrix entries per lane
 
 template <class Src>
-__global__ void __launch_bounds__(32) smooth_geo_kernel(const __grid_constant__ Src src,
+__global__ void __launch_bounds__(kSmoothGeoThreads) smooth_geo_kernel(const __grid_constant__ Src src,
                                                          const SmoothArgs a) {
   const Req& rq = src.req(blockIdx.x);
   const GeoF* gsrc = src.geom(rq);
@@ -437,24 +442,23 @@ __global__ void __launch_bounds__(32) smooth_geo_kernel(const __grid_constant__ 
   __shared__ RobotF rf;
   __shared__ RobotD rd;
   __shared__ GeoF g;
-  __shared__ double S[kMaxJ * kMaxJ], Lc[kMaxJ * kMaxJ], Wp[kMaxJ * kMaxJ], il[kMaxJ];
+  __shared__ double Sb[2][kMaxJ * kMaxJ];  // S_i, inverted in place; S_{i-1}^{-1}
   __shared__ double yb[2][kMaxJ], xs[kMaxJ];
-  __shared__ int chol_fail;
   stage_robot(src.rob(rq.robot), 0.0, &rf, &rd);
   {
     const uint32_t* from = reinterpret_cast<const uint32_t*>(gsrc);
     uint32_t* to = reinterpret_cast<uint32_t*>(&g);
-    for (int w = threadIdx.x; w < (int)(sizeof(GeoF) / 4); w += 32) to[w] = from[w];
+    for (int w = threadIdx.x; w < (int)(sizeof(GeoF) / 4); w += kSmoothGeoThreads) to[w] = from[w];
   }
   __syncthreads();
-  const int n = rd.n, T = rq.T, lane = threadIdx.x, NP = n * (n + 1) / 2;
+  const int n = rd.n, T = rq.T, tid = threadIdx.x, lane = tid & 31, NP = n * (n + 1) / 2;
   double* Gh = rq.smooth_ws;                       // [T][NP + n]
   double* Wg = Gh + (size_t)T * (NP + n);          // [T][n * n]
   double* Yg = Wg + (size_t)T * n * n;             // [T][n]
   const float margin = (float)a.coll_margin, wt = (float)a.coll_weight;
 
   bool ok = true, any_rows = false;
-  for (int i = lane; i < T; i += 32) {
+  for (int i = tid; i < T; i += kSmoothGeoThreads) {
     double qd[kMaxJ], R[9], p[3], Rt[9];
     float qf[kMaxJ];
     for (int j = 0; j < n; ++j) { qf[j] = rq.q_out[(size_t)i * n + j]; qd[j] = (double)qf[j]; }
@@ -552,87 +556,118 @@ __global__ void __launch_bounds__(32) smooth_geo_kernel(const __grid_constant__ 
     for (int k = 0; k < NP; ++k) dst[k] = G[k];
     for (int k = 0; k < n; ++k) dst[NP + k] = h[k];
   }
-  if (!__all_sync(0xffffffffu, ok) || T < 2) return;
-  if (!__any_sync(0xffffffffu, any_rows)) {  // no active row: the scalar-identity step
-    __syncwarp();
+  ok = __syncthreads_and(ok);
+  any_rows = __syncthreads_or(any_rows);  // also orders the scratch stores before phase 2
+  if (!ok || T < 2 || tid >= 32) return;
+  if (!any_rows) {  // no active row: the scalar-identity step
     scalar_thomas(rq, rd, a.lambda_d, Wg, Wg + T, lane);
     return;
   }
-  if (lane == 0) chol_fail = 0;
-  __syncwarp();
 
   const float* qc = rq.q_out;
-  for (int i = 0; i < T; ++i) {
+  const int nn = n * n;
+  // lane's entries e = lane + 32 m of an n x n block, and the packed index of G
+  int gidx[kGjPerLane];
+#pragma unroll
+  for (int m = 0; m < kGjPerLane; ++m) {
+    const int e = lane + 32 * m, r = e / n, c = e - (e / n) * n;
+    const int hi = r > c ? r : c, lo = r > c ? c : r;
+    gidx[m] = e < nn ? hi * (hi + 1) / 2 + lo : 0;
+  }
+  double gn[kGjPerLane], hn = 0.0, qm = 0.0, q0 = 0.0, q1 = 0.0;  // step i + 1's inputs
+  auto load_step = [&](int i) {
     const double* Gi = Gh + (size_t)i * (NP + n);
+#pragma unroll
+    for (int m = 0; m < kGjPerLane; ++m) gn[m] = lane + 32 * m < nn ? Gi[gidx[m]] : 0.0;
+    if (lane < n) {
+      hn = Gi[NP + lane];
+      q0 = (double)qc[(size_t)i * n + lane];
+      qm = i > 0 ? (double)qc[(size_t)(i - 1) * n + lane] : 0.0;
+      q1 = i + 1 < T ? (double)qc[(size_t)(i + 1) * n + lane] : 0.0;
+    }
+  };
+  load_step(0);
+  for (int i = 0; i < T; ++i) {
+    double* S = Sb[i & 1];
+    const double* Wp = Sb[(i + 1) & 1];
     const double* yprev = yb[(i + 1) & 1];
     double* ycur = yb[i & 1];
+    const double diag = (i > 0 ? 1.0 : 0.0) + (i + 1 < T ? 1.0 : 0.0) + a.lambda_d;
+#pragma unroll
+    for (int m = 0; m < kGjPerLane; ++m) {
+      const int e = lane + 32 * m;
+      if (e >= nn) break;
+      double v = gn[m] + (e % (n + 1) == 0 ? diag : 0.0);
+      if (i > 0) v -= Wp[e];
+      S[e] = v;
+    }
     if (lane < n) {
       const int c = lane;
-      const double diag = (i > 0 ? 1.0 : 0.0) + (i + 1 < T ? 1.0 : 0.0) + a.lambda_d;
-      for (int r = 0; r < n; ++r) {
-        const int hi = r > c ? r : c, lo = r > c ? c : r;
-        double v = Gi[hi * (hi + 1) / 2 + lo] + (r == c ? diag : 0.0);
-        if (i > 0) v -= Wp[r * n + c];
-        S[r * n + c] = v;
-      }
-      const double qi = (double)qc[(size_t)i * n + c];
-      double b = -Gi[NP + c];
-      if (i + 1 < T) b += (double)qc[(size_t)(i + 1) * n + c] - qi;
-      if (i > 0) b -= qi - (double)qc[(size_t)(i - 1) * n + c];
+      double b = -hn;
+      if (i + 1 < T) b += q1 - q0;
+      if (i > 0) b -= q0 - qm;
       if (i > 0)
         for (int k = 0; k < n; ++k) b += Wp[c * n + k] * yprev[k];
       ycur[c] = b;
     }
+    if (i + 1 < T) load_step(i + 1);
     __syncwarp();
-    // Cholesky S = L L^T by columns: lane 0 the pivot and its reciprocal, lanes
-    // r > j the rest of column j (one division per pivot)
+    // S <- S^{-1}: pivot j scales row j by 1/p, column j by -1/p, and takes
+    // S[r][j] S[j][c] / p from the other entries
     for (int j = 0; j < n; ++j) {
-      if (lane == 0) {
-        double v = S[j * n + j];
-        for (int k = 0; k < j; ++k) v -= Lc[j * n + k] * Lc[j * n + k];
-        if (!(v > 0.0)) chol_fail = 1;
-        const double l = sqrt(v);
-        Lc[j * n + j] = l;
-        il[j] = 1.0 / l;
+      const double pv = S[j * n + j];
+      if (!(pv > 0.0)) return;  // warp-uniform: leave q unchanged
+      const double ip = 1.0 / pv;
+      double nv[kGjPerLane];
+#pragma unroll
+      for (int m = 0; m < kGjPerLane; ++m) {
+        const int e = lane + 32 * m;
+        if (e >= nn) break;
+        const int r = e / n, c = e - r * n;
+        const double v = S[e];
+        if (r == j)
+          nv[m] = c == j ? ip : v * ip;
+        else if (c == j)
+          nv[m] = -v * ip;
+        else
+          nv[m] = fma(-(S[r * n + j] * ip), S[j * n + c], v);
       }
       __syncwarp();
-      if (chol_fail) return;  // warp-uniform: leave q unchanged
-      if (lane > j && lane < n) {
-        double t = S[lane * n + j];
-        for (int k = 0; k < j; ++k) t -= Lc[lane * n + k] * Lc[j * n + k];
-        Lc[lane * n + j] = t * il[j];
+#pragma unroll
+      for (int m = 0; m < kGjPerLane; ++m) {
+        const int e = lane + 32 * m;
+        if (e >= nn) break;
+        S[e] = nv[m];
       }
       __syncwarp();
     }
-    if (lane < n) {  // column c of S^{-1}: L L^T w = e_c
-      const int c = lane;
-      double v[kMaxJ];
-      for (int k = 0; k < n; ++k) {
-        double t = k == c ? 1.0 : 0.0;
-        for (int m = 0; m < k; ++m) t -= Lc[k * n + m] * v[m];
-        v[k] = t * il[k];
-      }
-      for (int k = n - 1; k >= 0; --k) {
-        double t = v[k];
-        for (int m = k + 1; m < n; ++m) t -= Lc[m * n + k] * v[m];
-        v[k] = t * il[k];
-      }
-      for (int k = 0; k < n; ++k) {
-        Wp[k * n + c] = v[k];
-        Wg[(size_t)i * n * n + k * n + c] = v[k];
-      }
-      Yg[(size_t)i * n + c] = ycur[c];
+    double* Wi = Wg + (size_t)i * nn;
+#pragma unroll
+    for (int m = 0; m < kGjPerLane; ++m) {
+      const int e = lane + 32 * m;
+      if (e >= nn) break;
+      Wi[e] = S[e];
     }
+    if (lane < n) Yg[(size_t)i * n + lane] = ycur[lane];
     __syncwarp();
   }
+  // x_i = S_i^{-1} (y_i + x_{i+1}): lane c takes row c; step i - 1's row is loaded
+  // during step i
+  double wr[kMaxJ], yr[kMaxJ];
+  auto load_back = [&](int i) {
+#pragma unroll
+    for (int k = 0; k < kMaxJ; ++k) {
+      wr[k] = lane < n && k < n ? Wg[(size_t)i * nn + lane * n + k] : 0.0;
+      yr[k] = k < n ? Yg[(size_t)i * n + k] : 0.0;
+    }
+  };
+  load_back(T - 1);
   for (int i = T - 1; i >= 0; --i) {
     double v = 0.0;
-    if (lane < n) {
-      const int c = lane;
-      const double* Wi = Wg + (size_t)i * n * n;
-      for (int k = 0; k < n; ++k)
-        v += Wi[c * n + k] * (Yg[(size_t)i * n + k] + (i + 1 < T ? xs[k] : 0.0));
-    }
+#pragma unroll
+    for (int k = 0; k < kMaxJ; ++k)
+      if (k < n) v += wr[k] * (yr[k] + (i + 1 < T ? xs[k] : 0.0));
+    if (i > 0) load_back(i - 1);
     __syncwarp();
     if (lane < n) {
       const int c = lane;
@@ -681,7 +716,7 @@ static cudaError_t launch_smooth_t(const Src& s, int n, int nreq, int max_T, con
                                    bool any_geo, cudaStream_t st) {
   const SmoothArgs a{P.tau_pos, P.tau_rot, P.smooth_lambda, P.coll_margin, P.coll_weight};
   if (any_geo) {
-    smooth_geo_kernel<Src><<<nreq, 32, 0, st>>>(s, a);
+    smooth_geo_kernel<Src><<<nreq, kSmoothGeoThreads, 0, st>>>(s, a);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
