@@ -311,11 +311,14 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __gri
 //  * the 8 partial (minimum, tile) pairs merge in warp order, the lower range
 //    winning ties, and the 8 warps re-evaluate 2 nodes each of the winning
 //    tile for the lowest index attaining the minimum;
-//  * each new record [-q', C'] is stored into the record buffer of every CTA of
-//    the cluster (distributed shared memory), and a release/acquire cluster
-//    barrier ends the step. Records are double-buffered: a CTA that starts step
-//    i+1 writes only the buffer every CTA finished reading before the barrier
-//    of step i.
+//  * each new record [-q', C'] goes into the record buffer of every CTA of the
+//    cluster by asynchronous distributed-shared-memory stores that count their
+//    bytes on the receiving CTA's mbarrier for that buffer; a CTA starts step
+//    i+1 once its barrier has seen all Kp records of layer i+1 (a bounded wait).
+//    Records are double-buffered. A CTA writes layer i+2 into a peer only after
+//    it has received the peer's layer-i+1 records, which the peer sends after
+//    its last read of the buffer that layer i+2 overwrites, so no step needs a
+//    cluster-wide barrier.
 constexpr int kDpcThreads = 256;
 constexpr int kDpcWarps = kDpcThreads / 32;
 static_assert(kDp2Tile == 2 * kDpcWarps, "the rescan gives each warp 2 nodes of a tile");
@@ -335,20 +338,17 @@ __device__ __forceinline__ uint32_t map_peer(uint32_t smem_addr, uint32_t rank) 
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr), "r"(rank));
   return r;
 }
-__device__ __forceinline__ void st_peer_v4(uint32_t addr, float4 v) {
-  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y),
-               "f"(v.z), "f"(v.w)
-               : "memory");
-}
 __device__ __forceinline__ void cluster_barrier() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n"
                "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+// 16 bytes into a peer's shared memory; completion counts 16 bytes on the
+// peer's mbarrier (both addresses from mapa).
+__device__ __forceinline__ void st_async_v4(uint32_t addr, float4 v, uint32_t bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::
+          "r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+      : "memory");
 }
 
 template <int NJ, int R, int OBJ, class Src>
@@ -365,7 +365,16 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
   float* const xmin = recb + 2 * (size_t)RL;             // [warps][S]
   int* const xtile = reinterpret_cast<int*>(xmin + kDpcWarps * S);
   int* const xarg = xtile + kDpcWarps * S;
+  __shared__ uint64_t rbar[2];  // layer L's records arrive on rbar[L & 1]
+  __shared__ int timeout_flag;
   const float* __restrict__ cand = rq.cand;
+  const uint32_t layer_bytes = (uint32_t)Kp * NW * 4;
+  if (tid == 0) {
+    timeout_flag = 0;
+    mbar_init(&rbar[0], 1);
+    mbar_init(&rbar[1], 1);
+    fence_mbar_init();
+  }
 
   // layer 0: every CTA builds all records locally
   {
@@ -404,10 +413,19 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
   __syncthreads();
   cluster_barrier();
 
+  // layer L >= 1 completes phase (L - 1) / 2 of rbar[L & 1]
+  auto wait_layer = [&](int L) {
+    if (!mbar_wait_bounded_cluster(&rbar[L & 1], (uint32_t)(((L - 1) >> 1) & 1))) {
+      timeout_flag = 1;
+      raise_status(rq.status, CPP_ERR_TIMEOUT);
+    }
+  };
   for (int i = 0; i + 1 < T; ++i) {
     const int L = i + 1;
     const float* cur = recb + (size_t)(i & 1) * RL;
     float* nxt = recb + (size_t)(L & 1) * RL;
+    if (tid == 0) mbar_expect_tx(&rbar[L & 1], layer_bytes);
+    if (i > 0) wait_layer(i);
     uint64_t own[R][NP];
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -456,6 +474,7 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       xtile[warp * S + lane + 32 * r] = btile[r];
     }
     __syncthreads();
+    if (timeout_flag) break;  // CTA-uniform after the barrier
     // every warp merges the 8 ranges of its lane's slots in order (the same
     // result in all warps) and re-evaluates 2 records of the winning tile:
     // warp w takes nodes 2w, 2w + 1 of it, so the lowest match is the first
@@ -483,10 +502,8 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       xarg[warp * S + slot] = found;
     }
     __syncthreads();
-    // every warp takes the lowest match of its lane's slots and writes the new
-    // records into the CTAs c = warp, warp + 8 of the cluster; the backpointers
-    // go to global memory between the arrival at the cluster barrier and the
-    // wait, outside the release
+    // every warp takes the lowest match of its lane's slots and sends the new
+    // records to the CTAs c = warp, warp + 8 of the cluster
     int bsel[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -506,23 +523,27 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       v[NJ] = kp[r] < K ? comb<OBJ>(bvr[r], rpen[r]) : CUDART_INF_F;
 #pragma unroll
       for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
-      const uint32_t base = smem_u32(nxt + rec_off(NW, kp[r]));
+      const uint32_t base = smem_u32(nxt + rec_off(NW, kp[r])), bar = smem_u32(&rbar[L & 1]);
       for (int c = warp; c < CS; c += kDpcWarps) {
-        const uint32_t peer = map_peer(base, (uint32_t)c);
+        const uint32_t peer = map_peer(base, (uint32_t)c), pbar = map_peer(bar, (uint32_t)c);
 #pragma unroll
         for (int w = 0; w < NW / 4; ++w)
-          st_peer_v4(peer + 16 * w, make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]));
+          st_async_v4(peer + 16 * w, make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]),
+                      pbar);
       }
     }
-    cluster_arrive();
 #pragma unroll
     for (int r = 0; r < R; ++r)
       if (warp == (r & (kDpcWarps - 1)) && kp[r] < Kp) rq.bp[(size_t)L * Kb + kp[r]] = (uint16_t)bsel[r];
-    cluster_wait();
   }
-  const float* fin = recb + (size_t)((T - 1) & 1) * RL;
-  for (int k = (int)crank * S + tid; k < min(Kp, ((int)crank + 1) * S); k += kDpcThreads)
-    rq.costT[k] = fin[rec_off(NW, k) + NJ];
+  if (T > 1 && !timeout_flag) wait_layer(T - 1);
+  __syncthreads();
+  if (!timeout_flag) {
+    const float* fin = recb + (size_t)((T - 1) & 1) * RL;
+    for (int k = (int)crank * S + tid; k < min(Kp, ((int)crank + 1) * S); k += kDpcThreads)
+      rq.costT[k] = fin[rec_off(NW, k) + NJ];
+  }
+  cluster_barrier();  // no CTA leaves while a peer may still store into it
 }
 
 // Any n and Kp that fit in shared memory: successor values are read back from
