@@ -194,8 +194,14 @@ __device__ __forceinline__ bool collides(const GeoF& g, const float (*cA)[3], co
     if (!aabb_meet(cA[u], cB[u], g.r[u] + 1e-5f, cA[v], cB[v], g.r[v] + 1e-5f)) continue;
     if (sqrtf(seg_seg_d2(cA[u], cB[u], cA[v], cB[v])) - g.r[u] - g.r[v] < 0.f) return true;
   }
-  for (int o = 0; o < g.n_boxes; ++o) {
-    for (int c = 0; c < g.n_caps; ++c) {
+  // capsule-box: disjoint bounding spheres first (both radii carry 1e-5 m of
+  // slack), then the box-frame bounding boxes, then the exact distance
+  for (int c = 0; c < g.n_caps; ++c) {
+    float m[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) m[q] = 0.5f * (cA[c][q] + cB[c][q]);
+    for (int o = 0; o < g.n_boxes; ++o) {
+      if (!spheres_meet(m, g.bound[c], g.p[o], g.box_bound[o], 0.f)) continue;
       float a[3], b[3];
       to_box(g, o, cA[c], a);
       to_box(g, o, cB[c], b);

@@ -528,6 +528,9 @@ __global__ void __launch_bounds__(kSmoothGeoThreads) smooth_geo_kernel(const __g
     }
     for (int ob = 0; ob < g.n_boxes; ++ob) {
       for (int c = 0; c < g.n_caps; ++c) {
+        float mc[3];
+        for (int q = 0; q < 3; ++q) mc[q] = 0.5f * (cA[c][q] + cB[c][q]);
+        if (!spheres_meet(mc, g.bound[c], g.p[ob], g.box_bound[ob], margin)) continue;
         float ab[3], bb[3];
         to_box(g, ob, cA[c], ab);
         to_box(g, ob, cB[c], bb);
