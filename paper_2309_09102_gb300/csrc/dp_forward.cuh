@@ -328,20 +328,6 @@ inline size_t dpc_smem_bytes(int nj, int Kp, int R) {
   return (size_t)2 * rec_layer_floats(NW, Kp) * 4 + (size_t)3 * kDpcWarps * 32 * R * 4;
 }
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t map_peer(uint32_t smem_addr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void cluster_barrier() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n"
-               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 // 16 bytes into a peer's shared memory; completion counts 16 bytes on the
 // peer's mbarrier (both addresses from mapa).
 __device__ __forceinline__ void st_async_v4(uint32_t addr, float4 v, uint32_t bar) {

@@ -23,8 +23,9 @@
 
 namespace cppflow {
 
-constexpr int kLmThreads = 128;
-constexpr int kChkThreads = 256;
+constexpr int kLmThreads = 32;   // one warp per block: a lone request spreads over T / 32 SMs
+constexpr int kChkThreads = 64;
+constexpr int kChkCluster = 8;   // CTAs per request in the check
 
 struct LmArgs {
   double lambda0, lambda_up, lambda_down, lambda_min, lambda_max, freeze_step, freeze_cost;
@@ -246,19 +247,33 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
 }
 
 // ------------------------------------------------------------------ FP64 check
-template <class Src>
-__global__ void __launch_bounds__(kChkThreads) check_kernel(const __grid_constant__ Src src,
-                                                             const CheckArgs a) {
-  const Req& rq = src.req(blockIdx.x);
+// Waypoints are split over kChkCluster groups of 64 threads: group c takes
+// waypoints c * 64 + t + 512 k. Each group reduces its two warps in a fixed
+// order into one partial, and the 8 partials combine in group order. The FP64
+// FK of a waypoint costs a few hundred FP64 operations and GB300 issues FP64 at
+// two lanes per clock per SM, so a lone request (or a small batch) runs the
+// groups as the CTAs of a thread-block cluster on 8 SMs, the partials combined
+// through distributed shared memory (CL = true); a large batch runs them as
+// the warps of one 512-thread CTA per request (CL = false). Both orders are the
+// same, so a request's report is the same alone and in any batch.
+template <bool CL, class Src>
+__global__ void __launch_bounds__(CL ? kChkThreads : kChkThreads * kChkCluster)
+    check_kernel(const __grid_constant__ Src src, const CheckArgs a) {
+  constexpr int NWARP = (CL ? kChkThreads : kChkThreads * kChkCluster) / 32;
+  const Req& rq = src.req(CL ? blockIdx.x / kChkCluster : blockIdx.x);
+  const uint32_t crank = CL ? cluster_rank() : 0;
   __shared__ RobotD rd;
-  __shared__ double red[5][kChkThreads / 32];
-  __shared__ int redi[3][kChkThreads / 32];
+  __shared__ double red[5][NWARP];
+  __shared__ int redi[3][NWARP];
+  __shared__ double part[CL ? 1 : kChkCluster][5];  // group partials
+  __shared__ int parti[CL ? 1 : kChkCluster][3];
   stage_robot(src.rob(rq.robot), 0.0, nullptr, &rd);
   __syncthreads();
   const int n = rd.n, T = rq.T, tid = threadIdx.x;
+  const int group = CL ? (int)crank : tid / kChkThreads, gt = CL ? tid : tid % kChkThreads;
   double mpos = 0, mrot = 0, mjac = 0, slinf = 0, tlen = 0;
   int npose = 0, nlim = 0, njump = 0;
-  for (int i = tid; i < T; i += kChkThreads) {
+  for (int i = group * kChkThreads + gt; i < T; i += kChkCluster * kChkThreads) {
     double q[kMaxJ], R[9], p[3], Rt[9];
     for (int j = 0; j < n; ++j) q[j] = (double)rq.q_out[(size_t)i * n + j];
     fk_f64(rd, q, R, p);
@@ -290,7 +305,7 @@ __global__ void __launch_bounds__(kChkThreads) check_kernel(const __grid_constan
       if (linf > a.jump_max) ++njump;
     }
   }
-  // fixed-order block reduction
+  // fixed-order reduction: warps by shuffles, a group's two warps in order
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     mpos = fmax(mpos, __shfl_xor_sync(0xffffffffu, mpos, o));
@@ -309,29 +324,48 @@ __global__ void __launch_bounds__(kChkThreads) check_kernel(const __grid_constan
     redi[0][warp] = npose; redi[1][warp] = nlim; redi[2][warp] = njump;
   }
   __syncthreads();
-  if (tid == 0 && rq.report) {
-    cpp_report_t r;
-    r.max_pos = r.max_rot = r.mjac = r.sum_linf = r.traj_len = 0.0;
-    r.n_pose_fail = r.n_limit_fail = r.n_jump_fail = 0;
-    for (int w = 0; w < kChkThreads / 32; ++w) {
-      r.max_pos = fmax(r.max_pos, red[0][w]);
-      r.max_rot = fmax(r.max_rot, red[1][w]);
-      r.mjac = fmax(r.mjac, red[2][w]);
-      r.sum_linf += red[3][w];
-      r.traj_len += red[4][w];
-      r.n_pose_fail += redi[0][w];
-      r.n_limit_fail += redi[1][w];
-      r.n_jump_fail += redi[2][w];
+  constexpr int WPG = kChkThreads / 32;  // warps per group
+  if (gt == 0) {
+    const int w0 = CL ? 0 : group * WPG, slot = CL ? 0 : group;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int c[3] = {0, 0, 0};
+    for (int w = w0; w < w0 + WPG; ++w) {
+      for (int k = 0; k < 3; ++k) v[k] = fmax(v[k], red[k][w]);
+      v[3] += red[3][w];
+      v[4] += red[4][w];
+      for (int k = 0; k < 3; ++k) c[k] += redi[k][w];
     }
+    for (int k = 0; k < 5; ++k) part[slot][k] = v[k];
+    for (int k = 0; k < 3; ++k) parti[slot][k] = c[k];
+  }
+  if (CL)
+    cluster_barrier();  // every CTA's partial is visible to CTA 0
+  else
+    __syncthreads();
+  if (crank == 0 && tid == 0 && rq.report) {
+    cpp_report_t r;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int c[3] = {0, 0, 0};
+    for (int g = 0; g < kChkCluster; ++g) {
+      for (int k = 0; k < 5; ++k) {
+        const double x = CL ? ld_peer_f64(map_peer(smem_u32(&part[0][k]), (uint32_t)g)) : part[g][k];
+        v[k] = k < 3 ? fmax(v[k], x) : v[k] + x;
+      }
+      for (int k = 0; k < 3; ++k)
+        c[k] += CL ? ld_peer_s32(map_peer(smem_u32(&parti[0][k]), (uint32_t)g)) : parti[g][k];
+    }
+    r.max_pos = v[0]; r.max_rot = v[1]; r.mjac = v[2]; r.sum_linf = v[3]; r.traj_len = v[4];
+    r.n_pose_fail = c[0]; r.n_limit_fail = c[1]; r.n_jump_fail = c[2];
     r.valid = (r.n_pose_fail == 0 && r.n_limit_fail == 0 && r.n_jump_fail == 0) ? 1 : 0;
     *rq.report = r;
   }
+  if (CL) cluster_barrier();  // no CTA leaves before CTA 0 has read its partial
 }
 
 // ------------------------------------------------------------------ trajectory-length step
 // §III-C non-stationary objective: pose-only LM phases alternate with single
-// steps on the differencing residual r_diff = [q_{i+1} - q_i] (the collision
-// rows of r_diff are not built). A step is taken only when every waypoint is
+// steps on the differencing residual r_diff = [q_{i+1} - q_i] (requests with a
+// collision model add its rows: smooth_geo_kernel below). A step is taken only when every waypoint is
 // within tau_pos / tau_rot (FP64 FK of q_out). It is the damped least-squares
 // step delta = -(J^T J + lambda_d I)^{-1} J^T r_diff; J^T J is block tridiagonal
 // with blocks (c_i + lambda_d) I on the diagonal (c_i = 1 at the ends, 2 inside)
@@ -776,11 +810,26 @@ int lm_launches(const cpp_params_t& P, bool any_geo) {
   return 1 + (any_geo ? 3 : 2) * (P.smooth_rounds > 0 ? P.smooth_rounds : 0);
 }
 
+// A batch whose clusters would not fit on the GPU at once runs one CTA per request.
 template <class Src>
 static cudaError_t launch_check_t(const Src& s, int nreq, const cpp_params_t& P, cudaStream_t st) {
   CheckArgs a{P.tau_pos, P.tau_rot, P.jump_max};
-  check_kernel<Src><<<nreq, kChkThreads, 0, st>>>(s, a);
-  return cudaGetLastError();
+  if (nreq * kChkCluster > device_sm_count()) {
+    check_kernel<false, Src><<<nreq, kChkThreads * kChkCluster, 0, st>>>(s, a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nreq * kChkCluster));
+  cfg.blockDim = dim3(kChkThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kChkCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, check_kernel<true, Src>, s, a);
 }
 cudaError_t launch_check(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st) {
   return launch_check_t(s, 1, P, st);

@@ -182,11 +182,15 @@ def test_plan_matches_oracle(w):
     assert abs(r["sum_linf"] - ref["report"]["sum_linf"]) <= JUMP_TOL * pb.w.T
 
 
-def test_batch_equals_alone():
+@pytest.mark.parametrize("count", [6, 24])
+def test_batch_equals_alone(count):
     """Requests of different T and K in one batched launch give exactly the results each
-    gets alone (same kernels, same inputs)."""
+    gets alone (same kernels, same inputs), report included. A lone request's FP64 check
+    runs as an 8-CTA cluster; a batch of 24 (more clusters than SMs) runs one CTA per
+    request with the same summation order."""
     tt = torch()
-    shapes = [(30, 40), (61, 128), (12, 7), (45, 256), (2, 3)]
+    base = [(30, 40), (61, 128), (12, 7), (45, 256), (2, 3), (700, 16)]
+    shapes = [base[i % len(base)] for i in range(count)]
     pbs = [problems.small(T=T, K=K, seed=500 + i) for i, (T, K) in enumerate(shapes)]
     op, cp = params_pair(lm_iters=10)
     robots = [crob(pb.arm) for pb in pbs]
@@ -215,6 +219,7 @@ def test_batch_equals_alone():
         np.testing.assert_array_equal(keep[r]["q"].cpu().numpy(), alone["q"])
         np.testing.assert_array_equal(keep[r]["err"].cpu().numpy(), alone["err"])
         assert float(keep[r]["best"].item()) == float(alone["best"])
+        assert cppflow.report_from_bytes(keep[r]["rep"].cpu().numpy().tobytes()) == alone["report"]
 
 
 @pytest.mark.parametrize("n", [7, 9, 6])
