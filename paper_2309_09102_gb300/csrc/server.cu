@@ -11,8 +11,11 @@
 //  * one worker thread: it retires finished launches (event query), then forms
 //    the next batch from the queue -- requests of the oldest request's size
 //    class (joint count, K bucket, T bucket) in arrival order, while the class
-//    cap, slots and arena space allow -- and enqueues H2D copies, the six stage
-//    launches and the D2H copy of results on one of max_inflight streams.
+//    cap, slots and arena space allow -- stages it (H2D copies of its inputs
+//    and request table on a copy stream) and enqueues the six stage launches and
+//    the D2H copy of results on one of max_inflight streams. When every stream
+//    is busy and a full batch is queued, one batch is formed and staged ahead,
+//    so its copies overlap the running launches instead of idling a stream.
 //    Requests that arrive while earlier batches run are admitted into the next
 //    batch as memory frees up, and the batches overlap on the device. At light
 //    load batches hold one or a few requests and run as clusters (low latency);
@@ -154,8 +157,12 @@ Layout slot_layout(int T, int Kp, int n) {
 struct Launch {
   std::vector<Request*> reqs;
   bool improve = false;  // an anytime improvement round (slots already resident)
-  int stream = 0;
+  int stream = -1;       // compute stream, set when the kernels are enqueued
+  cudaEvent_t copied = nullptr;  // inputs and table on the device (copy stream)
   cudaEvent_t done = nullptr;
+  int n = 0, max_T = 0, max_Kp = 0;
+  long long max_tasks = 0;
+  bool any_geo = false;
   size_t tab_off = 0, tab_bytes = 0;      // device: Req[] | robots[] | status[]
   size_t tab_pin = 0, tab_pin_bytes = 0;  // pinned host mirror
   bool tab_pinned = false;
@@ -173,6 +180,8 @@ struct cpp_server {
   Arena parena;
   std::vector<cudaStream_t> streams;
   std::vector<bool> stream_busy;
+  cudaStream_t copy_stream = nullptr;  // host-to-device copies of formed launches
+  std::deque<Launch*> staged;          // formed, inputs copying, waiting for a stream
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> queue;
@@ -193,6 +202,7 @@ struct cpp_server {
   bool alloc_table(Launch* L);
   void finish(Request* r);
   void anytime_step(Request* r, bool improve_round);
+  cpp_status stage(Launch* L);
   cpp_status enqueue(Launch* L);
   void retire(Launch* L, cudaError_t e);
   void release_host(Request* r);
@@ -336,8 +346,12 @@ void cpp_server::anytime_step(Request* r, bool improve_round) {
   }
 }
 
-cpp_status cpp_server::enqueue(Launch* L) {
-  const cudaStream_t st = streams[L->stream];
+// The host-to-device part of a launch, on the copy stream: the requests'
+// inputs (not for improvement rounds, whose inputs are resident) and the request
+// table; `copied` marks the end. Launches staged while every compute stream is
+// busy thus copy while the earlier launches compute.
+cpp_status cpp_server::stage(Launch* L) {
+  const cudaStream_t st = copy_stream;
   const int count = (int)L->reqs.size();
   const int n = L->reqs[0]->n;
   char* tab_d = d_arena + L->tab_off;
@@ -393,7 +407,31 @@ cpp_status cpp_server::enqueue(Launch* L) {
     max_tasks = std::max(max_tasks, mask_tasks(r->T, r->Kp));
   }
   cudaError_t e = cudaMemcpyAsync(tab_d, L->tab_h, L->tab_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(L->copied, st);
   if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server H2D table: %s", cudaGetErrorString(e));
+  L->n = n;
+  L->max_T = max_T;
+  L->max_Kp = max_Kp;
+  L->max_tasks = max_tasks;
+  L->any_geo = any_geo;
+  return CPP_OK;
+}
+
+// The device part of a staged launch on its compute stream: wait for its copies,
+// the stage kernels, the device-to-host copies of the results, `done`.
+cpp_status cpp_server::enqueue(Launch* L) {
+  const cudaStream_t st = streams[L->stream];
+  const int count = (int)L->reqs.size();
+  const int n = L->n, max_T = L->max_T, max_Kp = L->max_Kp;
+  const long long max_tasks = L->max_tasks;
+  const bool any_geo = L->any_geo;
+  char* tab_d = d_arena + L->tab_off;
+  int32_t* tst = reinterpret_cast<int32_t*>(L->tab_h + align256(sizeof(Req) * count) +
+                                            align256(sizeof(cpp_robot_t) * count));
+  int32_t* tst_d = reinterpret_cast<int32_t*>(tab_d + align256(sizeof(Req) * count) +
+                                              align256(sizeof(cpp_robot_t) * count));
+  cudaError_t e = cudaStreamWaitEvent(st, L->copied, 0);
+  if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server launch: %s", cudaGetErrorString(e));
   BatchSrc src{reinterpret_cast<const Req*>(tab_d),
                reinterpret_cast<const cpp_robot_t*>(tab_d + align256(sizeof(Req) * count))};
   if (L->improve) {
@@ -453,7 +491,13 @@ void cpp_server::retire(Launch* L, cudaError_t e) {
   }
   darena.release(L->tab_off, L->tab_bytes);
   if (L->tab_pinned) parena.release(L->tab_pin, L->tab_pin_bytes);
-  stream_busy[L->stream] = false;
+  if (L->stream >= 0) stream_busy[L->stream] = false;
+}
+
+static void drop_launch(Launch* L) {
+  if (L->copied) cudaEventDestroy(L->copied);
+  if (L->done) cudaEventDestroy(L->done);
+  delete L;
 }
 
 void cpp_server::run() {
@@ -466,52 +510,70 @@ void cpp_server::run() {
       const cudaError_t q = cudaEventQuery(L->done);
       if (q == cudaErrorNotReady) { ++k; continue; }
       retire(L, q);
-      cudaEventDestroy(L->done);
-      delete L;
+      drop_launch(L);
       inflight.erase(inflight.begin() + k);
       cv_done.notify_all();
     }
-    if (stop && inflight.empty()) break;
-    // launch the next batch
-    bool launched = false;
-    if (!stop && (int)inflight.size() < cfg.max_inflight && (!queue.empty() || !improve_q.empty())) {
-      int sidx = -1;
+    if (stop && inflight.empty() && staged.empty()) break;
+    int sidx = -1;
+    if ((int)inflight.size() < cfg.max_inflight)
       for (int k = 0; k < (int)streams.size(); ++k)
         if (!stream_busy[k]) { sidx = k; break; }
+    // form and stage a launch: when a stream is free, or ahead of time (one
+    // launch) when every stream is busy and a full batch is waiting, so its
+    // copies overlap the running launches
+    bool progressed = false;
+    const bool ahead = sidx < 0 && staged.empty() && (int)queue.size() >= cfg.max_batch;
+    if (!stop && ((sidx >= 0 && staged.empty()) || ahead) && (!queue.empty() || !improve_q.empty())) {
       Launch* L = new Launch;
       // new plans first; anytime improvement rounds fill the remaining capacity
       bool formed = false;
-      if (sidx >= 0) {
-        if (!queue.empty()) formed = form_batch(L);
-        if (!formed && !improve_q.empty()) formed = form_improve(L);
-      }
+      if (!queue.empty()) formed = form_batch(L);
+      if (!formed && !ahead && !improve_q.empty()) formed = form_improve(L);
       if (formed) {
-        L->stream = sidx;
-        stream_busy[sidx] = true;
+        cudaEventCreateWithFlags(&L->copied, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
         ++stats.batches;
         if (L->improve) ++stats.improve_batches;
         stats.max_batch_seen = std::max<int32_t>(stats.max_batch_seen, (int32_t)L->reqs.size());
         stats.sum_batch += L->reqs.size();
         lk.unlock();
-        const cpp_status s = enqueue(L);
+        const cpp_status st = stage(L);
         lk.lock();
-        if (s != CPP_OK) {
+        if (st != CPP_OK) {
           fatal = cpp_last_error();
           retire(L, cudaErrorUnknown);
-          cudaEventDestroy(L->done);
-          delete L;
+          drop_launch(L);
           cv_done.notify_all();
         } else {
-          inflight.push_back(L);
-          launched = true;
+          staged.push_back(L);
         }
+        progressed = true;
       } else {
         delete L;
       }
     }
-    if (launched) continue;
-    if (inflight.empty()) {
+    // enqueue the oldest staged launch on a free stream
+    if (sidx >= 0 && !staged.empty()) {
+      Launch* L = staged.front();
+      staged.pop_front();
+      L->stream = sidx;
+      stream_busy[sidx] = true;
+      lk.unlock();
+      const cpp_status st = enqueue(L);
+      lk.lock();
+      if (st != CPP_OK) {
+        fatal = cpp_last_error();
+        retire(L, cudaErrorUnknown);
+        drop_launch(L);
+        cv_done.notify_all();
+      } else {
+        inflight.push_back(L);
+      }
+      progressed = true;
+    }
+    if (progressed) continue;
+    if (inflight.empty() && staged.empty()) {
       cv_work.wait(lk, [&] { return stop || !queue.empty() || !improve_q.empty(); });
     } else {
       lk.unlock();
@@ -588,6 +650,7 @@ cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out)
   s->streams.resize(cfg->max_inflight);
   s->stream_busy.assign(cfg->max_inflight, false);
   for (auto& st : s->streams) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
   s->worker = std::thread([s] { s->run(); });
   *out = s;
   return CPP_OK;
@@ -826,6 +889,7 @@ void cpp_server_destroy(cpp_server_t* s) {
   }
   s->reqs.clear();
   for (auto st : s->streams) cudaStreamDestroy(st);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->d_arena) cudaFree(s->d_arena);
   if (s->h_pinned) cudaFreeHost(s->h_pinned);
   delete s;
