@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
     int btile[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; btile[r] = -1; }
-#pragma unroll 1
+#pragma unroll (R == 2 ? 2 : 1)  // measured: two tiles per iteration help only R = 2
     for (int t = t_lo; t < t_hi; ++t) {
       const int kb = t * kDp2Tile;
       const float* base = cur + rec_off(NW, kb);

@@ -43,6 +43,28 @@ def test_served_equals_alone():
         assert res["latency_ms"] > 0
 
 
+def test_batches_staged_ahead_equal_alone():
+    """One compute stream and batches of 2 from 6 same-class requests queued at once: while
+    a batch runs, the next is formed and its inputs copied ahead; every result (report
+    included) equals cpp_plan alone."""
+    pbs = [problems.small(T=40, K=64, seed=760 + i) for i in range(6)]
+    _, cp = params_pair(lm_iters=10)
+    robots = [cppflow.robot_from_arm(pb.arm) for pb in pbs]
+    with cppflow.Server(cp, hbm_budget=1 << 30, max_inflight=1, max_batch=2) as srv:
+        tickets = [srv.submit(robots[i], pb.cand, pb.targets, pb.K) for i, pb in enumerate(pbs)]
+        results = [srv.wait(t) for t in tickets]
+        stats = srv.stats()
+    # the first batch may leave before the others are submitted
+    assert stats["completed"] == 6 and stats["batches"] >= 3 and stats["max_batch_seen"] == 2
+    for i, pb in enumerate(pbs):
+        st, res = results[i]
+        assert st == cppflow.OK
+        alone = run_plan(robots[i], cp, pb.cand, pb.targets, pb.K)
+        np.testing.assert_array_equal(res["sel"], alone["sel"])
+        np.testing.assert_array_equal(res["q"], alone["q"])
+        assert res["report"] == alone["report"]
+
+
 def test_borrowed_inputs_and_tiny_budget():
     """A budget that holds about one request at a time: every request still completes,
     admitted as memory frees up; a request larger than the whole budget is refused."""
