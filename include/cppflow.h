@@ -444,7 +444,7 @@ void cpp_batch_destroy(cpp_batch_t* batch);
  * waypoint (32, 64 or 128; 0 = 64 up to Kp = 512 and 128 above, as long as the
  * cluster has 2..8 CTAs; an explicit 32 or 64 also allows the non-portable sizes
  * of 9..16 CTAs): fewer per CTA shorten a long request's latency, more halve the
- * per-step cluster traffic and barriers per candidate. The automatic form
+ * per-step record exchange and waits per candidate. The automatic form
  * (alpha = 0, single-request calls, the server) takes the smallest tile (32 per
  * CTA up to Kp = 512, 64 above, clusters of up to 16 CTAs) when the device holds
  * all the requests' clusters at once with one CTA per SM.
