@@ -455,12 +455,14 @@ void cpp_batch_destroy(cpp_batch_t* batch);
  * sweep (CUDA events, best of two runs after one warm-up) for alpha = 0 and,
  * for each cands_per_cta in {64, 128}, a ladder of alpha values from 8 down to
  * 1e-9 (every cluster-capable request heavy), skipping values that give the same
- * split, and keeps the fastest. With a
+ * split, and keeps the fastest; then it times the mask stage the same way for
+ * 1, 2, 4, 8 and 16 tasks per warp and keeps the fastest. With a
  * non-NULL table_path the choice is looked up first under a key of the batch's
  * shape (joints, objective, request count and longest T in powers of two,
  * cluster sizes present, skew of the largest lattice over the mean, SM count;
- * plain text, one "key alpha cands_per_cta ms" line per entry, the last entry
- * wins) and, when
+ * plain text, one "key alpha cands_per_cta ms mask_tasks_per_warp" line per
+ * entry, the last entry wins; a line without the last field means the default)
+ * and, when
  * missing, appended after tuning. The call synchronizes `stream`; the batch's
  * outputs are undefined until its next cpp_batch_run. A new schedule drops any
  * captured graph. */
@@ -473,10 +475,16 @@ typedef struct cpp_tune_result {
     int32_t from_table;      /* 1: alpha came from the tuning table */
     float dp_ms;             /* forward sweep time of the choice (-1 from the table) */
     float dp_ms_unsplit;     /* forward sweep time with alpha = 0 (-1 from the table) */
-    int32_t reserved;
+    int32_t mask_tasks_per_warp; /* 128-candidate tasks per warp of the mask stage in use */
+    float mask_ms;           /* mask stage time of the choice (-1 from the table) */
+    float mask_ms_default;   /* mask stage time with 4 tasks per warp (-1 from the table) */
 } cpp_tune_result_t;
 cpp_status cpp_batch_set_split(cpp_batch_t* batch, double alpha, int32_t cands_per_cta,
                                cpp_stream_t stream);
+/* Tasks per warp of the mask stage (S1+S2): a task is one waypoint and 128
+ * candidates, so a warp covers tasks_per_warp * 128 / Kp waypoints of a request
+ * (0: the default, 4). Results do not depend on it. INVALID_ARG outside [0, 64]. */
+cpp_status cpp_batch_set_mask_tasks(cpp_batch_t* batch, int32_t tasks_per_warp);
 cpp_status cpp_batch_tune(cpp_batch_t* batch, const char* table_path, cpp_stream_t stream,
                           cpp_tune_result_t* result);
 

@@ -108,10 +108,12 @@ REQ_ANYTIME = 2
 class TuneResult(C.Structure):
     _fields_ = [("alpha", C.c_double), ("cands_per_cta", C.c_int32), ("heavy", C.c_int32),
                 ("forward_launches", C.c_int32), ("timed", C.c_int32), ("from_table", C.c_int32),
-                ("dp_ms", C.c_float), ("dp_ms_unsplit", C.c_float), ("reserved", C.c_int32)]
+                ("dp_ms", C.c_float), ("dp_ms_unsplit", C.c_float),
+                ("mask_tasks_per_warp", C.c_int32), ("mask_ms", C.c_float),
+                ("mask_ms_default", C.c_float)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class ServerConfig(C.Structure):
@@ -182,6 +184,7 @@ _SIGS = {
     "cpp_batch_launches": (C.c_int32, [_P, C.c_uint32]),
     "cpp_batch_destroy": (None, [_P]),
     "cpp_batch_set_split": (C.c_int, [_P, C.c_double, C.c_int32, _P]),
+    "cpp_batch_set_mask_tasks": (C.c_int, [_P, C.c_int32]),
     "cpp_batch_tune": (C.c_int, [_P, C.c_char_p, _P, _P]),
     "cpp_batch_capture": (C.c_int, [_P, C.c_uint32, _P]),
     "cpp_batch_replay": (C.c_int, [_P, _P]),
@@ -447,6 +450,10 @@ class Batch:
     def set_split(self, alpha: float, cands_per_cta: int = 0, stream=None):
         _check(lib().cpp_batch_set_split(self.handle, float(alpha), int(cands_per_cta),
                                          stream_handle(stream)), "cpp_batch_set_split")
+
+    def set_mask_tasks(self, tasks_per_warp: int):
+        _check(lib().cpp_batch_set_mask_tasks(self.handle, int(tasks_per_warp)),
+               "cpp_batch_set_mask_tasks")
 
     def tune(self, table_path: str | None = None, stream=None) -> dict:
         r = TuneResult()

@@ -581,6 +581,7 @@ struct cpp_batch {
   bool any_geo;  // some request has a collision model
   double alpha;
   int cpc;  // successor candidates per CTA of the cluster form (0: default)
+  int mask_tpw;  // 128-candidate tasks per warp of the mask stage (0: default)
   int heavy;
   cudaStream_t aux[kMaxGroups];
   cudaEvent_t fork, join[kMaxGroups];
@@ -687,7 +688,8 @@ cudaError_t run_forward(cpp_batch* b, cudaStream_t st) {
 cpp_status run_stages(cpp_batch* b, uint32_t stages, cudaStream_t st) {
   if (stages & CPP_STAGE_MASK)
     if (cpp_status e = cuda_status(launch_mask_batch(b->src, b->n, b->count, b->max_tasks,
-                                                     b->params, b->any_geo, st), "batch/mask"))
+                                                     b->params, b->any_geo, st, b->mask_tpw),
+                                   "batch/mask"))
       return e;
   if (stages & CPP_STAGE_LAYER_MIN)
     if (cpp_status e = cuda_status(launch_dp_batch(b->src, CPP_STAGE_LAYER_MIN, b->params.dp_objective,
@@ -730,16 +732,24 @@ std::string tune_key(const cpp_batch* b) {
   return buf;
 }
 
-bool table_lookup(const char* path, const std::string& key, double* alpha, int* cpc) {
+// One line per entry: "key alpha cands_per_cta ms [mask_tasks_per_warp]" (the
+// last field absent in older tables: the default); the last entry of a key wins.
+bool table_lookup(const char* path, const std::string& key, double* alpha, int* cpc, int* tpw) {
   if (!path) return false;
   FILE* f = fopen(path, "r");
   if (!f) return false;
-  char k[200];
-  double a, ms;
-  int c;
+  char line[512], k[200];
   bool found = false;
-  while (fscanf(f, "%199s %lf %d %lf", k, &a, &c, &ms) == 4)
-    if (key == k) { *alpha = a; *cpc = c; found = true; }  // the last entry wins
+  while (fgets(line, sizeof(line), f)) {
+    double a, ms;
+    int c, t = 0;
+    const int got = sscanf(line, "%199s %lf %d %lf %d", k, &a, &c, &ms, &t);
+    if (got < 4 || key != k) continue;
+    *alpha = a;
+    *cpc = c;
+    *tpw = got == 5 && t >= 1 && t <= 64 ? t : 0;
+    found = true;
+  }
   fclose(f);
   return found;
 }
@@ -840,6 +850,7 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
   b->any_geo = !geos.empty();
   b->alpha = 0;
   b->cpc = 0;
+  b->mask_tpw = 0;
   b->heavy = 0;
   for (int g = 0; g < kMaxGroups; ++g) { b->aux[g] = nullptr; b->join[g] = nullptr; }
   b->fork = nullptr;
@@ -879,18 +890,28 @@ cpp_status cpp_batch_set_split(cpp_batch_t* b, double alpha, int32_t cands_per_c
   return set_schedule(b, alpha, cands_per_cta, (cudaStream_t)stream);
 }
 
+cpp_status cpp_batch_set_mask_tasks(cpp_batch_t* b, int32_t tasks_per_warp) {
+  if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
+  if (tasks_per_warp < 0 || tasks_per_warp > 64)
+    return fail(CPP_ERR_INVALID_ARG, "tasks_per_warp must be in [0, 64]");
+  b->mask_tpw = tasks_per_warp;
+  drop_graph(b);
+  return CPP_OK;
+}
+
 cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t stream,
                           cpp_tune_result_t* res) {
   if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   cpp_tune_result_t out;
   memset(&out, 0, sizeof(out));
-  out.dp_ms = out.dp_ms_unsplit = -1.f;
+  out.dp_ms = out.dp_ms_unsplit = out.mask_ms = out.mask_ms_default = -1.f;
   const std::string key = tune_key(b);
   double alpha = 0;
-  int cpc = 0;
-  if (table_lookup(table_path, key, &alpha, &cpc)) {
+  int cpc = 0, tpw = 0;
+  if (table_lookup(table_path, key, &alpha, &cpc, &tpw)) {
     if (cpp_status e = set_schedule(b, alpha, cpc, st)) return e;
+    b->mask_tpw = tpw;
     out.from_table = 1;
   } else {
     // node costs first: the sweeps read them
@@ -933,20 +954,47 @@ cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t s
       if (c.alpha == 0.0) out.dp_ms_unsplit = ms;
       if (ms < best_ms) { best_ms = ms; best = c; }
     }
+    // the mask stage: 128-candidate tasks per warp (how many waypoints a warp
+    // covers at each K), same timing rule
+    float best_mask = HUGE_VALF;
+    int best_tpw = 0;
+    for (int t : {1, 2, 4, 8, 16}) {
+      if (err != CPP_OK) break;
+      b->mask_tpw = t;
+      float ms = HUGE_VALF;
+      for (int rep = 0; rep < 3 && err == CPP_OK; ++rep) {
+        cudaError_t ce = cudaEventRecord(e0, st);
+        if (ce == cudaSuccess)
+          ce = launch_mask_batch(b->src, b->n, b->count, b->max_tasks, b->params, b->any_geo, st, t);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float tm = 0;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&tm, e0, e1);
+        err = cuda_status(ce, "cpp_batch_tune");
+        if (rep > 0) ms = std::min(ms, tm);
+      }
+      if (err != CPP_OK) break;
+      ++out.timed;
+      if (t == 4) out.mask_ms_default = ms;
+      if (ms < best_mask) { best_mask = ms; best_tpw = t; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != CPP_OK) return err;
+    b->mask_tpw = best_tpw;
+    out.mask_ms = best_mask;
     if (cpp_status e = set_schedule(b, best.alpha, best.cpc, st)) return e;
     out.dp_ms = best_ms;
     if (table_path) {
       FILE* f = fopen(table_path, "a");
       if (!f) return fail(CPP_ERR_INVALID_ARG, "cannot append to tuning table %s", table_path);
-      fprintf(f, "%s %.9g %d %.4f\n", key.c_str(), best.alpha, best.cpc, best_ms);
+      fprintf(f, "%s %.9g %d %.4f %d\n", key.c_str(), best.alpha, best.cpc, best_ms, best_tpw);
       fclose(f);
     }
   }
   out.alpha = b->alpha;
   out.cands_per_cta = b->cpc;
+  out.mask_tasks_per_warp = b->mask_tpw > 0 ? b->mask_tpw : 4;
   out.heavy = b->heavy;
   out.forward_launches = 0;
   for (const SchedGroup& g : b->groups) out.forward_launches += g.count > 0 ? 1 : 0;

@@ -3,9 +3,10 @@
 // limits"; §III-B node costs).
 //
 // Layout: candidates are [T][n][Kp] FP32, k fastest. A task is one waypoint and
-// a block of 128 candidates; one warp runs kMaskTasksPerWarp consecutive tasks
-// (the 4 blocks of one waypoint at K = 512), so the robot staging of a block and
-// the target conversion of a waypoint are paid once for several tasks. Lane l
+// a block of 128 candidates; one warp runs tasks_per_warp consecutive tasks
+// (default 4: the 4 blocks of one waypoint at K = 512; the batch autotuner
+// picks it per batch), so the robot staging of a block and the target
+// conversion of a waypoint are paid once for several tasks. Lane l
 // reads joints j of candidates 4l .. 4l+3 as one float4 per joint (512
 // contiguous bytes per warp per joint), runs the FP32 DH chain for its four
 // candidates in registers, and writes one uchar4 mask word, one float4 of costs
@@ -18,13 +19,14 @@ namespace cppflow {
 constexpr int kMaskThreads = 256;
 constexpr int kMaskWarps = kMaskThreads / 32;
 constexpr int kMaskBlockK = 128;
-constexpr int kMaskTasksPerWarp = 4;
+constexpr int kMaskTasksPerWarp = 4;  // default tasks per warp
 
 struct MaskArgs {
   float tau_pos, tau_rot;
   float pen_table[8];  // [limit bit | pose bit << 1 | collision bit << 2]: each the FP64 sum
                        // of its costs in that order, rounded once
   double near_margin;
+  int tasks_per_warp;
 };
 
 // The target of waypoint i as FP32 rotation + position. The quaternion is
@@ -132,8 +134,9 @@ __global__ void __launch_bounds__(kMaskThreads) mask_kernel(const __grid_constan
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (rq.Kp + kMaskBlockK - 1) / kMaskBlockK;
   const long long ntask = (long long)rq.T * nblk;
-  const long long t0 = ((long long)blockIdx.x * kMaskWarps + warp) * kMaskTasksPerWarp;
-  const long long t1 = t0 + kMaskTasksPerWarp < ntask ? t0 + kMaskTasksPerWarp : ntask;
+  const int tpw = a.tasks_per_warp;
+  const long long t0 = ((long long)blockIdx.x * kMaskWarps + warp) * tpw;
+  const long long t1 = t0 + tpw < ntask ? t0 + tpw : ntask;
   const int n = NJ ? NJ : rq.n;
 
   int cur_i = -1;
@@ -251,6 +254,7 @@ static MaskArgs make_mask_args(const cpp_params_t& P) {
     a.pen_table[m] = (float)c;
   }
   a.near_margin = P.near_margin;
+  a.tasks_per_warp = kMaskTasksPerWarp;
   return a;
 }
 
@@ -266,9 +270,11 @@ static void launch_mask_c(const Src& src, int n, dim3 grid, const MaskArgs& a, c
 
 template <class Src>
 static cudaError_t launch_mask_t(const Src& src, int n, int nreq, long long max_tasks,
-                                 const cpp_params_t& P, bool coll, cudaStream_t st) {
-  const MaskArgs a = make_mask_args(P);
-  constexpr int per_block = kMaskWarps * kMaskTasksPerWarp;
+                                 const cpp_params_t& P, bool coll, int tasks_per_warp,
+                                 cudaStream_t st) {
+  MaskArgs a = make_mask_args(P);
+  a.tasks_per_warp = tasks_per_warp > 0 ? tasks_per_warp : kMaskTasksPerWarp;
+  const long long per_block = (long long)kMaskWarps * a.tasks_per_warp;
   dim3 grid((unsigned)((max_tasks + per_block - 1) / per_block), (unsigned)nreq);
   if (coll) launch_mask_c<true>(src, n, grid, a, st);
   else launch_mask_c<false>(src, n, grid, a, st);
@@ -277,12 +283,13 @@ static cudaError_t launch_mask_t(const Src& src, int n, int nreq, long long max_
 
 cudaError_t launch_mask(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st) {
   const long long tasks = (long long)s.r.T * ((s.r.Kp + kMaskBlockK - 1) / kMaskBlockK);
-  return launch_mask_t(s, s.r.n, 1, tasks, P, s.has_geo != 0, st);
+  return launch_mask_t(s, s.r.n, 1, tasks, P, s.has_geo != 0, 0, st);
 }
 
 cudaError_t launch_mask_batch(const BatchSrc& s, int n, int nreq, long long max_tasks,
-                              const cpp_params_t& P, bool any_geo, cudaStream_t st) {
-  return launch_mask_t(s, n, nreq, max_tasks, P, any_geo, st);
+                              const cpp_params_t& P, bool any_geo, cudaStream_t st,
+                              int tasks_per_warp) {
+  return launch_mask_t(s, n, nreq, max_tasks, P, any_geo, tasks_per_warp, st);
 }
 
 long long mask_tasks(int T, int Kp) {

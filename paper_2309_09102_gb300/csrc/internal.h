@@ -12,8 +12,10 @@ namespace cppflow {
 
 // fk_mask.cu
 cudaError_t launch_mask(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st);
+// tasks_per_warp: 128-candidate tasks per warp (0: the default, 4)
 cudaError_t launch_mask_batch(const BatchSrc& s, int n, int nreq, long long max_tasks,
-                              const cpp_params_t& P, bool any_geo, cudaStream_t st);
+                              const cpp_params_t& P, bool any_geo, cudaStream_t st,
+                              int tasks_per_warp = 0);
 long long mask_tasks(int T, int Kp);
 cudaError_t launch_fk_batch(const cpp_robot_t& r, const float* q, long long N, float* R,
                             float* p, cudaStream_t st);

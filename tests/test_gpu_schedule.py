@@ -133,17 +133,39 @@ def test_tuner_and_its_table(batch_setup, tmp_path):
     r1 = S["batch"].tune(str(table), S["stream"])
     assert r1["timed"] >= 2 and r1["from_table"] == 0
     assert r1["dp_ms"] > 0 and r1["dp_ms"] <= r1["dp_ms_unsplit"]
+    assert r1["mask_tasks_per_warp"] in (1, 2, 4, 8, 16)
+    assert 0 < r1["mask_ms"] <= r1["mask_ms_default"]
     lines = table.read_text().split("\n")
     assert len([x for x in lines if x]) == 1
-    key, alpha, cpc, ms = lines[0].split()
+    key, alpha, cpc, ms, tpw = lines[0].split()
     assert key.startswith("n7_obj0_") and float(alpha) == pytest.approx(r1["alpha"], rel=1e-6)
-    assert int(cpc) == r1["cands_per_cta"]
+    assert int(cpc) == r1["cands_per_cta"] and int(tpw) == r1["mask_tasks_per_warp"]
     after = results_after_run(S)
     r2 = S["batch"].tune(str(table), S["stream"])
     assert r2["from_table"] == 1 and r2["timed"] == 0
     assert r2["alpha"] == pytest.approx(r1["alpha"], rel=1e-6) and r2["heavy"] == r1["heavy"]
+    assert r2["mask_tasks_per_warp"] == r1["mask_tasks_per_warp"]
     assert_same(results_after_run(S), after)
     assert_same(after, run_with(S, 0.0))
+    # an entry written before the mask knob existed (four fields): the default
+    table.write_text(f"{key} {alpha} {cpc} {ms}\n")
+    r3 = S["batch"].tune(str(table), S["stream"])
+    assert r3["from_table"] == 1 and r3["mask_tasks_per_warp"] == 4
+
+
+@pytest.mark.parametrize("tpw", [1, 2, 8, 16, 64])
+def test_mask_tasks_per_warp_gives_the_same_plans(batch_setup, tpw):
+    """Waypoints per warp of the mask stage (tasks of 128 candidates per warp) change
+    only the launch shape, never a result."""
+    S = batch_setup
+    base = run_with(S, 1.0)
+    S["batch"].set_mask_tasks(tpw)
+    try:
+        assert_same(run_with(S, 1.0), base)
+    finally:
+        S["batch"].set_mask_tasks(0)
+    with pytest.raises(cppflow.CppflowError):
+        S["batch"].set_mask_tasks(65)
 
 
 def results_after_run(S):
