@@ -317,6 +317,60 @@ def build_inputs(cppflow, torch, dev, reqs, want_truth: bool = False):
     return arms, robots, cand_h, targets_h
 
 
+def stress_leg(cppflow, torch, dev) -> dict:
+    """The stress / precision workload: a 9-DoF chain with a spherical wrist, T = 2000,
+    K = 1024, the true path through near-singular wrist poses (joint 6 within 0.02 rad
+    of 0). One request through cpp_plan with the FP32-Jacobian LM (FP64 normal equations
+    and Cholesky, the default) and again with the all-FP64 LM: plan time, per-path pose
+    errors (FP64 check) and joint jumps of each. The comparison with the FP64 CPU
+    oracle's LM is part of the parity tests."""
+    w = synth.STRESS
+    arm = synth.draw_arm(w.arm_seed, w.n, w.wrist)
+    rob = cppflow.robot_from_arm(arm)
+    truth = synth.draw_truth(w.path_seed, w.n, w.T, w.wrist)
+    tgt = torch.empty(w.T, 7, dtype=torch.float64, device=dev)
+    cppflow.fk_pose_f64(rob, torch.from_numpy(truth).to(dev), tgt)
+    P_wb = cppflow.make_params(lm_iters=30, lm_fp64=1, free_mask=synth.wrong_branch_free_mask(w.n))
+    qwb = torch.empty(w.T, w.n, dtype=torch.float32, device=dev)
+    cppflow.lm_refine(rob, P_wb, torch.from_numpy(synth.wrong_branch_start(truth).astype(np.float32)).to(dev),
+                      tgt, qwb)
+    torch.cuda.synchronize()
+    draws = synth.draw_candidates(w.cand_seed, w.T, w.K, w.n, w.p_wb, w.p_out)
+    cand = synth.assemble(truth, qwb.cpu().numpy().astype(np.float64), draws, w.sigma,
+                          arm.lo, arm.hi, synth.pad_k(w.K))
+    cd = torch.from_numpy(cand).to(dev)
+    T, n, Kp = cand.shape
+    st = torch.cuda.current_stream()
+    out = {"workload": f"stress: {n}-DoF spherical wrist, T={T}, K={w.K}, joint 6 within 0.02 rad "
+                       "of 0 along the true path; one request, cpp_plan"}
+    qs = {}
+    for mode, name in ((0, "fp32_jacobian_lm"), (1, "all_fp64_lm")):
+        P = cppflow.make_params(lm_iters=w.lm_iters, lambda0=w.lambda0, lm_fp64=mode)
+        ws = torch.empty(cppflow.plan_workspace_size(T, w.K, Kp, n), dtype=torch.uint8, device=dev)
+        sel = torch.empty(T, dtype=torch.int32, device=dev)
+        best = torch.empty(1, device=dev)
+        q = torch.empty(T, n, device=dev)
+        err = torch.empty(T, 2, dtype=torch.float64, device=dev)
+        rep = torch.zeros(cppflow.REPORT_BYTES, dtype=torch.uint8, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        times = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record(st)
+            cppflow.plan(rob, P, cd, tgt, w.K, ws, sel, best, q, err, rep, status, stream=st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        r = cppflow.report_from_bytes(rep.cpu().numpy().tobytes())
+        qs[mode] = q.cpu().numpy()
+        out[name] = {"plan_ms": round(min(times[1:]), 3), "valid": int(r["valid"]),
+                     "max_pos_m": float(r["max_pos"]), "max_rot_deg": math.degrees(r["max_rot"]),
+                     "mjac_rad": float(r["mjac"]), "sum_linf_rad": float(r["sum_linf"]),
+                     "status": int(status.item())}
+    out["max_abs_q_diff_rad"] = float(np.abs(qs[0].astype(np.float64) - qs[1]).max())
+    return out
+
+
 def path_clearance(cppflow, torch, dev, robot, geometry, q, params):
     """Smallest clearance of each configuration of q [T][n] under a collision model,
     from the library's collision mask (the configurations as one-lane lattices)."""
@@ -649,6 +703,7 @@ def run_cuda(args, rank: int, world: int, dist):
 
     uneven = uneven_batch(cppflow, torch, dev, args.uneven) if args.uneven and rank == 0 else None
     coll = collision_leg(cppflow, torch, dev, args.collision) if args.collision and rank == 0 else None
+    stress = stress_leg(cppflow, torch, dev) if args.stress and rank == 0 else None
     mix = None
     if args.serve_rates and rank == 0:
         mix = serving_mix(cppflow, torch, dev, [float(x) for x in args.serve_rates.split(",")],
@@ -674,6 +729,8 @@ def run_cuda(args, rank: int, world: int, dist):
         line["batched_uneven"] = uneven
     if coll is not None:
         line["collision_aware"] = coll
+    if stress is not None:
+        line["stress_precision"] = stress
     if mix is not None:
         line["serving_mix"] = {"workload": "serving mix: T = floor(exp U(ln 50, ln 2000)), "
                                            "K in {128, 256, 512, 1024}, 7-DoF, Poisson arrivals",
@@ -698,6 +755,8 @@ def main():
                     help="requests of the batched uneven leg (0: skip)")
     ap.add_argument("--collision", type=int, default=304,
                     help="requests of the collision-aware leg (0: skip)")
+    ap.add_argument("--stress", type=int, default=1,
+                    help="run the 9-DoF T=2000 K=1024 precision leg (0: skip)")
     ap.add_argument("--serve-rates", default="1000", help="Poisson rates (req/s) of the serving "
                     "mix, comma separated; empty to skip")
     ap.add_argument("--mix-pool", type=int, default=48, help="distinct requests in the mix pool")
