@@ -453,15 +453,16 @@ void cpp_batch_destroy(cpp_batch_t* batch);
  * schedule on `stream`. cpp_batch_tune picks both by measurement on the batch
  * itself: it enqueues the mask and node-cost stages, then times the forward
  * sweep (CUDA events, best of two runs after one warm-up) for alpha = 0 and,
- * for each cands_per_cta in {64, 128}, a ladder of alpha values from 8 down to
- * 1e-9 (every cluster-capable request heavy), skipping values that give the same
- * split, and keeps the fastest; then it times the mask stage the same way for
+ * for each cands_per_cta in {64, 128} and each smallest clustered Kp (any, or
+ * each Kp of the batch above its smallest), a ladder of alpha values from 8 down
+ * to 1e-9 (every cluster-capable request heavy), skipping values that give the
+ * same split, and keeps the fastest; then it times the mask stage the same way for
  * 1, 2, 4, 8 and 16 tasks per warp and keeps the fastest. With a
  * non-NULL table_path the choice is looked up first under a key of the batch's
  * shape (joints, objective, request count and longest T in powers of two,
  * cluster sizes present, skew of the largest lattice over the mean, SM count;
- * plain text, one "key alpha cands_per_cta ms mask_tasks_per_warp" line per
- * entry, the last entry wins; a line without the last field means the default)
+ * plain text, one "key alpha cands_per_cta ms mask_tasks_per_warp min_kp" line
+ * per entry, the last entry wins; missing trailing fields mean the defaults)
  * and, when
  * missing, appended after tuning. The call synchronizes `stream`; the batch's
  * outputs are undefined until its next cpp_batch_run. A new schedule drops any
@@ -478,9 +479,15 @@ typedef struct cpp_tune_result {
     int32_t mask_tasks_per_warp; /* 128-candidate tasks per warp of the mask stage in use */
     float mask_ms;           /* mask stage time of the choice (-1 from the table) */
     float mask_ms_default;   /* mask stage time with 4 tasks per warp (-1 from the table) */
+    int32_t cluster_min_kp;  /* smallest Kp allowed to run as a cluster (0: any) */
+    int32_t reserved;
 } cpp_tune_result_t;
 cpp_status cpp_batch_set_split(cpp_batch_t* batch, double alpha, int32_t cands_per_cta,
                                cpp_stream_t stream);
+/* Smallest Kp that may run as a cluster (0: any): heavier requests of smaller K
+ * then stay one CTA each, longest first. Re-applies the current alpha and
+ * cands_per_cta and uploads the schedule on `stream`. INVALID_ARG if negative. */
+cpp_status cpp_batch_set_cluster_min_kp(cpp_batch_t* batch, int32_t min_kp, cpp_stream_t stream);
 /* Tasks per warp of the mask stage (S1+S2): a task is one waypoint and 128
  * candidates, so a warp covers tasks_per_warp * 128 / Kp waypoints of a request
  * (0: the default, 4). Results do not depend on it. INVALID_ARG outside [0, 64]. */

@@ -110,10 +110,11 @@ class TuneResult(C.Structure):
                 ("forward_launches", C.c_int32), ("timed", C.c_int32), ("from_table", C.c_int32),
                 ("dp_ms", C.c_float), ("dp_ms_unsplit", C.c_float),
                 ("mask_tasks_per_warp", C.c_int32), ("mask_ms", C.c_float),
-                ("mask_ms_default", C.c_float)]
+                ("mask_ms_default", C.c_float), ("cluster_min_kp", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class ServerConfig(C.Structure):
@@ -185,6 +186,7 @@ _SIGS = {
     "cpp_batch_destroy": (None, [_P]),
     "cpp_batch_set_split": (C.c_int, [_P, C.c_double, C.c_int32, _P]),
     "cpp_batch_set_mask_tasks": (C.c_int, [_P, C.c_int32]),
+    "cpp_batch_set_cluster_min_kp": (C.c_int, [_P, C.c_int32, _P]),
     "cpp_batch_tune": (C.c_int, [_P, C.c_char_p, _P, _P]),
     "cpp_batch_capture": (C.c_int, [_P, C.c_uint32, _P]),
     "cpp_batch_replay": (C.c_int, [_P, _P]),
@@ -450,6 +452,10 @@ class Batch:
     def set_split(self, alpha: float, cands_per_cta: int = 0, stream=None):
         _check(lib().cpp_batch_set_split(self.handle, float(alpha), int(cands_per_cta),
                                          stream_handle(stream)), "cpp_batch_set_split")
+
+    def set_cluster_min_kp(self, min_kp: int, stream=None):
+        _check(lib().cpp_batch_set_cluster_min_kp(self.handle, int(min_kp), stream_handle(stream)),
+               "cpp_batch_set_cluster_min_kp")
 
     def set_mask_tasks(self, tasks_per_warp: int):
         _check(lib().cpp_batch_set_mask_tasks(self.handle, int(tasks_per_warp)),

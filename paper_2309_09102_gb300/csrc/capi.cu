@@ -582,6 +582,7 @@ struct cpp_batch {
   double alpha;
   int cpc;  // successor candidates per CTA of the cluster form (0: default)
   int mask_tpw;  // 128-candidate tasks per warp of the mask stage (0: default)
+  int min_kp;    // smallest Kp that may run as a cluster (0: any)
   int heavy;
   cudaStream_t aux[kMaxGroups];
   cudaEvent_t fork, join[kMaxGroups];
@@ -608,7 +609,8 @@ cpp_status set_schedule(cpp_batch* b, double alpha, int cpc, cudaStream_t st) {
   std::vector<int> heavy, light;
   for (int r = 0; r < count; ++r) {
     const bool h =
-        fast_n(b->n) && cluster_size(b->reqs[r].Kp, cpc) > 0 && (double)b->edges[r] >= thr;
+        fast_n(b->n) && cluster_size(b->reqs[r].Kp, cpc) > 0 && (double)b->edges[r] >= thr &&
+        b->reqs[r].Kp >= b->min_kp;
     (h ? heavy : light).push_back(r);
   }
   auto longer = [&](int x, int y) {
@@ -732,9 +734,10 @@ std::string tune_key(const cpp_batch* b) {
   return buf;
 }
 
-// One line per entry: "key alpha cands_per_cta ms [mask_tasks_per_warp]" (the
-// last field absent in older tables: the default); the last entry of a key wins.
-bool table_lookup(const char* path, const std::string& key, double* alpha, int* cpc, int* tpw) {
+// One line per entry: "key alpha cands_per_cta ms [mask_tasks_per_warp [min_kp]]"
+// (fields absent in older tables: the defaults); the last entry of a key wins.
+bool table_lookup(const char* path, const std::string& key, double* alpha, int* cpc, int* tpw,
+                  int* min_kp) {
   if (!path) return false;
   FILE* f = fopen(path, "r");
   if (!f) return false;
@@ -742,12 +745,13 @@ bool table_lookup(const char* path, const std::string& key, double* alpha, int* 
   bool found = false;
   while (fgets(line, sizeof(line), f)) {
     double a, ms;
-    int c, t = 0;
-    const int got = sscanf(line, "%199s %lf %d %lf %d", k, &a, &c, &ms, &t);
+    int c, t = 0, m = 0;
+    const int got = sscanf(line, "%199s %lf %d %lf %d %d", k, &a, &c, &ms, &t, &m);
     if (got < 4 || key != k) continue;
     *alpha = a;
     *cpc = c;
-    *tpw = got == 5 && t >= 1 && t <= 64 ? t : 0;
+    *tpw = got >= 5 && t >= 1 && t <= 64 ? t : 0;
+    *min_kp = got == 6 && m >= 0 ? m : 0;
     found = true;
   }
   fclose(f);
@@ -851,6 +855,7 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
   b->alpha = 0;
   b->cpc = 0;
   b->mask_tpw = 0;
+  b->min_kp = 0;
   b->heavy = 0;
   for (int g = 0; g < kMaxGroups; ++g) { b->aux[g] = nullptr; b->join[g] = nullptr; }
   b->fork = nullptr;
@@ -890,6 +895,13 @@ cpp_status cpp_batch_set_split(cpp_batch_t* b, double alpha, int32_t cands_per_c
   return set_schedule(b, alpha, cands_per_cta, (cudaStream_t)stream);
 }
 
+cpp_status cpp_batch_set_cluster_min_kp(cpp_batch_t* b, int32_t min_kp, cpp_stream_t stream) {
+  if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
+  if (min_kp < 0) return fail(CPP_ERR_INVALID_ARG, "min_kp must be >= 0");
+  b->min_kp = min_kp;
+  return set_schedule(b, b->alpha, b->cpc, (cudaStream_t)stream);
+}
+
 cpp_status cpp_batch_set_mask_tasks(cpp_batch_t* b, int32_t tasks_per_warp) {
   if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
   if (tasks_per_warp < 0 || tasks_per_warp > 64)
@@ -908,8 +920,9 @@ cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t s
   out.dp_ms = out.dp_ms_unsplit = out.mask_ms = out.mask_ms_default = -1.f;
   const std::string key = tune_key(b);
   double alpha = 0;
-  int cpc = 0, tpw = 0;
-  if (table_lookup(table_path, key, &alpha, &cpc, &tpw)) {
+  int cpc = 0, tpw = 0, mk = 0;
+  if (table_lookup(table_path, key, &alpha, &cpc, &tpw, &mk)) {
+    b->min_kp = mk;
     if (cpp_status e = set_schedule(b, alpha, cpc, st)) return e;
     b->mask_tpw = tpw;
     out.from_table = 1;
@@ -918,10 +931,19 @@ cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t s
     if (cpp_status e = run_stages(b, CPP_STAGE_MASK | CPP_STAGE_LAYER_MIN, st)) return e;
     static const double kAlphas[] = {8.0, 4.0, 3.0, 2.0, 1.5, 1.0, 0.75, 0.5,
                                      0.35, 0.25, 0.15, 0.1, 0.05, 1e-9};
-    struct Cand { double alpha; int cpc; };
-    std::vector<Cand> cands{{0.0, 0}};
+    // the smallest Kp that may run as a cluster: any, or each Kp of the batch above
+    // its smallest (long requests of small K then stay one CTA each, longest first)
+    std::vector<int> kps;
+    for (const Req& q : b->reqs) kps.push_back(q.Kp);
+    std::sort(kps.begin(), kps.end());
+    kps.erase(std::unique(kps.begin(), kps.end()), kps.end());
+    std::vector<int> mks{0};
+    for (size_t i = 1; i < kps.size(); ++i) mks.push_back(kps[i]);
+    struct Cand { double alpha; int cpc, mk; };
+    std::vector<Cand> cands{{0.0, 0, 0}};
     for (int c : {64, 128})
-      for (double a : kAlphas) cands.push_back({a, c});
+      for (int m : mks)
+        for (double a : kAlphas) cands.push_back({a, c, m});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cpp_status e = cuda_status(cudaEventCreate(&e0), "cpp_batch_tune")) return e;
     if (cpp_status e = cuda_status(cudaEventCreate(&e1), "cpp_batch_tune")) {
@@ -929,14 +951,17 @@ cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t s
       return e;
     }
     float best_ms = HUGE_VALF;
-    Cand best{0.0, 0};
-    int last_heavy = -1, last_cpc = -1;
+    Cand best{0.0, 0, 0};
+    int last_heavy = -1, last_cpc = -1, last_mk = -1;
     cpp_status err = CPP_OK;
     for (const Cand& c : cands) {
+      b->min_kp = c.mk;
       if ((err = set_schedule(b, c.alpha, c.cpc, st)) != CPP_OK) break;
-      if (b->heavy == last_heavy && c.cpc == last_cpc) continue;  // same split as before
+      // same split as before (the heavy set only grows down the ladder)
+      if (b->heavy == last_heavy && c.cpc == last_cpc && c.mk == last_mk) continue;
       last_heavy = b->heavy;
       last_cpc = c.cpc;
+      last_mk = c.mk;
       if (c.alpha > 0 && b->heavy == 0) continue;                 // same as alpha = 0
       float ms = HUGE_VALF;
       for (int rep = 0; rep < 3 && err == CPP_OK; ++rep) {  // the first run warms up
@@ -983,18 +1008,21 @@ cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t s
     if (err != CPP_OK) return err;
     b->mask_tpw = best_tpw;
     out.mask_ms = best_mask;
+    b->min_kp = best.mk;
     if (cpp_status e = set_schedule(b, best.alpha, best.cpc, st)) return e;
     out.dp_ms = best_ms;
     if (table_path) {
       FILE* f = fopen(table_path, "a");
       if (!f) return fail(CPP_ERR_INVALID_ARG, "cannot append to tuning table %s", table_path);
-      fprintf(f, "%s %.9g %d %.4f %d\n", key.c_str(), best.alpha, best.cpc, best_ms, best_tpw);
+      fprintf(f, "%s %.9g %d %.4f %d %d\n", key.c_str(), best.alpha, best.cpc, best_ms, best_tpw,
+              best.mk);
       fclose(f);
     }
   }
   out.alpha = b->alpha;
   out.cands_per_cta = b->cpc;
   out.mask_tasks_per_warp = b->mask_tpw > 0 ? b->mask_tpw : 4;
+  out.cluster_min_kp = b->min_kp;
   out.heavy = b->heavy;
   out.forward_launches = 0;
   for (const SchedGroup& g : b->groups) out.forward_launches += g.count > 0 ? 1 : 0;

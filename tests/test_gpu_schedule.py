@@ -104,6 +104,13 @@ def test_every_split_gives_the_same_plans_as_the_oracle(batch_setup):
     # the default threshold (the two K = 512, T = 300 requests and a few more run as clusters)
     assert_same(run_with(S, 2.0), base)
     assert_same(run_with(S, 0.5, 128), base)
+    # clusters only for K = 512: K = 256 requests stay one CTA each
+    S["batch"].set_cluster_min_kp(512, S["stream"])
+    try:
+        assert_same(run_with(S, 0.01), base)
+        assert S["batch"].launches(cppflow.STAGE_DP_FORWARD) == 2
+    finally:
+        S["batch"].set_cluster_min_kp(0, S["stream"])
 
 
 def test_graph_replay_equals_run(batch_setup):
@@ -137,20 +144,22 @@ def test_tuner_and_its_table(batch_setup, tmp_path):
     assert 0 < r1["mask_ms"] <= r1["mask_ms_default"]
     lines = table.read_text().split("\n")
     assert len([x for x in lines if x]) == 1
-    key, alpha, cpc, ms, tpw = lines[0].split()
+    key, alpha, cpc, ms, tpw, mk = lines[0].split()
     assert key.startswith("n7_obj0_") and float(alpha) == pytest.approx(r1["alpha"], rel=1e-6)
     assert int(cpc) == r1["cands_per_cta"] and int(tpw) == r1["mask_tasks_per_warp"]
+    assert int(mk) == r1["cluster_min_kp"] and int(mk) in (0, 256, 512)
     after = results_after_run(S)
     r2 = S["batch"].tune(str(table), S["stream"])
     assert r2["from_table"] == 1 and r2["timed"] == 0
     assert r2["alpha"] == pytest.approx(r1["alpha"], rel=1e-6) and r2["heavy"] == r1["heavy"]
     assert r2["mask_tasks_per_warp"] == r1["mask_tasks_per_warp"]
+    assert r2["cluster_min_kp"] == r1["cluster_min_kp"]
     assert_same(results_after_run(S), after)
     assert_same(after, run_with(S, 0.0))
     # an entry written before the mask knob existed (four fields): the default
     table.write_text(f"{key} {alpha} {cpc} {ms}\n")
     r3 = S["batch"].tune(str(table), S["stream"])
-    assert r3["from_table"] == 1 and r3["mask_tasks_per_warp"] == 4
+    assert r3["from_table"] == 1 and r3["mask_tasks_per_warp"] == 4 and r3["cluster_min_kp"] == 0
 
 
 @pytest.mark.parametrize("tpw", [1, 2, 8, 16, 64])
