@@ -166,6 +166,16 @@ const char* cpp_last_error(void);          /* thread-local message of the last f
 const char* cpp_status_string(int status);
 int32_t cpp_version(void);                 /* major * 10000 + minor * 100 + patch */
 void cpp_params_default(cpp_params_t* p);  /* fills the defaults listed above */
+/* Diagnostic (not in the paper): a bounded device wait that nothing completes.
+ * One thread waits up to limit_ns (1e3 .. 1e10) on an mbarrier that never
+ * completes, with the CTA-scope (cluster_scope = 0) or the cluster-scope
+ * (cluster_scope = 1) bounded wait that the search kernels use, and records
+ * CPP_ERR_TIMEOUT in *dev_status (device int32) when the limit runs out: a
+ * stuck wait ends with a status the host reads, the context stays usable.
+ * Asynchronous on `stream`. INVALID_ARG for a limit outside the range or a
+ * NULL status. */
+cpp_status cpp_wait_selftest(int64_t limit_ns, int32_t cluster_scope, int32_t* dev_status,
+                             cpp_stream_t stream);
 
 /* ------------------------------------------------------------------ FK (§II)
  * FK(q): R^n -> SE(3) for N configurations in FP32.

@@ -186,6 +186,7 @@ _SIGS = {
     "cpp_batch_destroy": (None, [_P]),
     "cpp_batch_set_split": (C.c_int, [_P, C.c_double, C.c_int32, _P]),
     "cpp_batch_set_mask_tasks": (C.c_int, [_P, C.c_int32]),
+    "cpp_wait_selftest": (C.c_int, [C.c_int64, C.c_int32, _P, _P]),
     "cpp_batch_set_cluster_min_kp": (C.c_int, [_P, C.c_int32, _P]),
     "cpp_batch_tune": (C.c_int, [_P, C.c_char_p, _P, _P]),
     "cpp_batch_capture": (C.c_int, [_P, C.c_uint32, _P]),
@@ -271,6 +272,12 @@ def make_params(**kw) -> Params:
             raise AttributeError(k)
         setattr(p, k, v)
     return p
+
+
+def wait_selftest(limit_ns: int, cluster_scope: bool, dev_status, stream=None):
+    """A bounded device wait that nothing completes: CPP_ERR_TIMEOUT lands in dev_status."""
+    _check(lib().cpp_wait_selftest(int(limit_ns), 1 if cluster_scope else 0, ptr(dev_status),
+                                   stream_handle(stream)), "cpp_wait_selftest")
 
 
 # ------------------------------------------------------------------ stage calls

@@ -169,6 +169,21 @@ bool make_geo(const cpp_geometry_t& g, int n, void* out, char* err) {
 }
 }  // namespace cppflow
 
+namespace cppflow {
+// One thread initialises an mbarrier that expects one arrival, never arrives,
+// and waits for its first phase with the library's bounded wait; when the limit
+// runs out it records CPP_ERR_TIMEOUT.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, bool cluster_scope, int32_t* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  const bool done = cluster_scope ? mbar_wait_bounded_cluster(&bar, 0, limit_ns)
+                                  : mbar_wait_bounded(&bar, 0, limit_ns);
+  if (!done) raise_status(status, CPP_ERR_TIMEOUT);
+}
+}  // namespace cppflow
+
 extern "C" {
 
 const char* cpp_last_error(void) { return g_err.c_str(); }
@@ -402,6 +417,16 @@ cpp_status cpp_smooth_step_geo(const cpp_robot_t* robot, const cpp_params_t* par
   s.robot = *robot;
   if (cpp_status e = set_geo(s, geometry, robot->n)) return e;
   return cuda_status(launch_smooth(s, *params, (cudaStream_t)stream), "cpp_smooth_step_geo");
+}
+
+cpp_status cpp_wait_selftest(int64_t limit_ns, int32_t cluster_scope, int32_t* dev_status,
+                             cpp_stream_t stream) {
+  if (limit_ns < 1000 || limit_ns > 10000000000LL)
+    return fail(CPP_ERR_INVALID_ARG, "limit_ns must be in [1e3, 1e10]");
+  if (!dev_status) return fail(CPP_ERR_INVALID_ARG, "dev_status is NULL");
+  wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((uint64_t)limit_ns, cluster_scope != 0,
+                                                           dev_status);
+  return cuda_status(cudaGetLastError(), "cpp_wait_selftest");
 }
 
 cpp_status cpp_check(const cpp_robot_t* robot, const cpp_params_t* params, const float* q,
