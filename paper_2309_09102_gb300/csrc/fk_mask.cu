@@ -116,8 +116,11 @@ __device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, co
   cost = coll ? c1 : c0;
 }
 
+// The collision variant is bound by instruction fetch and dependency latency, not
+// registers: four CTAs per SM (64 registers, small spills) measured faster than
+// two (117 registers).
 template <int NJ, bool COLL, class Src>
-__global__ void __launch_bounds__(kMaskThreads) mask_kernel(const __grid_constant__ Src src,
+__global__ void __launch_bounds__(kMaskThreads, COLL ? 4 : 0) mask_kernel(const __grid_constant__ Src src,
                                                              const MaskArgs a) {
   const Req& rq = src.req(blockIdx.y);
   __shared__ RobotF rb;
