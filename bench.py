@@ -12,6 +12,11 @@ resident in HBM. Beside it the script measures, on the same requests:
   * the search kernel's duration (CUDA events on its stream) for the roofline,
   * SM clocks during the timed region (nvidia-smi),
   * the CPU oracle on a bounded sample of the same workload (rank 0 only).
+Further legs on rank 0, each reported beside the headline and not as it: the
+batched uneven workload (tuned schedule, CUDA graph; --uneven), the
+collision-aware workload (--collision), the 9-DoF T = 2000, K = 1024 precision
+case with both LM precisions (--stress) and the serving mix under Poisson
+arrivals (--serve-rates).
 ``--impl reference`` times the CPU oracle alone as the reference arm.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl cuda|reference]
