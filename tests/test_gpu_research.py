@@ -86,7 +86,7 @@ def test_research_with_appended_candidates():
     best = tt.empty(1, dtype=tt.float32, device="cuda:0")
     mj = tt.empty(1, dtype=tt.float32, device="cuda:0")
     st = tt.zeros(1, dtype=tt.int32, device="cuda:0")
-    # round 1: lanes [0, K0)
+    # first search: lanes [0, K0)
     cppflow.mask(rob, cp, cand_d, tg, K0, mask, pen)
     cppflow.dp_search_ex(cand_d, pen, K0, cppflow.DP_MINMAX, ws, sel, best, None, mj, st)
     tt.cuda.synchronize()
@@ -95,7 +95,7 @@ def test_research_with_appended_candidates():
     np.testing.assert_array_equal(sel.cpu().numpy(), ref0["sel"])
     mjac0 = float(mj.item())
     assert mjac0 == np.float32(oracle.path_mjac_f32(pb.cand, ref0["sel"]))
-    # round 2: mask only the appended lanes [K0, K1), keep the first round's costs
+    # re-search: mask only the appended lanes [K0, K1), keep the first search's costs
     cppflow.mask_range(rob, cp, cand_d, tg, K1, K0, mask, pen)
     cppflow.dp_search_ex(cand_d, pen, K1, cppflow.DP_MINMAX, ws, sel, best, None, mj, st)
     tt.cuda.synchronize()
