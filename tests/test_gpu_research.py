@@ -73,7 +73,7 @@ def test_research_with_appended_candidates():
     K0, K1 = 32, 96
     w = synth.Workload("research_T80", 7, 80, K1, 0.08, 0.35, 0.05, 10, arm_seed=21, path_seed=22,
                        cand_seed=23)
-    pb = problems.build(w)          # K1 candidates; the first K0 lanes form the first round
+    pb = problems.build(w)          # K1 candidates; the first K0 lanes form the first search
     T, n, Kp = pb.cand.shape
     _, cp = params_pair()
     rob = cppflow.robot_from_arm(pb.arm)
