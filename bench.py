@@ -652,7 +652,7 @@ def run_cuda(args, rank: int, world: int, dist):
     d2h_per_req = T * 4 + T * n * 4 + T * 16 + cppflow.REPORT_BYTES + 4
     cand_np = [c.numpy() for c in cand_h]     # pinned host memory, borrowed by the server
     targ_np = [t.numpy() for t in targets_h]
-    e2e_steps = max(20, min(args.steps, 40))
+    e2e_steps = max(40, min(args.steps, 80))  # fill and drain of the pipeline amortised
     lat = []
     e2e_valid = 0
 
