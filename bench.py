@@ -570,6 +570,9 @@ def run_cuda(args, rank: int, world: int, dist):
     ws = torch.empty(cppflow.plan_batch_workspace_size(descs, robots), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     batch = cppflow.Batch(robots, P, descs, ws, status, stream)
+    # the library's autotuner, once, before the warm-up (a user's setup step): the search
+    # split and the mask stage's tasks per warp for this batch
+    tuned = batch.tune(None, stream)
     launches_per_step = batch.launches(cppflow.STAGE_ALL)
 
     def barrier():
@@ -720,7 +723,9 @@ def run_cuda(args, rank: int, world: int, dist):
             "config": {"workload": synth.SINGLE.name, "T": T, "K": K, "n": n,
                        "requests_per_step": B, "per_gpu_requests": B,
                        "l2": f"inputs larger than L2 ({B * T * n * Kp * 4 / 1e6:.0f} MB lattice per step)",
-                       "lm_iters": P.lm_iters, "parallelism": f"replicas x{world}"},
+                       "lm_iters": P.lm_iters, "parallelism": f"replicas x{world}",
+                       "tuned": {"heavy": tuned["heavy"], "alpha": round(tuned["alpha"], 4),
+                                 "mask_tasks_per_warp": tuned["mask_tasks_per_warp"]}},
             "p99_ms": round(ms_per_step, 4),
             "stage_ms": {"mask_and_layer_min": round(statistics.mean(pre_ms), 4),
                          "dp_forward": round(statistics.mean(dp_ms), 4),
