@@ -4,7 +4,6 @@ that nothing completes (the flag that nobody sets) runs out after a short limit,
 CTA-scope and the cluster-scope waits the search kernels use; the context stays usable."""
 import time
 
-import numpy as np
 import pytest
 
 import problems

@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 import problems
-from gpu_util import dev, params_pair, run_dp, run_dp_ex, run_mask, torch
+from gpu_util import dev, params_pair, run_dp_ex, run_mask, torch
 from paper_2309_09102_gb300 import cppflow, synth
 
 pytestmark = pytest.mark.gpu

@@ -5,7 +5,6 @@ timing reduction of the benchmark, and the per-rank request sets must be disjoin
 import os
 import socket
 
-import pytest
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
