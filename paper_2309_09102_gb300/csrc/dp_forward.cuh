@@ -91,7 +91,7 @@ inline size_t dp3_smem_bytes(int nj, int Kp, int R) {
   return (size_t)rec_layer_floats(NW, Kp) * 4  // records
          + (size_t)nj * Kp * 4                  // raw layer staging
          + (size_t)Kp * 4                       // node-cost staging
-         + (size_t)3 * R * kDp3Group * 4        // group exchange: min, tile, index
+         + (size_t)4 * R * kDp3Group * 4        // group exchange: min, tile per group
          + 64;                                  // barrier
 }
 
@@ -126,10 +126,9 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __gri
   float* const rec = sm3;                                   // [RL] records (skewed)
   float* const stg = rec + RL;                              // [NJ][Kp] staged layer
   float* const pst = stg + (size_t)NJ * Kp;                 // [Kp] staged node costs
-  float* const xmin = pst + Kp;                             // [R][128]
-  int* const xtile = reinterpret_cast<int*>(xmin + R * kDp3Group);  // [R][128]
-  int* const xarg = xtile + R * kDp3Group;                  // [R][128]
-  uint64_t* const bar = reinterpret_cast<uint64_t*>(xarg + R * kDp3Group);
+  float* const xmin = pst + Kp;                             // [2][R][128]
+  int* const xtile = reinterpret_cast<int*>(xmin + 2 * R * kDp3Group);  // [2][R][128]
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(xtile + 2 * R * kDp3Group);
   __shared__ int timeout_flag;
 
   const uint32_t layer_bytes = (uint32_t)(NJ * Kp * 4), pen_bytes = (uint32_t)(Kp * 4);
@@ -198,7 +197,9 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __gri
       }
       rpen[r] = kp[r] < K ? pst[kp[r]] - m1 : CUDART_INF_F;
     }
-    __syncthreads();  // everyone holds its layer-L values: the staging buffer is free
+    // everyone holds its layer-L values (the staging buffer is free) and the
+    // previous step's records are complete
+    __syncthreads();
     if (timeout_flag) {
       raise_status(rq.status, CPP_ERR_TIMEOUT);
       if (tid == 0) wait_layer(L);
@@ -240,29 +241,27 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __gri
       for (int r = 0; r < R; ++r)
         if (tb[r] < best[r]) { best[r] = tb[r]; btile[r] = t; }
     }
-    // merge the halves: the upper half (larger k) replaces only a strictly smaller minimum
-    if (g == 1) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) { xmin[r * kDp3Group + lt] = best[r]; xtile[r * kDp3Group + lt] = btile[r]; }
-    }
-    __syncthreads();
-    if (g == 0) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float b1 = xmin[r * kDp3Group + lt];
-        const int t1 = xtile[r * kDp3Group + lt];
-        if (b1 < best[r]) { best[r] = b1; btile[r] = t1; }
-        xmin[r * kDp3Group + lt] = best[r];
-        xtile[r * kDp3Group + lt] = btile[r];
-      }
-    }
-    __syncthreads();
-    // rescans: successor r is handled by group r % 2 (group 0 when R == 1)
+    // both halves publish their (minimum, tile); successor r is finished by group r % 2
+    // (group 0 when R == 1), which merges the halves -- the upper half (larger k)
+    // replaces only a strictly smaller minimum, so the lowest index still wins --
+    // and rescans the winning tile
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+      xmin[(g * R + r) * kDp3Group + lt] = best[r];
+      xtile[(g * R + r) * kDp3Group + lt] = btile[r];
+    }
+    __syncthreads();
+    float mv[R];
+    int ma[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      mv[r] = 0.f;
+      ma[r] = 0;
       if ((R == 1 ? 0 : (r & 1)) != g) continue;
-      const float bv = xmin[r * kDp3Group + lt];
-      const int bt = xtile[r * kDp3Group + lt];
+      float bv = xmin[r * kDp3Group + lt];
+      int bt = xtile[r * kDp3Group + lt];
+      const float b1 = xmin[(R + r) * kDp3Group + lt];
+      if (b1 < bv) { bv = b1; bt = xtile[(R + r) * kDp3Group + lt]; }
       int arg = 0;
       if (bt >= 0) {
         const int kb = bt * kDp2Tile, ke = min(kb + kDp2Tile, K4);
@@ -272,7 +271,8 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __gri
           if (comb<OBJ>(rk[NJ], linf_rec<NJ>(own[r], rk)) == bv) { arg = k; break; }
         }
       }
-      xarg[r * kDp3Group + lt] = arg;
+      mv[r] = bv;
+      ma[r] = arg;
     }
     __syncthreads();  // rescans done: the records may be replaced
     uint16_t* bprow = rq.bp + (size_t)L * Kb;
@@ -287,16 +287,17 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __gri
         v[2 * p] = -a;
         if (2 * p + 1 < NJ) v[2 * p + 1] = -b;
       }
-      v[NJ] = kp[r] < K ? comb<OBJ>(xmin[r * kDp3Group + lt], rpen[r]) : CUDART_INF_F;
+      v[NJ] = kp[r] < K ? comb<OBJ>(mv[r], rpen[r]) : CUDART_INF_F;
 #pragma unroll
       for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
       float4* dst = reinterpret_cast<float4*>(rec + rec_off(NW, kp[r]));
 #pragma unroll
       for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
-      bprow[kp[r]] = (uint16_t)xarg[r * kDp3Group + lt];
+      bprow[kp[r]] = (uint16_t)ma[r];
     }
-    __syncthreads();
+    // the next step's first barrier orders these records before its sweep
   }
+  __syncthreads();
   for (int k = tid; k < Kp; k += kDp3Threads) rq.costT[k] = rec[rec_off(NW, k) + NJ];
 }
 
