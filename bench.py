@@ -49,7 +49,7 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one dp3_forward_kernel launch on this workload (304 requests,
 # T = 300, K = 512, n = 7), from one ncu capture of the current kernel build
 # (profiles/dp3_forward_single_t300_k512_b304.md); None once the kernel changes.
-DP3_TRAFFIC_BYTES = 1.498145e9 + 92.664576e6
+DP3_TRAFFIC_BYTES = 1.496150e9 + 91.826176e6
 
 
 def workload_requests(B: int, rank: int):
