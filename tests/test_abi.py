@@ -57,6 +57,21 @@ def test_host_only_calls(lib):
                                    None) == cppflow.ERR_INVALID_ARG
 
 
+def test_diagnostics_and_batch_knobs_are_validated_on_the_host(lib):
+    """Bad arguments of the bounded-wait self-test and of the batch schedule knobs are
+    refused before any device work."""
+    from paper_2309_09102_gb300 import cppflow
+    L = cppflow.lib()
+    dummy = ctypes.c_void_p(8)  # never dereferenced: the limit is checked first
+    assert L.cpp_wait_selftest(10, 0, dummy, None) == cppflow.ERR_INVALID_ARG
+    assert "limit" in cppflow.last_error()
+    assert L.cpp_wait_selftest(2 * 10 ** 10, 1, dummy, None) == cppflow.ERR_INVALID_ARG
+    assert L.cpp_wait_selftest(10 ** 6, 0, None, None) == cppflow.ERR_INVALID_ARG
+    assert L.cpp_batch_set_mask_tasks(None, 4) == cppflow.ERR_INVALID_ARG
+    assert L.cpp_batch_set_cluster_min_kp(None, 512, None) == cppflow.ERR_INVALID_ARG
+    assert L.cpp_batch_set_split(None, 1.0, 64, None) == cppflow.ERR_INVALID_ARG
+
+
 def test_smoothing_params_are_validated_on_the_host(lib):
     """smooth_lambda must be positive, smooth_rounds within [0, 1000], and the
     trajectory-length step's (n + 1) T doubles must fit in shared memory; every
