@@ -116,11 +116,13 @@ __device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, co
   cost = coll ? c1 : c0;
 }
 
-// The collision variant is bound by instruction fetch and dependency latency, not
-// registers: four CTAs per SM (64 registers, small spills) measured faster than
-// two (117 registers).
+// Both variants are bound by issue and dependency latency rather than registers:
+// more resident warps measured faster -- three CTAs per SM for the plain mask (80
+// registers, a few spills; 0.86 -> 0.81 ms with the layer minima on the 304-request
+// batch, four measured slower) and four for the collision variant (64 registers;
+// two at 117 registers were 1.1 ms slower per batch).
 template <int NJ, bool COLL, class Src>
-__global__ void __launch_bounds__(kMaskThreads, COLL ? 4 : 0) mask_kernel(const __grid_constant__ Src src,
+__global__ void __launch_bounds__(kMaskThreads, COLL ? 4 : 3) mask_kernel(const __grid_constant__ Src src,
                                                              const MaskArgs a) {
   const Req& rq = src.req(blockIdx.y);
   __shared__ RobotF rb;
