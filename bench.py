@@ -24,6 +24,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl c
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -246,7 +247,10 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_
             done = start + service[k]
             plat.append(done - a)
         plain_span = done - arr[0]
-        # served: real-time open-loop submission
+        # served: real-time open-loop submission (Python's cyclic collector is run before
+        # and paused during the loop, so no collection pause delays the arrivals)
+        gc.collect()
+        gc.disable()
         with cppflow.Server(P, device=dev.index or 0, hbm_budget=40 << 30, max_batch=512,
                             max_inflight=16, pinned_bytes=64 << 20) as srv:
             t0 = time.perf_counter()
@@ -266,6 +270,7 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_
                 valid += int(res["report"]["valid"])
             span = time.perf_counter() - t0
             ss = srv.stats()
+        gc.enable()
         drop = count // 10
 
         def pct(v, q):
@@ -666,6 +671,8 @@ def run_cuda(args, rank: int, world: int, dist):
     # The client keeps two steps in flight (it submits step s + 1 before it waits for the
     # results of step s), as a serving front end would; every step's H2D copies, batching,
     # kernels and D2H copies lie inside the timed region.
+    gc.collect()
+    gc.disable()  # no collection pause inside the timed client loop
     with cppflow.Server(P, device=local, hbm_budget=2 * int(B * 6.5e6) + (256 << 20),
                         max_batch=args.serve_batch, max_inflight=args.serve_inflight,
                         pinned_bytes=64 << 20) as srv:
@@ -681,6 +688,7 @@ def run_cuda(args, rank: int, world: int, dist):
             pending = nxt
         e2e_total = time.perf_counter() - t0
         sstats = srv.stats()
+    gc.enable()
     lat.sort()
     e2e = {"value": round(world * B * e2e_steps / e2e_total, 3), "unit": "plans/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(B * d2h_per_req),
