@@ -265,10 +265,10 @@ cpp_status cpp_dp_search(const float* cand, const float* pen, int32_t T, int32_t
 
 /* ------------------------------------------------------------------ search without allocation
  * The paper has no counterpart to this entry point; it exists for callers that
- * cannot allocate device memory when they plan: code between stream-capture
- * begin and end (a plain cudaMalloc breaks the capture), real-time loops that
- * forbid allocation after start-up, and plug-ins whose host application owns
- * every device allocation. It computes exactly what cpp_dp_search computes, but
+ * cannot allocate device memory when they plan: real-time control loops that
+ * forbid allocation after start-up (an allocation can block for an unbounded
+ * time), and plug-ins whose host application owns every device allocation. It
+ * computes exactly what cpp_dp_search computes, but
  * its scratch (layer minima, backpointers, final costs) lives in one
  * file-scope device array of CPP_DP_STATIC_SCRATCH_BYTES inside the library.
  * That array is reserved on every GPU that loads the library and held until the
@@ -283,8 +283,11 @@ cpp_status cpp_dp_search(const float* cand, const float* pen, int32_t T, int32_t
  * before any stream capture. Every call uses the same array and leaves its
  * contents behind, so calls that overlap on the GPU (other streams, other host
  * threads) race with each other. Each call writes every scratch word it reads,
- * so nothing needs clearing between calls. Arguments, layouts and errors
- * otherwise as cpp_dp_search. */
+ * so nothing needs clearing between calls (after a CPP_ERR_TIMEOUT the unfinished
+ * rows keep older values; the backtracking clamps what it reads from them to
+ * [0, K)). The cached address does not survive a device reset (cudaDeviceReset
+ * or a primary-context reset): do not call this entry point on a device after
+ * resetting it. Arguments, layouts and errors otherwise as cpp_dp_search. */
 #define CPP_DP_STATIC_SCRATCH_BYTES (8u << 20)
 cpp_status cpp_dp_search_static(const float* cand, const float* pen, int32_t T, int32_t K,
                                 int32_t Kp, int32_t n, int32_t* sel, float* best_cost,

@@ -131,13 +131,19 @@ __global__ void __launch_bounds__(kBtThreads) dp_backtrack_kernel(const __grid_c
       if (!mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1))) {
         raise_status(rq.status, CPP_ERR_TIMEOUT);
         ok = false;
+        // both copies in flight (chunks c and c + 1) must land before the CTA
+        // leaves: wait for each once more, again with a limit
+        mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1));
         if (chunk_hi(c + 1) >= 1) mbar_wait_bounded(&bars[(c + 1) & 1], (uint32_t)(((c + 1) >> 1) & 1));
         break;
       }
       const int hi = chunk_hi(c), lo = max(1, hi - L + 1);
       const uint16_t* b = (c & 1) ? buf1 : buf0;
+      // Every stored backpointer is below K. Rows a timed-out forward sweep never
+      // wrote hold stale values, so the walk clamps each step to [0, K) and can
+      // never leave the staged rows or the candidate lanes.
       for (int row = hi; row >= lo; --row) {
-        k = b[(size_t)(row - lo) * Kb + k];
+        k = min((int)b[(size_t)(row - lo) * Kb + k], K - 1);
         rq.sel[row - 1] = k;
       }
       // the buffer was read through the generic proxy; order those reads before

@@ -3,10 +3,10 @@
 // cpp_dp_search needs device scratch (per-waypoint cost minima, the T x Kb
 // backpointer table and the final cost row) that its caller allocates and
 // passes in. Some callers cannot call cudaMalloc, or any allocating routine,
-// at the point where they plan: code running between stream-capture begin and
-// end (a plain cudaMalloc breaks a capture), hard real-time control loops that
-// forbid allocation after start-up, and plug-ins whose host application owns
-// every device allocation. cpp_dp_search_static serves them from one
+// at the point where they plan: hard real-time control loops that forbid
+// allocation after start-up (an allocation can block for an unbounded time),
+// and plug-ins whose host application owns every device allocation and gives
+// them none of their own. cpp_dp_search_static serves them from one
 // fixed-size scratch array that lives in this library's device image: it is
 // reserved when the library is loaded on a device and held until the process
 // exits, and the call itself allocates nothing.
@@ -15,7 +15,10 @@
 // not a device address; passing it to a kernel would fault (or, where the GPU
 // can reach host memory, silently touch the wrong memory). The device address
 // is therefore looked up once per device, with that device current, through
-// cudaGetSymbolAddress, and cached.
+// cudaGetSymbolAddress, and cached. The cache does not survive a reset of the
+// device (cudaDeviceReset, or a reset of its primary context): the cached
+// address then points into a context that no longer exists, so a process that
+// resets a device must not call this entry point on it afterwards.
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -91,7 +94,10 @@ cpp_status cpp_dp_search_static(const float* cand, const float* pen, int32_t T, 
                   cudaGetErrorString(e));
   // Every scratch word the kernels read is written earlier in the same call
   // (layer minima, all Kp backpointers of rows 1..T-1, the final cost row), so
-  // nothing left over from a previous call is ever used and nothing is cleared.
+  // nothing left over from a previous call is used and nothing is cleared. The
+  // one exception is a forward sweep that gives up on a bounded wait (status
+  // CPP_ERR_TIMEOUT): the rows after that step keep an earlier call's values,
+  // and the backtracking clamps every index it reads from them to [0, K).
   char* ws = static_cast<char*>(base);
   SingleSrc s;
   memset(&s, 0, sizeof(s));

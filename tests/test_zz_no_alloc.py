@@ -1,11 +1,13 @@
 """The allocation-free search entry point gives what the workspace one gives.
 
 Some callers of this library cannot allocate device memory at the moment they
-plan -- code between stream-capture begin and end, real-time loops that forbid
-allocation after start-up, plug-ins whose host application owns every
-allocation. cpp_dp_search_static serves them from a fixed scratch array inside
-the library. This file calls it through the C ABI on two different lattices in
-a row (the second call reuses the scratch the first one left behind) and checks
+plan -- real-time control loops that forbid allocation after start-up (an
+allocation can block for an unbounded time), plug-ins whose host application
+owns every allocation. cpp_dp_search_static serves them from a fixed scratch
+array inside the library. This file calls it through the C ABI on lattices of
+different sizes in a row, small then large then small again (each call reuses
+the scratch the one before left behind, and the last one finds rows beyond its
+own lattice filled by a larger one), and checks
 each result against cpp_dp_search run with its own workspace: the search is
 exact, so indices, cost and seed must be identical. It also checks that a
 lattice larger than the scratch is refused with a clear message.
@@ -44,7 +46,7 @@ def test_static_scratch_matches_workspace_search():
     fn = _static_entry()
     dev = "cuda:0"
     stream = torch.cuda.current_stream().cuda_stream or None
-    for T, K, n, seed in [(40, 300, 7, 1), (25, 130, 9, 2)]:
+    for T, K, n, seed in [(25, 130, 9, 2), (40, 300, 7, 1), (30, 200, 7, 3)]:
         cand, pen, Kp = _lattice(T, K, n, seed)
         c_d = torch.from_numpy(cand).to(dev)
         p_d = torch.from_numpy(pen).to(dev)
