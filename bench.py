@@ -1,22 +1,25 @@
-"""Benchmark of the GB300 planner core: served plans/s on the T = 300, K = 512,
-7-DoF workload (the single-request-at-scale configuration), batched.
+"""Benchmark of the GB300 planner core on the T = 300, K = 512, 7-DoF workload (the
+single-request-at-scale configuration).
 
-One step = one pass of the whole path (FK + masks, search, backtracking, LM,
-FP64 check) over one batch of B synthetic requests of that shape, inputs
-resident in HBM. Beside it the script measures, on the same requests:
-  * the plain per-request GPU path (cpp_plan one request at a time, one stream):
-    plans/s and p50 / p99 latency,
-  * end to end through the serving API (cpp_plan_submit / cpp_plan_wait): host
-    inputs copied in, continuous batching, results copied out to host memory,
-    all inside the timed region, with per-request p50 / p99 latency,
-  * the search kernel's duration (CUDA events on its stream) for the roofline,
+The headline `value` is plans/s of the batched path with its inputs resident in HBM:
+one step = one pass of the whole path (FK + masks, search, backtracking, LM, FP64
+check) over one batch of B synthetic requests of that shape. `e2e` is the same metric
+served end to end through the serving API (cpp_plan_submit / cpp_plan_wait): host
+inputs copied in, continuous batching, results copied out, all inside the timed
+region. Beside them, on rank 0:
+  * the plain per-request GPU path (cpp_plan one request at a time, one stream),
+  * the roofline of the search kernel (FP32 lane operations) and of the LM kernel
+    (FP64 flops) against peaks measured in the same run by the library's
+    throughput probe,
   * SM clocks during the timed region (nvidia-smi),
-  * the CPU oracle on a bounded sample of the same workload (rank 0 only).
-Further legs on rank 0, each reported beside the headline and not as it: the
-batched uneven workload (tuned schedule, CUDA graph; --uneven), the
-collision-aware workload (--collision), the 9-DoF T = 2000, K = 1024 precision
-case with both LM precisions (--stress) and the serving mix under Poisson
-arrivals (--serve-rates).
+  * the serving mix under open-loop Poisson arrivals at 100, 1000 and 5000 req/s:
+    served (continuous batching) and plain (the same arrival trace, in real time,
+    one request at a time through cpp_plan_host) -- plans/s, p50 / p99 latency,
+  * the batched uneven workload (tuned schedule, CUDA graph), the collision-aware
+    workload, the 9-DoF T = 2000, K = 1024 precision case with both LM precisions,
+  * the CPU-oracle leg: the FP64 oracle timed on the host's cores on a bounded
+    sample of the workload (the same inputs as the GPU's first requests), with the
+    GPU results of those requests and of the precision case compared against it.
 ``--impl reference`` times the CPU oracle alone as the reference arm.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl cuda|reference]
@@ -43,14 +46,23 @@ if ROOT not in sys.path:
 
 from paper_2309_09102_gb300 import synth  # noqa: E402
 
-METRIC = "served plans/s, T=300 K=512 7-DoF, valid at <=1mm/<=0.1deg"
-SMS = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+METRIC = "served plans/s & p99 latency at \u22641mm/\u22640.1\u00b0 vs plain per-request GPU path"
+VALUE_IS = ("plans/s of the batched path, inputs resident in HBM (T=300 K=512 7-DoF, valid at "
+            "<=1mm/<=0.1deg); e2e = the same through the serving API from host memory; the "
+            "served-vs-plain comparison under Poisson arrivals is in serving_mix")
 # DRAM bytes (read + write) of one dp3_forward_kernel launch on this workload (304 requests,
-# T = 300, K = 512, n = 7), from one ncu capture of the current kernel build
-# (profiles/dp3_forward_single_t300_k512_b304.md); None once the kernel changes.
+# T = 300, K = 512, n = 7), from one ncu capture of the kernel build it names
+# (profiles/dp3_forward_single_t300_k512_b304.md). Set to None whenever the kernel changes.
 DP3_TRAFFIC_BYTES = 1.496150e9 + 91.826176e6
+
+
+def lm_flops_per_iter(n: int) -> int:
+    """FP64 flops of one LM iteration of one waypoint (FP32 Jacobian mode): J^T J lower
+    triangle 6 n (n + 1), J^T e 12 n, lambda on the diagonal n, Cholesky sum_j [2 j + 2 +
+    (n - 1 - j)(2 j + 1)], two triangular solves 2 n^2, the step n, the trial cost 12
+    (691 at n = 7). FP32 work (chains, Jacobian columns) is not counted."""
+    chol = sum(2 * j + 2 + (n - 1 - j) * (2 * j + 1) for j in range(n))
+    return 6 * n * (n + 1) + 12 * n + n + chol + 2 * n * n + n + 12
 
 
 def workload_requests(B: int, rank: int):
@@ -124,47 +136,88 @@ def oracle_problem(w: synth.Workload):
     return rob, targets, cand
 
 
-def cpu_oracle_run(reqs, threads: int, steps: int = 1):
+def cpu_oracle_run(reqs, threads: int, steps: int = 1, probs=None):
     """Time the oracle (mask, FP32 search, LM, check) on `reqs`, one request per thread
-    (the C oracle releases the GIL), `steps` times. Returns (plans/s, valid, seconds)."""
+    (the C oracle releases the GIL), `steps` times. probs: the inputs (robot, targets,
+    lattice) per request, else built with the oracle. Returns (plans/s, valid, seconds,
+    results of the last step)."""
     import oracle
     oracle.build()
-    with ThreadPoolExecutor(max_workers=threads) as ex:
-        probs = list(ex.map(oracle_problem, reqs))
+    if probs is None:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            probs = list(ex.map(oracle_problem, reqs))
     P = oracle.make_params(lm_iters=reqs[0].lm_iters, lambda0=reqs[0].lambda0)
 
     def one(i):
         rob, targets, cand = probs[i]
-        return oracle.plan(rob, P, cand, targets, reqs[i].K)["report"]["valid"]
+        return oracle.plan(rob, P, cand, targets, reqs[i].K)
 
     t0 = time.perf_counter()
     valid = 0
+    outs = []
     with ThreadPoolExecutor(max_workers=threads) as ex:
         for _ in range(steps):
-            valid += sum(ex.map(one, range(len(probs))))
+            outs = list(ex.map(one, range(len(probs))))
+            valid += sum(o["report"]["valid"] for o in outs)
     dt = time.perf_counter() - t0
-    return len(probs) * steps / dt, valid, dt
+    return len(probs) * steps / dt, valid, dt, outs
 
 
-def cpu_baseline(rank: int, per_core: int = 4) -> dict:
+def oracle_leg(arms, reqs, cand_h, targets_h, gpu, stress, per_core: int = 4) -> dict:
+    """The CPU-oracle leg (rank 0 at N = 1). (1) The FP64 oracle plans the first
+    cores * per_core requests of the batch on the GPU's own inputs, one request per host
+    thread on every core, timed: the CPU baseline. Its results are compared with the
+    GPU's for the same requests: search indices, refined joints, mjac. (2) The precision
+    case: the oracle's LM from the GPU search's seed, compared with both GPU LM modes."""
+    import oracle
     cores = os.cpu_count() or 1
-    S = max(1, min(cores, 16))
-    reqs = workload_requests(S * per_core, 0)
-    value, valid, dt = cpu_oracle_run(reqs, S)
-    return {"value": round(value, 3), "unit": "plans/s", "cores": S, "kind": "oracle",
-            "sample": f"{len(reqs)} requests of T=300 K=512 n=7 (mask + FP32 search + FP64 LM + "
-                      f"check) on {S} threads, {dt:.1f} s wall (~{dt * S:.0f} s of CPU work)",
-            "valid": int(valid)}
+    S = cores
+    m = min(len(reqs), S * per_core)
+    probs = []
+    for r in range(m):
+        a = arms[reqs[r].arm_seed - 100]
+        probs.append((oracle.make_robot(a.a, a.d, a.alpha, a.lo, a.hi, a.theta0),
+                      targets_h[r].numpy(), cand_h[r].numpy()))
+    value, valid, dt, outs = cpu_oracle_run(reqs[:m], S, probs=probs)
+    same_sel = sum(int(np.array_equal(o["sel"], gpu["sel"][r])) for r, o in enumerate(outs))
+    dq = max(float(np.abs(gpu["q"][r].astype(np.float64) - o["q"]).max()) for r, o in enumerate(outs))
+    dmjac = max(abs(gpu["mjac"][r] - o["report"]["mjac"]) for r, o in enumerate(outs))
+    base = {"value": round(value, 3), "unit": "plans/s", "cores": S, "host_cpu_count": cores,
+            "kind": "oracle",
+            "sample": f"{m} requests of T=300 K=512 n=7 (the GPU batch's first {m}, same inputs; "
+                      f"mask + FP32 search + FP64 LM + check) on {S} threads, {dt:.1f} s wall "
+                      f"(~{dt * S:.0f} s of CPU work)",
+            "valid": int(valid),
+            "vs_gpu": {"requests": m, "identical_search_indices": f"{same_sel}/{m}",
+                       "max_abs_q_diff_rad": dq, "max_abs_mjac_diff_rad": dmjac,
+                       "gpu_max_pos_err_m": max(gpu["max_pos"][:m]),
+                       "gpu_max_rot_err_deg": math.degrees(max(gpu["max_rot"][:m]))}}
+    st = None
+    if stress is not None:
+        rob = oracle.make_robot(*stress["arm"])
+        P = oracle.make_params(lm_iters=stress["lm_iters"], lambda0=stress["lambda0"])
+        t0 = time.perf_counter()
+        q_o, _, iters = oracle.lm(rob, P, stress["seed"], stress["targets"])
+        t_lm = time.perf_counter() - t0
+        err_o, rep_o = oracle.check(rob, P, q_o, stress["targets"])
+        st = {"oracle_lm_s": round(t_lm, 2), "oracle_max_pos_m": float(err_o[:, 0].max()),
+              "oracle_max_rot_deg": math.degrees(float(err_o[:, 1].max())),
+              "oracle_mjac_rad": float(rep_o["mjac"]), "oracle_valid": int(rep_o["valid"]),
+              "oracle_mean_lm_iters": round(float(iters.mean()), 2)}
+        for name, q in stress["q"].items():
+            st[name] = {"max_abs_q_diff_rad": float(np.abs(q.astype(np.float64) - q_o).max()),
+                        "abs_mjac_diff_rad": abs(stress["mjac"][name] - float(rep_o["mjac"]))}
+    return {"cpu_baseline": base, "stress_vs_oracle": st}
 
 
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
     cores = os.cpu_count() or 1
-    S = max(1, min(cores, 16))
+    S = cores
     reqs = workload_requests(S, 0)
     cpu_oracle_run(reqs[:1], 1)  # warm the library
-    value, valid, dt = cpu_oracle_run(reqs, S, steps=args.steps)
+    value, valid, dt, _ = cpu_oracle_run(reqs, S, steps=args.steps)
     line = {"metric": METRIC, "value": round(value, 3), "unit": "plans/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1000 * dt / args.steps, 3), "higher_is_better": True,
@@ -173,7 +226,7 @@ def run_reference(args, rank: int, world: int):
             "config": {"workload": synth.SINGLE.name, "T": 300, "K": 512, "n": 7,
                        "requests_per_step": S},
             "cpu_baseline": {"value": round(value, 3), "unit": "plans/s", "cores": S,
-                             "kind": "oracle",
+                             "host_cpu_count": cores, "kind": "oracle",
                              "sample": f"{S} requests per step, one per thread"},
             "e2e": {"value": round(value, 3), "unit": "plans/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -181,74 +234,96 @@ def run_reference(args, rank: int, world: int):
 
 
 # ----------------------------------------------------------------------------- serving mix
-def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_requests: int):
-    """Open-loop Poisson arrivals of the serving mix (T = floor(exp U(ln 50, ln 2000)),
-    K in {128, 256, 512, 1024}, 7-DoF arms), drawn with replacement from a pool of
-    distinct requests. Served: real-time submission to cpp_plan_submit, latency =
-    arrival -> completion. Plain: the same arrivals through one stream, one request at
-    a time (cpp_plan), as a FIFO queue fed by each request's measured GPU service
-    time. The first 10 % of requests are dropped as warm-up."""
+def serving_pool(cppflow, torch, dev, pool_size: int):
+    """pool_size distinct requests of the serving mix (T = floor(exp U(ln 50, ln 2000)),
+    K in {128, 256, 512, 1024}, 7-DoF arms r mod 8): target poses by the library's FP64
+    FK and wrong-branch solutions by its FP64 LM on the GPU, random draws and assembly
+    on the host threads, every lattice in one pinned host buffer."""
     n = 7
-    pool = []
-    P = cppflow.make_params()
-    P_wb = cppflow.make_params(lm_iters=30, lm_fp64=1, free_mask=synth.wrong_branch_free_mask(n))
     arms = [synth.draw_arm(100 + k, n) for k in range(8)]
     robots = [cppflow.robot_from_arm(a) for a in arms]
-
-    def draw(r):
-        w = synth.serving_request(r)
-        truth = synth.draw_truth(w.path_seed, n, w.T)
-        return w, truth, synth.draw_candidates(w.cand_seed, w.T, w.K, n, w.p_wb, w.p_out)
-
-    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
-        drawn = list(ex.map(draw, range(pool_size)))
-    for w, truth, d in drawn:
+    P_wb = cppflow.make_params(lm_iters=30, lm_fp64=1, free_mask=synth.wrong_branch_free_mask(n))
+    ws = [synth.serving_request(r) for r in range(pool_size)]
+    threads = os.cpu_count() or 1
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        truths = list(ex.map(lambda w: synth.draw_truth(w.path_seed, n, w.T), ws))
+    targets, qwb = [], []
+    for w, truth in zip(ws, truths):
         rob = robots[w.arm_seed - 100]
         tgt = torch.empty(w.T, 7, dtype=torch.float64, device=dev)
         cppflow.fk_pose_f64(rob, torch.from_numpy(truth).to(dev), tgt)
-        qwb = torch.empty(w.T, n, dtype=torch.float32, device=dev)
-        cppflow.lm_refine(rob, P_wb, torch.from_numpy(synth.wrong_branch_start(truth).astype(np.float32)).to(dev),
-                          tgt, qwb)
-        torch.cuda.synchronize()
+        q = torch.empty(w.T, n, dtype=torch.float32, device=dev)
+        cppflow.lm_refine(rob, P_wb, torch.from_numpy(
+            synth.wrong_branch_start(truth).astype(np.float32)).to(dev), tgt, q)
+        targets.append(tgt)
+        qwb.append(q)
+    torch.cuda.synchronize()
+    sizes = [w.T * n * synth.pad_k(w.K) for w in ws]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    big = torch.empty(int(offs[-1]), dtype=torch.float32, pin_memory=True)
+    bnp = big.numpy()
+    tsz = [w.T * 7 for w in ws]
+    toffs = np.concatenate([[0], np.cumsum(tsz)])
+    tbig = torch.empty(int(toffs[-1]), dtype=torch.float64, pin_memory=True)
+    tnp = tbig.numpy()
+    qwb_h = [q.cpu().numpy().astype(np.float64) for q in qwb]
+    for r in range(pool_size):
+        tnp[toffs[r]:toffs[r + 1]] = targets[r].cpu().numpy().ravel()
+
+    def fill(r):
+        w = ws[r]
         arm = arms[w.arm_seed - 100]
-        cand = synth.assemble(truth, qwb.cpu().numpy().astype(np.float64), d, w.sigma, arm.lo, arm.hi)
-        pool.append((w, rob, torch.from_numpy(cand).pin_memory(), tgt.cpu().pin_memory(),
-                     torch.from_numpy(cand).to(dev), tgt))
-    # plain service time of every pool entry (cpp_plan alone, one stream)
-    st = torch.cuda.current_stream()
-    service = []
-    for w, rob, ch, th, cd, td in pool:
-        T, Kp = w.T, cd.shape[2]
-        ws = torch.empty(cppflow.plan_workspace_size(T, w.K, Kp, n), dtype=torch.uint8, device=dev)
-        bufs = (torch.empty(T, dtype=torch.int32, device=dev), torch.empty(1, device=dev),
-                torch.empty(T, n, device=dev), torch.empty(T, 2, dtype=torch.float64, device=dev),
-                torch.zeros(cppflow.REPORT_BYTES, dtype=torch.uint8, device=dev),
-                torch.zeros(1, dtype=torch.int32, device=dev))
-        times = []
-        for rep in range(3):
-            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-            e0.record(st)
-            cppflow.plan(rob, P, cd, td, w.K, ws, *bufs, stream=st)
-            e1.record(st)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-        service.append(min(times[1:]) / 1000.0)
-    out = {}
-    rng_pick = synth.uniform(991, synth.S_MIX, 10 * max_requests)
+        d = synth.draw_candidates(w.cand_seed, w.T, w.K, n, w.p_wb, w.p_out)
+        lat = synth.assemble(truths[r], qwb_h[r], d, w.sigma, arm.lo, arm.hi, synth.pad_k(w.K))
+        bnp[offs[r]:offs[r + 1]] = lat.ravel()
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(fill, range(pool_size)))
+    pool = []
+    for r, w in enumerate(ws):
+        Kp = synth.pad_k(w.K)
+        pool.append((w, robots[w.arm_seed - 100], bnp[offs[r]:offs[r + 1]].reshape(w.T, n, Kp),
+                     tnp[toffs[r]:toffs[r + 1]].reshape(w.T, 7)))
+    return pool, (big, tbig)
+
+
+def _pct(v, q):
+    v = sorted(v)
+    return round(1000 * v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))], 3)
+
+
+def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_requests: int):
+    """Open-loop Poisson arrivals of the serving mix at each rate, drawn with replacement
+    from a pool of distinct requests. The first 10 % of the requests are a warm-up; the
+    rest (at least `seconds` of arrivals or `max_requests` requests) are reported.
+    served: real-time submission to cpp_plan_submit (borrowed pinned inputs), latency =
+    arrival -> completion. plain: the same arrival trace in real time through
+    cpp_plan_host, one request at a time on one stream (inputs copied in, results copied
+    out, the next request starts when the previous one is done), latency = arrival ->
+    completion. plans/s = reported requests / (last completion - first reported arrival)."""
+    pool, keep = serving_pool(cppflow, torch, dev, pool_size)
+    n = 7
+    P = cppflow.make_params()
+    T_max = max(w.T for w, *_ in pool)
+    Kp_max = max(synth.pad_k(w.K) for w, *_ in pool)
+    ws = torch.empty(cppflow.plan_host_workspace_size(T_max, Kp_max, Kp_max, n), dtype=torch.uint8,
+                     device=dev)
+    sel_h = torch.empty(T_max, dtype=torch.int32, pin_memory=True).numpy()
+    q_h = torch.empty(T_max * n, dtype=torch.float32, pin_memory=True).numpy()
+    rep_h = cppflow.Report()
+    pstream = torch.cuda.Stream()
+    for w, rob, ch, th in pool[:4]:  # warm the plain path
+        cppflow.plan_host(rob, P, ch, th, w.K, ws, sel_h[:w.T], None, q_h[:w.T * n], None, rep_h,
+                          stream=pstream)
+    out = {"pool_requests": pool_size}
     for rate in rates:
-        count = int(min(max_requests, rate * seconds))
+        target = int(min(max_requests, math.ceil(rate * seconds)))
+        count = int(math.ceil(target / 0.9))
+        drop = count - target
         arr = synth.poisson_arrivals(rate, count, seed=int(rate))
-        pick = (rng_pick[:count] * len(pool)).astype(int)
-        # plain: FIFO single server with measured service times
-        done = 0.0
-        plat = []
-        for a, k in zip(arr, pick):
-            start = max(a, done)
-            done = start + service[k]
-            plat.append(done - a)
-        plain_span = done - arr[0]
-        # served: real-time open-loop submission (Python's cyclic collector is run before
-        # and paused during the loop, so no collection pause delays the arrivals)
+        pick = (synth.uniform(991 + int(rate), synth.S_MIX, count) * len(pool)).astype(int)
+        # served: real-time open-loop submission (Python's cyclic collector is run before and
+        # paused during the loop, so no collection pause delays the arrivals)
         gc.collect()
         gc.disable()
         with cppflow.Server(P, device=dev.index or 0, hbm_budget=40 << 30, max_batch=512,
@@ -259,31 +334,48 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_
                 now = time.perf_counter() - t0
                 if a > now:
                     time.sleep(a - now)
-                w, rob, ch, th, cd, td = pool[k]
-                lag = max(0.0, time.perf_counter() - t0 - a)  # submitted after its arrival time
-                tickets.append((srv.submit(rob, ch.numpy(), th.numpy(), w.K, borrow=True), lag))
-            slat = []
-            valid = 0
-            for tk, lag in tickets:
+                w, rob, ch, th = pool[k]
+                sub = time.perf_counter() - t0
+                tickets.append((srv.submit(rob, ch, th, w.K, borrow=True), sub))
+            done, valid = [], 0
+            for i, (tk, sub) in enumerate(tickets):
                 stt, res = srv.wait(tk)
-                slat.append(lag + res["latency_ms"] / 1000.0)
-                valid += int(res["report"]["valid"])
-            span = time.perf_counter() - t0
+                done.append(sub + res["latency_ms"] / 1000.0)
+                if i >= drop:
+                    valid += int(stt == cppflow.OK and res["report"]["valid"])
             ss = srv.stats()
         gc.enable()
-        drop = count // 10
-
-        def pct(v, q):
-            v = sorted(v[drop:])
-            return round(1000 * v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)], 3)
-
-        out[str(rate)] = {
-            "requests": count,
-            "served": {"plans_per_s": round(count / span, 1), "p50_ms": pct(slat, 0.5),
-                       "p99_ms": pct(slat, 0.99), "valid": f"{valid}/{count}",
-                       "mean_batch": round(ss["sum_batch"] / max(1, ss["batches"]), 1)},
-            "plain": {"plans_per_s": round(count / plain_span, 1), "p50_ms": pct(plat, 0.5),
-                      "p99_ms": pct(plat, 0.99)}}
+        slat = [d - a for d, a in zip(done[drop:], arr[drop:])]
+        sspan = max(done[drop:]) - arr[drop]
+        # plain: the same trace through one stream, one request at a time
+        gc.collect()
+        gc.disable()
+        pdone, pvalid = [], 0
+        t0 = time.perf_counter()
+        for i, (a, k) in enumerate(zip(arr, pick)):
+            now = time.perf_counter() - t0
+            if a > now:
+                time.sleep(a - now)
+            w, rob, ch, th = pool[k]
+            st = cppflow.plan_host(rob, P, ch, th, w.K, ws, sel_h[:w.T], None, q_h[:w.T * n], None,
+                                   rep_h, stream=pstream)
+            pdone.append(time.perf_counter() - t0)
+            if i >= drop:
+                pvalid += int(st == cppflow.OK and rep_h.valid)
+        gc.enable()
+        plat = [d - a for d, a in zip(pdone[drop:], arr[drop:])]
+        pspan = max(pdone[drop:]) - arr[drop]
+        out[str(int(rate))] = {
+            "requests": count, "reported": target,
+            "offered_per_s": round(target / (arr[-1] - arr[drop]), 1),
+            "served": {"plans_per_s": round(target / sspan, 1), "p50_ms": _pct(slat, 0.5),
+                       "p99_ms": _pct(slat, 0.99), "valid": f"{valid}/{target}",
+                       "mean_batch": round(ss["sum_batch"] / max(1, ss["batches"]), 2),
+                       "batches": ss["batches"], "max_batch": ss["max_batch_seen"],
+                       "hbm_high_water_bytes": ss["hbm_high_water"]},
+            "plain": {"plans_per_s": round(target / pspan, 1), "p50_ms": _pct(plat, 0.5),
+                      "p99_ms": _pct(plat, 0.99), "valid": f"{pvalid}/{target}"}}
+    del keep
     return out
 
 
@@ -327,13 +419,14 @@ def build_inputs(cppflow, torch, dev, reqs, want_truth: bool = False):
     return arms, robots, cand_h, targets_h
 
 
-def stress_leg(cppflow, torch, dev) -> dict:
+def stress_leg(cppflow, torch, dev):
     """The stress / precision workload: a 9-DoF chain with a spherical wrist, T = 2000,
     K = 1024, the true path through near-singular wrist poses (joint 6 within 0.02 rad
     of 0). One request through cpp_plan with the FP32-Jacobian LM (FP64 normal equations
     and Cholesky, the default) and again with the all-FP64 LM: plan time, per-path pose
-    errors (FP64 check) and joint jumps of each. The comparison with the FP64 CPU
-    oracle's LM is part of the parity tests."""
+    errors (FP64 check) and joint jumps of each, and the smallest singular value of the
+    library's FP64 Jacobian along the refined path. Returns (report, data for the
+    comparison with the oracle in the CPU-oracle leg)."""
     w = synth.STRESS
     arm = synth.draw_arm(w.arm_seed, w.n, w.wrist)
     rob = cppflow.robot_from_arm(arm)
@@ -353,7 +446,8 @@ def stress_leg(cppflow, torch, dev) -> dict:
     st = torch.cuda.current_stream()
     out = {"workload": f"stress: {n}-DoF spherical wrist, T={T}, K={w.K}, joint 6 within 0.02 rad "
                        "of 0 along the true path; one request, cpp_plan"}
-    qs = {}
+    qs, mj = {}, {}
+    sel_h = None
     for mode, name in ((0, "fp32_jacobian_lm"), (1, "all_fp64_lm")):
         P = cppflow.make_params(lm_iters=w.lm_iters, lambda0=w.lambda0, lm_fp64=mode)
         ws = torch.empty(cppflow.plan_workspace_size(T, w.K, Kp, n), dtype=torch.uint8, device=dev)
@@ -372,13 +466,26 @@ def stress_leg(cppflow, torch, dev) -> dict:
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         r = cppflow.report_from_bytes(rep.cpu().numpy().tobytes())
-        qs[mode] = q.cpu().numpy()
+        qs[name] = q.cpu().numpy()
+        mj[name] = float(r["mjac"])
+        sel_h = sel.cpu().numpy()
+        # smallest singular value of the FP64 geometric Jacobian at every refined waypoint
+        J = torch.empty(T, 6, n, dtype=torch.float64, device=dev)
+        cppflow.jacobian_f64(rob, q.to(torch.float64).contiguous(), J)
+        sv = np.linalg.svd(J.cpu().numpy(), compute_uv=False)[:, -1]
         out[name] = {"plan_ms": round(min(times[1:]), 3), "valid": int(r["valid"]),
                      "max_pos_m": float(r["max_pos"]), "max_rot_deg": math.degrees(r["max_rot"]),
                      "mjac_rad": float(r["mjac"]), "sum_linf_rad": float(r["sum_linf"]),
-                     "status": int(status.item())}
-    out["max_abs_q_diff_rad"] = float(np.abs(qs[0].astype(np.float64) - qs[1]).max())
-    return out
+                     "status": int(status.item()),
+                     "sigma_min_J": {"min": float(sv.min()), "median": float(np.median(sv)),
+                                     "argmin_waypoint": int(sv.argmin())}}
+    out["max_abs_q_diff_between_modes_rad"] = float(np.abs(qs["fp32_jacobian_lm"].astype(np.float64)
+                                                           - qs["all_fp64_lm"]).max())
+    data = {"arm": (arm.a, arm.d, arm.alpha, arm.lo, arm.hi, arm.theta0),
+            "seed": cand[np.arange(T), :, sel_h].astype(np.float64),
+            "targets": tgt.cpu().numpy(), "lm_iters": w.lm_iters, "lambda0": w.lambda0,
+            "q": qs, "mjac": mj}
+    return out, data
 
 
 def path_clearance(cppflow, torch, dev, robot, geometry, q, params):
@@ -541,6 +648,36 @@ def uneven_batch(cppflow, torch, dev, nreq: int) -> dict:
     return out
 
 
+def measure_peaks(cppflow, torch, dev) -> dict:
+    """FP32 lane-operation and FP64 flop rates of the library's throughput probe
+    (cpp_peak_probe: 4 blocks of 256 threads per SM, 8 independent chains per thread):
+    each probe sized to about 25 ms, best of 6 launches timed with CUDA events on the
+    launching stream, SM clocks sampled meanwhile."""
+    st = torch.cuda.current_stream()
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    out = {}
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    time.sleep(0.2)
+    for kind, name in ((cppflow.PROBE_FP32, "fp32_lane_ops_per_s"),
+                       (cppflow.PROBE_FP64, "fp64_flops_per_s")):
+        iters, best = 1024, 0.0
+        for rep in range(8):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ops = cppflow.peak_probe(kind, 4, iters, sink, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if rep < 2:  # size the probe to about 25 ms
+                iters = int(min(1e9, max(1024, iters * 25.0 / max(ms, 1e-3))))
+                continue
+            best = max(best, ops / (ms / 1e3))
+        out[name] = best
+    out["clocks"] = clocks.stop()
+    return out
+
+
 def run_cuda(args, rank: int, world: int, dist):
     import torch
 
@@ -589,10 +726,15 @@ def run_cuda(args, rank: int, world: int, dist):
         batch.run(cppflow.STAGE_ALL, stream)
     torch.cuda.synchronize()
 
-    # ---- timed region: device-resident batched path
-    pre = cppflow.STAGE_MASK | cppflow.STAGE_LAYER_MIN
-    post = cppflow.STAGE_BACKTRACK | cppflow.STAGE_LM | cppflow.STAGE_CHECK
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    # ---- measured peaks (rank 0 runs the probe; its figures enter the rooflines it prints)
+    peaks = measure_peaks(cppflow, torch, dev) if rank == 0 else None
+
+    # ---- timed region: device-resident batched path, the stages bracketed by events
+    stages = [cppflow.STAGE_MASK | cppflow.STAGE_LAYER_MIN, cppflow.STAGE_DP_FORWARD,
+              cppflow.STAGE_BACKTRACK, cppflow.STAGE_LM, cppflow.STAGE_CHECK]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
+          for _ in range(args.steps)]
+    cppflow.counters_reset(stream)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -600,19 +742,17 @@ def run_cuda(args, rank: int, world: int, dist):
     torch.cuda.synchronize()
     for s in range(args.steps):
         ev[s][0].record(stream)
-        batch.run(pre, stream)
-        ev[s][1].record(stream)
-        batch.run(cppflow.STAGE_DP_FORWARD, stream)
-        ev[s][2].record(stream)
-        batch.run(post, stream)
-        ev[s][3].record(stream)
+        for k, stg in enumerate(stages):
+            batch.run(stg, stream)
+            ev[s][k + 1].record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    total_ms = ev[0][0].elapsed_time(ev[-1][3])
-    dp_ms = [ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps)]
-    pre_ms = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)]
-    post_ms = [ev[s][2].elapsed_time(ev[s][3]) for s in range(args.steps)]
+    counters = cppflow.counters_read()
+    total_ms = ev[0][0].elapsed_time(ev[-1][-1])
+    stage_ms = [[ev[s][k].elapsed_time(ev[s][k + 1]) for s in range(args.steps)]
+                for k in range(len(stages))]
+    pre_ms, dp_ms, bt_ms, lm_ms, chk_ms = stage_ms
     if dist is not None:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -623,6 +763,9 @@ def run_cuda(args, rank: int, world: int, dist):
     # ---- results valid?
     st = status.cpu().numpy()
     reps = [cppflow.report_from_bytes(rep[r].cpu().numpy().tobytes()) for r in range(B)]
+    gpu_res = {"sel": sel.cpu().numpy(), "q": q_out.cpu().numpy(),
+               "mjac": [r["mjac"] for r in reps], "max_pos": [r["max_pos"] for r in reps],
+               "max_rot": [r["max_rot"] for r in reps]}
     valid = sum(int(r["valid"]) for r in reps)
     max_pos = max(r["max_pos"] for r in reps)
     max_rot = max(r["max_rot"] for r in reps)
@@ -700,30 +843,57 @@ def run_cuda(args, rank: int, world: int, dist):
            "valid_plans": f"{e2e_valid}/{B * e2e_steps}",
            "batches_per_step": round(sstats["batches"] / (e2e_steps + 1), 2), "steps": e2e_steps}
 
-    # ---- roofline of the search kernel (the dominant kernel)
+    # ---- rooflines: the search kernel (dominant) and the LM kernel, against the peaks
+    # measured above by the library's throughput probe
     edges = B * (T - 1) * K * K
     ops_per_edge = 2 * n + 1
     dp_s = statistics.mean(dp_ms) / 1000.0
-    achieved = edges * ops_per_edge / dp_s / 1e12
-    peak = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    roof = {"bound": "alu", "kernel": "dp3_forward_kernel", "achieved": round(achieved, 3),
-            "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+    achieved = edges * ops_per_edge / dp_s
+    if peaks is not None:
+        peak, basis = peaks["fp32_lane_ops_per_s"], (
+            "measured: cpp_peak_probe FP32 add + max chains, best of 6 launches in this run "
+            f"(SM clock median {peaks['clocks'].get('sm_mhz')} MHz during the probe)")
+    else:
+        peak, basis = 152 * 128 * 2070e6, "derived: 152 SMs x 128 FP32 lanes x 2070 MHz"
+    roof = {"bound": "alu", "kernel": "dp3_forward_kernel", "achieved": round(achieved / 1e12, 3),
+            "peak": round(peak / 1e12, 3), "unit": "T FP32 lane-ops/s",
+            "frac": round(achieved / peak, 4),
             "traffic": DP3_TRAFFIC_BYTES if (B, T, K, n) == (304, 300, 512, 7) else None,
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "algorithmic_bytes": B * T * Kp * (4 * n + 4) + B * T * synth.pad_k(K, 8) * 2,
             "ops": f"{ops_per_edge} FP32 ALU ops per edge (n sub, n-1 abs-max, add, min) x "
                    f"{edges:.4g} edges per launch",
-            "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz max clock (derived, not measured)",
-            "kernel_ms": round(statistics.mean(dp_ms), 4),
+            "peak_basis": basis, "kernel_ms": round(statistics.mean(dp_ms), 4),
             "edges_per_s": round(edges / dp_s, 1)}
+    lm_iters_launch = counters["lm_iterations"] / args.steps
+    lm_wp_launch = counters["lm_waypoints"] / args.steps
+    lm_s = statistics.mean(lm_ms) / 1000.0
+    lm_achieved = lm_iters_launch * lm_flops_per_iter(n) / lm_s
+    roof_lm = None
+    if peaks is not None:
+        roof_lm = {"bound": "fp64", "kernel": "lm_kernel", "achieved": round(lm_achieved / 1e12, 4),
+                   "peak": round(peaks["fp64_flops_per_s"] / 1e12, 4), "unit": "TFLOP/s (FP64)",
+                   "frac": round(lm_achieved / peaks["fp64_flops_per_s"], 4),
+                   "ops": f"{lm_flops_per_iter(n)} FP64 flops per waypoint-iteration x "
+                          f"{lm_iters_launch:.0f} iterations per launch (library counters: "
+                          f"{lm_wp_launch:.0f} waypoints, "
+                          f"{lm_iters_launch / max(1.0, lm_wp_launch):.2f} iterations each)",
+                   "peak_basis": "measured: cpp_peak_probe FP64 fma chains, best of 6 launches "
+                                 "in this run",
+                   "kernel_ms": round(statistics.mean(lm_ms), 4)}
 
     uneven = uneven_batch(cppflow, torch, dev, args.uneven) if args.uneven and rank == 0 else None
     coll = collision_leg(cppflow, torch, dev, args.collision) if args.collision and rank == 0 else None
-    stress = stress_leg(cppflow, torch, dev) if args.stress and rank == 0 else None
+    stress, stress_data = stress_leg(cppflow, torch, dev) if args.stress and rank == 0 else (None, None)
     mix = None
     if args.serve_rates and rank == 0:
         mix = serving_mix(cppflow, torch, dev, [float(x) for x in args.serve_rates.split(",")],
                           args.mix_pool, args.mix_seconds, args.mix_max)
+    orc = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        orc = oracle_leg(arms, reqs, cand_h, targets_h, gpu_res, stress_data)
+        if stress is not None and orc["stress_vs_oracle"] is not None:
+            stress["vs_oracle"] = orc["stress_vs_oracle"]
     line = {"metric": METRIC, "value": round(value, 3), "unit": "plans/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -734,14 +904,20 @@ def run_cuda(args, rank: int, world: int, dist):
                        "lm_iters": P.lm_iters, "parallelism": f"replicas x{world}",
                        "tuned": {"heavy": tuned["heavy"], "alpha": round(tuned["alpha"], 4),
                                  "mask_tasks_per_warp": tuned["mask_tasks_per_warp"]}},
-            "p99_ms": round(ms_per_step, 4),
+            "value_is": VALUE_IS,
             "stage_ms": {"mask_and_layer_min": round(statistics.mean(pre_ms), 4),
                          "dp_forward": round(statistics.mean(dp_ms), 4),
-                         "backtrack_lm_check": round(statistics.mean(post_ms), 4)},
+                         "backtrack": round(statistics.mean(bt_ms), 4),
+                         "lm": round(statistics.mean(lm_ms), 4),
+                         "check": round(statistics.mean(chk_ms), 4)},
             "plain_per_request": plain,
             "valid_plans": f"{valid}/{B}", "max_pos_err_m": max_pos, "max_rot_err_rad": max_rot,
             "dev_status_nonzero": int((st != 0).sum()),
-            "roofline": roof, "e2e": e2e, "clocks": clk,
+            "roofline": roof, "roofline_lm": roof_lm, "peaks_measured": (
+                None if peaks is None else
+                {"fp32_lane_ops_per_s": peaks["fp32_lane_ops_per_s"],
+                 "fp64_flops_per_s": peaks["fp64_flops_per_s"], "clocks": peaks["clocks"]}),
+            "e2e": e2e, "clocks": clk,
             "gpu_launches": launches_per_step * args.steps}
     if uneven is not None:
         line["batched_uneven"] = uneven
@@ -751,10 +927,14 @@ def run_cuda(args, rank: int, world: int, dist):
         line["stress_precision"] = stress
     if mix is not None:
         line["serving_mix"] = {"workload": "serving mix: T = floor(exp U(ln 50, ln 2000)), "
-                                           "K in {128, 256, 512, 1024}, 7-DoF, Poisson arrivals",
+                                           "K in {128, 256, 512, 1024}, 7-DoF, open-loop Poisson "
+                                           "arrivals; served = cpp_plan_submit (continuous "
+                                           "batching), plain = the same trace through "
+                                           "cpp_plan_host one request at a time; host copies "
+                                           "inside both latencies; first 10 % dropped",
                                "rates": mix}
-    if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(rank)
+    if orc is not None:
+        line["cpu_baseline"] = orc["cpu_baseline"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     batch.close()
@@ -775,11 +955,12 @@ def main():
                     help="requests of the collision-aware leg (0: skip)")
     ap.add_argument("--stress", type=int, default=1,
                     help="run the 9-DoF T=2000 K=1024 precision leg (0: skip)")
-    ap.add_argument("--serve-rates", default="1000", help="Poisson rates (req/s) of the serving "
-                    "mix, comma separated; empty to skip")
-    ap.add_argument("--mix-pool", type=int, default=48, help="distinct requests in the mix pool")
-    ap.add_argument("--mix-seconds", type=float, default=2.0)
-    ap.add_argument("--mix-max", type=int, default=3000)
+    ap.add_argument("--serve-rates", default="100,1000,5000", help="Poisson rates (req/s) of the "
+                    "serving mix, comma separated; empty to skip")
+    ap.add_argument("--mix-pool", type=int, default=512, help="distinct requests in the mix pool")
+    ap.add_argument("--mix-seconds", type=float, default=10.0,
+                    help="seconds of reported arrivals per rate (or --mix-max requests)")
+    ap.add_argument("--mix-max", type=int, default=10000)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     args = ap.parse_args()

@@ -371,6 +371,60 @@ cpp_status cpp_plan_geo(const cpp_robot_t* robot, const cpp_params_t* params,
                         float* q_out, double* pose_err, cpp_report_t* report,
                         int32_t* dev_status, cpp_stream_t stream);
 
+/* The plain per-request path from HOST memory: copies cand [T][n][Kp] FP32 and
+ * targets [T][7] FP64 from host buffers to the device, runs cpp_plan on `stream`,
+ * copies sel [T], best_cost [1], q_out [T][n], pose_err [T][2] and report [1] back
+ * into host buffers (each may be NULL) and waits for the stream. This is the path a
+ * single client with host data takes, one request at a time. Pinned host buffers
+ * make the copies direct DMA; pageable ones work (slower). workspace: DEVICE
+ * scratch of cpp_plan_host_workspace_size(T, K, Kp, n) bytes, 256-byte aligned
+ * (the device copies of inputs and outputs, a status word and the plan's scratch).
+ * Returns INVALID_ARG as cpp_plan, CUDA on a failed copy or launch, otherwise the
+ * plan's device status after the wait (OK, INFEASIBLE or TIMEOUT). */
+size_t cpp_plan_host_workspace_size(int32_t T, int32_t K, int32_t Kp, int32_t n);
+cpp_status cpp_plan_host(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
+                         const double* targets, int32_t T, int32_t K, int32_t Kp,
+                         void* workspace, size_t ws_bytes, int32_t* sel, float* best_cost,
+                         float* q_out, double* pose_err, cpp_report_t* report,
+                         cpp_stream_t stream);
+
+/* ------------------------------------------------------------------ diagnostics (not in the paper)
+ * Arithmetic throughput probe, the measured peak the kernels are compared with.
+ * CPP_PROBE_FP32: every thread runs 8 independent chains x = max(x + a, b), one
+ * FP32 add and one FP32 max per link (the two operations of the search's inner
+ * loop, each one FP32 lane operation); CPP_PROBE_FP64: 8 chains x = fma(x, a, b)
+ * in FP64 (2 flops per link). One launch of blocks_per_sm * SMs blocks of 256
+ * threads, `iters` links per chain, on `stream`; time it with events on that
+ * stream. *lane_ops (host) receives the operations one launch performs (FP32 lane
+ * operations, or FP64 flops). sink: device buffer of one double that keeps the
+ * chains from being removed (its value is meaningless). INVALID_ARG for another
+ * kind, blocks_per_sm outside [1, 8], iters outside [1, 1e9]. */
+#define CPP_PROBE_FP32 0
+#define CPP_PROBE_FP64 1
+cpp_status cpp_peak_probe(int32_t kind, int32_t blocks_per_sm, int64_t iters, double* sink,
+                          double* lane_ops, cpp_stream_t stream);
+
+/* Work counters of the LM stage (S5), accumulated over every LM launch of the
+ * process on the current device: waypoints refined and LM iterations that built
+ * and solved a damped system (accepted or rejected; a waypoint stops early at
+ * F < freeze_cost or max|delta| < freeze_step). cpp_counters_reset zeroes them on
+ * `stream`; cpp_counters_read copies them to the host once every earlier launch has
+ * completed (synchronize the streams that ran them first). */
+typedef struct cpp_counters {
+    uint64_t lm_waypoints;
+    uint64_t lm_iterations;
+} cpp_counters_t;
+cpp_status cpp_counters_reset(cpp_stream_t stream);
+cpp_status cpp_counters_read(cpp_counters_t* out);
+
+/* FP64 geometric Jacobian in the world frame (§III-C, the matrix of the LM step):
+ * q [N][n] FP64 -> J [N][6][n] FP64, rows 0..2 the linear part z_{j-1} x (p_e - o_{j-1}),
+ * rows 3..5 the angular part z_{j-1} (frame 0 = base). For conditioning reports
+ * (the smallest singular value along a path). INVALID_ARG if N < 0 or the robot
+ * is malformed. */
+cpp_status cpp_jacobian_f64(const cpp_robot_t* robot, const double* q, int64_t N, double* J,
+                            cpp_stream_t stream);
+
 /* ------------------------------------------------------------------ cpf-BatchOpt
  * The paper's fastest planner variant (§III, in its commented text): refine the
  * smoothest of the K candidate trajectories directly instead of searching. Lane

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcppflow_gb300.so")
 SOURCES = ["fk_mask.cu", "dp.cu", "dp_fwd_sum.cu", "dp_fwd_minmax.cu", "lm.cu", "capi.cu",
-           "server.cu", "dp_static.cu", "batchopt.cu"]
+           "server.cu", "dp_static.cu", "batchopt.cu", "diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

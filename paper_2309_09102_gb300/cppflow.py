@@ -145,6 +145,14 @@ class ServerStats(C.Structure):
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
+
+class Counters(C.Structure):
+    _fields_ = [("lm_waypoints", C.c_uint64), ("lm_iterations", C.c_uint64)]
+
+
+PROBE_FP32 = 0
+PROBE_FP64 = 1
+
 _lib = None
 _P = C.c_void_p
 _SIGS = {
@@ -200,6 +208,13 @@ _SIGS = {
     "cpp_plan_peek": (C.c_int, [_P, C.c_uint64, _P]),
     "cpp_server_get_stats": (C.c_int, [_P, _P]),
     "cpp_server_destroy": (None, [_P]),
+    "cpp_plan_host_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "cpp_plan_host": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_size_t,
+                                _P, _P, _P, _P, _P, _P]),
+    "cpp_peak_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, _P, C.POINTER(C.c_double), _P]),
+    "cpp_counters_reset": (C.c_int, [_P]),
+    "cpp_counters_read": (C.c_int, [_P]),
+    "cpp_jacobian_f64": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
 }
 
 
@@ -391,6 +406,53 @@ def plan(robot: Robot, params: Params, cand, targets, K: int, workspace, sel, be
                           ptr(workspace), nbytes, ptr(sel), ptr(best_cost), ptr(q_out),
                           ptr(pose_err), ptr(report), ptr(dev_status), stream_handle(stream)),
            "cpp_plan")
+
+
+def plan_host_workspace_size(T: int, K: int, Kp: int, n: int) -> int:
+    return lib().cpp_plan_host_workspace_size(T, K, Kp, n)
+
+
+def plan_host(robot: Robot, params: Params, cand, targets, K: int, workspace, sel=None,
+              best_cost=None, q_out=None, pose_err=None, report=None, stream=None) -> int:
+    """cpp_plan_host: HOST numpy inputs cand [T][n][Kp] FP32 and targets [T][7] FP64 (pinned
+    memory makes the copies DMA), DEVICE workspace; outputs into HOST numpy arrays (or None,
+    report: a Report). Synchronous. Returns the plan's status (OK, INFEASIBLE, TIMEOUT);
+    raises for invalid arguments and CUDA failures."""
+    T, n, Kp = cand.shape
+    nbytes = workspace.numel() * workspace.element_size()
+    host = lambda a: None if a is None else a.ctypes.data
+    st = lib().cpp_plan_host(C.byref(robot), C.byref(params), host(cand), host(targets), T, K, Kp,
+                             ptr(workspace), nbytes, host(sel), host(best_cost), host(q_out),
+                             host(pose_err), C.addressof(report) if report is not None else None,
+                             stream_handle(stream))
+    if st in (OK, ERR_INFEASIBLE, ERR_TIMEOUT):
+        return st
+    raise CppflowError(st, f"cpp_plan_host: {last_error()}")
+
+
+def peak_probe(kind: int, blocks_per_sm: int, iters: int, sink, stream=None) -> float:
+    """Enqueue one throughput-probe launch; returns the lane operations (FP32) or flops
+    (FP64) it performs."""
+    ops = C.c_double()
+    _check(lib().cpp_peak_probe(kind, blocks_per_sm, int(iters), ptr(sink), C.byref(ops),
+                                stream_handle(stream)), "cpp_peak_probe")
+    return ops.value
+
+
+def counters_reset(stream=None):
+    _check(lib().cpp_counters_reset(stream_handle(stream)), "cpp_counters_reset")
+
+
+def counters_read() -> dict:
+    c = Counters()
+    _check(lib().cpp_counters_read(C.byref(c)), "cpp_counters_read")
+    return {"lm_waypoints": c.lm_waypoints, "lm_iterations": c.lm_iterations}
+
+
+def jacobian_f64(robot: Robot, q, J, stream=None):
+    """q [N][n] FP64 -> J [N][6][n] FP64 (device tensors)."""
+    _check(lib().cpp_jacobian_f64(C.byref(robot), ptr(q), q.numel() // robot.n, ptr(J),
+                                  stream_handle(stream)), "cpp_jacobian_f64")
 
 
 def plan_geo(robot: Robot, params: Params, geometry: Geometry | None, cand, targets, K: int,

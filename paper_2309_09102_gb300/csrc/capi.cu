@@ -506,6 +506,95 @@ cpp_status cpp_plan_geo(const cpp_robot_t* robot, const cpp_params_t* params,
   return cuda_status(launch_check(s, *params, st), "cpp_plan/check");
 }
 
+// ------------------------------------------------------------------ plain path from host memory
+namespace {
+struct HostPlanLayout {  // device copies of inputs and outputs, status word, plan scratch
+  size_t cand, tgt, sel, q, err, rep, best, status, plan, total;
+};
+HostPlanLayout host_plan_layout(int T, int Kp, int n) {
+  HostPlanLayout L;
+  size_t o = 0;
+  L.cand = o;   o += align256((size_t)T * n * Kp * sizeof(float));
+  L.tgt = o;    o += align256((size_t)T * 7 * sizeof(double));
+  L.sel = o;    o += align256((size_t)T * sizeof(int32_t));
+  L.q = o;      o += align256((size_t)T * n * sizeof(float));
+  L.err = o;    o += align256((size_t)T * 2 * sizeof(double));
+  L.rep = o;    o += align256(sizeof(cpp_report_t));
+  L.best = o;   o += align256(sizeof(float));
+  L.status = o; o += align256(sizeof(int32_t));
+  L.plan = o;   o += plan_layout(T, Kp, n).total;
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+size_t cpp_plan_host_workspace_size(int32_t T, int32_t K, int32_t Kp, int32_t n) {
+  if (T < 1 || K < 1 || Kp < K || n < 1) return 0;
+  return host_plan_layout(T, Kp, n).total;
+}
+
+cpp_status cpp_plan_host(const cpp_robot_t* robot, const cpp_params_t* params, const float* cand,
+                         const double* targets, int32_t T, int32_t K, int32_t Kp,
+                         void* workspace, size_t ws_bytes, int32_t* sel, float* best_cost,
+                         float* q_out, double* pose_err, cpp_report_t* report,
+                         cpp_stream_t stream) {
+  if (cpp_status s = check_robot(robot)) return s;
+  if (cpp_status s = check_params(params)) return s;
+  const int n = robot->n;
+  if (cpp_status s = check_lattice(T, K, Kp, n)) return s;
+  if (cpp_status s = check_smooth(params, T, n)) return s;
+  if (!dp_supported(n, Kp))
+    return fail(CPP_ERR_INVALID_ARG, "Kp * (n + 1) exceeds the shared-memory limit");
+  if (!cand || !targets || !workspace) return fail(CPP_ERR_INVALID_ARG, "NULL buffer");
+  const HostPlanLayout L = host_plan_layout(T, Kp, n);
+  if (ws_bytes < L.total || !aligned(workspace, 256))
+    return fail(CPP_ERR_INVALID_ARG, "workspace needs %zu bytes, 256-byte aligned", L.total);
+  char* ws = static_cast<char*>(workspace);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t cand_b = (size_t)T * n * Kp * sizeof(float), tgt_b = (size_t)T * 7 * sizeof(double);
+  int32_t* d_status = reinterpret_cast<int32_t*>(ws + L.status);
+  if (cpp_status e = cuda_status(cudaMemcpyAsync(ws + L.cand, cand, cand_b, cudaMemcpyHostToDevice, st),
+                                 "cpp_plan_host/H2D"))
+    return e;
+  if (cpp_status e = cuda_status(cudaMemcpyAsync(ws + L.tgt, targets, tgt_b, cudaMemcpyHostToDevice, st),
+                                 "cpp_plan_host/H2D"))
+    return e;
+  if (cpp_status e = cuda_status(cudaMemsetAsync(d_status, 0, sizeof(int32_t), st), "cpp_plan_host"))
+    return e;
+  const cpp_status ps = cpp_plan(robot, params, reinterpret_cast<const float*>(ws + L.cand),
+                                 reinterpret_cast<const double*>(ws + L.tgt), T, K, Kp, ws + L.plan,
+                                 ws_bytes - L.plan, reinterpret_cast<int32_t*>(ws + L.sel),
+                                 reinterpret_cast<float*>(ws + L.best),
+                                 reinterpret_cast<float*>(ws + L.q),
+                                 reinterpret_cast<double*>(ws + L.err),
+                                 reinterpret_cast<cpp_report_t*>(ws + L.rep), d_status, stream);
+  if (ps != CPP_OK) {
+    cudaStreamSynchronize(st);  // the input copies read host memory the caller may free
+    return ps;
+  }
+  struct Back { void* dst; size_t off, bytes; } back[] = {
+      {sel, L.sel, (size_t)T * sizeof(int32_t)},
+      {best_cost, L.best, sizeof(float)},
+      {q_out, L.q, (size_t)T * n * sizeof(float)},
+      {pose_err, L.err, (size_t)T * 2 * sizeof(double)},
+      {report, L.rep, sizeof(cpp_report_t)}};
+  for (const Back& b : back) {
+    if (!b.dst) continue;
+    if (cpp_status e = cuda_status(cudaMemcpyAsync(b.dst, ws + b.off, b.bytes, cudaMemcpyDeviceToHost, st),
+                                   "cpp_plan_host/D2H"))
+      return e;
+  }
+  int32_t h_status = 0;
+  if (cpp_status e = cuda_status(cudaMemcpyAsync(&h_status, d_status, sizeof(int32_t),
+                                                 cudaMemcpyDeviceToHost, st),
+                                 "cpp_plan_host/D2H"))
+    return e;
+  if (cpp_status e = cuda_status(cudaStreamSynchronize(st), "cpp_plan_host/wait")) return e;
+  if (h_status != 0)
+    return fail((cpp_status)h_status, "cpp_plan_host: device status %d", h_status);
+  return CPP_OK;
+}
+
 // ------------------------------------------------------------------ cpf-BatchOpt
 size_t cpp_batch_opt_workspace_size(int32_t T, int32_t K, int32_t n, int32_t lanes) {
   if (T < 1 || K < 1 || n < 1 || lanes < 1) return 0;

@@ -39,6 +39,9 @@ struct CheckArgs {
   double tau_pos, tau_rot, jump_max;
 };
 
+// Work counters of the LM stage (cpp_counters_read): one atomic add per warp.
+__device__ cpp_counters_t g_lm_counters;
+
 __device__ __forceinline__ float to_angle(double q, const RobotF& rb, int j) {
   return (float)q + rb.th0[j];
 }
@@ -103,6 +106,9 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
   __syncthreads();
   const int i = blockIdx.x * kLmThreads + threadIdx.x;
   if (i >= rq.T) return;
+  // lanes of this warp that hold a waypoint (the others have returned)
+  const int left = rq.T - (int)blockIdx.x * kLmThreads;
+  const unsigned live = left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
   const auto& rb = RobotFor<F>::get(rf, rd);
   const int n = NJ ? NJ : rd.n;
 
@@ -124,8 +130,10 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
   double Fc = lm_eval<NJ, false, F>(rb, n, q, Rt, pt, e, nullptr, nullptr, nullptr);
   double lam = a.lambda0;
 
+  unsigned worked = 0;  // iterations that built and solved a damped system
   for (int it = 0; it < a.iters; ++it) {
     if (Fc < a.freeze_cost) break;
+    ++worked;
     F z[MJ][3], o[MJ][3], pe[3];
     lm_eval<NJ, true, F>(rb, n, q, Rt, pt, e, z, o, pe);
     // J^T J + lam I (packed lower triangle) and J^T e, one Jacobian row at a time
@@ -233,6 +241,15 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
 #pragma unroll
   for (int j = 0; j < MJ; ++j)
     if (NJ || j < n) rq.q_out[(size_t)i * n + j] = (float)q[j];
+  {
+    const unsigned sum = __reduce_add_sync(live, worked);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&g_lm_counters.lm_iterations),
+                (unsigned long long)sum);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&g_lm_counters.lm_waypoints),
+                (unsigned long long)__popc(live));
+    }
+  }
   if (a.want_err && rq.pose_err) {
     // FP64 pose error of the delivered (FP32-rounded) configuration
     double qq[kMaxJ], R[9], p[3], RtD[9];
@@ -840,3 +857,35 @@ cudaError_t launch_check_batch(const BatchSrc& s, int nreq, const cpp_params_t& 
 }
 
 }  // namespace cppflow
+
+extern "C" {
+
+cpp_status cpp_counters_reset(cpp_stream_t stream) {
+  const cpp_counters_t zero = {0, 0};
+  const cudaError_t e = cudaMemcpyToSymbolAsync(cppflow::g_lm_counters, &zero, sizeof(zero), 0,
+                                                cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (e == cudaSuccess) {
+    // the source is a stack variable: wait until the copy has read it
+    const cudaError_t w = cudaStreamSynchronize((cudaStream_t)stream);
+    if (w == cudaSuccess) return CPP_OK;
+    cppflow::set_last_error(cudaGetErrorString(w));
+    return CPP_ERR_CUDA;
+  }
+  cppflow::set_last_error(cudaGetErrorString(e));
+  return CPP_ERR_CUDA;
+}
+
+cpp_status cpp_counters_read(cpp_counters_t* out) {
+  if (!out) {
+    cppflow::set_last_error("cpp_counters_read: out is NULL");
+    return CPP_ERR_INVALID_ARG;
+  }
+  const cudaError_t e = cudaMemcpyFromSymbol(out, cppflow::g_lm_counters, sizeof(*out));
+  if (e != cudaSuccess) {
+    cppflow::set_last_error(cudaGetErrorString(e));
+    return CPP_ERR_CUDA;
+  }
+  return CPP_OK;
+}
+
+}  // extern "C"
