@@ -292,15 +292,21 @@ def _pct(v, q):
     return round(1000 * v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))], 3)
 
 
-def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_requests: int):
+def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, min_requests: int,
+                plain_max: int):
     """Open-loop Poisson arrivals of the serving mix at each rate, drawn with replacement
-    from a pool of distinct requests. The first 10 % of the requests are a warm-up; the
-    rest (at least `seconds` of arrivals or `max_requests` requests) are reported.
+    from a pool of distinct requests. Per rate, max(`seconds` of arrivals, `min_requests`)
+    requests are reported after a warm-up of 10 % more.
     served: real-time submission to cpp_plan_submit (borrowed pinned inputs), latency =
-    arrival -> completion. plain: the same arrival trace in real time through
-    cpp_plan_host, one request at a time on one stream (inputs copied in, results copied
-    out, the next request starts when the previous one is done), latency = arrival ->
-    completion. plans/s = reported requests / (last completion - first reported arrival)."""
+    arrival -> completion; the p50 of the first and the last third of the reported
+    requests show whether the server keeps up (a server that falls behind sees its
+    latency grow over the window).
+    plain: the same arrival trace in real time through cpp_plan_host, one request at a
+    time on one stream (inputs copied in, results copied out, the next request starts
+    when the previous one is done), latency = arrival -> completion, over the trace's
+    first `plain_max` reported requests (a saturated plain path falls further behind
+    with every request, so a longer trace only lengthens its queue).
+    plans/s = reported requests / (last completion - first reported arrival)."""
     pool, keep = serving_pool(cppflow, torch, dev, pool_size)
     n = 7
     P = cppflow.make_params()
@@ -317,9 +323,11 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_
                           stream=pstream)
     out = {"pool_requests": pool_size}
     for rate in rates:
-        target = int(min(max_requests, math.ceil(rate * seconds)))
+        target = int(max(min_requests, math.ceil(rate * seconds)))
         count = int(math.ceil(target / 0.9))
         drop = count - target
+        ptarget = min(target, plain_max)
+        pcount = drop + ptarget
         arr = synth.poisson_arrivals(rate, count, seed=int(rate))
         pick = (synth.uniform(991 + int(rate), synth.S_MIX, count) * len(pool)).astype(int)
         # served: real-time open-loop submission (Python's cyclic collector is run before and
@@ -327,7 +335,7 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_
         gc.collect()
         gc.disable()
         with cppflow.Server(P, device=dev.index or 0, hbm_budget=40 << 30, max_batch=512,
-                            max_inflight=16, pinned_bytes=64 << 20) as srv:
+                            max_inflight=16) as srv:
             t0 = time.perf_counter()
             tickets = []
             for a, k in zip(arr, pick):
@@ -347,12 +355,13 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_
         gc.enable()
         slat = [d - a for d, a in zip(done[drop:], arr[drop:])]
         sspan = max(done[drop:]) - arr[drop]
+        third = max(1, target // 3)
         # plain: the same trace through one stream, one request at a time
         gc.collect()
         gc.disable()
         pdone, pvalid = [], 0
         t0 = time.perf_counter()
-        for i, (a, k) in enumerate(zip(arr, pick)):
+        for i, (a, k) in enumerate(zip(arr[:pcount], pick[:pcount])):
             now = time.perf_counter() - t0
             if a > now:
                 time.sleep(a - now)
@@ -363,18 +372,22 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, max_
             if i >= drop:
                 pvalid += int(st == cppflow.OK and rep_h.valid)
         gc.enable()
-        plat = [d - a for d, a in zip(pdone[drop:], arr[drop:])]
+        plat = [d - a for d, a in zip(pdone[drop:], arr[drop:pcount])]
         pspan = max(pdone[drop:]) - arr[drop]
         out[str(int(rate))] = {
             "requests": count, "reported": target,
             "offered_per_s": round(target / (arr[-1] - arr[drop]), 1),
             "served": {"plans_per_s": round(target / sspan, 1), "p50_ms": _pct(slat, 0.5),
-                       "p99_ms": _pct(slat, 0.99), "valid": f"{valid}/{target}",
+                       "p99_ms": _pct(slat, 0.99),
+                       "p50_first_third_ms": _pct(slat[:third], 0.5),
+                       "p50_last_third_ms": _pct(slat[-third:], 0.5),
+                       "valid": f"{valid}/{target}",
                        "mean_batch": round(ss["sum_batch"] / max(1, ss["batches"]), 2),
                        "batches": ss["batches"], "max_batch": ss["max_batch_seen"],
                        "hbm_high_water_bytes": ss["hbm_high_water"]},
-            "plain": {"plans_per_s": round(target / pspan, 1), "p50_ms": _pct(plat, 0.5),
-                      "p99_ms": _pct(plat, 0.99), "valid": f"{pvalid}/{target}"}}
+            "plain": {"plans_per_s": round(ptarget / pspan, 1), "p50_ms": _pct(plat, 0.5),
+                      "p99_ms": _pct(plat, 0.99), "reported": ptarget,
+                      "valid": f"{pvalid}/{ptarget}"}}
     del keep
     return out
 
@@ -888,7 +901,7 @@ def run_cuda(args, rank: int, world: int, dist):
     mix = None
     if args.serve_rates and rank == 0:
         mix = serving_mix(cppflow, torch, dev, [float(x) for x in args.serve_rates.split(",")],
-                          args.mix_pool, args.mix_seconds, args.mix_max)
+                          args.mix_pool, args.mix_seconds, args.mix_min, args.mix_plain_max)
     orc = None
     if rank == 0 and world == 1 and not args.no_cpu:
         orc = oracle_leg(arms, reqs, cand_h, targets_h, gpu_res, stress_data)
@@ -959,8 +972,10 @@ def main():
                     "serving mix, comma separated; empty to skip")
     ap.add_argument("--mix-pool", type=int, default=512, help="distinct requests in the mix pool")
     ap.add_argument("--mix-seconds", type=float, default=10.0,
-                    help="seconds of reported arrivals per rate (or --mix-max requests)")
-    ap.add_argument("--mix-max", type=int, default=10000)
+                    help="seconds of reported arrivals per rate (at least --mix-min requests)")
+    ap.add_argument("--mix-min", type=int, default=1000)
+    ap.add_argument("--mix-plain-max", type=int, default=10000,
+                    help="reported requests of the plain arm per rate (a prefix of the trace)")
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     args = ap.parse_args()

@@ -508,10 +508,13 @@ void cpp_batch_destroy(cpp_batch_t* batch);
  * covers the whole batch). cpp_batch_create applies alpha = 2.
  *
  * The cluster form gives each CTA cands_per_cta successor candidates of a
- * waypoint (32, 64 or 128; 0 = 64 up to Kp = 512 and 128 above, as long as the
- * cluster has 2..8 CTAs; an explicit 32 or 64 also allows the non-portable sizes
- * of 9..16 CTAs): fewer per CTA shorten a long request's latency, more halve the
- * per-step record exchange and waits per candidate. The automatic form
+ * waypoint (32, 64 or 128: the CTAs exchange whole records [-q, C] every step;
+ * 256 or 512: the wide form, in which every CTA stages each layer's joint values
+ * itself and only the node costs C cross the cluster; 0 = 64 up to Kp = 512 and
+ * 128 above, as long as the cluster has 2..8 CTAs; an explicit 32 or 64 also
+ * allows the non-portable sizes of 9..16 CTAs): fewer per CTA shorten a long
+ * request's latency, more raise the edge rate per SM (fewer exchanges and waits
+ * per candidate). The automatic form
  * (alpha = 0, single-request calls, the server) takes the smallest tile (32 per
  * CTA up to Kp = 512, 64 above, clusters of up to 16 CTAs) when the device holds
  * all the requests' clusters at once with one CTA per SM.
@@ -520,7 +523,7 @@ void cpp_batch_destroy(cpp_batch_t* batch);
  * schedule on `stream`. cpp_batch_tune picks both by measurement on the batch
  * itself: it enqueues the mask and node-cost stages, then times the forward
  * sweep (CUDA events, best of two runs after one warm-up) for alpha = 0 and,
- * for each cands_per_cta in {64, 128} and each smallest clustered Kp (any, or
+ * for each cands_per_cta in {64, 128, 256, 512} and each smallest clustered Kp (any, or
  * each Kp of the batch above its smallest), a ladder of alpha values from 8 down
  * to 1e-9 (every cluster-capable request heavy), skipping values that give the
  * same split, and keeps the fastest; then it times the mask stage the same way for
@@ -587,10 +590,26 @@ typedef struct cpp_server_config {
     int32_t device;           /* CUDA device ordinal */
     int32_t max_slots;        /* requests resident on the device at once (default 1024) */
     int32_t max_batch;        /* requests per launch (default 512) */
-    int32_t max_inflight;     /* launches in flight, 1..16 (default 8) */
+    int32_t max_inflight;     /* launches in flight, 1..32 (default 8) */
     size_t hbm_budget_bytes;  /* device arena for resident requests (default 40 GiB) */
     size_t pinned_bytes;      /* pinned host staging; 0 = pageable only (default 1 GiB) */
     cpp_params_t params;      /* settings of every request */
+    /* Search form by load. While at most latency_requests requests are queued or on
+     * the device, a launch runs each request's search in the latency form (the
+     * smallest tile: clusters of up to 16 CTAs, 32 or 64 successors per CTA), the
+     * fastest for one request; above it, in the throughput form: clusters of
+     * throughput_cands_per_cta successors per CTA (Kp / that many CTAs; requests
+     * with Kp at or below it run one CTA each; 256 and 512 take the wide cluster
+     * form of cpp_batch_set_split), the form with the highest edge rate per SM.
+     * Results are identical in every form. (defaults 8 and 128;
+     * throughput_cands_per_cta in {64, 128, 256, 512}, latency_requests >= 0) */
+    int32_t latency_requests;
+    int32_t throughput_cands_per_cta;
+    /* Under load, a request whose search takes at most this long on one CTA (at
+     * one CTA's edge rate, about 7.7e9 edges/s on GB300) runs on one CTA, the form
+     * with the highest edge rate per SM; 0 keeps every cluster-capable request in
+     * clusters (ms, >= 0, default 0). */
+    double one_cta_budget_ms;
 } cpp_server_config_t;
 
 #define CPP_REQ_BORROW 1  /* inputs stay valid and unchanged until the plan is collected:

@@ -1004,8 +1004,9 @@ cpp_status cpp_batch_set_split(cpp_batch_t* b, double alpha, int32_t cands_per_c
                                cpp_stream_t stream) {
   if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
   if (!std::isfinite(alpha) || alpha < 0) return fail(CPP_ERR_INVALID_ARG, "alpha must be >= 0");
-  if (cands_per_cta != 0 && cands_per_cta != 32 && cands_per_cta != 64 && cands_per_cta != 128)
-    return fail(CPP_ERR_INVALID_ARG, "cands_per_cta must be 0, 32, 64 or 128");
+  if (cands_per_cta != 0 && cands_per_cta != 32 && cands_per_cta != 64 && cands_per_cta != 128 &&
+      cands_per_cta != 256 && cands_per_cta != 512)
+    return fail(CPP_ERR_INVALID_ARG, "cands_per_cta must be 0, 32, 64, 128, 256 or 512");
   return set_schedule(b, alpha, cands_per_cta, (cudaStream_t)stream);
 }
 
@@ -1055,7 +1056,7 @@ cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t s
     for (size_t i = 1; i < kps.size(); ++i) mks.push_back(kps[i]);
     struct Cand { double alpha; int cpc, mk; };
     std::vector<Cand> cands{{0.0, 0, 0}};
-    for (int c : {64, 128})
+    for (int c : {64, 128, 256, 512})
       for (int m : mks)
         for (double a : kAlphas) cands.push_back({a, c, m});
     cudaEvent_t e0 = nullptr, e1 = nullptr;

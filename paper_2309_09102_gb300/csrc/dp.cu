@@ -183,7 +183,8 @@ __global__ void __launch_bounds__(kBtThreads) dp_backtrack_kernel(const __grid_c
 // ------------------------------------------------------------------ launchers
 template <class Src>
 static cudaError_t launch_dp_t(const Src& s, unsigned stages, int objective, int n, int nreq,
-                               int max_T, int max_Kp, cudaStream_t st) {
+                               int max_T, int max_Kp, cudaStream_t st, int form = kFormAuto,
+                               int cpc = 0) {
   cudaError_t e = cudaSuccess;
   if (stages & CPP_STAGE_LAYER_MIN) {
     dim3 grid((unsigned)((max_T + 7) / 8), (unsigned)nreq);
@@ -191,8 +192,8 @@ static cudaError_t launch_dp_t(const Src& s, unsigned stages, int objective, int
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (stages & CPP_STAGE_DP_FORWARD) {
-    e = objective == CPP_DP_MINMAX ? launch_forward_minmax(s, n, nreq, max_Kp, kFormAuto, 0, st)
-                                   : launch_forward_sum(s, n, nreq, max_Kp, kFormAuto, 0, st);
+    e = objective == CPP_DP_MINMAX ? launch_forward_minmax(s, n, nreq, max_Kp, form, cpc, st)
+                                   : launch_forward_sum(s, n, nreq, max_Kp, form, cpc, st);
     if (e != cudaSuccess) return e;
   }
   if (stages & CPP_STAGE_BACKTRACK) {
@@ -212,6 +213,11 @@ cudaError_t launch_dp_batch(const BatchSrc& s, unsigned stages, int objective, i
   return launch_dp_t(s, stages, objective, n, nreq, max_T, max_Kp, st);
 }
 
+cudaError_t launch_dp_batch_form(const BatchSrc& s, unsigned stages, int objective, int n, int nreq,
+                                 int max_T, int max_Kp, int form, int cpc, cudaStream_t st) {
+  return launch_dp_t(s, stages, objective, n, nreq, max_T, max_Kp, st, form, cpc);
+}
+
 cudaError_t launch_forward(const BatchSrc& s, int objective, int n, int nreq, int max_Kp, int form,
                            int cpc, cudaStream_t st) {
   return objective == CPP_DP_MINMAX ? launch_forward_minmax(s, n, nreq, max_Kp, form, cpc, st)
@@ -228,14 +234,15 @@ int device_sm_count() {
   return n;
 }
 
-// Successor candidates per CTA of the cluster form: cpc (64 or 128) or the
+// Successor candidates per CTA of the cluster form: cpc (32, 64, 128: the record
+// exchange form; 256, 512: the wide form, which exchanges node costs only) or the
 // default (64 up to Kp = 512, 128 above), as long as the cluster has 2..8 CTAs,
-// or up to 16 (a non-portable cluster size, opted into at launch) when 64 per
-// CTA is asked for explicitly.
+// or up to 16 (a non-portable cluster size, opted into at launch) when 32 or 64
+// per CTA is asked for explicitly.
 int cluster_succ(int Kp, int cpc) {
   if (Kp <= 64 || Kp > 1024) return 0;
   const int S = cpc ? cpc : (Kp <= 512 ? 64 : 128);
-  if (S != 32 && S != 64 && S != 128) return 0;
+  if (S != 32 && S != 64 && S != 128 && S != 256 && S != 512) return 0;
   const int CS = (Kp + S - 1) / S;
   const int max_cs = (cpc == 64 || cpc == 32) ? 16 : 8;
   return CS >= 2 && CS <= max_cs ? S : 0;

@@ -533,6 +533,245 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
   cluster_barrier();  // no CTA leaves while a peer may still store into it
 }
 
+// ------------------------------------------------------------------ forward sweep, wide cluster
+// The throughput form for long requests: the one-CTA sweep above spread over a
+// cluster of CS CTAs (2..8), each owning S = 128 R successors (256 or 512), with
+// only the node costs crossing the cluster:
+//  * every CTA stages the whole next layer [n][Kp] and its node-cost row by 1-D
+//    bulk copies (TMA engine) a step ahead, takes its own successors' values from
+//    it, and writes the joint part [-q] of every node's record into the next
+//    record buffer itself;
+//  * the two thread groups split the predecessor tiles and merge as in the
+//    one-CTA form, so the lowest index wins ties;
+//  * the owner of successor k' sends C_{i+1}[k'] (4 bytes) into the record's cost
+//    slot of every other CTA by an asynchronous distributed-shared-memory store
+//    that counts its bytes on the receiver's mbarrier for that buffer; a CTA
+//    starts step i+1 once its barrier has seen every peer's costs of layer i+1
+//    (a bounded wait). Record buffers are double-buffered; a CTA writes layer
+//    i+2's costs into a peer only after it has received the peer's layer i+1
+//    costs, which the peer sends after its last read of the buffer that layer
+//    i+2 overwrites, so no step needs a cluster-wide barrier.
+// Per step a CTA exchanges S * (CS - 1) * 4 bytes instead of S * (CS - 1) * 32,
+// and sweeps S * Kp edges between three CTA barriers.
+inline size_t dpx_smem_bytes(int nj, int Kp, int R) {
+  const int NW = ((nj + 1 + 3) / 4) * 4;
+  return (size_t)2 * rec_layer_floats(NW, Kp) * 4  // records, double-buffered
+         + (size_t)nj * Kp * 4                      // raw layer staging
+         + (size_t)Kp * 4                           // node-cost staging
+         + (size_t)4 * R * kDp3Group * 4;           // group exchange
+}
+
+// 4 bytes into a peer's shared memory; completion counts 4 bytes on the peer's
+// mbarrier (both addresses from mapa).
+__device__ __forceinline__ void st_async_f32(uint32_t addr, float v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+               "r"(__float_as_uint(v)), "r"(bar)
+               : "memory");
+}
+
+template <int NJ, int R, int OBJ, class Src>
+__global__ void __launch_bounds__(kDp3Threads, 2) dpx_forward_kernel(const __grid_constant__ Src src,
+                                                                      const int CS) {
+  constexpr int NW = Rec<NJ>::NW, NP = Rec<NJ>::NP, S = R * kDp3Group;
+  const uint32_t crank = cluster_rank();
+  const Req& rq = src.req(blockIdx.x / CS);
+  const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
+  const int tid = threadIdx.x, g = tid / kDp3Group, lt = tid % kDp3Group;
+  extern __shared__ __align__(128) float smx[];
+  const int RL = rec_layer_floats(NW, Kp);
+  float* const recb = smx;                                  // [2][RL] records (skewed)
+  float* const stg = recb + 2 * (size_t)RL;                 // [NJ][Kp] staged layer
+  float* const pst = stg + (size_t)NJ * Kp;                 // [Kp] staged node costs
+  float* const xmin = pst + Kp;                             // [2][R][128]
+  int* const xtile = reinterpret_cast<int*>(xmin + 2 * R * kDp3Group);  // [2][R][128]
+  __shared__ uint64_t tbar;     // layer L's staging completes phase L
+  __shared__ uint64_t cbar[2];  // peers' costs of layer L arrive on cbar[L & 1]
+  __shared__ int timeout_flag;
+
+  const int own_lo = (int)crank * S, own_n = max(0, min(S, Kp - own_lo));
+  const uint32_t recv_bytes = (uint32_t)(Kp - own_n) * 4u;
+  const uint32_t layer_bytes = (uint32_t)(NJ * Kp * 4), pen_bytes = (uint32_t)(Kp * 4);
+  auto issue = [&](int L) {  // one thread
+    mbar_expect_tx(&tbar, layer_bytes + pen_bytes);
+    bulk_g2s(stg, rq.cand + (size_t)L * NJ * Kp, layer_bytes, &tbar);
+    bulk_g2s(pst, rq.pen + (size_t)L * Kp, pen_bytes, &tbar);
+  };
+  if (tid == 0) {
+    timeout_flag = 0;
+    mbar_init(&tbar, 1);
+    mbar_init(&cbar[0], 1);
+    mbar_init(&cbar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  cluster_barrier();  // every CTA's barriers exist before any peer stores into it
+  int pending = -1;  // thread 0: the layer whose bulk copy is issued and not yet seen complete
+  if (tid == 0) { issue(0); pending = 0; }
+  if (!mbar_wait_bounded(&tbar, 0)) atomicExch(&timeout_flag, 1);
+  else if (tid == 0) pending = -1;
+  {  // layer 0: every CTA builds all records locally
+    const float m0 = rq.pen_min[0];
+    for (int k = tid; k < Kp; k += kDp3Threads) {
+      float v[NW];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) v[j] = -stg[(size_t)j * Kp + k];
+      v[NJ] = k < K ? pst[k] - m0 : CUDART_INF_F;
+#pragma unroll
+      for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
+      float4* dst = reinterpret_cast<float4*>(recb + rec_off(NW, k));
+#pragma unroll
+      for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
+    }
+  }
+  __syncthreads();
+  const bool ok0 = !timeout_flag;  // read right after a barrier: the same in every thread
+  if (ok0 && tid == 0 && T > 1) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(1);
+    pending = 1;
+  }
+
+  int kp[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) kp[r] = own_lo + lt + r * kDp3Group;
+  const int K4 = (K + 3) & ~3;
+  const int ntiles = (K4 + kDp2Tile - 1) / kDp2Tile;
+  const int half = (ntiles + 1) / 2;
+  const int t_lo = g == 0 ? 0 : half, t_hi = g == 0 ? half : ntiles;
+  for (int i = 0; ok0 && i + 1 < T; ++i) {
+    const int L = i + 1;
+    const float* cur = recb + (size_t)(i & 1) * RL;
+    float* nxt = recb + (size_t)(L & 1) * RL;
+    if (tid == 0) mbar_expect_tx(&cbar[L & 1], recv_bytes);
+    // layer i's costs from the peers (layer 0 is local)
+    if (i > 0 && !mbar_wait_bounded_cluster(&cbar[i & 1], (uint32_t)(((i - 1) >> 1) & 1)))
+      atomicExch(&timeout_flag, 1);
+    if (!mbar_wait_bounded(&tbar, (uint32_t)(L & 1))) atomicExch(&timeout_flag, 1);
+    else if (tid == 0) pending = -1;
+    uint64_t own[R][NP];
+    float rpen[R];
+    const float m1 = rq.pen_min[L];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = kp[r] < Kp ? kp[r] : Kp - 1;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const float a = stg[(size_t)(2 * p) * Kp + k];
+        const float b = (2 * p + 1 < NJ) ? stg[(size_t)(2 * p + 1) * Kp + k] : 0.f;
+        own[r][p] = pack2(a, b);
+      }
+      rpen[r] = kp[r] < K ? pst[kp[r]] - m1 : CUDART_INF_F;
+    }
+    // the joint part of every node's record of layer L (cost slots are filled by
+    // the owners: this CTA below, the peers through the cluster)
+    for (int k = tid; k < Kp; k += kDp3Threads) {
+      float v[NW];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) v[j] = -stg[(size_t)j * Kp + k];
+      float* dst = nxt + rec_off(NW, k);
+      *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+#pragma unroll
+      for (int j = 4; j < NJ; ++j) dst[j] = v[j];
+#pragma unroll
+      for (int j = NJ + 1; j < NW; ++j) dst[j] = 0.f;
+    }
+    // everyone holds its layer-L values (the staging buffer is free), layer i's
+    // records are complete
+    __syncthreads();
+    if (timeout_flag) break;  // read right after a barrier: the same in every thread
+    if (tid == 0 && L + 1 < T) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(L + 1);
+      pending = L + 1;
+    }
+
+    float best[R];
+    int btile[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; btile[r] = -1; }
+#pragma unroll 1
+    for (int t = t_lo; t < t_hi; ++t) {
+      const int kb = t * kDp2Tile;
+      const float* base = cur + rec_off(NW, kb);
+      float tb[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) tb[r] = CUDART_INF_F;
+      if (kb + kDp2Tile <= K4) {
+#pragma unroll
+        for (int k = 0; k < kDp2Tile; k += 2) {
+          float r0[NW], r1[NW];
+          load_rec<NW>(base + k * NW, r0);
+          load_rec<NW>(base + (k + 1) * NW, r1);
+          sweep_pair<NJ, R, OBJ>(own, r0, r1, tb);
+        }
+      } else {
+        for (int k = 0; kb + k < K4; k += 2) {
+          float r0[NW], r1[NW];
+          load_rec<NW>(base + k * NW, r0);
+          load_rec<NW>(base + (k + 1) * NW, r1);
+          sweep_pair<NJ, R, OBJ>(own, r0, r1, tb);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (tb[r] < best[r]) { best[r] = tb[r]; btile[r] = t; }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      xmin[(g * R + r) * kDp3Group + lt] = best[r];
+      xtile[(g * R + r) * kDp3Group + lt] = btile[r];
+    }
+    __syncthreads();
+    // successor slot r is finished by group r % 2 (group 0 when R == 1): merge of the
+    // halves (the upper half replaces only a strictly smaller minimum), rescan of the
+    // winning tile, the cost sent to every CTA of the cluster
+    uint16_t* bprow = rq.bp + (size_t)L * Kb;
+    const uint32_t nbar = smem_u32(&cbar[L & 1]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if ((R == 1 ? 0 : (r & 1)) != g || kp[r] >= Kp) continue;
+      float bv = xmin[r * kDp3Group + lt];
+      int bt = xtile[r * kDp3Group + lt];
+      const float b1 = xmin[(R + r) * kDp3Group + lt];
+      if (b1 < bv) { bv = b1; bt = xtile[(R + r) * kDp3Group + lt]; }
+      int arg = 0;
+      if (bt >= 0) {
+        const int kb = bt * kDp2Tile, ke = min(kb + kDp2Tile, K4);
+        const float* base = cur + rec_off(NW, kb);
+        for (int k = kb; k < ke; ++k) {
+          const float* rk = base + (k - kb) * NW;
+          if (comb<OBJ>(rk[NJ], linf_rec<NJ>(own[r], rk)) == bv) { arg = k; break; }
+        }
+      }
+      const float c = kp[r] < K ? comb<OBJ>(bv, rpen[r]) : CUDART_INF_F;
+      float* slot = nxt + rec_off(NW, kp[r]) + NJ;
+      *slot = c;
+      const uint32_t a = smem_u32(slot);
+      for (int p = 1; p < CS; ++p) {
+        const uint32_t peer = (crank + (uint32_t)p) % (uint32_t)CS;
+        st_async_f32(map_peer(a, peer), c, map_peer(nbar, peer));
+      }
+      bprow[kp[r]] = (uint16_t)arg;
+    }
+    __syncthreads();  // rescans of `cur` done: the next step writes its joint part
+  }
+  __syncthreads();
+  if (timeout_flag) {
+    // a copy that never completed: wait for it once more (bounded) before leaving
+    raise_status(rq.status, CPP_ERR_TIMEOUT);
+    if (tid == 0 && pending >= 0) mbar_wait_bounded(&tbar, (uint32_t)(pending & 1));
+  } else if (T > 1) {
+    if (!mbar_wait_bounded_cluster(&cbar[(T - 1) & 1], (uint32_t)(((T - 2) >> 1) & 1)))
+      raise_status(rq.status, CPP_ERR_TIMEOUT);
+  }
+  __syncthreads();
+  if (!timeout_flag) {
+    const float* fin = recb + (size_t)((T - 1) & 1) * RL;
+    for (int k = own_lo + tid; k < own_lo + own_n; k += kDp3Threads) rq.costT[k] = fin[rec_off(NW, k) + NJ];
+  }
+  cluster_barrier();  // no CTA leaves while a peer may still store into it
+}
+
 // Any n and Kp that fit in shared memory: successor values are read back from
 // shared memory instead of registers.
 template <int OBJ, class Src>
@@ -590,6 +829,27 @@ static cudaError_t launch_fwd3_r(const Src& s, int nreq, int max_Kp, cudaStream_
   if (e != cudaSuccess) return e;
   dp3_forward_kernel<NJ, R, OBJ, Src><<<nreq, kDp3Threads, smem, st>>>(s);
   return cudaGetLastError();
+}
+
+template <int NJ, int R, int OBJ, class Src>
+static cudaError_t launch_fwdx_r(const Src& s, int nreq, int max_Kp, cudaStream_t st) {
+  const int CS = (max_Kp + R * kDp3Group - 1) / (R * kDp3Group);
+  const size_t smem = dpx_smem_bytes(NJ, max_Kp, R);
+  cudaError_t e = allow_smem(dpx_forward_kernel<NJ, R, OBJ, Src>, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nreq * CS));
+  cfg.blockDim = dim3(kDp3Threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, dpx_forward_kernel<NJ, R, OBJ, Src>, s, CS);
 }
 
 template <int NJ, int R, int OBJ, class Src>
@@ -712,6 +972,9 @@ static cudaError_t launch_fwd_nj(const Src& s, int nreq, int max_Kp, int form, i
       cpc = 64;
   }
   const int S = cluster_succ(max_Kp, cpc), CS = cluster_size(max_Kp, cpc);
+  if (S >= 256 && form != kFormCta && (form == kFormCluster || nreq * CS <= sm_count()))
+    return S == 256 ? launch_fwdx_r<NJ, 2, OBJ>(s, nreq, max_Kp, st)
+                    : launch_fwdx_r<NJ, 4, OBJ>(s, nreq, max_Kp, st);
   if (S > 0 && form != kFormCta && (form == kFormCluster || nreq * CS <= sm_count()))
     return S == 32 ? launch_fwdc_r<NJ, 1, OBJ>(s, nreq, max_Kp, st)
          : S == 64 ? launch_fwdc_r<NJ, 2, OBJ>(s, nreq, max_Kp, st)

@@ -29,6 +29,9 @@ bool dp_supported(int n, int Kp);
 cudaError_t launch_dp(const SingleSrc& s, unsigned stages, int objective, cudaStream_t st);
 cudaError_t launch_dp_batch(const BatchSrc& s, unsigned stages, int objective, int n, int nreq,
                             int max_T, int max_Kp, cudaStream_t st);
+// the same with the forward sweep's form and successors per CTA (see launch_forward)
+cudaError_t launch_dp_batch_form(const BatchSrc& s, unsigned stages, int objective, int n, int nreq,
+                                 int max_T, int max_Kp, int form, int cpc, cudaStream_t st);
 
 // dp_fwd_sum.cu, dp_fwd_minmax.cu
 constexpr int kFormAuto = 0;     // clusters when one wave of them covers the requests

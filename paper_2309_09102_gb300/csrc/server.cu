@@ -17,9 +17,17 @@
 //    is busy and a full batch is queued, one batch is formed and staged ahead,
 //    so its copies overlap the running launches instead of idling a stream.
 //    Requests that arrive while earlier batches run are admitted into the next
-//    batch as memory frees up, and the batches overlap on the device. At light
-//    load batches hold one or a few requests and run as clusters (low latency);
-//    as a class queues up its batches grow (high throughput).
+//    batch as memory frees up, and the batches overlap on the device.
+//  * two regimes. At light load (few requests queued or on the device) a batch
+//    holds requests of one size class (joint count, K bucket, T bucket) and each
+//    search runs in the latency form (the smallest tile: clusters of up to 16
+//    CTAs), the fastest for a lone request. Under load a batch takes requests of
+//    every K whose search takes about as long (one joint count and a factor-4
+//    band of the search's work per CTA, so short requests never wait for long
+//    ones), and each search runs in the throughput form (clusters of
+//    Kp / throughput_cands_per_cta CTAs, small K one CTA each): the search is
+//    launched once per K bucket, the launches forked onto auxiliary streams of
+//    the batch's stream so the buckets run side by side.
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -154,9 +162,16 @@ Layout slot_layout(int T, int Kp, int n) {
   return L;
 }
 
+struct SearchGroup {  // requests of one K bucket and form in a launch's table: [begin, begin + count)
+  int begin = 0, count = 0, max_Kp = 0;
+  bool one_cta = false;  // one CTA per request (else clusters of the throughput form)
+};
+
 struct Launch {
   std::vector<Request*> reqs;
   bool improve = false;  // an anytime improvement round (slots already resident)
+  bool latency = true;   // search in the latency form (light load) or the throughput form
+  std::vector<SearchGroup> groups;  // the search's launches (throughput form)
   int stream = -1;       // compute stream, set when the kernels are enqueued
   cudaEvent_t copied = nullptr;  // inputs and table on the device (copy stream)
   cudaEvent_t done = nullptr;
@@ -180,6 +195,12 @@ struct cpp_server {
   Arena parena;
   std::vector<cudaStream_t> streams;
   std::vector<bool> stream_busy;
+  // per compute stream: auxiliary streams and events that fork the search of a
+  // mixed-K launch into one launch per K bucket and join it back
+  static constexpr int kBuckets = 8;  // K buckets x {one CTA, clusters}
+  std::vector<cudaStream_t> aux;       // [max_inflight][kBuckets]
+  std::vector<cudaEvent_t> aux_done;   // [max_inflight][kBuckets]
+  std::vector<cudaEvent_t> fork_ev;    // [max_inflight]
   cudaStream_t copy_stream = nullptr;  // host-to-device copies of formed launches
   std::deque<Launch*> staged;          // formed, inputs copying, waiting for a stream
   std::mutex mu;
@@ -204,6 +225,7 @@ struct cpp_server {
   void anytime_step(Request* r, bool improve_round);
   cpp_status stage(Launch* L);
   cpp_status enqueue(Launch* L);
+  cudaError_t search(Launch* L, const BatchSrc& src, cudaStream_t st);
   void retire(Launch* L, cudaError_t e);
   void release_host(Request* r);
 };
@@ -217,35 +239,67 @@ void cpp_server::release_host(Request* r) {
   r->own_in.shrink_to_fit();
 }
 
-// Size class of a request: joint count, K bucket and T bucket. A launch holds one
-// class only, so a small request never waits for a large one in its batch (a
-// batch completes as a whole), and a K = 1024 request never widens the kernel
-// of K = 128 ones.
-static int size_class(const Request* r) {
-  const int kc = r->Kp <= 128 ? 0 : r->Kp <= 256 ? 1 : r->Kp <= 512 ? 2 : 3;
-  const int tc = r->T <= 256 ? 0 : r->T <= 1024 ? 1 : 2;
-  return (r->n * 4 + kc) * 3 + tc;
+// K bucket of a request (the search's launch groups) and T bucket.
+static int k_bucket(const Request* r) {
+  return r->Kp <= 128 ? 0 : r->Kp <= 256 ? 1 : r->Kp <= 512 ? 2 : 3;
+}
+static int t_bucket(const Request* r) { return r->T <= 256 ? 0 : r->T <= 1024 ? 1 : 2; }
+
+// Under load a request's search runs on one CTA, the form with the highest edge
+// rate, when that takes at most `budget_ms` at one CTA's edge rate (measured:
+// 2.35e12 edges/s over 304 CTAs, about 7.7e9 edges/s each): a short request then
+// costs no more latency than the queue already adds, and its SMs do more work.
+static bool one_cta_search(const Request* r, double budget_ms) {
+  const double edges = (double)(r->T > 1 ? r->T - 1 : 1) * r->Kp * r->Kp;
+  return edges / 7.7e9 * 1e3 <= budget_ms;
 }
 
-// Largest batch of a class: heavy classes (K > 512 or T > 1024) are capped so
-// the batch runs as clusters (8 CTAs per request, lower latency per request);
-// the others up to max_batch.
-static int class_cap(const Request* r, int max_batch, int sms) {
+// Search time class under load: the search of a request in the throughput form
+// walks T - 1 steps of min(Kp, S) x Kp edges per CTA (S successors per CTA of the
+// cluster, the whole Kp on one CTA), so requests whose (T - 1) min(Kp, S) Kp fall
+// in the same factor-4 band finish at about the same time.
+static int time_class(const Request* r, int S) {
+  const double w = (double)(r->T > 1 ? r->T - 1 : 1) * std::min(r->Kp, S) * r->Kp;
+  return std::max(0, std::min(15, (int)(std::log2(w) / 2.0)));
+}
+
+// Size class of a request. At light load: joint count, K bucket and T bucket --
+// a launch holds one class only, so a small request never waits for a large one
+// in its batch (a batch completes as a whole) and a K = 1024 request never widens
+// the kernel of K = 128 ones. Under load: joint count and search time class --
+// every K shares the launch (its search runs one launch per K bucket), and the
+// requests of a launch finish their searches at about the same time, so few of
+// them wait for the others.
+static int size_class(const Request* r, bool latency, int S) {
+  if (latency) return (r->n * 4 + k_bucket(r)) * 3 + t_bucket(r);
+  return 1000 + r->n * 16 + time_class(r, S);
+}
+
+// Largest batch of a class under light load: heavy classes (K > 512 or T > 1024)
+// are capped so the batch runs as clusters (8 CTAs per request, lower latency per
+// request); the others up to max_batch. Under load (the throughput form, whose
+// clusters are formed per request whatever the batch size) every class takes
+// up to max_batch.
+static int class_cap(const Request* r, int max_batch, int sms, bool latency) {
+  if (!latency) return max_batch;
   const bool heavy = r->Kp > 512 || r->T > 1024;
   const int cs = cluster_size(r->Kp, 0);
   return heavy ? std::max(1, std::min(max_batch, sms / std::max(1, cs))) : max_batch;
 }
 
 // Take requests of the oldest request's size class, in arrival order, while the
-// class cap, slots and arena allow.
+// class cap, slots and arena allow. The launch takes the latency form while the
+// requests queued and on the device are few, the throughput form otherwise.
 bool cpp_server::form_batch(Launch* L) {
   if (queue.empty()) return false;
-  const int cls = size_class(queue.front());
-  const int cap = class_cap(queue.front(), cfg.max_batch, sms);
+  L->latency = (int)queue.size() + resident <= cfg.latency_requests;
+  const int S = cfg.throughput_cands_per_cta;
+  const int cls = size_class(queue.front(), L->latency, S);
+  const int cap = class_cap(queue.front(), cfg.max_batch, sms, L->latency);
   for (auto it = queue.begin(); it != queue.end();) {
     Request* r = *it;
     if ((int)L->reqs.size() >= cap || resident >= cfg.max_slots) break;
-    if (size_class(r) != cls) { ++it; continue; }
+    if (size_class(r, L->latency, S) != cls) { ++it; continue; }
     size_t off;
     if (!darena.alloc(r->dev_bytes, &off)) break;  // keep arrival order within the class
     r->dev_off = off;
@@ -353,6 +407,27 @@ void cpp_server::anytime_step(Request* r, bool improve_round) {
 cpp_status cpp_server::stage(Launch* L) {
   const cudaStream_t st = copy_stream;
   const int count = (int)L->reqs.size();
+  if (!L->latency && !L->improve) {
+    // the table in K buckets (largest first), each bucket longest request first:
+    // one contiguous sub-table per search launch, and the one-CTA bucket hands
+    // its longest requests to the block scheduler first
+    const double budget = cfg.one_cta_budget_ms;
+    auto key = [budget](const Request* r) {  // search launch group of a request
+      return 2 * k_bucket(r) + (one_cta_search(r, budget) ? 1 : 0);
+    };
+    std::stable_sort(L->reqs.begin(), L->reqs.end(), [&](const Request* a, const Request* b) {
+      const int ka = key(a), kb = key(b);
+      return ka != kb ? ka > kb : a->T > b->T;
+    });
+    L->groups.clear();
+    for (int i = 0; i < count; ++i) {
+      if (L->groups.empty() || key(L->reqs[L->groups.back().begin]) != key(L->reqs[i]))
+        L->groups.push_back(SearchGroup{i, 0, 0, one_cta_search(L->reqs[i], budget)});
+      SearchGroup& g = L->groups.back();
+      ++g.count;
+      g.max_Kp = std::max(g.max_Kp, L->reqs[i]->Kp);
+    }
+  }
   const int n = L->reqs[0]->n;
   char* tab_d = d_arena + L->tab_off;
   Req* tq = reinterpret_cast<Req*>(L->tab_h);
@@ -417,6 +492,42 @@ cpp_status cpp_server::stage(Launch* L) {
   return CPP_OK;
 }
 
+// The search of a launch on its compute stream. Light load: one launch in the
+// latency form. Under load: layer minima over the whole table, then one forward
+// launch per K bucket in the throughput form -- a single bucket on the stream
+// itself, several forked onto the stream's auxiliary streams and joined back --
+// then the backtracking over the whole table.
+cudaError_t cpp_server::search(Launch* L, const BatchSrc& src, cudaStream_t st) {
+  const int count = (int)L->reqs.size(), n = L->n;
+  const int obj = cfg.params.dp_objective;
+  if (L->latency || L->groups.size() <= 1) {
+    const bool cta = !L->latency && !L->groups.empty() && L->groups[0].one_cta;
+    const int form = L->latency ? kFormAuto : cta ? kFormCta : kFormCluster;
+    const int cpc = L->latency ? 0 : cfg.throughput_cands_per_cta;
+    return launch_dp_batch_form(src, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK,
+                                obj, n, count, L->max_T, L->max_Kp, form, cpc, st);
+  }
+  cudaError_t e = launch_dp_batch_form(src, CPP_STAGE_LAYER_MIN, obj, n, count, L->max_T, L->max_Kp,
+                                       kFormAuto, 0, st);
+  if (e != cudaSuccess) return e;
+  const int s = L->stream;
+  if ((e = cudaEventRecord(fork_ev[s], st)) != cudaSuccess) return e;
+  for (size_t g = 0; g < L->groups.size(); ++g) {
+    const SearchGroup& G = L->groups[g];
+    const cudaStream_t a = aux[(size_t)s * kBuckets + g];
+    if ((e = cudaStreamWaitEvent(a, fork_ev[s], 0)) != cudaSuccess) return e;
+    // the forward sweep reads the request table only (Req::robot indexes the full table)
+    const BatchSrc sub{src.r + G.begin, src.robots};
+    if ((e = launch_forward(sub, obj, n, G.count, G.max_Kp, G.one_cta ? kFormCta : kFormCluster,
+                            cfg.throughput_cands_per_cta, a)) != cudaSuccess)
+      return e;
+    if ((e = cudaEventRecord(aux_done[(size_t)s * kBuckets + g], a)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, aux_done[(size_t)s * kBuckets + g], 0)) != cudaSuccess) return e;
+  }
+  return launch_dp_batch_form(src, CPP_STAGE_BACKTRACK, obj, n, count, L->max_T, L->max_Kp,
+                              kFormAuto, 0, st);
+}
+
 // The device part of a staged launch on its compute stream: wait for its copies,
 // the stage kernels, the device-to-host copies of the results, `done`.
 cpp_status cpp_server::enqueue(Launch* L) {
@@ -439,10 +550,7 @@ cpp_status cpp_server::enqueue(Launch* L) {
       return sfail(CPP_ERR_CUDA, "server launch: %s", cudaGetErrorString(e));
   } else if ((e = launch_mask_batch(src, n, count, max_tasks, cfg.params, any_geo, st)) !=
                  cudaSuccess ||
-             (e = launch_dp_batch(src, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD |
-                                       CPP_STAGE_BACKTRACK,
-                                  cfg.params.dp_objective, n, count, max_T, max_Kp, st)) !=
-                 cudaSuccess ||
+             (e = search(L, src, st)) != cudaSuccess ||
              (e = launch_lm_batch_geo(src, n, count, max_T, cfg.params, any_geo, st)) !=
                  cudaSuccess ||
              (e = launch_check_batch(src, count, cfg.params, st)) != cudaSuccess) {
@@ -606,14 +714,23 @@ void cpp_server_config_default(cpp_server_config_t* c) {
   c->hbm_budget_bytes = (size_t)40 << 30;
   c->pinned_bytes = (size_t)1 << 30;
   cpp_params_default(&c->params);
+  c->latency_requests = 8;
+  c->throughput_cands_per_cta = 128;
+  c->one_cta_budget_ms = 0.0;
 }
 
 cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out) {
   if (!out) return sfail(CPP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!cfg) return sfail(CPP_ERR_INVALID_ARG, "config is NULL");
-  if (cfg->max_slots < 1 || cfg->max_batch < 1 || cfg->max_inflight < 1 || cfg->max_inflight > 16)
-    return sfail(CPP_ERR_INVALID_ARG, "max_slots, max_batch >= 1 and max_inflight in [1, 16]");
+  if (cfg->max_slots < 1 || cfg->max_batch < 1 || cfg->max_inflight < 1 || cfg->max_inflight > 32)
+    return sfail(CPP_ERR_INVALID_ARG, "max_slots, max_batch >= 1 and max_inflight in [1, 32]");
+  const int tcpc = cfg->throughput_cands_per_cta;
+  if (cfg->latency_requests < 0 || (tcpc != 64 && tcpc != 128 && tcpc != 256 && tcpc != 512))
+    return sfail(CPP_ERR_INVALID_ARG,
+                 "latency_requests >= 0 and throughput_cands_per_cta in {64, 128, 256, 512}");
+  if (!(std::isfinite(cfg->one_cta_budget_ms) && cfg->one_cta_budget_ms >= 0))
+    return sfail(CPP_ERR_INVALID_ARG, "one_cta_budget_ms must be finite and >= 0");
   if (cfg->hbm_budget_bytes < 4096) return sfail(CPP_ERR_INVALID_ARG, "hbm_budget_bytes too small");
   const cpp_params_t& P = cfg->params;
   if (P.lm_iters < 0 || P.smooth_rounds < 0 || P.smooth_rounds > 1000 ||
@@ -650,6 +767,12 @@ cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out)
   s->streams.resize(cfg->max_inflight);
   s->stream_busy.assign(cfg->max_inflight, false);
   for (auto& st : s->streams) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  s->aux.resize((size_t)cfg->max_inflight * cpp_server::kBuckets);
+  s->aux_done.resize(s->aux.size());
+  s->fork_ev.resize(cfg->max_inflight);
+  for (auto& st : s->aux) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  for (auto& ev : s->aux_done) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  for (auto& ev : s->fork_ev) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
   s->worker = std::thread([s] { s->run(); });
   *out = s;
@@ -889,6 +1012,9 @@ void cpp_server_destroy(cpp_server_t* s) {
   }
   s->reqs.clear();
   for (auto st : s->streams) cudaStreamDestroy(st);
+  for (auto st : s->aux) cudaStreamDestroy(st);
+  for (auto ev : s->aux_done) cudaEventDestroy(ev);
+  for (auto ev : s->fork_ev) cudaEventDestroy(ev);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->d_arena) cudaFree(s->d_arena);
   if (s->h_pinned) cudaFreeHost(s->h_pinned);

@@ -182,3 +182,54 @@ def results_after_run(S):
     S["batch"].run(cppflow.STAGE_ALL, S["stream"])
     S["stream"].synchronize()
     return results(S)
+
+
+WIDE = [(40, 1024), (25, 700), (33, 520), (50, 300), (20, 1000), (31, 128), (3, 1024), (1, 600),
+        (28, 800)]
+
+
+@pytest.mark.parametrize("objective", [0, 1])
+def test_wide_clusters_match_the_oracle(objective):
+    """The wide cluster form (256 or 512 successors per CTA, only node costs crossing the
+    cluster) on a batch with K up to 1024 and ragged tails (Kp not a multiple of the
+    tile, so the last CTA of a cluster owns fewer successors), T = 1 and T = 3
+    included: indices and costs equal the oracle's FP32 search on the GPU's node costs,
+    for both objectives, and equal the one-CTA form bit for bit."""
+    tt = torch()
+    pbs = [problems.build(workload(900 + r, T, K)) for r, (T, K) in enumerate(WIDE)]
+    _, cp = params_pair(lm_iters=10, dp_objective=objective)
+    robots = [cppflow.robot_from_arm(pb.arm) for pb in pbs]
+    bufs, descs = [], []
+    for r, pb in enumerate(pbs):
+        T, n, Kp = pb.cand.shape
+        b = dict(cand=dev(pb.cand), targets=dev(pb.targets),
+                 sel=tt.empty(T, dtype=tt.int32, device="cuda:0"),
+                 q=tt.empty(T, n, dtype=tt.float32, device="cuda:0"),
+                 err=tt.empty(T, 2, dtype=tt.float64, device="cuda:0"),
+                 rep=tt.zeros(cppflow.REPORT_BYTES, dtype=tt.uint8, device="cuda:0"),
+                 best=tt.empty(1, dtype=tt.float32, device="cuda:0"))
+        bufs.append(b)
+        descs.append(cppflow.PlanDesc(T, pb.K, Kp, r, b["cand"].data_ptr(), b["targets"].data_ptr(),
+                                      b["sel"].data_ptr(), b["q"].data_ptr(), b["err"].data_ptr(),
+                                      b["rep"].data_ptr(), b["best"].data_ptr()))
+    ws = tt.empty(cppflow.plan_batch_workspace_size(descs, robots), dtype=tt.uint8, device="cuda:0")
+    st = tt.zeros(len(descs), dtype=tt.int32, device="cuda:0")
+    stream = tt.cuda.Stream()
+    batch = cppflow.Batch(robots, cp, descs, ws, st, stream)
+    S = dict(bufs=bufs, st=st, stream=stream, batch=batch)
+    try:
+        base = run_with(S, 0.0)            # one CTA per request
+        for r, pb in enumerate(pbs):
+            g = run_mask(robots[r], cp, pb.cand, pb.targets, pb.K)
+            ref = oracle.dp_f32(pb.cand, g.pen, pb.K, objective)
+            np.testing.assert_array_equal(base[r]["sel"], ref["sel"])
+            assert float(base[r]["best"][0]) == float(ref["best"])
+        for cpc in (256, 512):
+            wide = run_with(S, 1e-9, cpc)
+            assert S["batch"].launches(cppflow.STAGE_DP_FORWARD) >= 2
+            for r in range(len(pbs)):
+                np.testing.assert_array_equal(wide[r]["sel"], base[r]["sel"], err_msg=f"cpc {cpc} r {r}")
+                np.testing.assert_array_equal(wide[r]["best"], base[r]["best"])
+                np.testing.assert_array_equal(wide[r]["q"], base[r]["q"])
+    finally:
+        batch.close()
