@@ -597,19 +597,17 @@ typedef struct cpp_server_config {
     /* Search form by load. While at most latency_requests requests are queued or on
      * the device, a launch runs each request's search in the latency form (the
      * smallest tile: clusters of up to 16 CTAs, 32 or 64 successors per CTA), the
-     * fastest for one request; above it, in the throughput form: clusters of
-     * throughput_cands_per_cta successors per CTA (Kp / that many CTAs; requests
-     * with Kp at or below it run one CTA each; 256 and 512 take the wide cluster
-     * form of cpp_batch_set_split), the form with the highest edge rate per SM.
-     * Results are identical in every form. (defaults 8 and 128;
-     * throughput_cands_per_cta in {64, 128, 256, 512}, latency_requests >= 0) */
+     * fastest for one request. Above it, a launch takes requests of every K whose
+     * searches take about as long, and runs each search in the form with the
+     * highest edge rate per SM whose estimated time is at most search_budget_ms:
+     * one CTA, clusters of 512 or of 256 successors per CTA (the wide form of
+     * cpp_batch_set_split), else clusters of 128 successors per CTA (estimates from
+     * rates measured on GB300, stated in the server source). Results are identical
+     * in every form. (defaults 8 and 12 ms; latency_requests >= 0,
+     * search_budget_ms >= 0) */
     int32_t latency_requests;
-    int32_t throughput_cands_per_cta;
-    /* Under load, a request whose search takes at most this long on one CTA (at
-     * one CTA's edge rate, about 7.7e9 edges/s on GB300) runs on one CTA, the form
-     * with the highest edge rate per SM; 0 keeps every cluster-capable request in
-     * clusters (ms, >= 0, default 0). */
-    double one_cta_budget_ms;
+    int32_t reserved_;
+    double search_budget_ms;
 } cpp_server_config_t;
 
 #define CPP_REQ_BORROW 1  /* inputs stay valid and unchanged until the plan is collected:

@@ -121,7 +121,7 @@ class ServerConfig(C.Structure):
     _fields_ = [("device", C.c_int32), ("max_slots", C.c_int32), ("max_batch", C.c_int32),
                 ("max_inflight", C.c_int32), ("hbm_budget_bytes", C.c_size_t),
                 ("pinned_bytes", C.c_size_t), ("params", Params), ("latency_requests", C.c_int32),
-                ("throughput_cands_per_cta", C.c_int32), ("one_cta_budget_ms", C.c_double)]
+                ("reserved_", C.c_int32), ("search_budget_ms", C.c_double)]
 
 
 class PlanReq(C.Structure):
@@ -564,8 +564,7 @@ class Server:
     def __init__(self, params: Params | None = None, device: int = 0, hbm_budget: int | None = None,
                  max_slots: int | None = None, max_batch: int | None = None,
                  max_inflight: int | None = None, pinned_bytes: int | None = None,
-                 latency_requests: int | None = None, throughput_cands_per_cta: int | None = None,
-                 one_cta_budget_ms: float | None = None):
+                 latency_requests: int | None = None, search_budget_ms: float | None = None):
         cfg = ServerConfig()
         lib().cpp_server_config_default(C.byref(cfg))
         cfg.device = device
@@ -574,8 +573,7 @@ class Server:
         for name, v in (("hbm_budget_bytes", hbm_budget), ("max_slots", max_slots),
                         ("max_batch", max_batch), ("max_inflight", max_inflight),
                         ("pinned_bytes", pinned_bytes), ("latency_requests", latency_requests),
-                        ("throughput_cands_per_cta", throughput_cands_per_cta),
-                        ("one_cta_budget_ms", one_cta_budget_ms)):
+                        ("search_budget_ms", search_budget_ms)):
             if v is not None:
                 setattr(cfg, name, v)
         h = C.c_void_p()

@@ -22,12 +22,13 @@
 //    holds requests of one size class (joint count, K bucket, T bucket) and each
 //    search runs in the latency form (the smallest tile: clusters of up to 16
 //    CTAs), the fastest for a lone request. Under load a batch takes requests of
-//    every K whose search takes about as long (one joint count and a factor-4
-//    band of the search's work per CTA, so short requests never wait for long
-//    ones), and each search runs in the throughput form (clusters of
-//    Kp / throughput_cands_per_cta CTAs, small K one CTA each): the search is
-//    launched once per K bucket, the launches forked onto auxiliary streams of
-//    the batch's stream so the buckets run side by side.
+//    every K whose searches take about as long (one joint count and a factor-2
+//    band of estimated search time, so short requests never wait for long
+//    ones), and each search runs in the form with the highest edge rate per SM
+//    that stays within search_budget_ms (one CTA, wide clusters of 512 or 256
+//    successors per CTA, clusters of 128): the search is launched once per K
+//    bucket and form, the launches forked onto auxiliary streams of the batch's
+//    stream so they run side by side.
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -162,9 +163,10 @@ Layout slot_layout(int T, int Kp, int n) {
   return L;
 }
 
-struct SearchGroup {  // requests of one K bucket and form in a launch's table: [begin, begin + count)
+struct SearchGroup {  // requests of one K bucket and search form in a launch's table:
+                     // [begin, begin + count)
   int begin = 0, count = 0, max_Kp = 0;
-  bool one_cta = false;  // one CTA per request (else clusters of the throughput form)
+  int form = 0, cpc = 0;  // the forward sweep's form and successors per CTA
 };
 
 struct Launch {
@@ -197,7 +199,7 @@ struct cpp_server {
   std::vector<bool> stream_busy;
   // per compute stream: auxiliary streams and events that fork the search of a
   // mixed-K launch into one launch per K bucket and join it back
-  static constexpr int kBuckets = 8;  // K buckets x {one CTA, clusters}
+  static constexpr int kBuckets = 8;  // auxiliary streams per compute stream
   std::vector<cudaStream_t> aux;       // [max_inflight][kBuckets]
   std::vector<cudaEvent_t> aux_done;   // [max_inflight][kBuckets]
   std::vector<cudaEvent_t> fork_ev;    // [max_inflight]
@@ -245,22 +247,41 @@ static int k_bucket(const Request* r) {
 }
 static int t_bucket(const Request* r) { return r->T <= 256 ? 0 : r->T <= 1024 ? 1 : 2; }
 
-// Under load a request's search runs on one CTA, the form with the highest edge
-// rate, when that takes at most `budget_ms` at one CTA's edge rate (measured:
-// 2.35e12 edges/s over 304 CTAs, about 7.7e9 edges/s each): a short request then
-// costs no more latency than the queue already adds, and its SMs do more work.
-static bool one_cta_search(const Request* r, double budget_ms) {
-  const double edges = (double)(r->T > 1 ? r->T - 1 : 1) * r->Kp * r->Kp;
-  return edges / 7.7e9 * 1e3 <= budget_ms;
+// The search form of a request under load: the form with the highest edge rate
+// per SM whose search takes at most `budget_ms`, else the fastest throughput form.
+// Per CTA at two CTAs per SM a one-CTA search sweeps about 7.7e9 edges/s on GB300
+// (measured: 2.35e12 edges/s over 304 CTAs); relative to it, measured at full
+// occupancy with T = 300: the wide cluster form at 512 successors per CTA 1.0 (K =
+// 1024), at 256 per CTA 0.79 (K = 1024) and 0.98 (K = 512), the record-exchange
+// form at 128 per CTA 0.66. A cluster of CS CTAs owning S successors each takes
+// (T - 1) S Kp / (7.7e9 x efficiency) seconds.
+struct SearchForm {
+  int form, cpc;   // forward sweep form and successors per CTA
+  double est_ms;   // estimated search time
+  int rank;        // index of the form (one CTA, wide 512, wide 256, 128 per CTA)
+};
+static SearchForm throughput_form(const Request* r, double budget_ms) {
+  constexpr double kCtaEdgesPerS = 7.7e9;
+  const double steps = r->T > 1 ? r->T - 1 : 1, Kp = r->Kp;
+  const SearchForm cand[4] = {
+      {kFormCta, 0, steps * Kp * Kp / kCtaEdgesPerS * 1e3, 0},
+      {kFormCluster, 512, steps * 512.0 * Kp / (kCtaEdgesPerS * 1.0) * 1e3, 1},
+      {kFormCluster, 256, steps * 256.0 * Kp / (kCtaEdgesPerS * (r->Kp > 512 ? 0.79 : 0.98)) * 1e3, 2},
+      {kFormCluster, 128, steps * 128.0 * Kp / (kCtaEdgesPerS * 0.66) * 1e3, 3}};
+  const SearchForm* last = &cand[0];
+  for (const SearchForm& f : cand) {
+    if (f.form == kFormCluster && cluster_size(r->Kp, f.cpc) < 2) continue;  // no such cluster
+    last = &f;
+    if (f.est_ms <= budget_ms) return f;
+  }
+  return *last;
 }
 
-// Search time class under load: the search of a request in the throughput form
-// walks T - 1 steps of min(Kp, S) x Kp edges per CTA (S successors per CTA of the
-// cluster, the whole Kp on one CTA), so requests whose (T - 1) min(Kp, S) Kp fall
-// in the same factor-4 band finish at about the same time.
-static int time_class(const Request* r, int S) {
-  const double w = (double)(r->T > 1 ? r->T - 1 : 1) * std::min(r->Kp, S) * r->Kp;
-  return std::max(0, std::min(15, (int)(std::log2(w) / 2.0)));
+// Search time class under load: requests whose estimated search times (in their
+// throughput forms) fall in the same factor-2 band finish at about the same time.
+static int time_class(const Request* r, double budget_ms) {
+  const double ms = throughput_form(r, budget_ms).est_ms;
+  return std::max(0, std::min(31, (int)std::floor(std::log2(std::max(ms, 1e-3)) + 10.0)));
 }
 
 // Size class of a request. At light load: joint count, K bucket and T bucket --
@@ -270,9 +291,9 @@ static int time_class(const Request* r, int S) {
 // every K shares the launch (its search runs one launch per K bucket), and the
 // requests of a launch finish their searches at about the same time, so few of
 // them wait for the others.
-static int size_class(const Request* r, bool latency, int S) {
+static int size_class(const Request* r, bool latency, double budget_ms) {
   if (latency) return (r->n * 4 + k_bucket(r)) * 3 + t_bucket(r);
-  return 1000 + r->n * 16 + time_class(r, S);
+  return 1000 + r->n * 32 + time_class(r, budget_ms);
 }
 
 // Largest batch of a class under light load: heavy classes (K > 512 or T > 1024)
@@ -293,13 +314,13 @@ static int class_cap(const Request* r, int max_batch, int sms, bool latency) {
 bool cpp_server::form_batch(Launch* L) {
   if (queue.empty()) return false;
   L->latency = (int)queue.size() + resident <= cfg.latency_requests;
-  const int S = cfg.throughput_cands_per_cta;
-  const int cls = size_class(queue.front(), L->latency, S);
+  const double budget = cfg.search_budget_ms;
+  const int cls = size_class(queue.front(), L->latency, budget);
   const int cap = class_cap(queue.front(), cfg.max_batch, sms, L->latency);
   for (auto it = queue.begin(); it != queue.end();) {
     Request* r = *it;
     if ((int)L->reqs.size() >= cap || resident >= cfg.max_slots) break;
-    if (size_class(r, L->latency, S) != cls) { ++it; continue; }
+    if (size_class(r, L->latency, budget) != cls) { ++it; continue; }
     size_t off;
     if (!darena.alloc(r->dev_bytes, &off)) break;  // keep arrival order within the class
     r->dev_off = off;
@@ -411,9 +432,9 @@ cpp_status cpp_server::stage(Launch* L) {
     // the table in K buckets (largest first), each bucket longest request first:
     // one contiguous sub-table per search launch, and the one-CTA bucket hands
     // its longest requests to the block scheduler first
-    const double budget = cfg.one_cta_budget_ms;
+    const double budget = cfg.search_budget_ms;
     auto key = [budget](const Request* r) {  // search launch group of a request
-      return 2 * k_bucket(r) + (one_cta_search(r, budget) ? 1 : 0);
+      return 4 * k_bucket(r) + throughput_form(r, budget).rank;
     };
     std::stable_sort(L->reqs.begin(), L->reqs.end(), [&](const Request* a, const Request* b) {
       const int ka = key(a), kb = key(b);
@@ -421,8 +442,10 @@ cpp_status cpp_server::stage(Launch* L) {
     });
     L->groups.clear();
     for (int i = 0; i < count; ++i) {
-      if (L->groups.empty() || key(L->reqs[L->groups.back().begin]) != key(L->reqs[i]))
-        L->groups.push_back(SearchGroup{i, 0, 0, one_cta_search(L->reqs[i], budget)});
+      if (L->groups.empty() || key(L->reqs[L->groups.back().begin]) != key(L->reqs[i])) {
+        const SearchForm f = throughput_form(L->reqs[i], budget);
+        L->groups.push_back(SearchGroup{i, 0, 0, f.form, f.cpc});
+      }
       SearchGroup& g = L->groups.back();
       ++g.count;
       g.max_Kp = std::max(g.max_Kp, L->reqs[i]->Kp);
@@ -501,9 +524,8 @@ cudaError_t cpp_server::search(Launch* L, const BatchSrc& src, cudaStream_t st) 
   const int count = (int)L->reqs.size(), n = L->n;
   const int obj = cfg.params.dp_objective;
   if (L->latency || L->groups.size() <= 1) {
-    const bool cta = !L->latency && !L->groups.empty() && L->groups[0].one_cta;
-    const int form = L->latency ? kFormAuto : cta ? kFormCta : kFormCluster;
-    const int cpc = L->latency ? 0 : cfg.throughput_cands_per_cta;
+    const int form = L->latency ? kFormAuto : L->groups[0].form;
+    const int cpc = L->latency ? 0 : L->groups[0].cpc;
     return launch_dp_batch_form(src, CPP_STAGE_LAYER_MIN | CPP_STAGE_DP_FORWARD | CPP_STAGE_BACKTRACK,
                                 obj, n, count, L->max_T, L->max_Kp, form, cpc, st);
   }
@@ -514,15 +536,15 @@ cudaError_t cpp_server::search(Launch* L, const BatchSrc& src, cudaStream_t st) 
   if ((e = cudaEventRecord(fork_ev[s], st)) != cudaSuccess) return e;
   for (size_t g = 0; g < L->groups.size(); ++g) {
     const SearchGroup& G = L->groups[g];
-    const cudaStream_t a = aux[(size_t)s * kBuckets + g];
+    const size_t slot = (size_t)s * kBuckets + g % kBuckets;  // groups beyond kBuckets share
+    const cudaStream_t a = aux[slot];
     if ((e = cudaStreamWaitEvent(a, fork_ev[s], 0)) != cudaSuccess) return e;
     // the forward sweep reads the request table only (Req::robot indexes the full table)
     const BatchSrc sub{src.r + G.begin, src.robots};
-    if ((e = launch_forward(sub, obj, n, G.count, G.max_Kp, G.one_cta ? kFormCta : kFormCluster,
-                            cfg.throughput_cands_per_cta, a)) != cudaSuccess)
+    if ((e = launch_forward(sub, obj, n, G.count, G.max_Kp, G.form, G.cpc, a)) != cudaSuccess)
       return e;
-    if ((e = cudaEventRecord(aux_done[(size_t)s * kBuckets + g], a)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(st, aux_done[(size_t)s * kBuckets + g], 0)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(aux_done[slot], a)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, aux_done[slot], 0)) != cudaSuccess) return e;
   }
   return launch_dp_batch_form(src, CPP_STAGE_BACKTRACK, obj, n, count, L->max_T, L->max_Kp,
                               kFormAuto, 0, st);
@@ -715,8 +737,7 @@ void cpp_server_config_default(cpp_server_config_t* c) {
   c->pinned_bytes = (size_t)1 << 30;
   cpp_params_default(&c->params);
   c->latency_requests = 8;
-  c->throughput_cands_per_cta = 128;
-  c->one_cta_budget_ms = 0.0;
+  c->search_budget_ms = 12.0;
 }
 
 cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out) {
@@ -725,12 +746,9 @@ cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out)
   if (!cfg) return sfail(CPP_ERR_INVALID_ARG, "config is NULL");
   if (cfg->max_slots < 1 || cfg->max_batch < 1 || cfg->max_inflight < 1 || cfg->max_inflight > 32)
     return sfail(CPP_ERR_INVALID_ARG, "max_slots, max_batch >= 1 and max_inflight in [1, 32]");
-  const int tcpc = cfg->throughput_cands_per_cta;
-  if (cfg->latency_requests < 0 || (tcpc != 64 && tcpc != 128 && tcpc != 256 && tcpc != 512))
-    return sfail(CPP_ERR_INVALID_ARG,
-                 "latency_requests >= 0 and throughput_cands_per_cta in {64, 128, 256, 512}");
-  if (!(std::isfinite(cfg->one_cta_budget_ms) && cfg->one_cta_budget_ms >= 0))
-    return sfail(CPP_ERR_INVALID_ARG, "one_cta_budget_ms must be finite and >= 0");
+  if (cfg->latency_requests < 0) return sfail(CPP_ERR_INVALID_ARG, "latency_requests must be >= 0");
+  if (!(std::isfinite(cfg->search_budget_ms) && cfg->search_budget_ms >= 0))
+    return sfail(CPP_ERR_INVALID_ARG, "search_budget_ms must be finite and >= 0");
   if (cfg->hbm_budget_bytes < 4096) return sfail(CPP_ERR_INVALID_ARG, "hbm_budget_bytes too small");
   const cpp_params_t& P = cfg->params;
   if (P.lm_iters < 0 || P.smooth_rounds < 0 || P.smooth_rounds > 1000 ||

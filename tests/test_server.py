@@ -115,20 +115,22 @@ def test_cancel_and_validation():
     assert s["completed"] == len(pbs) - len(cancelled)
 
 
-@pytest.mark.parametrize("cpc,budget", [(256, 0.0), (512, 0.0), (128, 0.0), (256, 1000.0)])
-def test_throughput_form_mixed_k_equals_alone(cpc, budget):
+@pytest.mark.parametrize("budget", [0.0, 0.05, 0.5, 1000.0])
+def test_throughput_form_mixed_k_equals_alone(budget):
     """Under load (latency_requests = 0: every launch in the throughput form) requests of
-    different K share a launch; the search runs once per K bucket on forked streams, as
-    clusters of `cpc` successors per CTA (a K bucket's largest Kp sets the cluster, so a
-    smaller request's last CTAs may own nothing) or, within the one-CTA budget, one CTA
-    per request. Every plan equals cpp_plan alone."""
+    different K share a launch; the search runs once per K bucket and form on forked
+    streams, each request in the most efficient form within the time budget: one CTA,
+    wide clusters of 512 or 256 successors per CTA, clusters of 128 (a group's largest
+    Kp sets the cluster, so a smaller request's last CTAs may own nothing). The budgets
+    here move these small requests across all four forms. Every plan equals cpp_plan
+    alone."""
     shapes = [(30, 1000), (45, 300), (20, 128), (61, 600), (12, 1024), (33, 260), (40, 90),
               (25, 544), (1, 700), (2, 513)]
     pbs = [problems.small(T=T, K=K, seed=800 + i) for i, (T, K) in enumerate(shapes)]
     _, cp = params_pair(lm_iters=10)
     robots = [cppflow.robot_from_arm(pb.arm) for pb in pbs]
     with cppflow.Server(cp, hbm_budget=1 << 30, max_inflight=4, max_batch=64, latency_requests=0,
-                        throughput_cands_per_cta=cpc, one_cta_budget_ms=budget) as srv:
+                        search_budget_ms=budget) as srv:
         tickets = [srv.submit(robots[i], pb.cand, pb.targets, pb.K) for i, pb in enumerate(pbs)]
         results = [srv.wait(t) for t in tickets]
         stats = srv.stats()
