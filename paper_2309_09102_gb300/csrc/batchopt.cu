@@ -99,6 +99,7 @@ BatchOptLayout batch_opt_layout(int T, int K, int n, int lanes) {
   L.mjac = o;  o += align256(sizeof(float) * (size_t)K);
   L.reqs = o;  o += align256(sizeof(Req) * (size_t)lanes);
   L.robot = o; o += align256(sizeof(cpp_robot_t));
+  L.lm = o;    o += lm_aux_layout(1, lanes).total;
   L.q_in = o;  o += align256(sizeof(float) * (size_t)lanes * T * n);
   L.total = o;
   return L;
@@ -131,6 +132,16 @@ cudaError_t launch_batch_opt(const cpp_robot_t& robot, const cpp_params_t& P, co
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ws + L.robot, &robot, sizeof(cpp_robot_t), cudaMemcpyHostToDevice, st);
+  // the LM's work distribution: waypoint prefix sums and the robot's views
+  const LmAuxLayout LA = lm_aux_layout(1, lanes);
+  std::vector<int> wp(lanes + 1);
+  const int wp_total = lm_prefix(reqs.data(), lanes, wp.data());
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ws + L.lm + LA.wp, wp.data(), sizeof(int) * (lanes + 1),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = launch_robot_views(reinterpret_cast<const cpp_robot_t*>(ws + L.robot), 1,
+                           reinterpret_cast<RobotViews*>(ws + L.lm + LA.views), st);
   if (e != cudaSuccess) return e;
   lane_mjac_kernel<<<(K + 255) / 256, 256, 0, st>>>(cand, T, K, Kp, n, mjac);
   select_lanes_kernel<<<1, kSelThreads, 0, st>>>(mjac, K, lanes, sel, sel_mjac);
@@ -139,7 +150,8 @@ cudaError_t launch_batch_opt(const cpp_robot_t& robot, const cpp_params_t& P, co
   gather_lanes_kernel<<<blocks, 256, 0, st>>>(cand, T, Kp, n, lanes, sel, q_in);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const BatchSrc src{reinterpret_cast<const Req*>(ws + L.reqs),
-                     reinterpret_cast<const cpp_robot_t*>(ws + L.robot)};
+                     reinterpret_cast<const cpp_robot_t*>(ws + L.robot),
+                     lm_aux_at(ws + L.lm, LA, lanes, wp_total)};
   if ((e = launch_lm_batch(src, n, lanes, T, P, st)) != cudaSuccess) return e;
   if ((e = launch_check_batch(src, lanes, P, st)) != cudaSuccess) return e;
   first_valid_kernel<<<1, 1, 0, st>>>(reports, lanes, best);

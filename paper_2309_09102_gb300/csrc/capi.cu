@@ -626,7 +626,8 @@ cpp_status cpp_batch_opt(const cpp_robot_t* robot, const cpp_params_t* params, c
 // ------------------------------------------------------------------ many requests
 namespace {
 struct BatchLayout {
-  size_t reqs, sched, robots, per_req_base, total;
+  size_t reqs, sched, robots, lm, per_req_base, total;
+  LmAuxLayout lm_layout;
   std::vector<PlanLayout> L;
   std::vector<size_t> off;
 };
@@ -636,6 +637,8 @@ BatchLayout batch_layout(const cpp_plan_desc_t* d, int count, int n_robots, cons
   B.reqs = o;   o += align256(sizeof(Req) * (size_t)count);
   B.sched = o;  o += align256(sizeof(Req) * (size_t)count);
   B.robots = o; o += align256(sizeof(cpp_robot_t) * (size_t)n_robots);
+  B.lm_layout = lm_aux_layout(n_robots, count);
+  B.lm = o;     o += B.lm_layout.total;
   B.per_req_base = o;
   for (int r = 0; r < count; ++r) {
     const int n = robots[d[r].robot].n;
@@ -955,10 +958,23 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
                                                  sizeof(cpp_robot_t) * n_robots,
                                                  cudaMemcpyHostToDevice, st), "cpp_batch_create"))
     return e;
+  // the LM's work distribution: waypoint prefix sums and robot views
+  std::vector<int> wp(count + 1);
+  const int wp_total = lm_prefix(reqs.data(), count, wp.data());
+  if (cpp_status e = cuda_status(cudaMemcpyAsync(ws + B.lm + B.lm_layout.wp, wp.data(),
+                                                 sizeof(int) * (count + 1), cudaMemcpyHostToDevice,
+                                                 st), "cpp_batch_create"))
+    return e;
+  if (cpp_status e = cuda_status(
+          launch_robot_views(reinterpret_cast<const cpp_robot_t*>(ws + B.robots), n_robots,
+                             reinterpret_cast<RobotViews*>(ws + B.lm + B.lm_layout.views), st),
+          "cpp_batch_create"))
+    return e;
   cpp_batch* b = new (std::nothrow) cpp_batch;
   if (!b) return fail(CPP_ERR_OOM, "host allocation failed");
   b->src = BatchSrc{reinterpret_cast<const Req*>(ws + B.reqs),
-                    reinterpret_cast<const cpp_robot_t*>(ws + B.robots)};
+                    reinterpret_cast<const cpp_robot_t*>(ws + B.robots),
+                    lm_aux_at(ws + B.lm, B.lm_layout, count, wp_total)};
   b->params = *params;
   b->n = n; b->count = count; b->max_T = max_T; b->max_Kp = max_Kp; b->max_tasks = max_tasks;
   b->d_sched = reinterpret_cast<Req*>(ws + B.sched);

@@ -75,9 +75,20 @@ struct SingleSrc {
   __device__ __forceinline__ const cpp_robot_t& rob(int) const { return robot; }
   __device__ __forceinline__ const GeoF* geom(const Req&) const { return has_geo ? &geo : nullptr; }
 };
+struct RobotViews;  // FP32 and FP64 views of a robot (below)
+// Work distribution of a batched LM launch: robot views of the robot table,
+// prefix sums of the requests' waypoint counts (wp_begin[r], nreq + 1 entries)
+// and a counter that is zero when the launch starts.
+struct LmAux {
+  const RobotViews* views;
+  const int* wp_begin;
+  int* counter;
+  int total, nreq;
+};
 struct BatchSrc {
   const Req* r;
   const cpp_robot_t* robots;
+  LmAux lm;  // set by callers that run the LM on this table
   __device__ __forceinline__ const Req& req(int i) const { return r[i]; }
   __device__ __forceinline__ const cpp_robot_t& rob(int i) const { return robots[i]; }
   __device__ __forceinline__ const GeoF* geom(const Req& q) const { return q.geo; }
@@ -96,6 +107,13 @@ struct RobotF {      // FP32 view for the FP32 kernels
 struct RobotD {      // FP64 view for the FP64 paths
   int n;
   double a[kMaxJ], d[kMaxJ], ca[kMaxJ], sa[kMaxJ], th0[kMaxJ], lo[kMaxJ], hi[kMaxJ];
+};
+// Both views of one robot in device memory (formed as stage_robot forms them with
+// the FP64 view wanted): a lane of the batched LM may hold a waypoint of any
+// request, so it reads its robot from an array of these.
+struct RobotViews {
+  RobotF f;
+  RobotD d;
 };
 
 // Threads 0..15 of the block fill the views; the caller synchronises afterwards.

@@ -54,6 +54,9 @@ int cluster_size(int Kp, int cpc);  // CTAs per cluster (0: no cluster form)
 int device_sm_count();     // SMs of the current device
 
 // lm.cu
+// Robot views (RobotViews) of n robots, for the batched LM (one block per robot).
+cudaError_t launch_robot_views(const cpp_robot_t* robots, int n, RobotViews* views,
+                               cudaStream_t st);
 cudaError_t launch_lm(const SingleSrc& s, const cpp_params_t& P, bool want_err, cudaStream_t st);
 cudaError_t launch_lm_batch(const BatchSrc& s, int n, int nreq, int max_T, const cpp_params_t& P,
                             cudaStream_t st);
@@ -75,7 +78,7 @@ cudaError_t launch_check_batch(const BatchSrc& s, int nreq, const cpp_params_t& 
 // batchopt.cu
 struct BatchOptLayout {  // workspace of cpf-BatchOpt: lane mjac, pseudo-request table, robot,
                          // gathered trajectories
-  size_t mjac, reqs, robot, q_in, total;
+  size_t mjac, reqs, robot, lm, q_in, total;
 };
 BatchOptLayout batch_opt_layout(int T, int K, int n, int lanes);
 cudaError_t launch_batch_opt(const cpp_robot_t& robot, const cpp_params_t& P, const float* cand,
@@ -132,6 +135,37 @@ inline PlanLayout plan_layout(int T, int Kp, int n) {
   L.smooth = o;  o += align256(smooth_ws_bytes(T, n));
   L.total = o;
   return L;
+}
+
+// Device region of a batched LM's work distribution (LmAux): robot views of the
+// robot table, waypoint prefix sums, the counter.
+struct LmAuxLayout {
+  size_t views, wp, counter, total;
+};
+inline LmAuxLayout lm_aux_layout(int n_views, int nreq) {
+  LmAuxLayout L;
+  size_t o = 0;
+  L.views = o;   o += align256(sizeof(RobotViews) * (size_t)n_views);
+  L.wp = o;      o += align256(sizeof(int) * (size_t)(nreq + 1));
+  L.counter = o; o += 256;
+  L.total = o;
+  return L;
+}
+// Prefix sums of the waypoint counts of `reqs` (nreq + 1 entries); returns the total.
+inline int lm_prefix(const Req* reqs, int nreq, int* wp) {
+  int t = 0;
+  for (int r = 0; r < nreq; ++r) { wp[r] = t; t += reqs[r].T; }
+  wp[nreq] = t;
+  return t;
+}
+inline LmAux lm_aux_at(char* base, const LmAuxLayout& L, int nreq, int total) {
+  LmAux a;
+  a.views = reinterpret_cast<const RobotViews*>(base + L.views);
+  a.wp_begin = reinterpret_cast<const int*>(base + L.wp);
+  a.counter = reinterpret_cast<int*>(base + L.counter);
+  a.total = total;
+  a.nreq = nreq;
+  return a;
 }
 
 // Fill the scratch pointers of a request from a plan workspace at `base`.

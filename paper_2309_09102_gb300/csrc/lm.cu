@@ -18,6 +18,8 @@
 // over a warp leaves most lanes of every FP64 instruction idle; a thread per
 // waypoint fills all 32.
 // The joint state is held in FP64; q_out is its FP32 rounding.
+#include <type_traits>
+
 #include "collide.cuh"
 #include "internal.h"
 
@@ -38,6 +40,8 @@ struct LmArgs {
 struct CheckArgs {
   double tau_pos, tau_rot, jump_max;
 };
+
+
 
 // Work counters of the LM stage (cpp_counters_read): one atomic add per warp.
 __device__ cpp_counters_t g_lm_counters;
@@ -94,50 +98,154 @@ __device__ __forceinline__ double lm_eval(const RB& rb, int n, const double* q, 
   return 0.5 * s;
 }
 
+__global__ void __launch_bounds__(32) robot_views_kernel(const cpp_robot_t* robots, RobotViews* views) {
+  __shared__ RobotF rf;
+  __shared__ RobotD rd;
+  stage_robot(robots[blockIdx.x], 0.0, &rf, &rd);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    views[blockIdx.x].f = rf;
+    views[blockIdx.x].d = rd;
+  }
+}
+
+// One LM refinement kernel for single requests and batches. Each lane carries
+// the state of one waypoint (q, the target, F, lambda, the iteration count) and
+// every trip of the loop runs one iteration of its waypoint, so the lanes of a
+// warp advance together whatever waypoints they hold. A single request gives
+// each lane one waypoint (one warp per 32 waypoints). A batch runs a persistent
+// grid of one-warp blocks whose lanes take waypoints from a counter over the
+// batch's waypoints (prefix sums over its requests) as their previous ones
+// finish, so a warp no longer waits for its slowest waypoint and no second wave
+// of blocks follows the first. The arithmetic of every waypoint is the same in
+// both, so a request's result does not depend on its batch.
 template <int NJ, class F, class Src>
 __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ Src src,
                                                          const LmArgs a) {
   constexpr int MJ = NJ ? NJ : kMaxJ;
   constexpr int MT = MJ * (MJ + 1) / 2;  // packed lower triangle
-  const Req& rq = src.req(blockIdx.y);
-  __shared__ RobotF rf;
-  __shared__ RobotD rd;
-  stage_robot(src.rob(rq.robot), 0.0, &rf, &rd);
-  __syncthreads();
-  const int i = blockIdx.x * kLmThreads + threadIdx.x;
-  if (i >= rq.T) return;
-  // lanes of this warp that hold a waypoint (the others have returned)
-  const int left = rq.T - (int)blockIdx.x * kLmThreads;
-  const unsigned live = left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
-  const auto& rb = RobotFor<F>::get(rf, rd);
-  const int n = NJ ? NJ : rd.n;
+  constexpr bool DYN = std::is_same<Src, BatchSrc>::value;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  __shared__ RobotF srf;
+  __shared__ RobotD srd;
+  // J^T J (packed lower triangle) and J^T e of each lane's current q, kept across
+  // rejected steps: a rejected step leaves q, and so J and e, unchanged, and the
+  // next iteration only needs the factorisation with the larger lambda
+  __shared__ double sA[MT * kLmThreads], sg[MJ * kLmThreads];
+  if (!DYN) {
+    stage_robot(src.rob(src.req(0).robot), 0.0, &srf, &srd);
+    __syncthreads();
+  }
 
+  // state of the lane's waypoint
+  bool have = false, exhausted = false, cached = false;
+  const Req* rq = nullptr;
+  const RobotF* rfp = &srf;
+  const RobotD* rdp = &srd;
+  int i = 0, it = 0;
   F Rt[9], pt[3];
-  {
+  double q[MJ];
+  double Fc = 0.0, lam = 0.0;
+  unsigned worked = 0, waypoints = 0;  // counters of this lane
+
+  auto start = [&](int r, int w) {  // take waypoint w of request r
+    rq = &src.req(r);
+    if constexpr (DYN) {
+      rfp = &src.lm.views[rq->robot].f;
+      rdp = &src.lm.views[rq->robot].d;
+    }
+    i = w;
+    const int n = NJ ? NJ : rdp->n;
     double R[9];
-    const double* t7 = rq.targets + 7 * (size_t)i;
+    const double* t7 = rq->targets + 7 * (size_t)i;
     quat_to_rot(t7 + 3, R);
 #pragma unroll
     for (int k = 0; k < 9; ++k) Rt[k] = (F)R[k];
     pt[0] = (F)t7[0]; pt[1] = (F)t7[1]; pt[2] = (F)t7[2];
-  }
-  double q[MJ];
-  const float* q_src = a.from_out ? rq.q_out : rq.q_in;
+    const float* q_src = a.from_out ? rq->q_out : rq->q_in;
 #pragma unroll
-  for (int j = 0; j < MJ; ++j) q[j] = (NJ || j < n) ? (double)q_src[(size_t)i * n + j] : 0.0;
+    for (int j = 0; j < MJ; ++j) q[j] = (NJ || j < n) ? (double)q_src[(size_t)i * n + j] : 0.0;
+    F e[6];
+    Fc = lm_eval<NJ, false, F>(RobotFor<F>::get(*rfp, *rdp), n, q, Rt, pt, e, nullptr, nullptr,
+                               nullptr);
+    lam = a.lambda0;
+    it = 0;
+    have = true;
+    cached = false;
+    ++waypoints;
+  };
 
-  F e[6];
-  double Fc = lm_eval<NJ, false, F>(rb, n, q, Rt, pt, e, nullptr, nullptr, nullptr);
-  double lam = a.lambda0;
+  auto finish = [&]() {  // deliver the waypoint's result
+    const RobotD& rd = *rdp;
+    const int n = NJ ? NJ : rd.n;
+#pragma unroll
+    for (int j = 0; j < MJ; ++j)
+      if (NJ || j < n) rq->q_out[(size_t)i * n + j] = (float)q[j];
+    if (a.want_err && rq->pose_err) {
+      // FP64 pose error of the delivered (FP32-rounded) configuration
+      double qq[kMaxJ], R[9], p[3], RtD[9];
+      for (int j = 0; j < n; ++j) qq[j] = (double)(float)q[j];
+      fk_f64(rd, qq, R, p);
+      const double* t7 = rq->targets + 7 * (size_t)i;
+      quat_to_rot(t7 + 3, RtD);
+      const double dx = p[0] - t7[0], dy = p[1] - t7[1], dz = p[2] - t7[2];
+      rq->pose_err[2 * (size_t)i] = sqrt(dx * dx + dy * dy + dz * dz);
+      rq->pose_err[2 * (size_t)i + 1] = geodesic<double>(RtD, R);
+    }
+    have = false;
+  };
 
-  unsigned worked = 0;  // iterations that built and solved a damped system
-  for (int it = 0; it < a.iters; ++it) {
-    if (Fc < a.freeze_cost) break;
+  if (!DYN) {  // a single request: one waypoint per lane
+    const int w = blockIdx.x * kLmThreads + lane;
+    if (w < src.req(0).T) start(0, w);
+    exhausted = true;
+  }
+
+  for (;;) {
+    if constexpr (DYN) if (!exhausted) {
+      const LmAux& aux = src.lm;
+      // lanes without a waypoint take the next ones of the batch (one atomic per warp)
+      const unsigned need = __ballot_sync(FULL, !have);
+      if (need) {
+        const int leader = __ffs(need) - 1, cnt = __popc(need);
+        int base = 0;
+        if (lane == leader) base = atomicAdd(aux.counter, cnt);
+        base = __shfl_sync(FULL, base, leader);
+        if (!have) {
+          const int w = base + __popc(need & ((1u << lane) - 1u));
+          if (w < aux.total) {
+            int lo = 0, hi = aux.nreq - 1;  // request r with wp_begin[r] <= w < wp_begin[r + 1]
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (aux.wp_begin[mid] <= w) lo = mid; else hi = mid - 1;
+            }
+            start(lo, w - aux.wp_begin[lo]);
+          }
+        }
+        if (base + cnt >= aux.total) exhausted = true;  // base and cnt are the same in every lane
+      }
+    }
+    if (!__any_sync(FULL, have)) break;
+    if (!have) continue;
+
+    // one LM iteration of the lane's waypoint
+    const auto& rb = RobotFor<F>::get(*rfp, *rdp);
+    const RobotD& rd = *rdp;
+    const int n = NJ ? NJ : rd.n;
+    if (it >= a.iters || Fc < a.freeze_cost) { finish(); continue; }
     ++worked;
+    double A[MT], g[MJ];
+    if (cached) {
+#pragma unroll
+      for (int t = 0; t < MT; ++t) A[t] = sA[t * kLmThreads + lane];
+#pragma unroll
+      for (int j = 0; j < MJ; ++j) g[j] = sg[j * kLmThreads + lane];
+    } else {
+    F e[6];
     F z[MJ][3], o[MJ][3], pe[3];
     lm_eval<NJ, true, F>(rb, n, q, Rt, pt, e, z, o, pe);
-    // J^T J + lam I (packed lower triangle) and J^T e, one Jacobian row at a time
-    double A[MT], g[MJ];
+    // J^T J (packed lower triangle) and J^T e, one Jacobian row at a time
 #pragma unroll
     for (int t = 0; t < MT; ++t) A[t] = 0.0;
 #pragma unroll
@@ -165,7 +273,13 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
         for (int y = 0; y <= x; ++y) A[x * (x + 1) / 2 + y] += Jr[x] * Jr[y];
       }
     }
-    // Cholesky, left-looking, in place: L_jj = sqrt(A_jj - sum L_jm^2),
+#pragma unroll
+    for (int t = 0; t < MT; ++t) sA[t * kLmThreads + lane] = A[t];
+#pragma unroll
+    for (int j = 0; j < MJ; ++j) sg[j * kLmThreads + lane] = g[j];
+    cached = true;
+    }
+    // Cholesky of J^T J + lam I, left-looking, in place: L_jj = sqrt(A_jj + lam - sum L_jm^2),
     // L_xj = (A_xj - sum L_xm L_jm) / L_jj
     bool ok = true;
     double inv[MJ];
@@ -190,6 +304,7 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
     }
     if (!ok) {
       lam = fmin(lam * a.lambda_up, a.lambda_max);
+      ++it;
       continue;
     }
     // L y = g, then L^T x = y (x overwrites g)
@@ -216,7 +331,7 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
 #pragma unroll
     for (int j = 0; j < MJ; ++j)
       if (NJ || j < n) mx = fmax(mx, fabs(g[j]));
-    if (mx < a.freeze_step) break;
+    if (mx < a.freeze_step) { finish(); continue; }
     double qt[MJ];
 #pragma unroll
     for (int j = 0; j < MJ; ++j) {
@@ -234,32 +349,20 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
       for (int j = 0; j < MJ; ++j) q[j] = qt[j];
       Fc = Ft;
       lam = fmax(lam / a.lambda_down, a.lambda_min);
+      cached = false;  // q moved: J and e change
     } else {
       lam = fmin(lam * a.lambda_up, a.lambda_max);
     }
+    ++it;
   }
-#pragma unroll
-  for (int j = 0; j < MJ; ++j)
-    if (NJ || j < n) rq.q_out[(size_t)i * n + j] = (float)q[j];
-  {
-    const unsigned sum = __reduce_add_sync(live, worked);
-    if ((threadIdx.x & 31) == 0) {
+  {  // work counters: one atomic add per warp
+    const unsigned sw = __reduce_add_sync(FULL, worked), sp = __reduce_add_sync(FULL, waypoints);
+    if (lane == 0) {
       atomicAdd(reinterpret_cast<unsigned long long*>(&g_lm_counters.lm_iterations),
-                (unsigned long long)sum);
+                (unsigned long long)sw);
       atomicAdd(reinterpret_cast<unsigned long long*>(&g_lm_counters.lm_waypoints),
-                (unsigned long long)__popc(live));
+                (unsigned long long)sp);
     }
-  }
-  if (a.want_err && rq.pose_err) {
-    // FP64 pose error of the delivered (FP32-rounded) configuration
-    double qq[kMaxJ], R[9], p[3], RtD[9];
-    for (int j = 0; j < n; ++j) qq[j] = (double)(float)q[j];
-    fk_f64(rd, qq, R, p);
-    const double* t7 = rq.targets + 7 * (size_t)i;
-    quat_to_rot(t7 + 3, RtD);
-    const double dx = p[0] - t7[0], dy = p[1] - t7[1], dz = p[2] - t7[2];
-    rq.pose_err[2 * (size_t)i] = sqrt(dx * dx + dy * dy + dz * dz);
-    rq.pose_err[2 * (size_t)i + 1] = geodesic<double>(RtD, R);
   }
 }
 
@@ -745,23 +848,61 @@ static LmArgs make_lm_args(const cpp_params_t& P, bool want_err, bool from_out) 
   return a;
 }
 
+// Resident one-warp blocks of an LM kernel per SM (asked once per instantiation).
+template <class KernelT>
+static int lm_blocks_per_sm(KernelT kernel) {
+  int v = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kLmThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    v = 0;
+  }
+  return v > 0 ? v : 1;
+}
+
+// A single request: one warp per 32 waypoints. A batch: a persistent grid of as
+// many one-warp blocks as the device holds at once (no more than the waypoints
+// need), the work counter zeroed first.
+template <int NJ, class F, class Src>
+static cudaError_t launch_lm_kernel(const Src& s, int max_T, const LmArgs& a, cudaStream_t st) {
+  auto kernel = lm_kernel<NJ, F, Src>;
+  if constexpr (std::is_same<Src, BatchSrc>::value) {
+    if (!s.lm.counter || !s.lm.views || !s.lm.wp_begin) return cudaErrorInvalidValue;
+    if (s.lm.total < 1) return cudaSuccess;
+    static const int per_sm = lm_blocks_per_sm(kernel);
+    const long long want = ((long long)s.lm.total + kLmThreads - 1) / kLmThreads;
+    const int blocks = (int)std::min<long long>(want, (long long)per_sm * device_sm_count());
+    cudaError_t e = cudaMemsetAsync(s.lm.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    kernel<<<blocks, kLmThreads, 0, st>>>(s, a);
+  } else {
+    kernel<<<(unsigned)((max_T + kLmThreads - 1) / kLmThreads), kLmThreads, 0, st>>>(s, a);
+  }
+  return cudaGetLastError();
+}
+
 template <int NJ, class Src>
-static void launch_lm_nj(const Src& s, dim3 grid, const LmArgs& a, bool fp64, cudaStream_t st) {
-  if (fp64) lm_kernel<NJ, double, Src><<<grid, kLmThreads, 0, st>>>(s, a);
-  else lm_kernel<NJ, float, Src><<<grid, kLmThreads, 0, st>>>(s, a);
+static cudaError_t launch_lm_nj(const Src& s, int max_T, const LmArgs& a, bool fp64, cudaStream_t st) {
+  return fp64 ? launch_lm_kernel<NJ, double>(s, max_T, a, st) : launch_lm_kernel<NJ, float>(s, max_T, a, st);
 }
 
 template <class Src>
 static cudaError_t launch_lm_phase(const Src& s, int n, int nreq, int max_T, const cpp_params_t& P,
                                    bool want_err, bool from_out, cudaStream_t st) {
+  (void)nreq;
   const LmArgs a = make_lm_args(P, want_err, from_out);
-  dim3 grid((unsigned)((max_T + kLmThreads - 1) / kLmThreads), (unsigned)nreq);
+  const bool fp64 = P.lm_fp64 != 0;
   switch (n) {
-    case 6: launch_lm_nj<6>(s, grid, a, P.lm_fp64 != 0, st); break;
-    case 7: launch_lm_nj<7>(s, grid, a, P.lm_fp64 != 0, st); break;
-    case 9: launch_lm_nj<9>(s, grid, a, P.lm_fp64 != 0, st); break;
-    default: launch_lm_nj<0>(s, grid, a, P.lm_fp64 != 0, st); break;
+    case 6: return launch_lm_nj<6>(s, max_T, a, fp64, st);
+    case 7: return launch_lm_nj<7>(s, max_T, a, fp64, st);
+    case 9: return launch_lm_nj<9>(s, max_T, a, fp64, st);
+    default: return launch_lm_nj<0>(s, max_T, a, fp64, st);
   }
+}
+
+cudaError_t launch_robot_views(const cpp_robot_t* robots, int n, RobotViews* views,
+                               cudaStream_t st) {
+  if (n < 1) return cudaSuccess;
+  robot_views_kernel<<<n, 32, 0, st>>>(robots, views);
   return cudaGetLastError();
 }
 

@@ -180,7 +180,8 @@ struct Launch {
   int n = 0, max_T = 0, max_Kp = 0;
   long long max_tasks = 0;
   bool any_geo = false;
-  size_t tab_off = 0, tab_bytes = 0;      // device: Req[] | robots[] | status[]
+  size_t tab_off = 0, tab_bytes = 0;      // device: Req[] | robots[] | status[] | LM aux
+  int wp_total = 0;                       // waypoints of the launch's requests
   size_t tab_pin = 0, tab_pin_bytes = 0;  // pinned host mirror
   bool tab_pinned = false;
   std::vector<char> tab_host;             // pageable fallback
@@ -344,11 +345,17 @@ bool cpp_server::form_batch(Launch* L) {
   return true;
 }
 
-// Device table (Req[] | robots[] | status[]) of a launch and its host mirror.
+// Device table of a launch: Req[] | robots[] | status[] | the LM's work
+// distribution (robot views, waypoint prefix sums, counter); the host mirror
+// holds the same bytes (the views are formed on the device after the copy).
+static size_t tab_robots(int count) { return align256(sizeof(Req) * count); }
+static size_t tab_status(int count) { return tab_robots(count) + align256(sizeof(cpp_robot_t) * count); }
+static size_t tab_lm(int count) { return tab_status(count) + align256(sizeof(int32_t) * count); }
+static size_t tab_total(int count) { return tab_lm(count) + lm_aux_layout(count, count).total; }
+
 bool cpp_server::alloc_table(Launch* L) {
   const int count = (int)L->reqs.size();
-  L->tab_bytes = align256(sizeof(Req) * count) + align256(sizeof(cpp_robot_t) * count) +
-                 align256(sizeof(int32_t) * count);
+  L->tab_bytes = tab_total(count);
   if (!darena.alloc(L->tab_bytes, &L->tab_off)) return false;
   L->tab_pin_bytes = L->tab_bytes;
   if (parena.alloc(L->tab_pin_bytes, &L->tab_pin)) {
@@ -454,7 +461,7 @@ cpp_status cpp_server::stage(Launch* L) {
   const int n = L->reqs[0]->n;
   char* tab_d = d_arena + L->tab_off;
   Req* tq = reinterpret_cast<Req*>(L->tab_h);
-  cpp_robot_t* trob = reinterpret_cast<cpp_robot_t*>(L->tab_h + align256(sizeof(Req) * count));
+  cpp_robot_t* trob = reinterpret_cast<cpp_robot_t*>(L->tab_h + tab_robots(count));
   int32_t* tst = reinterpret_cast<int32_t*>(L->tab_h + align256(sizeof(Req) * count) +
                                             align256(sizeof(cpp_robot_t) * count));
   int32_t* tst_d = reinterpret_cast<int32_t*>(tab_d + align256(sizeof(Req) * count) +
@@ -504,7 +511,14 @@ cpp_status cpp_server::stage(Launch* L) {
     max_Kp = std::max(max_Kp, r->Kp);
     max_tasks = std::max(max_tasks, mask_tasks(r->T, r->Kp));
   }
+  // the LM's work distribution: waypoint prefix sums (copied with the table) and
+  // robot views (formed on the device after it)
+  const LmAuxLayout LA = lm_aux_layout(count, count);
+  L->wp_total = lm_prefix(tq, count, reinterpret_cast<int*>(L->tab_h + tab_lm(count) + LA.wp));
   cudaError_t e = cudaMemcpyAsync(tab_d, L->tab_h, L->tab_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = launch_robot_views(reinterpret_cast<const cpp_robot_t*>(tab_d + tab_robots(count)), count,
+                           reinterpret_cast<RobotViews*>(tab_d + tab_lm(count) + LA.views), st);
   if (e == cudaSuccess) e = cudaEventRecord(L->copied, st);
   if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server H2D table: %s", cudaGetErrorString(e));
   L->n = n;
@@ -566,7 +580,8 @@ cpp_status cpp_server::enqueue(Launch* L) {
   cudaError_t e = cudaStreamWaitEvent(st, L->copied, 0);
   if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server launch: %s", cudaGetErrorString(e));
   BatchSrc src{reinterpret_cast<const Req*>(tab_d),
-               reinterpret_cast<const cpp_robot_t*>(tab_d + align256(sizeof(Req) * count))};
+               reinterpret_cast<const cpp_robot_t*>(tab_d + tab_robots(count)),
+               lm_aux_at(tab_d + tab_lm(count), lm_aux_layout(count, count), count, L->wp_total)};
   if (L->improve) {
     if ((e = launch_improve_batch(src, n, count, max_T, cfg.params, any_geo, st)) != cudaSuccess)
       return sfail(CPP_ERR_CUDA, "server launch: %s", cudaGetErrorString(e));
@@ -823,7 +838,7 @@ cpp_status cpp_plan_submit(cpp_server_t* s, const cpp_plan_req_t* rq, uint64_t* 
       return sfail(CPP_ERR_INVALID_ARG, "target %d: quaternion norm %.9f is not 1", i, std::sqrt(qn));
   }
   const Layout L = slot_layout(T, Kp, n);
-  const size_t table = 3 * 256 + align256(sizeof(Req)) + align256(sizeof(cpp_robot_t));
+  const size_t table = tab_total(1);
   if (L.total + table > s->cfg.hbm_budget_bytes)
     return sfail(CPP_ERR_BUDGET, "request needs %zu bytes of device memory; the budget is %zu",
                  L.total + table, s->cfg.hbm_budget_bytes);
