@@ -185,12 +185,23 @@ __device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sinco
 // hardware sine/cosine (__sincosf: absolute error below 2^-21.4 on [-pi, pi],
 // which covers every in-limit joint angle; it carries at most a few 1e-6 m /
 // rad into the pose), the LM uses the correctly range-reduced sincosf.
+// The first link starts from the identity, so its product is written out: the
+// same roundings as dh_step from the identity (one per product), without the
+// multiplications by 0 and 1.
 template <int NJ>
 __device__ __forceinline__ void fk_f32(const RobotF& rb, const float* q, float R[9], float p[3]) {
-  pose_identity(R, p);
   const int n = NJ ? NJ : rb.n;
+  {
+    float s, c;
+    __sincosf(q[0] + rb.th0[0], &s, &c);
+    const float ca = rb.ca[0], sa = rb.sa[0];
+    R[0] = c; R[1] = -(ca * s); R[2] = sa * s;
+    R[3] = s; R[4] = ca * c;    R[5] = -(sa * c);
+    R[6] = 0.f; R[7] = sa;      R[8] = ca;
+    p[0] = rb.a[0] * c; p[1] = rb.a[0] * s; p[2] = rb.d[0];
+  }
 #pragma unroll
-  for (int j = 0; j < (NJ ? NJ : kMaxJ); ++j) {
+  for (int j = 1; j < (NJ ? NJ : kMaxJ); ++j) {
     if (!NJ && j >= n) break;
     float s, c;
     __sincosf(q[j] + rb.th0[j], &s, &c);
