@@ -321,6 +321,16 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, min_
     for w, rob, ch, th in pool[:4]:  # warm the plain path
         cppflow.plan_host(rob, P, ch, th, w.K, ws, sel_h[:w.T], None, q_h[:w.T * n], None, rep_h,
                           stream=pstream)
+    # Warm the served path: CUDA loads a kernel on its first launch, which would stall
+    # the server's worker the first time each search form and size appears. The whole
+    # pool at once (every throughput form) and a few requests one by one (the latency
+    # forms) load them before any measured window.
+    with cppflow.Server(P, device=dev.index or 0, hbm_budget=40 << 30, max_batch=512,
+                        max_inflight=16) as srv:
+        for tk in [srv.submit(rob, ch, th, w.K, borrow=True) for w, rob, ch, th in pool]:
+            srv.wait(tk)
+        for w, rob, ch, th in pool[:64]:
+            srv.wait(srv.submit(rob, ch, th, w.K, borrow=True))
     out = {"pool_requests": pool_size}
     for rate in rates:
         target = int(max(min_requests, math.ceil(rate * seconds)))

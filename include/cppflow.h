@@ -657,7 +657,11 @@ typedef struct cpp_server_stats {
 
 void cpp_server_config_default(cpp_server_config_t* cfg);
 /* Allocates the device arena and pinned pool and starts the worker.
- * OOM if the arena cannot be allocated. */
+ * OOM if the arena cannot be allocated. CUDA loads each kernel on its first
+ * launch (lazy module loading), so the first launch of each search form and
+ * size stalls the worker briefly: plan a few requests of each expected shape,
+ * singly and together, before serving latency-sensitive traffic (or run the
+ * process with CUDA_MODULE_LOADING=EAGER). */
 cpp_status cpp_server_create(const cpp_server_config_t* cfg, cpp_server_t** out);
 /* Validates on the host (robot, lattice shape, finite targets with unit
  * quaternions within 1e-6), copies the inputs unless CPP_REQ_BORROW, queues the
