@@ -312,14 +312,17 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __gri
 //  * the 8 partial (minimum, tile) pairs merge in warp order, the lower range
 //    winning ties, and the 8 warps re-evaluate 2 nodes each of the winning
 //    tile for the lowest index attaining the minimum;
-//  * each new record [-q', C'] goes into the record buffer of every CTA of the
-//    cluster by asynchronous distributed-shared-memory stores that count their
-//    bytes on the receiving CTA's mbarrier for that buffer; a CTA starts step
-//    i+1 once its barrier has seen all Kp records of layer i+1 (a bounded wait).
-//    Records are double-buffered. A CTA writes layer i+2 into a peer only after
-//    it has received the peer's layer-i+1 records, which the peer sends after
-//    its last read of the buffer that layer i+2 overwrites, so no step needs a
-//    cluster-wide barrier.
+//  * each new record [-q', C'] goes into the record buffer of every CTA that
+//    owns successors of the request by asynchronous distributed-shared-memory
+//    stores that count their bytes on the receiving CTA's mbarrier for that
+//    buffer; a CTA starts step i+1 once its barrier has seen all Kp records of
+//    layer i+1 (a bounded wait). Records are double-buffered. A CTA writes
+//    layer i+2 into a peer only after it has received the peer's layer-i+1
+//    records, which the peer sends after its last read of the buffer that
+//    layer i+2 overwrites, so no step needs a cluster-wide barrier. That
+//    argument needs every receiver to be a sender too: CTAs of the cluster
+//    beyond the request's own Kp (a launch's cluster fits its largest Kp) own
+//    nothing, so they receive nothing either.
 constexpr int kDpcThreads = 256;
 constexpr int kDpcWarps = kDpcThreads / 32;
 static_assert(kDp2Tile == 2 * kDpcWarps, "the rescan gives each warp 2 nodes of a tile");
@@ -345,6 +348,17 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
   const uint32_t crank = cluster_rank();
   const Req& rq = src.req(blockIdx.x / CS);
   const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
+  // The cluster is sized for the launch's largest Kp. A CTA past this request's
+  // own extent owns no successor: it sends nothing, so the owners never wait for
+  // it and could run layers ahead of it, into buffers and barrier phases it has
+  // not finished with. It takes no part in the exchange and only keeps the
+  // cluster's two barriers.
+  if ((int)crank * S >= Kp) {
+    cluster_barrier();
+    cluster_barrier();
+    return;
+  }
+  const int CSr = (Kp + S - 1) / S;  // CTAs that own successors of this request
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   extern __shared__ __align__(16) float smc[];
   const int RL = rec_layer_floats(NW, Kp);
@@ -511,7 +525,7 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
 #pragma unroll
       for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
       const uint32_t base = smem_u32(nxt + rec_off(NW, kp[r])), bar = smem_u32(&rbar[L & 1]);
-      for (int c = warp; c < CS; c += kDpcWarps) {
+      for (int c = warp; c < CSr; c += kDpcWarps) {
         const uint32_t peer = map_peer(base, (uint32_t)c), pbar = map_peer(bar, (uint32_t)c);
 #pragma unroll
         for (int w = 0; w < NW / 4; ++w)
@@ -550,7 +564,8 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
 //    (a bounded wait). Record buffers are double-buffered; a CTA writes layer
 //    i+2's costs into a peer only after it has received the peer's layer i+1
 //    costs, which the peer sends after its last read of the buffer that layer
-//    i+2 overwrites, so no step needs a cluster-wide barrier.
+//    i+2 overwrites, so no step needs a cluster-wide barrier (CTAs beyond the
+//    request's own Kp send and receive nothing).
 // Per step a CTA exchanges S * (CS - 1) * 4 bytes instead of S * (CS - 1) * 32,
 // and sweeps S * Kp edges between three CTA barriers.
 inline size_t dpx_smem_bytes(int nj, int Kp, int R) {
@@ -576,6 +591,14 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dpx_forward_kernel(const __gri
   const uint32_t crank = cluster_rank();
   const Req& rq = src.req(blockIdx.x / CS);
   const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
+  // a CTA past this request's own extent owns no successor and stays out of the
+  // exchange, as in the record-exchange form above
+  if ((int)crank * S >= Kp) {
+    cluster_barrier();
+    cluster_barrier();
+    return;
+  }
+  const int CSr = (Kp + S - 1) / S;  // CTAs that own successors of this request
   const int tid = threadIdx.x, g = tid / kDp3Group, lt = tid % kDp3Group;
   extern __shared__ __align__(128) float smx[];
   const int RL = rec_layer_floats(NW, Kp);
@@ -588,7 +611,7 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dpx_forward_kernel(const __gri
   __shared__ uint64_t cbar[2];  // peers' costs of layer L arrive on cbar[L & 1]
   __shared__ int timeout_flag;
 
-  const int own_lo = (int)crank * S, own_n = max(0, min(S, Kp - own_lo));
+  const int own_lo = (int)crank * S, own_n = min(S, Kp - own_lo);
   const uint32_t recv_bytes = (uint32_t)(Kp - own_n) * 4u;
   const uint32_t layer_bytes = (uint32_t)(NJ * Kp * 4), pen_bytes = (uint32_t)(Kp * 4);
   auto issue = [&](int L) {  // one thread
@@ -747,8 +770,8 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dpx_forward_kernel(const __gri
       float* slot = nxt + rec_off(NW, kp[r]) + NJ;
       *slot = c;
       const uint32_t a = smem_u32(slot);
-      for (int p = 1; p < CS; ++p) {
-        const uint32_t peer = (crank + (uint32_t)p) % (uint32_t)CS;
+      for (int p = 1; p < CSr; ++p) {
+        const uint32_t peer = (crank + (uint32_t)p) % (uint32_t)CSr;
         st_async_f32(map_peer(a, peer), c, map_peer(nbar, peer));
       }
       bprow[kp[r]] = (uint16_t)arg;
