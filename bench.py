@@ -34,11 +34,19 @@ import os
 import statistics
 import subprocess
 import sys
+import queue
 import tempfile
+import threading
 import time
 from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
+
+# The server runs its launches on up to 16 streams, each forking its search groups onto
+# side streams. CUDA maps streams onto 8 hardware queues by default, and work in one
+# queue runs in order, so launches of unrelated streams wait on each other. 32 queues
+# remove most of that (set before the first CUDA call; a value set by the caller wins).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -297,10 +305,11 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, min_
     """Open-loop Poisson arrivals of the serving mix at each rate, drawn with replacement
     from a pool of distinct requests. Per rate, max(`seconds` of arrivals, `min_requests`)
     requests are reported after a warm-up of 10 % more.
-    served: real-time submission to cpp_plan_submit (borrowed pinned inputs), latency =
-    arrival -> completion; the p50 of the first and the last third of the reported
-    requests show whether the server keeps up (a server that falls behind sees its
-    latency grow over the window).
+    served: real-time submission to cpp_plan_submit (borrowed pinned inputs) while a
+    second client thread collects the results in submission order (cpp_plan_wait),
+    latency = arrival -> completion seen by the server; the p50 of the first and the
+    last third of the reported requests show whether the server keeps up (a server
+    that falls behind sees its latency grow over the window).
     plain: the same arrival trace in real time through cpp_plan_host, one request at a
     time on one stream (inputs copied in, results copied out, the next request starts
     when the previous one is done), latency = arrival -> completion, over the trace's
@@ -318,7 +327,12 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, min_
     q_h = torch.empty(T_max * n, dtype=torch.float32, pin_memory=True).numpy()
     rep_h = cppflow.Report()
     pstream = torch.cuda.Stream()
-    for w, rob, ch, th in pool[:4]:  # warm the plain path
+    # warm the plain path: one request of every K in the pool (each K takes its own
+    # kernel instances, which CUDA loads on their first launch)
+    first_of_k = {}
+    for item in pool:
+        first_of_k.setdefault(item[0].K, item)
+    for w, rob, ch, th in first_of_k.values():
         cppflow.plan_host(rob, P, ch, th, w.K, ws, sel_h[:w.T], None, q_h[:w.T * n], None, rep_h,
                           stream=pstream)
     # Warm the served path: CUDA loads a kernel on its first launch, which would stall
@@ -346,21 +360,29 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, min_
         gc.disable()
         with cppflow.Server(P, device=dev.index or 0, hbm_budget=40 << 30, max_batch=512,
                             max_inflight=16) as srv:
+            done, ok = [0.0] * count, [False] * count
+            handoff = queue.SimpleQueue()
+
+            def collector():
+                while (item := handoff.get()) is not None:
+                    i, tk, sub = item
+                    stt, res = srv.wait(tk)
+                    done[i] = sub + res["latency_ms"] / 1000.0
+                    ok[i] = stt == cppflow.OK and bool(res["report"]["valid"])
+
+            coll = threading.Thread(target=collector)
+            coll.start()
             t0 = time.perf_counter()
-            tickets = []
-            for a, k in zip(arr, pick):
+            for i, (a, k) in enumerate(zip(arr, pick)):
                 now = time.perf_counter() - t0
                 if a > now:
                     time.sleep(a - now)
                 w, rob, ch, th = pool[k]
                 sub = time.perf_counter() - t0
-                tickets.append((srv.submit(rob, ch, th, w.K, borrow=True), sub))
-            done, valid = [], 0
-            for i, (tk, sub) in enumerate(tickets):
-                stt, res = srv.wait(tk)
-                done.append(sub + res["latency_ms"] / 1000.0)
-                if i >= drop:
-                    valid += int(stt == cppflow.OK and res["report"]["valid"])
+                handoff.put((i, srv.submit(rob, ch, th, w.K, borrow=True), sub))
+            handoff.put(None)
+            coll.join()
+            valid = sum(ok[drop:])
             ss = srv.stats()
         gc.enable()
         slat = [d - a for d, a in zip(done[drop:], arr[drop:])]

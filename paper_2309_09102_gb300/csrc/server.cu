@@ -7,7 +7,11 @@
 //    a request is admitted only when its whole footprint (lattice, targets,
 //    plan scratch, outputs) fits, so lattices and search tables stay resident
 //    on the device for the request's lifetime on the GPU;
-//  * a pinned host pool for staged inputs and results (pageable fallback);
+//  * a pinned host pool for copied inputs (pageable fallback) and, per launch,
+//    the request table's mirror and the staging of its results: the worker moves
+//    each result into its request when the launch retires, so pinned memory
+//    holds only what is in flight, however late the clients collect, and no
+//    copy to or from pageable memory stalls the worker while launches run;
 //  * one worker thread: it retires finished launches (event query), then forms
 //    the next batch from the queue -- requests of the oldest request's size
 //    class (joint count, K bucket, T bucket) in arrival order, while the class
@@ -118,8 +122,8 @@ struct Request {
   const float* cand = nullptr;
   const double* targets = nullptr;
   std::vector<char> own_in;
-  // results on the host (pinned or pageable)
-  char* h_out = nullptr;
+  // results on the host: copied here from the launch's pinned staging when the
+  // launch retires (for an anytime request, the latest pass's result)
   std::vector<char> own_out;
   std::vector<char> geo;  // device form of the collision model (empty: none)
   size_t pin_off = 0, pin_bytes = 0;
@@ -182,10 +186,12 @@ struct Launch {
   bool any_geo = false;
   size_t tab_off = 0, tab_bytes = 0;      // device: Req[] | robots[] | status[] | LM aux
   int wp_total = 0;                       // waypoints of the launch's requests
-  size_t tab_pin = 0, tab_pin_bytes = 0;  // pinned host mirror
+  size_t tab_pin = 0, tab_pin_bytes = 0;  // pinned host mirror, then the results' staging
   bool tab_pinned = false;
   std::vector<char> tab_host;             // pageable fallback
   char* tab_h = nullptr;
+  std::vector<size_t> out_off;            // per request (table order): its results' offset
+                                          // in tab_h, set when the launch is enqueued
 };
 
 }  // namespace
@@ -225,7 +231,7 @@ struct cpp_server {
   bool form_improve(Launch* L);
   bool alloc_table(Launch* L);
   void finish(Request* r);
-  void anytime_step(Request* r, bool improve_round);
+  void anytime_step(Request* r, bool improve_round, const char* res);
   cpp_status stage(Launch* L);
   cpp_status enqueue(Launch* L);
   cudaError_t search(Launch* L, const BatchSrc& src, cudaStream_t st);
@@ -353,16 +359,29 @@ static size_t tab_status(int count) { return tab_robots(count) + align256(sizeof
 static size_t tab_lm(int count) { return tab_status(count) + align256(sizeof(int32_t) * count); }
 static size_t tab_total(int count) { return tab_lm(count) + lm_aux_layout(count, count).total; }
 
+// The host side is pinned: the table's mirror, then every request's results
+// (the device-to-host copies land there; the worker moves them into the request
+// when the launch retires). A copy to or from pageable memory would block the
+// worker until the stream's earlier work is done, so without pinned room the
+// launch waits for launches in flight to retire; with none in flight it takes
+// pageable memory.
 bool cpp_server::alloc_table(Launch* L) {
   const int count = (int)L->reqs.size();
   L->tab_bytes = tab_total(count);
-  if (!darena.alloc(L->tab_bytes, &L->tab_off)) return false;
-  L->tab_pin_bytes = L->tab_bytes;
-  if (parena.alloc(L->tab_pin_bytes, &L->tab_pin)) {
+  size_t o = align256(L->tab_bytes);
+  for (const Request* r : L->reqs) o += align256(r->out_bytes);
+  L->tab_pin_bytes = o;
+  const bool pin = h_pinned && parena.alloc(L->tab_pin_bytes, &L->tab_pin);
+  if (!pin && (!inflight.empty() || !staged.empty())) return false;
+  if (!darena.alloc(L->tab_bytes, &L->tab_off)) {
+    if (pin) parena.release(L->tab_pin, L->tab_pin_bytes);
+    return false;
+  }
+  if (pin) {
     L->tab_pinned = true;
     L->tab_h = h_pinned + L->tab_pin;
   } else {
-    L->tab_host.resize(L->tab_bytes);
+    L->tab_host.resize(L->tab_pin_bytes);
     L->tab_h = L->tab_host.data();
   }
   return true;
@@ -394,7 +413,7 @@ bool cpp_server::form_improve(Launch* L) {
 // A finished request: its best published result (anytime) becomes the result;
 // the device slot is freed.
 void cpp_server::finish(Request* r) {
-  if (r->have_best) memcpy(r->h_out, r->best_out.data(), r->out_bytes);
+  if (r->have_best) r->own_out = r->best_out;
   darena.release(r->dev_off, r->dev_bytes);
   --resident;
   r->t_done = Clock::now();
@@ -403,18 +422,20 @@ void cpp_server::finish(Request* r) {
   ++stats.completed;
 }
 
-// After a pass or an improvement round of an anytime request: publish the result
-// when it is valid and (after the first) shorter; queue the next round or finish.
-void cpp_server::anytime_step(Request* r, bool improve_round) {
+// After a pass or an improvement round of an anytime request (its results at
+// `res`): publish the result when it is valid and (after the first) shorter;
+// queue the next round or finish.
+void cpp_server::anytime_step(Request* r, bool improve_round, const char* res) {
   if (improve_round) {
     ++r->rounds_done;
     --r->rounds_left;
     ++stats.improve_rounds;
   }
   cpp_report_t rep;
-  memcpy(&rep, r->h_out + r->o_rep, sizeof(rep));
+  memcpy(&rep, res + r->o_rep, sizeof(rep));
+  r->own_out.assign(res, res + r->out_bytes);
   if (r->dev_status == 0 && rep.valid && (!r->have_best || rep.traj_len < r->best_len)) {
-    r->best_out.assign(r->h_out, r->h_out + r->out_bytes);
+    r->best_out.assign(res, res + r->out_bytes);
     r->have_best = true;
     r->best_len = rep.traj_len;
     r->best_rounds = r->rounds_done;
@@ -593,9 +614,16 @@ cpp_status cpp_server::enqueue(Launch* L) {
              (e = launch_check_batch(src, count, cfg.params, st)) != cudaSuccess) {
     return sfail(CPP_ERR_CUDA, "server launch: %s", cudaGetErrorString(e));
   }
+  // results staging after the table, in table order (stage() may have reordered reqs)
+  L->out_off.resize(count);
+  size_t o = align256(L->tab_bytes);
+  for (int i = 0; i < count; ++i) {
+    L->out_off[i] = o;
+    o += align256(L->reqs[i]->out_bytes);
+  }
   for (int i = 0; i < count; ++i) {
     Request* r = L->reqs[i];
-    e = cudaMemcpyAsync(r->h_out, d_arena + r->dev_off + r->o_out, r->out_bytes,
+    e = cudaMemcpyAsync(L->tab_h + L->out_off[i], d_arena + r->dev_off + r->o_out, r->out_bytes,
                         cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return sfail(CPP_ERR_CUDA, "server D2H: %s", cudaGetErrorString(e));
   }
@@ -623,10 +651,13 @@ void cpp_server::retire(Launch* L, cudaError_t e) {
       continue;
     }
     r->dev_status = tst[i];
+    release_host(r);  // the inputs were copied long before
+    const char* res = L->tab_h + L->out_off[i];
     if (r->anytime) {
-      anytime_step(r, L->improve);
+      anytime_step(r, L->improve, res);
       continue;
     }
+    r->own_out.assign(res, res + r->out_bytes);
     darena.release(r->dev_off, r->dev_bytes);
     --resident;
     r->t_done = now;
@@ -868,33 +899,25 @@ cpp_status cpp_plan_submit(cpp_server_t* s, const cpp_plan_req_t* rq, uint64_t* 
   const bool borrow = (rq->flags & CPP_REQ_BORROW) != 0;
   const size_t in_b = borrow ? 0 : align256(cand_b) + align256(tgt_b);
   std::unique_lock<std::mutex> lk(s->mu);
-  if (s->h_pinned && s->parena.alloc(in_b + r->out_bytes, &r->pin_off)) {
-    r->pinned = true;
-    r->pin_bytes = in_b + r->out_bytes;
-    char* base = s->h_pinned + r->pin_off;
-    r->h_out = base + in_b;
-    if (!borrow) {
-      lk.unlock();
-      memcpy(base, rq->cand, cand_b);
-      memcpy(base + align256(cand_b), rq->targets, tgt_b);
-      lk.lock();
-      r->cand = reinterpret_cast<const float*>(base);
-      r->targets = reinterpret_cast<const double*>(base + align256(cand_b));
-    }
-  } else {
-    r->own_out.resize(r->out_bytes);
-    r->h_out = r->own_out.data();
-    if (!borrow) {
-      r->own_in.resize(align256(cand_b) + tgt_b);
-      memcpy(r->own_in.data(), rq->cand, cand_b);
-      memcpy(r->own_in.data() + align256(cand_b), rq->targets, tgt_b);
-      r->cand = reinterpret_cast<const float*>(r->own_in.data());
-      r->targets = reinterpret_cast<const double*>(r->own_in.data() + align256(cand_b));
-    }
-  }
   if (borrow) {
     r->cand = rq->cand;
     r->targets = rq->targets;
+  } else if (s->h_pinned && s->parena.alloc(in_b, &r->pin_off)) {
+    r->pinned = true;
+    r->pin_bytes = in_b;
+    char* base = s->h_pinned + r->pin_off;
+    lk.unlock();
+    memcpy(base, rq->cand, cand_b);
+    memcpy(base + align256(cand_b), rq->targets, tgt_b);
+    lk.lock();
+    r->cand = reinterpret_cast<const float*>(base);
+    r->targets = reinterpret_cast<const double*>(base + align256(cand_b));
+  } else {
+    r->own_in.resize(align256(cand_b) + tgt_b);
+    memcpy(r->own_in.data(), rq->cand, cand_b);
+    memcpy(r->own_in.data() + align256(cand_b), rq->targets, tgt_b);
+    r->cand = reinterpret_cast<const float*>(r->own_in.data());
+    r->targets = reinterpret_cast<const double*>(r->own_in.data() + align256(cand_b));
   }
   if (s->stop) {
     s->release_host(r);
@@ -920,7 +943,7 @@ static cpp_status collect(cpp_server_t* s, Request* r, cpp_plan_result_t* res) {
     res->dev_status = r->dev_status;
     res->rounds = r->have_best ? r->best_rounds : r->rounds_done;
     if (r->state == St::Done) {
-      const char* o = r->h_out;
+      const char* o = r->own_out.data();
       if (res->sel) memcpy(res->sel, o + r->o_sel, (size_t)r->T * sizeof(int32_t));
       if (res->q) memcpy(res->q, o + r->o_q, (size_t)r->T * r->n * sizeof(float));
       if (res->pose_err) memcpy(res->pose_err, o + r->o_err, (size_t)r->T * 2 * sizeof(double));
@@ -955,7 +978,7 @@ cpp_status cpp_plan_peek(cpp_server_t* s, uint64_t ticket, cpp_plan_result_t* re
   Request* r = it->second;
   const char* o = nullptr;
   if (r->have_best) o = r->best_out.data();
-  else if (r->state == St::Done) o = r->h_out;
+  else if (r->state == St::Done) o = r->own_out.data();
   else if (r->state == St::Failed || r->state == St::Cancelled) return r->result;
   else return CPP_PENDING;
   if (res) {

@@ -143,3 +143,29 @@ def test_throughput_form_mixed_k_equals_alone(budget):
         np.testing.assert_array_equal(res["q"], alone["q"])
         np.testing.assert_array_equal(res["err"], alone["err"])
         assert res["best"] == float(alone["best"])
+
+
+@pytest.mark.parametrize("pinned", [0, 96 << 10, 1 << 20])
+def test_small_or_no_pinned_pool_equals_alone(pinned):
+    """The pinned pool holds copied inputs until their launch retires and each launch's table
+    and results while it is in flight; results then move into their requests. With no pool
+    (pageable only), or one too small for more than a launch or two at a time, requests
+    submitted together and collected only after all are submitted still return exactly
+    what cpp_plan returns alone."""
+    pbs = _mix(16, seed0=880)
+    _, cp = params_pair(lm_iters=10)
+    robots = [cppflow.robot_from_arm(pb.arm) for pb in pbs]
+    with cppflow.Server(cp, hbm_budget=1 << 30, max_inflight=4, max_batch=3,
+                        pinned_bytes=pinned) as srv:
+        tickets = [srv.submit(robots[i], pb.cand, pb.targets, pb.K) for i, pb in enumerate(pbs)]
+        results = [srv.wait(t) for t in tickets]
+        stats = srv.stats()
+    assert stats["completed"] == len(pbs) and stats["failed"] == 0
+    for i, pb in enumerate(pbs):
+        st, res = results[i]
+        assert st == cppflow.OK
+        alone = run_plan(robots[i], cp, pb.cand, pb.targets, pb.K)
+        np.testing.assert_array_equal(res["sel"], alone["sel"])
+        np.testing.assert_array_equal(res["q"], alone["q"])
+        np.testing.assert_array_equal(res["err"], alone["err"])
+        assert res["best"] == float(alone["best"])
