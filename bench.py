@@ -856,24 +856,25 @@ def run_cuda(args, rank: int, world: int, dist):
         return [srv.submit(robots[reqs[r].arm_seed - 100], cand_np[r], targ_np[r], K, borrow=True)
                 for r in range(B)]
 
-    # The client keeps two steps in flight (it submits step s + 1 before it waits for the
-    # results of step s), as a serving front end would; every step's H2D copies, batching,
-    # kernels and D2H copies lie inside the timed region.
+    # The client keeps `serve_depth` steps in flight (it submits step s + depth - 1 before
+    # it waits for the results of step s), as a serving front end would; every step's H2D
+    # copies, batching, kernels and D2H copies lie inside the timed region.
+    depth = max(1, args.serve_depth)
     gc.collect()
     gc.disable()  # no collection pause inside the timed client loop
-    with cppflow.Server(P, device=local, hbm_budget=2 * int(B * 6.5e6) + (256 << 20),
+    with cppflow.Server(P, device=local, hbm_budget=(depth + 1) * int(B * 6.5e6) + (256 << 20),
                         max_batch=args.serve_batch, max_inflight=args.serve_inflight,
                         pinned_bytes=64 << 20) as srv:
         for tk in submit_step(srv):              # one closed step warms the server up
             srv.wait(tk)
         t0 = time.perf_counter()
-        pending = submit_step(srv)
+        pending = [submit_step(srv) for _ in range(min(depth - 1, e2e_steps))]
         for s_i in range(e2e_steps):
-            nxt = submit_step(srv) if s_i + 1 < e2e_steps else []
-            outs = [srv.wait(tk) for tk in pending]
+            if s_i + depth - 1 < e2e_steps:
+                pending.append(submit_step(srv))
+            outs = [srv.wait(tk) for tk in pending.pop(0)]
             lat += [o[1]["latency_ms"] for o in outs]
             e2e_valid += sum(int(o[1]["report"]["valid"]) for o in outs)
-            pending = nxt
         e2e_total = time.perf_counter() - t0
         sstats = srv.stats()
     gc.enable()
@@ -881,8 +882,9 @@ def run_cuda(args, rank: int, world: int, dist):
     e2e = {"value": round(world * B * e2e_steps / e2e_total, 3), "unit": "plans/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(B * d2h_per_req),
            "path": "cpp_plan_submit (pinned host inputs, borrowed) -> continuous batching -> "
-                   "cpp_plan_wait (results in host memory); client keeps 2 steps in flight",
+                   f"cpp_plan_wait (results in host memory); client keeps {depth} steps in flight",
            "server": {"max_batch": args.serve_batch, "max_inflight": args.serve_inflight},
+           "steps_in_flight": depth,
            "p50_ms": round(lat[len(lat) // 2], 3),
            "p99_ms": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 3),
            "valid_plans": f"{e2e_valid}/{B * e2e_steps}",
@@ -992,8 +994,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=304)
     ap.add_argument("--plain", type=int, default=32, help="requests timed on the plain path")
-    ap.add_argument("--serve-batch", type=int, default=38, help="server: requests per launch")
+    ap.add_argument("--serve-batch", type=int, default=76, help="server: requests per launch")
     ap.add_argument("--serve-inflight", type=int, default=8, help="server: launches in flight")
+    ap.add_argument("--serve-depth", type=int, default=3,
+                    help="e2e client: steps of requests in flight")
     ap.add_argument("--uneven", type=int, default=256,
                     help="requests of the batched uneven leg (0: skip)")
     ap.add_argument("--collision", type=int, default=304,
