@@ -442,23 +442,39 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
     int btile[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; btile[r] = -1; }
-#pragma unroll (R == 2 ? 2 : 1)  // measured: two tiles per iteration help only R = 2
+    // The records are swept a pair at a time with the next pair already loaded (the
+    // first pair of the next tile included), so the shared-memory load latency of a
+    // pair overlaps the arithmetic of the one before: with 8 warps per SM it is not
+    // hidden otherwise.
+    float p0[NW], p1[NW];  // the pair swept next
+    if (t_lo < t_hi) {
+      const float* b0 = cur + rec_off(NW, t_lo * kDp2Tile);
+      load_rec<NW>(b0, p0);
+      load_rec<NW>(b0 + NW, p1);
+    }
+#pragma unroll 1
     for (int t = t_lo; t < t_hi; ++t) {
       const int kb = t * kDp2Tile;
       const float* base = cur + rec_off(NW, kb);
+      // the next tile's first record (this tile's own first one for the last tile)
+      const float* nbase = t + 1 < t_hi ? base + kDp2Tile * NW + 4 : base;
       float tb[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) tb[r] = CUDART_INF_F;
       if (kb + kDp2Tile <= K4) {
 #pragma unroll
         for (int k = 0; k < kDp2Tile; k += 2) {
-          float r0[NW], r1[NW];
-          load_rec<NW>(base + k * NW, r0);
-          load_rec<NW>(base + (k + 1) * NW, r1);
-          sweep_pair<NJ, R, OBJ>(own, r0, r1, tb);
+          float q0[NW], q1[NW];
+          const float* np = k + 2 < kDp2Tile ? base + (k + 2) * NW : nbase;
+          load_rec<NW>(np, q0);
+          load_rec<NW>(np + NW, q1);
+          sweep_pair<NJ, R, OBJ>(own, p0, p1, tb);
+#pragma unroll
+          for (int w = 0; w < NW; ++w) { p0[w] = q0[w]; p1[w] = q1[w]; }
         }
-      } else {
-        for (int k = 0; kb + k < K4; k += 2) {
+      } else {  // the ragged last tile: its first pair is in p0, p1
+        sweep_pair<NJ, R, OBJ>(own, p0, p1, tb);
+        for (int k = 2; kb + k < K4; k += 2) {
           float r0[NW], r1[NW];
           load_rec<NW>(base + k * NW, r0);
           load_rec<NW>(base + (k + 1) * NW, r1);
