@@ -328,13 +328,20 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, min_
     rep_h = cppflow.Report()
     pstream = torch.cuda.Stream()
     # warm the plain path: one request of every K in the pool (each K takes its own
-    # kernel instances, which CUDA loads on their first launch)
+    # kernel instances, which CUDA loads on their first launch); repeated before each
+    # plain timing, after the served run's teardown, so no one-time cost of the
+    # device or driver falls inside the plain window
     first_of_k = {}
     for item in pool:
         first_of_k.setdefault(item[0].K, item)
-    for w, rob, ch, th in first_of_k.values():
-        cppflow.plan_host(rob, P, ch, th, w.K, ws, sel_h[:w.T], None, q_h[:w.T * n], None, rep_h,
-                          stream=pstream)
+
+    def warm_plain():
+        for w, rob, ch, th in first_of_k.values():
+            cppflow.plan_host(rob, P, ch, th, w.K, ws, sel_h[:w.T], None, q_h[:w.T * n], None,
+                              rep_h, stream=pstream)
+        torch.cuda.synchronize()
+
+    warm_plain()
     # Warm the served path: CUDA loads a kernel on its first launch, which would stall
     # the server's worker the first time each search form and size appears. The whole
     # pool at once (every throughput form) and a few requests one by one (the latency
@@ -389,6 +396,7 @@ def serving_mix(cppflow, torch, dev, rates, pool_size: int, seconds: float, min_
         sspan = max(done[drop:]) - arr[drop]
         third = max(1, target // 3)
         # plain: the same trace through one stream, one request at a time
+        warm_plain()
         gc.collect()
         gc.disable()
         pdone, pvalid = [], 0
