@@ -327,17 +327,26 @@ constexpr int kDpcThreads = 256;
 constexpr int kDpcWarps = kDpcThreads / 32;
 static_assert(kDp2Tile == 2 * kDpcWarps, "the rescan gives each warp 2 nodes of a tile");
 
-inline size_t dpc_smem_bytes(int nj, int Kp, int R) {
-  const int NW = ((nj + 1 + 3) / 4) * 4;
-  return (size_t)2 * rec_layer_floats(NW, Kp) * 4 + (size_t)3 * kDpcWarps * 32 * R * 4;
+// Floats from node lo's record to the end of node lo + n - 1's (the skew gaps
+// between tiles included): one contiguous span of the record layout.
+__host__ __device__ __forceinline__ int rec_span_floats(int NW, int lo, int n) {
+  return (lo + n - 1) * NW + ((lo + n - 1) / kDp2Tile) * 4 + NW - (lo * NW + (lo / kDp2Tile) * 4);
 }
 
-// 16 bytes into a peer's shared memory; completion counts 16 bytes on the
-// peer's mbarrier (both addresses from mapa).
-__device__ __forceinline__ void st_async_v4(uint32_t addr, float4 v, uint32_t bar) {
+inline size_t dpc_smem_bytes(int nj, int Kp, int R) {
+  const int NW = ((nj + 1 + 3) / 4) * 4;
+  return (size_t)2 * rec_layer_floats(NW, Kp) * 4 + (size_t)3 * kDpcWarps * 32 * R * 4 +
+         (size_t)2 * rec_span_floats(NW, 0, 32 * R) * 4;  // send staging, double-buffered
+}
+
+// A bulk copy (TMA engine) from this CTA's shared memory into a CTA of the
+// cluster; completion counts its bytes on that CTA's mbarrier (dst and bar from
+// mapa). Both addresses 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_s2cluster(uint32_t dst, uint32_t src, uint32_t bytes,
+                                               uint32_t bar) {
   asm volatile(
-      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::
-          "r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst), "r"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
 
@@ -366,10 +375,19 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
   float* const xmin = recb + 2 * (size_t)RL;             // [warps][S]
   int* const xtile = reinterpret_cast<int*>(xmin + kDpcWarps * S);
   int* const xarg = xtile + kDpcWarps * S;
+  const int SPAN = rec_span_floats(NW, 0, S);
+  float* const sendb = reinterpret_cast<float*>(xarg + kDpcWarps * S);  // [2][SPAN] staging
   __shared__ uint64_t rbar[2];  // layer L's records arrive on rbar[L & 1]
   __shared__ int timeout_flag;
   const float* __restrict__ cand = rq.cand;
-  const uint32_t layer_bytes = (uint32_t)Kp * NW * 4;
+  // this CTA's records as one span of the layout, and the bytes a layer brings
+  // (every owner's span, this CTA's own included)
+  const int own_lo = (int)crank * S, own_n = min(S, Kp - own_lo);
+  const int own_base = rec_off(NW, own_lo);
+  const uint32_t own_bytes = (uint32_t)rec_span_floats(NW, own_lo, own_n) * 4u;
+  uint32_t layer_bytes = 0;
+  for (int c = 0; c < CSr; ++c)
+    layer_bytes += (uint32_t)rec_span_floats(NW, c * S, min(S, Kp - c * S)) * 4u;
   if (tid == 0) {
     timeout_flag = 0;
     mbar_init(&rbar[0], 1);
@@ -519,8 +537,12 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       xarg[warp * S + slot] = found;
     }
     __syncthreads();
-    // every warp takes the lowest match of its lane's slots and sends the new
-    // records to the CTAs c = warp, warp + 8 of the cluster
+    // every warp takes the lowest match of its lane's slots; warp 0 writes the new
+    // records into the send staging (laid out as the span they fill), which one
+    // bulk copy per owner CTA (this one included) carries into its record buffer.
+    // The staging of layer L is rewritten for layer L + 2, after every owner has
+    // sent layer L + 1, which each did only after receiving layer L.
+    float* const sb = sendb + (size_t)(L & 1) * SPAN;
     int bsel[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -528,7 +550,7 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       int ba = xarg[slot];
       for (int w = 1; w < kDpcWarps; ++w) ba = min(ba, xarg[w * S + slot]);
       bsel[r] = ba == 0x7fffffff ? 0 : ba;
-      if (kp[r] >= Kp) continue;
+      if (warp != 0 || kp[r] >= Kp) continue;
       float v[NW];
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
@@ -540,14 +562,16 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       v[NJ] = kp[r] < K ? comb<OBJ>(bvr[r], rpen[r]) : CUDART_INF_F;
 #pragma unroll
       for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
-      const uint32_t base = smem_u32(nxt + rec_off(NW, kp[r])), bar = smem_u32(&rbar[L & 1]);
-      for (int c = warp; c < CSr; c += kDpcWarps) {
-        const uint32_t peer = map_peer(base, (uint32_t)c), pbar = map_peer(bar, (uint32_t)c);
+      float4* dst = reinterpret_cast<float4*>(sb + (rec_off(NW, kp[r]) - own_base));
 #pragma unroll
-        for (int w = 0; w < NW / 4; ++w)
-          st_async_v4(peer + 16 * w, make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]),
-                      pbar);
-      }
+      for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
+    }
+    if (warp == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the staging, to the copy engine
+      __syncwarp();
+      if (lane < CSr)
+        bulk_s2cluster(map_peer(smem_u32(nxt + own_base), (uint32_t)lane), smem_u32(sb), own_bytes,
+                       map_peer(smem_u32(&rbar[L & 1]), (uint32_t)lane));
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
