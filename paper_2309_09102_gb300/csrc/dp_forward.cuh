@@ -336,7 +336,16 @@ __host__ __device__ __forceinline__ int rec_span_floats(int NW, int lo, int n) {
 inline size_t dpc_smem_bytes(int nj, int Kp, int R) {
   const int NW = ((nj + 1 + 3) / 4) * 4;
   return (size_t)2 * rec_layer_floats(NW, Kp) * 4 + (size_t)3 * kDpcWarps * 32 * R * 4 +
-         (size_t)2 * rec_span_floats(NW, 0, 32 * R) * 4;  // send staging, double-buffered
+         (R <= 2 ? (size_t)2 * rec_span_floats(NW, 0, 32 * R) * 4 : 0);  // bulk send staging
+}
+
+// 16 bytes into a peer's shared memory; completion counts 16 bytes on the
+// peer's mbarrier (both addresses from mapa).
+__device__ __forceinline__ void st_async_v4(uint32_t addr, float4 v, uint32_t bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::
+          "r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+      : "memory");
 }
 
 // A bulk copy (TMA engine) from this CTA's shared memory into a CTA of the
@@ -354,6 +363,11 @@ template <int NJ, int R, int OBJ, class Src>
 __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_constant__ Src src,
                                                                    const int CS) {
   constexpr int NW = Rec<NJ>::NW, NP = Rec<NJ>::NP, S = 32 * R;
+  // how records travel: 32 and 64 successors per CTA (the latency forms) as one
+  // bulk copy per owner CTA from a staging span written by warp 0; 128 per CTA
+  // (a throughput form, 4 records per lane) by asynchronous stores from every
+  // warp (measured: the single writing warp slowed that form in full batches)
+  constexpr bool kBulk = R <= 2;
   const uint32_t crank = cluster_rank();
   const Req& rq = src.req(blockIdx.x / CS);
   const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
@@ -385,8 +399,8 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
   const int own_lo = (int)crank * S, own_n = min(S, Kp - own_lo);
   const int own_base = rec_off(NW, own_lo);
   const uint32_t own_bytes = (uint32_t)rec_span_floats(NW, own_lo, own_n) * 4u;
-  uint32_t layer_bytes = 0;
-  for (int c = 0; c < CSr; ++c)
+  uint32_t layer_bytes = kBulk ? 0u : (uint32_t)Kp * NW * 4u;
+  for (int c = 0; kBulk && c < CSr; ++c)
     layer_bytes += (uint32_t)rec_span_floats(NW, c * S, min(S, Kp - c * S)) * 4u;
   if (tid == 0) {
     timeout_flag = 0;
@@ -460,10 +474,11 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
     int btile[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { best[r] = CUDART_INF_F; btile[r] = -1; }
-    // The records are swept a pair at a time with the next pair already loaded (the
-    // first pair of the next tile included), so the shared-memory load latency of a
-    // pair overlaps the arithmetic of the one before: with 8 warps per SM it is not
-    // hidden otherwise.
+    // The records are swept a pair at a time (two pairs into two running minima for
+    // one successor per lane), with the next pair already loaded (the first pair of
+    // the next tile included), so the shared-memory load latency overlaps the
+    // arithmetic before it: with 8 warps per SM it is not hidden otherwise. (min is
+    // exact: the split changes no value.)
     float p0[NW], p1[NW];  // the pair swept next
     if (t_lo < t_hi) {
       const float* b0 = cur + rec_off(NW, t_lo * kDp2Tile);
@@ -476,10 +491,26 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       const float* base = cur + rec_off(NW, kb);
       // the next tile's first record (this tile's own first one for the last tile)
       const float* nbase = t + 1 < t_hi ? base + kDp2Tile * NW + 4 : base;
-      float tb[R];
+      float tb[R], tb2[R];  // two running minima (two pairs in flight), merged per tile
 #pragma unroll
-      for (int r = 0; r < R; ++r) tb[r] = CUDART_INF_F;
-      if (kb + kDp2Tile <= K4) {
+      for (int r = 0; r < R; ++r) tb[r] = tb2[r] = CUDART_INF_F;
+      if (kb + kDp2Tile <= K4 && R == 1) {  // measured: two pairs in flight help only R = 1
+#pragma unroll
+        for (int k = 0; k < kDp2Tile; k += 4) {
+          float q0[NW], q1[NW], n0[NW], n1[NW];
+          load_rec<NW>(base + (k + 2) * NW, q0);
+          load_rec<NW>(base + (k + 3) * NW, q1);
+          const float* np = k + 4 < kDp2Tile ? base + (k + 4) * NW : nbase;
+          load_rec<NW>(np, n0);
+          load_rec<NW>(np + NW, n1);
+          sweep_pair<NJ, R, OBJ>(own, p0, p1, tb);
+          sweep_pair<NJ, R, OBJ>(own, q0, q1, tb2);
+#pragma unroll
+          for (int w = 0; w < NW; ++w) { p0[w] = n0[w]; p1[w] = n1[w]; }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) tb[r] = fminf(tb[r], tb2[r]);
+      } else if (kb + kDp2Tile <= K4) {
 #pragma unroll
         for (int k = 0; k < kDp2Tile; k += 2) {
           float q0[NW], q1[NW];
@@ -537,11 +568,12 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       xarg[warp * S + slot] = found;
     }
     __syncthreads();
-    // every warp takes the lowest match of its lane's slots; warp 0 writes the new
-    // records into the send staging (laid out as the span they fill), which one
-    // bulk copy per owner CTA (this one included) carries into its record buffer.
-    // The staging of layer L is rewritten for layer L + 2, after every owner has
-    // sent layer L + 1, which each did only after receiving layer L.
+    // every warp takes the lowest match of its lane's slots. Bulk form: warp 0
+    // writes the new records into the send staging (laid out as the span they
+    // fill), which one bulk copy per owner CTA (this one included) carries into
+    // its record buffer; the staging of layer L is rewritten for layer L + 2,
+    // after every owner has sent layer L + 1, which each did only after receiving
+    // layer L. Store form: warp w sends its lanes' records to CTAs w, w + 8.
     float* const sb = sendb + (size_t)(L & 1) * SPAN;
     int bsel[R];
 #pragma unroll
@@ -550,7 +582,7 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       int ba = xarg[slot];
       for (int w = 1; w < kDpcWarps; ++w) ba = min(ba, xarg[w * S + slot]);
       bsel[r] = ba == 0x7fffffff ? 0 : ba;
-      if (warp != 0 || kp[r] >= Kp) continue;
+      if ((kBulk && warp != 0) || kp[r] >= Kp) continue;
       float v[NW];
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
@@ -562,11 +594,22 @@ __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_c
       v[NJ] = kp[r] < K ? comb<OBJ>(bvr[r], rpen[r]) : CUDART_INF_F;
 #pragma unroll
       for (int j = NJ + 1; j < NW; ++j) v[j] = 0.f;
-      float4* dst = reinterpret_cast<float4*>(sb + (rec_off(NW, kp[r]) - own_base));
+      if (kBulk) {
+        float4* dst = reinterpret_cast<float4*>(sb + (rec_off(NW, kp[r]) - own_base));
 #pragma unroll
-      for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
+        for (int w = 0; w < NW / 4; ++w) dst[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
+      } else {
+        const uint32_t base = smem_u32(nxt + rec_off(NW, kp[r])), bar = smem_u32(&rbar[L & 1]);
+        for (int c = warp; c < CSr; c += kDpcWarps) {
+          const uint32_t peer = map_peer(base, (uint32_t)c), pbar = map_peer(bar, (uint32_t)c);
+#pragma unroll
+          for (int w = 0; w < NW / 4; ++w)
+            st_async_v4(peer + 16 * w, make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]),
+                        pbar);
+        }
+      }
     }
-    if (warp == 0) {
+    if (kBulk && warp == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the staging, to the copy engine
       __syncwarp();
       if (lane < CSr)
