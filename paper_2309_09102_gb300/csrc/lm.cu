@@ -280,7 +280,10 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
     cached = true;
     }
     // Cholesky of J^T J + lam I, left-looking, in place: L_jj = sqrt(A_jj + lam - sum L_jm^2),
-    // L_xj = (A_xj - sum L_xm L_jm) / L_jj
+    // L_xj = (A_xj - sum L_xm L_jm) / L_jj. Only 1 / L_jj is used (the off-diagonal
+    // entries and both solves multiply by it), so each pivot takes one reciprocal
+    // square root (rsqrt, within 1 ulp) where a square root and a division would
+    // take two FP64 sequences on GB300's narrow FP64 pipe.
     bool ok = true;
     double inv[MJ];
 #pragma unroll
@@ -290,9 +293,7 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
 #pragma unroll
       for (int m = 0; m < j; ++m) d -= A[j * (j + 1) / 2 + m] * A[j * (j + 1) / 2 + m];
       ok = ok && (d > 0.0) && isfinite(d);
-      const double ljj = sqrt(d);
-      A[j * (j + 1) / 2 + j] = ljj;
-      inv[j] = 1.0 / ljj;
+      inv[j] = rsqrt(d);
 #pragma unroll
       for (int x = j + 1; x < MJ; ++x) {
         if (!NJ && x >= n) break;
