@@ -607,9 +607,9 @@ typedef struct cpp_server_config {
      * searches take about as long, and runs each search in the form with the
      * highest edge rate per SM whose estimated time is at most search_budget_ms:
      * one CTA, clusters of 512 or of 256 successors per CTA (the wide form of
-     * cpp_batch_set_split), else clusters of 128 successors per CTA (estimates from
-     * rates measured on GB300, stated in the server source). Results are identical
-     * in every form. (defaults 8 and 12 ms; latency_requests >= 0,
+     * cpp_batch_set_split), clusters of 128 successors per CTA, else clusters of 64
+     * (estimates from rates measured on GB300, stated in the server source).
+     * Results are identical in every form. (defaults 8 and 12 ms; latency_requests >= 0,
      * search_budget_ms >= 0) */
     int32_t latency_requests;
     int32_t reserved_;

@@ -120,10 +120,10 @@ def test_throughput_form_mixed_k_equals_alone(budget):
     """Under load (latency_requests = 0: every launch in the throughput form) requests of
     different K share a launch; the search runs once per K bucket and form on forked
     streams, each request in the most efficient form within the time budget: one CTA,
-    wide clusters of 512 or 256 successors per CTA, clusters of 128 (a group's largest
-    Kp sets the cluster, so a smaller request's last CTAs may own nothing). The budgets
-    here move these small requests across all four forms. Every plan equals cpp_plan
-    alone."""
+    wide clusters of 512 or 256 successors per CTA, clusters of 128, else of 64 (a
+    group's largest Kp sets the cluster, so a smaller request's last CTAs may own
+    nothing). The budgets here move these small requests across all five forms. Every
+    plan equals cpp_plan alone."""
     shapes = [(30, 1000), (45, 300), (20, 128), (61, 600), (12, 1024), (33, 260), (40, 90),
               (25, 544), (1, 700), (2, 513)]
     pbs = [problems.small(T=T, K=K, seed=800 + i) for i, (T, K) in enumerate(shapes)]
