@@ -550,10 +550,20 @@ typedef struct cpp_tune_result {
     float mask_ms;           /* mask stage time of the choice (-1 from the table) */
     float mask_ms_default;   /* mask stage time with 4 tasks per warp (-1 from the table) */
     int32_t cluster_min_kp;  /* smallest Kp allowed to run as a cluster (0: any) */
-    int32_t reserved;
+    float budget_ms;         /* > 0: per-request forms within this time (cpp_batch_set_budget);
+                                0: the alpha split */
 } cpp_tune_result_t;
 cpp_status cpp_batch_set_split(cpp_batch_t* batch, double alpha, int32_t cands_per_cta,
                                cpp_stream_t stream);
+/* The search schedule of the serving loop under load: each request runs in the
+ * form with the highest edge rate per SM whose estimated search time is at most
+ * budget_ms (one CTA, clusters of 512, 256, 128 or 64 successors per CTA; rates
+ * measured on GB300, stated in the library source), else in the fastest of them.
+ * Cluster requests are grouped by tile and cluster size, one launch per group.
+ * Results are identical in every schedule. INVALID_ARG if budget_ms <= 0 or the
+ * choice makes more than 8 cluster groups; cpp_batch_set_split returns to the
+ * alpha split. Drops any captured graph. */
+cpp_status cpp_batch_set_budget(cpp_batch_t* batch, double budget_ms, cpp_stream_t stream);
 /* Smallest Kp that may run as a cluster (0: any): heavier requests of smaller K
  * then stay one CTA each, longest first. Re-applies the current alpha and
  * cands_per_cta and uploads the schedule on `stream`. INVALID_ARG if negative. */

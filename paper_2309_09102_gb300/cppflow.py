@@ -111,7 +111,7 @@ class TuneResult(C.Structure):
                 ("dp_ms", C.c_float), ("dp_ms_unsplit", C.c_float),
                 ("mask_tasks_per_warp", C.c_int32), ("mask_ms", C.c_float),
                 ("mask_ms_default", C.c_float), ("cluster_min_kp", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("budget_ms", C.c_float)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -194,6 +194,7 @@ _SIGS = {
     "cpp_batch_launches": (C.c_int32, [_P, C.c_uint32]),
     "cpp_batch_destroy": (None, [_P]),
     "cpp_batch_set_split": (C.c_int, [_P, C.c_double, C.c_int32, _P]),
+    "cpp_batch_set_budget": (C.c_int, [_P, C.c_double, _P]),
     "cpp_batch_set_mask_tasks": (C.c_int, [_P, C.c_int32]),
     "cpp_wait_selftest": (C.c_int, [C.c_int64, C.c_int32, _P, _P]),
     "cpp_batch_set_cluster_min_kp": (C.c_int, [_P, C.c_int32, _P]),
@@ -522,6 +523,10 @@ class Batch:
     def set_split(self, alpha: float, cands_per_cta: int = 0, stream=None):
         _check(lib().cpp_batch_set_split(self.handle, float(alpha), int(cands_per_cta),
                                          stream_handle(stream)), "cpp_batch_set_split")
+
+    def set_budget(self, budget_ms: float, stream=None):
+        _check(lib().cpp_batch_set_budget(self.handle, float(budget_ms), stream_handle(stream)),
+               "cpp_batch_set_budget")
 
     def set_cluster_min_kp(self, min_kp: int, stream=None):
         _check(lib().cpp_batch_set_cluster_min_kp(self.handle, int(min_kp), stream_handle(stream)),

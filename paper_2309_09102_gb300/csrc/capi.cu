@@ -698,6 +698,7 @@ struct cpp_batch {
   bool any_geo;  // some request has a collision model
   double alpha;
   int cpc;  // successor candidates per CTA of the cluster form (0: default)
+  double budget_ms;  // > 0: per-request forms within this search time (alpha, cpc unused)
   int mask_tpw;  // 128-candidate tasks per warp of the mask stage (0: default)
   int min_kp;    // smallest Kp that may run as a cluster (0: any)
   int heavy;
@@ -715,26 +716,22 @@ void drop_graph(cpp_batch* b) {
   b->graph_stages = 0;
 }
 
-// Split the requests for alpha (<= 0: none heavy) and cluster tiles of cpc
-// successors per CTA, and upload the schedule table.
-cpp_status set_schedule(cpp_batch* b, double alpha, int cpc, cudaStream_t st) {
+// The schedule from a per-request choice: cpc_of[r] < 0 runs request r on one
+// CTA, 0 as a cluster of the default tile, > 0 as a cluster of that many
+// successors per CTA. Cluster requests are grouped by that choice and cluster
+// size (one launch per group, each on its own stream), the rest form the
+// one-CTA group in a table sorted longest first. Uploads the schedule table.
+cpp_status build_schedule(cpp_batch* b, const std::vector<int>& cpc_of, cudaStream_t st) {
   const int count = b->count;
-  long long total = 0;
-  for (long long e : b->edges) total += e;
-  const double slots = 2.0 * device_sm_count();
-  const double thr = alpha > 0 ? alpha * (double)total / slots : HUGE_VAL;
   std::vector<int> heavy, light;
-  for (int r = 0; r < count; ++r) {
-    const bool h =
-        fast_n(b->n) && cluster_size(b->reqs[r].Kp, cpc) > 0 && (double)b->edges[r] >= thr &&
-        b->reqs[r].Kp >= b->min_kp;
-    (h ? heavy : light).push_back(r);
-  }
+  for (int r = 0; r < count; ++r) (cpc_of[r] >= 0 ? heavy : light).push_back(r);
   auto longer = [&](int x, int y) {
     return b->edges[x] != b->edges[y] ? b->edges[x] > b->edges[y] : x < y;
   };
+  auto cs_of = [&](int r) { return cluster_size(b->reqs[r].Kp, cpc_of[r]); };
   std::sort(heavy.begin(), heavy.end(), [&](int x, int y) {
-    const int cx = cluster_size(b->reqs[x].Kp, cpc), cy = cluster_size(b->reqs[y].Kp, cpc);
+    if (cpc_of[x] != cpc_of[y]) return cpc_of[x] > cpc_of[y];
+    const int cx = cs_of(x), cy = cs_of(y);
     return cx != cy ? cx > cy : longer(x, y);
   });
   std::sort(light.begin(), light.end(), longer);
@@ -742,9 +739,9 @@ cpp_status set_schedule(cpp_batch* b, double alpha, int cpc, cudaStream_t st) {
   std::vector<Req> table;
   table.reserve(count);
   for (size_t i = 0; i < heavy.size();) {
-    const int cs = cluster_size(b->reqs[heavy[i]].Kp, cpc);
+    const int cpc = cpc_of[heavy[i]], cs = cs_of(heavy[i]);
     SchedGroup g{(int)table.size(), 0, 0, kFormCluster, cpc};
-    for (; i < heavy.size() && cluster_size(b->reqs[heavy[i]].Kp, cpc) == cs; ++i) {
+    for (; i < heavy.size() && cpc_of[heavy[i]] == cpc && cs_of(heavy[i]) == cs; ++i) {
       table.push_back(b->reqs[heavy[i]]);
       g.max_Kp = std::max(g.max_Kp, b->reqs[heavy[i]].Kp);
       ++g.count;
@@ -777,10 +774,54 @@ cpp_status set_schedule(cpp_batch* b, double alpha, int cpc, cudaStream_t st) {
                                                  cudaMemcpyHostToDevice, st), "batch schedule"))
     return e;
   b->groups = groups;
-  b->alpha = alpha;
-  b->cpc = cpc;
   b->heavy = (int)heavy.size();
   drop_graph(b);
+  return CPP_OK;
+}
+
+// Split the requests for alpha (<= 0: none heavy) and cluster tiles of cpc
+// successors per CTA: requests whose lattice (edges (T - 1) Kp^2) is at least
+// alpha times the mean load of a CTA slot run as clusters.
+cpp_status set_schedule(cpp_batch* b, double alpha, int cpc, cudaStream_t st) {
+  long long total = 0;
+  for (long long e : b->edges) total += e;
+  const double slots = 2.0 * device_sm_count();
+  const double thr = alpha > 0 ? alpha * (double)total / slots : HUGE_VAL;
+  std::vector<int> cpc_of(b->count, -1);
+  for (int r = 0; r < b->count; ++r) {
+    const bool h =
+        fast_n(b->n) && cluster_size(b->reqs[r].Kp, cpc) > 0 && (double)b->edges[r] >= thr &&
+        b->reqs[r].Kp >= b->min_kp;
+    if (h) cpc_of[r] = cpc;
+  }
+  if (cpp_status e = build_schedule(b, cpc_of, st)) return e;
+  b->alpha = alpha;
+  b->cpc = cpc;
+  b->budget_ms = 0.0;
+  return CPP_OK;
+}
+
+// Each request in the search form with the highest edge rate per SM whose
+// estimated time is within budget_ms (the server's policy, pick_search_form).
+std::vector<int> budget_forms(const cpp_batch* b, double budget_ms) {
+  std::vector<int> cpc_of(b->count, -1);
+  if (!fast_n(b->n)) return cpc_of;
+  for (int r = 0; r < b->count; ++r) {
+    const SearchForm f = pick_search_form(b->reqs[r].T, b->reqs[r].Kp, budget_ms);
+    if (f.form == kFormCluster) cpc_of[r] = f.cpc;
+  }
+  return cpc_of;
+}
+int schedule_groups(const cpp_batch* b, const std::vector<int>& cpc_of) {
+  std::vector<std::pair<int, int>> keys;
+  for (int r = 0; r < b->count; ++r)
+    if (cpc_of[r] >= 0) keys.emplace_back(cpc_of[r], cluster_size(b->reqs[r].Kp, cpc_of[r]));
+  std::sort(keys.begin(), keys.end());
+  return (int)(std::unique(keys.begin(), keys.end()) - keys.begin());
+}
+cpp_status set_budget(cpp_batch* b, double budget_ms, cudaStream_t st) {
+  if (cpp_status e = build_schedule(b, budget_forms(b, budget_ms), st)) return e;
+  b->budget_ms = budget_ms;
   return CPP_OK;
 }
 
@@ -851,24 +892,26 @@ std::string tune_key(const cpp_batch* b) {
   return buf;
 }
 
-// One line per entry: "key alpha cands_per_cta ms [mask_tasks_per_warp [min_kp]]"
-// (fields absent in older tables: the defaults); the last entry of a key wins.
+// One line per entry: "key alpha cands_per_cta ms [mask_tasks_per_warp [min_kp
+// [budget_ms]]]" (fields absent in older tables: the defaults; budget_ms > 0
+// selects per-request forms within that time); the last entry of a key wins.
 bool table_lookup(const char* path, const std::string& key, double* alpha, int* cpc, int* tpw,
-                  int* min_kp) {
+                  int* min_kp, double* budget_ms) {
   if (!path) return false;
   FILE* f = fopen(path, "r");
   if (!f) return false;
   char line[512], k[200];
   bool found = false;
   while (fgets(line, sizeof(line), f)) {
-    double a, ms;
+    double a, ms, bud = 0.0;
     int c, t = 0, m = 0;
-    const int got = sscanf(line, "%199s %lf %d %lf %d %d", k, &a, &c, &ms, &t, &m);
+    const int got = sscanf(line, "%199s %lf %d %lf %d %d %lf", k, &a, &c, &ms, &t, &m, &bud);
     if (got < 4 || key != k) continue;
     *alpha = a;
     *cpc = c;
     *tpw = got >= 5 && t >= 1 && t <= 64 ? t : 0;
-    *min_kp = got == 6 && m >= 0 ? m : 0;
+    *min_kp = got >= 6 && m >= 0 ? m : 0;
+    *budget_ms = got == 7 && std::isfinite(bud) && bud > 0 ? bud : 0.0;
     found = true;
   }
   fclose(f);
@@ -984,6 +1027,7 @@ cpp_status cpp_batch_create(const cpp_robot_t* robots, int32_t n_robots, const c
   b->any_geo = !geos.empty();
   b->alpha = 0;
   b->cpc = 0;
+  b->budget_ms = 0.0;
   b->mask_tpw = 0;
   b->min_kp = 0;
   b->heavy = 0;
@@ -1026,11 +1070,22 @@ cpp_status cpp_batch_set_split(cpp_batch_t* b, double alpha, int32_t cands_per_c
   return set_schedule(b, alpha, cands_per_cta, (cudaStream_t)stream);
 }
 
+cpp_status cpp_batch_set_budget(cpp_batch_t* b, double budget_ms, cpp_stream_t stream) {
+  if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
+  if (!std::isfinite(budget_ms) || budget_ms <= 0)
+    return fail(CPP_ERR_INVALID_ARG, "budget_ms must be > 0");
+  if (schedule_groups(b, budget_forms(b, budget_ms)) > kMaxGroups)
+    return fail(CPP_ERR_INVALID_ARG, "budget %.3g ms gives more than %d cluster groups", budget_ms,
+                kMaxGroups);
+  return set_budget(b, budget_ms, (cudaStream_t)stream);
+}
+
 cpp_status cpp_batch_set_cluster_min_kp(cpp_batch_t* b, int32_t min_kp, cpp_stream_t stream) {
   if (!b) return fail(CPP_ERR_INVALID_ARG, "batch is NULL");
   if (min_kp < 0) return fail(CPP_ERR_INVALID_ARG, "min_kp must be >= 0");
   b->min_kp = min_kp;
-  return set_schedule(b, b->alpha, b->cpc, (cudaStream_t)stream);
+  return b->budget_ms > 0 ? set_budget(b, b->budget_ms, (cudaStream_t)stream)
+                          : set_schedule(b, b->alpha, b->cpc, (cudaStream_t)stream);
 }
 
 cpp_status cpp_batch_set_mask_tasks(cpp_batch_t* b, int32_t tasks_per_warp) {
@@ -1050,11 +1105,12 @@ cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t s
   memset(&out, 0, sizeof(out));
   out.dp_ms = out.dp_ms_unsplit = out.mask_ms = out.mask_ms_default = -1.f;
   const std::string key = tune_key(b);
-  double alpha = 0;
+  double alpha = 0, budget = 0;
   int cpc = 0, tpw = 0, mk = 0;
-  if (table_lookup(table_path, key, &alpha, &cpc, &tpw, &mk)) {
+  if (table_lookup(table_path, key, &alpha, &cpc, &tpw, &mk, &budget)) {
     b->min_kp = mk;
-    if (cpp_status e = set_schedule(b, alpha, cpc, st)) return e;
+    if (cpp_status e = budget > 0 ? set_budget(b, budget, st) : set_schedule(b, alpha, cpc, st))
+      return e;
     b->mask_tpw = tpw;
     out.from_table = 1;
   } else {
@@ -1070,11 +1126,23 @@ cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t s
     kps.erase(std::unique(kps.begin(), kps.end()), kps.end());
     std::vector<int> mks{0};
     for (size_t i = 1; i < kps.size(); ++i) mks.push_back(kps[i]);
-    struct Cand { double alpha; int cpc, mk; };
-    std::vector<Cand> cands{{0.0, 0, 0}};
+    // and per-request forms within a search-time budget (ms), the budgets that
+    // give distinct schedules with at most kMaxGroups cluster groups
+    struct Cand { double alpha; int cpc, mk; double budget; };
+    std::vector<Cand> cands{{0.0, 0, 0, 0.0}};
     for (int c : {64, 128, 256, 512})
       for (int m : mks)
-        for (double a : kAlphas) cands.push_back({a, c, m});
+        for (double a : kAlphas) cands.push_back({a, c, m, 0.0});
+    {
+      std::vector<std::vector<int>> seen;
+      for (double bud : {1.0, 1.5, 2.0, 3.0, 4.0, 5.0, 6.0, 8.0, 10.0, 12.0, 16.0, 24.0}) {
+        const std::vector<int> f = budget_forms(b, bud);
+        if (schedule_groups(b, f) > kMaxGroups) continue;
+        if (std::find(seen.begin(), seen.end(), f) != seen.end()) continue;
+        seen.push_back(f);
+        cands.push_back({0.0, 0, 0, bud});
+      }
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cpp_status e = cuda_status(cudaEventCreate(&e0), "cpp_batch_tune")) return e;
     if (cpp_status e = cuda_status(cudaEventCreate(&e1), "cpp_batch_tune")) {
@@ -1082,18 +1150,22 @@ cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t s
       return e;
     }
     float best_ms = HUGE_VALF;
-    Cand best{0.0, 0, 0};
+    Cand best{0.0, 0, 0, 0.0};
     int last_heavy = -1, last_cpc = -1, last_mk = -1;
     cpp_status err = CPP_OK;
     for (const Cand& c : cands) {
       b->min_kp = c.mk;
-      if ((err = set_schedule(b, c.alpha, c.cpc, st)) != CPP_OK) break;
+      if ((err = c.budget > 0 ? set_budget(b, c.budget, st) : set_schedule(b, c.alpha, c.cpc, st)) !=
+          CPP_OK)
+        break;
       // same split as before (the heavy set only grows down the ladder)
-      if (b->heavy == last_heavy && c.cpc == last_cpc && c.mk == last_mk) continue;
+      if (c.budget <= 0 && b->heavy == last_heavy && c.cpc == last_cpc && c.mk == last_mk)
+        continue;
       last_heavy = b->heavy;
       last_cpc = c.cpc;
       last_mk = c.mk;
-      if (c.alpha > 0 && b->heavy == 0) continue;                 // same as alpha = 0
+      if (c.budget <= 0 && c.alpha > 0 && b->heavy == 0) continue;  // same as alpha = 0
+      if (c.budget > 0 && b->heavy == 0) continue;                  // same as alpha = 0
       float ms = HUGE_VALF;
       for (int rep = 0; rep < 3 && err == CPP_OK; ++rep) {  // the first run warms up
         cudaError_t ce = cudaEventRecord(e0, st);
@@ -1140,13 +1212,15 @@ cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t s
     b->mask_tpw = best_tpw;
     out.mask_ms = best_mask;
     b->min_kp = best.mk;
-    if (cpp_status e = set_schedule(b, best.alpha, best.cpc, st)) return e;
+    if (cpp_status e = best.budget > 0 ? set_budget(b, best.budget, st)
+                                       : set_schedule(b, best.alpha, best.cpc, st))
+      return e;
     out.dp_ms = best_ms;
     if (table_path) {
       FILE* f = fopen(table_path, "a");
       if (!f) return fail(CPP_ERR_INVALID_ARG, "cannot append to tuning table %s", table_path);
-      fprintf(f, "%s %.9g %d %.4f %d %d\n", key.c_str(), best.alpha, best.cpc, best_ms, best_tpw,
-              best.mk);
+      fprintf(f, "%s %.9g %d %.4f %d %d %.9g\n", key.c_str(), best.alpha, best.cpc, best_ms,
+              best_tpw, best.mk, best.budget);
       fclose(f);
     }
   }
@@ -1154,6 +1228,7 @@ cpp_status cpp_batch_tune(cpp_batch_t* b, const char* table_path, cpp_stream_t s
   out.cands_per_cta = b->cpc;
   out.mask_tasks_per_warp = b->mask_tpw > 0 ? b->mask_tpw : 4;
   out.cluster_min_kp = b->min_kp;
+  out.budget_ms = (float)b->budget_ms;
   out.heavy = b->heavy;
   out.forward_launches = 0;
   for (const SchedGroup& g : b->groups) out.forward_launches += g.count > 0 ? 1 : 0;

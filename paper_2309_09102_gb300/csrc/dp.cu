@@ -239,6 +239,32 @@ int device_sm_count() {
 // default (64 up to Kp = 512, 128 above), as long as the cluster has 2..8 CTAs,
 // or up to 16 (a non-portable cluster size, opted into at launch) when 32 or 64
 // per CTA is asked for explicitly.
+// Per CTA at two CTAs per SM a one-CTA search sweeps about 7.7e9 edges/s on GB300
+// (measured: 2.35e12 edges/s over 304 CTAs); relative to it, measured at full
+// occupancy with T = 300: the wide cluster form at 512 successors per CTA 1.0 (K =
+// 1024), at 256 per CTA 0.79 (K = 1024) and 0.98 (K = 512), the record-exchange
+// form at 128 per CTA 0.66, and at 64 per CTA (bulk record copies) about the same
+// per SM at twice the width (T = 300, K = 1024 alone: 1.88 ms on 16 CTAs), the
+// fallback for the longest requests. A cluster of CS CTAs owning S successors
+// each takes (T - 1) S Kp / (7.7e9 x efficiency) seconds.
+SearchForm pick_search_form(int T, int Kp_, double budget_ms) {
+  constexpr double kCtaEdgesPerS = 7.7e9;
+  const double steps = T > 1 ? T - 1 : 1, Kp = Kp_;
+  const SearchForm cand[5] = {
+      {kFormCta, 0, steps * Kp * Kp / kCtaEdgesPerS * 1e3, 0},
+      {kFormCluster, 512, steps * 512.0 * Kp / (kCtaEdgesPerS * 1.0) * 1e3, 1},
+      {kFormCluster, 256, steps * 256.0 * Kp / (kCtaEdgesPerS * (Kp_ > 512 ? 0.79 : 0.98)) * 1e3, 2},
+      {kFormCluster, 128, steps * 128.0 * Kp / (kCtaEdgesPerS * 0.66) * 1e3, 3},
+      {kFormCluster, 64, steps * 64.0 * Kp / (kCtaEdgesPerS * 0.66) * 1e3, 4}};
+  const SearchForm* last = &cand[0];
+  for (const SearchForm& f : cand) {
+    if (f.form == kFormCluster && cluster_size(Kp_, f.cpc) < 2) continue;  // no such cluster
+    last = &f;
+    if (f.est_ms <= budget_ms) return f;
+  }
+  return *last;
+}
+
 int cluster_succ(int Kp, int cpc) {
   if (Kp <= 64 || Kp > 1024) return 0;
   const int S = cpc ? cpc : (Kp <= 512 ? 64 : 128);

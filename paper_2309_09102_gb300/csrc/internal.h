@@ -49,6 +49,14 @@ cudaError_t launch_forward_minmax(const BatchSrc& s, int n, int nreq, int max_Kp
 // candidates per CTA of the cluster form, 0 for the default)
 cudaError_t launch_forward(const BatchSrc& s, int objective, int n, int nreq, int max_Kp, int form,
                            int cpc, cudaStream_t st);
+// The search form with the highest edge rate per SM whose estimated time is at
+// most budget_ms, else the fastest of them (see pick_search_form in dp.cu).
+struct SearchForm {
+  int form, cpc;   // forward sweep form and successors per CTA
+  double est_ms;   // estimated search time
+  int rank;        // index of the form (one CTA, wide 512, wide 256, 128, 64 per CTA)
+};
+SearchForm pick_search_form(int T, int Kp, double budget_ms);
 int cluster_succ(int Kp, int cpc);  // successors per CTA of the cluster form (0: no cluster form)
 int cluster_size(int Kp, int cpc);  // CTAs per cluster (0: no cluster form)
 int device_sm_count();     // SMs of the current device

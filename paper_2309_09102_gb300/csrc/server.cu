@@ -254,37 +254,9 @@ static int k_bucket(const Request* r) {
 }
 static int t_bucket(const Request* r) { return r->T <= 256 ? 0 : r->T <= 1024 ? 1 : 2; }
 
-// The search form of a request under load: the form with the highest edge rate
-// per SM whose search takes at most `budget_ms`, else the fastest throughput form.
-// Per CTA at two CTAs per SM a one-CTA search sweeps about 7.7e9 edges/s on GB300
-// (measured: 2.35e12 edges/s over 304 CTAs); relative to it, measured at full
-// occupancy with T = 300: the wide cluster form at 512 successors per CTA 1.0 (K =
-// 1024), at 256 per CTA 0.79 (K = 1024) and 0.98 (K = 512), the record-exchange
-// form at 128 per CTA 0.66, and at 64 per CTA (bulk record copies) about the same
-// per SM at twice the width (T = 300, K = 1024 alone: 1.88 ms on 16 CTAs), the
-// fallback for the longest requests. A cluster of CS CTAs owning S successors
-// each takes (T - 1) S Kp / (7.7e9 x efficiency) seconds.
-struct SearchForm {
-  int form, cpc;   // forward sweep form and successors per CTA
-  double est_ms;   // estimated search time
-  int rank;        // index of the form (one CTA, wide 512, wide 256, 128, 64 per CTA)
-};
+// The search form of a request under load (the library's measured-rate policy).
 static SearchForm throughput_form(const Request* r, double budget_ms) {
-  constexpr double kCtaEdgesPerS = 7.7e9;
-  const double steps = r->T > 1 ? r->T - 1 : 1, Kp = r->Kp;
-  const SearchForm cand[5] = {
-      {kFormCta, 0, steps * Kp * Kp / kCtaEdgesPerS * 1e3, 0},
-      {kFormCluster, 512, steps * 512.0 * Kp / (kCtaEdgesPerS * 1.0) * 1e3, 1},
-      {kFormCluster, 256, steps * 256.0 * Kp / (kCtaEdgesPerS * (r->Kp > 512 ? 0.79 : 0.98)) * 1e3, 2},
-      {kFormCluster, 128, steps * 128.0 * Kp / (kCtaEdgesPerS * 0.66) * 1e3, 3},
-      {kFormCluster, 64, steps * 64.0 * Kp / (kCtaEdgesPerS * 0.66) * 1e3, 4}};
-  const SearchForm* last = &cand[0];
-  for (const SearchForm& f : cand) {
-    if (f.form == kFormCluster && cluster_size(r->Kp, f.cpc) < 2) continue;  // no such cluster
-    last = &f;
-    if (f.est_ms <= budget_ms) return f;
-  }
-  return *last;
+  return pick_search_form(r->T, r->Kp, budget_ms);
 }
 
 // Search time class under load: requests whose estimated search times (in their

@@ -144,22 +144,54 @@ def test_tuner_and_its_table(batch_setup, tmp_path):
     assert 0 < r1["mask_ms"] <= r1["mask_ms_default"]
     lines = table.read_text().split("\n")
     assert len([x for x in lines if x]) == 1
-    key, alpha, cpc, ms, tpw, mk = lines[0].split()
+    key, alpha, cpc, ms, tpw, mk, bud = lines[0].split()
     assert key.startswith("n7_obj0_") and float(alpha) == pytest.approx(r1["alpha"], rel=1e-6)
     assert int(cpc) == r1["cands_per_cta"] and int(tpw) == r1["mask_tasks_per_warp"]
     assert int(mk) == r1["cluster_min_kp"] and int(mk) in (0, 256, 512)
+    assert float(bud) == pytest.approx(r1["budget_ms"], rel=1e-6) and float(bud) >= 0
     after = results_after_run(S)
     r2 = S["batch"].tune(str(table), S["stream"])
     assert r2["from_table"] == 1 and r2["timed"] == 0
     assert r2["alpha"] == pytest.approx(r1["alpha"], rel=1e-6) and r2["heavy"] == r1["heavy"]
     assert r2["mask_tasks_per_warp"] == r1["mask_tasks_per_warp"]
     assert r2["cluster_min_kp"] == r1["cluster_min_kp"]
+    assert r2["budget_ms"] == pytest.approx(r1["budget_ms"], rel=1e-6)
     assert_same(results_after_run(S), after)
     assert_same(after, run_with(S, 0.0))
     # an entry written before the mask knob existed (four fields): the default
     table.write_text(f"{key} {alpha} {cpc} {ms}\n")
     r3 = S["batch"].tune(str(table), S["stream"])
     assert r3["from_table"] == 1 and r3["mask_tasks_per_warp"] == 4 and r3["cluster_min_kp"] == 0
+    assert r3["budget_ms"] == 0
+    # an entry with a search-time budget: per-request forms
+    table.write_text(f"{key} 0 0 {ms} 4 0 1.0\n")
+    r4 = S["batch"].tune(str(table), S["stream"])
+    assert r4["from_table"] == 1 and r4["budget_ms"] == pytest.approx(1.0) and r4["heavy"] == 6
+    assert_same(results_after_run(S), after)
+    S["batch"].set_split(0.0, 0, S["stream"])
+
+
+@pytest.mark.parametrize("budget", [0.05, 0.3, 1.0, 3.0, 10.0])
+def test_budget_schedules_give_the_same_plans(batch_setup, budget):
+    """Per-request search forms within a time budget (the serving loop's policy): small
+    budgets put every request on clusters of 64 successors per CTA (2, 4 and 8 CTAs),
+    1 ms mixes wide clusters of 256 per CTA with them, 3 ms clusters of 128, 10 ms only
+    the T = 300, K = 512 request on a wide cluster (estimated 10.2 ms on one CTA). Every schedule gives the same
+    plans, bit for bit; a budget <= 0 is refused."""
+    S = batch_setup
+    base = run_with(S, 0.0)
+    groups = {0.05: 3, 0.3: 4, 1.0: 4, 3.0: 3, 10.0: 2}[budget]  # cluster groups + one-CTA
+    try:
+        clear(S)
+        S["batch"].set_budget(budget, S["stream"])
+        S["batch"].run(cppflow.STAGE_ALL, S["stream"])
+        S["stream"].synchronize()
+        assert_same(results(S), base)
+        assert S["batch"].launches(cppflow.STAGE_DP_FORWARD) == groups
+        rc = cppflow.lib().cpp_batch_set_budget(S["batch"].handle, 0.0, None)
+        assert rc == cppflow.ERR_INVALID_ARG
+    finally:
+        S["batch"].set_split(0.0, 0, S["stream"])
 
 
 @pytest.mark.parametrize("tpw", [1, 2, 8, 16, 64])
