@@ -1002,8 +1002,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=304)
     ap.add_argument("--plain", type=int, default=32, help="requests timed on the plain path")
-    ap.add_argument("--serve-batch", type=int, default=76, help="server: requests per launch")
-    ap.add_argument("--serve-inflight", type=int, default=8, help="server: launches in flight")
+    ap.add_argument("--serve-batch", type=int, default=38, help="server: requests per launch")
+    ap.add_argument("--serve-inflight", type=int, default=16, help="server: launches in flight")
     ap.add_argument("--serve-depth", type=int, default=3,
                     help="e2e client: steps of requests in flight")
     ap.add_argument("--uneven", type=int, default=256,
