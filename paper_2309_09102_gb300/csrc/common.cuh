@@ -230,22 +230,29 @@ __device__ inline void quat_to_rot(const double* q4, double R[9]) {
 
 // Geodesic angle between two rotations (§II "Pose error"): the angle of
 // E = Rt^T R from its skew part and trace, atan2(|vee(E - E^T)| / 2, (tr E - 1) / 2).
+// Its parts: c = (tr E - 1) / 2 (the cosine of the angle) and vv = |vee(E - E^T)|^2
+// (four times the squared sine), from which threshold tests need no root or atan2.
 template <class F>
-__device__ __forceinline__ F geodesic(const F Rt[9], const F R[9]) {
+__device__ __forceinline__ void geodesic_parts(const F Rt[9], const F R[9], F& c, F& vv) {
   // E_ab = sum_c Rt_ca R_cb
   F tr = F(0);
 #pragma unroll
   for (int i = 0; i < 9; ++i) tr += Rt[i] * R[i];
   F vx = F(0), vy = F(0), vz = F(0);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    vx += Rt[3 * c + 2] * R[3 * c + 1] - Rt[3 * c + 1] * R[3 * c + 2];  // E21 - E12
-    vy += Rt[3 * c + 0] * R[3 * c + 2] - Rt[3 * c + 2] * R[3 * c + 0];  // E02 - E20
-    vz += Rt[3 * c + 1] * R[3 * c + 0] - Rt[3 * c + 0] * R[3 * c + 1];  // E10 - E01
+  for (int k = 0; k < 3; ++k) {
+    vx += Rt[3 * k + 2] * R[3 * k + 1] - Rt[3 * k + 1] * R[3 * k + 2];  // E21 - E12
+    vy += Rt[3 * k + 0] * R[3 * k + 2] - Rt[3 * k + 2] * R[3 * k + 0];  // E02 - E20
+    vz += Rt[3 * k + 1] * R[3 * k + 0] - Rt[3 * k + 0] * R[3 * k + 1];  // E10 - E01
   }
-  const F s = F(0.5) * sqrt(vx * vx + vy * vy + vz * vz);
-  const F c = F(0.5) * (tr - F(1));
-  return atan2(s, c);
+  vv = vx * vx + vy * vy + vz * vz;
+  c = F(0.5) * (tr - F(1));
+}
+template <class F>
+__device__ __forceinline__ F geodesic(const F Rt[9], const F R[9]) {
+  F c, vv;
+  geodesic_parts(Rt, R, c, vv);
+  return atan2(F(0.5) * sqrt(vv), c);
 }
 
 // Rotation vector w = log(M) of a rotation M (world-frame LM residual).

@@ -11,6 +11,9 @@
 // contiguous bytes per warp per joint), runs the FP32 DH chain for its four
 // candidates in registers, and writes one uchar4 mask word, one float4 of costs
 // and two float4 of errors.
+#include <cmath>
+#include <type_traits>
+
 #include "collide.cuh"
 #include "internal.h"
 
@@ -23,6 +26,10 @@ constexpr int kMaskTasksPerWarp = 4;  // default tasks per warp
 
 struct MaskArgs {
   float tau_pos, tau_rot;
+  // the pose test without a root or atan2: |dp|^2 > tau_pos^2, and (for tau_rot <
+  // pi / 2) angle > tau_rot <=> c <= 0 or |v|^2 > 4 c^2 tan^2 tau_rot (geodesic_parts)
+  float tau_pos2, tan2_rot;
+  int rot_fast;
   float pen_table[8];  // [limit bit | pose bit << 1 | collision bit << 2]: each the FP64 sum
                        // of its costs in that order, rounded once
   double near_margin;
@@ -67,7 +74,9 @@ __device__ __forceinline__ void fk_caps(const RobotF& rb, const GeoF& g, const f
   }
 }
 
-template <int NJ, bool COLL>
+// ERR: also the pose errors themselves (cpp_mask with an error buffer); the
+// decision is the same either way, so every path masks alike.
+template <int NJ, bool COLL, bool ERR>
 __device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, const float* q,
                                          int n, bool pad, const float Rt[9], const float pt[3],
                                          const GeoF* g, bool want_clear, uint8_t& bits,
@@ -105,9 +114,18 @@ __device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, co
     fk_f32<NJ>(rb, q, R, p);
   }
   const float dx = p[0] - pt[0], dy = p[1] - pt[1], dz = p[2] - pt[2];
-  epos = sqrtf(dx * dx + dy * dy + dz * dz);
-  erot = geodesic<float>(Rt, R);
-  if (epos > a.tau_pos || erot > a.tau_rot) b |= CPP_MASK_POSE;
+  const float d2 = dx * dx + dy * dy + dz * dz;
+  float c, vv;
+  geodesic_parts<float>(Rt, R, c, vv);
+  const bool rot_fail = a.rot_fast ? (c <= 0.f || vv > 4.f * c * c * a.tan2_rot)
+                                   : atan2f(0.5f * sqrtf(vv), c) > a.tau_rot;
+  if (d2 > a.tau_pos2 || rot_fail) b |= CPP_MASK_POSE;
+  if (ERR) {
+    epos = sqrtf(d2);
+    erot = atan2f(0.5f * sqrtf(vv), c);
+  } else {
+    epos = erot = 0.f;
+  }
   bits = (uint8_t)b;
   const bool lim = (b & (CPP_MASK_OUT | CPP_MASK_NEAR)) != 0, pose = (b & CPP_MASK_POSE) != 0;
   const bool coll = (b & CPP_MASK_COLLIDE) != 0;
@@ -121,7 +139,7 @@ __device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, co
 // registers, a few spills; 0.86 -> 0.81 ms with the layer minima on the 304-request
 // batch, four measured slower) and four for the collision variant (64 registers;
 // two at 117 registers were 1.1 ms slower per batch).
-template <int NJ, bool COLL, class Src>
+template <int NJ, bool COLL, bool ERR, class Src>
 __global__ void __launch_bounds__(kMaskThreads, COLL ? 4 : 3) mask_kernel(const __grid_constant__ Src src,
                                                              const MaskArgs a) {
   const Req& rq = src.req(blockIdx.y);
@@ -174,13 +192,13 @@ __global__ void __launch_bounds__(kMaskThreads, COLL ? 4 : 3) mask_kernel(const 
         if (!NJ && j >= n) break;
         q[j] = c == 0 ? qv[j].x : c == 1 ? qv[j].y : c == 2 ? qv[j].z : qv[j].w;
       }
-      mask_one<NJ, COLL>(rb, a, q, n, k0 + c >= rq.K, Rt, pt, g, rq.clear != nullptr, bits[c],
+      mask_one<NJ, COLL, ERR>(rb, a, q, n, k0 + c >= rq.K, Rt, pt, g, rq.clear != nullptr, bits[c],
                          cost[c], ep[c], er[c], cl[c]);
     }
     const size_t o = (size_t)i * rq.Kp + k0;
     *reinterpret_cast<uchar4*>(rq.mask + o) = make_uchar4(bits[0], bits[1], bits[2], bits[3]);
     *reinterpret_cast<float4*>(rq.pen + o) = make_float4(cost[0], cost[1], cost[2], cost[3]);
-    if (rq.err) {
+    if (ERR && rq.err) {
       float4* e = reinterpret_cast<float4*>(rq.err + 2 * o);
       e[0] = make_float4(ep[0], er[0], ep[1], er[1]);
       e[1] = make_float4(ep[2], er[2], ep[3], er[3]);
@@ -251,6 +269,9 @@ static MaskArgs make_mask_args(const cpp_params_t& P) {
   MaskArgs a;
   a.tau_pos = (float)P.tau_pos;
   a.tau_rot = (float)P.tau_rot;
+  a.tau_pos2 = (float)(P.tau_pos * P.tau_pos);
+  a.rot_fast = P.tau_rot < 1.5 ? 1 : 0;  // below pi / 2: tan is finite and increasing
+  a.tan2_rot = a.rot_fast ? (float)(std::tan(P.tau_rot) * std::tan(P.tau_rot)) : 0.f;
   for (int m = 0; m < 8; ++m) {
     double c = 0.0;
     if (m & 1) c += P.pen_limit;
@@ -263,38 +284,46 @@ static MaskArgs make_mask_args(const cpp_params_t& P) {
   return a;
 }
 
-template <bool COLL, class Src>
+template <bool COLL, bool ERR, class Src>
 static void launch_mask_c(const Src& src, int n, dim3 grid, const MaskArgs& a, cudaStream_t st) {
   switch (n) {
-    case 6: mask_kernel<6, COLL, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
-    case 7: mask_kernel<7, COLL, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
-    case 9: mask_kernel<9, COLL, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
-    default: mask_kernel<0, COLL, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+    case 6: mask_kernel<6, COLL, ERR, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+    case 7: mask_kernel<7, COLL, ERR, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+    case 9: mask_kernel<9, COLL, ERR, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
+    default: mask_kernel<0, COLL, ERR, Src><<<grid, kMaskThreads, 0, st>>>(src, a); break;
   }
 }
 
+// err: some request has an error buffer (only cpp_mask's single request can)
 template <class Src>
 static cudaError_t launch_mask_t(const Src& src, int n, int nreq, long long max_tasks,
-                                 const cpp_params_t& P, bool coll, int tasks_per_warp,
+                                 const cpp_params_t& P, bool coll, bool err, int tasks_per_warp,
                                  cudaStream_t st) {
   MaskArgs a = make_mask_args(P);
   a.tasks_per_warp = tasks_per_warp > 0 ? tasks_per_warp : kMaskTasksPerWarp;
   const long long per_block = (long long)kMaskWarps * a.tasks_per_warp;
   dim3 grid((unsigned)((max_tasks + per_block - 1) / per_block), (unsigned)nreq);
-  if (coll) launch_mask_c<true>(src, n, grid, a, st);
-  else launch_mask_c<false>(src, n, grid, a, st);
+  if constexpr (std::is_same<Src, SingleSrc>::value) {
+    if (err) {
+      if (coll) launch_mask_c<true, true>(src, n, grid, a, st);
+      else launch_mask_c<false, true>(src, n, grid, a, st);
+      return cudaGetLastError();
+    }
+  }
+  if (coll) launch_mask_c<true, false>(src, n, grid, a, st);
+  else launch_mask_c<false, false>(src, n, grid, a, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mask(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st) {
   const long long tasks = (long long)s.r.T * ((s.r.Kp + kMaskBlockK - 1) / kMaskBlockK);
-  return launch_mask_t(s, s.r.n, 1, tasks, P, s.has_geo != 0, 0, st);
+  return launch_mask_t(s, s.r.n, 1, tasks, P, s.has_geo != 0, s.r.err != nullptr, 0, st);
 }
 
 cudaError_t launch_mask_batch(const BatchSrc& s, int n, int nreq, long long max_tasks,
                               const cpp_params_t& P, bool any_geo, cudaStream_t st,
                               int tasks_per_warp) {
-  return launch_mask_t(s, n, nreq, max_tasks, P, any_geo, tasks_per_warp, st);
+  return launch_mask_t(s, n, nreq, max_tasks, P, any_geo, false, tasks_per_warp, st);
 }
 
 long long mask_tasks(int T, int Kp) {
