@@ -30,9 +30,9 @@
 //    band of estimated search time, so short requests never wait for long
 //    ones), and each search runs in the form with the highest edge rate per SM
 //    that stays within search_budget_ms (one CTA, wide clusters of 512 or 256
-//    successors per CTA, clusters of 128): the search is launched once per K
-//    bucket and form, the launches forked onto auxiliary streams of the batch's
-//    stream so they run side by side.
+//    successors per CTA, clusters of 128, else of 64; pick_search_form): the
+//    search is launched once per K bucket and form, the launches forked onto
+//    auxiliary streams of the batch's stream so they run side by side.
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
