@@ -365,6 +365,17 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
   return ok != 0;
 }
 
+// Programmatic dependent launch (the single-request chain of stages): a kernel
+// launched with the programmatic-serialization attribute may be scheduled while
+// its predecessor in the stream finishes. pdl_trigger() lets the next kernel be
+// scheduled once every CTA of this one has started; pdl_wait() blocks until the
+// predecessor has completed and its writes are visible. Both return at once in
+// an ordinary launch.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -54,6 +54,8 @@ bool dp_supported(int n, int Kp) {
 // ------------------------------------------------------------------ layer minimum
 template <class Src>
 __global__ void __launch_bounds__(256) layer_min_kernel(const __grid_constant__ Src src) {
+  pdl_trigger();
+  pdl_wait();
   const Req& rq = src.req(blockIdx.y);
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -69,6 +71,8 @@ __global__ void __launch_bounds__(256) layer_min_kernel(const __grid_constant__ 
 // ------------------------------------------------------------------ backtrack
 template <class Src>
 __global__ void __launch_bounds__(kBtThreads) dp_backtrack_kernel(const __grid_constant__ Src src) {
+  pdl_trigger();
+  pdl_wait();
   const Req& rq = src.req(blockIdx.x);
   const int T = rq.T, K = rq.K, Kb = rq.Kb, n = rq.n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -188,8 +192,8 @@ static cudaError_t launch_dp_t(const Src& s, unsigned stages, int objective, int
   cudaError_t e = cudaSuccess;
   if (stages & CPP_STAGE_LAYER_MIN) {
     dim3 grid((unsigned)((max_T + 7) / 8), (unsigned)nreq);
-    layer_min_kernel<Src><<<grid, 256, 0, st>>>(s);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_k(layer_min_kernel<Src>, grid, dim3(256), 0, st, 1, kPdl<Src>, s)) != cudaSuccess)
+      return e;
   }
   if (stages & CPP_STAGE_DP_FORWARD) {
     e = objective == CPP_DP_MINMAX ? launch_forward_minmax(s, n, nreq, max_Kp, form, cpc, st)
@@ -198,8 +202,8 @@ static cudaError_t launch_dp_t(const Src& s, unsigned stages, int objective, int
   }
   if (stages & CPP_STAGE_BACKTRACK) {
     if ((e = allow_smem(dp_backtrack_kernel<Src>, 2 * kBtChunkBytes)) != cudaSuccess) return e;
-    dp_backtrack_kernel<Src><<<nreq, kBtThreads, 2 * kBtChunkBytes, st>>>(s);
-    e = cudaGetLastError();
+    e = launch_k(dp_backtrack_kernel<Src>, dim3((unsigned)nreq), dim3(kBtThreads),
+                 2 * kBtChunkBytes, st, 1, kPdl<Src>, s);
   }
   return e;
 }

@@ -117,6 +117,8 @@ __device__ __forceinline__ void load_rec(const float* p, float (&v)[NW]) {
 
 template <int NJ, int R, int OBJ, class Src>
 __global__ void __launch_bounds__(kDp3Threads, 2) dp3_forward_kernel(const __grid_constant__ Src src) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int NW = Rec<NJ>::NW, NP = Rec<NJ>::NP;
   const Req& rq = src.req(blockIdx.x);
   const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb;
@@ -362,6 +364,8 @@ __device__ __forceinline__ void bulk_s2cluster(uint32_t dst, uint32_t src, uint3
 template <int NJ, int R, int OBJ, class Src>
 __global__ void __launch_bounds__(kDpcThreads) dpc_forward_kernel(const __grid_constant__ Src src,
                                                                    const int CS) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int NW = Rec<NJ>::NW, NP = Rec<NJ>::NP, S = 32 * R;
   // how records travel: 32 and 64 successors per CTA (the latency forms) as one
   // bulk copy per owner CTA from a staging span written by warp 0; 128 per CTA
@@ -670,6 +674,8 @@ __device__ __forceinline__ void st_async_f32(uint32_t addr, float v, uint32_t ba
 template <int NJ, int R, int OBJ, class Src>
 __global__ void __launch_bounds__(kDp3Threads, 2) dpx_forward_kernel(const __grid_constant__ Src src,
                                                                       const int CS) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int NW = Rec<NJ>::NW, NP = Rec<NJ>::NP, S = R * kDp3Group;
   const uint32_t crank = cluster_rank();
   const Req& rq = src.req(blockIdx.x / CS);
@@ -882,6 +888,8 @@ __global__ void __launch_bounds__(kDp3Threads, 2) dpx_forward_kernel(const __gri
 // shared memory instead of registers.
 template <int OBJ, class Src>
 __global__ void __launch_bounds__(kDpThreads) dp_forward_generic(const __grid_constant__ Src src) {
+  pdl_trigger();
+  pdl_wait();
   const Req& rq = src.req(blockIdx.x);
   const int T = rq.T, K = rq.K, Kp = rq.Kp, Kb = rq.Kb, n = rq.n;
   extern __shared__ __align__(16) float sm[];
@@ -933,8 +941,8 @@ static cudaError_t launch_fwd3_r(const Src& s, int nreq, int max_Kp, cudaStream_
   const size_t smem = dp3_smem_bytes(NJ, max_Kp, R);
   cudaError_t e = allow_smem(dp3_forward_kernel<NJ, R, OBJ, Src>, smem);
   if (e != cudaSuccess) return e;
-  dp3_forward_kernel<NJ, R, OBJ, Src><<<nreq, kDp3Threads, smem, st>>>(s);
-  return cudaGetLastError();
+  return launch_k(dp3_forward_kernel<NJ, R, OBJ, Src>, dim3((unsigned)nreq), dim3(kDp3Threads), smem,
+                  st, 1, kPdl<Src>, s);
 }
 
 template <int NJ, int R, int OBJ, class Src>
@@ -943,19 +951,8 @@ static cudaError_t launch_fwdx_r(const Src& s, int nreq, int max_Kp, cudaStream_
   const size_t smem = dpx_smem_bytes(NJ, max_Kp, R);
   cudaError_t e = allow_smem(dpx_forward_kernel<NJ, R, OBJ, Src>, smem);
   if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nreq * CS));
-  cfg.blockDim = dim3(kDp3Threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)CS;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, dpx_forward_kernel<NJ, R, OBJ, Src>, s, CS);
+  return launch_k(dpx_forward_kernel<NJ, R, OBJ, Src>, dim3((unsigned)(nreq * CS)), dim3(kDp3Threads),
+                  smem, st, (unsigned)CS, kPdl<Src>, s, CS);
 }
 
 template <int NJ, int R, int OBJ, class Src>
@@ -969,19 +966,8 @@ static cudaError_t launch_fwdc_r(const Src& s, int nreq, int max_Kp, cudaStream_
                              cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nreq * CS));
-  cfg.blockDim = dim3(kDpcThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)CS;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, dpc_forward_kernel<NJ, R, OBJ, Src>, s, CS);
+  return launch_k(dpc_forward_kernel<NJ, R, OBJ, Src>, dim3((unsigned)(nreq * CS)), dim3(kDpcThreads),
+                  smem, st, (unsigned)CS, kPdl<Src>, s, CS);
 }
 
 // Requests that one wave of clusters covers use the cluster form (lower latency);
@@ -1106,8 +1092,8 @@ static cudaError_t launch_forward_t(const Src& s, int n, int nreq, int max_Kp, i
   const size_t smem = dp_smem_bytes(n, max_Kp);
   cudaError_t e = allow_smem(dp_forward_generic<OBJ, Src>, smem);
   if (e != cudaSuccess) return e;
-  dp_forward_generic<OBJ, Src><<<nreq, kDpThreads, smem, st>>>(s);
-  return cudaGetLastError();
+  return launch_k(dp_forward_generic<OBJ, Src>, dim3((unsigned)nreq), dim3(kDpThreads), smem, st, 1,
+                  kPdl<Src>, s);
 }
 
 }  // namespace cppflow

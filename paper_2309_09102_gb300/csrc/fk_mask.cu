@@ -142,6 +142,8 @@ __device__ __forceinline__ void mask_one(const RobotF& rb, const MaskArgs& a, co
 template <int NJ, bool COLL, bool ERR, class Src>
 __global__ void __launch_bounds__(kMaskThreads, COLL ? 4 : 3) mask_kernel(const __grid_constant__ Src src,
                                                              const MaskArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const Req& rq = src.req(blockIdx.y);
   __shared__ RobotF rb;
   __shared__ GeoF gsh;

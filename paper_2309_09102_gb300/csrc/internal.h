@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <math_constants.h>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -102,6 +103,39 @@ size_t geo_bytes();                    // sizeof(GeoF)
 // device form (FP32, capsules sorted by frame) in `out` (geo_bytes() bytes).
 // Returns false with a message in err (>= 160 bytes) when the model is invalid.
 bool make_geo(const cpp_geometry_t& g, int n, void* out, char* err);
+
+// Launch of `kernel` with an optional thread-block cluster (cluster > 1) and, for
+// the single-request chain (pdl), programmatic serialization after the previous
+// kernel in the stream (the kernels call pdl_trigger / pdl_wait first).
+template <class Src>
+constexpr bool kPdl = std::is_same<Src, SingleSrc>::value;
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, unsigned cluster, bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  unsigned na = 0;
+  if (cluster > 1) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = cluster;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  if (pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 // ------------------------------------------------------------------ workspace layouts
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

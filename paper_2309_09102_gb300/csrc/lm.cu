@@ -122,6 +122,8 @@ __global__ void __launch_bounds__(32) robot_views_kernel(const cpp_robot_t* robo
 template <int NJ, class F, class Src>
 __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ Src src,
                                                          const LmArgs a) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int MJ = NJ ? NJ : kMaxJ;
   constexpr int MT = MJ * (MJ + 1) / 2;  // packed lower triangle
   constexpr bool DYN = std::is_same<Src, BatchSrc>::value;
@@ -380,6 +382,8 @@ __global__ void __launch_bounds__(kLmThreads) lm_kernel(const __grid_constant__ 
 template <bool CL, class Src>
 __global__ void __launch_bounds__(CL ? kChkThreads : kChkThreads * kChkCluster)
     check_kernel(const __grid_constant__ Src src, const CheckArgs a) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int NWARP = (CL ? kChkThreads : kChkThreads * kChkCluster) / 32;
   const Req& rq = src.req(CL ? blockIdx.x / kChkCluster : blockIdx.x);
   const uint32_t crank = CL ? cluster_rank() : 0;
@@ -876,7 +880,8 @@ static cudaError_t launch_lm_kernel(const Src& s, int max_T, const LmArgs& a, cu
     if (e != cudaSuccess) return e;
     kernel<<<blocks, kLmThreads, 0, st>>>(s, a);
   } else {
-    kernel<<<(unsigned)((max_T + kLmThreads - 1) / kLmThreads), kLmThreads, 0, st>>>(s, a);
+    return launch_k(kernel, dim3((unsigned)((max_T + kLmThreads - 1) / kLmThreads)), dim3(kLmThreads),
+                    0, st, 1, kPdl<Src>, s, a);
   }
   return cudaGetLastError();
 }
@@ -977,18 +982,8 @@ static cudaError_t launch_check_t(const Src& s, int nreq, const cpp_params_t& P,
     check_kernel<false, Src><<<nreq, kChkThreads * kChkCluster, 0, st>>>(s, a);
     return cudaGetLastError();
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nreq * kChkCluster));
-  cfg.blockDim = dim3(kChkThreads);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kChkCluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, check_kernel<true, Src>, s, a);
+  return launch_k(check_kernel<true, Src>, dim3((unsigned)(nreq * kChkCluster)), dim3(kChkThreads), 0,
+                  st, kChkCluster, kPdl<Src>, s, a);
 }
 cudaError_t launch_check(const SingleSrc& s, const cpp_params_t& P, cudaStream_t st) {
   return launch_check_t(s, 1, P, st);
