@@ -20,9 +20,13 @@ def plain():
     return problems.build(synth.PLAIN)
 
 
-def test_rounds_equal_the_same_refinement_in_one_plan(plain):
+@pytest.mark.parametrize("pinned", [None, 0])
+def test_rounds_equal_the_same_refinement_in_one_plan(plain, pinned):
     """R improvement rounds after the first pass run the kernels of a plan with
-    smooth_rounds = R; when every round is published the result is bit-identical."""
+    smooth_rounds = R; when every round is published the result is bit-identical.
+    With the default pinned pool each round's results pass through the launch's pinned
+    staging; with none (pinned = 0) through pageable memory; either way they end in
+    the request's own buffer."""
     pb = plain
     R = 3
     _, cp = params_pair(lm_iters=pb.w.lm_iters)
@@ -30,7 +34,7 @@ def test_rounds_equal_the_same_refinement_in_one_plan(plain):
     rob = cppflow.robot_from_arm(pb.arm)
     first = run_plan(rob, cp, pb.cand, pb.targets, pb.K)
     ref = run_plan(rob, cpR, pb.cand, pb.targets, pb.K)
-    with cppflow.Server(cp, hbm_budget=1 << 30) as srv:
+    with cppflow.Server(cp, hbm_budget=1 << 30, pinned_bytes=pinned) as srv:
         t = srv.submit(rob, pb.cand, pb.targets, pb.K, anytime_rounds=R)
         st, res = srv.wait(t)
         stats = srv.stats()
