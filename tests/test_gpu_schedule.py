@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import problems
-from gpu_util import TAU_POS, TAU_ROT, dev, params_pair, run_mask, torch
+from gpu_util import TAU_POS, TAU_ROT, dev, params_pair, run_mask, run_plan, torch
 from paper_2309_09102_gb300 import cppflow, synth
 
 pytestmark = pytest.mark.gpu
@@ -132,6 +132,32 @@ def test_graph_replay_equals_run(batch_setup):
     # the legacy default stream cannot be captured
     rc = cppflow.lib().cpp_batch_capture(S["batch"].handle, cppflow.STAGE_ALL, None)
     assert rc == cppflow.ERR_INVALID_ARG
+
+
+def test_graph_replay_equals_each_plan_alone(batch_setup):
+    """The whole uneven batch under a tuned schedule, captured into one CUDA graph
+    (cluster groups on forked streams, the persistent LM grid) and replayed: every
+    request's plan equals cpp_plan run on that request alone, bit for bit, and its
+    search equals the oracle's FP32 search."""
+    S = batch_setup
+    S["batch"].tune(None, S["stream"])
+    try:
+        S["batch"].capture(cppflow.STAGE_ALL, S["stream"])
+        clear(S)
+        torch().cuda.synchronize()
+        S["batch"].replay(S["stream"])
+        S["stream"].synchronize()
+        got = results(S)
+        for r, pb in enumerate(S["pbs"]):
+            alone = run_plan(S["robots"][r], S["cp"], pb.cand, pb.targets, pb.K)
+            np.testing.assert_array_equal(got[r]["sel"], alone["sel"], err_msg=f"request {r}")
+            np.testing.assert_array_equal(got[r]["q"], alone["q"])
+            np.testing.assert_array_equal(got[r]["err"], alone["err"])
+            assert float(got[r]["best"][0]) == float(alone["best"])
+            g = run_mask(S["robots"][r], S["cp"], pb.cand, pb.targets, pb.K)
+            np.testing.assert_array_equal(got[r]["sel"], oracle.dp_f32(pb.cand, g.pen, pb.K)["sel"])
+    finally:
+        S["batch"].set_split(0.0, 0, S["stream"])
 
 
 def test_tuner_and_its_table(batch_setup, tmp_path):
