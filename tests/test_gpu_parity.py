@@ -84,6 +84,31 @@ def test_mask_matches_oracle(T, K, n, wrist):
     assert guarded <= max(2, m.size // 1000)
 
 
+@pytest.mark.parametrize("T,K,n,wrist,tau_deg", [(12, 300, 7, False, 5.0), (9, 130, 9, True, 5.0),
+                                                  (6, 200, 6, False, 2.0), (4, 70, 12, False, 95.0)])
+def test_mask_decides_alike_with_and_without_errors(T, K, n, wrist, tau_deg):
+    """The mask stage with an error buffer (cpp_mask returning the pose errors) and without
+    one (every plan path) takes the pose decision the same way, from squared distances and
+    the geodesic's trace and skew parts, so mask bits and node costs are identical, also at
+    a rotation threshold above pi / 2 (the atan2 form of the test)."""
+    tt = torch()
+    pb = problems.small(T=T, K=K, n=n, wrist=wrist, seed=T * 7 + K)
+    _, cp = params_pair(tau_pos=0.05, tau_rot=math.radians(tau_deg))
+    Kp = pb.cand.shape[2]
+    outs = []
+    for want_err in (True, False):
+        m = tt.empty(T, Kp, dtype=tt.uint8, device="cuda:0")
+        p = tt.empty(T, Kp, dtype=tt.float32, device="cuda:0")
+        e = tt.empty(T, Kp, 2, dtype=tt.float32, device="cuda:0") if want_err else None
+        cppflow.mask(crob(pb.arm), cp, dev(pb.cand), dev(pb.targets), pb.K, m, p, e)
+        tt.cuda.synchronize()
+        outs.append((m.cpu().numpy(), p.cpu().numpy()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    pose = (outs[0][0] & np.uint8(cppflow.MASK_POSE)) != 0
+    assert pose.any() and not pose.all()  # the thresholds split the candidates
+
+
 def test_mask_nonfinite_and_padding():
     pb = problems.small(T=4, K=30, seed=5)
     cand = pb.cand.copy()
