@@ -99,8 +99,7 @@ cpp_status cpp_dp_search_static(const float* cand, const float* pen, int32_t T, 
   // CPP_ERR_TIMEOUT): the rows after that step keep an earlier call's values,
   // and the backtracking clamps every index it reads from them to [0, K).
   char* ws = static_cast<char*>(base);
-  SingleSrc s;
-  memset(&s, 0, sizeof(s));
+  SingleSrc s{};  // value-initialised: every field not set below is zero
   s.r.T = T; s.r.K = K; s.r.Kp = Kp; s.r.n = n; s.r.Kb = bp_stride(Kp);
   s.r.cand = cand; s.r.pen = const_cast<float*>(pen);
   s.r.pen_min = reinterpret_cast<float*>(ws + L.pen_min);

@@ -565,7 +565,7 @@ cudaError_t cpp_server::search(Launch* L, const BatchSrc& src, cudaStream_t st) 
 cpp_status cpp_server::enqueue(Launch* L) {
   const cudaStream_t st = streams[L->stream];
   const int count = (int)L->reqs.size();
-  const int n = L->n, max_T = L->max_T, max_Kp = L->max_Kp;
+  const int n = L->n, max_T = L->max_T;
   const long long max_tasks = L->max_tasks;
   const bool any_geo = L->any_geo;
   char* tab_d = d_arena + L->tab_off;
